@@ -1,0 +1,810 @@
+/*
+ * lb_oracle.c -- plain, slow CPU FP64 oracle for the transformation of a
+ * GKSL (Lindblad) generator into the real linear system dv/dt = (Q+R)v + K
+ * (Meyerov et al., "Transforming Lindblad Equations into Systems of
+ * Real-Valued Linear Equations", Sec. 2, Eqs. (02)-(09)).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library's product path may call,
+ * link or load this file; only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark do.  It shares no code, header, table or
+ * helper with the CUDA path.
+ *
+ * What it computes, and how (deliberately naive):
+ *   * the SU(N) basis {F_i} of Sec. 2 as explicit sparse N x N matrices
+ *     (S^(j,k), J^(j,k), D^l; D^l is read as the Hermitian, orthonormal
+ *     matrix (sum_{k<=l} e_k e_k^T - l e_{l+1} e_{l+1}^T)/sqrt(l(l+1)), the
+ *     printed prefactor i/sqrt(l(l+1)) contradicts Tr(F_n F_m) = delta_nm);
+ *     0-based order: S block (pairs j<k lexicographic), J block, D_1..D_{N-1};
+ *   * f_mns = -i Tr(F_s [F_m,F_n]) and d_mns = Tr(F_s {F_m,F_n}) (Eq. (05))
+ *     by multiplying the sparse basis matrices and projecting the commutator
+ *     and anticommutator back onto the basis -- no closed-form rules;
+ *   * expansion coefficients a_j = Tr(F_j A) (Eq. (02));
+ *   * q_sn = sum_m h_m f_mns (Eq. (07));
+ *   * k_s = (i/N) sum_jk a_jk f_jks (Eq. (08), with the sum over channels
+ *     folded into the Kossakowski matrix a_jk = sum_p gamma_p l_pj conj(l_pk));
+ *   * r_sn = -1/4 sum_jkl a_jk (z_jln f_kls + conj(z_kln) f_jls) (Eq. (09)
+ *     with z = f + i d, Eq. (06)); the prefactor -1/4 (not the printed -1/2)
+ *     is the one the brute-force definition Tr(F_s L_D(F_n)) fixes for this
+ *     two-term form;
+ *   * classical fourth-order Runge-Kutta for dv/dt = A v + K (Sec. 4, step 3).
+ *
+ * Values are "nonzero" when |x| > 1e-12 * (largest |x| of the tensor).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------ basis */
+
+typedef struct {
+    int nnz;          /* number of stored entries            */
+    int *row, *col;   /* positions                           */
+    double *re, *im;  /* values                              */
+} sp_mat;
+
+typedef struct {
+    int N;
+    int64_t M, P;
+    sp_mat *F;        /* F[0..M-1] */
+    /* ordered nonzero triples of f and d: (m, n, s, value) */
+    int64_t nf, nd;
+    int32_t *f_idx;   /* 3 * nf */
+    double *f_val;
+    int32_t *d_idx;   /* 3 * nd */
+    double *d_val;
+} ora_ctx;
+
+static void sp_alloc(sp_mat *A, int nnz) {
+    A->nnz = nnz;
+    A->row = (int *)malloc(sizeof(int) * (size_t)nnz);
+    A->col = (int *)malloc(sizeof(int) * (size_t)nnz);
+    A->re = (double *)calloc((size_t)nnz, sizeof(double));
+    A->im = (double *)calloc((size_t)nnz, sizeof(double));
+}
+
+static void sp_free(sp_mat *A) {
+    free(A->row); free(A->col); free(A->re); free(A->im);
+}
+
+/* Sec. 2, Eqs. for S^(j,k), J^(j,k), D^l (0-based indices). */
+static void build_basis(ora_ctx *c) {
+    int N = c->N;
+    int64_t P = c->P, i = 0;
+    double r2 = 1.0 / sqrt(2.0);
+    c->F = (sp_mat *)calloc((size_t)c->M, sizeof(sp_mat));
+    for (int a = 0; a < N; ++a)
+        for (int b = a + 1; b < N; ++b, ++i) {
+            sp_mat *S = &c->F[i];
+            sp_alloc(S, 2);
+            S->row[0] = a; S->col[0] = b; S->re[0] = r2;
+            S->row[1] = b; S->col[1] = a; S->re[1] = r2;
+            sp_mat *J = &c->F[P + i];
+            sp_alloc(J, 2);
+            J->row[0] = a; J->col[0] = b; J->im[0] = -r2;  /* -i/sqrt2 e_a e_b^T */
+            J->row[1] = b; J->col[1] = a; J->im[1] = r2;   /* +i/sqrt2 e_b e_a^T */
+        }
+    for (int l = 1; l < N; ++l) {
+        sp_mat *D = &c->F[2 * P + (l - 1)];
+        double nrm = 1.0 / sqrt((double)l * (double)(l + 1));
+        sp_alloc(D, l + 1);
+        for (int k = 0; k < l; ++k) {
+            D->row[k] = k; D->col[k] = k; D->re[k] = nrm;
+        }
+        D->row[l] = l; D->col[l] = l; D->re[l] = -(double)l * nrm;
+    }
+}
+
+/* Dense N x N complex scratch with a list of touched positions. */
+typedef struct {
+    int N;
+    double *re, *im;
+    char *mark;
+    int *touched;
+    int nt;
+} scratch;
+
+static void scr_init(scratch *w, int N) {
+    w->N = N;
+    w->re = (double *)calloc((size_t)N * N, sizeof(double));
+    w->im = (double *)calloc((size_t)N * N, sizeof(double));
+    w->mark = (char *)calloc((size_t)N * N, 1);
+    w->touched = (int *)malloc(sizeof(int) * (size_t)N * N);
+    w->nt = 0;
+}
+
+static void scr_free(scratch *w) {
+    free(w->re); free(w->im); free(w->mark); free(w->touched);
+}
+
+static void scr_add(scratch *w, int r, int c, double xr, double xi) {
+    int p = r * w->N + c;
+    if (!w->mark[p]) { w->mark[p] = 1; w->touched[w->nt++] = p; }
+    w->re[p] += xr;
+    w->im[p] += xi;
+}
+
+static void scr_clear(scratch *w) {
+    for (int t = 0; t < w->nt; ++t) {
+        int p = w->touched[t];
+        w->re[p] = 0; w->im[p] = 0; w->mark[p] = 0;
+    }
+    w->nt = 0;
+}
+
+/* Tr(F_s X) = sum_pq (F_s)_pq X_qp for a dense X held in scratch. */
+static void trace_with(const sp_mat *Fs, const double *Xr, const double *Xi,
+                       int N, double *tr, double *ti) {
+    double sr = 0, si = 0;
+    for (int e = 0; e < Fs->nnz; ++e) {
+        int q = Fs->col[e], p = Fs->row[e];
+        double xr = Xr[q * N + p], xi = Xi[q * N + p];
+        sr += Fs->re[e] * xr - Fs->im[e] * xi;
+        si += Fs->re[e] * xi + Fs->im[e] * xr;
+    }
+    *tr = sr; *ti = si;
+}
+
+/* growable triple list */
+typedef struct { int64_t n, cap; int32_t *idx; double *val; } tlist;
+
+static void tl_push(tlist *t, int32_t m, int32_t n, int32_t s, double v) {
+    if (t->n == t->cap) {
+        t->cap = t->cap ? 2 * t->cap : 1024;
+        t->idx = (int32_t *)realloc(t->idx, sizeof(int32_t) * 3 * (size_t)t->cap);
+        t->val = (double *)realloc(t->val, sizeof(double) * (size_t)t->cap);
+    }
+    t->idx[3 * t->n] = m; t->idx[3 * t->n + 1] = n; t->idx[3 * t->n + 2] = s;
+    t->val[t->n] = v;
+    t->n++;
+}
+
+/* index of the pair (a,b), a<b, in lexicographic order */
+static int64_t pair_index(int N, int a, int b) {
+    return (int64_t)a * (2 * N - a - 1) / 2 + (b - a - 1);
+}
+
+/*
+ * Eq. (05): enumerate all ordered (m,n,s) with f_mns or d_mns nonzero.
+ * For every ordered pair (m,n) whose product F_m F_n can be nonzero, form
+ * P = F_m F_n explicitly, then [F_m,F_n] = P - P^dagger and
+ * {F_m,F_n} = P + P^dagger (the F are Hermitian), and take traces with every
+ * basis element whose support meets the result.
+ */
+static void enumerate_fd(ora_ctx *c) {
+    int N = c->N;
+    int64_t M = c->M, P = c->P;
+    /* elements touching each index v (support rows) */
+    int **touch = (int **)malloc(sizeof(int *) * (size_t)N);
+    int *ntouch = (int *)calloc((size_t)N, sizeof(int));
+    for (int64_t i = 0; i < M; ++i)
+        for (int e = 0; e < c->F[i].nnz; ++e) ntouch[c->F[i].row[e]]++;
+    for (int v = 0; v < N; ++v) touch[v] = (int *)malloc(sizeof(int) * (size_t)(ntouch[v] + 1));
+    int *fill = (int *)calloc((size_t)N, sizeof(int));
+    for (int64_t i = 0; i < M; ++i)
+        for (int e = 0; e < c->F[i].nnz; ++e) {
+            int v = c->F[i].row[e];
+            touch[v][fill[v]++] = (int)i;
+        }
+
+    tlist tf = {0, 0, NULL, NULL}, td = {0, 0, NULL, NULL};
+    scratch Pm, Cm, Am;
+    scr_init(&Pm, N); scr_init(&Cm, N); scr_init(&Am, N);
+    char *cand_mark = (char *)calloc((size_t)M, 1);
+    int64_t *cand = (int64_t *)malloc(sizeof(int64_t) * (size_t)M);
+    char *seen = (char *)calloc((size_t)M, 1);
+    int64_t *nlist = (int64_t *)malloc(sizeof(int64_t) * (size_t)M);
+    double *fraw = NULL, *draw = NULL; /* values before thresholding */
+    int64_t nraw = 0, capraw = 0;
+    int32_t *rawidx = NULL;
+
+    for (int64_t m = 0; m < M; ++m) {
+        const sp_mat *Fm = &c->F[m];
+        /* candidates n: elements whose rows meet the columns of F_m */
+        int64_t nn = 0;
+        for (int e = 0; e < Fm->nnz; ++e) {
+            int v = Fm->col[e];
+            for (int t = 0; t < ntouch[v]; ++t) {
+                int n = touch[v][t];
+                if (!seen[n]) { seen[n] = 1; nlist[nn++] = n; }
+            }
+        }
+        for (int64_t q = 0; q < nn; ++q) {
+            int64_t n = nlist[q];
+            seen[n] = 0;
+            const sp_mat *Fn = &c->F[n];
+            /* P = F_m F_n */
+            for (int e = 0; e < Fm->nnz; ++e)
+                for (int g = 0; g < Fn->nnz; ++g)
+                    if (Fm->col[e] == Fn->row[g]) {
+                        double xr = Fm->re[e] * Fn->re[g] - Fm->im[e] * Fn->im[g];
+                        double xi = Fm->re[e] * Fn->im[g] + Fm->im[e] * Fn->re[g];
+                        scr_add(&Pm, Fm->row[e], Fn->col[g], xr, xi);
+                    }
+            if (Pm.nt == 0) continue;
+            /* C = P - P^dag, A = P + P^dag */
+            for (int t = 0; t < Pm.nt; ++t) {
+                int p = Pm.touched[t], r = p / N, cc = p % N;
+                double pr = Pm.re[p], pi = Pm.im[p];
+                scr_add(&Cm, r, cc, pr, pi);
+                scr_add(&Cm, cc, r, -pr, pi);     /* -(conj P)^T */
+                scr_add(&Am, r, cc, pr, pi);
+                scr_add(&Am, cc, r, pr, -pi);     /* +(conj P)^T */
+            }
+            /* candidate s: pairs on touched off-diagonal positions, all D */
+            int64_t ns = 0;
+            for (int t = 0; t < Cm.nt; ++t) {
+                int p = Cm.touched[t], r = p / N, cc = p % N;
+                if (r == cc) continue;
+                int a = r < cc ? r : cc, b = r < cc ? cc : r;
+                int64_t ps = pair_index(N, a, b);
+                if (!cand_mark[ps]) { cand_mark[ps] = 1; cand[ns++] = ps; }
+                if (!cand_mark[P + ps]) { cand_mark[P + ps] = 1; cand[ns++] = P + ps; }
+            }
+            for (int l = 1; l < N; ++l) {
+                int64_t s = 2 * P + (l - 1);
+                if (!cand_mark[s]) { cand_mark[s] = 1; cand[ns++] = s; }
+            }
+            for (int64_t u = 0; u < ns; ++u) {
+                int64_t s = cand[u];
+                cand_mark[s] = 0;
+                double cr, ci, ar, ai;
+                trace_with(&c->F[s], Cm.re, Cm.im, N, &cr, &ci);
+                trace_with(&c->F[s], Am.re, Am.im, N, &ar, &ai);
+                /* f = -i Tr(F_s C) -> real part = Im Tr(F_s C); d = Tr(F_s A) */
+                double fv = ci, dv = ar;
+                if (fv != 0.0 || dv != 0.0) {
+                    if (nraw == capraw) {
+                        capraw = capraw ? 2 * capraw : 4096;
+                        fraw = (double *)realloc(fraw, sizeof(double) * (size_t)capraw);
+                        draw = (double *)realloc(draw, sizeof(double) * (size_t)capraw);
+                        rawidx = (int32_t *)realloc(rawidx, sizeof(int32_t) * 3 * (size_t)capraw);
+                    }
+                    fraw[nraw] = fv; draw[nraw] = dv;
+                    rawidx[3 * nraw] = (int32_t)m;
+                    rawidx[3 * nraw + 1] = (int32_t)n;
+                    rawidx[3 * nraw + 2] = (int32_t)s;
+                    nraw++;
+                }
+            }
+            scr_clear(&Pm); scr_clear(&Cm); scr_clear(&Am);
+        }
+    }
+    /* threshold relative to the largest magnitude of each tensor */
+    double fmax = 0, dmax = 0;
+    for (int64_t r = 0; r < nraw; ++r) {
+        if (fabs(fraw[r]) > fmax) fmax = fabs(fraw[r]);
+        if (fabs(draw[r]) > dmax) dmax = fabs(draw[r]);
+    }
+    for (int64_t r = 0; r < nraw; ++r) {
+        int32_t *x = &rawidx[3 * r];
+        if (fabs(fraw[r]) > 1e-12 * fmax) tl_push(&tf, x[0], x[1], x[2], fraw[r]);
+        if (fabs(draw[r]) > 1e-12 * dmax) tl_push(&td, x[0], x[1], x[2], draw[r]);
+    }
+    free(fraw); free(draw); free(rawidx);
+    c->nf = tf.n; c->f_idx = tf.idx; c->f_val = tf.val;
+    c->nd = td.n; c->d_idx = td.idx; c->d_val = td.val;
+
+    scr_free(&Pm); scr_free(&Cm); scr_free(&Am);
+    free(cand_mark); free(cand); free(seen); free(nlist);
+    for (int v = 0; v < N; ++v) free(touch[v]);
+    free(touch); free(ntouch); free(fill);
+}
+
+ora_ctx *ora_create(int N) {
+    if (N < 2) return NULL;
+    ora_ctx *c = (ora_ctx *)calloc(1, sizeof(ora_ctx));
+    c->N = N;
+    c->M = (int64_t)N * N - 1;
+    c->P = (int64_t)N * (N - 1) / 2;
+    build_basis(c);
+    enumerate_fd(c);
+    return c;
+}
+
+void ora_destroy(ora_ctx *c) {
+    if (!c) return;
+    for (int64_t i = 0; i < c->M; ++i) sp_free(&c->F[i]);
+    free(c->F);
+    free(c->f_idx); free(c->f_val); free(c->d_idx); free(c->d_val);
+    free(c);
+}
+
+int64_t ora_M(const ora_ctx *c) { return c->M; }
+
+/* Dense copy of basis element i (N x N complex, interleaved re,im). */
+void ora_basis_dense(const ora_ctx *c, int64_t i, double *out) {
+    int N = c->N;
+    memset(out, 0, sizeof(double) * 2 * (size_t)N * N);
+    const sp_mat *A = &c->F[i];
+    for (int e = 0; e < A->nnz; ++e) {
+        size_t p = (size_t)A->row[e] * N + A->col[e];
+        out[2 * p] = A->re[e];
+        out[2 * p + 1] = A->im[e];
+    }
+}
+
+/* which: 0 = f, 1 = d.  ordered != 0 -> all ordered triples, else only m<=n<=s. */
+int64_t ora_nnz(const ora_ctx *c, int which, int ordered) {
+    int64_t n = which ? c->nd : c->nf;
+    const int32_t *x = which ? c->d_idx : c->f_idx;
+    if (ordered) return n;
+    int64_t k = 0;
+    for (int64_t r = 0; r < n; ++r)
+        if (x[3 * r] <= x[3 * r + 1] && x[3 * r + 1] <= x[3 * r + 2]) k++;
+    return k;
+}
+
+static const int32_t *g_sort_idx;
+static int cmp_triple(const void *pa, const void *pb) {
+    int64_t a = *(const int64_t *)pa, b = *(const int64_t *)pb;
+    const int32_t *x = &g_sort_idx[3 * a], *y = &g_sort_idx[3 * b];
+    for (int q = 0; q < 3; ++q) {
+        if (x[q] < y[q]) return -1;
+        if (x[q] > y[q]) return 1;
+    }
+    return 0;
+}
+
+/* Canonical list (m<=n<=s), sorted lexicographically, with values. */
+void ora_export(const ora_ctx *c, int which, int32_t *idx3, double *val) {
+    int64_t n = which ? c->nd : c->nf;
+    const int32_t *x = which ? c->d_idx : c->f_idx;
+    const double *v = which ? c->d_val : c->f_val;
+    int64_t k = 0;
+    int64_t *ord = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    for (int64_t r = 0; r < n; ++r)
+        if (x[3 * r] <= x[3 * r + 1] && x[3 * r + 1] <= x[3 * r + 2]) ord[k++] = r;
+    g_sort_idx = x;
+    qsort(ord, (size_t)k, sizeof(int64_t), cmp_triple);
+    for (int64_t q = 0; q < k; ++q) {
+        int64_t r = ord[q];
+        idx3[3 * q] = x[3 * r]; idx3[3 * q + 1] = x[3 * r + 1]; idx3[3 * q + 2] = x[3 * r + 2];
+        val[q] = v[r];
+    }
+    free(ord);
+}
+
+/* All ordered triples (unsorted) -- for symmetry checks in the tests. */
+void ora_export_ordered(const ora_ctx *c, int which, int32_t *idx3, double *val) {
+    int64_t n = which ? c->nd : c->nf;
+    memcpy(idx3, which ? c->d_idx : c->f_idx, sizeof(int32_t) * 3 * (size_t)n);
+    memcpy(val, which ? c->d_val : c->f_val, sizeof(double) * (size_t)n);
+}
+
+/* Eq. (02): coef_j = Tr(F_j A) for j = 0..M-1 (complex, interleaved);
+ * a0 = Tr(A)/N (complex).  A is N x N complex row-major, interleaved. */
+void ora_expand(const ora_ctx *c, const double *A, double *coef, double *a0) {
+    int N = c->N;
+    for (int64_t j = 0; j < c->M; ++j) {
+        const sp_mat *F = &c->F[j];
+        double sr = 0, si = 0;
+        for (int e = 0; e < F->nnz; ++e) {
+            size_t q = (size_t)F->col[e] * N + F->row[e];
+            double xr = A[2 * q], xi = A[2 * q + 1];
+            sr += F->re[e] * xr - F->im[e] * xi;
+            si += F->re[e] * xi + F->im[e] * xr;
+        }
+        coef[2 * j] = sr; coef[2 * j + 1] = si;
+    }
+    double tr = 0, ti = 0;
+    for (int k = 0; k < N; ++k) { tr += A[2 * ((size_t)k * N + k)]; ti += A[2 * ((size_t)k * N + k) + 1]; }
+    a0[0] = tr / N; a0[1] = ti / N;
+}
+
+/* Eq. (rho): rho = F_0 + sum_i v_i F_i, F_0 = 1/N.  Output N x N complex. */
+void ora_rho(const ora_ctx *c, const double *v, double *rho) {
+    int N = c->N;
+    memset(rho, 0, sizeof(double) * 2 * (size_t)N * N);
+    for (int k = 0; k < N; ++k) rho[2 * ((size_t)k * N + k)] = 1.0 / N;
+    for (int64_t i = 0; i < c->M; ++i) {
+        const sp_mat *F = &c->F[i];
+        for (int e = 0; e < F->nnz; ++e) {
+            size_t p = (size_t)F->row[e] * N + F->col[e];
+            rho[2 * p] += v[i] * F->re[e];
+            rho[2 * p + 1] += v[i] * F->im[e];
+        }
+    }
+}
+
+/* Eq. (07): Q[s*M+n] = sum_m h_m f_mns (dense M x M). */
+void ora_Q(const ora_ctx *c, const double *h, double *Q) {
+    int64_t M = c->M;
+    memset(Q, 0, sizeof(double) * (size_t)M * M);
+    for (int64_t r = 0; r < c->nf; ++r) {
+        int32_t m = c->f_idx[3 * r], n = c->f_idx[3 * r + 1], s = c->f_idx[3 * r + 2];
+        Q[(size_t)s * M + n] += h[m] * c->f_val[r];
+    }
+}
+
+/* Eq. (08): k_s = (i/N) sum_jk a_jk f_jks; a is M x M complex (interleaved).
+ * Kimag receives the imaginary part of the result (zero for Hermitian a). */
+void ora_K(const ora_ctx *c, const double *a, double *K, double *Kimag) {
+    int64_t M = c->M;
+    double *sr = (double *)calloc((size_t)M, sizeof(double));
+    double *si = (double *)calloc((size_t)M, sizeof(double));
+    for (int64_t r = 0; r < c->nf; ++r) {
+        int32_t j = c->f_idx[3 * r], k = c->f_idx[3 * r + 1], s = c->f_idx[3 * r + 2];
+        size_t q = (size_t)j * M + k;
+        sr[s] += a[2 * q] * c->f_val[r];
+        si[s] += a[2 * q + 1] * c->f_val[r];
+    }
+    for (int64_t s = 0; s < M; ++s) {
+        /* (i/N)(sr + i si) = (-si + i sr)/N */
+        K[s] = -si[s] / c->N;
+        if (Kimag) Kimag[s] = sr[s] / c->N;
+    }
+    free(sr); free(si);
+}
+
+/* Lists grouped by the middle index l: F-section (k,s,f_kls) and
+ * Z-section (j,n,z_jln); f and d never share a position, so z items are
+ * either (f,0) or (0,d). */
+typedef struct {
+    int64_t *fptr, *zptr;
+    int32_t *fk, *fs; double *fv;
+    int32_t *zj, *zn; double *zr, *zi;
+} sections;
+
+static void build_sections(const ora_ctx *c, sections *S) {
+    int64_t M = c->M;
+    S->fptr = (int64_t *)calloc((size_t)M + 1, sizeof(int64_t));
+    S->zptr = (int64_t *)calloc((size_t)M + 1, sizeof(int64_t));
+    for (int64_t r = 0; r < c->nf; ++r) { S->fptr[c->f_idx[3 * r + 1] + 1]++; S->zptr[c->f_idx[3 * r + 1] + 1]++; }
+    for (int64_t r = 0; r < c->nd; ++r) S->zptr[c->d_idx[3 * r + 1] + 1]++;
+    for (int64_t l = 0; l < M; ++l) { S->fptr[l + 1] += S->fptr[l]; S->zptr[l + 1] += S->zptr[l]; }
+    int64_t nf = S->fptr[M], nz = S->zptr[M];
+    S->fk = (int32_t *)malloc(sizeof(int32_t) * (size_t)nf); S->fs = (int32_t *)malloc(sizeof(int32_t) * (size_t)nf);
+    S->fv = (double *)malloc(sizeof(double) * (size_t)nf);
+    S->zj = (int32_t *)malloc(sizeof(int32_t) * (size_t)nz); S->zn = (int32_t *)malloc(sizeof(int32_t) * (size_t)nz);
+    S->zr = (double *)malloc(sizeof(double) * (size_t)nz); S->zi = (double *)malloc(sizeof(double) * (size_t)nz);
+    int64_t *pf = (int64_t *)malloc(sizeof(int64_t) * (size_t)M), *pz = (int64_t *)malloc(sizeof(int64_t) * (size_t)M);
+    memcpy(pf, S->fptr, sizeof(int64_t) * (size_t)M); memcpy(pz, S->zptr, sizeof(int64_t) * (size_t)M);
+    for (int64_t r = 0; r < c->nf; ++r) {
+        int32_t a = c->f_idx[3 * r], l = c->f_idx[3 * r + 1], b = c->f_idx[3 * r + 2];
+        int64_t q = pf[l]++;
+        S->fk[q] = a; S->fs[q] = b; S->fv[q] = c->f_val[r];
+        q = pz[l]++;
+        S->zj[q] = a; S->zn[q] = b; S->zr[q] = c->f_val[r]; S->zi[q] = 0.0;
+    }
+    for (int64_t r = 0; r < c->nd; ++r) {
+        int32_t a = c->d_idx[3 * r], l = c->d_idx[3 * r + 1], b = c->d_idx[3 * r + 2];
+        int64_t q = pz[l]++;
+        S->zj[q] = a; S->zn[q] = b; S->zr[q] = 0.0; S->zi[q] = c->d_val[r];
+    }
+    free(pf); free(pz);
+}
+
+static void free_sections(sections *S) {
+    free(S->fptr); free(S->zptr); free(S->fk); free(S->fs); free(S->fv);
+    free(S->zj); free(S->zn); free(S->zr); free(S->zi);
+}
+
+/* Number of join terms W = sum_l |Z-section(l)| * |F-section(l)|. */
+int64_t ora_join_terms(const ora_ctx *c) {
+    sections S;
+    build_sections(c, &S);
+    int64_t W = 0;
+    for (int64_t l = 0; l < c->M; ++l)
+        W += (S.zptr[l + 1] - S.zptr[l]) * (S.fptr[l + 1] - S.fptr[l]);
+    free_sections(&S);
+    return W;
+}
+
+/*
+ * Eq. (09), both printed terms, prefactor -1/4:
+ *   r_sn = -1/4 sum_l sum_jk a_jk ( z_jln f_kls + conj(z_kln) f_jls ).
+ * R receives the real part (M x M, R[s*M+n]); Rimag (optional) the imaginary
+ * part, which must vanish; Sc (optional) the scale 1/4 sum |term|.
+ */
+void ora_R(const ora_ctx *c, const double *a, double *R, double *Rimag, double *Sc) {
+    int64_t M = c->M;
+    sections S;
+    build_sections(c, &S);
+    double *acc_i = (double *)calloc((size_t)M * M, sizeof(double));
+    double *acc_s = (double *)calloc((size_t)M * M, sizeof(double));
+    memset(R, 0, sizeof(double) * (size_t)M * M);
+    for (int64_t l = 0; l < M; ++l) {
+        for (int64_t zq = S.zptr[l]; zq < S.zptr[l + 1]; ++zq) {
+            int32_t x = S.zj[zq], n = S.zn[zq];
+            double zr = S.zr[zq], zi = S.zi[zq];
+            for (int64_t fq = S.fptr[l]; fq < S.fptr[l + 1]; ++fq) {
+                int32_t y = S.fk[fq], s = S.fs[fq];
+                double fv = S.fv[fq];
+                size_t o = (size_t)s * M + n;
+                /* first term: j = x, k = y: a_jk z_jln f_kls */
+                size_t q1 = (size_t)x * M + y;
+                double ar = a[2 * q1], ai = a[2 * q1 + 1];
+                double t1r = (ar * zr - ai * zi) * fv, t1i = (ar * zi + ai * zr) * fv;
+                /* second term: k = x, j = y: a_jk conj(z_kln) f_jls */
+                size_t q2 = (size_t)y * M + x;
+                double br = a[2 * q2], bi = a[2 * q2 + 1];
+                double t2r = (br * zr + bi * zi) * fv, t2i = (bi * zr - br * zi) * fv;
+                R[o] += t1r + t2r;
+                acc_i[o] += t1i + t2i;
+                acc_s[o] += sqrt(t1r * t1r + t1i * t1i) + sqrt(t2r * t2r + t2i * t2i);
+            }
+        }
+    }
+    for (size_t o = 0; o < (size_t)M * M; ++o) {
+        R[o] *= -0.25;
+        if (Rimag) Rimag[o] = -0.25 * acc_i[o];
+        if (Sc) Sc[o] = 0.25 * acc_s[o];
+    }
+    free(acc_i); free(acc_s);
+    free_sections(&S);
+}
+
+/* Lists grouped by the LAST index, sorted by the middle one, for evaluating
+ * single entries r_sn: Fc(s) = {(k,l,f_kls)}, Zc(n) = {(j,l,z_jln)}. */
+typedef struct {
+    int64_t *fptr, *zptr;
+    int32_t *fk, *fl; double *fv;
+    int32_t *zj, *zl; double *zr, *zi;
+} columns;
+
+static int64_t *g_key;
+static int cmp_key(const void *pa, const void *pb) {
+    int64_t a = g_key[*(const int64_t *)pa], b = g_key[*(const int64_t *)pb];
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+static void build_columns(const ora_ctx *c, columns *C) {
+    int64_t M = c->M, nf = c->nf, nz = c->nf + c->nd;
+    C->fptr = (int64_t *)calloc((size_t)M + 1, sizeof(int64_t));
+    C->zptr = (int64_t *)calloc((size_t)M + 1, sizeof(int64_t));
+    /* sort f items by (last, middle) and z items likewise */
+    int64_t *kf = (int64_t *)malloc(sizeof(int64_t) * (size_t)nf), *of = (int64_t *)malloc(sizeof(int64_t) * (size_t)nf);
+    for (int64_t r = 0; r < nf; ++r) { kf[r] = (int64_t)c->f_idx[3 * r + 2] * M + c->f_idx[3 * r + 1]; of[r] = r; }
+    g_key = kf; qsort(of, (size_t)nf, sizeof(int64_t), cmp_key);
+    int64_t *kz = (int64_t *)malloc(sizeof(int64_t) * (size_t)nz), *oz = (int64_t *)malloc(sizeof(int64_t) * (size_t)nz);
+    for (int64_t r = 0; r < nz; ++r) {
+        const int32_t *x = r < nf ? &c->f_idx[3 * r] : &c->d_idx[3 * (r - nf)];
+        kz[r] = (int64_t)x[2] * M + x[1]; oz[r] = r;
+    }
+    g_key = kz; qsort(oz, (size_t)nz, sizeof(int64_t), cmp_key);
+    C->fk = (int32_t *)malloc(sizeof(int32_t) * (size_t)nf); C->fl = (int32_t *)malloc(sizeof(int32_t) * (size_t)nf);
+    C->fv = (double *)malloc(sizeof(double) * (size_t)nf);
+    C->zj = (int32_t *)malloc(sizeof(int32_t) * (size_t)nz); C->zl = (int32_t *)malloc(sizeof(int32_t) * (size_t)nz);
+    C->zr = (double *)malloc(sizeof(double) * (size_t)nz); C->zi = (double *)malloc(sizeof(double) * (size_t)nz);
+    for (int64_t q = 0; q < nf; ++q) {
+        int64_t r = of[q];
+        C->fk[q] = c->f_idx[3 * r]; C->fl[q] = c->f_idx[3 * r + 1]; C->fv[q] = c->f_val[r];
+        C->fptr[c->f_idx[3 * r + 2] + 1]++;
+    }
+    for (int64_t q = 0; q < nz; ++q) {
+        int64_t r = oz[q];
+        if (r < nf) {
+            C->zj[q] = c->f_idx[3 * r]; C->zl[q] = c->f_idx[3 * r + 1];
+            C->zr[q] = c->f_val[r]; C->zi[q] = 0.0;
+            C->zptr[c->f_idx[3 * r + 2] + 1]++;
+        } else {
+            r -= nf;
+            C->zj[q] = c->d_idx[3 * r]; C->zl[q] = c->d_idx[3 * r + 1];
+            C->zr[q] = 0.0; C->zi[q] = c->d_val[r];
+            C->zptr[c->d_idx[3 * r + 2] + 1]++;
+        }
+    }
+    for (int64_t s = 0; s < M; ++s) { C->fptr[s + 1] += C->fptr[s]; C->zptr[s + 1] += C->zptr[s]; }
+    free(kf); free(of); free(kz); free(oz);
+}
+
+static void free_columns(columns *C) {
+    free(C->fptr); free(C->zptr); free(C->fk); free(C->fl); free(C->fv);
+    free(C->zj); free(C->zl); free(C->zr); free(C->zi);
+}
+
+/*
+ * Eq. (09) for selected entries (s_i, n_i) only; same two-term form and
+ * prefactor as ora_R.  a_at(j,k) reads the dense M x M complex matrix.
+ * Entries are independent, so they may be spread over OpenMP threads.
+ */
+void ora_R_entries(const ora_ctx *c, const double *a, int64_t cnt,
+                   const int64_t *si, const int64_t *ni, double *out,
+                   double *out_imag, double *out_scale) {
+    int64_t M = c->M;
+    columns C;
+    build_columns(c, &C);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t e = 0; e < cnt; ++e) {
+        int64_t s = si[e], n = ni[e];
+        double accr = 0, acci = 0, accs = 0;
+        int64_t pf = C.fptr[s], ef = C.fptr[s + 1];
+        int64_t pz = C.zptr[n], ez = C.zptr[n + 1];
+        /* merge-join on the middle index l (both lists sorted by l) */
+        while (pf < ef && pz < ez) {
+            int32_t lf = C.fl[pf], lz = C.zl[pz];
+            if (lf < lz) { pf++; continue; }
+            if (lz < lf) { pz++; continue; }
+            int64_t f0 = pf, z0 = pz;
+            while (pf < ef && C.fl[pf] == lf) pf++;
+            while (pz < ez && C.zl[pz] == lf) pz++;
+            for (int64_t zq = z0; zq < pz; ++zq)
+                for (int64_t fq = f0; fq < pf; ++fq) {
+                    int32_t x = C.zj[zq], y = C.fk[fq];
+                    double zr = C.zr[zq], zi = C.zi[zq], fv = C.fv[fq];
+                    size_t q1 = (size_t)x * M + y, q2 = (size_t)y * M + x;
+                    double ar = a[2 * q1], ai = a[2 * q1 + 1];
+                    double br = a[2 * q2], bi = a[2 * q2 + 1];
+                    double t1r = (ar * zr - ai * zi) * fv, t1i = (ar * zi + ai * zr) * fv;
+                    double t2r = (br * zr + bi * zi) * fv, t2i = (bi * zr - br * zi) * fv;
+                    accr += t1r + t2r; acci += t1i + t2i;
+                    accs += sqrt(t1r * t1r + t1i * t1i) + sqrt(t2r * t2r + t2i * t2i);
+                }
+        }
+        out[e] = -0.25 * accr;
+        if (out_imag) out_imag[e] = -0.25 * acci;
+        if (out_scale) out_scale[e] = 0.25 * accs;
+    }
+    free_columns(&C);
+}
+
+/* Eq. (07) for selected entries. */
+void ora_Q_entries(const ora_ctx *c, const double *h, int64_t cnt,
+                   const int64_t *si, const int64_t *ni, double *out) {
+    columns C;
+    build_columns(c, &C);
+    for (int64_t e = 0; e < cnt; ++e) {
+        int64_t s = si[e], n = ni[e];
+        double acc = 0;
+        /* f_mns with last index s and middle index n: Fc(s) items with l == n */
+        for (int64_t q = C.fptr[s]; q < C.fptr[s + 1]; ++q)
+            if (C.fl[q] == n) acc += h[C.fk[q]] * C.fv[q];
+        out[e] = acc;
+    }
+    free_columns(&C);
+}
+
+/*
+ * Eq. (09) for a Kossakowski matrix given in spectral (low-rank) form,
+ * a_jk = sum_p gamma_p l_pj conj(l_pk), with sparse l_p.  Only the nonzero
+ * a_jk are visited.  Output dense M x M (small N) plus the symbolic mask:
+ * mask[s*M+n] = 1 iff some (p, j, k, l) with l_pj != 0, l_pk != 0,
+ * z_jln != 0 and f_kls != 0 reaches (s, n).
+ * lp_ptr: P+1 offsets into (lp_idx, lp_re, lp_im).
+ */
+void ora_R_lowrank(const ora_ctx *c, int nP, const double *gamma,
+                   const int64_t *lp_ptr, const int64_t *lp_idx,
+                   const double *lp_re, const double *lp_im,
+                   double *R, unsigned char *mask) {
+    int64_t M = c->M;
+    sections S;
+    build_sections(c, &S);
+    memset(R, 0, sizeof(double) * (size_t)M * M);
+    if (mask) memset(mask, 0, (size_t)M * M);
+    /* per-element sorted lists of (l, n) for z and (l, s) for f keyed by
+     * the FIRST index, derived from the sections */
+    /* simple approach: for every nonzero a_jk, loop over all l and test */
+    for (int p = 0; p < nP; ++p) {
+        for (int64_t u = lp_ptr[p]; u < lp_ptr[p + 1]; ++u)
+            for (int64_t w = lp_ptr[p]; w < lp_ptr[p + 1]; ++w) {
+                int64_t j = lp_idx[u], k = lp_idx[w];
+                /* a_jk = gamma l_j conj(l_k) */
+                double ar = gamma[p] * (lp_re[u] * lp_re[w] + lp_im[u] * lp_im[w]);
+                double ai = gamma[p] * (lp_im[u] * lp_re[w] - lp_re[u] * lp_im[w]);
+                for (int64_t l = 0; l < M; ++l) {
+                    for (int64_t zq = S.zptr[l]; zq < S.zptr[l + 1]; ++zq) {
+                        int32_t x = S.zj[zq], n = S.zn[zq];
+                        if (x != j && x != k) continue;
+                        for (int64_t fq = S.fptr[l]; fq < S.fptr[l + 1]; ++fq) {
+                            int32_t y = S.fk[fq], s = S.fs[fq];
+                            double zr = S.zr[zq], zi = S.zi[zq], fv = S.fv[fq];
+                            size_t o = (size_t)s * M + n;
+                            if (x == j && y == k) {  /* a_jk z_jln f_kls */
+                                R[o] += (ar * zr - ai * zi) * fv;
+                                if (mask) mask[o] = 1;
+                            }
+                            if (x == k && y == j) {  /* a_jk conj(z_kln) f_jls */
+                                R[o] += (ar * zr + ai * zi) * fv;
+                                if (mask) mask[o] = 1;
+                            }
+                        }
+                    }
+                }
+            }
+    }
+    for (size_t o = 0; o < (size_t)M * M; ++o) R[o] *= -0.25;
+    free_sections(&S);
+}
+
+/* -------------------------------------------------------------- RK4 */
+
+/* y = A x + K (dense, row-major M x M) */
+static void dense_rhs(int64_t M, const double *A, const double *K, const double *x, double *y) {
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < M; ++s) {
+        const double *row = A + (size_t)s * M;
+        double acc = 0;
+        for (int64_t n = 0; n < M; ++n) acc += row[n] * x[n];
+        y[s] = acc + K[s];
+    }
+}
+
+/*
+ * Classical RK4 with fixed step dt for dv/dt = A v + K (Eq. (04) with
+ * time-independent Q and R), nsteps steps.  Snapshots of v after every
+ * snap_every steps go to out ((nsteps/snap_every) x M); the final v to vout.
+ */
+void ora_rk4_dense(int64_t M, const double *A, const double *K, const double *v0,
+                   double dt, int64_t nsteps, int64_t snap_every, double *out, double *vout) {
+    double *v = (double *)malloc(sizeof(double) * (size_t)M);
+    double *x = (double *)malloc(sizeof(double) * (size_t)M);
+    double *k1 = (double *)malloc(sizeof(double) * (size_t)M);
+    double *k2 = (double *)malloc(sizeof(double) * (size_t)M);
+    double *k3 = (double *)malloc(sizeof(double) * (size_t)M);
+    double *k4 = (double *)malloc(sizeof(double) * (size_t)M);
+    memcpy(v, v0, sizeof(double) * (size_t)M);
+    int64_t snap = 0;
+    for (int64_t t = 0; t < nsteps; ++t) {
+        dense_rhs(M, A, K, v, k1);
+        for (int64_t i = 0; i < M; ++i) x[i] = v[i] + 0.5 * dt * k1[i];
+        dense_rhs(M, A, K, x, k2);
+        for (int64_t i = 0; i < M; ++i) x[i] = v[i] + 0.5 * dt * k2[i];
+        dense_rhs(M, A, K, x, k3);
+        for (int64_t i = 0; i < M; ++i) x[i] = v[i] + dt * k3[i];
+        dense_rhs(M, A, K, x, k4);
+        for (int64_t i = 0; i < M; ++i)
+            v[i] += dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+        if (out && snap_every > 0 && (t + 1) % snap_every == 0) {
+            memcpy(out + (size_t)snap * M, v, sizeof(double) * (size_t)M);
+            snap++;
+        }
+    }
+    if (vout) memcpy(vout, v, sizeof(double) * (size_t)M);
+    free(v); free(x); free(k1); free(k2); free(k3); free(k4);
+}
+
+/* y = A x + K for CSR A (int64 row pointers, int32 columns). */
+static void csr_rhs(int64_t M, const int64_t *rp, const int32_t *ci, const double *val,
+                    const double *K, const double *x, double *y) {
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < M; ++s) {
+        double acc = 0;
+        for (int64_t q = rp[s]; q < rp[s + 1]; ++q) acc += val[q] * x[ci[q]];
+        y[s] = acc + (K ? K[s] : 0.0);
+    }
+}
+
+void ora_rk4_csr(int64_t M, const int64_t *rp, const int32_t *ci, const double *val,
+                 const double *K, const double *v0, double dt, int64_t nsteps, double *vout) {
+    double *v = (double *)malloc(sizeof(double) * (size_t)M);
+    double *x = (double *)malloc(sizeof(double) * (size_t)M);
+    double *k1 = (double *)malloc(sizeof(double) * (size_t)M);
+    double *k2 = (double *)malloc(sizeof(double) * (size_t)M);
+    double *k3 = (double *)malloc(sizeof(double) * (size_t)M);
+    double *k4 = (double *)malloc(sizeof(double) * (size_t)M);
+    memcpy(v, v0, sizeof(double) * (size_t)M);
+    for (int64_t t = 0; t < nsteps; ++t) {
+        csr_rhs(M, rp, ci, val, K, v, k1);
+        for (int64_t i = 0; i < M; ++i) x[i] = v[i] + 0.5 * dt * k1[i];
+        csr_rhs(M, rp, ci, val, K, x, k2);
+        for (int64_t i = 0; i < M; ++i) x[i] = v[i] + 0.5 * dt * k2[i];
+        csr_rhs(M, rp, ci, val, K, x, k3);
+        for (int64_t i = 0; i < M; ++i) x[i] = v[i] + dt * k3[i];
+        csr_rhs(M, rp, ci, val, K, x, k4);
+        for (int64_t i = 0; i < M; ++i)
+            v[i] += dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+    }
+    memcpy(vout, v, sizeof(double) * (size_t)M);
+    free(v); free(x); free(k1); free(k2); free(k3); free(k4);
+}
+
+int ora_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void ora_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

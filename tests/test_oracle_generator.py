@@ -1,0 +1,219 @@
+"""Pins for the oracle's Q, K, R (Eqs. (07)-(09)) and RK4 (CPU only).
+
+Independent references: brute-force traces of the literal Lindbladian (O1),
+the matrix-unit superoperator (O2), textbook Bloch equations for N = 2,
+the completeness relation of an orthonormal operator basis (a = gamma 1),
+the exact propagator (expm), the exact death process of the ladder model.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import workloads as wl
+from oracle import Oracle, brute, rk4_dense, superop
+
+
+def _random_case(N, seed):
+    H = wl.gue_hamiltonian(N, seed)
+    a = wl.wishart_kossakowski(N, seed + 1)
+    return H, a
+
+
+def _oracle_system(o, H, a):
+    h, _ = o.expand(H)
+    Q = o.Q(h.real)
+    K = o.K(a)
+    R = o.R(a)
+    return Q, R, K
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+def test_equals_brute_force(N):
+    H, a = _random_case(N, 100 + N)
+    Qb, Rb, Kb = brute.split_generator(N, H, a)
+    with Oracle(N) as o:
+        Q, R, K = _oracle_system(o, H, a)
+        Rr, Ri = o.R(a, return_imag=True)
+        Kr, Ki = o.K(a, return_imag=True)
+    assert np.abs(Q - Qb).max() < 1e-13
+    assert np.abs(R - Rb).max() < 1e-14
+    assert np.abs(K - Kb).max() < 1e-14
+    assert np.abs(Ri).max() < 1e-15 and np.abs(Ki).max() < 1e-15
+
+
+@pytest.mark.parametrize("N", [2, 3, 6, 8])
+def test_equals_superoperator_route(N):
+    H, a = _random_case(N, 200 + N)
+    Qs, Rs, Ks, imag = superop.generator(N, H, a)
+    assert imag < 1e-13
+    with Oracle(N) as o:
+        Q, R, K = _oracle_system(o, H, a)
+    scale = max(1.0, np.abs(Rs).max())
+    assert np.abs(Q - Qs).max() < 1e-12 * max(1.0, np.abs(Qs).max())
+    assert np.abs(R - Rs).max() < 1e-13 * scale
+    assert np.abs(K - Ks).max() < 1e-13 * scale
+
+
+def test_q_antisymmetric_and_k_r_real():
+    N = 7
+    H, a = _random_case(N, 7)
+    with Oracle(N) as o:
+        h, a0 = o.expand(H)
+        assert np.abs(h.imag).max() < 1e-14          # Hermitian H -> real h (Eq. (02))
+        Q = o.Q(h.real)
+        assert np.abs(Q + Q.T).max() < 1e-14 * np.abs(Q).max()   # up to summation order
+        _, Ri = o.R(a, return_imag=True)
+        _, Ki = o.K(a, return_imag=True)
+    assert np.abs(Ri).max() < 1e-15 and np.abs(Ki).max() < 1e-15
+
+
+def test_n2_bloch_precession():
+    """H = (w/2) sigma_z: d<sx>/dt = -w <sy>, d<sy>/dt = w <sx>."""
+    w = 1.7
+    H = np.diag([w / 2, -w / 2]).astype(complex)
+    with Oracle(2) as o:
+        h, _ = o.expand(H)
+        Q = o.Q(h.real)
+    assert np.allclose(Q, [[0, -w, 0], [w, 0, 0], [0, 0, 0]], atol=1e-15)
+
+
+def test_n2_amplitude_damping():
+    """L = sqrt(gamma) |0><1|: rho_11' = -gamma rho_11, rho_01' = -gamma/2 rho_01.
+    In Bloch components (S, J, D) = (<sx>, <sy>, <sz>)/sqrt 2:
+    R = diag(-g/2, -g/2, -g), K = (0, 0, g/sqrt 2)."""
+    g = 0.37
+    L = np.array([[0, 1], [0, 0]], complex)
+    with Oracle(2) as o:
+        l, l0 = o.expand(L)
+        assert abs(l0) < 1e-15
+        a = g * np.outer(l, l.conj())
+        R = o.R(a)
+        K = o.K(a)
+        Rl, mask = o.R_lowrank([g], [(np.arange(3), l)])
+    assert np.allclose(R, np.diag([-g / 2, -g / 2, -g]), atol=1e-15)
+    assert np.allclose(K, [0, 0, g / math.sqrt(2)], atol=1e-15)
+    assert np.allclose(Rl, R, atol=1e-15)
+
+
+@pytest.mark.parametrize("N", [2, 3, 5])
+def test_identity_kossakowski(N):
+    """a = gamma 1: sum_j F_j X F_j = Tr(X) 1 - X/N gives L_D(X) = gamma(Tr X 1 - N X),
+    so R = -gamma N 1 and K = 0."""
+    g = 0.3
+    M = N * N - 1
+    with Oracle(N) as o:
+        R = o.R(g * np.eye(M))
+        K = o.K(g * np.eye(M))
+    assert np.allclose(R, -g * N * np.eye(M), atol=1e-14)
+    assert np.abs(K).max() < 1e-15
+
+
+@pytest.mark.parametrize("N", [4, 9])
+def test_entrywise_matches_full(N):
+    H, a = _random_case(N, 300 + N)
+    with Oracle(N) as o:
+        R, S = o.R(a, return_scale=True)
+        h, _ = o.expand(H)
+        Q = o.Q(h.real)
+        g = np.random.default_rng(1)
+        s = g.integers(0, o.M, 300)
+        n = g.integers(0, o.M, 300)
+        Re, Rim, Se = o.R_entries(a, s, n)
+        Qe = o.Q_entries(h.real, s, n)
+    assert np.abs(Re - R[s, n]).max() < 1e-15
+    assert np.abs(Se - S[s, n]).max() < 1e-14
+    assert np.abs(Rim).max() < 1e-15
+    assert np.abs(Qe - Q[s, n]).max() == 0
+
+
+def test_lowrank_equals_dense():
+    N = 6
+    H, L, g = wl.ladder_model(N, 5)
+    with Oracle(N) as o:
+        l, _ = o.expand(L)
+        nz = np.nonzero(np.abs(l) > 0)[0]
+        a = g * np.outer(l, l.conj())
+        Rd = o.R(a)
+        Rl, mask = o.R_lowrank([g], [(nz, l[nz])])
+    assert np.abs(Rd - Rl).max() < 1e-15
+    assert np.all(mask[np.abs(Rd) > 1e-14])
+
+
+def _exact(A, K, v0, t):
+    """exp of the augmented generator [[A, K], [0, 0]] applied to (v0, 1)."""
+    M = len(v0)
+    B = np.zeros((M + 1, M + 1))
+    B[:M, :M] = A
+    B[:M, M] = K
+    x = scipy.linalg.expm(B * t) @ np.concatenate([v0, [1.0]])
+    return x[:M]
+
+
+def test_rk4_fourth_order_against_expm():
+    N = 4
+    H, a = _random_case(N, 11)
+    with Oracle(N) as o:
+        Q, R, K = _oracle_system(o, H, a)
+        rho0 = wl.pure_state(N, 0)
+        v0 = o.expand(rho0)[0].real
+    A = Q + R
+    T = 1.0
+    ref = _exact(A, K, v0, T)
+    errs = []
+    for steps in (40, 80, 160):
+        v, _ = rk4_dense(A, K, v0, T / steps, steps)
+        errs.append(np.abs(v - ref).max())
+    assert errs[0] / errs[1] > 14 and errs[1] / errs[2] > 14
+
+
+def test_rk4_trace_positivity_steady_state():
+    N = 5
+    H, a = _random_case(N, 21)
+    with Oracle(N) as o:
+        Q, R, K = _oracle_system(o, H, a)
+        v0 = o.expand(wl.pure_state(N, 2))[0].real
+        A = Q + R
+        v, snaps = rk4_dense(A, K, v0, 1e-2, 400, snap_every=100)
+        for vv in snaps:
+            rho = o.rho(vv)
+            assert abs(np.trace(rho) - 1) < 1e-14
+            assert np.allclose(rho, rho.conj().T, atol=1e-15)
+            assert np.linalg.eigvalsh(rho).min() > -1e-10
+        vs = np.linalg.solve(A, -K)             # steady state (Q+R) v* = -K
+        rho = o.rho(vs)
+        assert abs(np.trace(rho) - 1) < 1e-13
+        assert np.linalg.eigvalsh(rho).min() > -1e-10
+
+
+def test_unitary_norm_conserved():
+    N = 4
+    H, _ = _random_case(N, 31)
+    with Oracle(N) as o:
+        h, _ = o.expand(H)
+        Q = o.Q(h.real)
+        v0 = o.expand(wl.pure_state(N, 1))[0].real
+    v, _ = rk4_dense(Q, np.zeros(len(v0)), v0, 1e-3, 2000)
+    assert abs(np.linalg.norm(v) - np.linalg.norm(v0)) < 1e-10
+
+
+def test_ladder_death_process():
+    """H diagonal: populations follow p_n(t) = C(n0,n) e^{-g n t}(1-e^{-g t})^{n0-n}."""
+    N = 6
+    H, L, g = wl.ladder_model(N, 3)
+    H = np.diag(np.diag(H))
+    n0 = N - 1
+    with Oracle(N) as o:
+        h, _ = o.expand(H)
+        l, _ = o.expand(L)
+        a = g * np.outer(l, l.conj())
+        A = o.Q(h.real) + o.R(a)
+        K = o.K(a)
+        v0 = o.expand(wl.pure_state(N, n0))[0].real
+        T = 3.0
+        v, _ = rk4_dense(A, K, v0, 1e-3, 3000)
+        p = np.diag(o.rho(v)).real
+    e = math.exp(-g * T)
+    ref = np.array([math.comb(n0, n) * e**n * (1 - e) ** (n0 - n) for n in range(N)])
+    assert np.abs(p - ref).max() < 1e-11
