@@ -1,0 +1,216 @@
+/*
+ * lindblad.h -- C ABI of liblindblad.so: the transformation of a GKSL
+ * (Lindblad) generator into the real linear system dv/dt = (Q + R) v + K over
+ * the generalized Gell-Mann basis, and its RK4 integration, on one sm_103a GPU.
+ *
+ * Method: Meyerov et al., "Transforming Lindblad Equations into Systems of
+ * Real-Valued Linear Equations" -- Sec. 2 (basis, Eqs. (02)-(09)), Table 1
+ * (Data Preparation steps 2.1-2.6, ODE Integration steps 3.1-3.2), Sec. 4.
+ *
+ * Conventions (all functions):
+ *   - N is the Hilbert-space dimension, M = N*N - 1, P = N*(N-1)/2.
+ *   - Basis order, 0-based: S_ab (pairs a<b, lexicographic) at 0..P-1,
+ *     J_ab at P..2P-1, D_l (l = 1..N-1) at 2P..M-1.  D_l is the Hermitian,
+ *     orthonormal matrix (sum_{k<l} E_kk - l E_ll)/sqrt(l(l+1)).
+ *   - Complex arrays are interleaved (re, im) doubles; matrices are row-major.
+ *   - The Kossakowski matrix `a` follows the index convention of Eqs. (08)
+ *     and (09): L_D(rho) = sum_jk a_jk (F_j rho F_k - 1/2 {F_k F_j, rho}),
+ *     i.e. a = K^T for the matrix K_mn of Eq. (1); a must be Hermitian and is
+ *     passed as the full M x M matrix (both triangles).
+ *   - Every function returns an int status (LB_OK = 0 on success).  On error
+ *     nothing is half-written to caller buffers except where stated, no
+ *     exception or abort crosses the ABI, and lb_last_error() returns a
+ *     thread-local description of the last failure on the calling thread.
+ *   - "device" pointers are CUDA device addresses on the current device;
+ *     "host" pointers are ordinary (pageable or pinned) host memory.  Stream
+ *     arguments are cudaStream_t values passed as void* (NULL = legacy
+ *     default stream); device-pointer functions are asynchronous with
+ *     respect to the host unless stated.
+ *   - Caller-owned buffers are only read (inputs) or written (outputs) during
+ *     the call and its stream work; the library keeps no reference to them.
+ *   - Handles (lb_basis_t, lb_system_t) own device memory; they are not
+ *     thread-safe: use one handle per host thread or serialise calls.
+ */
+#ifndef LINDBLAD_H
+#define LINDBLAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LB_OK 0
+#define LB_EINVAL 1         /* bad argument (size, pointer, range)           */
+#define LB_ENOMEM 2         /* device memory refused (admission or cudaMalloc) */
+#define LB_ECUDA 3          /* a CUDA runtime call or kernel failed           */
+#define LB_ETIMEOUT 4       /* a bounded device-side wait ran out              */
+#define LB_EUNSUPPORTED 5   /* valid request that this build does not handle   */
+#define LB_EAGAIN 6         /* result not ready yet                            */
+
+/* structure tensors (Eq. (05)) */
+#define LB_F 0
+#define LB_D 1
+
+/* storage precision of the integration matrix A = Q + R */
+#define LB_FP64 0
+#define LB_FP32 1
+#define LB_BF16 2
+
+/* parts of an assembled system */
+#define LB_SYS_A 0
+#define LB_SYS_Q 1
+#define LB_SYS_R 2
+#define LB_SYS_K 3
+
+typedef struct lb_basis lb_basis_t;
+typedef struct lb_system lb_system_t;
+
+/* Thread-local text of the last error on this thread ("" if none). */
+const char *lb_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int lb_version(void);
+
+/* ------------------------------------------------------------------------
+ * a1 -- basis and structure constants.  Table 1 step 2.2, Sec. 4 item 2.2:
+ * only the O(N^3) nonzero f_mns, d_mns (Eq. (05)) exist, each O(1) to
+ * compute; they are enumerated by index arithmetic, never stored densely.
+ * --------------------------------------------------------------------- */
+
+/* Build the device index tables of the basis for dimension N (2 <= N <= 4096):
+ * the lexicographic pair table and c_l = 1/sqrt(l(l+1)).  *out is owned by
+ * the caller and released with lb_basis_destroy; it must outlive every
+ * lb_system_t assembled from it.  Synchronous.  LB_EINVAL for bad N,
+ * LB_ENOMEM / LB_ECUDA on device failure. */
+int lb_basis_create(int N, void *stream, lb_basis_t **out);
+int lb_basis_destroy(lb_basis_t *b);
+
+/* N, M, P of a basis (any output pointer may be NULL). */
+int lb_basis_dims(const lb_basis_t *b, int *N, int64_t *M, int64_t *P);
+
+/* Label of basis index i: type 'S', 'J' (pair j<k) or 'D' (j = k = l). */
+int lb_basis_label(const lb_basis_t *b, int64_t i, char *type, int *j, int *k);
+
+/* Number of canonical nonzero triples (m <= n <= s) of f (which = LB_F) or
+ * d (LB_D) of the basis, counted on the GPU by kernel (a) without storing
+ * them.  Synchronous (default stream). */
+int lb_structure_count(const lb_basis_t *b, int which, int64_t *nnz);
+
+/* Kernel (a): enumerate the canonical nonzero triples, sorted
+ * lexicographically by (m, n, s), into caller DEVICE buffers idx3 (3*nnz
+ * int32) and val (nnz doubles) by a count pass, an exclusive scan and a fill
+ * pass.  capacity is the buffer length in triples; *nnz always receives the
+ * count, and LB_EINVAL is returned (buffers untouched) if capacity < nnz.
+ * Synchronous with respect to `stream`. */
+int lb_structure_export(const lb_basis_t *b, int which, int32_t *idx3, double *val,
+                        int64_t capacity, int64_t *nnz, void *stream);
+
+/* Number of join terms W = #{(j,l,n,k,s): z_jln != 0, f_kls != 0} visited by
+ * the dense R assembly (Eq. (09)); counted on the GPU.  Synchronous. */
+int lb_join_terms(const lb_basis_t *b, int64_t *W);
+
+/* ------------------------------------------------------------------------
+ * a2 -- expansion and reconstruction.  Table 1 steps 2.1, 2.6, 3.2.
+ * --------------------------------------------------------------------- */
+
+/* Eq. (02): coef_j = Tr(F_j A), j = 0..M-1, for an N x N complex matrix A
+ * (device, interleaved).  coef is M complex (device).  For Hermitian A the
+ * coefficients are real; for a jump operator they are the complex l_j.  The
+ * identity component Tr(A)/N is not part of coef. */
+int lb_expand(const lb_basis_t *b, const double *A, double *coef, void *stream);
+
+/* Eq. (rho): rho = 1/N + sum_i v_i F_i as an N x N complex matrix (device). */
+int lb_rho(const lb_basis_t *b, const double *v, double *rho, void *stream);
+
+/* ------------------------------------------------------------------------
+ * a3-a5 -- dense assembly.  Eqs. (07)-(09), Table 1 steps 2.3-2.5.
+ * --------------------------------------------------------------------- */
+
+/* Dense assembly from device buffers.
+ *   h : M real Hamiltonian coefficients h_m = Tr(F_m H) (Eq. (07)), or NULL (H = 0)
+ *   a : M x M complex Kossakowski matrix (convention above)
+ * Outputs (each may be NULL, at least one of A, Q, R must not be):
+ *   A = Q + R, Q, R : M x M doubles, row s = equation for dv_s/dt, column n
+ *   K : M doubles (Eq. (08))
+ * Each R entry is the sum of its join terms over the shared index l
+ * (Eq. (09) in the one-term form r_sn = -1/2 Re sum_jkl a_jk z_jln f_kls,
+ * identical to the printed two-term form with prefactor -1/4 for Hermitian a),
+ * accumulated in FP64 by the thread that owns the entry. */
+int lb_assemble_dense(const lb_basis_t *b, const double *h, const double *a,
+                      double *A, double *Q, double *R, double *K, void *stream);
+
+/* ------------------------------------------------------------------------
+ * a6-a8 -- RK4 integration (Table 1 step 3.1; Sec. 4 item 3), with the
+ * matrix stored in FP64, FP32, or BF16 with per-row scales.
+ * --------------------------------------------------------------------- */
+
+/* A32 = fl32(A) (device, M x M). */
+int lb_pack_fp32(int64_t M, const double *A, float *A32, void *stream);
+
+/* Abf = bf16(A_sn / r_s), row_scale[s] = r_s = max_n |A_sn| (1 for a zero row). */
+int lb_pack_bf16(int64_t M, const double *A, uint16_t *Abf, float *row_scale, void *stream);
+
+/* Bytes of device workspace lb_rk4_dense needs for size M. */
+size_t lb_rk4_workspace_bytes(int64_t M);
+
+/* Classical RK4 with fixed step dt for dv/dt = A v + K, nsteps steps, all on
+ * device.  precision selects the storage of Ap: LB_FP64 (double*), LB_FP32
+ * (float*), LB_BF16 (uint16_t* bf16 with row_scale).  For FP32/BF16 the
+ * stage products are FP32 multiply-adds of FP32-rounded stage vectors; the
+ * state v and the stage combination stay FP64.  If correct_every > 0 and A64
+ * is given, every correct_every steps the FP64 defect c = (A64 - A_lp) v at
+ * the current v is formed in FP64 and added to K until the next correction.
+ * v (M doubles) is the initial state on entry and the final state on exit.
+ * snaps (may be NULL): after every snap_every steps a copy of v is stored in
+ * row t/snap_every - 1 of snaps ((nsteps/snap_every) x M).
+ * work: lb_rk4_workspace_bytes(M) bytes of device memory. */
+int lb_rk4_dense(int64_t M, int precision, const void *Ap, const float *row_scale,
+                 const double *A64, int correct_every, const double *K, double *v,
+                 double dt, int64_t nsteps, double *snaps, int64_t snap_every,
+                 void *work, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Host-buffer interface (one call per paper step, inputs and outputs in
+ * host memory, copies included).  The assembled system stays on the device
+ * inside an lb_system_t.
+ * --------------------------------------------------------------------- */
+
+/* Expand H (host N x N complex, may be NULL) and assemble Q, R, K from the
+ * host Kossakowski matrix a (M x M complex).  keep_parts != 0 also keeps Q
+ * and R separately.  The device copy of a is freed before returning.
+ * LB_ENOMEM if the device cannot hold a, A (and Q, R). Synchronous. */
+int lb_assemble(const lb_basis_t *b, const double *H, const double *a, int keep_parts,
+                lb_system_t **out);
+int lb_system_destroy(lb_system_t *sys);
+
+/* Copy one part (LB_SYS_A, _Q, _R: M x M; LB_SYS_K: M) into host memory.
+ * LB_EINVAL if the part was not kept. */
+int lb_system_get(const lb_system_t *sys, int part, double *out);
+
+/* RK4 from the host initial state v0 (M doubles) for n = round(t/dt) steps
+ * (LB_EINVAL if |n dt - t| > 1e-9 t); the final state goes to v_out (host).
+ * precision and correct_every as for lb_rk4_dense; the low-precision copy is
+ * made (and cached in the system) on first use.  Synchronous. */
+int lb_integrate(lb_system_t *sys, int precision, int correct_every, const double *v0,
+                 double t, double dt, double *v_out);
+
+/* ------------------------------------------------------------------------
+ * Measurement helpers (no counterpart in the paper).
+ * --------------------------------------------------------------------- */
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+long long lb_launch_count(void);
+
+/* FP64 fused multiply-add throughput of the current device in TFLOP/s
+ * (2 flops per FMA), measured with eight independent FMA chains per thread
+ * over 4 blocks of 256 threads per SM.  The roofline denominator of the
+ * FP64-bound kernels.  Synchronous. */
+int lb_probe_fp64(double *tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LINDBLAD_H */

@@ -62,6 +62,10 @@ def load_library():
         lib.ora_R.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
         lib.ora_R_entries.argtypes = [ctypes.c_void_p, _dp, _i64, _i64p, _i64p, _dp, _dp, _dp]
         lib.ora_Q_entries.argtypes = [ctypes.c_void_p, _dp, _i64, _i64p, _i64p, _dp]
+        lib.ora_R_rows_needed.restype = _i64
+        lib.ora_R_rows_needed.argtypes = [ctypes.c_void_p, _i64, _i64p, _i64p, _i64]
+        lib.ora_R_entries_rows.restype = ctypes.c_int
+        lib.ora_R_entries_rows.argtypes = [ctypes.c_void_p, _i64, _i64p, _dp, _i64, _i64p, _i64p, _dp, _dp]
         lib.ora_R_lowrank.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _i64p, _i64p,
                                       _dp, _dp, _dp, _u8p]
         lib.ora_rk4_dense.argtypes = [_i64, _dp, _dp, _dp, ctypes.c_double, _i64, _i64, _dp, _dp]
@@ -224,6 +228,28 @@ class Oracle:
         self.lib.ora_R_entries(self._ctx, _p(af), cnt, _p(s_idx, _i64p), _p(n_idx, _i64p),
                                _p(out), _p(im), _p(sc))
         return (out, im, sc) if with_scale else out
+
+    def rows_needed(self, s_idx):
+        """Sorted row indices of a read by R_entries_rows for rows s_idx."""
+        s_idx = np.ascontiguousarray(np.unique(s_idx), np.int64)
+        n = self.lib.ora_R_rows_needed(self._ctx, len(s_idx), _p(s_idx, _i64p), None, 0)
+        out = np.zeros(n, np.int64)
+        self.lib.ora_R_rows_needed(self._ctx, len(s_idx), _p(s_idx, _i64p), _p(out, _i64p), n)
+        return out
+
+    def R_entries_rows(self, row_ids, rows, s_idx, n_idx):
+        """Eq. (09) at (s_idx, n_idx) with a given by the rows row_ids (complex (r, M))."""
+        row_ids = np.ascontiguousarray(row_ids, np.int64)
+        rows, rf = _c128(rows)
+        s_idx = np.ascontiguousarray(s_idx, np.int64)
+        n_idx = np.ascontiguousarray(n_idx, np.int64)
+        out = np.zeros(len(s_idx))
+        sc = np.zeros(len(s_idx))
+        rc = self.lib.ora_R_entries_rows(self._ctx, len(row_ids), _p(row_ids, _i64p), _p(rf), len(s_idx),
+                                         _p(s_idx, _i64p), _p(n_idx, _i64p), _p(out), _p(sc))
+        if rc != 0:
+            raise ValueError("a row needed by the requested entries was not supplied")
+        return out, sc
 
     def Q_entries(self, h, s_idx, n_idx):
         h = np.ascontiguousarray(np.real(h), np.float64)

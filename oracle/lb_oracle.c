@@ -149,6 +149,24 @@ static void trace_with(const sp_mat *Fs, const double *Xr, const double *Xi,
     *tr = sr; *ti = si;
 }
 
+/* Same trace, summed over the touched positions of X instead (X sparse):
+ * Tr(F_s X) = sum over touched (q,p) of (F_s)_pq X_qp.  Entries of F_s are
+ * found by a scan of its (short) entry list. */
+static void trace_touched(const sp_mat *Fs, const scratch *X, double *tr, double *ti) {
+    int N = X->N;
+    double sr = 0, si = 0;
+    for (int t = 0; t < X->nt; ++t) {
+        int pos = X->touched[t], q = pos / N, p = pos % N;
+        for (int e = 0; e < Fs->nnz; ++e)
+            if (Fs->row[e] == p && Fs->col[e] == q) {
+                double xr = X->re[pos], xi = X->im[pos];
+                sr += Fs->re[e] * xr - Fs->im[e] * xi;
+                si += Fs->re[e] * xi + Fs->im[e] * xr;
+            }
+    }
+    *tr = sr; *ti = si;
+}
+
 /* growable triple list */
 typedef struct { int64_t n, cap; int32_t *idx; double *val; } tlist;
 
@@ -235,17 +253,20 @@ static void enumerate_fd(ora_ctx *c) {
                 scr_add(&Am, r, cc, pr, pi);
                 scr_add(&Am, cc, r, pr, -pi);     /* +(conj P)^T */
             }
-            /* candidate s: pairs on touched off-diagonal positions, all D */
+            /* candidate s: pairs on touched off-diagonal positions; every D
+             * if a diagonal position was touched (a D has only diagonal
+             * entries, so otherwise all its traces vanish) */
             int64_t ns = 0;
+            int diag = 0;
             for (int t = 0; t < Cm.nt; ++t) {
                 int p = Cm.touched[t], r = p / N, cc = p % N;
-                if (r == cc) continue;
+                if (r == cc) { diag = 1; continue; }
                 int a = r < cc ? r : cc, b = r < cc ? cc : r;
                 int64_t ps = pair_index(N, a, b);
                 if (!cand_mark[ps]) { cand_mark[ps] = 1; cand[ns++] = ps; }
                 if (!cand_mark[P + ps]) { cand_mark[P + ps] = 1; cand[ns++] = P + ps; }
             }
-            for (int l = 1; l < N; ++l) {
+            for (int l = 1; diag && l < N; ++l) {
                 int64_t s = 2 * P + (l - 1);
                 if (!cand_mark[s]) { cand_mark[s] = 1; cand[ns++] = s; }
             }
@@ -253,8 +274,14 @@ static void enumerate_fd(ora_ctx *c) {
                 int64_t s = cand[u];
                 cand_mark[s] = 0;
                 double cr, ci, ar, ai;
-                trace_with(&c->F[s], Cm.re, Cm.im, N, &cr, &ci);
-                trace_with(&c->F[s], Am.re, Am.im, N, &ar, &ai);
+                if (c->F[s].nnz <= 2 || Cm.nt <= 2) {
+                    /* short side: scan the touched positions */
+                    trace_touched(&c->F[s], &Cm, &cr, &ci);
+                    trace_touched(&c->F[s], &Am, &ar, &ai);
+                } else {
+                    trace_with(&c->F[s], Cm.re, Cm.im, N, &cr, &ci);
+                    trace_with(&c->F[s], Am.re, Am.im, N, &ar, &ai);
+                }
                 /* f = -i Tr(F_s C) -> real part = Im Tr(F_s C); d = Tr(F_s A) */
                 double fv = ci, dv = ar;
                 if (fv != 0.0 || dv != 0.0) {
@@ -641,6 +668,90 @@ void ora_R_entries(const ora_ctx *c, const double *a, int64_t cnt,
         if (out_scale) out_scale[e] = 0.25 * accs;
     }
     free_columns(&C);
+}
+
+/*
+ * The rows of a that ora_R_entries_rows needs for entries with row indices
+ * si: the first indices k of every f_kls with s in si (both terms of
+ * Eq. (09) read a only at (j,k) and (k,j) with such a k).  Returns the count;
+ * fills out (sorted, unique) when out != NULL and cap suffices.
+ */
+int64_t ora_R_rows_needed(const ora_ctx *c, int64_t cnt, const int64_t *si, int64_t *out, int64_t cap) {
+    int64_t M = c->M;
+    columns C;
+    build_columns(c, &C);
+    char *mark = (char *)calloc((size_t)M, 1);
+    for (int64_t e = 0; e < cnt; ++e)
+        for (int64_t q = C.fptr[si[e]]; q < C.fptr[si[e] + 1]; ++q) mark[C.fk[q]] = 1;
+    int64_t n = 0;
+    for (int64_t k = 0; k < M; ++k)
+        if (mark[k]) {
+            if (out && n < cap) out[n] = k;
+            n++;
+        }
+    free(mark);
+    free_columns(&C);
+    return n;
+}
+
+/*
+ * Eq. (09) at selected entries, with a given only by some of its rows:
+ * rows[r*M + j] = a_{row_ids[r], j} (row_ids sorted).  Same two-term form and
+ * prefactor as ora_R; an a_jk whose row is not supplied is read as
+ * conj(a_kj) (a is Hermitian).  Returns -1 if a needed value is missing.
+ */
+static int find_row(const int64_t *ids, int64_t n, int64_t k) {
+    int64_t lo = 0, hi = n - 1;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (ids[mid] == k) return (int)mid;
+        if (ids[mid] < k) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+int ora_R_entries_rows(const ora_ctx *c, int64_t nrows, const int64_t *row_ids, const double *rows,
+                       int64_t cnt, const int64_t *si, const int64_t *ni, double *out, double *out_scale) {
+    int64_t M = c->M;
+    columns C;
+    build_columns(c, &C);
+    int missing = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : missing)
+    for (int64_t e = 0; e < cnt; ++e) {
+        int64_t s = si[e], n = ni[e];
+        double accr = 0, accs = 0;
+        int64_t pf = C.fptr[s], ef = C.fptr[s + 1];
+        int64_t pz = C.zptr[n], ez = C.zptr[n + 1];
+        while (pf < ef && pz < ez) {
+            int32_t lf = C.fl[pf], lz = C.zl[pz];
+            if (lf < lz) { pf++; continue; }
+            if (lz < lf) { pz++; continue; }
+            int64_t f0 = pf, z0 = pz;
+            while (pf < ef && C.fl[pf] == lf) pf++;
+            while (pz < ez && C.zl[pz] == lf) pz++;
+            for (int64_t fq = f0; fq < pf; ++fq) {
+                int32_t y = C.fk[fq];
+                int r = find_row(row_ids, nrows, y);
+                if (r < 0) { missing = 1; continue; }
+                const double *row = rows + 2 * (size_t)r * M;
+                for (int64_t zq = z0; zq < pz; ++zq) {
+                    int32_t x = C.zj[zq];
+                    double zr = C.zr[zq], zi = C.zi[zq], fv = C.fv[fq];
+                    /* a_xy = conj(a_yx), a_yx from row y */
+                    double br = row[2 * (size_t)x], bi = row[2 * (size_t)x + 1];
+                    double ar = br, ai = -bi;
+                    double t1r = (ar * zr - ai * zi) * fv, t1i = (ar * zi + ai * zr) * fv;
+                    double t2r = (br * zr + bi * zi) * fv, t2i = (bi * zr - br * zi) * fv;
+                    accr += t1r + t2r;
+                    accs += sqrt(t1r * t1r + t1i * t1i) + sqrt(t2r * t2r + t2i * t2i);
+                }
+            }
+        }
+        out[e] = -0.25 * accr;
+        if (out_scale) out_scale[e] = 0.25 * accs;
+    }
+    free_columns(&C);
+    return missing ? -1 : 0;
 }
 
 /* Eq. (07) for selected entries. */

@@ -1,0 +1,11 @@
+"""GB300-native transformation of GKSL (Lindblad) equations into real linear
+ODE systems dv/dt = (Q + R) v + K over the generalized Gell-Mann basis, and
+their RK4 integration (Meyerov et al., Sec. 2 and Table 1).
+
+The computation lives in ``liblindblad.so`` (hand-written sm_103a CUDA
+behind the C ABI of ``include/lindblad.h``); ``native`` is its ctypes
+binding.  Build with ``python -m paper_1912_01491_gb300.build``.
+"""
+from . import native  # noqa: F401
+from .native import (LBError, Basis, System, pack_bf16, pack_fp32, rk4_dense,  # noqa: F401
+                     rk4_workspace)

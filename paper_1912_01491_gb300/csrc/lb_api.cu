@@ -1,0 +1,418 @@
+// lb_api.cu -- the extern "C" boundary of liblindblad.so (declared in
+// include/lindblad.h).  Argument checking, error codes, the thread-local
+// error text, device memory for the host-buffer interface, and launches of
+// the kernels in lb_basis.cu, lb_assemble.cu and lb_rk4.cu.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <cmath>
+#include <cub/cub.cuh>
+#include <string>
+
+#include "lb_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+// Owning device buffer (freed on scope exit unless released).
+struct DevBuf {
+  void* p = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t n) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    return cudaMalloc(&p, n ? n : 1);
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+  void* release() {
+    void* q = p;
+    p = nullptr;
+    return q;
+  }
+};
+
+#define LB_TRY_CUDA(call, what)                          \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return lbi::cuda_fail(_e, what); \
+  } while (0)
+
+#define LB_REQUIRE(cond, ...)        \
+  do {                               \
+    if (!(cond)) {                   \
+      lbi::set_error(__VA_ARGS__);   \
+      return LB_EINVAL;              \
+    }                                \
+  } while (0)
+
+inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+int alloc_or_enomem(DevBuf& b, size_t n, const char* what) {
+  cudaError_t e = b.alloc(n);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    lbi::set_error("device allocation of %zu bytes for %s refused", n, what);
+    return LB_ENOMEM;
+  }
+  if (e != cudaSuccess) return lbi::cuda_fail(e, what);
+  return LB_OK;
+}
+
+}  // namespace
+
+namespace lbi {
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  return LB_ECUDA;
+}
+
+}  // namespace lbi
+
+struct lb_system {
+  const lb_basis* basis = nullptr;
+  int64_t M = 0;
+  double* A = nullptr;
+  double* Q = nullptr;
+  double* R = nullptr;
+  double* K = nullptr;
+  float* A32 = nullptr;
+  uint16_t* Abf = nullptr;
+  float* scale = nullptr;
+};
+
+extern "C" {
+
+const char* lb_last_error(void) { return g_err.c_str(); }
+
+int lb_version(void) { return 100; }
+
+int lb_basis_create(int N, void* stream, lb_basis_t** out) {
+  LB_REQUIRE(out != nullptr, "lb_basis_create: out is NULL");
+  LB_REQUIRE(N >= 2 && N <= 4096, "lb_basis_create: N = %d outside [2, 4096]", N);
+  *out = nullptr;
+  const int64_t P = (int64_t)N * (N - 1) / 2;
+  DevBuf pab, c, lc;
+  int rc;
+  if ((rc = alloc_or_enomem(pab, sizeof(int32_t) * P, "pair table")) != LB_OK) return rc;
+  if ((rc = alloc_or_enomem(c, sizeof(double) * N, "basis constants")) != LB_OK) return rc;
+  if ((rc = alloc_or_enomem(lc, sizeof(double) * N, "basis constants")) != LB_OK) return rc;
+  LB_TRY_CUDA(lbi::build_tables(N, pab.as<int32_t>(), c.as<double>(), lc.as<double>(), S(stream)),
+              "basis tables");
+  LB_TRY_CUDA(cudaStreamSynchronize(S(stream)), "basis tables");
+  lb_basis* b = new lb_basis;
+  b->N = N;
+  b->P = P;
+  b->M = (int64_t)N * N - 1;
+  b->d_pair_ab = static_cast<int32_t*>(pab.release());
+  b->d_c = static_cast<double*>(c.release());
+  b->d_lc = static_cast<double*>(lc.release());
+  *out = b;
+  return LB_OK;
+}
+
+int lb_basis_destroy(lb_basis_t* b) {
+  if (!b) return LB_OK;
+  cudaFree(b->d_pair_ab);
+  cudaFree(b->d_c);
+  cudaFree(b->d_lc);
+  delete b;
+  return LB_OK;
+}
+
+int lb_basis_dims(const lb_basis_t* b, int* N, int64_t* M, int64_t* P) {
+  LB_REQUIRE(b != nullptr, "lb_basis_dims: basis is NULL");
+  if (N) *N = b->N;
+  if (M) *M = b->M;
+  if (P) *P = b->P;
+  return LB_OK;
+}
+
+int lb_basis_label(const lb_basis_t* b, int64_t i, char* type, int* j, int* k) {
+  LB_REQUIRE(b != nullptr, "lb_basis_label: basis is NULL");
+  LB_REQUIRE(i >= 0 && i < b->M, "lb_basis_label: index %lld outside [0, %lld)", (long long)i,
+             (long long)b->M);
+  char t;
+  int a, c;
+  if (i < 2 * b->P) {
+    int64_t p = i < b->P ? i : i - b->P;
+    t = i < b->P ? 'S' : 'J';
+    a = 0;
+    while (p >= b->N - 1 - a) {
+      p -= b->N - 1 - a;
+      ++a;
+    }
+    c = a + 1 + (int)p;
+  } else {
+    t = 'D';
+    a = c = (int)(i - 2 * b->P + 1);
+  }
+  if (type) *type = t;
+  if (j) *j = a;
+  if (k) *k = c;
+  return LB_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// count per m -> exclusive scan; offsets has M+1 entries, offsets[M] = total.
+int count_and_scan(const lb_basis_t* b, int which, DevBuf& offsets, int64_t* total, cudaStream_t st) {
+  const int64_t M = b->M;
+  int rc;
+  DevBuf per;
+  if ((rc = alloc_or_enomem(per, sizeof(int64_t) * (M + 1), "structure counts")) != LB_OK) return rc;
+  if ((rc = alloc_or_enomem(offsets, sizeof(int64_t) * (M + 1), "structure offsets")) != LB_OK) return rc;
+  LB_TRY_CUDA(cudaMemsetAsync(per.as<int64_t>() + M, 0, sizeof(int64_t), st), "structure counts");
+  LB_TRY_CUDA(lbi::structure_count(b->view(), which, per.as<int64_t>(), st), "kernel (a) count");
+  size_t tmp = 0;
+  LB_TRY_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, per.as<int64_t>(), offsets.as<int64_t>(),
+                                            (int)(M + 1), st),
+              "scan");
+  DevBuf tb;
+  if ((rc = alloc_or_enomem(tb, tmp, "scan workspace")) != LB_OK) return rc;
+  LB_TRY_CUDA(cub::DeviceScan::ExclusiveSum(tb.p, tmp, per.as<int64_t>(), offsets.as<int64_t>(),
+                                            (int)(M + 1), st),
+              "scan");
+  LB_TRY_CUDA(cudaMemcpyAsync(total, offsets.as<int64_t>() + M, sizeof(int64_t),
+                              cudaMemcpyDeviceToHost, st),
+              "structure total");
+  LB_TRY_CUDA(cudaStreamSynchronize(st), "kernel (a)");
+  return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_structure_count(const lb_basis_t* b, int which, int64_t* nnz) {
+  LB_REQUIRE(b != nullptr && nnz != nullptr, "lb_structure_count: NULL argument");
+  LB_REQUIRE(which == LB_F || which == LB_D, "lb_structure_count: which = %d", which);
+  DevBuf off;
+  return count_and_scan(b, which, off, nnz, nullptr);
+}
+
+int lb_structure_export(const lb_basis_t* b, int which, int32_t* idx3, double* val, int64_t capacity,
+                        int64_t* nnz, void* stream) {
+  LB_REQUIRE(b != nullptr && nnz != nullptr, "lb_structure_export: NULL argument");
+  LB_REQUIRE(which == LB_F || which == LB_D, "lb_structure_export: which = %d", which);
+  LB_REQUIRE(b->M <= 0x7fffffffLL, "lb_structure_export: M too large for int32 indices");
+  DevBuf off;
+  int64_t total = 0;
+  int rc = count_and_scan(b, which, off, &total, S(stream));
+  if (rc != LB_OK) return rc;
+  *nnz = total;
+  LB_REQUIRE(idx3 != nullptr && val != nullptr, "lb_structure_export: NULL output buffer");
+  LB_REQUIRE(capacity >= total, "lb_structure_export: capacity %lld < %lld triples",
+             (long long)capacity, (long long)total);
+  LB_TRY_CUDA(lbi::structure_fill(b->view(), which, off.as<int64_t>(), idx3, val, S(stream)),
+              "kernel (a) fill");
+  // offsets are freed at scope exit: wait for the fill that reads them
+  LB_TRY_CUDA(cudaStreamSynchronize(S(stream)), "kernel (a) fill");
+  return LB_OK;
+}
+
+int lb_join_terms(const lb_basis_t* b, int64_t* W) {
+  LB_REQUIRE(b != nullptr && W != nullptr, "lb_join_terms: NULL argument");
+  DevBuf cnt;
+  int rc;
+  if ((rc = alloc_or_enomem(cnt, sizeof(unsigned long long), "term counter")) != LB_OK) return rc;
+  LB_TRY_CUDA(cudaMemset(cnt.p, 0, sizeof(unsigned long long)), "term counter");
+  LB_TRY_CUDA(lbi::join_terms(b->view(), cnt.as<unsigned long long>(), nullptr), "join-term count");
+  unsigned long long h = 0;
+  LB_TRY_CUDA(cudaMemcpy(&h, cnt.p, sizeof h, cudaMemcpyDeviceToHost), "join-term count");
+  *W = (int64_t)h;
+  return LB_OK;
+}
+
+int lb_expand(const lb_basis_t* b, const double* A, double* coef, void* stream) {
+  LB_REQUIRE(b && A && coef, "lb_expand: NULL argument");
+  LB_TRY_CUDA(lbi::expand(b->view(), reinterpret_cast<const double2*>(A), reinterpret_cast<double2*>(coef),
+                          S(stream)),
+              "lb_expand");
+  return LB_OK;
+}
+
+int lb_rho(const lb_basis_t* b, const double* v, double* rho, void* stream) {
+  LB_REQUIRE(b && v && rho, "lb_rho: NULL argument");
+  LB_TRY_CUDA(lbi::rho(b->view(), v, reinterpret_cast<double2*>(rho), S(stream)), "lb_rho");
+  return LB_OK;
+}
+
+int lb_assemble_dense(const lb_basis_t* b, const double* h, const double* a, double* A, double* Q,
+                      double* R, double* K, void* stream) {
+  LB_REQUIRE(b != nullptr && a != nullptr, "lb_assemble_dense: NULL basis or a");
+  LB_REQUIRE(A || Q || R || K, "lb_assemble_dense: no output requested");
+  LB_REQUIRE(b->M <= 0x7fffffffLL, "lb_assemble_dense: M too large");
+  LB_TRY_CUDA(lbi::assemble_dense(b->view(), h, reinterpret_cast<const double2*>(a), A, Q, R, K, S(stream)),
+              "lb_assemble_dense");
+  return LB_OK;
+}
+
+int lb_pack_fp32(int64_t M, const double* A, float* A32, void* stream) {
+  LB_REQUIRE(M > 0 && A && A32, "lb_pack_fp32: bad argument");
+  LB_TRY_CUDA(lbi::pack_fp32(M, A, A32, S(stream)), "lb_pack_fp32");
+  return LB_OK;
+}
+
+int lb_pack_bf16(int64_t M, const double* A, uint16_t* Abf, float* row_scale, void* stream) {
+  LB_REQUIRE(M > 0 && A && Abf && row_scale, "lb_pack_bf16: bad argument");
+  LB_TRY_CUDA(lbi::pack_bf16(M, A, Abf, row_scale, S(stream)), "lb_pack_bf16");
+  return LB_OK;
+}
+
+size_t lb_rk4_workspace_bytes(int64_t M) { return M > 0 ? lbi::rk4_workspace_bytes(M) : 0; }
+
+int lb_rk4_dense(int64_t M, int precision, const void* Ap, const float* row_scale, const double* A64,
+                 int correct_every, const double* K, double* v, double dt, int64_t nsteps, double* snaps,
+                 int64_t snap_every, void* work, void* stream) {
+  LB_REQUIRE(M > 0 && Ap && K && v && work, "lb_rk4_dense: NULL argument or M <= 0");
+  LB_REQUIRE(precision == LB_FP64 || precision == LB_FP32 || precision == LB_BF16,
+             "lb_rk4_dense: precision = %d", precision);
+  LB_REQUIRE(precision != LB_BF16 || row_scale, "lb_rk4_dense: BF16 needs row_scale");
+  LB_REQUIRE(nsteps >= 0 && std::isfinite(dt), "lb_rk4_dense: bad step count or dt");
+  LB_REQUIRE(!snaps || snap_every > 0, "lb_rk4_dense: snaps given without snap_every");
+  LB_REQUIRE(correct_every >= 0, "lb_rk4_dense: correct_every < 0");
+  LB_TRY_CUDA(lbi::rk4_dense(M, precision, Ap, row_scale, A64, correct_every, K, v, dt, nsteps, snaps,
+                             snap_every, work, S(stream)),
+              "lb_rk4_dense");
+  return LB_OK;
+}
+
+// ------------------------------------------------------------------ host API
+
+int lb_assemble(const lb_basis_t* b, const double* H, const double* a, int keep_parts, lb_system_t** out) {
+  LB_REQUIRE(b && a && out, "lb_assemble: NULL argument");
+  *out = nullptr;
+  const int64_t M = b->M, N = b->N;
+  const size_t mm = (size_t)M * (size_t)M;
+  size_t need = 16 * mm + 8 * mm * (keep_parts ? 3 : 1) + 64 * (size_t)M;
+  size_t fr = 0, tot = 0;
+  LB_TRY_CUDA(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+  if (need > fr) {
+    lbi::set_error("lb_assemble: needs %zu bytes of device memory, %zu free", need, fr);
+    return LB_ENOMEM;
+  }
+  int rc;
+  DevBuf da, dA, dQ, dR, dK, dH, dcoef, dh;
+  if ((rc = alloc_or_enomem(da, 16 * mm, "a")) != LB_OK) return rc;
+  if ((rc = alloc_or_enomem(dA, 8 * mm, "A")) != LB_OK) return rc;
+  if ((rc = alloc_or_enomem(dK, 8 * (size_t)M, "K")) != LB_OK) return rc;
+  if (keep_parts) {
+    if ((rc = alloc_or_enomem(dQ, 8 * mm, "Q")) != LB_OK) return rc;
+    if ((rc = alloc_or_enomem(dR, 8 * mm, "R")) != LB_OK) return rc;
+  }
+  LB_TRY_CUDA(cudaMemcpy(da.p, a, 16 * mm, cudaMemcpyHostToDevice), "copy a");
+  if (H) {
+    if ((rc = alloc_or_enomem(dH, 16 * (size_t)N * N, "H")) != LB_OK) return rc;
+    if ((rc = alloc_or_enomem(dcoef, 16 * (size_t)M, "h")) != LB_OK) return rc;
+    if ((rc = alloc_or_enomem(dh, 8 * (size_t)M, "h")) != LB_OK) return rc;
+    LB_TRY_CUDA(cudaMemcpy(dH.p, H, 16 * (size_t)N * N, cudaMemcpyHostToDevice), "copy H");
+    LB_TRY_CUDA(lbi::expand(b->view(), dH.as<double2>(), dcoef.as<double2>(), nullptr), "expand H");
+    // h_m = Re coef_m (strided copy of the real parts)
+    LB_TRY_CUDA(cudaMemcpy2D(dh.p, sizeof(double), dcoef.p, 2 * sizeof(double), sizeof(double), (size_t)M,
+                             cudaMemcpyDeviceToDevice),
+                "real part of h");
+  }
+  LB_TRY_CUDA(lbi::assemble_dense(b->view(), H ? dh.as<double>() : nullptr, da.as<double2>(), dA.as<double>(),
+                                  dQ.as<double>(), dR.as<double>(), dK.as<double>(), nullptr),
+              "assemble");
+  LB_TRY_CUDA(cudaDeviceSynchronize(), "assemble");
+  lb_system* s = new lb_system;
+  s->basis = b;
+  s->M = M;
+  s->A = static_cast<double*>(dA.release());
+  s->K = static_cast<double*>(dK.release());
+  s->Q = static_cast<double*>(dQ.release());
+  s->R = static_cast<double*>(dR.release());
+  *out = s;
+  return LB_OK;
+}
+
+int lb_system_destroy(lb_system_t* s) {
+  if (!s) return LB_OK;
+  cudaFree(s->A);
+  cudaFree(s->Q);
+  cudaFree(s->R);
+  cudaFree(s->K);
+  cudaFree(s->A32);
+  cudaFree(s->Abf);
+  cudaFree(s->scale);
+  delete s;
+  return LB_OK;
+}
+
+int lb_system_get(const lb_system_t* s, int part, double* out) {
+  LB_REQUIRE(s && out, "lb_system_get: NULL argument");
+  const double* src = part == LB_SYS_A ? s->A : part == LB_SYS_Q ? s->Q : part == LB_SYS_R ? s->R
+                      : part == LB_SYS_K ? s->K : nullptr;
+  LB_REQUIRE(src != nullptr, "lb_system_get: part %d not available", part);
+  const size_t n = part == LB_SYS_K ? (size_t)s->M : (size_t)s->M * (size_t)s->M;
+  LB_TRY_CUDA(cudaMemcpy(out, src, 8 * n, cudaMemcpyDeviceToHost), "lb_system_get");
+  return LB_OK;
+}
+
+int lb_integrate(lb_system_t* s, int precision, int correct_every, const double* v0, double t, double dt,
+                 double* v_out) {
+  LB_REQUIRE(s && v0 && v_out, "lb_integrate: NULL argument");
+  LB_REQUIRE(dt > 0 && t >= 0 && std::isfinite(t) && std::isfinite(dt), "lb_integrate: bad t or dt");
+  const double nr = std::nearbyint(t / dt);
+  const int64_t n = (int64_t)nr;
+  LB_REQUIRE(std::fabs(nr * dt - t) <= 1e-9 * t, "lb_integrate: t = %g is not a multiple of dt = %g", t, dt);
+  const int64_t M = s->M;
+  const size_t mm = (size_t)M * (size_t)M;
+  int rc;
+  const void* Ap = s->A;
+  if (precision == LB_FP32) {
+    if (!s->A32) {
+      DevBuf b32;
+      if ((rc = alloc_or_enomem(b32, 4 * mm, "A32")) != LB_OK) return rc;
+      LB_TRY_CUDA(lbi::pack_fp32(M, s->A, b32.as<float>(), nullptr), "pack fp32");
+      s->A32 = static_cast<float*>(b32.release());
+    }
+    Ap = s->A32;
+  } else if (precision == LB_BF16) {
+    if (!s->Abf) {
+      DevBuf bb, sc;
+      if ((rc = alloc_or_enomem(bb, 2 * mm, "Abf16")) != LB_OK) return rc;
+      if ((rc = alloc_or_enomem(sc, 4 * (size_t)M, "row scales")) != LB_OK) return rc;
+      LB_TRY_CUDA(lbi::pack_bf16(M, s->A, bb.as<uint16_t>(), sc.as<float>(), nullptr), "pack bf16");
+      s->Abf = static_cast<uint16_t*>(bb.release());
+      s->scale = static_cast<float*>(sc.release());
+    }
+    Ap = s->Abf;
+  } else {
+    LB_REQUIRE(precision == LB_FP64, "lb_integrate: precision = %d", precision);
+  }
+  DevBuf dv, work;
+  if ((rc = alloc_or_enomem(dv, 8 * (size_t)M, "v")) != LB_OK) return rc;
+  if ((rc = alloc_or_enomem(work, lbi::rk4_workspace_bytes(M), "RK4 workspace")) != LB_OK) return rc;
+  LB_TRY_CUDA(cudaMemcpy(dv.p, v0, 8 * (size_t)M, cudaMemcpyHostToDevice), "copy v0");
+  LB_TRY_CUDA(lbi::rk4_dense(M, precision, Ap, s->scale, s->A, correct_every, s->K, dv.as<double>(), dt, n,
+                             nullptr, 0, work.p, nullptr),
+              "RK4");
+  LB_TRY_CUDA(cudaMemcpy(v_out, dv.p, 8 * (size_t)M, cudaMemcpyDeviceToHost), "copy v");
+  return LB_OK;
+}
+
+}  // extern "C"

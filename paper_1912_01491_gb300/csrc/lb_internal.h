@@ -1,0 +1,61 @@
+// lb_internal.h -- declarations shared by the translation units of
+// liblindblad.so (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "lindblad.h"
+#include "su_n.cuh"
+
+// Device-resident basis: index tables plus (for N <= kMaxListN) the
+// canonical nonzero f and d lists produced by kernel (a).
+struct lb_basis {
+  int N;
+  int64_t P, M;
+  int32_t* d_pair_ab = nullptr;  // P
+  double* d_c = nullptr;         // N
+  double* d_lc = nullptr;        // N
+  int64_t nnz[2] = {0, 0};       // canonical counts of f, d
+  int32_t* d_idx[2] = {nullptr, nullptr};
+  double* d_val[2] = {nullptr, nullptr};
+  lb::BasisView view() const {
+    lb::BasisView v;
+    v.N = N; v.P = P; v.M = M;
+    v.pair_ab = d_pair_ab; v.c = d_c; v.lc = d_lc;
+    return v;
+  }
+};
+
+namespace lbi {
+
+constexpr int kMaxListN = 512;
+
+void set_error(const char* fmt, ...);
+void note_launch(int n);
+int cuda_fail(cudaError_t e, const char* what);
+
+// kernel (a) and friends (lb_basis.cu)
+cudaError_t build_tables(int N, int32_t* pair_ab, double* c, double* lc, cudaStream_t st);
+cudaError_t structure_count(const lb::BasisView& B, int which, int64_t* per_m, cudaStream_t st);
+cudaError_t structure_fill(const lb::BasisView& B, int which, const int64_t* offsets,
+                           int32_t* idx3, double* val, cudaStream_t st);
+cudaError_t expand(const lb::BasisView& B, const double2* A, double2* coef, cudaStream_t st);
+cudaError_t rho(const lb::BasisView& B, const double* v, double2* out, cudaStream_t st);
+
+// dense assembly (lb_assemble.cu)
+cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double2* a,
+                           double* A, double* Q, double* R, double* K, cudaStream_t st);
+cudaError_t join_terms(const lb::BasisView& B, unsigned long long* d_count, cudaStream_t st);
+
+// RK4 (lb_rk4.cu)
+cudaError_t pack_fp32(int64_t M, const double* A, float* A32, cudaStream_t st);
+cudaError_t pack_bf16(int64_t M, const double* A, uint16_t* Ab, float* scale, cudaStream_t st);
+size_t rk4_workspace_bytes(int64_t M);
+cudaError_t rk4_dense(int64_t M, int precision, const void* Ap, const float* scale,
+                      const double* A64, int correct_every, const double* K, double* v,
+                      double dt, int64_t nsteps, double* snaps, int64_t snap_every,
+                      void* work, cudaStream_t st);
+
+}  // namespace lbi

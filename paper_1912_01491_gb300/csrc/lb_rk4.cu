@@ -1,0 +1,260 @@
+// lb_rk4.cu -- kernel (c): classical fourth-order Runge-Kutta for
+// dv/dt = A v + K (Eq. (04) with time-independent Q and R; Table 1 step 3.1,
+// Sec. 4 item 3), as one fused GEMV + stage-update kernel per RK stage.
+//
+// Stage i computes k_i = A x_i + K row by row (one warp per row) and, in the
+// same kernel's epilogue, forms the next stage input and the running
+// combination:
+//   stage 1: acc  = k1,     x2 = v + h/2 k1
+//   stage 2: acc += 2 k2,   x3 = v + h/2 k2
+//   stage 3: acc += 2 k3,   x4 = v + h k3
+//   stage 4: v   += h/6 (acc + k4),  x1' = v
+// so each stage reads A once and O(M) vectors, and nothing else.
+//
+// Storage precisions (a6): FP64; FP32 (A32 = fl32(A)); BF16 with per-row
+// scales r_s = max_n |A_sn|.  For FP32/BF16 the products use FP32 multiply-
+// adds on an FP32 copy of the stage vector, per-lane partial sums are FP32
+// and the 32 lane sums are combined in FP64; state and stage combination
+// stay FP64.  Optional FP64 defect correction (a8): every k steps
+// c = (A64 - A_lp) v at the current v, added to K until the next one.
+#include <cuda_bf16.h>
+
+#include "lb_internal.h"
+
+namespace {
+
+constexpr int kWarpsPerBlock = 8;
+
+__device__ __forceinline__ float bf16_bits_to_float(uint16_t u) {
+  return __uint_as_float(((uint32_t)u) << 16);
+}
+
+template <int PREC>
+__device__ __forceinline__ double row_dot(int64_t M, int64_t s, const void* __restrict__ Ap,
+                                          const float* __restrict__ scale,
+                                          const double* __restrict__ x,
+                                          const float* __restrict__ x32, int lane) {
+  if (PREC == LB_FP64) {
+    const double* __restrict__ row = static_cast<const double*>(Ap) + s * M;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int64_t n = lane;
+    for (; n + 96 < M; n += 128) {
+      a0 = fma(__ldcs(row + n), __ldg(x + n), a0);
+      a1 = fma(__ldcs(row + n + 32), __ldg(x + n + 32), a1);
+      a2 = fma(__ldcs(row + n + 64), __ldg(x + n + 64), a2);
+      a3 = fma(__ldcs(row + n + 96), __ldg(x + n + 96), a3);
+    }
+    for (; n < M; n += 32) a0 = fma(__ldcs(row + n), __ldg(x + n), a0);
+    double t = (a0 + a1) + (a2 + a3);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
+  } else if (PREC == LB_FP32) {
+    const float* __restrict__ row = static_cast<const float*>(Ap) + s * M;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int64_t n = lane;
+    for (; n + 96 < M; n += 128) {
+      a0 = fmaf(__ldcs(row + n), __ldg(x32 + n), a0);
+      a1 = fmaf(__ldcs(row + n + 32), __ldg(x32 + n + 32), a1);
+      a2 = fmaf(__ldcs(row + n + 64), __ldg(x32 + n + 64), a2);
+      a3 = fmaf(__ldcs(row + n + 96), __ldg(x32 + n + 96), a3);
+    }
+    for (; n < M; n += 32) a0 = fmaf(__ldcs(row + n), __ldg(x32 + n), a0);
+    double t = ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
+  } else {
+    const uint16_t* __restrict__ row = static_cast<const uint16_t*>(Ap) + s * M;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int64_t n = lane;
+    for (; n + 96 < M; n += 128) {
+      a0 = fmaf(bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(row + n))), __ldg(x32 + n), a0);
+      a1 = fmaf(bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(row + n + 32))), __ldg(x32 + n + 32), a1);
+      a2 = fmaf(bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(row + n + 64))), __ldg(x32 + n + 64), a2);
+      a3 = fmaf(bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(row + n + 96))), __ldg(x32 + n + 96), a3);
+    }
+    for (; n < M; n += 32)
+      a0 = fmaf(bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(row + n))), __ldg(x32 + n), a0);
+    double t = ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t * (double)__ldg(scale + s);
+  }
+}
+
+template <int PREC, int STAGE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_stage(int64_t M, const void* __restrict__ Ap, const float* __restrict__ scale,
+            const double* __restrict__ Keff, const double* __restrict__ x,
+            const float* __restrict__ x32, double* __restrict__ xn, float* __restrict__ xn32,
+            double* __restrict__ acc, double* __restrict__ v, double h) {
+  const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= M) return;
+  const double y = row_dot<PREC>(M, s, Ap, scale, x, x32, lane);
+  if (lane != 0) return;
+  const double k = y + Keff[s];
+  double nx;
+  if (STAGE == 1) {
+    acc[s] = k;
+    nx = v[s] + 0.5 * h * k;
+  } else if (STAGE == 2) {
+    acc[s] += 2.0 * k;
+    nx = v[s] + 0.5 * h * k;
+  } else if (STAGE == 3) {
+    acc[s] += 2.0 * k;
+    nx = v[s] + h * k;
+  } else {
+    nx = v[s] + (h / 6.0) * (acc[s] + k);
+    v[s] = nx;
+  }
+  xn[s] = nx;
+  if (PREC != LB_FP64) xn32[s] = (float)nx;
+}
+
+// c = (A64 - A_lp) v in FP64;  Keff = K + c.
+template <int PREC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_correction(int64_t M, const double* __restrict__ A64, const void* __restrict__ Ap,
+                 const float* __restrict__ scale, const double* __restrict__ v,
+                 const double* __restrict__ K, double* __restrict__ Keff) {
+  const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= M) return;
+  const double* __restrict__ r64 = A64 + s * M;
+  double t = 0.0;
+  if (PREC == LB_FP32) {
+    const float* __restrict__ r = static_cast<const float*>(Ap) + s * M;
+    for (int64_t n = lane; n < M; n += 32) t = fma(__ldcs(r64 + n) - (double)__ldcs(r + n), v[n], t);
+  } else {
+    const uint16_t* __restrict__ r = static_cast<const uint16_t*>(Ap) + s * M;
+    const double sc = (double)scale[s];
+    for (int64_t n = lane; n < M; n += 32) {
+      const double q = (double)bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(r + n))) * sc;
+      t = fma(__ldcs(r64 + n) - q, v[n], t);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) Keff[s] = K[s] + t;
+}
+
+__global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) b[i] = (float)a[i];
+}
+
+// One warp per row: r_s = max |A_sn| (as float), then bf16(A_sn / r_s).
+__global__ void k_pack_bf16(int64_t M, const double* __restrict__ A, uint16_t* __restrict__ Ab,
+                            float* __restrict__ scale) {
+  const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= M) return;
+  const double* row = A + s * M;
+  double mx = 0.0;
+  for (int64_t n = lane; n < M; n += 32) mx = fmax(mx, fabs(row[n]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  float r = (float)mx;
+  if (!(r > 0.f)) r = 1.f;
+  const double inv = 1.0 / (double)r;
+  uint16_t* out = Ab + s * M;
+  for (int64_t n = lane; n < M; n += 32) {
+    __nv_bfloat16 q = __double2bfloat16(row[n] * inv);
+    out[n] = *reinterpret_cast<uint16_t*>(&q);
+  }
+  if (lane == 0) scale[s] = r;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Work {
+  double *X, *Y, *acc, *Keff;
+  float *X32, *Y32;
+};
+
+Work carve(void* base, int64_t M) {
+  char* p = static_cast<char*>(base);
+  Work w;
+  size_t d = align256(sizeof(double) * (size_t)M), f = align256(sizeof(float) * (size_t)M);
+  w.X = reinterpret_cast<double*>(p); p += d;
+  w.Y = reinterpret_cast<double*>(p); p += d;
+  w.acc = reinterpret_cast<double*>(p); p += d;
+  w.Keff = reinterpret_cast<double*>(p); p += d;
+  w.X32 = reinterpret_cast<float*>(p); p += f;
+  w.Y32 = reinterpret_cast<float*>(p);
+  return w;
+}
+
+template <int PREC>
+cudaError_t run_steps(int64_t M, const void* Ap, const float* scale, const double* A64,
+                      int correct_every, const double* K, double* v, double dt, int64_t nsteps,
+                      double* snaps, int64_t snap_every, const Work& w, cudaStream_t st) {
+  const unsigned grid = (unsigned)((M + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  const unsigned bs = kWarpsPerBlock * 32;
+  cudaError_t e;
+  e = cudaMemcpyAsync(w.X, v, sizeof(double) * M, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(w.Keff, K, sizeof(double) * M, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  if (PREC != LB_FP64) {
+    k_to_f32<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, v, w.X32);
+    lbi::note_launch(1);
+  }
+  const bool correct = PREC != LB_FP64 && correct_every > 0 && A64 != nullptr;
+  for (int64_t t = 0; t < nsteps; ++t) {
+    if (correct && t % correct_every == 0) {
+      k_correction<PREC><<<grid, bs, 0, st>>>(M, A64, Ap, scale, v, K, w.Keff);
+      lbi::note_launch(1);
+    }
+    k_stage<PREC, 1><<<grid, bs, 0, st>>>(M, Ap, scale, w.Keff, w.X, w.X32, w.Y, w.Y32, w.acc, v, dt);
+    k_stage<PREC, 2><<<grid, bs, 0, st>>>(M, Ap, scale, w.Keff, w.Y, w.Y32, w.X, w.X32, w.acc, v, dt);
+    k_stage<PREC, 3><<<grid, bs, 0, st>>>(M, Ap, scale, w.Keff, w.X, w.X32, w.Y, w.Y32, w.acc, v, dt);
+    k_stage<PREC, 4><<<grid, bs, 0, st>>>(M, Ap, scale, w.Keff, w.Y, w.Y32, w.X, w.X32, w.acc, v, dt);
+    lbi::note_launch(4);
+    if (snaps && snap_every > 0 && (t + 1) % snap_every == 0) {
+      e = cudaMemcpyAsync(snaps + ((t + 1) / snap_every - 1) * M, v, sizeof(double) * M,
+                          cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace lbi {
+
+cudaError_t pack_fp32(int64_t M, const double* A, float* A32, cudaStream_t st) {
+  const int64_t n = M * M;
+  k_to_f32<<<4 * 152 * 8, 256, 0, st>>>(n, A, A32);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t pack_bf16(int64_t M, const double* A, uint16_t* Ab, float* scale, cudaStream_t st) {
+  k_pack_bf16<<<(unsigned)((M + kWarpsPerBlock - 1) / kWarpsPerBlock), kWarpsPerBlock * 32, 0, st>>>(
+      M, A, Ab, scale);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+size_t rk4_workspace_bytes(int64_t M) {
+  return 4 * align256(sizeof(double) * (size_t)M) + 2 * align256(sizeof(float) * (size_t)M);
+}
+
+cudaError_t rk4_dense(int64_t M, int precision, const void* Ap, const float* scale,
+                      const double* A64, int correct_every, const double* K, double* v, double dt,
+                      int64_t nsteps, double* snaps, int64_t snap_every, void* work,
+                      cudaStream_t st) {
+  Work w = carve(work, M);
+  switch (precision) {
+    case LB_FP64:
+      return run_steps<LB_FP64>(M, Ap, scale, A64, correct_every, K, v, dt, nsteps, snaps, snap_every, w, st);
+    case LB_FP32:
+      return run_steps<LB_FP32>(M, Ap, scale, A64, correct_every, K, v, dt, nsteps, snaps, snap_every, w, st);
+    case LB_BF16:
+      return run_steps<LB_BF16>(M, Ap, scale, A64, correct_every, K, v, dt, nsteps, snaps, snap_every, w, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace lbi

@@ -1,0 +1,302 @@
+"""ctypes binding of liblindblad.so (include/lindblad.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch supplies device memory (tensors' data_ptr) and streams.
+If the shared library is missing this module raises: there is no CPU
+fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblindblad.so")
+
+LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ETIMEOUT, LB_EUNSUPPORTED, LB_EAGAIN = range(7)
+LB_F, LB_D = 0, 1
+LB_FP64, LB_FP32, LB_BF16 = 0, 1, 2
+LB_SYS_A, LB_SYS_Q, LB_SYS_R, LB_SYS_K = 0, 1, 2, 3
+PRECISIONS = {"fp64": LB_FP64, "fp32": LB_FP32, "bf16": LB_BF16}
+
+_c_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+_lib = None
+
+
+class LBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("liblindblad error %d: %s" % (code, msg))
+        self.code = code
+
+
+def load():
+    """Load liblindblad.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            "liblindblad.so is not built (%s); run `python -m paper_1912_01491_gb300.build` "
+            "or __graft_entry__.build() -- there is no CPU fallback" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "lb_last_error": (ctypes.c_char_p, []),
+        "lb_version": (ctypes.c_int, []),
+        "lb_basis_create": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+        "lb_basis_destroy": (ctypes.c_int, [_vp]),
+        "lb_basis_dims": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), _i64p, _i64p]),
+        "lb_basis_label": (ctypes.c_int, [_vp, _c_i64, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
+        "lb_structure_count": (ctypes.c_int, [_vp, ctypes.c_int, _i64p]),
+        "lb_structure_export": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_i64, _i64p, _vp]),
+        "lb_join_terms": (ctypes.c_int, [_vp, _i64p]),
+        "lb_expand": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+        "lb_rho": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+        "lb_assemble_dense": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "lb_pack_fp32": (ctypes.c_int, [_c_i64, _vp, _vp, _vp]),
+        "lb_pack_bf16": (ctypes.c_int, [_c_i64, _vp, _vp, _vp, _vp]),
+        "lb_rk4_workspace_bytes": (ctypes.c_size_t, [_c_i64]),
+        "lb_rk4_dense": (ctypes.c_int, [_c_i64, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp, _vp,
+                                        ctypes.c_double, _c_i64, _vp, _c_i64, _vp, _vp]),
+        "lb_assemble": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)]),
+        "lb_system_destroy": (ctypes.c_int, [_vp]),
+        "lb_system_get": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+        "lb_integrate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double,
+                                        ctypes.c_double, _vp]),
+        "lb_launch_count": (ctypes.c_longlong, []),
+        "lb_probe_fp64": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names the binding declares (each must be exported by the library)."""
+    load()
+    return [n for n in dir(_lib) if n.startswith("lb_")]
+
+
+def launch_count():
+    """Kernels launched by liblindblad.so in this process."""
+    return int(load().lb_launch_count())
+
+
+def probe_fp64_tflops():
+    """Measured FP64 FMA throughput of the current device (TFLOP/s)."""
+    out = ctypes.c_double()
+    _check(load().lb_probe_fp64(ctypes.byref(out)))
+    return out.value
+
+
+def _check(rc):
+    if rc != LB_OK:
+        raise LBError(rc, load().lb_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    """Device (or host) address of a torch tensor / numpy array, or None."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def _f64(t):
+    """float64 view of a complex128 tensor (interleaved re, im)."""
+    import torch
+    if t.dtype == torch.complex128:
+        return torch.view_as_real(t)
+    return t
+
+
+class Basis:
+    """Device index tables of the SU(N) basis (lb_basis_create)."""
+
+    def __init__(self, N, stream=None):
+        lib = load()
+        h = _vp()
+        _check(lib.lb_basis_create(int(N), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        n = ctypes.c_int()
+        M = _c_i64()
+        P = _c_i64()
+        _check(lib.lb_basis_dims(h, ctypes.byref(n), ctypes.byref(M), ctypes.byref(P)))
+        self.N, self.M, self.P = n.value, M.value, P.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().lb_basis_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def label(self, i):
+        t = ctypes.create_string_buffer(2)
+        j = ctypes.c_int()
+        k = ctypes.c_int()
+        _check(load().lb_basis_label(self._h, int(i), t, ctypes.byref(j), ctypes.byref(k)))
+        return t.value.decode(), j.value, k.value
+
+    def structure_count(self, which):
+        n = _c_i64()
+        _check(load().lb_structure_count(self._h, {"f": LB_F, "d": LB_D}[which], ctypes.byref(n)))
+        return n.value
+
+    def structure(self, which, stream=None):
+        """Kernel (a): canonical sorted nonzero (idx int32 (n,3), val float64) on the device."""
+        import torch
+        w = {"f": LB_F, "d": LB_D}[which]
+        n = self.structure_count(which)
+        idx = torch.empty((max(n, 1), 3), dtype=torch.int32, device="cuda")
+        val = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+        got = _c_i64()
+        _check(load().lb_structure_export(self._h, w, _ptr(idx), _ptr(val), n, ctypes.byref(got),
+                                          _stream(stream)))
+        return idx[:n], val[:n]
+
+    def join_terms(self):
+        W = _c_i64()
+        _check(load().lb_join_terms(self._h, ctypes.byref(W)))
+        return W.value
+
+    def expand(self, A, stream=None):
+        """Eq. (02) for an N x N complex128 device tensor -> M complex128 coefficients."""
+        import torch
+        assert A.dtype == torch.complex128 and A.is_contiguous() and A.shape == (self.N, self.N)
+        coef = torch.empty(self.M, dtype=torch.complex128, device=A.device)
+        _check(load().lb_expand(self._h, _ptr(A), _ptr(coef), _stream(stream)))
+        return coef
+
+    def rho(self, v, stream=None):
+        import torch
+        assert v.dtype == torch.float64 and v.is_contiguous() and v.numel() == self.M
+        out = torch.empty((self.N, self.N), dtype=torch.complex128, device=v.device)
+        _check(load().lb_rho(self._h, _ptr(v), _ptr(out), _stream(stream)))
+        return out
+
+    def assemble_dense(self, a, h=None, A=True, Q=False, R=False, K=True, stream=None):
+        """Dense Q, R, K (Eqs. (07)-(09)).  a: M x M complex128 device tensor.
+
+        A, Q, R, K may be True (allocate), False/None (skip) or a preallocated
+        float64 tensor.  Returns dict of the requested outputs."""
+        import torch
+        M = self.M
+        assert a.dtype == torch.complex128 and a.is_contiguous() and a.shape == (M, M)
+        if h is not None:
+            assert h.dtype == torch.float64 and h.is_contiguous() and h.numel() == M
+        out = {}
+        for name, want, shape in (("A", A, (M, M)), ("Q", Q, (M, M)), ("R", R, (M, M)), ("K", K, (M,))):
+            if want is True:
+                out[name] = torch.empty(shape, dtype=torch.float64, device=a.device)
+            elif want is not None and want is not False:
+                out[name] = want
+        _check(load().lb_assemble_dense(self._h, _ptr(h), _ptr(a), _ptr(out.get("A")), _ptr(out.get("Q")),
+                                        _ptr(out.get("R")), _ptr(out.get("K")), _stream(stream)))
+        return out
+
+
+def pack_fp32(A, out=None, stream=None):
+    import torch
+    M = A.shape[0]
+    out = torch.empty((M, M), dtype=torch.float32, device=A.device) if out is None else out
+    _check(load().lb_pack_fp32(M, _ptr(A), _ptr(out), _stream(stream)))
+    return out
+
+
+def pack_bf16(A, out=None, scale=None, stream=None):
+    import torch
+    M = A.shape[0]
+    out = torch.empty((M, M), dtype=torch.int16, device=A.device) if out is None else out
+    scale = torch.empty(M, dtype=torch.float32, device=A.device) if scale is None else scale
+    _check(load().lb_pack_bf16(M, _ptr(A), _ptr(out), _ptr(scale), _stream(stream)))
+    return out, scale
+
+
+def rk4_workspace(M, device="cuda"):
+    import torch
+    n = load().lb_rk4_workspace_bytes(M)
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def rk4_dense(Ap, K, v, dt, nsteps, precision="fp64", scale=None, A64=None, correct_every=0,
+              snap_every=0, work=None, stream=None):
+    """Classical RK4 on device; v (float64, M) is updated in place.  Returns snapshots or None."""
+    import torch
+    M = v.numel()
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    work = rk4_workspace(M, v.device) if work is None else work
+    snaps = None
+    if snap_every:
+        snaps = torch.empty((nsteps // snap_every, M), dtype=torch.float64, device=v.device)
+    _check(load().lb_rk4_dense(M, p, _ptr(Ap), _ptr(scale), _ptr(A64), int(correct_every), _ptr(K), _ptr(v),
+                               float(dt), int(nsteps), _ptr(snaps), int(snap_every), _ptr(work),
+                               _stream(stream)))
+    return snaps
+
+
+class System:
+    """Host-buffer interface: lb_assemble / lb_system_get / lb_integrate."""
+
+    def __init__(self, basis, a, H=None, keep_parts=False):
+        lib = load()
+        a = np.ascontiguousarray(a, np.complex128)
+        assert a.shape == (basis.M, basis.M)
+        Hc = None if H is None else np.ascontiguousarray(H, np.complex128)
+        h = _vp()
+        _check(lib.lb_assemble(basis.handle, _ptr(Hc), _ptr(a), int(bool(keep_parts)), ctypes.byref(h)))
+        self._h = h
+        self.basis = basis
+        self.M = basis.M
+
+    def close(self):
+        if self._h:
+            load().lb_system_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get(self, part):
+        p = {"A": LB_SYS_A, "Q": LB_SYS_Q, "R": LB_SYS_R, "K": LB_SYS_K}[part]
+        out = np.zeros(self.M if part == "K" else (self.M, self.M))
+        _check(load().lb_system_get(self._h, p, _ptr(out)))
+        return out
+
+    def integrate(self, v0, t, dt, precision="fp64", correct_every=0, out=None):
+        v0 = np.ascontiguousarray(v0, np.float64)
+        out = np.zeros(self.M) if out is None else out
+        _check(load().lb_integrate(self._h, PRECISIONS[precision], int(correct_every), _ptr(v0), float(t),
+                                   float(dt), _ptr(out)))
+        return out

@@ -1,0 +1,235 @@
+"""GPU-versus-oracle parity through the C ABI (needs an sm_103a GPU).
+
+Bars: index lists bit-exact; values within the per-entry tolerance
+|x_gpu - x_ora| <= 1e-12 max(|x_ora|, S) with S = 1/4 sum |terms| the
+oracle's absolute-sum scale of the entry (summation order is free, so an
+entry with heavy cancellation is judged against its condition); FP64
+trajectories within 1e-12 ||v|| of the oracle's RK4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import Oracle, rk4_dense as ora_rk4
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_01491_gb300 import build
+    build.build()
+
+
+def lbm():
+    import paper_1912_01491_gb300 as lbm
+    return lbm
+
+
+def _canonical_d_count(N):
+    pd = sum(N - max(a, 1) for a in range(N) for b in range(a + 1, N))
+    return 4 * math.comb(N, 3) + 2 * pd - (2 if N >= 2 else 0) + (N - 1) * (N - 2) // 2 + (N - 2)
+
+
+@pytest.mark.parametrize("N", list(range(2, 13)) + [16, 21, 32])
+def test_structure_lists_bit_exact(N):
+    with lbm().Basis(N) as B, Oracle(N) as o:
+        for w in "fd":
+            idx, val = B.structure(w)
+            oi, ov = o.structure(w)
+            assert idx.shape[0] == oi.shape[0]
+            assert np.array_equal(idx.cpu().numpy(), oi)
+            if len(ov):
+                assert np.abs(val.cpu().numpy() - ov).max() < 1e-14
+
+
+@pytest.mark.parametrize("N", [50, 200, 1000, 2000])
+def test_structure_counts_large_n(N):
+    with lbm().Basis(N) as B:
+        assert 6 * B.structure_count("f") == 5 * N**3 - 9 * N**2 - 2 * N + 6
+        assert B.structure_count("d") == _canonical_d_count(N)
+
+
+def test_labels():
+    with lbm().Basis(5) as B, Oracle(5) as o:
+        for i in range(B.M):
+            assert B.label(i) == o.label(i)
+
+
+@pytest.mark.parametrize("N", [3, 7, 17])
+def test_expand_and_rho(N):
+    g = np.random.default_rng(N)
+    A = g.standard_normal((N, N)) + 1j * g.standard_normal((N, N))
+    v = g.standard_normal(N * N - 1)
+    with lbm().Basis(N) as B, Oracle(N) as o:
+        coef = B.expand(torch.tensor(A, device="cuda")).cpu().numpy()
+        ref, _ = o.expand(A)
+        assert np.abs(coef - ref).max() < 1e-13
+        rho = B.rho(torch.tensor(v, device="cuda")).cpu().numpy()
+        assert np.abs(rho - o.rho(v)).max() < 1e-13
+
+
+def _case(N, seed):
+    return wl.gue_hamiltonian(N, seed), wl.wishart_kossakowski(N, seed + 1)
+
+
+def _assert_entries(x, ref, scale, what):
+    err = np.abs(x - ref)
+    tol = 1e-12 * np.maximum(np.abs(ref), scale) + 1e-300
+    bad = np.argwhere(err > tol)
+    assert len(bad) == 0, "%s: %d entries out of tolerance, first %s (err %g, tol %g)" % (
+        what, len(bad), bad[:3].tolist(), err[tuple(bad[0])], tol[tuple(bad[0])])
+
+
+def _gpu_system(B, H, a):
+    h = B.expand(torch.tensor(H, device="cuda")).real.contiguous()
+    out = B.assemble_dense(torch.tensor(a, device="cuda"), h=h, A=True, Q=True, R=True, K=True)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+@pytest.mark.parametrize("N", list(range(2, 13)) + [16, 23])
+def test_dense_assembly_parity(N):
+    H, a = _case(N, 1000 + N)
+    with lbm().Basis(N) as B, Oracle(N) as o:
+        g = _gpu_system(B, H, a)
+        h, _ = o.expand(H)
+        Q = o.Q(h.real)
+        R, S = o.R(a, return_scale=True)
+        K = o.K(a)
+        W = o.join_terms()
+        assert B.join_terms() == W
+    _assert_entries(g["R"], R, S, "R")
+    qs = np.abs(Q).max()
+    assert np.abs(g["Q"] - Q).max() <= 1e-12 * qs
+    _assert_entries(g["A"], Q + R, S + np.abs(Q), "A")
+    assert np.abs(g["K"] - K).max() <= 1e-12 * max(np.abs(K).max(), 1e-300) + 1e-17
+
+
+def test_dense_assembly_n50_random_lindbladian():
+    """The 50-level random Lindbladian (M = 2499): full R, Q, K parity."""
+    N = 50
+    H, a = _case(N, 1050)
+    with lbm().Basis(N) as B, Oracle(N) as o:
+        g = _gpu_system(B, H, a)
+        h, _ = o.expand(H)
+        Q = o.Q(h.real)
+        R, S = o.R(a, return_scale=True)
+        K = o.K(a)
+        assert B.join_terms() == o.join_terms()
+    _assert_entries(g["R"], R, S, "R")
+    assert np.abs(g["Q"] - Q).max() <= 1e-12 * np.abs(Q).max()
+    assert np.abs(g["K"] - K).max() <= 1e-12 * np.abs(K).max()
+
+
+def test_identity_and_amplitude_damping_closed_forms():
+    g = 0.3
+    for N in (2, 4):
+        M = N * N - 1
+        with lbm().Basis(N) as B:
+            out = B.assemble_dense(torch.eye(M, dtype=torch.complex128, device="cuda") * g, R=True)
+            assert torch.allclose(out["R"], -g * N * torch.eye(M, dtype=torch.float64, device="cuda"), atol=1e-14)
+            assert out["K"].abs().max().item() < 1e-15
+    with lbm().Basis(2) as B:
+        L = torch.tensor([[0, 1], [0, 0]], dtype=torch.complex128, device="cuda")
+        l = B.expand(L)
+        a = g * torch.outer(l, l.conj())
+        out = B.assemble_dense(a.contiguous(), R=True)
+        ref = torch.tensor(np.diag([-g / 2, -g / 2, -g]), device="cuda")
+        assert torch.allclose(out["R"], ref, atol=1e-15)
+        assert torch.allclose(out["K"], torch.tensor([0, 0, g / math.sqrt(2)], device="cuda",
+                                                     dtype=torch.float64), atol=1e-15)
+
+
+def _oracle_system(o, H, a):
+    h, _ = o.expand(H)
+    return o.Q(h.real) + o.R(a), o.K(a)
+
+
+def test_rk4_fp64_n10_full_trajectory():
+    """Dense N = 10 random Lindbladian, rho0 = |0><0|, t = 10, dt = 1e-3 (10^4 steps)."""
+    N, dt, steps, every = 10, 1e-3, 10_000, 1000
+    H, a = _case(N, 1010)
+    lb = lbm()
+    with lb.Basis(N) as B, Oracle(N) as o:
+        A, K = _oracle_system(o, H, a)
+        v0 = o.expand(wl.pure_state(N, 0))[0].real
+        ref_v, ref_snaps = ora_rk4(A, K, v0, dt, steps, snap_every=every)
+        g = B.assemble_dense(torch.tensor(a, device="cuda"),
+                             h=B.expand(torch.tensor(H, device="cuda")).real.contiguous())
+        v = torch.tensor(v0, device="cuda")
+        snaps = lb.rk4_dense(g["A"], g["K"], v, dt, steps, precision="fp64", snap_every=every)
+        torch.cuda.synchronize()
+    snaps = snaps.cpu().numpy()
+    for t in range(len(ref_snaps)):
+        assert np.linalg.norm(snaps[t] - ref_snaps[t]) <= 1e-12 * np.linalg.norm(ref_snaps[t])
+    assert np.linalg.norm(v.cpu().numpy() - ref_v) <= 1e-12 * np.linalg.norm(ref_v)
+
+
+@pytest.mark.parametrize("precision,tol_plain,tol_corr", [("fp32", 1e-5, 2e-6), ("bf16", 2e-2, 1e-3)])
+def test_rk4_low_precision_with_correction(precision, tol_plain, tol_corr):
+    """FP32 / BF16-with-row-scale storage: stated trajectory error against the
+    FP64 oracle, and the FP64 defect correction every 50 steps reduces it."""
+    N, dt, steps = 12, 1e-3, 2000
+    H, a = _case(N, 1212)
+    lb = lbm()
+    with lb.Basis(N) as B, Oracle(N) as o:
+        A, K = _oracle_system(o, H, a)
+        v0 = o.expand(wl.pure_state(N, 0))[0].real
+        ref_v, _ = ora_rk4(A, K, v0, dt, steps)
+        g = B.assemble_dense(torch.tensor(a, device="cuda"),
+                             h=B.expand(torch.tensor(H, device="cuda")).real.contiguous())
+        if precision == "fp32":
+            Ap, sc = lb.pack_fp32(g["A"]), None
+        else:
+            Ap, sc = lb.pack_bf16(g["A"])
+        errs = []
+        for corr in (0, 50):
+            v = torch.tensor(v0, device="cuda")
+            lb.rk4_dense(Ap, g["K"], v, dt, steps, precision=precision, scale=sc, A64=g["A"],
+                         correct_every=corr)
+            torch.cuda.synchronize()
+            errs.append(np.linalg.norm(v.cpu().numpy() - ref_v) / np.linalg.norm(ref_v))
+    assert errs[0] < tol_plain, errs
+    assert errs[1] < tol_corr, errs
+    assert errs[1] < 0.5 * errs[0], errs
+
+
+def test_host_buffer_api():
+    N = 6
+    H, a = _case(N, 606)
+    lb = lbm()
+    with lb.Basis(N) as B, Oracle(N) as o:
+        sysm = lb.System(B, a, H=H, keep_parts=True)
+        A, K = _oracle_system(o, H, a)
+        R, S = o.R(a, return_scale=True)
+        _assert_entries(sysm.get("R"), R, S, "R")
+        assert np.abs(sysm.get("A") - A).max() < 1e-12 * np.abs(A).max()
+        v0 = o.expand(wl.pure_state(N, 1))[0].real
+        ref, _ = ora_rk4(A, K, v0, 1e-3, 500)
+        v = sysm.integrate(v0, 0.5, 1e-3)
+        assert np.linalg.norm(v - ref) <= 1e-12 * np.linalg.norm(ref)
+        with pytest.raises(lb.LBError) as e:
+            sysm.integrate(v0, 0.5, 0.3)
+        assert e.value.code == lb.native.LB_EINVAL
+        sysm.close()
+
+
+def test_empty_and_degenerate_inputs():
+    lb = lbm()
+    # a = 0, H = 0: everything vanishes
+    with lb.Basis(3) as B:
+        out = B.assemble_dense(torch.zeros((8, 8), dtype=torch.complex128, device="cuda"), A=True, K=True)
+        assert out["A"].abs().max().item() == 0 and out["K"].abs().max().item() == 0
+        # zero steps leave v untouched
+        v = torch.arange(8, dtype=torch.float64, device="cuda")
+        lb.rk4_dense(out["A"], out["K"], v, 1e-3, 0)
+        assert torch.equal(v, torch.arange(8, dtype=torch.float64, device="cuda"))
+    with pytest.raises(lb.LBError):
+        lb.Basis(1)

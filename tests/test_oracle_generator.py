@@ -217,3 +217,20 @@ def test_ladder_death_process():
     e = math.exp(-g * T)
     ref = np.array([math.comb(n0, n) * e**n * (1 - e) ** (n0 - n) for n in range(N)])
     assert np.abs(p - ref).max() < 1e-11
+
+
+def test_entries_from_rows_match_full():
+    N = 8
+    H, a = _random_case(N, 808)
+    with Oracle(N) as o:
+        R, S = o.R(a, return_scale=True)
+        g = np.random.default_rng(2)
+        s = np.repeat([0, 5, o.P + 3, o.M - 1], 20)
+        n = g.integers(0, o.M, len(s))
+        rows = o.rows_needed(s)
+        assert len(rows) < o.M
+        out, sc = o.R_entries_rows(rows, a[rows], s, n)
+        with pytest.raises(ValueError):
+            o.R_entries_rows(rows[1:], a[rows[1:]], s, n)
+    assert np.abs(out - R[s, n]).max() < 1e-15
+    assert np.abs(sc - S[s, n]).max() < 1e-14
