@@ -137,10 +137,24 @@ int lb_rho(const lb_basis_t *b, const double *v, double *rho, void *stream);
  *   K : M doubles (Eq. (08))
  * Each R entry is the sum of its join terms over the shared index l
  * (Eq. (09) in the one-term form r_sn = -1/2 Re sum_jkl a_jk z_jln f_kls,
- * identical to the printed two-term form with prefactor -1/4 for Hermitian a),
- * accumulated in FP64 by the thread that owns the entry. */
+ * identical to the printed two-term form with prefactor -1/4 for Hermitian a;
+ * Sec. 4 item 2.5), accumulated in FP64 by the thread or warp that owns the
+ * entry (no atomics).  N <= 512 (LB_EINVAL otherwise).  Same as
+ * lb_assemble_dense_ex with algorithm = LB_ALG_JOIN. */
 int lb_assemble_dense(const lb_basis_t *b, const double *h, const double *a,
                       double *A, double *Q, double *R, double *K, void *stream);
+
+/* algorithms of the dense R assembly */
+#define LB_ALG_JOIN 0   /* every join term visited, as in Sec. 4 item 2.5 (O(N^5)) */
+#define LB_ALG_CLOSED 1 /* the runs of D-section terms whose coefficients are all
+                           c_l^2 = 1/(l(l+1)) summed in closed form,
+                           sum_{l=x}^{y} c_l^2 = 1/x - 1/(y+1) (O(N^4)); same R
+                           up to rounding */
+
+/* lb_assemble_dense with a choice of algorithm (LB_ALG_JOIN or LB_ALG_CLOSED). */
+int lb_assemble_dense_ex(const lb_basis_t *b, const double *h, const double *a,
+                         double *A, double *Q, double *R, double *K, int algorithm,
+                         void *stream);
 
 /* ------------------------------------------------------------------------
  * a6-a8 -- RK4 integration (Table 1 step 3.1; Sec. 4 item 3), with the
@@ -179,11 +193,13 @@ int lb_rk4_dense(int64_t M, int precision, const void *Ap, const float *row_scal
  * --------------------------------------------------------------------- */
 
 /* Expand H (host N x N complex, may be NULL) and assemble Q, R, K from the
- * host Kossakowski matrix a (M x M complex).  keep_parts != 0 also keeps Q
- * and R separately.  The device copy of a is freed before returning.
- * LB_ENOMEM if the device cannot hold a, A (and Q, R). Synchronous. */
+ * host Kossakowski matrix a (M x M complex) with the given algorithm
+ * (LB_ALG_JOIN or LB_ALG_CLOSED).  keep_parts != 0 also keeps Q and R
+ * separately.  The device copy of a is freed before returning.  LB_ENOMEM if
+ * the device cannot hold a, A (and Q, R): checked against cudaMemGetInfo
+ * before any allocation.  Synchronous. */
 int lb_assemble(const lb_basis_t *b, const double *H, const double *a, int keep_parts,
-                lb_system_t **out);
+                int algorithm, lb_system_t **out);
 int lb_system_destroy(lb_system_t *sys);
 
 /* Copy one part (LB_SYS_A, _Q, _R: M x M; LB_SYS_K: M) into host memory.

@@ -111,21 +111,18 @@ int lb_basis_create(int N, void* stream, lb_basis_t** out) {
   LB_REQUIRE(N >= 2 && N <= 4096, "lb_basis_create: N = %d outside [2, 4096]", N);
   *out = nullptr;
   const int64_t P = (int64_t)N * (N - 1) / 2;
-  DevBuf pab, c, lc;
+  DevBuf pab, tab;
   int rc;
   if ((rc = alloc_or_enomem(pab, sizeof(int32_t) * P, "pair table")) != LB_OK) return rc;
-  if ((rc = alloc_or_enomem(c, sizeof(double) * N, "basis constants")) != LB_OK) return rc;
-  if ((rc = alloc_or_enomem(lc, sizeof(double) * N, "basis constants")) != LB_OK) return rc;
-  LB_TRY_CUDA(lbi::build_tables(N, pab.as<int32_t>(), c.as<double>(), lc.as<double>(), S(stream)),
-              "basis tables");
+  if ((rc = alloc_or_enomem(tab, sizeof(double) * (4 * (size_t)N + 1), "basis constants")) != LB_OK) return rc;
+  LB_TRY_CUDA(lbi::build_tables(N, pab.as<int32_t>(), tab.as<double>(), S(stream)), "basis tables");
   LB_TRY_CUDA(cudaStreamSynchronize(S(stream)), "basis tables");
   lb_basis* b = new lb_basis;
   b->N = N;
   b->P = P;
   b->M = (int64_t)N * N - 1;
   b->d_pair_ab = static_cast<int32_t*>(pab.release());
-  b->d_c = static_cast<double*>(c.release());
-  b->d_lc = static_cast<double*>(lc.release());
+  b->d_tab = static_cast<double*>(tab.release());
   *out = b;
   return LB_OK;
 }
@@ -133,8 +130,7 @@ int lb_basis_create(int N, void* stream, lb_basis_t** out) {
 int lb_basis_destroy(lb_basis_t* b) {
   if (!b) return LB_OK;
   cudaFree(b->d_pair_ab);
-  cudaFree(b->d_c);
-  cudaFree(b->d_lc);
+  cudaFree(b->d_tab);
   delete b;
   return LB_OK;
 }
@@ -259,14 +255,22 @@ int lb_rho(const lb_basis_t* b, const double* v, double* rho, void* stream) {
   return LB_OK;
 }
 
-int lb_assemble_dense(const lb_basis_t* b, const double* h, const double* a, double* A, double* Q,
-                      double* R, double* K, void* stream) {
+int lb_assemble_dense_ex(const lb_basis_t* b, const double* h, const double* a, double* A, double* Q,
+                         double* R, double* K, int algorithm, void* stream) {
   LB_REQUIRE(b != nullptr && a != nullptr, "lb_assemble_dense: NULL basis or a");
   LB_REQUIRE(A || Q || R || K, "lb_assemble_dense: no output requested");
-  LB_REQUIRE(b->M <= 0x7fffffffLL, "lb_assemble_dense: M too large");
-  LB_TRY_CUDA(lbi::assemble_dense(b->view(), h, reinterpret_cast<const double2*>(a), A, Q, R, K, S(stream)),
+  LB_REQUIRE(b->N <= lbi::kMaxDenseN, "lb_assemble_dense: N = %d above %d", b->N, lbi::kMaxDenseN);
+  LB_REQUIRE(algorithm == LB_ALG_JOIN || algorithm == LB_ALG_CLOSED, "lb_assemble_dense: algorithm = %d",
+             algorithm);
+  LB_TRY_CUDA(lbi::assemble_dense(b->view(), h, reinterpret_cast<const double2*>(a), A, Q, R, K, algorithm,
+                                  S(stream)),
               "lb_assemble_dense");
   return LB_OK;
+}
+
+int lb_assemble_dense(const lb_basis_t* b, const double* h, const double* a, double* A, double* Q,
+                      double* R, double* K, void* stream) {
+  return lb_assemble_dense_ex(b, h, a, A, Q, R, K, LB_ALG_JOIN, stream);
 }
 
 int lb_pack_fp32(int64_t M, const double* A, float* A32, void* stream) {
@@ -301,8 +305,11 @@ int lb_rk4_dense(int64_t M, int precision, const void* Ap, const float* row_scal
 
 // ------------------------------------------------------------------ host API
 
-int lb_assemble(const lb_basis_t* b, const double* H, const double* a, int keep_parts, lb_system_t** out) {
+int lb_assemble(const lb_basis_t* b, const double* H, const double* a, int keep_parts, int algorithm,
+                lb_system_t** out) {
   LB_REQUIRE(b && a && out, "lb_assemble: NULL argument");
+  LB_REQUIRE(b->N <= lbi::kMaxDenseN, "lb_assemble: N = %d above %d", b->N, lbi::kMaxDenseN);
+  LB_REQUIRE(algorithm == LB_ALG_JOIN || algorithm == LB_ALG_CLOSED, "lb_assemble: algorithm = %d", algorithm);
   *out = nullptr;
   const int64_t M = b->M, N = b->N;
   const size_t mm = (size_t)M * (size_t)M;
@@ -335,7 +342,7 @@ int lb_assemble(const lb_basis_t* b, const double* H, const double* a, int keep_
                 "real part of h");
   }
   LB_TRY_CUDA(lbi::assemble_dense(b->view(), H ? dh.as<double>() : nullptr, da.as<double2>(), dA.as<double>(),
-                                  dQ.as<double>(), dR.as<double>(), dK.as<double>(), nullptr),
+                                  dQ.as<double>(), dR.as<double>(), dK.as<double>(), algorithm, nullptr),
               "assemble");
   LB_TRY_CUDA(cudaDeviceSynchronize(), "assemble");
   lb_system* s = new lb_system;

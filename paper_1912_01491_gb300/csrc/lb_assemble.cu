@@ -412,20 +412,906 @@ __global__ void k_kvec(BasisView B, AView A, double* __restrict__ K) {
   if (lane == 0) K[s] = -acc / (double)N;
 }
 
+// ---------------------------------------------------------------------------
+// Production path.  The same join terms as entry<>, split by the relation of
+// the edges of s and n so that no warp carries another case's O(N) loops:
+//   k_entries : every entry -- the l = D_lambda part of pair-pair entries,
+//               the l-pair part of pair-pair entries on disjoint edges (16
+//               terms), entries with a diagonal s or n (via entry<>), and Q;
+//   k_shared  : the l-pair part of pair-pair entries whose edges share one
+//               vertex; one block per ordered vertex pair (p, q), entries
+//               s on (v, p), n on (v, q) for all v, with the entries of a
+//               common to every v staged in shared memory;
+//   k_same    : the l-pair part of pair-pair entries on the same edge; one
+//               block per edge.
+// A triangle value is +-1/sqrt2, so a triangle-triangle term is +-1/2 Re(a)
+// or +-1/2 Im(a): its sign comes from integer phase arithmetic and the term
+// costs one FP64 add.
+
+// +-1 of a triangle constant: f = Im(i^ph)/sqrt2 (odd ph), d = Re(i^ph)/sqrt2 (even ph)
+LB_HD int sgn_f(int ph) { return ((ph & 3) == 1) ? 1 : -1; }
+LB_HD int sgn_d(int ph) { return ((ph & 3) == 0) ? 1 : -1; }
+
+// s * x for s = +-1, by flipping the sign bit (no FP64 instruction)
+__device__ __forceinline__ double sgn_mul(int s, double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((unsigned long long)(s < 0) << 63));
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// delta_x(lam) = (D_lam)_xx
+__device__ __forceinline__ double dlt(const BasisView& B, int x, int lam) {
+  return x < lam ? ld_c(B, lam) : (x == lam ? ld_lc(B, lam) : 0.0);
+}
+
+// sum_{lam=x}^{y} c_lam^2: term by term (the join) or as 1/x - 1/(y+1)
+template <int ALG>
+__device__ __forceinline__ double seg_c2(const BasisView& B, int x, int y) {
+  if (x > y) return 0.0;
+  if (ALG == LB_ALG_CLOSED) return __ldg(B.inv + x) - __ldg(B.inv + y + 1);
+  double s = 0.0;
+  for (int l = x; l <= y; ++l) s += __ldg(B.c2 + l);
+  return s;
+}
+
+// Pair s = (as, bs), pair n = (an, bn): the l = D_lambda part,
+//   sum_lam f(partner(s), D, s) [Re a_{partner(n), partner(s)} f(partner(n), D, n)
+//                                 - Im a_{n, partner(s)} d(n, D, n)].
+// Inside (lo, hi) away from the four edge end points every factor is c_lam
+// (or 0, 2 c_lam past b_n), so the sum runs over c_lam^2 between the sorted
+// end points, which are evaluated from the delta's in full.
+template <int ALG>
+__device__ __forceinline__ double part_d_pp(const BasisView& B, const AView& A, int as, int bs, int ts,
+                                            int an, int bn, int tn, int64_t sb, int64_t n, int64_t nb) {
+  const int lo = imax(imax(as, an), 1), hi = bs;
+  if (lo > hi) return 0.0;
+  int sp0 = as, sp1 = an, sp2 = bn, sp3 = bs, t;
+  if (sp0 > sp1) { t = sp0; sp0 = sp1; sp1 = t; }
+  if (sp2 > sp3) { t = sp2; sp2 = sp3; sp3 = t; }
+  if (sp0 > sp2) { t = sp0; sp0 = sp2; sp2 = t; }
+  if (sp1 > sp3) { t = sp1; sp1 = sp3; sp3 = t; }
+  if (sp1 > sp2) { t = sp1; sp1 = sp2; sp2 = t; }
+  const int sp[4] = {sp0, sp1, sp2, sp3};
+  double accf = 0.0, accd = 0.0;
+  int prev = lo;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int x = sp[i];
+    if (x < prev || x > hi) continue;
+    if (prev <= x - 1) {
+      const double S = seg_c2<ALG>(B, prev, x - 1);
+      if (x - 1 < bn) { accf += S; accd += S; } else { accd += 2.0 * S; }
+    }
+    const double das = dlt(B, as, x), dbs = dlt(B, bs, x), dan = dlt(B, an, x), dbn = dlt(B, bn, x);
+    const double gs = das - dbs;
+    accf = fma(gs, dan - dbn, accf);
+    accd = fma(gs, dan + dbn, accd);
+    prev = x + 1;
+  }
+  if (prev <= hi) {
+    const double S = seg_c2<ALG>(B, prev, hi);
+    if (hi < bn) { accf += S; accd += S; } else { accd += 2.0 * S; }
+  }
+  const double2 a1 = ldA_row(A, nb, sb);  // a_{partner(n), partner(s)}
+  const double2 a2 = ldA_row(A, n, sb);   // a_{n, partner(s)}
+  const double sgs = ts == kS ? 1.0 : -1.0, sgn = tn == kS ? 1.0 : -1.0;
+  return sgs * (sgn * a1.x * accf - a2.y * accd);
+}
+
+// Pair s, pair n on disjoint edges: e(l) = (v, w), v in e(s), w in e(n);
+// k on (v', w), j on (v, w') with both types.  Lanes of a warp run over
+// consecutive n, so a_jk is read from the row (j or k) that is common to
+// the warp.
+__device__ __forceinline__ double part_p_disjoint(const BasisView& B, const AView& A, int as, int bs, int ts,
+                                                  int an, int bn, int tn) {
+  const int N = B.N;
+  const int64_t P = B.P;
+  double acc2 = 0.0;
+#pragma unroll
+  for (int vi = 0; vi < 2; ++vi) {
+    const int v = vi ? bs : as, vp = vi ? as : bs;
+    const int phs = coef_phase(ts, v, vp);
+#pragma unroll
+    for (int wi = 0; wi < 2; ++wi) {
+      const int w = wi ? bn : an, wp = wi ? an : bn;
+      const int phn = coef_phase(tn, w, wp);
+      const int64_t pk = pair_index_any(N, vp, w), pj = pair_index_any(N, v, wp);
+#pragma unroll
+      for (int tl = 0; tl < 2; ++tl) {
+        const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+        const int phl_wv = coef_phase(tl, w, v), phl_vw = coef_phase(tl, v, w);
+        const int sk = sgn_f(phs + coef_phase(tk, vp, w) + phl_wv);
+        const int sf = sgn_f(phn + coef_phase(tjf, wp, v) + phl_vw);
+        const int sd = sgn_d(phn + coef_phase(tjd, wp, v) + phl_vw);
+        const int64_t k = tk * P + pk, jf = tjf * P + pj, jd = tjd * P + pj;
+        double2 a1, a2;
+        if (wi == 0) {
+          a1 = ldA_row(A, jf, k);
+          a2 = ldA_row(A, jd, k);
+        } else {
+          a1 = ldA(A, jf, k);
+          a2 = ldA(A, jd, k);
+        }
+        acc2 += sgn_mul(sk * sf, a1.x);
+        acc2 -= sgn_mul(sk * sd, a2.y);
+      }
+    }
+  }
+  return 0.5 * acc2;
+}
+
+// Pair-pair block (s, n < 2P); one thread per entry, 256 consecutive n per block.
+template <int ALG>
+__global__ void __launch_bounds__(256) k_entries(BasisView B, AView A, const double* __restrict__ h,
+                                                 double* __restrict__ Aout, double* __restrict__ Qout,
+                                                 double* __restrict__ Rout) {
+  const int64_t M = B.M, P2 = 2 * B.P;
+  const int64_t chunks = (P2 + 255) / 256;
+  const int64_t s = blockIdx.x / chunks;
+  const int64_t n = (blockIdx.x % chunks) * 256 + threadIdx.x;
+  if (n >= P2) return;
+  const Elem es = decode(B, s), en = decode(B, n);
+  double q = 0.0;
+  const int as = es.a, bs = es.b, ts = es.kind, an = en.a, bn = en.b, tn = en.kind;
+  double acc = part_d_pp<ALG>(B, A, as, bs, ts, an, bn, tn, partner(B, s), n, partner(B, n));
+  int shared = 0, cv = -1;
+  if (as == an || as == bn) { ++shared; cv = as; }
+  if (bs == an || bs == bn) { ++shared; cv = bs; }
+  if (shared == 0) acc += part_p_disjoint(B, A, as, bs, ts, an, bn, tn);
+  if (h != nullptr) {
+    if (shared == 1) {
+      const int p = (as == cv) ? bs : as, qv = (an == cv) ? bn : an;
+      const Elem em = make_pair(1 ^ tn ^ ts, p, qv);
+      q = __ldg(h + elem_index(B, em.kind, em.a, em.b)) * f_value(B, em, en, es);
+    } else if (shared == 2 && tn != ts) {
+      for (int lam = imax(as, 1); lam <= bs; ++lam)
+        q += __ldg(h + d_index(B, lam)) * f_value(B, make_d(lam), en, es);
+    }
+  }
+  const double r = -0.5 * acc;
+  const int64_t o = s * M + n;
+  if (Rout) Rout[o] = r;
+  if (Qout) Qout[o] = q;
+  if (Aout) Aout[o] = q + r;
+}
+
+// Pair row s = (as, bs) type ts, diagonal columns n = D_nu.  One block per
+// row; the a entries every nu of the row needs are staged in shared memory:
+//   Y[x] = a[partner(s)][D_x],  Z[x] = a[s][D_x],
+//   W[(vi, w, tl)] = (a(l, k), a(partner(l), k)),  l = (v, w) tl, k = (v', w) (1^tl^ts).
+// With g_s = delta_as - delta_bs, h_s = delta_as + delta_bs:
+//   l = D_lam (lam in [lo_s, bs]), k = partner(s), f = sgs g_s(lam); j = D_min(lam,nu)
+//     with d = 2 c_max(lam,nu), or for lam = nu every D_mu, mu >= nu;
+//   l = (v, w) sharing one vertex with e(s): k on (v', w) (triangle), j = l
+//     (d = h_l(nu)) and j = partner(l) (f = -+ g_l(nu));
+//   l = partner(s): k = D_mu, f = -sgs g_s(mu); j = partner(s) (d = h_s(nu)),
+//     j = s (f = sgs g_s(nu)).
+constexpr int kRowThreads = 128;
+
+__global__ void __launch_bounds__(kRowThreads) k_pd(BasisView B, AView A, const double* __restrict__ h,
+                                                    double* __restrict__ Aout, double* __restrict__ Qout,
+                                                    double* __restrict__ Rout) {
+  extern __shared__ double2 sp[];
+  const int N = B.N;
+  const int64_t P = B.P, M = B.M;
+  const int64_t s = blockIdx.x;
+  const Elem es = decode(B, s);
+  const int as = es.a, bs = es.b, ts = es.kind;
+  const int64_t sb = partner(B, s);
+  const int lo_s = imax(as, 1);
+  const double sgs = ts == kS ? 1.0 : -1.0;
+  double2* Y = sp;          // [N]
+  double2* Z = sp + N;      // [N]
+  double2* Wt = sp + 2 * N; // [2][N][2] pairs of values -> 8N double2
+  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+    Y[x] = x >= 1 ? ldA(A, sb, d_index(B, x)) : make_double2(0.0, 0.0);
+    Z[x] = x >= 1 ? ldA(A, s, d_index(B, x)) : make_double2(0.0, 0.0);
+  }
+  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
+    const int vi = t / (2 * N), w = (t / 2) % N, tl = t & 1;
+    double2 v0 = make_double2(0.0, 0.0), v1 = v0;
+    if (w != as && w != bs) {
+      const int v = vi ? bs : as, vp = vi ? as : bs;
+      const int64_t pl = pair_index_any(N, v, w), pk = pair_index_any(N, vp, w);
+      const int64_t k = (int64_t)(1 ^ tl ^ ts) * P + pk;
+      v0 = ldA(A, (int64_t)tl * P + pl, k);
+      v1 = ldA(A, (int64_t)(1 - tl) * P + pl, k);
+    }
+    Wt[2 * t] = v0;
+    Wt[2 * t + 1] = v1;
+  }
+  __syncthreads();
+  for (int nu = 1 + threadIdx.x; nu < N; nu += blockDim.x) {
+    // l = D_lam
+    double accD = 0.0;
+    for (int lam = lo_s; lam <= bs; ++lam) {
+      const double gs = dlt(B, as, lam) - dlt(B, bs, lam);
+      if (lam != nu) {
+        const int jm = imin(lam, nu), mx = imax(lam, nu);
+        accD = fma(gs, Y[jm].y * 2.0 * ld_c(B, mx), accD);  // -Im a(D_j, partner(s)) = Im Y
+      } else {
+        double t2 = 0.0;
+        for (int mu = nu; mu < N; ++mu) {
+          if (mu == 1 && nu == 1) continue;
+          const double d = mu > nu ? 2.0 * ld_c(B, mu) : 2.0 * (double)(1 - nu) * ld_c(B, nu);
+          t2 = fma(Y[mu].y, d, t2);
+        }
+        accD = fma(gs, t2, accD);
+      }
+    }
+    double acc = sgs * accD;
+    // l = (v, w) on an edge sharing one vertex with e(s)
+    double accA = 0.0;
+    for (int vi = 0; vi < 2; ++vi) {
+      const int v = vi ? bs : as, vp = vi ? as : bs;
+      const int phs = coef_phase(ts, v, vp);
+      for (int w = 0; w < N; ++w) {
+        if (w == as || w == bs) continue;
+        const int x = imin(v, w), y = imax(v, w);
+        if (nu < imax(x, 1)) continue;  // both the d- and the f-fiber vanish
+        const double dx = dlt(B, x, nu), dy = dlt(B, y, nu);
+        const double hl = (x == 0 && y == 1 && nu == 1) ? 0.0 : dx + dy, gl = dx - dy;
+#pragma unroll
+        for (int tl = 0; tl < 2; ++tl) {
+          const int tk = 1 ^ tl ^ ts;
+          const int sk = sgn_f(phs + coef_phase(tk, vp, w) + coef_phase(tl, w, v));
+          const double2 al = Wt[2 * ((vi * N + w) * 2 + tl)], alb = Wt[2 * ((vi * N + w) * 2 + tl) + 1];
+          const double fl = tl == kS ? -gl : gl;  // f(partner(l), l, D_nu)
+          accA += sgn_mul(sk, alb.x * fl - al.y * hl);
+        }
+      }
+    }
+    acc += accA * kInvSqrt2;
+    // l = partner(s), k = D_mu
+    {
+      const double gnu = (nu >= lo_s && nu <= bs) ? dlt(B, as, nu) - dlt(B, bs, nu) : 0.0;
+      const double hnu = (nu >= lo_s && !(as == 0 && bs == 1 && nu == 1)) ? dlt(B, as, nu) + dlt(B, bs, nu) : 0.0;
+      double c1 = 0.0, c2 = 0.0;
+      for (int mu = lo_s; mu <= bs; ++mu) {
+        const double g = dlt(B, as, mu) - dlt(B, bs, mu);
+        c1 = fma(g, Z[mu].x, c1);
+        c2 = fma(g, Y[mu].y, c2);
+      }
+      acc += -gnu * c1 + sgs * hnu * c2;
+    }
+    double q = 0.0;
+    if (h != nullptr && nu >= lo_s && nu <= bs) q = __ldg(h + sb) * sgs * (dlt(B, as, nu) - dlt(B, bs, nu));
+    const double r = -0.5 * acc;
+    const int64_t o = s * M + d_index(B, nu);
+    if (Rout) Rout[o] = r;
+    if (Qout) Qout[o] = q;
+    if (Aout) Aout[o] = q + r;
+  }
+}
+
+// Diagonal row s = D_nu, pair columns n = (an, bn) type tn; one thread per entry.
+//   l = (v, w) sharing one vertex with e(n), nu in [max(x,1), y] for {x,y} = {v,w}:
+//     k = partner(l), f = -+ g_l(nu); j on (v', w), both types (triangle);
+//   l on e(n) itself when nu in [max(an,1), bn]: k = partner(l); j = D_mu
+//     (d = h_n(mu) if l = n, f = -+ g_n(mu) if l = partner(n)).
+__global__ void __launch_bounds__(256) k_dp(BasisView B, AView A, const double* __restrict__ h,
+                                            double* __restrict__ Aout, double* __restrict__ Qout,
+                                            double* __restrict__ Rout) {
+  const int N = B.N;
+  const int64_t P = B.P, M = B.M, P2 = 2 * P;
+  const int64_t chunks = (P2 + 255) / 256;
+  const int nu = 1 + (int)(blockIdx.x / chunks);
+  const int64_t n = (blockIdx.x % chunks) * 256 + threadIdx.x;
+  if (n >= P2) return;
+  const Elem en = decode(B, n);
+  const int an = en.a, bn = en.b, tn = en.kind;
+  double acc2 = 0.0;
+  for (int vi = 0; vi < 2; ++vi) {
+    const int v = vi ? bn : an, vp = vi ? an : bn;
+    const int phn = coef_phase(tn, v, vp);
+    for (int w = 0; w < N; ++w) {
+      if (w == an || w == bn) continue;
+      const int x = imin(v, w), y = imax(v, w);
+      if (nu < imax(x, 1) || nu > y) continue;
+      const double gl = dlt(B, x, nu) - dlt(B, y, nu);
+      const int64_t pl = pair_index_any(N, v, w), pj = pair_index_any(N, vp, w);
+#pragma unroll
+      for (int tl = 0; tl < 2; ++tl) {
+        const int tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+        const int phl = coef_phase(tl, w, v);
+        const int sf = sgn_f(phn + coef_phase(tjf, vp, w) + phl);
+        const int sd = sgn_d(phn + coef_phase(tjd, vp, w) + phl);
+        const int64_t kb = (int64_t)(1 - tl) * P + pl;  // partner(l)
+        // read from the row that is common to the lanes of a warp (v = an: k; v = bn: j)
+        const double2 a1 = vi ? ldA(A, (int64_t)tjf * P + pj, kb) : ldA_row(A, (int64_t)tjf * P + pj, kb);
+        const double2 a2 = vi ? ldA(A, (int64_t)tjd * P + pj, kb) : ldA_row(A, (int64_t)tjd * P + pj, kb);
+        const double t = sgn_mul(sf, a1.x) - sgn_mul(sd, a2.y);
+        acc2 += tl == kS ? -gl * t : gl * t;
+      }
+    }
+  }
+  double acc = acc2 * kInvSqrt2;
+  double q = 0.0;
+  const int lo_n = imax(an, 1);
+  if (nu >= lo_n && nu <= bn) {
+    const double gn = dlt(B, an, nu) - dlt(B, bn, nu);
+    const int64_t nb = partner(B, n);
+    for (int tl = 0; tl < 2; ++tl) {
+      const double fk = tl == kS ? -gn : gn;  // f(partner(l), l, D_nu), l on e(n)
+      const int64_t kb = (int64_t)(1 - tl) * P + (n % P);
+      double t = 0.0;
+      if (tl == tn) {
+        for (int mu = lo_n; mu < N; ++mu) {
+          if (an == 0 && bn == 1 && mu == 1) continue;
+          t -= ldA(A, d_index(B, mu), kb).y * (dlt(B, an, mu) + dlt(B, bn, mu));
+        }
+      } else {
+        for (int mu = lo_n; mu <= bn; ++mu) t += ldA(A, d_index(B, mu), kb).x * (dlt(B, an, mu) - dlt(B, bn, mu));
+        if (tn == kS) t = -t;
+      }
+      acc = fma(fk, t, acc);
+    }
+    if (h != nullptr) q = __ldg(h + nb) * (tn == kS ? -gn : gn);
+  }
+  const double r = -0.5 * acc;
+  const int64_t o = d_index(B, nu) * M + n;
+  if (Rout) Rout[o] = r;
+  if (Qout) Qout[o] = q;
+  if (Aout) Aout[o] = q + r;
+}
+
+// Diagonal row s = D_nu, diagonal column n = D_mu; one warp per entry.  Only
+// l = (x, y) with x <= min(nu, mu), y >= nu contribute, k = partner(l); the
+// two types of l combine to
+//   g_xy(nu) g_xy(mu) (Re a_{S S} + Re a_{J J}) + 2 g_xy(nu) h_xy(mu) Im a_{S J}.
+__global__ void __launch_bounds__(256) k_dd(BasisView B, AView A, double* __restrict__ Aout,
+                                            double* __restrict__ Qout, double* __restrict__ Rout) {
+  const int N = B.N;
+  const int64_t P = B.P, M = B.M;
+  const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (e >= (int64_t)(N - 1) * (N - 1)) return;
+  const int nu = 1 + (int)(e / (N - 1)), mu = 1 + (int)(e % (N - 1));
+  const int xm = imin(nu, mu);
+  double acc = 0.0;
+  const int64_t cnt = (int64_t)(xm + 1) * N;
+  for (int64_t t = lane; t < cnt; t += 32) {
+    const int x = (int)(t / N), y = (int)(t % N);
+    if (y <= x || y < nu) continue;
+    const double gn = dlt(B, x, nu) - dlt(B, y, nu);
+    const double gm = dlt(B, x, mu) - dlt(B, y, mu);
+    const double hm = (x == 0 && y == 1 && mu == 1) ? 0.0 : dlt(B, x, mu) + dlt(B, y, mu);
+    const int64_t p = pair_index(N, x, y);
+    const double ass = ldA(A, p, p).x, ajj = ldA(A, P + p, P + p).x, asj = ldA(A, p, P + p).y;
+    acc = fma(gn, fma(gm, ass + ajj, 2.0 * hm * asj), acc);
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    const double r = -0.5 * acc;
+    const int64_t o = d_index(B, nu) * M + d_index(B, mu);
+    if (Rout) Rout[o] = r;
+    if (Qout) Qout[o] = 0.0;
+    if (Aout) Aout[o] = r;
+  }
+}
+
+// Pair-pair entries whose edges share one vertex v: s on (v, p), n on (v, q).
+// Shared memory: T1[w][tj][tk] = a[(q,w) tj][(p,w) tk],  T2[mu][t] = a[D_mu][(p,q) t].
+__global__ void __launch_bounds__(256) k_shared(BasisView B, AView A, double* __restrict__ Aout,
+                                                double* __restrict__ Rout) {
+  extern __shared__ double2 sm[];
+  const int N = B.N;
+  const int64_t P = B.P, M = B.M;
+  const int p = blockIdx.x / (N - 1);
+  int q = blockIdx.x % (N - 1);
+  if (q >= p) ++q;
+  double2* T1 = sm;
+  double2* T2 = sm + 4 * N;
+  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
+    const int w = t >> 2, tj = (t >> 1) & 1, tk = t & 1;
+    double2 val = make_double2(0.0, 0.0);
+    if (w != p && w != q) val = ldA(A, tj * P + pair_index_any(N, q, w), tk * P + pair_index_any(N, p, w));
+    T1[t] = val;
+  }
+  const int64_t ppq = pair_index_any(N, p, q);
+  for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+    const int mu = t >> 1, tt = t & 1;
+    T2[t] = mu >= 1 ? ldA(A, d_index(B, mu), tt * P + ppq) : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int v = warp; v < N; v += nw) {
+    if (v == p || v == q) continue;
+    const int64_t pvp = pair_index_any(N, v, p), pvq = pair_index_any(N, v, q);
+    for (int combo = 0; combo < 4; ++combo) {
+      const int ts = combo >> 1, tn = combo & 1;
+      double acc2 = 0.0, accD = 0.0;
+      // (A1) e(l) = (v, w), w not in {v, p, q}: k on (p, w), j on (q, w)
+      for (int w = lane; w < N; w += 32) {
+        if (w == v || w == p || w == q) continue;
+#pragma unroll
+        for (int tl = 0; tl < 2; ++tl) {
+          const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+          const int phl = coef_phase(tl, w, v);
+          const int sk = sgn_f(coef_phase(ts, v, p) + coef_phase(tk, p, w) + phl);
+          const int base = coef_phase(tn, v, q) + phl;
+          const int sf = sgn_f(base + coef_phase(tjf, q, w));
+          const int sd = sgn_d(base + coef_phase(tjd, q, w));
+          acc2 += sgn_mul(sk * sf, T1[4 * w + 2 * tjf + tk].x);
+          acc2 -= sgn_mul(sk * sd, T1[4 * w + 2 * tjd + tk].y);
+        }
+      }
+      // (A3) e(l) = e(n) = (v, q): k on (p, q), j = D_mu
+      {
+        const int lo = imin(v, q), hi = imax(v, q);
+        for (int tl = 0; tl < 2; ++tl) {
+          const int tk = 1 ^ tl ^ ts;
+          const int sk = sgn_f(coef_phase(ts, v, p) + coef_phase(tk, p, q) + coef_phase(tl, q, v));
+          double part = 0.0;
+          if (tl == tn) {  // d(D_mu, n, n) = delta_lo + delta_hi, mu >= max(lo,1), not (0,1,1)
+            for (int mu = imax(lo, 1) + lane; mu < N; mu += 32) {
+              if (lo == 0 && hi == 1 && mu == 1) continue;
+              part -= T2[2 * mu + tk].y * (dlt(B, lo, mu) + dlt(B, hi, mu));
+            }
+          } else {  // f(D_mu, partner(n), n) = -+(delta_lo - delta_hi), mu in [max(lo,1), hi]
+            for (int mu = imax(lo, 1) + lane; mu <= hi; mu += 32)
+              part += T2[2 * mu + tk].x * (dlt(B, lo, mu) - dlt(B, hi, mu));
+            if (tn == kS) part = -part;
+          }
+          accD += sgn_mul(sk, part) * kInvSqrt2;
+        }
+      }
+      // (B) l = partner(s) on (v, p): k = D_mu, j on (p, q)
+      {
+        const int lo = imin(v, p), hi = imax(v, p), tl = 1 - ts;
+        const int tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+        const int base = coef_phase(tn, v, q) + coef_phase(tl, p, v);
+        const int sf = sgn_f(base + coef_phase(tjf, q, p));
+        const int sd = sgn_d(base + coef_phase(tjd, q, p));
+        double part = 0.0;
+        for (int mu = imax(lo, 1) + lane; mu <= hi; mu += 32) {
+          const double g = dlt(B, lo, mu) - dlt(B, hi, mu);
+          part = fma(g, sgn_mul(sf, T2[2 * mu + tjf].x) + sgn_mul(sd, T2[2 * mu + tjd].y), part);
+        }
+        if (ts == kS) part = -part;  // f(D_mu, partner(s), s) = -+ g_s(mu)
+        accD += part * kInvSqrt2;
+      }
+      // (A2) e(l) = (p, q): k on (v, q), j on (v, p)
+      if (lane == 0) {
+#pragma unroll
+        for (int tl = 0; tl < 2; ++tl) {
+          const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+          const int sk = sgn_f(coef_phase(ts, p, v) + coef_phase(tk, v, q) + coef_phase(tl, q, p));
+          const int base = coef_phase(tn, q, v) + coef_phase(tl, p, q);
+          const int sf = sgn_f(base + coef_phase(tjf, v, p));
+          const int sd = sgn_d(base + coef_phase(tjd, v, p));
+          const int64_t k = tk * P + pvq;
+          const double2 a1 = ldA(A, tjf * P + pvp, k), a2 = ldA(A, tjd * P + pvp, k);
+          acc2 += sgn_mul(sk * sf, a1.x);
+          acc2 -= sgn_mul(sk * sd, a2.y);
+        }
+      }
+      const double tot = warp_sum(0.5 * acc2 + accD);
+      if (lane == 0) {
+        const double r = -0.5 * tot;
+        const int64_t o = (ts * P + pvp) * M + (tn * P + pvq);
+        if (Rout) Rout[o] += r;
+        if (Aout) Aout[o] += r;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Closed-form variants (LB_ALG_CLOSED) of k_shared and k_pd.  Inside the sum
+// over the free vertex w of an l = (v, w) family (and over the levels mu of a
+// D-fiber) every coefficient -- triangle signs, delta_w(nu), the order of w
+// and v -- only changes where w crosses one of a few fixed vertices, so the
+// sum is a handful of interval sums of the staged a values, taken from
+// prefix sums: O(1) per entry after O(N) staging per block.
+
+// sum_{w=lo}^{hi} x_w from a prefix array pre[w+1] = sum_{w' <= w} x_w'
+__device__ __forceinline__ double isum(const double* pre, int lo, int hi) {
+  return lo <= hi ? pre[hi + 1] - pre[lo] : 0.0;
+}
+
+// Sequential in-place prefix sum of arr[1..n] (arr[0] = 0 on entry).
+__device__ __forceinline__ void scan_inplace(double* arr, int n) {
+  double s = 0.0;
+  for (int i = 1; i <= n; ++i) {
+    s += arr[i];
+    arr[i] = s;
+  }
+}
+
+// sum_{mu in [max(lo,1), hi]} (delta_lo(mu) + sg * delta_hi(mu)) x_mu, with
+// cpre the prefix of c_mu x_mu and x the raw values: the end points lo and hi
+// in full, the interior (where the factor is c_mu for both signs) from cpre.
+__device__ __forceinline__ double dsum(const BasisView& B, const double* cpre, const double* x, int lo, int hi,
+                                       double sg, int top) {
+  // mu = lo (lo >= 1): delta_lo = lc_lo, delta_hi = 0
+  double s = 0.0;
+  if (lo >= 1) s += ld_lc(B, lo) * x[lo];
+  // lo < mu < hi: delta_lo = c_mu, delta_hi = 0
+  s += isum(cpre, imax(lo + 1, 1), hi - 1);
+  // mu = hi: delta_lo = c_hi, delta_hi = lc_hi
+  if (hi >= 1 && hi <= top) s += (ld_c(B, hi) + sg * ld_lc(B, hi)) * x[hi];
+  // mu > hi (d-fibers only, sg = +1): delta_lo + delta_hi = 2 c_mu
+  if (top > hi) s += 2.0 * isum(cpre, hi + 1, top);
+  return s;
+}
+
+__global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, double* __restrict__ Aout,
+                                                       double* __restrict__ Rout) {
+  extern __shared__ double sc[];
+  const int N = B.N;
+  const int64_t P = B.P, M = B.M;
+  const int p = blockIdx.x / (N - 1);
+  int q = blockIdx.x % (N - 1);
+  if (q >= p) ++q;
+  const int L = N + 1;
+  double* PX = sc;            // [4][L]  prefix over w of Re a[(q,w) tj][(p,w) tk], index tj*2+tk
+  double* PY = sc + 4 * L;    // [4][L]  prefix of Im
+  double* TX = sc + 8 * L;    // [2][L]  Re a[D_mu][(p,q) t] at mu (raw, index mu)
+  double* TY = sc + 10 * L;   // [2][L]  Im
+  double* CX = sc + 12 * L;   // [2][L]  prefix over mu of c_mu Re a[D_mu][(p,q) t]
+  double* CY = sc + 14 * L;   // [2][L]  prefix of c_mu Im
+  const int64_t ppq = pair_index_any(N, p, q);
+  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
+    const int w = t >> 2, jk = t & 3, tj = jk >> 1, tk = jk & 1;
+    double2 val = make_double2(0.0, 0.0);
+    if (w != p && w != q) val = ldA(A, tj * P + pair_index_any(N, q, w), tk * P + pair_index_any(N, p, w));
+    PX[jk * L + w + 1] = val.x;
+    PY[jk * L + w + 1] = val.y;
+  }
+  for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+    const int mu = t >> 1, tt = t & 1;
+    const double2 val = mu >= 1 ? ldA(A, d_index(B, mu), tt * P + ppq) : make_double2(0.0, 0.0);
+    TX[tt * L + mu] = val.x;
+    TY[tt * L + mu] = val.y;
+    CX[tt * L + mu + 1] = mu >= 1 ? ld_c(B, mu) * val.x : 0.0;
+    CY[tt * L + mu + 1] = mu >= 1 ? ld_c(B, mu) * val.y : 0.0;
+  }
+  if (threadIdx.x < 12) {
+    double* arr = threadIdx.x < 4 ? PX + threadIdx.x * L
+                : threadIdx.x < 8 ? PY + (threadIdx.x - 4) * L
+                : threadIdx.x < 10 ? CX + (threadIdx.x - 8) * L : CY + (threadIdx.x - 10) * L;
+    arr[0] = 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x < 12) {
+    double* arr = threadIdx.x < 4 ? PX + threadIdx.x * L
+                : threadIdx.x < 8 ? PY + (threadIdx.x - 4) * L
+                : threadIdx.x < 10 ? CX + (threadIdx.x - 8) * L : CY + (threadIdx.x - 10) * L;
+    scan_inplace(arr, N);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
+    const int v = t >> 2, combo = t & 3;
+    if (v == p || v == q) continue;
+    const int ts = combo >> 1, tn = combo & 1;
+    double acc2 = 0.0, accD = 0.0;
+    // (A1): w outside {v, p, q}, in the four intervals between the sorted vertices
+    int b0 = v, b1 = p, b2 = q, tmp;
+    if (b0 > b1) { tmp = b0; b0 = b1; b1 = tmp; }
+    if (b1 > b2) { tmp = b1; b1 = b2; b2 = tmp; }
+    if (b0 > b1) { tmp = b0; b0 = b1; b1 = tmp; }
+    const int ilo[4] = {0, b0 + 1, b1 + 1, b2 + 1}, ihi[4] = {b0 - 1, b1 - 1, b2 - 1, N - 1};
+#pragma unroll
+    for (int iv = 0; iv < 4; ++iv) {
+      if (ilo[iv] > ihi[iv]) continue;
+      const int w = ilo[iv];  // any w of the interval gives the same signs
+#pragma unroll
+      for (int tl = 0; tl < 2; ++tl) {
+        const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+        const int phl = coef_phase(tl, w, v);
+        const int sk = sgn_f(coef_phase(ts, v, p) + coef_phase(tk, p, w) + phl);
+        const int base = coef_phase(tn, v, q) + phl;
+        const int sf = sgn_f(base + coef_phase(tjf, q, w));
+        const int sd = sgn_d(base + coef_phase(tjd, q, w));
+        acc2 += sgn_mul(sk * sf, isum(PX + (tjf * 2 + tk) * L, ilo[iv], ihi[iv]));
+        acc2 -= sgn_mul(sk * sd, isum(PY + (tjd * 2 + tk) * L, ilo[iv], ihi[iv]));
+      }
+    }
+    // (A3) e(l) = (v, q): k on (p, q), j = D_mu
+    {
+      const int lo = imin(v, q), hi = imax(v, q);
+      for (int tl = 0; tl < 2; ++tl) {
+        const int tk = 1 ^ tl ^ ts;
+        const int sk = sgn_f(coef_phase(ts, v, p) + coef_phase(tk, p, q) + coef_phase(tl, q, v));
+        double part;
+        if (tl == tn) part = -dsum(B, CY + tk * L, TY + tk * L, lo, hi, 1.0, N - 1);
+        else part = (tn == kS ? -1.0 : 1.0) * dsum(B, CX + tk * L, TX + tk * L, lo, hi, -1.0, hi);
+        accD += sgn_mul(sk, part) * kInvSqrt2;
+      }
+    }
+    // (B) l = partner(s) on (v, p): k = D_mu, j on (p, q)
+    {
+      const int lo = imin(v, p), hi = imax(v, p), tl = 1 - ts;
+      const int tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+      const int base = coef_phase(tn, v, q) + coef_phase(tl, p, v);
+      const int sf = sgn_f(base + coef_phase(tjf, q, p));
+      const int sd = sgn_d(base + coef_phase(tjd, q, p));
+      double part = sgn_mul(sf, dsum(B, CX + tjf * L, TX + tjf * L, lo, hi, -1.0, hi)) +
+                    sgn_mul(sd, dsum(B, CY + tjd * L, TY + tjd * L, lo, hi, -1.0, hi));
+      if (ts == kS) part = -part;
+      accD += part * kInvSqrt2;
+    }
+    // (A2) e(l) = (p, q): k on (v, q), j on (v, p)
+    const int64_t pvp = pair_index_any(N, v, p), pvq = pair_index_any(N, v, q);
+#pragma unroll
+    for (int tl = 0; tl < 2; ++tl) {
+      const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+      const int sk = sgn_f(coef_phase(ts, p, v) + coef_phase(tk, v, q) + coef_phase(tl, q, p));
+      const int base = coef_phase(tn, q, v) + coef_phase(tl, p, q);
+      const int sf = sgn_f(base + coef_phase(tjf, v, p));
+      const int sd = sgn_d(base + coef_phase(tjd, v, p));
+      const int64_t k = tk * P + pvq;
+      const double2 a1 = ldA(A, tjf * P + pvp, k), a2 = ldA(A, tjd * P + pvp, k);
+      acc2 += sgn_mul(sk * sf, a1.x);
+      acc2 -= sgn_mul(sk * sd, a2.y);
+    }
+    const double r = -0.5 * (0.5 * acc2 + accD);
+    const int64_t o = (ts * P + pvp) * M + (tn * P + pvq);
+    if (Rout) Rout[o] += r;
+    if (Aout) Aout[o] += r;
+  }
+}
+
+// Closed-form k_pd: per row s the nu-independent sums are prefix arrays,
+//   PGY[lam] = sum gs(lam') Im Y[lam'],  PG2C = sum 2 gs c,  PCY = sum c_mu Im Y[mu],
+//   and for each (vi, tl) the raw Re a(partner(l), k), Im a(l, k) over w.
+__global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A, const double* __restrict__ h,
+                                                           double* __restrict__ Aout, double* __restrict__ Qout,
+                                                           double* __restrict__ Rout) {
+  extern __shared__ double sq[];
+  const int N = B.N;
+  const int64_t P = B.P, M = B.M;
+  const int64_t s = blockIdx.x;
+  const Elem es = decode(B, s);
+  const int as = es.a, bs = es.b, ts = es.kind;
+  const int64_t sb = partner(B, s);
+  const int lo_s = imax(as, 1);
+  const double sgs = ts == kS ? 1.0 : -1.0;
+  const int L = N + 1;
+  double* YY = sq;            // Im a[partner(s)][D_x]   (raw, index x)
+  double* PGY = sq + L;       // prefix of gs(lam) YY[lam] over lam in [lo_s, bs]
+  double* PG2C = sq + 2 * L;  // prefix of 2 gs(lam) c_lam
+  double* PCY = sq + 3 * L;   // prefix of c_mu YY[mu]
+  double* PW = sq + 4 * L;    // [8][L]: (vi, tl, {Re a(partner(l),k), Im a(l,k)}) prefixes over w
+  __shared__ double cst[2];   // c1 = sum gs Re a[s][D_mu], c2 = sum gs Im a[partner(s)][D_mu]
+  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+    const double y = x >= 1 ? ldA(A, sb, d_index(B, x)).y : 0.0;
+    const double gs = (x >= lo_s && x <= bs) ? dlt(B, as, x) - dlt(B, bs, x) : 0.0;
+    YY[x] = y;
+    PGY[x + 1] = gs * y;
+    PG2C[x + 1] = x >= 1 ? 2.0 * gs * ld_c(B, x) : 0.0;
+    PCY[x + 1] = x >= 1 ? ld_c(B, x) * y : 0.0;
+  }
+  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
+    const int vi = t / (2 * N), w = (t / 2) % N, tl = t & 1;
+    double bx = 0.0, ly = 0.0;
+    if (w != as && w != bs) {
+      const int v = vi ? bs : as, vp = vi ? as : bs;
+      const int64_t pl = pair_index_any(N, v, w), pk = pair_index_any(N, vp, w);
+      const int64_t k = (int64_t)(1 ^ tl ^ ts) * P + pk;
+      ly = ldA(A, (int64_t)tl * P + pl, k).y;
+      bx = ldA(A, (int64_t)(1 - tl) * P + pl, k).x;
+    }
+    PW[((vi * 2 + tl) * 2 + 0) * L + w + 1] = bx;
+    PW[((vi * 2 + tl) * 2 + 1) * L + w + 1] = ly;
+  }
+  if (threadIdx.x < 11) {
+    double* arr = threadIdx.x < 3 ? PGY + threadIdx.x * L : PW + (threadIdx.x - 3) * L;
+    arr[0] = 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x < 11) {
+    double* arr = threadIdx.x < 3 ? PGY + threadIdx.x * L : PW + (threadIdx.x - 3) * L;
+    scan_inplace(arr, N);
+  } else if (threadIdx.x == 32) {
+    double c1 = 0.0;
+    for (int mu = lo_s; mu <= bs; ++mu) c1 += (dlt(B, as, mu) - dlt(B, bs, mu)) * ldA(A, s, d_index(B, mu)).x;
+    cst[0] = c1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) cst[1] = isum(PGY, lo_s, bs);
+  __syncthreads();
+  for (int nu = 1 + threadIdx.x; nu < N; nu += blockDim.x) {
+    // l = D_lam
+    double accD = 2.0 * ld_c(B, nu) * isum(PGY, lo_s, imin(bs, nu - 1));
+    accD += YY[nu] * isum(PG2C, imax(lo_s, nu + 1), bs);
+    if (nu >= lo_s && nu <= bs) {
+      const double gs = dlt(B, as, nu) - dlt(B, bs, nu);
+      double t2 = 2.0 * isum(PCY, nu + 1, N - 1);
+      if (nu != 1) t2 += 2.0 * (double)(1 - nu) * ld_c(B, nu) * YY[nu];
+      accD += gs * t2;
+    }
+    double acc = sgs * accD;
+    // l = (v, w) sharing a vertex with e(s): intervals of w split at as, bs, nu
+    double accA = 0.0;
+    int b0 = as, b1 = bs, b2 = nu, tmp;
+    if (b1 > b2) { tmp = b1; b1 = b2; b2 = tmp; }
+    if (b0 > b1) { tmp = b0; b0 = b1; b1 = tmp; }
+    const int nodes[3] = {b0, b1, b2};
+    for (int vi = 0; vi < 2; ++vi) {
+      const int v = vi ? bs : as, vp = vi ? as : bs;
+      const int phs = coef_phase(ts, v, vp);
+      const double dv = dlt(B, v, nu);
+      for (int tl = 0; tl < 2; ++tl) {
+        const int tk = 1 ^ tl ^ ts;
+        const double* PB = PW + ((vi * 2 + tl) * 2 + 0) * L;
+        const double* PL = PW + ((vi * 2 + tl) * 2 + 1) * L;
+        // one interval [lo, hi] of w values (none in e(s)) with the given delta_w(nu)
+        auto add = [&](int lo, int hi, double dw) {
+          if (lo > hi) return;
+          const int w = lo;
+          const double hl = dv + dw;
+          const double gl = w < v ? dw - dv : dv - dw;
+          const double fl = tl == kS ? -gl : gl;
+          const int sk = sgn_f(phs + coef_phase(tk, vp, w) + coef_phase(tl, w, v));
+          accA += sgn_mul(sk, fl * isum(PB, lo, hi) - hl * isum(PL, lo, hi));
+        };
+        int prev = 0;
+        for (int i = 0; i < 3; ++i) {
+          const int x = nodes[i];
+          if (x < prev) continue;  // repeated node
+          add(prev, x - 1, (x - 1) < nu ? ld_c(B, nu) : 0.0);
+          if (x == nu && x != as && x != bs) add(x, x, ld_lc(B, nu));
+          prev = x + 1;
+        }
+        add(prev, N - 1, 0.0);  // every w here is above nu
+      }
+    }
+    acc += accA * kInvSqrt2;
+    // l = partner(s), k = D_mu
+    {
+      const double gnu = (nu >= lo_s && nu <= bs) ? dlt(B, as, nu) - dlt(B, bs, nu) : 0.0;
+      const double hnu = (nu >= lo_s && !(as == 0 && bs == 1 && nu == 1)) ? dlt(B, as, nu) + dlt(B, bs, nu) : 0.0;
+      acc += -gnu * cst[0] + sgs * hnu * cst[1];
+    }
+    double q = 0.0;
+    if (h != nullptr && nu >= lo_s && nu <= bs) q = __ldg(h + sb) * sgs * (dlt(B, as, nu) - dlt(B, bs, nu));
+    const double r = -0.5 * acc;
+    const int64_t o = s * M + d_index(B, nu);
+    if (Rout) Rout[o] = r;
+    if (Qout) Qout[o] = q;
+    if (Aout) Aout[o] = q + r;
+  }
+}
+
+// Pair-pair entries on the same edge (a, b): s, n in {S_ab, J_ab}.  One block
+// per edge; shared memory: G[mu] = f(D_mu, partner(s), s), Z[nu] = the
+// z-fiber of (partner(s), n) at D_nu.
+constexpr int kSameThreads = 128;
+
+__global__ void __launch_bounds__(kSameThreads) k_same(BasisView B, AView A, double* __restrict__ Aout,
+                                                       double* __restrict__ Rout) {
+  extern __shared__ double shd[];
+  __shared__ double red[kSameThreads / 32];
+  const int N = B.N;
+  const int64_t P = B.P, M = B.M;
+  const int64_t e = blockIdx.x;
+  const int32_t ab = __ldg(B.pair_ab + e);
+  const int a = ab >> 16, b = ab & 0xffff;
+  const int lo = imax(a, 1);
+  double* G = shd;      // [N]
+  double* Z = shd + N;  // [N]
+  for (int combo = 0; combo < 4; ++combo) {
+    const int ts = combo >> 1, tn = combo & 1;
+    const bool dfib = ts != tn;  // n = partner(s) = l: d-fiber; n = s: f-fiber of partner(n)
+    __syncthreads();
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+      const double g = (t >= lo && t <= b) ? dlt(B, a, t) - dlt(B, b, t) : 0.0;
+      G[t] = ts == kS ? -g : g;
+      double z = 0.0;
+      if (dfib) {
+        if (t >= lo && !(a == 0 && b == 1 && t == 1)) z = dlt(B, a, t) + dlt(B, b, t);
+      } else if (t >= lo && t <= b) {
+        z = dlt(B, a, t) - dlt(B, b, t);
+        if (tn == kS) z = -z;
+      }
+      Z[t] = z;
+    }
+    __syncthreads();
+    double acc2 = 0.0, accD = 0.0;
+    // (A) e(l) = (v, w), v in {a, b}, w outside: k and j on (v', w)
+    for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+      const int vi = t / N, w = t % N;
+      if (w == a || w == b) continue;
+      const int v = vi ? b : a, vp = vi ? a : b;
+      const int64_t pw = pair_index_any(N, vp, w);
+#pragma unroll
+      for (int tl = 0; tl < 2; ++tl) {
+        const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+        const int phl = coef_phase(tl, w, v);
+        const int sk = sgn_f(coef_phase(ts, v, vp) + coef_phase(tk, vp, w) + phl);
+        const int base = coef_phase(tn, v, vp) + phl;
+        const int sf = sgn_f(base + coef_phase(tjf, vp, w));
+        const int sd = sgn_d(base + coef_phase(tjd, vp, w));
+        const double2 a1 = ldA(A, tjf * P + pw, tk * P + pw), a2 = ldA(A, tjd * P + pw, tk * P + pw);
+        acc2 += sgn_mul(sk * sf, a1.x);
+        acc2 -= sgn_mul(sk * sd, a2.y);
+      }
+    }
+    // (B) l = partner(s): k = D_mu (mu in [lo, b]), j = D_nu
+    const int nhi = dfib ? N - 1 : b;
+    for (int mu = lo + threadIdx.x; mu <= b; mu += blockDim.x) {
+      const int64_t kmu = d_index(B, mu);
+      double inner = 0.0;
+      for (int nu = lo; nu <= nhi; ++nu) {
+        const double2 av = ldA(A, d_index(B, nu), kmu);
+        inner = fma(Z[nu], dfib ? -av.y : av.x, inner);
+      }
+      accD = fma(G[mu], inner, accD);
+    }
+    double tot = warp_sum(0.5 * acc2 + accD);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int i = 0; i < kSameThreads / 32; ++i) sum += red[i];
+      const double r = -0.5 * sum;
+      const int64_t o = (ts * P + e) * M + (tn * P + e);
+      if (Rout) Rout[o] += r;
+      if (Aout) Aout[o] += r;
+    }
+  }
+}
+
 }  // namespace
 
 namespace lbi {
 
 cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double2* a, double* A,
-                           double* Q, double* R, double* K, cudaStream_t st) {
+                           double* Q, double* R, double* K, int algorithm, cudaStream_t st) {
   AView av{a, B.M};
-  const int64_t chunks = (B.M + 255) / 256;
-  const int64_t blocks = chunks * B.M;
-  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const int N = B.N;
+  const int64_t P2 = 2 * B.P;
+  const int64_t chunks = (P2 + 255) / 256;
+  if (P2 * chunks > 0x7fffffffLL || N > kMaxDenseN) return cudaErrorInvalidConfiguration;
+  cudaError_t e;
   if (A || Q || R) {
-    k_assemble<false><<<(unsigned)blocks, 256, 0, st>>>(B, av, h, A, Q, R, nullptr);
+    // pair x pair
+    if (algorithm == LB_ALG_CLOSED)
+      k_entries<LB_ALG_CLOSED><<<(unsigned)(P2 * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
+    else
+      k_entries<LB_ALG_JOIN><<<(unsigned)(P2 * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
+    // pair x diagonal
+    if (algorithm == LB_ALG_CLOSED) {
+      const size_t pd_smem = sizeof(double) * 12 * (size_t)(N + 1);
+      e = cudaFuncSetAttribute(k_pd_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pd_smem);
+      if (e != cudaSuccess) return e;
+      k_pd_closed<<<(unsigned)P2, kRowThreads, pd_smem, st>>>(B, av, h, A, Q, R);
+    } else {
+      const size_t pd_smem = sizeof(double2) * 10 * (size_t)N;
+      e = cudaFuncSetAttribute(k_pd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pd_smem);
+      if (e != cudaSuccess) return e;
+      k_pd<<<(unsigned)P2, kRowThreads, pd_smem, st>>>(B, av, h, A, Q, R);
+    }
+    // diagonal x pair, diagonal x diagonal
+    k_dp<<<(unsigned)((N - 1) * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
+    const int64_t dd_warps = (int64_t)(N - 1) * (N - 1);
+    k_dd<<<(unsigned)((dd_warps * 32 + 255) / 256), 256, 0, st>>>(B, av, A, Q, R);
+    note_launch(4);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (A || R) {
+    if (N >= 3 && algorithm == LB_ALG_CLOSED) {
+      const size_t sh_smem = sizeof(double) * 16 * (size_t)(N + 1);
+      e = cudaFuncSetAttribute(k_shared_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_smem);
+      if (e != cudaSuccess) return e;
+      k_shared_closed<<<(unsigned)(N * (N - 1)), 256, sh_smem, st>>>(B, av, A, R);
+      note_launch(1);
+    } else if (N >= 3) {
+      const size_t sh_smem = sizeof(double2) * 6 * (size_t)N;
+      e = cudaFuncSetAttribute(k_shared, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_smem);
+      if (e != cudaSuccess) return e;
+      k_shared<<<(unsigned)(N * (N - 1)), 256, sh_smem, st>>>(B, av, A, R);
+      note_launch(1);
+    }
+    k_same<<<(unsigned)B.P, kSameThreads, sizeof(double) * 2 * N, st>>>(B, av, A, R);
     note_launch(1);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   if (K) {

@@ -24,7 +24,7 @@ namespace {
 
 using namespace lb;
 
-__global__ void k_tables(int N, int32_t* pair_ab, double* c, double* lc) {
+__global__ void k_tables(int N, int32_t* pair_ab, double* tab) {
   int64_t P = (int64_t)N * (N - 1) / 2;
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < P) {
@@ -38,15 +38,23 @@ __global__ void k_tables(int N, int32_t* pair_ab, double* c, double* lc) {
     }
     pair_ab[t] = (a << 16) | (a + 1 + (int)p);
   }
+  double* c = tab;
+  double* lc = tab + N;
+  double* c2 = tab + 2 * N;
+  double* inv = tab + 3 * N;
+  if (t <= N) {
+    if (t >= 1) inv[t] = 1.0 / (double)t;
+    else inv[0] = 0.0;
+  }
   if (t < N) {
     if (t == 0) {
-      c[0] = 0.0;
-      lc[0] = 0.0;
+      c[0] = lc[0] = c2[0] = 0.0;
     } else {
       double l = (double)t;
       double cl = 1.0 / sqrt(l * (l + 1.0));
       c[t] = cl;
       lc[t] = -l * cl;
+      c2[t] = 1.0 / (l * (l + 1.0));
     }
   }
 }
@@ -206,10 +214,10 @@ inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs
 
 namespace lbi {
 
-cudaError_t build_tables(int N, int32_t* pair_ab, double* c, double* lc, cudaStream_t st) {
+cudaError_t build_tables(int N, int32_t* pair_ab, double* tab, cudaStream_t st) {
   int64_t P = (int64_t)N * (N - 1) / 2;
-  int64_t n = P > N ? P : N;
-  k_tables<<<nblocks(n, 256), 256, 0, st>>>(N, pair_ab, c, lc);
+  int64_t n = P > N + 1 ? P : N + 1;
+  k_tables<<<nblocks(n, 256), 256, 0, st>>>(N, pair_ab, tab);
   note_launch(1);
   return cudaGetLastError();
 }

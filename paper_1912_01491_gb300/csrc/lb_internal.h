@@ -9,35 +9,36 @@
 #include "lindblad.h"
 #include "su_n.cuh"
 
-// Device-resident basis: index tables plus (for N <= kMaxListN) the
-// canonical nonzero f and d lists produced by kernel (a).
+// Device-resident basis: the lexicographic pair table and the per-level
+// constants (layout of d_tab: c[N], lc[N], c2[N], inv[N+1]).
 struct lb_basis {
   int N;
   int64_t P, M;
   int32_t* d_pair_ab = nullptr;  // P
-  double* d_c = nullptr;         // N
-  double* d_lc = nullptr;        // N
-  int64_t nnz[2] = {0, 0};       // canonical counts of f, d
-  int32_t* d_idx[2] = {nullptr, nullptr};
-  double* d_val[2] = {nullptr, nullptr};
+  double* d_tab = nullptr;       // 4N + 1
   lb::BasisView view() const {
     lb::BasisView v;
     v.N = N; v.P = P; v.M = M;
-    v.pair_ab = d_pair_ab; v.c = d_c; v.lc = d_lc;
+    v.pair_ab = d_pair_ab;
+    v.c = d_tab;
+    v.lc = d_tab + N;
+    v.c2 = d_tab + 2 * N;
+    v.inv = d_tab + 3 * N;
     return v;
   }
 };
 
 namespace lbi {
 
-constexpr int kMaxListN = 512;
+// dense assembly keeps per-block tables of O(N) entries in shared memory
+constexpr int kMaxDenseN = 512;
 
 void set_error(const char* fmt, ...);
 void note_launch(int n);
 int cuda_fail(cudaError_t e, const char* what);
 
 // kernel (a) and friends (lb_basis.cu)
-cudaError_t build_tables(int N, int32_t* pair_ab, double* c, double* lc, cudaStream_t st);
+cudaError_t build_tables(int N, int32_t* pair_ab, double* tab, cudaStream_t st);
 cudaError_t structure_count(const lb::BasisView& B, int which, int64_t* per_m, cudaStream_t st);
 cudaError_t structure_fill(const lb::BasisView& B, int which, const int64_t* offsets,
                            int32_t* idx3, double* val, cudaStream_t st);
@@ -46,7 +47,7 @@ cudaError_t rho(const lb::BasisView& B, const double* v, double2* out, cudaStrea
 
 // dense assembly (lb_assemble.cu)
 cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double2* a,
-                           double* A, double* Q, double* R, double* K, cudaStream_t st);
+                           double* A, double* Q, double* R, double* K, int algorithm, cudaStream_t st);
 cudaError_t join_terms(const lb::BasisView& B, unsigned long long* d_count, cudaStream_t st);
 
 // RK4 (lb_rk4.cu)

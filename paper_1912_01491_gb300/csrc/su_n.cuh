@@ -46,6 +46,8 @@ struct BasisView {
   const int32_t* pair_ab;  // P entries, (a << 16) | b
   const double* c;         // c[l] = 1/sqrt(l(l+1)),   l = 1..N-1 (c[0] unused)
   const double* lc;        // lc[l] = -l * c[l]
+  const double* c2;        // c2[l] = c[l]^2 = 1/(l(l+1))
+  const double* inv;       // inv[l] = 1/l, l = 1..N  (sum_{l=x}^{y} c2[l] = inv[x] - inv[y+1])
 };
 
 struct Elem {

@@ -18,6 +18,8 @@ LB_F, LB_D = 0, 1
 LB_FP64, LB_FP32, LB_BF16 = 0, 1, 2
 LB_SYS_A, LB_SYS_Q, LB_SYS_R, LB_SYS_K = 0, 1, 2, 3
 PRECISIONS = {"fp64": LB_FP64, "fp32": LB_FP32, "bf16": LB_BF16}
+LB_ALG_JOIN, LB_ALG_CLOSED = 0, 1
+ALGORITHMS = {"join": LB_ALG_JOIN, "closed": LB_ALG_CLOSED}
 
 _c_i64 = ctypes.c_int64
 _vp = ctypes.c_void_p
@@ -56,12 +58,13 @@ def load():
         "lb_expand": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
         "lb_rho": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
         "lb_assemble_dense": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "lb_assemble_dense_ex": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
         "lb_pack_fp32": (ctypes.c_int, [_c_i64, _vp, _vp, _vp]),
         "lb_pack_bf16": (ctypes.c_int, [_c_i64, _vp, _vp, _vp, _vp]),
         "lb_rk4_workspace_bytes": (ctypes.c_size_t, [_c_i64]),
         "lb_rk4_dense": (ctypes.c_int, [_c_i64, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp, _vp,
                                         ctypes.c_double, _c_i64, _vp, _c_i64, _vp, _vp]),
-        "lb_assemble": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)]),
+        "lb_assemble": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
         "lb_system_destroy": (ctypes.c_int, [_vp]),
         "lb_system_get": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
         "lb_integrate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double,
@@ -203,7 +206,7 @@ class Basis:
         _check(load().lb_rho(self._h, _ptr(v), _ptr(out), _stream(stream)))
         return out
 
-    def assemble_dense(self, a, h=None, A=True, Q=False, R=False, K=True, stream=None):
+    def assemble_dense(self, a, h=None, A=True, Q=False, R=False, K=True, algorithm="join", stream=None):
         """Dense Q, R, K (Eqs. (07)-(09)).  a: M x M complex128 device tensor.
 
         A, Q, R, K may be True (allocate), False/None (skip) or a preallocated
@@ -219,8 +222,9 @@ class Basis:
                 out[name] = torch.empty(shape, dtype=torch.float64, device=a.device)
             elif want is not None and want is not False:
                 out[name] = want
-        _check(load().lb_assemble_dense(self._h, _ptr(h), _ptr(a), _ptr(out.get("A")), _ptr(out.get("Q")),
-                                        _ptr(out.get("R")), _ptr(out.get("K")), _stream(stream)))
+        _check(load().lb_assemble_dense_ex(self._h, _ptr(h), _ptr(a), _ptr(out.get("A")), _ptr(out.get("Q")),
+                                           _ptr(out.get("R")), _ptr(out.get("K")), ALGORITHMS[algorithm],
+                                           _stream(stream)))
         return out
 
 
@@ -266,13 +270,14 @@ def rk4_dense(Ap, K, v, dt, nsteps, precision="fp64", scale=None, A64=None, corr
 class System:
     """Host-buffer interface: lb_assemble / lb_system_get / lb_integrate."""
 
-    def __init__(self, basis, a, H=None, keep_parts=False):
+    def __init__(self, basis, a, H=None, keep_parts=False, algorithm="join"):
         lib = load()
         a = np.ascontiguousarray(a, np.complex128)
         assert a.shape == (basis.M, basis.M)
         Hc = None if H is None else np.ascontiguousarray(H, np.complex128)
         h = _vp()
-        _check(lib.lb_assemble(basis.handle, _ptr(Hc), _ptr(a), int(bool(keep_parts)), ctypes.byref(h)))
+        _check(lib.lb_assemble(basis.handle, _ptr(Hc), _ptr(a), int(bool(keep_parts)), ALGORITHMS[algorithm],
+                               ctypes.byref(h)))
         self._h = h
         self.basis = basis
         self.M = basis.M

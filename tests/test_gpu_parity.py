@@ -87,18 +87,20 @@ def _assert_entries(x, ref, scale, what):
         what, len(bad), bad[:3].tolist(), err[tuple(bad[0])], tol[tuple(bad[0])])
 
 
-def _gpu_system(B, H, a):
+def _gpu_system(B, H, a, algorithm="join"):
     h = B.expand(torch.tensor(H, device="cuda")).real.contiguous()
-    out = B.assemble_dense(torch.tensor(a, device="cuda"), h=h, A=True, Q=True, R=True, K=True)
+    out = B.assemble_dense(torch.tensor(a, device="cuda"), h=h, A=True, Q=True, R=True, K=True,
+                           algorithm=algorithm)
     torch.cuda.synchronize()
     return {k: v.cpu().numpy() for k, v in out.items()}
 
 
+@pytest.mark.parametrize("algorithm", ["join", "closed"])
 @pytest.mark.parametrize("N", list(range(2, 13)) + [16, 23])
-def test_dense_assembly_parity(N):
+def test_dense_assembly_parity(N, algorithm):
     H, a = _case(N, 1000 + N)
     with lbm().Basis(N) as B, Oracle(N) as o:
-        g = _gpu_system(B, H, a)
+        g = _gpu_system(B, H, a, algorithm)
         h, _ = o.expand(H)
         Q = o.Q(h.real)
         R, S = o.R(a, return_scale=True)
@@ -112,12 +114,13 @@ def test_dense_assembly_parity(N):
     assert np.abs(g["K"] - K).max() <= 1e-12 * max(np.abs(K).max(), 1e-300) + 1e-17
 
 
-def test_dense_assembly_n50_random_lindbladian():
+@pytest.mark.parametrize("algorithm", ["join", "closed"])
+def test_dense_assembly_n50_random_lindbladian(algorithm):
     """The 50-level random Lindbladian (M = 2499): full R, Q, K parity."""
     N = 50
     H, a = _case(N, 1050)
     with lbm().Basis(N) as B, Oracle(N) as o:
-        g = _gpu_system(B, H, a)
+        g = _gpu_system(B, H, a, algorithm)
         h, _ = o.expand(H)
         Q = o.Q(h.real)
         R, S = o.R(a, return_scale=True)
