@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-rows", type=int, default=2, help="rows of R in the CPU-oracle sample")
+    p.add_argument("--algorithm", default="closed", choices=["closed", "join"],
+                   help="dense R assembly: closed-form sums of the join (default) or every join term")
     return p.parse_args()
 
 
@@ -169,10 +171,11 @@ def run_gb300(args):
                                             ctypes.byref(got), st))
         # a2: expansions
         h = B.expand(H).real.contiguous()
+        hh[0] = h
         v0 = B.expand(rho0).real.contiguous()
-        # a3-a5: assembly
+        # a3-a5: assembly (per-kernel device times from CUDA events on this stream)
         ev[0].record(stream)
-        B.assemble_dense(a, h=h, A=A, K=K)
+        kms.append(B.assemble_dense_timed(a, h=h, A=A, K=K, algorithm=args.algorithm))
         ev[1].record(stream)
         # a6: packing
         lb.pack_fp32(A, out=A32)
@@ -186,11 +189,15 @@ def run_gb300(args):
         lb.rk4_dense(A32, K, v32, dt, nrk, precision="fp32", A64=A, correct_every=50, work=work)
         ev[4].record(stream)
 
+    hh = [None]
+
     def new_events():
         return [torch.cuda.Event(enable_timing=True) for _ in range(5)]
 
+    kms = []
     for _ in range(args.warmup):
         step(new_events())
+    kms.clear()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -211,9 +218,12 @@ def run_gb300(args):
     torch.cuda.synchronize()
     launches = native.launch_count() - launches0
     clk = clocks.stop()
+    h_last = hh[0]
 
     total_ms = t_start.elapsed_time(t_stop)
-    asm_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
+    asm_ms = sum(sum(d.values()) for d in kms)
+    kern = {k: sum(d[k] for d in kms) / len(kms) for k in kms[0]}
+    top = max(kern, key=kern.get)
     rk_ms = sum(e[2].elapsed_time(e[3]) for e in evs)
     rk32_ms = sum(e[3].elapsed_time(e[4]) for e in evs)
     times = torch.tensor([total_ms, asm_ms, rk_ms, rk32_ms], dtype=torch.float64, device=dev)
@@ -223,8 +233,14 @@ def run_gb300(args):
     K_ = args.steps
     value = world * K_ * M * M / (asm_ms * 1e-3)
     t_asm = asm_ms / K_ * 1e-3
-    achieved = 2.0 * W / t_asm / 1e12
     alg_bytes = 16.0 * M * M + 8.0 * M * M + 16.0 * M
+    # the other algorithm, timed outside the timed region for comparison
+    other = "join" if args.algorithm == "closed" else "closed"
+    other_ms = []
+    for _ in range(2):
+        other_ms.append(sum(B.assemble_dense_timed(a, h=h_last, A=A, K=K, algorithm=other).values()))
+    B.assemble_dense_timed(a, h=h_last, A=A, K=K, algorithm=args.algorithm)
+    roof = assembly_roofline(args.algorithm, top, kern[top], N, M, W, fp64_peak, measured_peaks())
 
     e2e = None
     if not args.no_e2e:
@@ -260,22 +276,13 @@ def run_gb300(args):
         },
         "rk4_steps_per_s": world * K_ * nrk / (rk_ms * 1e-3),
         "rk4_fp32_corrected_steps_per_s": world * K_ * nrk / (rk32_ms * 1e-3),
+        "assembly_algorithm": args.algorithm,
         "assembly_ms": asm_ms / K_,
-        "join_terms_per_s": world * K_ * W / (asm_ms * 1e-3),
-        "roofline": {
-            "kernel": "k_assemble (dense Q/R/A, one thread per entry) + k_kvec",
-            "bound": "alu",
-            "achieved": achieved,
-            "peak": fp64_peak,
-            "unit": "TFLOP/s",
-            "frac": achieved / fp64_peak,
-            "traffic": None,
-            "peak_source": "FP64 FMA probe (lb_probe_fp64) on this GPU",
-            "algorithmic_flops_per_launch": 2.0 * W,
-            "algorithmic_bytes_per_launch": alg_bytes,
-            "achieved_gbs": alg_bytes / t_asm / 1e9,
-            "hbm_peak_gbs": peaks.get("hbm_gbs"),
-        },
+        "assembly_kernel_ms": kern,
+        "assembly_%s_entries_per_s" % other: world * M * M / (statistics.mean(other_ms) * 1e-3),
+        "join_terms": W,
+        "assembly_gbs_algorithmic": alg_bytes / t_asm / 1e9,
+        "roofline": roof,
         "rk4_roofline": {
             "kernel": "k_stage<FP64> (fused GEMV + stage update)",
             "bound": "alu",
@@ -298,6 +305,32 @@ def run_gb300(args):
     return out
 
 
+def assembly_roofline(algorithm, top, top_ms, N, M, W, fp64_peak, peaks):
+    """Roofline of the dominant assembly kernel (algorithmic work per launch
+    over its event-timed launch duration)."""
+    P2 = N * (N - 1)
+    t = top_ms * 1e-3
+    hbm = peaks.get("hbm_gbs")
+    if top.startswith("k_entries") and algorithm == "closed":
+        # reads every a entry of the pair x pair block once, writes A there once
+        byts = 24.0 * P2 * P2
+        return {"kernel": top, "bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": byts / t / 1e9 / hbm if hbm else None, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "algorithmic_bytes_per_launch": byts}
+    if top.startswith("k_entries"):
+        # the pair x pair join terms of Eq. (09), one multiply-add each
+        flops = 2.0 * W * (P2 * P2) / (M * M)
+        return {"kernel": top, "bound": "alu", "achieved": flops / t / 1e12, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": flops / t / 1e12 / fp64_peak, "traffic": None,
+                "peak_source": "FP64 FMA probe lb_probe_fp64 (of measured)",
+                "algorithmic_flops_per_launch": flops}
+    byts = 16.0 * M * M + 8.0 * M * M
+    return {"kernel": top, "bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": byts / t / 1e9 / hbm if hbm else None, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "algorithmic_bytes_per_launch": byts}
+
+
 def run_e2e(args, lb, B, a, H_host, M, nrk, dt, dev, dist, world):
     """Same metric through lb_assemble / lb_integrate with host buffers."""
     import numpy as np
@@ -316,7 +349,7 @@ def run_e2e(args, lb, B, a, H_host, M, nrk, dt, dev, dist, world):
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sysm = lb.System(B, a_np, H=H_host)
+        sysm = lb.System(B, a_np, H=H_host, algorithm=args.algorithm)
         t1 = time.perf_counter()
         sysm.integrate(v0, nrk * dt, dt, precision="fp64", out=out)
         t2 = time.perf_counter()

@@ -156,6 +156,16 @@ int lb_assemble_dense_ex(const lb_basis_t *b, const double *h, const double *a,
                          double *A, double *Q, double *R, double *K, int algorithm,
                          void *stream);
 
+/* The same assembly, with the device time of each of its kernels, measured
+ * with CUDA events on `stream`, written to kernel_ms[0 .. count-1] (count =
+ * lb_assemble_kernel_count(); lb_assemble_kernel_name(i) names kernel i; a
+ * kernel that the requested outputs skip reports ~0).  Synchronous. */
+int lb_assemble_dense_timed(const lb_basis_t *b, const double *h, const double *a,
+                            double *A, double *Q, double *R, double *K, int algorithm,
+                            void *stream, float *kernel_ms);
+int lb_assemble_kernel_count(void);
+const char *lb_assemble_kernel_name(int i);
+
 /* ------------------------------------------------------------------------
  * a6-a8 -- RK4 integration (Table 1 step 3.1; Sec. 4 item 3), with the
  * matrix stored in FP64, FP32, or BF16 with per-row scales.

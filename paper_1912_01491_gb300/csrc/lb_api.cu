@@ -273,6 +273,32 @@ int lb_assemble_dense(const lb_basis_t* b, const double* h, const double* a, dou
   return lb_assemble_dense_ex(b, h, a, A, Q, R, K, LB_ALG_JOIN, stream);
 }
 
+int lb_assemble_kernel_count(void) { return lbi::kAssembleKernels; }
+
+const char* lb_assemble_kernel_name(int i) { return lbi::assemble_kernel_name(i); }
+
+int lb_assemble_dense_timed(const lb_basis_t* b, const double* h, const double* a, double* A, double* Q,
+                            double* R, double* K, int algorithm, void* stream, float* kernel_ms) {
+  LB_REQUIRE(b != nullptr && a != nullptr && kernel_ms != nullptr, "lb_assemble_dense_timed: NULL argument");
+  LB_REQUIRE(A || Q || R || K, "lb_assemble_dense_timed: no output requested");
+  LB_REQUIRE(b->N <= lbi::kMaxDenseN, "lb_assemble_dense_timed: N = %d above %d", b->N, lbi::kMaxDenseN);
+  LB_REQUIRE(algorithm == LB_ALG_JOIN || algorithm == LB_ALG_CLOSED, "lb_assemble_dense_timed: algorithm = %d",
+             algorithm);
+  cudaEvent_t ev[lbi::kAssembleKernels + 1] = {};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i <= lbi::kAssembleKernels && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+  if (e == cudaSuccess)
+    e = lbi::assemble_dense(b->view(), h, reinterpret_cast<const double2*>(a), A, Q, R, K, algorithm, S(stream),
+                            ev);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[lbi::kAssembleKernels]);
+  for (int i = 0; i < lbi::kAssembleKernels && e == cudaSuccess; ++i)
+    e = cudaEventElapsedTime(&kernel_ms[i], ev[i], ev[i + 1]);
+  for (int i = 0; i <= lbi::kAssembleKernels; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  if (e != cudaSuccess) return lbi::cuda_fail(e, "lb_assemble_dense_timed");
+  return LB_OK;
+}
+
 int lb_pack_fp32(int64_t M, const double* A, float* A32, void* stream) {
   LB_REQUIRE(M > 0 && A && A32, "lb_pack_fp32: bad argument");
   LB_TRY_CUDA(lbi::pack_fp32(M, A, A32, S(stream)), "lb_pack_fp32");

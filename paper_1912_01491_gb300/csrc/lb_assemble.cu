@@ -544,6 +544,64 @@ __device__ __forceinline__ double part_p_disjoint(const BasisView& B, const AVie
 }
 
 // Pair-pair block (s, n < 2P); one thread per entry, 256 consecutive n per block.
+// Closed form of part_d_pp.  The D_l (l = 1..N-1) together with 1/sqrt(N)
+// are an orthonormal basis of the diagonal matrices, so
+//   sum_lam delta_x(lam) delta_y(lam) = [x == y] - 1/N,
+// and the two lambda sums of part_d_pp are integer combinations of edge
+// coincidences (the 1/N terms cancel):
+//   sum gs gn = [as=an] - [as=bn] - [bs=an] + [bs=bn],
+//   sum gs hn = [as=an] + [as=bn] - [bs=an] - [bs=bn];
+// both vanish for disjoint edges.
+__device__ __forceinline__ double part_d_pp_closed(const AView& A, int as, int bs, int ts, int an, int bn,
+                                                   int tn, int64_t sb, int64_t n, int64_t nb) {
+  const int e1 = as == an, e2 = as == bn, e3 = bs == an, e4 = bs == bn;
+  const int cf = e1 - e2 - e3 + e4, cd = e1 + e2 - e3 - e4;
+  if (cf == 0 && cd == 0) return 0.0;
+  const double2 a1 = ldA_row(A, nb, sb);
+  const double2 a2 = ldA_row(A, n, sb);
+  const double sgs = ts == kS ? 1.0 : -1.0, sgn = tn == kS ? 1.0 : -1.0;
+  return sgs * (sgn * a1.x * (double)cf - a2.y * (double)cd);
+}
+
+// Closed form of part_p_disjoint.  The term of (v, w, l) and that of
+// (v', w', l') with the matching type of l' read the same entry of a, once
+// as a_jk and once as a_kj = conj(a_jk), with equal contributions, so the
+// eight terms with v = as, doubled, give the sum: 8 reads, 8 adds.
+__device__ __forceinline__ double part_p_disjoint_closed(const BasisView& B, const AView& A, int as, int bs,
+                                                         int ts, int an, int bn, int tn) {
+  const int N = B.N;
+  const int64_t P = B.P;
+  double acc2 = 0.0;
+  const int v = as, vp = bs;
+  const int phs = coef_phase(ts, v, vp);
+#pragma unroll
+  for (int wi = 0; wi < 2; ++wi) {
+    const int w = wi ? bn : an, wp = wi ? an : bn;
+    const int phn = coef_phase(tn, w, wp);
+    const int64_t pk = pair_index_any(N, vp, w), pj = pair_index_any(N, v, wp);
+#pragma unroll
+    for (int tl = 0; tl < 2; ++tl) {
+      const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+      const int phl_wv = coef_phase(tl, w, v), phl_vw = coef_phase(tl, v, w);
+      const int sk = sgn_f(phs + coef_phase(tk, vp, w) + phl_wv);
+      const int sf = sgn_f(phn + coef_phase(tjf, wp, v) + phl_vw);
+      const int sd = sgn_d(phn + coef_phase(tjd, wp, v) + phl_vw);
+      const int64_t k = tk * P + pk, jf = tjf * P + pj, jd = tjd * P + pj;
+      double2 a1, a2;
+      if (wi == 0) {
+        a1 = ldA_row(A, jf, k);
+        a2 = ldA_row(A, jd, k);
+      } else {
+        a1 = ldA(A, jf, k);
+        a2 = ldA(A, jd, k);
+      }
+      acc2 += sgn_mul(sk * sf, a1.x);
+      acc2 -= sgn_mul(sk * sd, a2.y);
+    }
+  }
+  return acc2;  // = 2 * (1/2) * acc2
+}
+
 template <int ALG>
 __global__ void __launch_bounds__(256) k_entries(BasisView B, AView A, const double* __restrict__ h,
                                                  double* __restrict__ Aout, double* __restrict__ Qout,
@@ -556,11 +614,15 @@ __global__ void __launch_bounds__(256) k_entries(BasisView B, AView A, const dou
   const Elem es = decode(B, s), en = decode(B, n);
   double q = 0.0;
   const int as = es.a, bs = es.b, ts = es.kind, an = en.a, bn = en.b, tn = en.kind;
-  double acc = part_d_pp<ALG>(B, A, as, bs, ts, an, bn, tn, partner(B, s), n, partner(B, n));
+  double acc = ALG == LB_ALG_CLOSED
+                   ? part_d_pp_closed(A, as, bs, ts, an, bn, tn, partner(B, s), n, partner(B, n))
+                   : part_d_pp<ALG>(B, A, as, bs, ts, an, bn, tn, partner(B, s), n, partner(B, n));
   int shared = 0, cv = -1;
   if (as == an || as == bn) { ++shared; cv = as; }
   if (bs == an || bs == bn) { ++shared; cv = bs; }
-  if (shared == 0) acc += part_p_disjoint(B, A, as, bs, ts, an, bn, tn);
+  if (shared == 0)
+    acc += ALG == LB_ALG_CLOSED ? part_p_disjoint_closed(B, A, as, bs, ts, an, bn, tn)
+                                : part_p_disjoint(B, A, as, bs, ts, an, bn, tn);
   if (h != nullptr) {
     if (shared == 1) {
       const int p = (as == cv) ? bs : as, qv = (an == cv) ? bn : an;
@@ -1262,64 +1324,93 @@ __global__ void __launch_bounds__(kSameThreads) k_same(BasisView B, AView A, dou
 namespace lbi {
 
 cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double2* a, double* A,
-                           double* Q, double* R, double* K, int algorithm, cudaStream_t st) {
+                           double* Q, double* R, double* K, int algorithm, cudaStream_t st,
+                           cudaEvent_t* ev) {
   AView av{a, B.M};
   const int N = B.N;
   const int64_t P2 = 2 * B.P;
   const int64_t chunks = (P2 + 255) / 256;
   if (P2 * chunks > 0x7fffffffLL || N > kMaxDenseN) return cudaErrorInvalidConfiguration;
-  cudaError_t e;
-  if (A || Q || R) {
-    // pair x pair
-    if (algorithm == LB_ALG_CLOSED)
-      k_entries<LB_ALG_CLOSED><<<(unsigned)(P2 * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
-    else
-      k_entries<LB_ALG_JOIN><<<(unsigned)(P2 * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
-    // pair x diagonal
-    if (algorithm == LB_ALG_CLOSED) {
-      const size_t pd_smem = sizeof(double) * 12 * (size_t)(N + 1);
-      e = cudaFuncSetAttribute(k_pd_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pd_smem);
-      if (e != cudaSuccess) return e;
-      k_pd_closed<<<(unsigned)P2, kRowThreads, pd_smem, st>>>(B, av, h, A, Q, R);
+  const bool closed = algorithm == LB_ALG_CLOSED;
+  cudaError_t e = cudaSuccess;
+  // ev (optional, kAssembleKernels + 1 events): recorded before the first and
+  // after every kernel of the sequence below, launched or not.
+  auto mark = [&](int i) {
+    if (ev && e == cudaSuccess) e = cudaEventRecord(ev[i], st);
+  };
+  mark(0);
+  const bool dense_out = A || Q || R;
+  // 0: pair x pair
+  if (dense_out) {
+    if (closed) k_entries<LB_ALG_CLOSED><<<(unsigned)(P2 * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
+    else k_entries<LB_ALG_JOIN><<<(unsigned)(P2 * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
+    note_launch(1);
+  }
+  mark(1);
+  // 1: pair x diagonal
+  if (dense_out && e == cudaSuccess) {
+    if (closed) {
+      const size_t smem = sizeof(double) * 12 * (size_t)(N + 1);
+      e = cudaFuncSetAttribute(k_pd_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) k_pd_closed<<<(unsigned)P2, kRowThreads, smem, st>>>(B, av, h, A, Q, R);
     } else {
-      const size_t pd_smem = sizeof(double2) * 10 * (size_t)N;
-      e = cudaFuncSetAttribute(k_pd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pd_smem);
-      if (e != cudaSuccess) return e;
-      k_pd<<<(unsigned)P2, kRowThreads, pd_smem, st>>>(B, av, h, A, Q, R);
+      const size_t smem = sizeof(double2) * 10 * (size_t)N;
+      e = cudaFuncSetAttribute(k_pd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) k_pd<<<(unsigned)P2, kRowThreads, smem, st>>>(B, av, h, A, Q, R);
     }
-    // diagonal x pair, diagonal x diagonal
+    note_launch(1);
+  }
+  mark(2);
+  // 2: diagonal x pair
+  if (dense_out && e == cudaSuccess) {
     k_dp<<<(unsigned)((N - 1) * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
+    note_launch(1);
+  }
+  mark(3);
+  // 3: diagonal x diagonal
+  if (dense_out && e == cudaSuccess) {
     const int64_t dd_warps = (int64_t)(N - 1) * (N - 1);
     k_dd<<<(unsigned)((dd_warps * 32 + 255) / 256), 256, 0, st>>>(B, av, A, Q, R);
-    note_launch(4);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    note_launch(1);
   }
-  if (A || R) {
-    if (N >= 3 && algorithm == LB_ALG_CLOSED) {
-      const size_t sh_smem = sizeof(double) * 16 * (size_t)(N + 1);
-      e = cudaFuncSetAttribute(k_shared_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_smem);
-      if (e != cudaSuccess) return e;
-      k_shared_closed<<<(unsigned)(N * (N - 1)), 256, sh_smem, st>>>(B, av, A, R);
-      note_launch(1);
-    } else if (N >= 3) {
-      const size_t sh_smem = sizeof(double2) * 6 * (size_t)N;
-      e = cudaFuncSetAttribute(k_shared, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_smem);
-      if (e != cudaSuccess) return e;
-      k_shared<<<(unsigned)(N * (N - 1)), 256, sh_smem, st>>>(B, av, A, R);
-      note_launch(1);
+  mark(4);
+  // 4: pair x pair on edges sharing one vertex (adds to R / A)
+  if ((A || R) && N >= 3 && e == cudaSuccess) {
+    if (closed) {
+      const size_t smem = sizeof(double) * 16 * (size_t)(N + 1);
+      e = cudaFuncSetAttribute(k_shared_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) k_shared_closed<<<(unsigned)(N * (N - 1)), 256, smem, st>>>(B, av, A, R);
+    } else {
+      const size_t smem = sizeof(double2) * 6 * (size_t)N;
+      e = cudaFuncSetAttribute(k_shared, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) k_shared<<<(unsigned)(N * (N - 1)), 256, smem, st>>>(B, av, A, R);
     }
+    note_launch(1);
+  }
+  mark(5);
+  // 5: pair x pair on the same edge (adds to R / A)
+  if ((A || R) && e == cudaSuccess) {
     k_same<<<(unsigned)B.P, kSameThreads, sizeof(double) * 2 * N, st>>>(B, av, A, R);
     note_launch(1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
   }
-  if (K) {
+  mark(6);
+  // 6: K
+  if (K && e == cudaSuccess) {
     const int64_t warps = B.M;
     k_kvec<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(B, av, K);
     note_launch(1);
   }
+  mark(7);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+const char* assemble_kernel_name(int i) {
+  static const char* names[kAssembleKernels] = {"k_entries (pair x pair)", "k_pd (pair x diagonal)",
+                                                "k_dp (diagonal x pair)", "k_dd (diagonal x diagonal)",
+                                                "k_shared (edges sharing a vertex)", "k_same (same edge)",
+                                                "k_kvec (K)"};
+  return (i >= 0 && i < kAssembleKernels) ? names[i] : nullptr;
 }
 
 cudaError_t join_terms(const lb::BasisView& B, unsigned long long* d_count, cudaStream_t st) {

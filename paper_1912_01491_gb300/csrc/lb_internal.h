@@ -46,8 +46,11 @@ cudaError_t expand(const lb::BasisView& B, const double2* A, double2* coef, cuda
 cudaError_t rho(const lb::BasisView& B, const double* v, double2* out, cudaStream_t st);
 
 // dense assembly (lb_assemble.cu)
+constexpr int kAssembleKernels = 7;
 cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double2* a,
-                           double* A, double* Q, double* R, double* K, int algorithm, cudaStream_t st);
+                           double* A, double* Q, double* R, double* K, int algorithm, cudaStream_t st,
+                           cudaEvent_t* ev = nullptr);
+const char* assemble_kernel_name(int i);
 cudaError_t join_terms(const lb::BasisView& B, unsigned long long* d_count, cudaStream_t st);
 
 // RK4 (lb_rk4.cu)

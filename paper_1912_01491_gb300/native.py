@@ -70,6 +70,10 @@ def load():
         "lb_integrate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double,
                                         ctypes.c_double, _vp]),
         "lb_launch_count": (ctypes.c_longlong, []),
+        "lb_assemble_dense_timed": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp,
+                                                   ctypes.POINTER(ctypes.c_float)]),
+        "lb_assemble_kernel_count": (ctypes.c_int, []),
+        "lb_assemble_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
         "lb_probe_fp64": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
@@ -185,6 +189,15 @@ class Basis:
         _check(load().lb_structure_export(self._h, w, _ptr(idx), _ptr(val), n, ctypes.byref(got),
                                           _stream(stream)))
         return idx[:n], val[:n]
+
+    def assemble_dense_timed(self, a, h=None, A=None, K=None, algorithm="closed", stream=None):
+        """Dense assembly into preallocated A (and K); returns {kernel name: ms}."""
+        lib = load()
+        n = lib.lb_assemble_kernel_count()
+        ms = (ctypes.c_float * n)()
+        _check(lib.lb_assemble_dense_timed(self._h, _ptr(h), _ptr(a), _ptr(A), None, None, _ptr(K),
+                                           ALGORITHMS[algorithm], _stream(stream), ms))
+        return {lib.lb_assemble_kernel_name(i).decode(): float(ms[i]) for i in range(n)}
 
     def join_terms(self):
         W = _c_i64()
