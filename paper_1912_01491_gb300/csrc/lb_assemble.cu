@@ -437,6 +437,15 @@ __device__ __forceinline__ double sgn_mul(int s, double x) {
   return __longlong_as_double(__double_as_longlong(x) ^ ((unsigned long long)(s < 0) << 63));
 }
 
+// -x/2, exactly, by exponent and sign-bit arithmetic for normal x (no FP64
+// instruction); zero, subnormal, inf and nan take the FP64 multiply.
+__device__ __forceinline__ double neg_half(double x) {
+  const long long b = __double_as_longlong(x);
+  const long long ex = (b >> 52) & 0x7ff;
+  if (ex > 1 && ex < 0x7ff) return __longlong_as_double((b - (1LL << 52)) ^ (long long)(1ULL << 63));
+  return -0.5 * x;
+}
+
 __device__ __forceinline__ double warp_sum(double x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
@@ -638,6 +647,114 @@ __global__ void __launch_bounds__(256) k_entries(BasisView B, AView A, const dou
   if (Rout) Rout[o] = r;
   if (Qout) Qout[o] = q;
   if (Aout) Aout[o] = q + r;
+}
+
+// Closed-form pair x pair block, one thread per pair of edges (e(s), e(n))
+// computing the four entries (S/J of e(s)) x (S/J of e(n)): on disjoint
+// edges they are signed sums of the same eight entries of a (two per type
+// pair of the k- and j-edges for each of the two edge pairs (b_s, w), (a_s, w')),
+// read once for all four.  Lanes run over consecutive e(n) of one e(s).
+__global__ void __launch_bounds__(256) k_entries4_closed(BasisView B, AView A, const double* __restrict__ h,
+                                                         double* __restrict__ Aout, double* __restrict__ Qout,
+                                                         double* __restrict__ Rout) {
+  const int N = B.N;
+  const int64_t P = B.P, M = B.M;
+  const int64_t chunks = (P + 255) / 256;
+  const int64_t ps = blockIdx.x / chunks;
+  const int64_t pn = (blockIdx.x % chunks) * 256 + threadIdx.x;
+  if (pn >= P) return;
+  const int32_t abs_ = __ldg(B.pair_ab + ps), abn = __ldg(B.pair_ab + pn);
+  const int as = abs_ >> 16, bs = abs_ & 0xffff, an = abn >> 16, bn = abn & 0xffff;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // combo = ts * 2 + tn
+  int shared = 0, cv = -1;
+  if (as == an || as == bn) { ++shared; cv = as; }
+  if (bs == an || bs == bn) { ++shared; cv = bs; }
+  if (shared == 0) {
+    // For each of the two k/j edge pairs (wi), the (J, J) entry gets the
+    // (S, S) terms times eps_wi and the (J, S) entry the (S, J) terms times
+    // -eps_wi, with eps_0 = -1, eps_1 = +1 for every order of the four
+    // vertices (the same entries of a, conjugated type pairs); so only the
+    // ts = S terms are formed and the J rows follow by sums and differences.
+    const int v = as, vp = bs;
+    double xs[2], xj[2];  // (S,S) and (S,J) partial sums per wi
+#pragma unroll
+    for (int wi = 0; wi < 2; ++wi) {
+      const int w = wi ? bn : an, wp = wi ? an : bn;
+      const int64_t pk = pair_index_any(N, vp, w), pj = pair_index_any(N, v, wp);
+      // X[tj][tk] = a((v,w') tj, (v',w) tk); for wi = 0 the row of k is common to
+      // the warp and the conjugate a[k][j] is read (the sign of Im is flipped below)
+      double xr[2][2], xi[2][2];
+#pragma unroll
+      for (int tj = 0; tj < 2; ++tj)
+#pragma unroll
+        for (int tk = 0; tk < 2; ++tk) {
+          const int64_t j = tj * P + pj, k = tk * P + pk;
+          const double2 t = wi ? ldA(A, j, k) : ldA(A, k, j);
+          xr[tj][tk] = t.x;
+          xi[tj][tk] = t.y;
+        }
+      const int isg = wi ? 1 : -1;  // Im a_jk = isg * xi
+      const int ts = kS;
+      const int phs = coef_phase(ts, v, vp);
+#pragma unroll
+      for (int tn = 0; tn < 2; ++tn) {
+        const int phn = coef_phase(tn, w, wp);
+        double part = 0.0;
+#pragma unroll
+        for (int tl = 0; tl < 2; ++tl) {
+          const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+          const int phl_wv = coef_phase(tl, w, v), phl_vw = coef_phase(tl, v, w);
+          const int sk = sgn_f(phs + coef_phase(tk, vp, w) + phl_wv);
+          const int sf = sgn_f(phn + coef_phase(tjf, wp, v) + phl_vw);
+          const int sd = sgn_d(phn + coef_phase(tjd, wp, v) + phl_vw);
+          part += sgn_mul(sk * sf, xr[tjf][tk]);
+          part -= sgn_mul(sk * sd * isg, xi[tjd][tk]);
+        }
+        if (tn == kS) xs[wi] = part; else xj[wi] = part;
+      }
+    }
+    acc[0] = xs[0] + xs[1];  // (S, S)
+    acc[3] = xs[1] - xs[0];  // (J, J)
+    acc[1] = xj[0] + xj[1];  // (S, J)
+    acc[2] = xj[0] - xj[1];  // (J, S)
+  } else {
+    // edges meet: the D-section part in closed form (the l-pair part is added by
+    // k_shared_closed / k_same)
+    const int e1 = as == an, e2 = as == bn, e3 = bs == an, e4 = bs == bn;
+    const double cf = (double)(e1 - e2 - e3 + e4), cd = (double)(e1 + e2 - e3 - e4);
+#pragma unroll
+    for (int ts = 0; ts < 2; ++ts)
+#pragma unroll
+      for (int tn = 0; tn < 2; ++tn) {
+        const int64_t sb = (int64_t)(1 - ts) * P + ps, n = (int64_t)tn * P + pn, nb = (int64_t)(1 - tn) * P + pn;
+        const double2 a1 = ldA_row(A, nb, sb), a2 = ldA_row(A, n, sb);
+        const double sgs = ts == kS ? 1.0 : -1.0, sgn = tn == kS ? 1.0 : -1.0;
+        acc[ts * 2 + tn] = sgs * (sgn * a1.x * cf - a2.y * cd);
+      }
+  }
+#pragma unroll
+  for (int ts = 0; ts < 2; ++ts)
+#pragma unroll
+    for (int tn = 0; tn < 2; ++tn) {
+      const int64_t s = (int64_t)ts * P + ps, n = (int64_t)tn * P + pn;
+      double q = 0.0;
+      if (h != nullptr && shared != 0) {
+        const Elem es = make_pair(ts, as, bs), en = make_pair(tn, an, bn);
+        if (shared == 1) {
+          const int p = (as == cv) ? bs : as, qv = (an == cv) ? bn : an;
+          const Elem em = make_pair(1 ^ tn ^ ts, p, qv);
+          q = __ldg(h + elem_index(B, em.kind, em.a, em.b)) * f_value(B, em, en, es);
+        } else if (tn != ts) {
+          for (int lam = imax(as, 1); lam <= bs; ++lam)
+            q += __ldg(h + d_index(B, lam)) * f_value(B, make_d(lam), en, es);
+        }
+      }
+      const double r = neg_half(acc[ts * 2 + tn]);
+      const int64_t o = s * M + n;
+      if (Rout) Rout[o] = r;
+      if (Qout) Qout[o] = q;
+      if (Aout) Aout[o] = shared ? q + r : r;  // Q vanishes on disjoint edges
+    }
 }
 
 // Pair row s = (as, bs) type ts, diagonal columns n = D_nu.  One block per
@@ -1001,22 +1118,175 @@ __device__ __forceinline__ double dsum(const BasisView& B, const double* cpre, c
   return s;
 }
 
-__global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, double* __restrict__ Aout,
+// Staged data of one unordered vertex pair {p < q}, and accessors for the
+// orientation (P_, Q_) = (p, q) (tr = 0) or (q, p) (tr = 1).  For (q, p) the
+// staged a[(q,w) tj][(p,w) tk] becomes a[(p,w) tj][(q,w) tk] = conj(a[(q,w) tk][(p,w) tj]).
+struct PairStage {
+  const double* PX;  // [4][L] prefix over w of Re a[(q,w) tj][(p,w) tk], index tj*2+tk
+  const double* PY;  // [4][L] prefix of Im
+  const double* TX;  // [2][L] Re a[D_mu][(p,q) t] (raw, index mu)
+  const double* TY;  // [2][L] Im
+  const double* CX;  // [2][L] prefix of c_mu Re a[D_mu][(p,q) t]
+  const double* CY;  // [2][L] prefix of c_mu Im
+  int L;
+  __device__ __forceinline__ double sre(int tr, int tj, int tk, int lo, int hi) const {
+    return isum(PX + (tr ? tk * 2 + tj : tj * 2 + tk) * L, lo, hi);
+  }
+  __device__ __forceinline__ double sim(int tr, int tj, int tk, int lo, int hi) const {
+    const double x = isum(PY + (tr ? tk * 2 + tj : tj * 2 + tk) * L, lo, hi);
+    return tr ? -x : x;
+  }
+};
+
+// l-pair part of the pair x pair entry s on (v, P_), n on (v, Q_) (edges
+// sharing the vertex v), in closed form; returns -1/2 of the join sum.
+__device__ __forceinline__ double shared_entry_closed(const BasisView& B, const AView& A, const PairStage& S,
+                                                      int tr, int P_, int Q_, int v, int ts, int tn) {
+  const int N = B.N;
+  const int64_t P = B.P;
+  double acc2 = 0.0, accD = 0.0;
+  // (A1): w outside {v, P_, Q_}, in the four intervals between the sorted vertices
+  int b0 = v, b1 = P_, b2 = Q_, tmp;
+  if (b0 > b1) { tmp = b0; b0 = b1; b1 = tmp; }
+  if (b1 > b2) { tmp = b1; b1 = b2; b2 = tmp; }
+  if (b0 > b1) { tmp = b0; b0 = b1; b1 = tmp; }
+  const int ilo[4] = {0, b0 + 1, b1 + 1, b2 + 1}, ihi[4] = {b0 - 1, b1 - 1, b2 - 1, N - 1};
+#pragma unroll
+  for (int iv = 0; iv < 4; ++iv) {
+    if (ilo[iv] > ihi[iv]) continue;
+    const int w = ilo[iv];  // any w of the interval gives the same signs
+#pragma unroll
+    for (int tl = 0; tl < 2; ++tl) {
+      const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+      const int phl = coef_phase(tl, w, v);
+      const int sk = sgn_f(coef_phase(ts, v, P_) + coef_phase(tk, P_, w) + phl);
+      const int base = coef_phase(tn, v, Q_) + phl;
+      const int sf = sgn_f(base + coef_phase(tjf, Q_, w));
+      const int sd = sgn_d(base + coef_phase(tjd, Q_, w));
+      acc2 += sgn_mul(sk * sf, S.sre(tr, tjf, tk, ilo[iv], ihi[iv]));
+      acc2 -= sgn_mul(sk * sd, S.sim(tr, tjd, tk, ilo[iv], ihi[iv]));
+    }
+  }
+  // (A3) e(l) = (v, Q_): k on (P_, Q_), j = D_mu
+  {
+    const int lo = imin(v, Q_), hi = imax(v, Q_);
+    for (int tl = 0; tl < 2; ++tl) {
+      const int tk = 1 ^ tl ^ ts;
+      const int sk = sgn_f(coef_phase(ts, v, P_) + coef_phase(tk, P_, Q_) + coef_phase(tl, Q_, v));
+      double part;
+      if (tl == tn) part = -dsum(B, S.CY + tk * S.L, S.TY + tk * S.L, lo, hi, 1.0, N - 1);
+      else part = (tn == kS ? -1.0 : 1.0) * dsum(B, S.CX + tk * S.L, S.TX + tk * S.L, lo, hi, -1.0, hi);
+      accD += sgn_mul(sk, part) * kInvSqrt2;
+    }
+  }
+  // (B) l = partner(s) on (v, P_): k = D_mu, j on (P_, Q_)
+  {
+    const int lo = imin(v, P_), hi = imax(v, P_), tl = 1 - ts;
+    const int tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+    const int base = coef_phase(tn, v, Q_) + coef_phase(tl, P_, v);
+    const int sf = sgn_f(base + coef_phase(tjf, Q_, P_));
+    const int sd = sgn_d(base + coef_phase(tjd, Q_, P_));
+    double part = sgn_mul(sf, dsum(B, S.CX + tjf * S.L, S.TX + tjf * S.L, lo, hi, -1.0, hi)) +
+                  sgn_mul(sd, dsum(B, S.CY + tjd * S.L, S.TY + tjd * S.L, lo, hi, -1.0, hi));
+    if (ts == kS) part = -part;
+    accD += part * kInvSqrt2;
+  }
+  // (A2) e(l) = (P_, Q_): k on (v, Q_), j on (v, P_)
+  const int64_t pvp = pair_index_any(N, v, P_), pvq = pair_index_any(N, v, Q_);
+#pragma unroll
+  for (int tl = 0; tl < 2; ++tl) {
+    const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+    const int sk = sgn_f(coef_phase(ts, P_, v) + coef_phase(tk, v, Q_) + coef_phase(tl, Q_, P_));
+    const int base = coef_phase(tn, Q_, v) + coef_phase(tl, P_, Q_);
+    const int sf = sgn_f(base + coef_phase(tjf, v, P_));
+    const int sd = sgn_d(base + coef_phase(tjd, v, P_));
+    const int64_t k = tk * P + pvq;
+    const double2 a1 = ldA(A, tjf * P + pvp, k), a2 = ldA(A, tjd * P + pvp, k);
+    acc2 += sgn_mul(sk * sf, a1.x);
+    acc2 -= sgn_mul(sk * sd, a2.y);
+  }
+  return -0.5 * (0.5 * acc2 + accD);
+}
+
+// Diagonal row D_nu, pair column n on {p, q} of type tn, in closed form: the
+// l = (v, w) families for v = p and v = q (k = partner(l), j on (v', w)), the
+// l on e(n) itself (j = D_mu), and Q.  Returns (R entry, Q entry).
+__device__ __forceinline__ void dp_entry_closed(const BasisView& B, const PairStage& S, const double* h, int p,
+                                                int q, int nu, int tn, double& r, double& qout) {
+  const int N = B.N;
+  const int64_t P = B.P;
+  const double cnu = ld_c(B, nu), lcnu = ld_lc(B, nu);
+  double acc2 = 0.0;
+  for (int tr = 0; tr < 2; ++tr) {
+    const int v = tr ? q : p, vp = tr ? p : q;  // shared vertex of l and n, and the other one
+    // staged (for this orientation) a[(vp,w) tj][(v,w) tk], k = partner(l) of type 1 - tl
+    const double dv = dlt(B, v, nu);
+    int b0 = p, b1 = q, b2 = nu, tmp;
+    if (b1 > b2) { tmp = b1; b1 = b2; b2 = tmp; }
+    if (b0 > b1) { tmp = b0; b0 = b1; b1 = tmp; }
+    const int nodes[3] = {b0, b1, b2};
+    auto add = [&](int lo, int hi, double dw) {
+      if (lo > hi) return;
+      const int w = lo;
+      const double g = w < v ? dw - dv : dv - dw;  // delta_x(nu) - delta_y(nu), {x < y} = {v, w}
+      if (g == 0.0) return;
+      for (int tl = 0; tl < 2; ++tl) {
+        const int tjf = 1 ^ tl ^ tn, tjd = tl ^ tn, tkb = 1 - tl;
+        const int phl = coef_phase(tl, w, v);
+        const int phn = coef_phase(tn, v, vp);
+        const int sf = sgn_f(phn + coef_phase(tjf, vp, w) + phl);
+        const int sd = sgn_d(phn + coef_phase(tjd, vp, w) + phl);
+        const double t = sgn_mul(sf, S.sre(tr, tjf, tkb, lo, hi)) - sgn_mul(sd, S.sim(tr, tjd, tkb, lo, hi));
+        acc2 += tl == kS ? -g * t : g * t;  // f(partner(l), l, D_nu) = -+ g
+      }
+    };
+    int prev = 0;
+    for (int i = 0; i < 3; ++i) {
+      const int x = nodes[i];
+      if (x < prev) continue;
+      add(prev, x - 1, (x - 1) < nu ? cnu : 0.0);
+      if (x == nu && x != p && x != q) add(x, x, lcnu);
+      prev = x + 1;
+    }
+    add(prev, N - 1, 0.0);
+  }
+  double acc = acc2 * kInvSqrt2;
+  qout = 0.0;
+  const int lo_n = imax(p, 1);
+  if (nu >= lo_n && nu <= q) {
+    const double gn = dlt(B, p, nu) - dlt(B, q, nu);
+    for (int tl = 0; tl < 2; ++tl) {
+      const double fk = tl == kS ? -gn : gn;  // f(partner(l), l, D_nu), l on e(n)
+      const int tkb = 1 - tl;
+      double t;
+      if (tl == tn) t = -dsum(B, S.CY + tkb * S.L, S.TY + tkb * S.L, p, q, 1.0, N - 1);
+      else t = (tn == kS ? -1.0 : 1.0) * dsum(B, S.CX + tkb * S.L, S.TX + tkb * S.L, p, q, -1.0, q);
+      acc = fma(fk, t, acc);
+    }
+    if (h != nullptr) qout = __ldg(h + (int64_t)(1 - tn) * P + pair_index(N, p, q)) * (tn == kS ? -gn : gn);
+  }
+  r = -0.5 * acc;
+}
+
+// One block per unordered vertex pair {p < q}: the l-pair part of every
+// pair x pair entry on edges (v, p), (v, q) in both orientations, and the
+// diagonal x pair entries of the edge (p, q).
+__global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, const double* __restrict__ h,
+                                                       double* __restrict__ Aout, double* __restrict__ Qout,
                                                        double* __restrict__ Rout) {
   extern __shared__ double sc[];
   const int N = B.N;
   const int64_t P = B.P, M = B.M;
-  const int p = blockIdx.x / (N - 1);
-  int q = blockIdx.x % (N - 1);
-  if (q >= p) ++q;
+  const int32_t ab = __ldg(B.pair_ab + blockIdx.x);
+  const int p = ab >> 16, q = ab & 0xffff;
   const int L = N + 1;
-  double* PX = sc;            // [4][L]  prefix over w of Re a[(q,w) tj][(p,w) tk], index tj*2+tk
-  double* PY = sc + 4 * L;    // [4][L]  prefix of Im
-  double* TX = sc + 8 * L;    // [2][L]  Re a[D_mu][(p,q) t] at mu (raw, index mu)
-  double* TY = sc + 10 * L;   // [2][L]  Im
-  double* CX = sc + 12 * L;   // [2][L]  prefix over mu of c_mu Re a[D_mu][(p,q) t]
-  double* CY = sc + 14 * L;   // [2][L]  prefix of c_mu Im
-  const int64_t ppq = pair_index_any(N, p, q);
+  double* PX = sc;
+  double* PY = sc + 4 * L;
+  double* TX = sc + 8 * L;
+  double* TY = sc + 10 * L;
+  double* CX = sc + 12 * L;
+  double* CY = sc + 14 * L;
+  const int64_t ppq = blockIdx.x;
   for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
     const int w = t >> 2, jk = t & 3, tj = jk >> 1, tk = jk & 1;
     double2 val = make_double2(0.0, 0.0);
@@ -1046,75 +1316,29 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, dou
     scan_inplace(arr, N);
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
-    const int v = t >> 2, combo = t & 3;
-    if (v == p || v == q) continue;
-    const int ts = combo >> 1, tn = combo & 1;
-    double acc2 = 0.0, accD = 0.0;
-    // (A1): w outside {v, p, q}, in the four intervals between the sorted vertices
-    int b0 = v, b1 = p, b2 = q, tmp;
-    if (b0 > b1) { tmp = b0; b0 = b1; b1 = tmp; }
-    if (b1 > b2) { tmp = b1; b1 = b2; b2 = tmp; }
-    if (b0 > b1) { tmp = b0; b0 = b1; b1 = tmp; }
-    const int ilo[4] = {0, b0 + 1, b1 + 1, b2 + 1}, ihi[4] = {b0 - 1, b1 - 1, b2 - 1, N - 1};
-#pragma unroll
-    for (int iv = 0; iv < 4; ++iv) {
-      if (ilo[iv] > ihi[iv]) continue;
-      const int w = ilo[iv];  // any w of the interval gives the same signs
-#pragma unroll
-      for (int tl = 0; tl < 2; ++tl) {
-        const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
-        const int phl = coef_phase(tl, w, v);
-        const int sk = sgn_f(coef_phase(ts, v, p) + coef_phase(tk, p, w) + phl);
-        const int base = coef_phase(tn, v, q) + phl;
-        const int sf = sgn_f(base + coef_phase(tjf, q, w));
-        const int sd = sgn_d(base + coef_phase(tjd, q, w));
-        acc2 += sgn_mul(sk * sf, isum(PX + (tjf * 2 + tk) * L, ilo[iv], ihi[iv]));
-        acc2 -= sgn_mul(sk * sd, isum(PY + (tjd * 2 + tk) * L, ilo[iv], ihi[iv]));
-      }
+  const PairStage S{PX, PY, TX, TY, CX, CY, L};
+  // pair x pair, edges sharing a vertex: 2 orientations x N vertices v x 4 type pairs
+  if (Aout || Rout) {
+    for (int t = threadIdx.x; t < 8 * N; t += blockDim.x) {
+      const int tr = t / (4 * N), v = (t >> 2) % N, combo = t & 3;
+      if (v == p || v == q) continue;
+      const int ts = combo >> 1, tn = combo & 1;
+      const int P_ = tr ? q : p, Q_ = tr ? p : q;
+      const double r = shared_entry_closed(B, A, S, tr, P_, Q_, v, ts, tn);
+      const int64_t o = (ts * P + pair_index_any(N, v, P_)) * M + (tn * P + pair_index_any(N, v, Q_));
+      if (Rout) Rout[o] += r;
+      if (Aout) Aout[o] += r;
     }
-    // (A3) e(l) = (v, q): k on (p, q), j = D_mu
-    {
-      const int lo = imin(v, q), hi = imax(v, q);
-      for (int tl = 0; tl < 2; ++tl) {
-        const int tk = 1 ^ tl ^ ts;
-        const int sk = sgn_f(coef_phase(ts, v, p) + coef_phase(tk, p, q) + coef_phase(tl, q, v));
-        double part;
-        if (tl == tn) part = -dsum(B, CY + tk * L, TY + tk * L, lo, hi, 1.0, N - 1);
-        else part = (tn == kS ? -1.0 : 1.0) * dsum(B, CX + tk * L, TX + tk * L, lo, hi, -1.0, hi);
-        accD += sgn_mul(sk, part) * kInvSqrt2;
-      }
-    }
-    // (B) l = partner(s) on (v, p): k = D_mu, j on (p, q)
-    {
-      const int lo = imin(v, p), hi = imax(v, p), tl = 1 - ts;
-      const int tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
-      const int base = coef_phase(tn, v, q) + coef_phase(tl, p, v);
-      const int sf = sgn_f(base + coef_phase(tjf, q, p));
-      const int sd = sgn_d(base + coef_phase(tjd, q, p));
-      double part = sgn_mul(sf, dsum(B, CX + tjf * L, TX + tjf * L, lo, hi, -1.0, hi)) +
-                    sgn_mul(sd, dsum(B, CY + tjd * L, TY + tjd * L, lo, hi, -1.0, hi));
-      if (ts == kS) part = -part;
-      accD += part * kInvSqrt2;
-    }
-    // (A2) e(l) = (p, q): k on (v, q), j on (v, p)
-    const int64_t pvp = pair_index_any(N, v, p), pvq = pair_index_any(N, v, q);
-#pragma unroll
-    for (int tl = 0; tl < 2; ++tl) {
-      const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
-      const int sk = sgn_f(coef_phase(ts, p, v) + coef_phase(tk, v, q) + coef_phase(tl, q, p));
-      const int base = coef_phase(tn, q, v) + coef_phase(tl, p, q);
-      const int sf = sgn_f(base + coef_phase(tjf, v, p));
-      const int sd = sgn_d(base + coef_phase(tjd, v, p));
-      const int64_t k = tk * P + pvq;
-      const double2 a1 = ldA(A, tjf * P + pvp, k), a2 = ldA(A, tjd * P + pvp, k);
-      acc2 += sgn_mul(sk * sf, a1.x);
-      acc2 -= sgn_mul(sk * sd, a2.y);
-    }
-    const double r = -0.5 * (0.5 * acc2 + accD);
-    const int64_t o = (ts * P + pvp) * M + (tn * P + pvq);
-    if (Rout) Rout[o] += r;
-    if (Aout) Aout[o] += r;
+  }
+  // diagonal x pair
+  for (int t = threadIdx.x; t < 2 * (N - 1); t += blockDim.x) {
+    const int nu = 1 + (t >> 1), tn = t & 1;
+    double r, qv;
+    dp_entry_closed(B, S, h, p, q, nu, tn, r, qv);
+    const int64_t o = d_index(B, nu) * M + (tn * P + ppq);
+    if (Rout) Rout[o] = r;
+    if (Qout) Qout[o] = qv;
+    if (Aout) Aout[o] = qv + r;
   }
 }
 
@@ -1340,10 +1564,14 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
   };
   mark(0);
   const bool dense_out = A || Q || R;
-  // 0: pair x pair
+  // 0: pair x pair (closed: four type pairs per thread)
   if (dense_out) {
-    if (closed) k_entries<LB_ALG_CLOSED><<<(unsigned)(P2 * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
-    else k_entries<LB_ALG_JOIN><<<(unsigned)(P2 * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
+    if (closed) {
+      const int64_t pc = (B.P + 255) / 256;
+      k_entries4_closed<<<(unsigned)(B.P * pc), 256, 0, st>>>(B, av, h, A, Q, R);
+    } else {
+      k_entries<LB_ALG_JOIN><<<(unsigned)(P2 * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
+    }
     note_launch(1);
   }
   mark(1);
@@ -1361,8 +1589,8 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
     note_launch(1);
   }
   mark(2);
-  // 2: diagonal x pair
-  if (dense_out && e == cudaSuccess) {
+  // 2: diagonal x pair (closed: produced by k_shared_closed below)
+  if (dense_out && !closed && e == cudaSuccess) {
     k_dp<<<(unsigned)((N - 1) * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
     note_launch(1);
   }
@@ -1374,17 +1602,17 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
     note_launch(1);
   }
   mark(4);
-  // 4: pair x pair on edges sharing one vertex (adds to R / A)
-  if ((A || R) && N >= 3 && e == cudaSuccess) {
-    if (closed) {
-      const size_t smem = sizeof(double) * 16 * (size_t)(N + 1);
-      e = cudaFuncSetAttribute(k_shared_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_shared_closed<<<(unsigned)(N * (N - 1)), 256, smem, st>>>(B, av, A, R);
-    } else {
-      const size_t smem = sizeof(double2) * 6 * (size_t)N;
-      e = cudaFuncSetAttribute(k_shared, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_shared<<<(unsigned)(N * (N - 1)), 256, smem, st>>>(B, av, A, R);
-    }
+  // 4: pair x pair on edges sharing one vertex (adds to R / A); closed: one
+  //    block per vertex pair, which also writes the diagonal x pair entries
+  if (dense_out && closed && e == cudaSuccess) {
+    const size_t smem = sizeof(double) * 16 * (size_t)(N + 1);
+    e = cudaFuncSetAttribute(k_shared_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_shared_closed<<<(unsigned)B.P, 256, smem, st>>>(B, av, h, A, Q, R);
+    note_launch(1);
+  } else if ((A || R) && N >= 3 && e == cudaSuccess) {
+    const size_t smem = sizeof(double2) * 6 * (size_t)N;
+    e = cudaFuncSetAttribute(k_shared, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_shared<<<(unsigned)(N * (N - 1)), 256, smem, st>>>(B, av, A, R);
     note_launch(1);
   }
   mark(5);
@@ -1408,8 +1636,8 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
 const char* assemble_kernel_name(int i) {
   static const char* names[kAssembleKernels] = {"k_entries (pair x pair)", "k_pd (pair x diagonal)",
                                                 "k_dp (diagonal x pair)", "k_dd (diagonal x diagonal)",
-                                                "k_shared (edges sharing a vertex)", "k_same (same edge)",
-                                                "k_kvec (K)"};
+                                                "k_shared (edges sharing a vertex; closed: + diagonal x pair)",
+                                                "k_same (same edge)", "k_kvec (K)"};
   return (i >= 0 && i < kAssembleKernels) ? names[i] : nullptr;
 }
 
