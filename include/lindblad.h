@@ -197,6 +197,53 @@ int lb_rk4_dense(int64_t M, int precision, const void *Ap, const float *row_scal
                  void *work, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Sparse models (Sec. 3: sparse H and a Kossakowski matrix of few channels,
+ * P = 1 for the paper's sparse model): CSR assembly of A = Q + R and K, and
+ * RK4 on CSR.
+ * --------------------------------------------------------------------- */
+
+typedef struct lb_csr lb_csr_t;
+
+/* Assemble A = Q + R (CSR) and K for a_jk = sum_p gamma_p l_pj conj(l_pk).
+ *   h      : M real Hamiltonian coefficients (device), or NULL (H = 0); its
+ *            zero entries are skipped, so a sparse H costs O(nnz).
+ *   nP     : number of channels p; gamma: nP rates (host)
+ *   lp_ptr : nP + 1 offsets (host, lp_ptr[0] = 0) into lp_idx / lp_val
+ *   lp_idx : basis indices of the nonzero l_pj (device int64)
+ *   lp_val : the values l_pj (device, complex interleaved), e.g. from lb_expand
+ * Eq. (09) is evaluated per channel as r_sn = -1/2 gamma_p Re sum_l W_ls U_ln,
+ * U_ln = sum_j l_j z_jln, W_ls = sum_k conj(l_k) f_kls (a sparse product).
+ * Pattern: an entry is stored iff |A_sn| exceeds 1e-12 times the sum of the
+ * magnitudes of its terms (exact cancellations leave rounding residue only);
+ * columns are sorted within rows.  *out owns the device arrays (see
+ * lb_csr_arrays); release with lb_csr_destroy.  Synchronous w.r.t. stream.
+ * LB_ENOMEM when the intermediate coordinate lists do not fit. */
+int lb_assemble_lowrank_csr(const lb_basis_t *b, const double *h, int nP, const double *gamma,
+                            const int64_t *lp_ptr, const int64_t *lp_idx, const double *lp_val,
+                            lb_csr_t **out, void *stream);
+
+/* M, stored entries, and the number of summed terms (R products + Q terms). */
+int lb_csr_info(const lb_csr_t *c, int64_t *M, int64_t *nnz, int64_t *terms);
+
+/* Device arrays owned by the handle: rowptr (M+1 int64), col (nnz int32),
+ * val (nnz doubles), K (M doubles).  Valid until lb_csr_destroy. */
+int lb_csr_arrays(const lb_csr_t *c, const int64_t **rowptr, const int32_t **col,
+                  const double **val, const double **K);
+int lb_csr_destroy(lb_csr_t *c);
+
+/* Copy the CSR arrays (and K) into caller buffers, host or device (any
+ * pointer may be NULL to skip it).  Synchronous with respect to stream. */
+int lb_csr_copy(const lb_csr_t *c, int64_t *rowptr, int32_t *col, double *val, double *K, void *stream);
+
+/* RK4 on the CSR system (same stage structure as lb_rk4_dense): precision
+ * LB_FP64, or LB_FP32 values (converted once and cached in the handle) with
+ * FP32 products and, if correct_every > 0, the FP64 defect
+ * (A64 - A32) v added to K every correct_every steps.  v (device, M doubles)
+ * in/out; work: lb_rk4_workspace_bytes(M) bytes of device memory. */
+int lb_rk4_csr(const lb_csr_t *c, int precision, int correct_every, double *v, double dt,
+               int64_t nsteps, void *work, void *stream);
+
+/* ------------------------------------------------------------------------
  * Host-buffer interface (one call per paper step, inputs and outputs in
  * host memory, copies included).  The assembled system stays on the device
  * inside an lb_system_t.

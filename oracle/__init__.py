@@ -15,5 +15,6 @@ Three independent routes to the same numbers (Meyerov et al., Sec. 2):
   (``lb_oracle.c``), with f and d obtained by multiplying sparse basis
   matrices (not by closed-form rules).  Plus classical RK4.
 """
-from .core import Oracle, load_library, build_library, rk4_dense, rk4_csr, num_threads, set_threads  # noqa: F401
+from .core import (Oracle, build_library, load_library, lowrank_csr, num_threads, rk4_csr,  # noqa: F401
+                   rk4_dense, set_threads)
 from . import brute, superop  # noqa: F401

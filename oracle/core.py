@@ -68,6 +68,11 @@ def load_library():
         lib.ora_R_entries_rows.argtypes = [ctypes.c_void_p, _i64, _i64p, _dp, _i64, _i64p, _i64p, _dp, _dp]
         lib.ora_R_lowrank.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _i64p, _i64p,
                                       _dp, _dp, _dp, _u8p]
+        lib.ora_lowrank_csr.restype = _i64
+        lib.ora_lowrank_csr.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, _dp, _i64p, _i64p, _dp, _dp,
+                                        ctypes.POINTER(_i64p), ctypes.POINTER(_i32p), ctypes.POINTER(_dp),
+                                        ctypes.POINTER(_dp), _dp]
+        lib.ora_free.argtypes = [ctypes.c_void_p]
         lib.ora_rk4_dense.argtypes = [_i64, _dp, _dp, _dp, ctypes.c_double, _i64, _i64, _dp, _dp]
         lib.ora_rk4_csr.argtypes = [_i64, _i64p, _i32p, _dp, _dp, _dp, ctypes.c_double, _i64, _dp]
         lib.ora_num_threads.restype = ctypes.c_int
@@ -276,6 +281,37 @@ class Oracle:
         self.lib.ora_R_lowrank(self._ctx, nP, _p(g), _p(ptr, _i64p), _p(idx, _i64p),
                                _p(re), _p(im), _p(R), _p(mask, _u8p))
         return R, mask.astype(bool)
+
+
+def _channels(lps, gammas):
+    ptr = np.zeros(len(gammas) + 1, np.int64)
+    for p, (idx, _) in enumerate(lps):
+        ptr[p + 1] = ptr[p] + len(idx)
+    idx = np.ascontiguousarray(np.concatenate([np.asarray(i, np.int64) for i, _ in lps]))
+    co = np.concatenate([np.asarray(c, np.complex128) for _, c in lps])
+    return ptr, idx, np.ascontiguousarray(co.real), np.ascontiguousarray(co.imag), \
+        np.ascontiguousarray(gammas, np.float64)
+
+
+def lowrank_csr(o, h, gammas, lps, with_mag=False):
+    """Sparse generator A = Q + R (CSR; entries nonzero beyond rounding) and K
+    for a Kossakowski matrix sum_p gamma_p l_p l_p^dagger.
+    Returns (rowptr, col, val, K) [+ mag, the summed magnitudes of each entry's terms]."""
+    lib = o.lib
+    ptr, idx, re, im, g = _channels(lps, gammas)
+    h = None if h is None else np.ascontiguousarray(np.real(h), np.float64)
+    rp, cp, vp, mp = _i64p(), _i32p(), _dp(), _dp()
+    K = np.zeros(o.M)
+    nnz = lib.ora_lowrank_csr(o._ctx, _p(h) if h is not None else None, len(gammas), _p(g), _p(ptr, _i64p),
+                              _p(idx, _i64p), _p(re), _p(im), ctypes.byref(rp), ctypes.byref(cp),
+                              ctypes.byref(vp), ctypes.byref(mp), _p(K))
+    rowptr = np.ctypeslib.as_array(rp, shape=(o.M + 1,)).copy()
+    col = np.ctypeslib.as_array(cp, shape=(max(nnz, 1),))[:nnz].copy()
+    val = np.ctypeslib.as_array(vp, shape=(max(nnz, 1),))[:nnz].copy()
+    mag = np.ctypeslib.as_array(mp, shape=(max(nnz, 1),))[:nnz].copy()
+    for ptr_ in (rp, cp, vp, mp):
+        lib.ora_free(ctypes.cast(ptr_, ctypes.c_void_p))
+    return (rowptr, col, val, K, mag) if with_mag else (rowptr, col, val, K)
 
 
 def rk4_dense(A, K, v0, dt, nsteps, snap_every=0):

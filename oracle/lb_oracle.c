@@ -822,6 +822,199 @@ void ora_R_lowrank(const ora_ctx *c, int nP, const double *gamma,
     free_sections(&S);
 }
 
+/* ---------------------------------------------- sparse (CSR) assembly */
+
+/* open-addressing map (s*M + n) -> value, for the sparse generator */
+typedef struct { int64_t cap, n; int64_t *key; double *val, *abs; } hmap;
+
+static void hm_init(hmap *h, int64_t cap) {
+    int64_t c = 1024;
+    while (c < 2 * cap) c <<= 1;
+    h->cap = c; h->n = 0;
+    h->key = (int64_t *)malloc(sizeof(int64_t) * (size_t)c);
+    h->val = (double *)calloc((size_t)c, sizeof(double));
+    h->abs = (double *)calloc((size_t)c, sizeof(double));
+    for (int64_t i = 0; i < c; ++i) h->key[i] = -1;
+}
+
+static void hm_add(hmap *h, int64_t key, double v, double a);
+
+static void hm_grow(hmap *h) {
+    hmap g;
+    hm_init(&g, h->cap);
+    for (int64_t i = 0; i < h->cap; ++i)
+        if (h->key[i] >= 0) hm_add(&g, h->key[i], h->val[i], h->abs[i]);
+    free(h->key); free(h->val); free(h->abs);
+    *h = g;
+}
+
+/* value v with its absolute size a (for the entry's scale) */
+static void hm_add(hmap *h, int64_t key, double v, double a) {
+    if (2 * (h->n + 1) > h->cap) hm_grow(h);
+    uint64_t x = (uint64_t)key * 0x9E3779B97F4A7C15ULL;
+    int64_t i = (int64_t)(x >> 11) & (h->cap - 1);
+    while (h->key[i] >= 0 && h->key[i] != key) i = (i + 1) & (h->cap - 1);
+    if (h->key[i] < 0) { h->key[i] = key; h->n++; }
+    h->val[i] += v;
+    h->abs[i] += a;
+}
+
+static int cmp_i64(const void *a, const void *b) {
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* Lists keyed by the FIRST index: Ff(k) = {(l, s, f_kls)}, Zf(j) = {(l, n, z_jln)}. */
+typedef struct {
+    int64_t *fptr, *zptr;
+    int32_t *fl, *fs; double *fv;
+    int32_t *zl, *zn; double *zr, *zi;
+} firsts;
+
+static void build_firsts(const ora_ctx *c, firsts *F) {
+    int64_t M = c->M, nf = c->nf, nz = c->nf + c->nd;
+    F->fptr = (int64_t *)calloc((size_t)M + 1, sizeof(int64_t));
+    F->zptr = (int64_t *)calloc((size_t)M + 1, sizeof(int64_t));
+    /* order the items by (first, middle) */
+    int64_t *kf = (int64_t *)malloc(sizeof(int64_t) * (size_t)nf), *of = (int64_t *)malloc(sizeof(int64_t) * (size_t)nf);
+    for (int64_t r = 0; r < nf; ++r) { kf[r] = (int64_t)c->f_idx[3 * r] * M + c->f_idx[3 * r + 1]; of[r] = r; }
+    g_key = kf; qsort(of, (size_t)nf, sizeof(int64_t), cmp_key);
+    int64_t *kz = (int64_t *)malloc(sizeof(int64_t) * (size_t)nz), *oz = (int64_t *)malloc(sizeof(int64_t) * (size_t)nz);
+    for (int64_t r = 0; r < nz; ++r) {
+        const int32_t *x = r < nf ? &c->f_idx[3 * r] : &c->d_idx[3 * (r - nf)];
+        kz[r] = (int64_t)x[0] * M + x[1]; oz[r] = r;
+    }
+    g_key = kz; qsort(oz, (size_t)nz, sizeof(int64_t), cmp_key);
+    F->fl = (int32_t *)malloc(sizeof(int32_t) * (size_t)nf); F->fs = (int32_t *)malloc(sizeof(int32_t) * (size_t)nf);
+    F->fv = (double *)malloc(sizeof(double) * (size_t)nf);
+    F->zl = (int32_t *)malloc(sizeof(int32_t) * (size_t)nz); F->zn = (int32_t *)malloc(sizeof(int32_t) * (size_t)nz);
+    F->zr = (double *)malloc(sizeof(double) * (size_t)nz); F->zi = (double *)malloc(sizeof(double) * (size_t)nz);
+    for (int64_t q = 0; q < nf; ++q) {
+        const int32_t *x = &c->f_idx[3 * of[q]];
+        F->fl[q] = x[1]; F->fs[q] = x[2]; F->fv[q] = c->f_val[of[q]];
+        F->fptr[x[0] + 1]++;
+    }
+    for (int64_t q = 0; q < nz; ++q) {
+        int64_t r = oz[q];
+        const int32_t *x = r < nf ? &c->f_idx[3 * r] : &c->d_idx[3 * (r - nf)];
+        F->zl[q] = x[1]; F->zn[q] = x[2];
+        F->zr[q] = r < nf ? c->f_val[r] : 0.0;
+        F->zi[q] = r < nf ? 0.0 : c->d_val[r - nf];
+        F->zptr[x[0] + 1]++;
+    }
+    for (int64_t i = 0; i < M; ++i) { F->fptr[i + 1] += F->fptr[i]; F->zptr[i + 1] += F->zptr[i]; }
+    free(kf); free(of); free(kz); free(oz);
+}
+
+static void free_firsts(firsts *F) {
+    free(F->fptr); free(F->zptr); free(F->fl); free(F->fs); free(F->fv);
+    free(F->zl); free(F->zn); free(F->zr); free(F->zi);
+}
+
+/*
+ * The generator for a Kossakowski matrix in spectral form,
+ * a_jk = sum_p gamma_p l_pj conj(l_pk) (sparse l_p), and sparse real h, as a
+ * CSR matrix A = Q + R.  Terms: h_m f_mns with h_m != 0 (Eq. (07)) and
+ * a_jk z_jln f_kls, a_jk conj(z_kln) f_jls with (j, k) in the support of some
+ * l_p (Eq. (09), two-term form, prefactor -1/4).  Pattern: the (s, n) whose
+ * summed value exceeds 1e-12 times the sum of its terms' magnitudes --
+ * entries whose terms cancel exactly (most of the ones the terms reach, for
+ * ladder-type models) are dropped, genuine nonzeros kept.
+ * Also K (Eq. (08)), dense.  The Eq. (09) sums run over the nonzero a_jk,
+ * joining the first-index lists of j and k on the middle index l.
+ * Arrays are malloc'ed; release with ora_free.
+ */
+int64_t ora_lowrank_csr(const ora_ctx *c, const double *h, int nP, const double *gamma,
+                        const int64_t *lp_ptr, const int64_t *lp_idx, const double *lp_re,
+                        const double *lp_im, int64_t **rowptr_out, int32_t **col_out,
+                        double **val_out, double **mag_out, double *K) {
+    int64_t M = c->M;
+    firsts F;
+    build_firsts(c, &F);
+    hmap hm;
+    hm_init(&hm, 16 * M);
+    /* Q */
+    if (h)
+        for (int64_t m = 0; m < M; ++m) {
+            if (h[m] == 0.0) continue;
+            for (int64_t q = F.fptr[m]; q < F.fptr[m + 1]; ++q)
+                hm_add(&hm, (int64_t)F.fs[q] * M + F.fl[q], h[m] * F.fv[q], fabs(h[m] * F.fv[q]));  /* f_{m n s}: n = l, s */
+        }
+    /* the union of the channel supports, and a_jk on it */
+    memset(K, 0, sizeof(double) * (size_t)M);
+    double *Ki = (double *)calloc((size_t)M, sizeof(double));
+    for (int p = 0; p < nP; ++p)
+        for (int64_t u = lp_ptr[p]; u < lp_ptr[p + 1]; ++u)
+            for (int64_t w = lp_ptr[p]; w < lp_ptr[p + 1]; ++w) {
+                int64_t j = lp_idx[u], k = lp_idx[w];
+                double ar = gamma[p] * (lp_re[u] * lp_re[w] + lp_im[u] * lp_im[w]);
+                double ai = gamma[p] * (lp_im[u] * lp_re[w] - lp_re[u] * lp_im[w]);
+                /* term 1: a_jk z_jln f_kls; term 2 of the pair (k, j) is added when
+                 * the loop reaches (k, j): a_kj conj(z_jln) f_kls, i.e. the printed
+                 * a_jk conj(z_kln) f_jls with the names exchanged */
+                int64_t zq = F.zptr[j], ze = F.zptr[j + 1], fq = F.fptr[k], fe = F.fptr[k + 1];
+                /* merge-join on l (both lists sorted by l) */
+                while (zq < ze && fq < fe) {
+                    int32_t lz = F.zl[zq], lf = F.fl[fq];
+                    if (lz < lf) { zq++; continue; }
+                    if (lf < lz) { fq++; continue; }
+                    int64_t z0 = zq, f0 = fq;
+                    while (zq < ze && F.zl[zq] == lz) zq++;
+                    while (fq < fe && F.fl[fq] == lz) fq++;
+                    for (int64_t a = z0; a < zq; ++a)
+                        for (int64_t b = f0; b < fq; ++b) {
+                            double zr = F.zr[a], zi = F.zi[a], fv = F.fv[b];
+                            int64_t key = (int64_t)F.fs[b] * M + F.zn[a];
+                            /* a_jk z f */
+                            double t1 = (ar * zr - ai * zi) * fv;
+                            /* the second printed term, written for the pair (j', k') = (k, j):
+                             * a_{k j} conj(z_{j l n}) f_{k l s} -- a_kj = conj(a_jk) */
+                            double t2 = (ar * zr - ai * zi) * fv;
+                            double mag = sqrt(ar * ar + ai * ai) * sqrt(zr * zr + zi * zi) * fabs(fv);
+                            hm_add(&hm, key, -0.25 * (t1 + t2), 0.5 * mag);
+                        }
+                }
+                /* Eq. (08): (i/N) a_jk f_jks */
+                for (int64_t b = F.fptr[j]; b < F.fptr[j + 1]; ++b)
+                    if (F.fl[b] == k) {
+                        K[F.fs[b]] += -ai * F.fv[b] / c->N;
+                        Ki[F.fs[b]] += ar * F.fv[b] / c->N;
+                    }
+            }
+    free(Ki);
+    /* to CSR, columns sorted; an entry is kept iff its value is not below
+     * 1e-12 of the sum of the magnitudes of its terms (terms that cancel
+     * exactly leave rounding residue only) */
+    int64_t nnz = 0, t = 0;
+    for (int64_t i = 0; i < hm.cap; ++i)
+        if (hm.key[i] >= 0 && fabs(hm.val[i]) > 1e-12 * hm.abs[i]) nnz++;
+    int64_t *keys = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz + 1));
+    for (int64_t i = 0; i < hm.cap; ++i)
+        if (hm.key[i] >= 0 && fabs(hm.val[i]) > 1e-12 * hm.abs[i]) keys[t++] = hm.key[i];
+    qsort(keys, (size_t)nnz, sizeof(int64_t), cmp_i64);
+    int64_t *rowptr = (int64_t *)calloc((size_t)M + 1, sizeof(int64_t));
+    int32_t *col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz + 1));
+    double *val = (double *)malloc(sizeof(double) * (size_t)(nnz + 1));
+    double *mag = (double *)malloc(sizeof(double) * (size_t)(nnz + 1));
+    for (int64_t e = 0; e < nnz; ++e) {
+        int64_t key = keys[e];
+        uint64_t x = (uint64_t)key * 0x9E3779B97F4A7C15ULL;
+        int64_t i = (int64_t)(x >> 11) & (hm.cap - 1);
+        while (hm.key[i] != key) i = (i + 1) & (hm.cap - 1);
+        rowptr[key / M + 1]++;
+        col[e] = (int32_t)(key % M);
+        val[e] = hm.val[i];
+        mag[e] = hm.abs[i];
+    }
+    for (int64_t s = 0; s < M; ++s) rowptr[s + 1] += rowptr[s];
+    free(keys); free(hm.key); free(hm.val); free(hm.abs);
+    free_firsts(&F);
+    *rowptr_out = rowptr; *col_out = col; *val_out = val; *mag_out = mag;
+    return nnz;
+}
+
+void ora_free(void *p) { free(p); }
+
 /* -------------------------------------------------------------- RK4 */
 
 /* y = A x + K (dense, row-major M x M) */

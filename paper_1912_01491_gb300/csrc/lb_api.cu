@@ -329,6 +329,112 @@ int lb_rk4_dense(int64_t M, int precision, const void* Ap, const float* row_scal
   return LB_OK;
 }
 
+// ------------------------------------------------------------------ sparse
+
+}  // extern "C"
+
+struct lb_csr {
+  lbi::CsrOut m;
+  float* val32 = nullptr;
+};
+
+extern "C" {
+
+int lb_assemble_lowrank_csr(const lb_basis_t* b, const double* h, int nP, const double* gamma,
+                            const int64_t* lp_ptr, const int64_t* lp_idx, const double* lp_val, lb_csr_t** out,
+                            void* stream) {
+  LB_REQUIRE(b && out && (nP == 0 || (gamma && lp_ptr)), "lb_assemble_lowrank_csr: NULL argument");
+  LB_REQUIRE(nP >= 0 && nP <= 4096, "lb_assemble_lowrank_csr: nP = %d", nP);
+  LB_REQUIRE(b->M <= 0x7fffffffLL, "lb_assemble_lowrank_csr: M too large for int32 columns");
+  LB_REQUIRE(lp_ptr == nullptr || lp_ptr[0] == 0, "lb_assemble_lowrank_csr: lp_ptr[0] must be 0");
+  for (int p = 0; p < nP; ++p) {
+    LB_REQUIRE(lp_ptr[p + 1] >= lp_ptr[p], "lb_assemble_lowrank_csr: lp_ptr not monotone");
+    LB_REQUIRE(std::isfinite(gamma[p]), "lb_assemble_lowrank_csr: gamma[%d] not finite", p);
+  }
+  LB_REQUIRE(nP == 0 || lp_ptr[nP] == 0 || (lp_idx && lp_val), "lb_assemble_lowrank_csr: NULL channel arrays");
+  LB_REQUIRE((double)nP * (double)b->M * (double)b->M < 9.0e18, "lb_assemble_lowrank_csr: key range overflow");
+  *out = nullptr;
+  lb_csr* c = new lb_csr;
+  static const int64_t zero_ptr[1] = {0};
+  cudaError_t e = lbi::assemble_lowrank_csr(b->view(), h, nP, gamma, nP ? lp_ptr : zero_ptr, lp_idx,
+                                            reinterpret_cast<const double2*>(lp_val), &c->m, S(stream));
+  if (e != cudaSuccess) {
+    delete c;
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      lbi::set_error("lb_assemble_lowrank_csr: device memory exhausted");
+      return LB_ENOMEM;
+    }
+    return lbi::cuda_fail(e, "lb_assemble_lowrank_csr");
+  }
+  *out = c;
+  return LB_OK;
+}
+
+int lb_csr_info(const lb_csr_t* c, int64_t* M, int64_t* nnz, int64_t* terms) {
+  LB_REQUIRE(c != nullptr, "lb_csr_info: NULL handle");
+  if (M) *M = c->m.M;
+  if (nnz) *nnz = c->m.nnz;
+  if (terms) *terms = c->m.terms;
+  return LB_OK;
+}
+
+int lb_csr_arrays(const lb_csr_t* c, const int64_t** rowptr, const int32_t** col, const double** val,
+                  const double** K) {
+  LB_REQUIRE(c != nullptr, "lb_csr_arrays: NULL handle");
+  if (rowptr) *rowptr = c->m.rowptr;
+  if (col) *col = c->m.col;
+  if (val) *val = c->m.val;
+  if (K) *K = c->m.K;
+  return LB_OK;
+}
+
+int lb_csr_copy(const lb_csr_t* c, int64_t* rowptr, int32_t* col, double* val, double* K, void* stream) {
+  LB_REQUIRE(c != nullptr, "lb_csr_copy: NULL handle");
+  const cudaStream_t st = S(stream);
+  if (rowptr)
+    LB_TRY_CUDA(cudaMemcpyAsync(rowptr, c->m.rowptr, sizeof(int64_t) * (c->m.M + 1), cudaMemcpyDefault, st), "copy");
+  if (col) LB_TRY_CUDA(cudaMemcpyAsync(col, c->m.col, sizeof(int32_t) * c->m.nnz, cudaMemcpyDefault, st), "copy");
+  if (val) LB_TRY_CUDA(cudaMemcpyAsync(val, c->m.val, sizeof(double) * c->m.nnz, cudaMemcpyDefault, st), "copy");
+  if (K) LB_TRY_CUDA(cudaMemcpyAsync(K, c->m.K, sizeof(double) * c->m.M, cudaMemcpyDefault, st), "copy");
+  LB_TRY_CUDA(cudaStreamSynchronize(st), "copy");
+  return LB_OK;
+}
+
+int lb_csr_destroy(lb_csr_t* c) {
+  if (!c) return LB_OK;
+  cudaFree(c->m.rowptr);
+  cudaFree(c->m.col);
+  cudaFree(c->m.val);
+  cudaFree(c->m.K);
+  cudaFree(c->val32);
+  delete c;
+  return LB_OK;
+}
+
+int lb_rk4_csr(const lb_csr_t* c, int precision, int correct_every, double* v, double dt, int64_t nsteps,
+               void* work, void* stream) {
+  LB_REQUIRE(c && v && work, "lb_rk4_csr: NULL argument");
+  LB_REQUIRE(precision == LB_FP64 || precision == LB_FP32, "lb_rk4_csr: precision = %d", precision);
+  LB_REQUIRE(nsteps >= 0 && std::isfinite(dt) && correct_every >= 0, "lb_rk4_csr: bad arguments");
+  lb_csr* cc = const_cast<lb_csr*>(c);
+  const void* val = c->m.val;
+  if (precision == LB_FP32) {
+    if (!cc->val32) {
+      DevBuf b32;
+      int rc;
+      if ((rc = alloc_or_enomem(b32, sizeof(float) * (size_t)(c->m.nnz + 1), "FP32 values")) != LB_OK) return rc;
+      LB_TRY_CUDA(lbi::to_f32(c->m.nnz, c->m.val, b32.as<float>(), S(stream)), "pack FP32 values");
+      cc->val32 = static_cast<float*>(b32.release());
+    }
+    val = cc->val32;
+  }
+  LB_TRY_CUDA(lbi::rk4_csr(c->m.M, precision, c->m.rowptr, c->m.col, val, c->m.val, correct_every, c->m.K, v, dt,
+                           nsteps, work, S(stream)),
+              "lb_rk4_csr");
+  return LB_OK;
+}
+
 // ------------------------------------------------------------------ host API
 
 int lb_assemble(const lb_basis_t* b, const double* H, const double* a, int keep_parts, int algorithm,

@@ -53,6 +53,22 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
 const char* assemble_kernel_name(int i);
 cudaError_t join_terms(const lb::BasisView& B, unsigned long long* d_count, cudaStream_t st);
 
+// sparse assembly (lb_csr.cu)
+struct CsrOut {
+  int64_t M = 0, nnz = 0, terms = 0;
+  int64_t* rowptr = nullptr;  // M + 1
+  int32_t* col = nullptr;     // nnz, sorted within rows
+  double* val = nullptr;      // nnz
+  double* K = nullptr;        // M
+};
+cudaError_t assemble_lowrank_csr(const lb::BasisView& B, const double* h, int nP, const double* gamma_host,
+                                 const int64_t* lp_ptr_host, const int64_t* lp_idx, const double2* lp_val,
+                                 CsrOut* out, cudaStream_t st);
+cudaError_t rk4_csr(int64_t M, int precision, const int64_t* rowptr, const int32_t* col, const void* val,
+                    const double* val64, int correct_every, const double* K, double* v, double dt, int64_t nsteps,
+                    void* work, cudaStream_t st);
+cudaError_t to_f32(int64_t n, const double* x, float* y, cudaStream_t st);
+
 // RK4 (lb_rk4.cu)
 cudaError_t pack_fp32(int64_t M, const double* A, float* A32, cudaStream_t st);
 cudaError_t pack_bf16(int64_t M, const double* A, uint16_t* Ab, float* scale, cudaStream_t st);

@@ -136,6 +136,78 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   if (lane == 0) Keff[s] = K[s] + t;
 }
 
+// ---------------------------------------------------------------- CSR
+// Eight lanes per row (four rows per warp): lanes stride the row's entries,
+// the partial sums meet in a segmented shuffle, and lane 0 of the group runs
+// the same stage epilogue as the dense kernel.
+constexpr int kCsrLanes = 8;
+
+template <int PREC>
+__device__ __forceinline__ double csr_row_dot(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                              const void* __restrict__ val, const double* __restrict__ x,
+                                              const float* __restrict__ x32, int64_t s, int sub, bool valid) {
+  // every lane of the warp reaches the shuffle below; rows past M add nothing
+  const int64_t b = valid ? __ldg(rowptr + s) : 0, e = valid ? __ldg(rowptr + s + 1) : 0;
+  double t;
+  if (PREC == LB_FP64) {
+    const double* __restrict__ v = static_cast<const double*>(val);
+    double a0 = 0.0;
+    for (int64_t q = b + sub; q < e; q += kCsrLanes) a0 = fma(__ldcs(v + q), __ldg(x + __ldcs(col + q)), a0);
+    t = a0;
+  } else {
+    const float* __restrict__ v = static_cast<const float*>(val);
+    float a0 = 0.f;
+    for (int64_t q = b + sub; q < e; q += kCsrLanes) a0 = fmaf(__ldcs(v + q), __ldg(x32 + __ldcs(col + q)), a0);
+    t = (double)a0;
+  }
+  for (int o = kCsrLanes / 2; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o, kCsrLanes);
+  return t;
+}
+
+template <int PREC, int STAGE>
+__global__ void __launch_bounds__(256)
+    k_stage_csr(int64_t M, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                const void* __restrict__ val, const double* __restrict__ Keff, const double* __restrict__ x,
+                const float* __restrict__ x32, double* __restrict__ xn, float* __restrict__ xn32,
+                double* __restrict__ acc, double* __restrict__ v, double h) {
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kCsrLanes;
+  const int sub = threadIdx.x % kCsrLanes;
+  const double y = csr_row_dot<PREC>(rowptr, col, val, x, x32, s, sub, s < M);
+  if (sub != 0 || s >= M) return;
+  const double k = y + Keff[s];
+  double nx;
+  if (STAGE == 1) {
+    acc[s] = k;
+    nx = v[s] + 0.5 * h * k;
+  } else if (STAGE == 2) {
+    acc[s] += 2.0 * k;
+    nx = v[s] + 0.5 * h * k;
+  } else if (STAGE == 3) {
+    acc[s] += 2.0 * k;
+    nx = v[s] + h * k;
+  } else {
+    nx = v[s] + (h / 6.0) * (acc[s] + k);
+    v[s] = nx;
+  }
+  xn[s] = nx;
+  if (PREC != LB_FP64) xn32[s] = (float)nx;
+}
+
+// c = (A64 - A32) v on the CSR pattern;  Keff = K + c.
+__global__ void __launch_bounds__(256)
+    k_correction_csr(int64_t M, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                     const double* __restrict__ v64, const float* __restrict__ v32, const double* __restrict__ x,
+                     const double* __restrict__ K, double* __restrict__ Keff) {
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kCsrLanes;
+  const int sub = threadIdx.x % kCsrLanes;
+  const bool valid = s < M;  // all lanes reach the shuffle
+  const int64_t b = valid ? rowptr[s] : 0, e = valid ? rowptr[s + 1] : 0;
+  double t = 0.0;
+  for (int64_t q = b + sub; q < e; q += kCsrLanes) t = fma(v64[q] - (double)v32[q], x[col[q]], t);
+  for (int o = kCsrLanes / 2; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o, kCsrLanes);
+  if (sub == 0 && valid) Keff[s] = K[s] + t;
+}
+
 __global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -218,9 +290,55 @@ cudaError_t run_steps(int64_t M, const void* Ap, const float* scale, const doubl
   return cudaGetLastError();
 }
 
+template <int PREC>
+cudaError_t run_steps_csr(int64_t M, const int64_t* rowptr, const int32_t* col, const void* val,
+                          const double* val64, int correct_every, const double* K, double* v, double dt,
+                          int64_t nsteps, const Work& w, cudaStream_t st) {
+  const unsigned grid = (unsigned)((M * kCsrLanes + 255) / 256);
+  cudaError_t e;
+  e = cudaMemcpyAsync(w.X, v, sizeof(double) * M, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(w.Keff, K, sizeof(double) * M, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  if (PREC != LB_FP64) {
+    k_to_f32<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, v, w.X32);
+    lbi::note_launch(1);
+  }
+  const bool correct = PREC == LB_FP32 && correct_every > 0 && val64 != nullptr;
+  for (int64_t t = 0; t < nsteps; ++t) {
+    if (correct && t % correct_every == 0) {
+      k_correction_csr<<<grid, 256, 0, st>>>(M, rowptr, col, val64, static_cast<const float*>(val), v, K, w.Keff);
+      lbi::note_launch(1);
+    }
+    k_stage_csr<PREC, 1><<<grid, 256, 0, st>>>(M, rowptr, col, val, w.Keff, w.X, w.X32, w.Y, w.Y32, w.acc, v, dt);
+    k_stage_csr<PREC, 2><<<grid, 256, 0, st>>>(M, rowptr, col, val, w.Keff, w.Y, w.Y32, w.X, w.X32, w.acc, v, dt);
+    k_stage_csr<PREC, 3><<<grid, 256, 0, st>>>(M, rowptr, col, val, w.Keff, w.X, w.X32, w.Y, w.Y32, w.acc, v, dt);
+    k_stage_csr<PREC, 4><<<grid, 256, 0, st>>>(M, rowptr, col, val, w.Keff, w.Y, w.Y32, w.X, w.X32, w.acc, v, dt);
+    lbi::note_launch(4);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 namespace lbi {
+
+cudaError_t rk4_csr(int64_t M, int precision, const int64_t* rowptr, const int32_t* col, const void* val,
+                    const double* val64, int correct_every, const double* K, double* v, double dt, int64_t nsteps,
+                    void* work, cudaStream_t st) {
+  Work w = carve(work, M);
+  if (precision == LB_FP64)
+    return run_steps_csr<LB_FP64>(M, rowptr, col, val, val64, correct_every, K, v, dt, nsteps, w, st);
+  if (precision == LB_FP32)
+    return run_steps_csr<LB_FP32>(M, rowptr, col, val, val64, correct_every, K, v, dt, nsteps, w, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t to_f32(int64_t n, const double* x, float* y, cudaStream_t st) {
+  k_to_f32<<<4 * 152 * 8, 256, 0, st>>>(n, x, y);
+  note_launch(1);
+  return cudaGetLastError();
+}
 
 cudaError_t pack_fp32(int64_t M, const double* A, float* A32, cudaStream_t st) {
   const int64_t n = M * M;

@@ -69,6 +69,13 @@ def load():
         "lb_system_get": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
         "lb_integrate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double,
                                         ctypes.c_double, _vp]),
+        "lb_assemble_lowrank_csr": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp,
+                                                   ctypes.POINTER(_vp), _vp]),
+        "lb_csr_info": (ctypes.c_int, [_vp, _i64p, _i64p, _i64p]),
+        "lb_csr_arrays": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+        "lb_csr_copy": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+        "lb_csr_destroy": (ctypes.c_int, [_vp]),
+        "lb_rk4_csr": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, _c_i64, _vp, _vp]),
         "lb_launch_count": (ctypes.c_longlong, []),
         "lb_assemble_dense_timed": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp,
                                                    ctypes.POINTER(ctypes.c_float)]),
@@ -278,6 +285,62 @@ def rk4_dense(Ap, K, v, dt, nsteps, precision="fp64", scale=None, A64=None, corr
                                float(dt), int(nsteps), _ptr(snaps), int(snap_every), _ptr(work),
                                _stream(stream)))
     return snaps
+
+
+class Csr:
+    """Sparse system A = Q + R (CSR) and K on the device (lb_assemble_lowrank_csr).
+
+    h: M float64 device tensor or None; channels: list of (gamma, idx, values)
+    with idx an int64 device tensor and values a complex128 device tensor."""
+
+    def __init__(self, basis, h=None, channels=(), stream=None):
+        import torch
+        lib = load()
+        gam = np.array([float(g) for g, _, _ in channels], np.float64)
+        ptr = np.zeros(len(channels) + 1, np.int64)
+        for p, (_, idx, _) in enumerate(channels):
+            ptr[p + 1] = ptr[p] + idx.numel()
+        dev = "cuda"
+        if channels:
+            idx = torch.cat([i.to(torch.int64) for _, i, _ in channels]).contiguous()
+            val = torch.cat([v.to(torch.complex128) for _, _, v in channels]).contiguous()
+        else:
+            idx = torch.zeros(1, dtype=torch.int64, device=dev)
+            val = torch.zeros(1, dtype=torch.complex128, device=dev)
+        self._keep = (idx, val)
+        hdl = _vp()
+        _check(lib.lb_assemble_lowrank_csr(basis.handle, _ptr(h), len(channels), _ptr(gam), _ptr(ptr), _ptr(idx),
+                                           _ptr(val), ctypes.byref(hdl), _stream(stream)))
+        self._h = hdl
+        M, nnz, terms = _c_i64(), _c_i64(), _c_i64()
+        _check(lib.lb_csr_info(hdl, ctypes.byref(M), ctypes.byref(nnz), ctypes.byref(terms)))
+        self.M, self.nnz, self.terms = M.value, nnz.value, terms.value
+
+    def close(self):
+        if self._h:
+            load().lb_csr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def to_host(self):
+        """(rowptr int64, col int32, val float64, K float64) as numpy arrays."""
+        rp = np.zeros(self.M + 1, np.int64)
+        col = np.zeros(max(self.nnz, 1), np.int32)
+        val = np.zeros(max(self.nnz, 1), np.float64)
+        K = np.zeros(self.M, np.float64)
+        _check(load().lb_csr_copy(self._h, _ptr(rp), _ptr(col), _ptr(val), _ptr(K), None))
+        return rp, col[:self.nnz], val[:self.nnz], K
+
+    def rk4(self, v, dt, nsteps, precision="fp64", correct_every=0, work=None, stream=None):
+        """RK4 on the CSR system; v (float64 device tensor) updated in place."""
+        work = rk4_workspace(self.M, v.device) if work is None else work
+        _check(load().lb_rk4_csr(self._h, PRECISIONS[precision], int(correct_every), _ptr(v), float(dt),
+                                 int(nsteps), _ptr(work), _stream(stream)))
 
 
 class System:

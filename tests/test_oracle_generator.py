@@ -234,3 +234,50 @@ def test_entries_from_rows_match_full():
             o.R_entries_rows(rows[1:], a[rows[1:]], s, n)
     assert np.abs(out - R[s, n]).max() < 1e-15
     assert np.abs(sc - S[s, n]).max() < 1e-14
+
+
+def _dense_from_csr(rowptr, col, val, M):
+    D = np.zeros((M, M))
+    mask = np.zeros((M, M), bool)
+    for s in range(M):
+        D[s, col[rowptr[s]:rowptr[s + 1]]] = val[rowptr[s]:rowptr[s + 1]]
+        mask[s, col[rowptr[s]:rowptr[s + 1]]] = True
+    return D, mask
+
+
+@pytest.mark.parametrize("N", [3, 5, 8])
+def test_lowrank_csr_equals_dense(N):
+    """Sparse generator of the ladder model equals the dense Q + R; its pattern
+    holds every entry that is nonzero beyond rounding and nothing else."""
+    from oracle import lowrank_csr
+    H, L, g = wl.ladder_model(N, 40 + N)
+    with Oracle(N) as o:
+        h, _ = o.expand(H)
+        l, _ = o.expand(L)
+        nz = np.nonzero(np.abs(l) > 0)[0]
+        rp, col, val, K = lowrank_csr(o, h.real, [g], [(nz, l[nz])])
+        a = g * np.outer(l, l.conj())
+        A = o.Q(h.real) + o.R(a)
+        Rl, mask_r = o.R_lowrank([g], [(nz, l[nz])])
+        Kd = o.K(a)
+    D, mask = _dense_from_csr(rp, col, val, o.M)
+    assert np.abs(D - A).max() < 1e-14
+    assert np.abs(K - Kd).max() < 1e-15
+    assert np.array_equal(mask, np.abs(A) > 1e-13)   # no value here is near the cut
+    assert np.all(np.diff(rp) >= 0)
+    for s in range(o.M):                       # sorted, unique columns
+        c = col[rp[s]:rp[s + 1]]
+        assert np.all(np.diff(c) > 0)
+
+
+@pytest.mark.parametrize("N", list(range(6, 15)))
+def test_ladder_pattern_counts(N):
+    """nnz of Q + R for the ladder model (tridiagonal H): 7N^2 - 11N + 1."""
+    from oracle import lowrank_csr
+    H, L, g = wl.ladder_model(N, 7)
+    with Oracle(N) as o:
+        h, _ = o.expand(H)
+        l, _ = o.expand(L)
+        nz = np.nonzero(np.abs(l) > 0)[0]
+        rp, col, val, K = lowrank_csr(o, h.real, [g], [(nz, l[nz])])
+    assert rp[-1] == 7 * N * N - 11 * N + 1
