@@ -244,6 +244,55 @@ int lb_rk4_csr(const lb_csr_t *c, int precision, int correct_every, double *v, d
                int64_t nsteps, void *work, void *stream);
 
 /* ------------------------------------------------------------------------
+ * a9 -- batched form: many independent realizations of mixed N (the
+ * ensemble sampling of Sec. 6, one sample per processor group), assembled
+ * and integrated together.
+ * --------------------------------------------------------------------- */
+
+typedef struct lb_batch lb_batch_t;
+
+/* A batch of `count` realizations with dimensions Ns[r] (2 <= N <= 64).  The
+ * batch owns one basis per distinct N and, per realization, the assembled
+ * A = Q + R (FP64 and FP32) and K.  Synchronous. */
+int lb_batch_create(int count, const int *Ns, lb_batch_t **out);
+
+/* Inputs and state of realization r: a (device M x M complex Kossakowski
+ * matrix), h (device M real Hamiltonian coefficients, or NULL), v (device M
+ * doubles: the initial state, overwritten by lb_batch_integrate).  The
+ * pointers are kept (not copied) and must stay valid while the batch uses them. */
+int lb_batch_set(lb_batch_t *b, int r, const double *a, const double *h, double *v);
+
+/* Assemble every realization (dense, LB_ALG_JOIN or LB_ALG_CLOSED) and pack
+ * its FP32 copy.  Synchronous. */
+int lb_batch_assemble(lb_batch_t *b, int algorithm, void *stream);
+
+/* Cluster size (1, 2, 4, 8, 16 blocks) used for realization r; default 1. */
+int lb_batch_set_cluster(lb_batch_t *b, int r, int C);
+
+/* Autotuner: bucket the realizations by N (bucket width `width`), time every
+ * cluster size on each bucket for probe_steps RK4 steps, keep the fastest
+ * (states restored afterwards).  choice (optional, count ints) receives it. */
+int lb_batch_tune(lb_batch_t *b, int width, int probe_steps, double dt, void *stream, int *choice);
+
+/* RK4 for every realization, nsteps steps of dt, FP32 matrix with FP32
+ * products, FP64 state, FP64 defect correction every correct_every steps (0:
+ * none).  One persistent cluster launch per cluster-size group: a cluster
+ * takes realizations from a queue (largest first), keeps its row slices of
+ * the matrix in shared memory when they fit, and exchanges the stage
+ * vector through distributed shared memory.  ms (optional) receives the
+ * device time.  Synchronous. */
+int lb_batch_integrate(lb_batch_t *b, int correct_every, double dt, int64_t nsteps, void *stream, float *ms);
+
+/* Device pointers of realization r's assembled system (owned by the batch). */
+int lb_batch_system(const lb_batch_t *b, int r, const double **A64, const float **A32, const double **K,
+                    int64_t *M);
+
+/* Copy realization r's FP64 A (M x M) and K (M) into caller buffers (host or
+ * device; either may be NULL).  Synchronous with respect to stream. */
+int lb_batch_copy_system(const lb_batch_t *b, int r, double *A64, double *K, void *stream);
+int lb_batch_destroy(lb_batch_t *b);
+
+/* ------------------------------------------------------------------------
  * Host-buffer interface (one call per paper step, inputs and outputs in
  * host memory, copies included).  The assembled system stays on the device
  * inside an lb_system_t.

@@ -1,0 +1,512 @@
+// lb_batch.cu -- the batched form: many independent realizations of mixed N
+// (the paper's Sec. 6 ensemble of random Lindbladians: one sample per group
+// of processors, trivially parallel), assembled and then integrated by one
+// persistent launch per cluster-size group.
+//
+// Integration: a thread-block cluster owns one realization at a time (taken
+// from a global counter by the cluster's rank-0 block).  Each block of the
+// cluster owns a contiguous slice of rows; its slice of the FP32 matrix stays
+// in shared memory for the whole 4 x nsteps stages when it fits, else it is
+// re-read from global memory (L2) every stage.  After each stage every block
+// publishes its slice of the next stage vector in its shared memory, the
+// cluster barrier orders the writes, and every block gathers the full vector
+// from its peers through distributed shared memory (double-buffered, one
+// barrier per stage).  State, stage combination and the FP64 defect
+// correction stay FP64, as in the single-system kernels.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "lb_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+struct BItem {
+  int64_t M;
+  const float* A32;   // M x M
+  const double* A64;  // M x M (for the correction) or null
+  const double* K;    // M
+  double* v;          // M, in/out
+};
+
+struct SmemLayout {
+  int64_t slice, mmax;
+  bool resident;
+  size_t off_x32, off_x64, off_pub32, off_pub64, off_v, off_acc, off_keff, off_r, off_item, total;
+};
+
+inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
+
+SmemLayout layout(int64_t mmax, int C, bool resident) {
+  SmemLayout L;
+  L.mmax = mmax;
+  L.slice = (mmax + C - 1) / C;
+  L.resident = resident;
+  size_t o = 0;
+  L.off_item = o; o = a16(o + 16);
+  L.off_x32 = o; o = a16(o + sizeof(float) * mmax);
+  L.off_x64 = o; o = a16(o + sizeof(double) * mmax);
+  L.off_pub32 = o; o = a16(o + sizeof(float) * 2 * L.slice);
+  L.off_pub64 = o; o = a16(o + sizeof(double) * L.slice);
+  L.off_v = o; o = a16(o + sizeof(double) * L.slice);
+  L.off_acc = o; o = a16(o + sizeof(double) * L.slice);
+  L.off_keff = o; o = a16(o + sizeof(double) * L.slice);
+  L.off_r = o;
+  if (resident) o = a16(o + sizeof(float) * L.slice * mmax);
+  L.total = o;
+  return L;
+}
+
+__global__ void __launch_bounds__(256) k_rk4_batch(const BItem* __restrict__ items, const int* __restrict__ order,
+                                                   int nitems, int* __restrict__ counter, int64_t nsteps, double dt,
+                                                   int correct_every, SmemLayout L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  int* item_slot = reinterpret_cast<int*>(smem + L.off_item);
+  float* x32 = reinterpret_cast<float*>(smem + L.off_x32);
+  double* x64 = reinterpret_cast<double*>(smem + L.off_x64);
+  float* pub32 = reinterpret_cast<float*>(smem + L.off_pub32);
+  double* pub64 = reinterpret_cast<double*>(smem + L.off_pub64);
+  double* vv = reinterpret_cast<double*>(smem + L.off_v);
+  double* acc = reinterpret_cast<double*>(smem + L.off_acc);
+  double* keff = reinterpret_cast<double*>(smem + L.off_keff);
+  float* Rs = reinterpret_cast<float*>(smem + L.off_r);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  while (true) {
+    if (rank == 0 && threadIdx.x == 0) *item_slot = atomicAdd(counter, 1);
+    cluster.sync();
+    const int* slot0 = cluster.map_shared_rank(item_slot, 0);
+    const int qi = *slot0;
+    cluster.sync();  // every block has read the slot before rank 0 may overwrite it
+    if (qi >= nitems) break;
+    const BItem it = items[order[qi]];
+    const int64_t M = it.M;
+    const int64_t slice = (M + C - 1) / C;
+    const int64_t r0 = rank * slice, r1 = r0 + slice < M ? r0 + slice : M;
+    const int64_t nrow = r1 > r0 ? r1 - r0 : 0;
+    const bool resident = L.resident;
+    // own rows: state, K, (resident) matrix slice; full initial vector
+    for (int64_t i = threadIdx.x; i < nrow; i += blockDim.x) {
+      vv[i] = it.v[r0 + i];
+      keff[i] = it.K[r0 + i];
+    }
+    if (resident)
+      for (int64_t e = threadIdx.x; e < nrow * M; e += blockDim.x) Rs[e] = it.A32[r0 * M + e];
+    for (int64_t n = threadIdx.x; n < M; n += blockDim.x) {
+      x32[n] = (float)it.v[n];
+      x64[n] = it.v[n];
+    }
+    __syncthreads();
+    int buf = 0;
+    for (int64_t t = 0; t < nsteps; ++t) {
+      if (correct_every > 0 && it.A64 != nullptr && t % correct_every == 0) {
+        // FP64 defect c = (A64 - A32) v on own rows, with the full current v in x64
+        for (int64_t i = warp; i < nrow; i += nw) {
+          const int64_t s = r0 + i;
+          double c = 0.0;
+          for (int64_t n = lane; n < M; n += 32)
+            c = fma(it.A64[s * M + n] - (double)it.A32[s * M + n], x64[n], c);
+          for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+          if (lane == 0) keff[i] = it.K[s] + c;
+        }
+        __syncthreads();
+      }
+      for (int stage = 1; stage <= 4; ++stage) {
+        for (int64_t i = warp; i < nrow; i += nw) {
+          const float* row = resident ? Rs + i * M : it.A32 + (r0 + i) * M;
+          float a = 0.f;
+          for (int64_t n = lane; n < M; n += 32) a = fmaf(row[n], x32[n], a);
+          double y = (double)a;
+          for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+          if (lane == 0) {
+            const double k = y + keff[i];
+            double nx;
+            if (stage == 1) {
+              acc[i] = k;
+              nx = vv[i] + 0.5 * dt * k;
+            } else if (stage == 2) {
+              acc[i] += 2.0 * k;
+              nx = vv[i] + 0.5 * dt * k;
+            } else if (stage == 3) {
+              acc[i] += 2.0 * k;
+              nx = vv[i] + dt * k;
+            } else {
+              nx = vv[i] + (dt / 6.0) * (acc[i] + k);
+              vv[i] = nx;
+              pub64[i] = nx;
+            }
+            pub32[buf * L.slice + i] = (float)nx;
+          }
+        }
+        cluster.sync();  // slices of the next stage vector are published
+        for (int q = 0; q < C; ++q) {
+          const int64_t q0 = q * slice, q1 = q0 + slice < M ? q0 + slice : M;
+          if (q1 <= q0) continue;
+          const float* src = cluster.map_shared_rank(pub32 + buf * L.slice, q);
+          for (int64_t n = threadIdx.x; n < q1 - q0; n += blockDim.x) x32[q0 + n] = src[n];
+          if (stage == 4 && correct_every > 0 && it.A64 != nullptr && (t + 1) % correct_every == 0) {
+            const double* s64 = cluster.map_shared_rank(pub64, q);
+            for (int64_t n = threadIdx.x; n < q1 - q0; n += blockDim.x) x64[q0 + n] = s64[n];
+          }
+        }
+        __syncthreads();
+        buf ^= 1;
+      }
+    }
+    for (int64_t i = threadIdx.x; i < nrow; i += blockDim.x) it.v[r0 + i] = vv[i];
+    cluster.sync();  // peers are done reading this realization's published slices
+  }
+}
+
+}  // namespace
+
+struct lb_batch {
+  int count = 0;
+  std::vector<int> N;
+  std::vector<int64_t> M;
+  std::vector<const double*> a, h;  // caller-owned device inputs
+  std::vector<double*> v;           // caller-owned device state
+  std::vector<lb_basis_t*> basis;   // one per distinct N (owned)
+  std::vector<int> basis_of;
+  std::vector<double*> A64, K;
+  std::vector<float*> A32;
+  std::vector<int> cluster;  // chosen cluster size per realization
+  BItem* d_items = nullptr;
+  int* d_order = nullptr;
+  int* d_counter = nullptr;
+};
+
+namespace lbi {
+
+cudaError_t batch_alloc(lb_batch* b) {
+  for (int r = 0; r < b->count; ++r) {
+    const size_t mm = (size_t)b->M[r] * (size_t)b->M[r];
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->A64[r], 8 * mm)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&b->A32[r], 4 * mm)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&b->K[r], 8 * (size_t)b->M[r])) != cudaSuccess) return e;
+  }
+  cudaError_t e;
+  if ((e = cudaMalloc(&b->d_items, sizeof(BItem) * b->count)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&b->d_order, sizeof(int) * b->count)) != cudaSuccess) return e;
+  return cudaMalloc(&b->d_counter, sizeof(int) * 8);
+}
+
+void batch_free(lb_batch* b) {
+  for (int r = 0; r < b->count; ++r) {
+    cudaFree(b->A64[r]);
+    cudaFree(b->A32[r]);
+    cudaFree(b->K[r]);
+  }
+  cudaFree(b->d_items);
+  cudaFree(b->d_order);
+  cudaFree(b->d_counter);
+}
+
+cudaError_t batch_assemble(lb_batch* b, const std::vector<lb::BasisView>& views, int algorithm, cudaStream_t st) {
+  for (int r = 0; r < b->count; ++r) {
+    const lb::BasisView& B = views[b->basis_of[r]];
+    cudaError_t e = assemble_dense(B, b->h[r], reinterpret_cast<const double2*>(b->a[r]), b->A64[r], nullptr,
+                                   nullptr, b->K[r], algorithm, st);
+    if (e != cudaSuccess) return e;
+    if ((e = pack_fp32(b->M[r], b->A64[r], b->A32[r], st)) != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+// Run the realizations `ids` (one cluster size C) for nsteps; synchronous when
+// ms is requested.  A cluster size the device cannot place with the needed
+// shared memory fails with cudaErrorInvalidConfiguration before any launch.
+cudaError_t batch_run_group(lb_batch* b, const std::vector<int>& ids, int C, int64_t nsteps, double dt,
+                            int correct_every, cudaStream_t st, float* ms) {
+  if (ids.empty()) {
+    if (ms) *ms = 0.f;
+    return cudaSuccess;
+  }
+  int64_t mmax = 0;
+  for (int r : ids) mmax = std::max<int64_t>(mmax, b->M[r]);
+  int dev = 0, smem_optin = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  SmemLayout L = layout(mmax, C, true);
+  if (L.total > (size_t)smem_optin) L = layout(mmax, C, false);
+  if (L.total > (size_t)smem_optin) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_rk4_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  if (e != cudaSuccess) return e;
+  if (C > 8) {
+    e = cudaFuncSetAttribute(k_rk4_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  // items in decreasing order of work (largest first)
+  std::vector<int> ord(ids.begin(), ids.end());
+  std::sort(ord.begin(), ord.end(), [&](int x, int y) { return b->M[x] > b->M[y]; });
+  std::vector<BItem> host(b->count);
+  for (int r = 0; r < b->count; ++r)
+    host[r] = BItem{b->M[r], b->A32[r], correct_every > 0 ? b->A64[r] : nullptr, b->K[r], b->v[r]};
+  if ((e = cudaMemcpyAsync(b->d_items, host.data(), sizeof(BItem) * b->count, cudaMemcpyHostToDevice, st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(b->d_order, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice, st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st)) != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = L.total;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3((unsigned)C, 1, 1);
+  int clusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&clusters, k_rk4_batch, &cfg);
+  if (e != cudaSuccess) return e;
+  if (clusters < 1) return cudaErrorInvalidConfiguration;
+  clusters = std::min<int>(clusters, (int)ord.size());
+  cfg.gridDim = dim3((unsigned)(clusters * C), 1, 1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ms) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+  }
+  e = cudaLaunchKernelEx(&cfg, k_rk4_batch, (const BItem*)b->d_items, (const int*)b->d_order, (int)ord.size(),
+                         b->d_counter, nsteps, dt, correct_every, L);
+  note_launch(1);
+  if (ms) {
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace lbi
+
+// ------------------------------------------------------------------ ABI
+
+extern "C" {
+
+int lb_batch_create(int count, const int* Ns, lb_batch_t** out) {
+  if (!out || !Ns || count <= 0) {
+    lbi::set_error("lb_batch_create: bad arguments");
+    return LB_EINVAL;
+  }
+  *out = nullptr;
+  lb_batch* b = new lb_batch;
+  b->count = count;
+  b->N.assign(Ns, Ns + count);
+  b->M.resize(count);
+  b->a.assign(count, nullptr);
+  b->h.assign(count, nullptr);
+  b->v.assign(count, nullptr);
+  b->A64.assign(count, nullptr);
+  b->A32.assign(count, nullptr);
+  b->K.assign(count, nullptr);
+  b->cluster.assign(count, 1);
+  b->basis_of.assign(count, -1);
+  std::vector<int> distinct;
+  for (int r = 0; r < count; ++r) {
+    if (Ns[r] < 2 || Ns[r] > 64) {
+      lbi::set_error("lb_batch_create: N = %d outside [2, 64]", Ns[r]);
+      delete b;
+      return LB_EINVAL;
+    }
+    b->M[r] = (int64_t)Ns[r] * Ns[r] - 1;
+    auto it = std::find(distinct.begin(), distinct.end(), Ns[r]);
+    if (it == distinct.end()) {
+      distinct.push_back(Ns[r]);
+      b->basis_of[r] = (int)distinct.size() - 1;
+    } else {
+      b->basis_of[r] = (int)(it - distinct.begin());
+    }
+  }
+  for (int n : distinct) {
+    lb_basis_t* bb = nullptr;
+    int rc = lb_basis_create(n, nullptr, &bb);
+    if (rc != LB_OK) {
+      for (auto* x : b->basis) lb_basis_destroy(x);
+      delete b;
+      return rc;
+    }
+    b->basis.push_back(bb);
+  }
+  cudaError_t e = lbi::batch_alloc(b);
+  if (e != cudaSuccess) {
+    lbi::batch_free(b);
+    for (auto* x : b->basis) lb_basis_destroy(x);
+    delete b;
+    cudaGetLastError();
+    lbi::set_error("lb_batch_create: device allocation failed (%s)", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA;
+  }
+  *out = b;
+  return LB_OK;
+}
+
+int lb_batch_set(lb_batch_t* b, int r, const double* a, const double* h, double* v) {
+  if (!b || r < 0 || r >= b->count || !a || !v) {
+    lbi::set_error("lb_batch_set: bad arguments");
+    return LB_EINVAL;
+  }
+  b->a[r] = a;
+  b->h[r] = h;
+  b->v[r] = v;
+  return LB_OK;
+}
+
+int lb_batch_assemble(lb_batch_t* b, int algorithm, void* stream) {
+  if (!b) {
+    lbi::set_error("lb_batch_assemble: NULL batch");
+    return LB_EINVAL;
+  }
+  for (int r = 0; r < b->count; ++r)
+    if (!b->a[r] || !b->v[r]) {
+      lbi::set_error("lb_batch_assemble: realization %d has no inputs (lb_batch_set)", r);
+      return LB_EINVAL;
+    }
+  std::vector<lb::BasisView> views;
+  for (auto* x : b->basis) views.push_back(x->view());
+  cudaError_t e = lbi::batch_assemble(b, views, algorithm, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return lbi::cuda_fail(e, "lb_batch_assemble");
+  return LB_OK;
+}
+
+int lb_batch_set_cluster(lb_batch_t* b, int r, int C) {
+  if (!b || r < 0 || r >= b->count || !(C == 1 || C == 2 || C == 4 || C == 8 || C == 16)) {
+    lbi::set_error("lb_batch_set_cluster: bad arguments");
+    return LB_EINVAL;
+  }
+  b->cluster[r] = C;
+  return LB_OK;
+}
+
+int lb_batch_integrate(lb_batch_t* b, int correct_every, double dt, int64_t nsteps, void* stream, float* ms) {
+  if (!b || nsteps < 0 || correct_every < 0) {
+    lbi::set_error("lb_batch_integrate: bad arguments");
+    return LB_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float total = 0.f;
+  for (int C : {16, 8, 4, 2, 1}) {
+    std::vector<int> ids;
+    for (int r = 0; r < b->count; ++r)
+      if (b->cluster[r] == C) ids.push_back(r);
+    float m = 0.f;
+    cudaError_t e = lbi::batch_run_group(b, ids, C, nsteps, dt, correct_every, st, ms ? &m : nullptr);
+    if (e != cudaSuccess) return lbi::cuda_fail(e, "lb_batch_integrate");
+    total += m;
+  }
+  if (ms) *ms = total;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return lbi::cuda_fail(e, "lb_batch_integrate");
+  return LB_OK;
+}
+
+// Autotuner: realizations are bucketed by N (bucket width `width`); for each
+// bucket every cluster size of {1, 2, 4, 8, 16} that the device can place
+// runs the bucket's realizations for probe_steps steps (timed with CUDA
+// events), the states are restored, and the size with the shortest time is
+// kept.  choice (optional, one per realization) receives the result.
+int lb_batch_tune(lb_batch_t* b, int width, int probe_steps, double dt, void* stream, int* choice) {
+  if (!b || width < 1 || probe_steps < 1) {
+    lbi::set_error("lb_batch_tune: bad arguments");
+    return LB_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // save the states
+  std::vector<double*> saved(b->count, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (int r = 0; r < b->count && e == cudaSuccess; ++r) {
+    if (!b->v[r]) {
+      lbi::set_error("lb_batch_tune: realization %d has no state (lb_batch_set)", r);
+      for (auto* p : saved) cudaFree(p);
+      return LB_EINVAL;
+    }
+    e = cudaMalloc(&saved[r], 8 * (size_t)b->M[r]);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(saved[r], b->v[r], 8 * (size_t)b->M[r], cudaMemcpyDeviceToDevice, st);
+  }
+  int nmax = 0;
+  for (int n : b->N) nmax = std::max(nmax, n);
+  for (int lo = 2; lo <= nmax && e == cudaSuccess; lo += width) {
+    std::vector<int> ids;
+    for (int r = 0; r < b->count; ++r)
+      if (b->N[r] >= lo && b->N[r] < lo + width) ids.push_back(r);
+    if (ids.empty()) continue;
+    float best = 3.4e38f;
+    int bestC = 1;
+    for (int C : {1, 2, 4, 8, 16}) {
+      float ms = 0.f;
+      cudaError_t ec = lbi::batch_run_group(b, ids, C, probe_steps, dt, 0, st, &ms);
+      if (ec != cudaSuccess) {  // size not placeable with this shared memory: skip it
+        cudaGetLastError();
+        continue;
+      }
+      if (ms < best) {
+        best = ms;
+        bestC = C;
+      }
+      for (int r : ids)
+        e = cudaMemcpyAsync(b->v[r], saved[r], 8 * (size_t)b->M[r], cudaMemcpyDeviceToDevice, st);
+    }
+    for (int r : ids) b->cluster[r] = bestC;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  for (auto* p : saved) cudaFree(p);
+  if (e != cudaSuccess) return lbi::cuda_fail(e, "lb_batch_tune");
+  if (choice)
+    for (int r = 0; r < b->count; ++r) choice[r] = b->cluster[r];
+  return LB_OK;
+}
+
+int lb_batch_system(const lb_batch_t* b, int r, const double** A64, const float** A32, const double** K,
+                    int64_t* M) {
+  if (!b || r < 0 || r >= b->count) {
+    lbi::set_error("lb_batch_system: bad arguments");
+    return LB_EINVAL;
+  }
+  if (A64) *A64 = b->A64[r];
+  if (A32) *A32 = b->A32[r];
+  if (K) *K = b->K[r];
+  if (M) *M = b->M[r];
+  return LB_OK;
+}
+
+int lb_batch_copy_system(const lb_batch_t* b, int r, double* A64, double* K, void* stream) {
+  if (!b || r < 0 || r >= b->count) {
+    lbi::set_error("lb_batch_copy_system: bad arguments");
+    return LB_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t M = (size_t)b->M[r];
+  cudaError_t e = cudaSuccess;
+  if (A64) e = cudaMemcpyAsync(A64, b->A64[r], 8 * M * M, cudaMemcpyDefault, st);
+  if (K && e == cudaSuccess) e = cudaMemcpyAsync(K, b->K[r], 8 * M, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return lbi::cuda_fail(e, "lb_batch_copy_system");
+  return LB_OK;
+}
+
+int lb_batch_destroy(lb_batch_t* b) {
+  if (!b) return LB_OK;
+  lbi::batch_free(b);
+  for (auto* x : b->basis) lb_basis_destroy(x);
+  delete b;
+  return LB_OK;
+}
+
+}  // extern "C"

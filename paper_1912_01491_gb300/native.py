@@ -76,6 +76,16 @@ def load():
         "lb_csr_copy": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
         "lb_csr_destroy": (ctypes.c_int, [_vp]),
         "lb_rk4_csr": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, _c_i64, _vp, _vp]),
+        "lb_batch_create": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+        "lb_batch_set": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+        "lb_batch_assemble": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+        "lb_batch_set_cluster": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+        "lb_batch_tune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp, _vp]),
+        "lb_batch_integrate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, _c_i64, _vp,
+                                              ctypes.POINTER(ctypes.c_float)]),
+        "lb_batch_system": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _i64p]),
+        "lb_batch_copy_system": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+        "lb_batch_destroy": (ctypes.c_int, [_vp]),
         "lb_launch_count": (ctypes.c_longlong, []),
         "lb_assemble_dense_timed": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp,
                                                    ctypes.POINTER(ctypes.c_float)]),
@@ -341,6 +351,61 @@ class Csr:
         work = rk4_workspace(self.M, v.device) if work is None else work
         _check(load().lb_rk4_csr(self._h, PRECISIONS[precision], int(correct_every), _ptr(v), float(dt),
                                  int(nsteps), _ptr(work), _stream(stream)))
+
+
+class Batch:
+    """Batched realizations of mixed N (lb_batch_*).  Inputs are torch tensors
+    on the device, kept alive by this object."""
+
+    def __init__(self, Ns):
+        Ns = np.ascontiguousarray(np.asarray(Ns, dtype=np.int32))
+        h = _vp()
+        _check(load().lb_batch_create(len(Ns), _ptr(Ns), ctypes.byref(h)))
+        self._h = h
+        self.Ns = [int(n) for n in Ns]
+        self.Ms = [n * n - 1 for n in self.Ns]
+        self._keep = {}
+
+    def close(self):
+        if self._h:
+            load().lb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set(self, r, a, h, v):
+        self._keep[r] = (a, h, v)
+        _check(load().lb_batch_set(self._h, int(r), _ptr(a), _ptr(h), _ptr(v)))
+
+    def assemble(self, algorithm="closed", stream=None):
+        _check(load().lb_batch_assemble(self._h, ALGORITHMS[algorithm], _stream(stream)))
+
+    def set_cluster(self, r, C):
+        _check(load().lb_batch_set_cluster(self._h, int(r), int(C)))
+
+    def tune(self, width=6, probe_steps=20, dt=1e-3, stream=None):
+        choice = np.zeros(len(self.Ns), np.int32)
+        _check(load().lb_batch_tune(self._h, int(width), int(probe_steps), float(dt), _stream(stream),
+                                    _ptr(choice)))
+        return choice
+
+    def integrate(self, dt, nsteps, correct_every=0, stream=None):
+        ms = ctypes.c_float()
+        _check(load().lb_batch_integrate(self._h, int(correct_every), float(dt), int(nsteps), _stream(stream),
+                                         ctypes.byref(ms)))
+        return ms.value
+
+    def system(self, r):
+        """(A64, K) of realization r as host numpy arrays."""
+        M = self.Ms[r]
+        A = np.zeros((M, M))
+        K = np.zeros(M)
+        _check(load().lb_batch_copy_system(self._h, int(r), _ptr(A), _ptr(K), None))
+        return A, K
 
 
 class System:

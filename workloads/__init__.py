@@ -92,6 +92,24 @@ def wishart_kossakowski_device(N, seed, device="cuda", scale=1.0, chunk=8192):
     return a
 
 
+def random_lindbladian_device(N, seed, device="cuda"):
+    """(H, a) of one random Lindbladian formed on the GPU in FP64 (moderate N):
+    GUE H from the host generator, a = G G^dagger / Tr with G from torch's
+    counter-based generator on the device."""
+    import torch
+    M = N * N - 1
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    s = 1.0 / np.sqrt(2.0)
+    G = torch.complex(torch.randn((M, M), generator=gen, device=device, dtype=torch.float64) * s,
+                      torch.randn((M, M), generator=gen, device=device, dtype=torch.float64) * s)
+    a = G @ G.conj().T
+    a = 0.5 * (a + a.conj().T)
+    a = a / torch.diagonal(a).real.sum()
+    H = torch.tensor(gue_hamiltonian(N, seed + 1), device=device)
+    return H, a.contiguous()
+
+
 def ladder_model(N, seed, gamma=0.1):
     """(H real tridiagonal N x N complex128, L N x N complex128, gamma)."""
     g = rng(seed)
