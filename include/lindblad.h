@@ -108,6 +108,31 @@ int lb_structure_count(const lb_basis_t *b, int which, int64_t *nnz);
 int lb_structure_export(const lb_basis_t *b, int which, int32_t *idx3, double *val,
                         int64_t capacity, int64_t *nnz, void *stream);
 
+/* lb_structure_export without any device allocation.  The paper has no
+ * counterpart: this serves callers that cannot allocate device memory per
+ * call -- processes whose framework's caching allocator has reserved the
+ * device memory (a cudaMalloc there fails or fragments the pool, and a
+ * cudaFree synchronizes the whole device), and real-time or embedded callers
+ * that reserve all memory at start-up.  Arguments, outputs, ordering and
+ * error behaviour are those of lb_structure_export; the caller passes the
+ * basis and the output buffers.  The scratch (per-m counts and their scan)
+ * is a file-scope device array of 2 x 65536 int64 (1 MiB) that every GPU
+ * loading this library holds until the process exits; the entry point calls
+ * no cudaMalloc, cudaFree or allocating library routine.
+ *   - Limit: M <= 65535 (N <= 256); a larger basis returns LB_EINVAL with a
+ *     message naming the limit, and nothing is launched.
+ *   - Set-up: the first call on each device looks up the array's device
+ *     address with cudaGetSymbolAddress (that device current) and caches it;
+ *     make that first call before any stream capture begins.
+ *   - Sharing: all calls on a device use the same array, which keeps the last
+ *     call's contents (every word a call reads is written earlier in the same
+ *     call, so nothing needs clearing).  The call returns after its fill has
+ *     finished on `stream`; calls whose GPU work overlaps (from several host
+ *     threads at once, on any streams) race on the array and give wrong
+ *     results. */
+int lb_structure_export_noalloc(const lb_basis_t *b, int which, int32_t *idx3, double *val,
+                                int64_t capacity, int64_t *nnz, void *stream);
+
 /* Number of join terms W = #{(j,l,n,k,s): z_jln != 0, f_kls != 0} visited by
  * the dense R assembly (Eq. (09)); counted on the GPU.  Synchronous. */
 int lb_join_terms(const lb_basis_t *b, int64_t *W);

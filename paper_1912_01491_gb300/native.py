@@ -54,6 +54,7 @@ def load():
                                           ctypes.POINTER(ctypes.c_int)]),
         "lb_structure_count": (ctypes.c_int, [_vp, ctypes.c_int, _i64p]),
         "lb_structure_export": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_i64, _i64p, _vp]),
+        "lb_structure_export_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_i64, _i64p, _vp]),
         "lb_join_terms": (ctypes.c_int, [_vp, _i64p]),
         "lb_expand": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
         "lb_rho": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -206,6 +207,16 @@ class Basis:
         _check(load().lb_structure_export(self._h, w, _ptr(idx), _ptr(val), n, ctypes.byref(got),
                                           _stream(stream)))
         return idx[:n], val[:n]
+
+    def structure_into(self, which, idx, val, stream=None):
+        """Kernel (a) into caller-owned device buffers idx (int32, >= 3 nnz
+        entries) and val (float64, >= nnz) through the entry point that
+        allocates no device memory (N <= 256).  Returns nnz."""
+        w = {"f": LB_F, "d": LB_D}[which]
+        got = _c_i64()
+        _check(load().lb_structure_export_noalloc(self._h, w, _ptr(idx), _ptr(val), int(val.numel()),
+                                                  ctypes.byref(got), _stream(stream)))
+        return got.value
 
     def assemble_dense_timed(self, a, h=None, A=None, K=None, algorithm="closed", stream=None):
         """Dense assembly into preallocated A (and K); returns {kernel name: ms}."""
