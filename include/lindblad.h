@@ -357,6 +357,111 @@ long long lb_launch_count(void);
  * FP64-bound kernels.  Synchronous. */
 int lb_probe_fp64(double *tflops);
 
+/* ------------------------------------------------------------------------
+ * a10 -- serving form.  Realizations of the random-Lindbladian model
+ * (Sec. 6: independent samples of an ensemble) arrive one by one as
+ * requests; each is assembled (Eqs. (07)-(09)) and integrated (RK4, Table 1
+ * step 3) on the GPU while earlier ones are still running.  A server owns a
+ * scheduler thread, a device-memory pool and per-request streams.
+ *
+ * Admission: a request holds lb_request_bytes(N, precision, H != NULL)
+ * bytes of server memory from admission to completion (A64, the low-
+ * precision copy, K, the state, the expansion of H and RK4 work vectors).
+ * Requests are admitted in arrival order while fewer than `slots` are in
+ * flight and their bytes fit in what `budget_bytes` has left; one that does
+ * not fit is passed by later requests only until it has waited `bypass_ms`.
+ * The caller's a, H and v0 stay caller-owned and are not counted: they are
+ * read until the request's state reaches LB_REQ_ASSEMBLED, after which the
+ * caller may free or reuse them.  v_out is written by the time the state is
+ * LB_REQ_DONE.
+ *
+ * Engines: N <= 64 with LB_FP32 runs on the cluster-persistent batched
+ * kernel (requests admitted together share one launch; cluster size from
+ * lb_server_set_cluster, else the smallest size that keeps the matrix in
+ * shared memory); every other request runs the fused RK4 stage kernels as a
+ * CUDA graph of about 50 steps (a multiple of correct_every) replayed on its
+ * own stream.  A request's result depends only on its own inputs, N and
+ * precision, not on the other requests in flight.
+ *
+ * Thread safety: every lb_server_* / lb_submit / lb_poll / lb_wait call may
+ * come from any host thread (one internal mutex).  All waits are bounded by
+ * the caller's timeout; lb_server_destroy cancels queued requests and waits
+ * for admitted ones to finish on the GPU.
+ * --------------------------------------------------------------------- */
+
+typedef struct lb_server lb_server_t;
+
+typedef struct lb_request {
+  int N;               /* 2 <= N <= 512 */
+  int precision;       /* LB_FP64 | LB_FP32 | LB_BF16 */
+  int correct_every;   /* FP64 defect-correction period for FP32/BF16 (0 = none) */
+  double dt;
+  int64_t nsteps;
+  const double *H;     /* device N x N complex128 Hermitian (interleaved), or NULL */
+  const double *a;     /* device M x M complex128 Hermitian Kossakowski matrix (Eq. (09) convention) */
+  const double *v0;    /* device M: initial state */
+  double *v_out;       /* device M: final state */
+  void *stream;        /* caller's cudaStream_t: a, H, v0 are complete in its order at
+                          submission (the server's work waits for it); NULL = legacy stream */
+} lb_request;
+
+#define LB_REQ_QUEUED 0
+#define LB_REQ_RUNNING 1     /* admitted; a, H, v0 may still be read */
+#define LB_REQ_ASSEMBLED 2   /* a, H, v0 no longer read */
+#define LB_REQ_DONE 3
+#define LB_REQ_FAILED 4
+#define LB_REQ_CANCELLED 5
+
+#define LB_ENGINE_CLUSTER 0
+#define LB_ENGINE_STREAM 1
+
+typedef struct lb_result {
+  int state;           /* LB_REQ_* */
+  int status;          /* LB_OK, or the error of a failed request */
+  int engine;          /* LB_ENGINE_* */
+  int cluster;         /* cluster size (cluster engine), else 0 */
+  double queue_ms;     /* submission -> admission */
+  double latency_ms;   /* submission -> completion seen by the host */
+  double gpu_ms;       /* device time from the request's first enqueue to its result copy */
+} lb_result;
+
+/* Server memory one request holds (bytes), or -1 for invalid arguments. */
+int64_t lb_request_bytes(int N, int precision, int with_H);
+
+/* Create a server on the current device.  budget_bytes > 0, slots >= 1,
+ * bypass_ms >= 0.  LB_ECUDA if the pool or streams cannot be created. */
+int lb_server_create(int64_t budget_bytes, int slots, double bypass_ms, lb_server_t **out);
+
+/* Cluster size C in {1, 2, 4, 8, 16} for requests of dimension N <= 64 on
+ * the cluster engine (takes effect for requests admitted afterwards). */
+int lb_server_set_cluster(lb_server_t *s, int N, int C);
+
+/* Queue a request; *id identifies it.  LB_EINVAL for a malformed request,
+ * LB_ENOMEM if it can never fit in the budget.  Returns at once. */
+int lb_submit(lb_server_t *s, const lb_request *q, uint64_t *id);
+
+/* State of a request.  LB_OK when done (out filled), LB_EAGAIN while queued
+ * or running, the request's error code if it failed. */
+int lb_poll(lb_server_t *s, uint64_t id, lb_result *out);
+
+/* Wait at most timeout_ms for a request to finish.  LB_ETIMEOUT if it has
+ * not (out holds its current state). */
+int lb_wait(lb_server_t *s, uint64_t id, double timeout_ms, lb_result *out);
+
+/* Nearest-rank p50 / p99 of the latency of completed requests, their
+ * throughput (completed / (last completion - first submission), per s) and
+ * count, since creation or the last lb_server_reset_stats. */
+int lb_server_stats(lb_server_t *s, double *p50_ms, double *p99_ms, double *throughput, int64_t *completed);
+int lb_server_reset_stats(lb_server_t *s);
+int lb_server_destroy(lb_server_t *s);
+
+/* Replay of the admission policy in virtual time (host only, no GPU):
+ * request i arrives at arrival_ms[i] (non-decreasing), holds bytes[i] and
+ * runs service_ms[i] once admitted.  start_ms / finish_ms receive its times
+ * (-1 if it exceeds the budget).  For capacity planning and tests. */
+int lb_sched_simulate(int n, const double *arrival_ms, const int64_t *bytes, const double *service_ms,
+                      int64_t budget, int slots, double bypass_ms, double *start_ms, double *finish_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,6 +16,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "lb_internal.h"
@@ -24,13 +25,7 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-struct BItem {
-  int64_t M;
-  const float* A32;   // M x M
-  const double* A64;  // M x M (for the correction) or null
-  const double* K;    // M
-  double* v;          // M, in/out
-};
+using BItem = lbi::BatchItem;
 
 struct SmemLayout {
   int64_t slice, mmax;
@@ -219,6 +214,55 @@ cudaError_t batch_assemble(lb_batch* b, const std::vector<lb::BasisView>& views,
   return cudaGetLastError();
 }
 
+int smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+// Shared-memory layout for (mmax, C): resident when the slice fits, else
+// streamed; total 0 if even the streamed layout does not fit.
+SmemLayout pick_layout(int64_t mmax, int C) {
+  const size_t cap = (size_t)smem_optin();
+  SmemLayout L = layout(mmax, C, true);
+  if (L.total > cap) L = layout(mmax, C, false);
+  if (L.total > cap) L.total = 0;
+  return L;
+}
+
+// Launch configuration of k_rk4_batch for n items at cluster size C; the
+// number of clusters is what the device can hold at once, capped at n.  The
+// dynamic shared-memory limit is raised to the device maximum once (the same
+// value from every thread), so concurrent launches never see a smaller limit.
+cudaError_t configure(int C, const SmemLayout& L, int n, cudaStream_t st, cudaLaunchConfig_t* cfg,
+                      cudaLaunchAttribute* attr) {
+  cudaError_t e = cudaFuncSetAttribute(k_rk4_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+  if (e != cudaSuccess) return e;
+  if (C > 8) {
+    e = cudaFuncSetAttribute(k_rk4_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  *cfg = cudaLaunchConfig_t{};
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg->blockDim = dim3(256, 1, 1);
+  cfg->dynamicSmemBytes = L.total;
+  cfg->stream = st;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
+  cfg->gridDim = dim3((unsigned)C, 1, 1);
+  int clusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&clusters, k_rk4_batch, cfg);
+  if (e != cudaSuccess) return e;
+  if (clusters < 1) return cudaErrorInvalidConfiguration;
+  clusters = std::min<int>(clusters, n);
+  cfg->gridDim = dim3((unsigned)(clusters * C), 1, 1);
+  return cudaSuccess;
+}
+
 // Run the realizations `ids` (one cluster size C) for nsteps; synchronous when
 // ms is requested.  A cluster size the device cannot place with the needed
 // shared memory fails with cudaErrorInvalidConfiguration before any launch.
@@ -230,19 +274,12 @@ cudaError_t batch_run_group(lb_batch* b, const std::vector<int>& ids, int C, int
   }
   int64_t mmax = 0;
   for (int r : ids) mmax = std::max<int64_t>(mmax, b->M[r]);
-  int dev = 0, smem_optin = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  SmemLayout L = layout(mmax, C, true);
-  if (L.total > (size_t)smem_optin) L = layout(mmax, C, false);
-  if (L.total > (size_t)smem_optin) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k_rk4_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  const SmemLayout L = pick_layout(mmax, C);
+  if (L.total == 0) return cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  cudaError_t e = configure(C, L, (int)ids.size(), st, &cfg, attr);
   if (e != cudaSuccess) return e;
-  if (C > 8) {
-    e = cudaFuncSetAttribute(k_rk4_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
   // items in decreasing order of work (largest first)
   std::vector<int> ord(ids.begin(), ids.end());
   std::sort(ord.begin(), ord.end(), [&](int x, int y) { return b->M[x] > b->M[y]; });
@@ -256,24 +293,6 @@ cudaError_t batch_run_group(lb_batch* b, const std::vector<int>& ids, int C, int
       cudaSuccess)
     return e;
   if ((e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st)) != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(256, 1, 1);
-  cfg.dynamicSmemBytes = L.total;
-  cfg.stream = st;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cfg.gridDim = dim3((unsigned)C, 1, 1);
-  int clusters = 0;
-  e = cudaOccupancyMaxActiveClusters(&clusters, k_rk4_batch, &cfg);
-  if (e != cudaSuccess) return e;
-  if (clusters < 1) return cudaErrorInvalidConfiguration;
-  clusters = std::min<int>(clusters, (int)ord.size());
-  cfg.gridDim = dim3((unsigned)(clusters * C), 1, 1);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ms) {
     cudaEventCreate(&e0);
@@ -291,6 +310,48 @@ cudaError_t batch_run_group(lb_batch* b, const std::vector<int>& ids, int C, int
     cudaEventDestroy(e1);
   }
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+int batch_default_cluster(int64_t M) {
+  const size_t cap = (size_t)smem_optin();
+  for (int C : {1, 2, 4, 8, 16})
+    if (layout(M, C, true).total <= cap) return C;
+  return 16;
+}
+
+cudaError_t batch_launch_async(const BatchItem* items, int n, int C, int64_t nsteps, double dt, int correct_every,
+                               cudaMemPool_t pool, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t mmax = 0;
+  for (int i = 0; i < n; ++i) mmax = std::max<int64_t>(mmax, items[i].M);
+  const SmemLayout L = pick_layout(mmax, C);
+  if (L.total == 0) return cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  cudaError_t e = configure(C, L, n, st, &cfg, attr);
+  if (e != cudaSuccess) return e;
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int x, int y) { return items[x].M > items[y].M; });
+  // one block: items, then order, then the counter
+  const size_t bi = sizeof(BItem) * (size_t)n, bo = sizeof(int) * (size_t)n;
+  const size_t off_o = (bi + 255) & ~size_t(255), off_c = (off_o + bo + 255) & ~size_t(255);
+  std::vector<unsigned char> host(off_c + sizeof(int), 0);
+  std::memcpy(host.data(), items, bi);
+  std::memcpy(host.data() + off_o, ord.data(), bo);
+  void* d = nullptr;
+  if ((e = cudaMallocFromPoolAsync(&d, host.size(), pool, st)) != cudaSuccess) return e;
+  unsigned char* db = static_cast<unsigned char*>(d);
+  e = cudaMemcpyAsync(d, host.data(), host.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaLaunchKernelEx(&cfg, k_rk4_batch, reinterpret_cast<const BItem*>(db),
+                           reinterpret_cast<const int*>(db + off_o), n, reinterpret_cast<int*>(db + off_c), nsteps,
+                           dt, correct_every, L);
+  note_launch(1);
+  const cudaError_t ef = cudaFreeAsync(d, st);
+  if (e != cudaSuccess) return e;
+  if (ef != cudaSuccess) return ef;
   return cudaGetLastError();
 }
 
@@ -320,8 +381,8 @@ int lb_batch_create(int count, const int* Ns, lb_batch_t** out) {
   b->basis_of.assign(count, -1);
   std::vector<int> distinct;
   for (int r = 0; r < count; ++r) {
-    if (Ns[r] < 2 || Ns[r] > 64) {
-      lbi::set_error("lb_batch_create: N = %d outside [2, 64]", Ns[r]);
+    if (Ns[r] < 2 || Ns[r] > lbi::kBatchMaxN) {
+      lbi::set_error("lb_batch_create: N = %d outside [2, %d]", Ns[r], lbi::kBatchMaxN);
       delete b;
       return LB_EINVAL;
     }

@@ -78,4 +78,22 @@ cudaError_t rk4_dense(int64_t M, int precision, const void* Ap, const float* sca
                       double dt, int64_t nsteps, double* snaps, int64_t snap_every,
                       void* work, cudaStream_t st);
 
+// batched form (lb_batch.cu): one realization of the cluster-persistent RK4
+struct BatchItem {
+  int64_t M;
+  const float* A32;   // M x M
+  const double* A64;  // M x M (for the correction) or null
+  const double* K;    // M
+  double* v;          // M, in/out
+};
+constexpr int kBatchMaxN = 64;
+// Cluster size the batched kernel uses for dimension M when none is chosen:
+// the smallest of {1, 2, 4, 8, 16} whose slice of the FP32 matrix stays
+// resident in shared memory, else 16.
+int batch_default_cluster(int64_t M);
+// Enqueue one launch over n items (host array) on st; the item list and work
+// counter are allocated from pool (stream-ordered) and freed after the launch.
+cudaError_t batch_launch_async(const BatchItem* items, int n, int C, int64_t nsteps, double dt, int correct_every,
+                               cudaMemPool_t pool, cudaStream_t st);
+
 }  // namespace lbi

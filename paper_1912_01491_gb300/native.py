@@ -24,6 +24,23 @@ ALGORITHMS = {"join": LB_ALG_JOIN, "closed": LB_ALG_CLOSED}
 _c_i64 = ctypes.c_int64
 _vp = ctypes.c_void_p
 _i64p = ctypes.POINTER(ctypes.c_int64)
+_dp = ctypes.POINTER(ctypes.c_double)
+
+LB_REQ_QUEUED, LB_REQ_RUNNING, LB_REQ_ASSEMBLED, LB_REQ_DONE, LB_REQ_FAILED, LB_REQ_CANCELLED = range(6)
+LB_ENGINE_CLUSTER, LB_ENGINE_STREAM = 0, 1
+
+
+class LbRequest(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("precision", ctypes.c_int), ("correct_every", ctypes.c_int),
+                ("dt", ctypes.c_double), ("nsteps", ctypes.c_int64), ("H", ctypes.c_void_p),
+                ("a", ctypes.c_void_p), ("v0", ctypes.c_void_p), ("v_out", ctypes.c_void_p),
+                ("stream", ctypes.c_void_p)]
+
+
+class LbResult(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("engine", ctypes.c_int),
+                ("cluster", ctypes.c_int), ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("gpu_ms", ctypes.c_double)]
 
 _lib = None
 
@@ -87,6 +104,17 @@ def load():
         "lb_batch_system": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _i64p]),
         "lb_batch_copy_system": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
         "lb_batch_destroy": (ctypes.c_int, [_vp]),
+        "lb_request_bytes": (_c_i64, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "lb_server_create": (ctypes.c_int, [_c_i64, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_vp)]),
+        "lb_server_set_cluster": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+        "lb_submit": (ctypes.c_int, [_vp, ctypes.POINTER(LbRequest), ctypes.POINTER(ctypes.c_uint64)]),
+        "lb_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(LbResult)]),
+        "lb_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(LbResult)]),
+        "lb_server_stats": (ctypes.c_int, [_vp, _dp, _dp, _dp, _i64p]),
+        "lb_server_reset_stats": (ctypes.c_int, [_vp]),
+        "lb_server_destroy": (ctypes.c_int, [_vp]),
+        "lb_sched_simulate": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _c_i64, ctypes.c_int, ctypes.c_double,
+                                             _vp, _vp]),
         "lb_launch_count": (ctypes.c_longlong, []),
         "lb_assemble_dense_timed": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp,
                                                    ctypes.POINTER(ctypes.c_float)]),
@@ -457,3 +485,116 @@ class System:
         _check(load().lb_integrate(self._h, PRECISIONS[precision], int(correct_every), _ptr(v0), float(t),
                                    float(dt), _ptr(out)))
         return out
+
+
+def request_bytes(N, precision="fp32", with_H=True):
+    """Server memory one request of dimension N holds from admission to completion."""
+    return int(load().lb_request_bytes(int(N), PRECISIONS[precision], int(bool(with_H))))
+
+
+def sched_simulate(arrival_ms, nbytes, service_ms, budget, slots, bypass_ms):
+    """Virtual-time replay of the server's admission policy (host only)."""
+    arrival = np.ascontiguousarray(arrival_ms, np.float64)
+    nb = np.ascontiguousarray(nbytes, np.int64)
+    service = np.ascontiguousarray(service_ms, np.float64)
+    n = len(arrival)
+    assert len(nb) == n and len(service) == n
+    start = np.zeros(n)
+    finish = np.zeros(n)
+    _check(load().lb_sched_simulate(n, _ptr(arrival), _ptr(nb), _ptr(service), int(budget), int(slots),
+                                    float(bypass_ms), _ptr(start), _ptr(finish)))
+    return start, finish
+
+
+def _result(r):
+    return {"state": r.state, "status": r.status, "engine": r.engine, "cluster": r.cluster,
+            "queue_ms": r.queue_ms, "latency_ms": r.latency_ms, "gpu_ms": r.gpu_ms}
+
+
+class Server:
+    """Serving form (lb_server_*).  Device tensors of a request are kept
+    referenced until the library no longer reads them."""
+
+    def __init__(self, budget_bytes, slots=16, bypass_ms=2000.0):
+        h = _vp()
+        _check(load().lb_server_create(int(budget_bytes), int(slots), float(bypass_ms), ctypes.byref(h)))
+        self._h = h
+        self._inputs = {}   # id -> (a, H, v0): read until LB_REQ_ASSEMBLED
+        self._outputs = {}  # id -> v_out: written until LB_REQ_DONE
+
+    def close(self):
+        if self._h:
+            load().lb_server_destroy(self._h)
+            self._h = None
+            self._inputs.clear()
+            self._outputs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_cluster(self, N, C):
+        _check(load().lb_server_set_cluster(self._h, int(N), int(C)))
+
+    def submit(self, a, v0, v_out, dt, nsteps, H=None, precision="fp32", correct_every=0, stream=None):
+        """Queue one realization; inputs must be complete in the order of
+        `stream` (default: torch's current stream) at this call."""
+        M = v0.numel()
+        N = int(round((M + 1) ** 0.5))
+        st = _stream(stream)
+        q = LbRequest(N, PRECISIONS[precision], int(correct_every), float(dt), int(nsteps), _ptr(H), _ptr(a),
+                      _ptr(v0), _ptr(v_out), st)
+        rid = ctypes.c_uint64()
+        _check(load().lb_submit(self._h, ctypes.byref(q), ctypes.byref(rid)))
+        self._inputs[rid.value] = (a, H, v0)
+        self._outputs[rid.value] = v_out
+        return rid.value
+
+    def _settle(self, rid, res):
+        if res.state >= LB_REQ_ASSEMBLED:
+            self._inputs.pop(rid, None)
+        if res.state >= LB_REQ_DONE:
+            self._outputs.pop(rid, None)
+
+    def poll(self, rid):
+        """Result dict once the request is done, None while it is pending."""
+        r = LbResult()
+        rc = load().lb_poll(self._h, int(rid), ctypes.byref(r))
+        self._settle(rid, r)
+        if rc == LB_EAGAIN:
+            return None
+        _check(rc)
+        return _result(r)
+
+    def state(self, rid):
+        r = LbResult()
+        rc = load().lb_poll(self._h, int(rid), ctypes.byref(r))
+        if rc not in (LB_OK, LB_EAGAIN):
+            _check(rc)
+        self._settle(rid, r)
+        return r.state
+
+    def wait(self, rid, timeout_ms=600_000.0):
+        r = LbResult()
+        rc = load().lb_wait(self._h, int(rid), float(timeout_ms), ctypes.byref(r))
+        self._settle(rid, r)
+        _check(rc)
+        return _result(r)
+
+    def stats(self):
+        p50, p99, thr = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = _c_i64()
+        _check(load().lb_server_stats(self._h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(thr),
+                                      ctypes.byref(n)))
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "throughput_per_s": thr.value, "completed": n.value}
+
+    def reset_stats(self):
+        _check(load().lb_server_reset_stats(self._h))
