@@ -49,6 +49,20 @@ def parse():
     p.add_argument("--count-terms", action="store_true", help="count the join terms W (extra pass)")
     p.add_argument("--algorithm", default="closed", choices=["closed", "join"],
                    help="dense R assembly: closed-form sums of the join (default) or every join term")
+    p.add_argument("--no-forms", action="store_true", help="skip the batched / serving / sparse / small-N lines")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-sparse", action="store_true")
+    p.add_argument("--no-small", action="store_true")
+    p.add_argument("--batch-count", type=int, default=512)
+    p.add_argument("--batch-steps", type=int, default=2000)
+    p.add_argument("--batch-fp64-sample", type=int, default=32)
+    p.add_argument("--serve-count", type=int, default=20)
+    p.add_argument("--serve-steps", type=int, default=5000)
+    p.add_argument("--serve-load", type=float, default=0.75)
+    p.add_argument("--serve-budget-gb", type=float, default=128.0)
+    p.add_argument("--sparse-n", type=int, default=2000)
+    p.add_argument("--sparse-steps", type=int, default=200)
     return p.parse_args()
 
 
@@ -250,6 +264,11 @@ def run_gb300(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, a, M, N)
+    forms = {}
+    if not args.no_forms:
+        del A, A32, work
+        torch.cuda.empty_cache()
+        forms = run_forms(args, dev, a200=a if N == 200 else None)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -300,6 +319,7 @@ def run_gb300(args):
         out["e2e"] = e2e
     if cpu:
         out["cpu_baseline"] = cpu
+    out.update(forms)
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -393,6 +413,299 @@ def cpu_baseline(args, a, M, N, rows=None):
     return {"value": len(s) / dt, "unit": "entries/s", "cores": num_threads(), "kind": "oracle",
             "sample": "%d full rows of R (%d entries) at N=%d; f/d enumeration setup %.1f s not timed"
                       % (len(s_rows), len(s), N, t_setup)}
+
+
+# ---------------------------------------------------------------- the other forms
+
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def run_forms(args, dev, a200=None):
+    """Measurements of the other workloads, outside the timed region of the
+    headline step: dense N=10 and N=50, the sparse ladder, the batched
+    ensemble and the serving loop."""
+    out = {}
+    if not args.no_small:
+        out["dense_n10"] = form_dense(args, dev, 10, 10_000, 1000)
+        out["dense_n50"] = form_dense(args, dev, 50, 10_000, 1050)
+    if not args.no_sparse:
+        out["sparse_ladder"] = form_sparse(args, dev)
+    if not args.no_batched:
+        out["batched"] = form_batched(args, dev)
+    if not args.no_serving:
+        out["serving"] = form_serving(args, dev, a200)
+    return out
+
+
+def form_dense(args, dev, N, steps, seed):
+    """One realization: assembly, FP64 RK4 and FP32-storage RK4 with the FP64
+    correction every 50 steps, `steps` steps each (rho0 = |0><0|, dt)."""
+    import torch
+
+    import paper_1912_01491_gb300 as lb
+    import workloads as wl
+    M = N * N - 1
+    H, a = wl.random_lindbladian_device(N, seed, device=dev)
+    B = lb.Basis(N)
+    h = B.expand(H).real.contiguous()
+    v0 = B.expand(torch.tensor(wl.pure_state(N, 0), device=dev)).real.contiguous()
+    A = torch.empty((M, M), dtype=torch.float64, device=dev)
+    K = torch.empty(M, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        kms = B.assemble_dense_timed(a, h=h, A=A, K=K, algorithm="closed")
+    A32 = lb.pack_fp32(A)
+    work = lb.rk4_workspace(M, dev)
+    ev = _events(4)
+    v64, v32 = v0.clone(), v0.clone()
+    lb.rk4_dense(A, K, v0.clone(), args.dt, 50, precision="fp64", work=work)
+    ev[0].record()
+    lb.rk4_dense(A, K, v64, args.dt, steps, precision="fp64", work=work)
+    ev[1].record()
+    lb.rk4_dense(A32, K, v32, args.dt, steps, precision="fp32", A64=A, correct_every=50, work=work)
+    ev[2].record()
+    torch.cuda.synchronize()
+    t64, t32 = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    err = float(torch.linalg.norm(v32 - v64) / torch.linalg.norm(v64))
+    rho = B.rho(v64)
+    B.close()
+    return {"N": N, "M": M, "steps": steps, "dt": args.dt, "assembly_ms": sum(kms.values()),
+            "entries_per_s": M * M / (sum(kms.values()) * 1e-3),
+            "rk4_fp64_ms": t64, "rk4_fp64_steps_per_s": steps / (t64 * 1e-3),
+            "rk4_fp32c_ms": t32, "rk4_fp32c_steps_per_s": steps / (t32 * 1e-3),
+            "fp32c_rel_err_vs_fp64": err,
+            "trace_rho_minus_1": float(abs(torch.diagonal(rho).real.sum() - 1.0)),
+            "note": "single realization on the stream engine (4 fused stage launches per step)"}
+
+
+def form_sparse(args, dev):
+    """Sparse ladder model: CSR assembly of Q + R and K, CSR RK4 (FP32 values
+    with FP64 correction every 50 steps, and FP64)."""
+    import torch
+
+    import paper_1912_01491_gb300 as lb
+    import workloads as wl
+    N = args.sparse_n
+    M = N * N - 1
+    H, L, g = wl.ladder_model(N, args.seed + 3)
+    B = lb.Basis(N)
+    l = B.expand(torch.tensor(L, device=dev))
+    nz = torch.nonzero(l.abs() > 0).flatten()
+    ch = [(g, nz, l[nz].contiguous())]
+    h = B.expand(torch.tensor(H, device=dev)).real.contiguous()
+    lb.Csr(B, h=h, channels=ch).close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c = lb.Csr(B, h=h, channels=ch)
+    torch.cuda.synchronize()
+    t_asm = time.perf_counter() - t0
+    rho0 = torch.zeros((N, N), dtype=torch.complex128, device=dev)
+    rho0[N - 1, N - 1] = 1.0
+    v0 = B.expand(rho0).real.contiguous()
+    work = lb.rk4_workspace(M, dev)
+    n = args.sparse_steps
+    res = {}
+    for prec, corr in (("fp32", 50), ("fp64", 0)):
+        v = v0.clone()
+        c.rk4(v, args.dt, 10, precision=prec, correct_every=corr, work=work)
+        ev = _events(2)
+        ev[0].record()
+        c.rk4(v, args.dt, n, precision=prec, correct_every=corr, work=work)
+        ev[1].record()
+        torch.cuda.synchronize()
+        res[prec] = ev[0].elapsed_time(ev[1])
+    nnz = c.nnz
+    # per stage: values + columns, row pointers, gathered x (once), Keff, v, acc, next x (FP64 + FP32)
+    stage_bytes = {"fp32": 8.0 * nnz + 8.0 * (M + 1) + 4.0 * M + 8.0 * M * 5 + 4.0 * M,
+                   "fp64": 12.0 * nnz + 8.0 * (M + 1) + 8.0 * M + 8.0 * M * 5}
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    gbs = {p: 4 * stage_bytes[p] * n / (res[p] * 1e-3) / 1e9 for p in res}
+    c.close()
+    B.close()
+    return {"N": N, "M": M, "nnz": nnz, "spgemm_terms": None, "assembly_s": t_asm,
+            "rk4_fp32c_steps_per_s": n / (res["fp32"] * 1e-3), "rk4_fp64_steps_per_s": n / (res["fp64"] * 1e-3),
+            "rk4_roofline": {"kernel": "k_stage_csr (fused SpMV + stage update)", "bound": "hbm",
+                             "achieved": gbs["fp32"], "peak": hbm, "unit": "GB/s",
+                             "frac": gbs["fp32"] / hbm if hbm else None,
+                             "algorithmic_bytes_per_step": 4 * stage_bytes["fp32"],
+                             "fp64_achieved_gbs": gbs["fp64"]},
+            "note": "FP32 row includes one FP64 correction SpMV every 50 steps in its time"}
+
+
+def form_batched(args, dev):
+    """Ensemble of random Lindbladians with N uniform in [4, 40]: assembly of
+    every realization, cluster-size tuning, one persistent launch per cluster
+    size over all realizations (FP32 storage, FP64 correction every 50 steps),
+    against the plain FP64 single-system path one realization at a time on a
+    sample."""
+    import numpy as np
+    import torch
+
+    import paper_1912_01491_gb300 as lb
+    import workloads as wl
+    count, steps, dt = args.batch_count, args.batch_steps, args.dt
+    Ns = [int(x) for x in wl.batch_sizes(count, args.seed + 11)]
+    inputs = []
+    for r, N in enumerate(Ns):
+        H, a = wl.random_lindbladian_device(N, args.seed + 100 + r, device=dev)
+        inputs.append((N, H, a))
+    bases = {N: lb.Basis(N) for N in sorted(set(Ns))}
+    hs, v0s = [], []
+    for r, (N, H, a) in enumerate(inputs):
+        B = bases[N]
+        hs.append(B.expand(H).real.contiguous())
+        rho0 = torch.zeros((N, N), dtype=torch.complex128, device=dev)
+        rho0[r % N, r % N] = 1.0
+        v0s.append(B.expand(rho0).real.contiguous())
+    b = lb.Batch(Ns)
+    vs = [v.clone() for v in v0s]
+    for r in range(count):
+        b.set(r, inputs[r][2], hs[r], vs[r])
+    b.assemble("closed")
+    torch.cuda.synchronize()
+    ev = _events(2)
+    ev[0].record()
+    b.assemble("closed")
+    ev[1].record()
+    torch.cuda.synchronize()
+    asm_ms = ev[0].elapsed_time(ev[1])
+    t0 = time.perf_counter()
+    choice = b.tune(width=6, probe_steps=20, dt=dt)
+    tune_s = time.perf_counter() - t0
+    int_ms = b.integrate(dt, steps, correct_every=50)
+    torch.cuda.synchronize()
+    # plain FP64, one realization at a time (assembly + RK4), on a sample
+    S = min(args.batch_fp64_sample, count)
+    errs = []
+    ev = _events(2)
+    ev[0].record()
+    outs = []
+    for r in range(S):
+        N = Ns[r]
+        M = N * N - 1
+        g = bases[N].assemble_dense(inputs[r][2], h=hs[r], algorithm="closed")
+        v = v0s[r].clone()
+        lb.rk4_dense(g["A"], g["K"], v, dt, steps, precision="fp64")
+        outs.append(v)
+    ev[1].record()
+    torch.cuda.synchronize()
+    fp64_ms = ev[0].elapsed_time(ev[1])
+    for r in range(S):
+        errs.append(float(torch.linalg.norm(vs[r] - outs[r]) / torch.linalg.norm(outs[r])))
+    Ms = np.array([n * n - 1 for n in Ns], dtype=np.float64)
+    for B in bases.values():
+        B.close()
+    b.close()
+    rate_b = count / ((asm_ms + int_ms) * 1e-3)
+    rate_1 = S / (fp64_ms * 1e-3)
+    hist = {int(c): int((np.asarray(choice) == c).sum()) for c in sorted(set(int(x) for x in choice))}
+    return {"realizations": count, "N_range": [4, 40], "steps": steps, "dt": dt,
+            "assembly_ms": asm_ms, "integrate_ms": int_ms, "tune_s": tune_s,
+            "realizations_per_s": rate_b,
+            "fp64_single_realizations_per_s": rate_1, "fp64_single_sample": S,
+            "speedup_vs_fp64_single": rate_b / rate_1,
+            "max_rel_err_vs_fp64": max(errs), "cluster_sizes": hist,
+            "rk4_stage_matrix_gb_per_s": float(4.0 * steps * (4.0 * Ms * Ms).sum() / (int_ms * 1e-3) / 1e9),
+            "note": "matrix bytes the stages consume per second (FP32 A read 4x per step); slices that stay "
+                    "in shared memory are not re-read from HBM, so this can exceed HBM bandwidth"}
+
+
+def form_serving(args, dev, a200=None):
+    """Poisson stream of realizations with N in {20, 50, 100, 150, 200}
+    through the server: FP32 storage for N <= 64 (cluster engine), BF16 above
+    (stream engine), FP64 correction every 50 steps, `serve_steps` RK4 steps.
+    Inputs are synthesised before submission (one realization per N, reused
+    by every request of that N; each request is assembled and integrated on
+    its own) and excluded from latency.  The arrival rate is `serve_load`
+    times the rate the measured alone-latencies can sustain."""
+    import numpy as np
+    import torch
+
+    import paper_1912_01491_gb300 as lb
+    import workloads as wl
+    Nset = (20, 50, 100, 150, 200)
+    steps, dt, corr = args.serve_steps, args.dt, 50
+    prec = {N: ("fp32" if N <= 64 else "bf16") for N in Nset}
+    pool, bases = {}, {}
+    for N in Nset:
+        H = torch.tensor(wl.gue_hamiltonian(N, args.seed + 500 + N), device=dev)
+        if N == 200 and a200 is not None:
+            a = a200
+        elif N <= 50:
+            a = wl.random_lindbladian_device(N, args.seed + 500 + N, device=dev)[1]
+        else:
+            a = wl.wishart_kossakowski_device(N, args.seed + 500 + N, device=dev)
+        pool[N] = (H, a)
+        bases[N] = lb.Basis(N)
+
+    def v0_for(N, k):
+        rho0 = torch.zeros((N, N), dtype=torch.complex128, device=dev)
+        rho0[k % N, k % N] = 1.0
+        return bases[N].expand(rho0).real.contiguous()
+
+    srv = lb.Server(int(args.serve_budget_gb * 2**30), slots=8, bypass_ms=2000.0)
+    # alone latencies (also warms the pool and the graph path)
+    alone = {}
+    for N in Nset:
+        H, a = pool[N]
+        v0 = v0_for(N, 0)
+        out = torch.empty_like(v0)
+        torch.cuda.synchronize()
+        rid = srv.submit(a, v0, out, dt, steps, H=H, precision=prec[N], correct_every=corr)
+        alone[N] = srv.wait(rid)["latency_ms"]
+    svc = float(np.mean([alone[N] for N in Nset]))
+    rate = args.serve_load * 1000.0 / svc  # requests / s
+    arr, Nreq = wl.serving_trace(args.serve_count, args.seed + 77, rate, Nset)
+    srv.reset_stats()
+    outs, ids = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(len(arr)):
+        N = int(Nreq[i])
+        v0 = v0_for(N, i + 1)
+        out = torch.empty_like(v0)
+        while time.perf_counter() - t0 < arr[i]:
+            time.sleep(0.0005)
+        H, a = pool[N]
+        ids.append(srv.submit(a, v0, out, dt, steps, H=H, precision=prec[N], correct_every=corr))
+        outs.append((N, i + 1, out))
+    res = [srv.wait(rid) for rid in ids]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    # trajectory error against FP64 for the N <= 100 requests (one per N)
+    errs = {}
+    for N in (20, 50, 100):
+        k = next((j for j, (n, _, _) in enumerate(outs) if n == N), None)
+        if k is None:
+            continue
+        n, seedk, out = outs[k]
+        H, a = pool[N]
+        B = bases[N]
+        g = B.assemble_dense(a, h=B.expand(H).real.contiguous(), algorithm="closed")
+        v = v0_for(N, seedk)
+        lb.rk4_dense(g["A"], g["K"], v, dt, steps, precision="fp64")
+        torch.cuda.synchronize()
+        errs[N] = float(torch.linalg.norm(out - v) / torch.linalg.norm(v))
+        del g
+    per_N = {}
+    for N in Nset:
+        lat = [r["latency_ms"] for r, n in zip(res, Nreq) if int(n) == N]
+        if lat:
+            per_N[N] = {"count": len(lat), "p50_ms": float(np.percentile(lat, 50)), "alone_ms": alone[N]}
+    srv.close()
+    for B in bases.values():
+        B.close()
+    return {"requests": len(arr), "steps": steps, "dt": dt, "correct_every": corr,
+            "precision": {str(N): prec[N] for N in Nset}, "arrival_rate_per_s": rate, "load": args.serve_load,
+            "p50_latency_ms": st["p50_ms"], "p99_latency_ms": st["p99_ms"],
+            "throughput_realizations_per_s": st["throughput_per_s"], "wall_s": wall,
+            "per_N": {str(k): v for k, v in per_N.items()},
+            "max_rel_err_vs_fp64": {str(k): v for k, v in errs.items()},
+            "budget_gb": args.serve_budget_gb, "slots": 8,
+            "note": "latency = submission to completion seen by the host; inputs synthesised before "
+                    "submission; p99 of %d requests is their maximum" % len(arr)}
 
 
 # ---------------------------------------------------------------- reference arm
