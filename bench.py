@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--serve-budget-gb", type=float, default=128.0)
     p.add_argument("--sparse-n", type=int, default=2000)
     p.add_argument("--sparse-steps", type=int, default=200)
+    p.add_argument("--only", default=None, choices=["dense_small", "sparse", "batched", "serving"],
+                   help="run one of the other workloads alone and print its JSON (profiling aid)")
     return p.parse_args()
 
 
@@ -516,12 +518,15 @@ def form_sparse(args, dev):
         torch.cuda.synchronize()
         res[prec] = ev[0].elapsed_time(ev[1])
     nnz = c.nnz
-    # per stage: values + columns, row pointers, gathered x (once), Keff, v, acc, next x (FP64 + FP32)
-    stage_bytes = {"fp32": 8.0 * nnz + 8.0 * (M + 1) + 4.0 * M + 8.0 * M * 5 + 4.0 * M,
-                   "fp64": 12.0 * nnz + 8.0 * (M + 1) + 8.0 * M + 8.0 * M * 5}
+    # per RK4 step (4 stages): values + columns and row pointers 4x; the stage
+    # vector gathered once per stage (FP32 or FP64); Keff and v read 4x, v
+    # written once; acc written (stage 1), read and written (2, 3), read (4);
+    # the next stage vector written 4x (FP32 copy only in FP32 mode)
+    step_bytes = {"fp32": 32.0 * nnz + 32.0 * (M + 1) + 16.0 * M + 32.0 * M + 40.0 * M + 48.0 * M + 16.0 * M,
+                  "fp64": 48.0 * nnz + 32.0 * (M + 1) + 32.0 * M + 32.0 * M + 40.0 * M + 48.0 * M + 32.0 * M}
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
-    gbs = {p: 4 * stage_bytes[p] * n / (res[p] * 1e-3) / 1e9 for p in res}
+    gbs = {p: step_bytes[p] * n / (res[p] * 1e-3) / 1e9 for p in res}
     c.close()
     B.close()
     return {"N": N, "M": M, "nnz": nnz, "spgemm_terms": None, "assembly_s": t_asm,
@@ -529,7 +534,7 @@ def form_sparse(args, dev):
             "rk4_roofline": {"kernel": "k_stage_csr (fused SpMV + stage update)", "bound": "hbm",
                              "achieved": gbs["fp32"], "peak": hbm, "unit": "GB/s",
                              "frac": gbs["fp32"] / hbm if hbm else None,
-                             "algorithmic_bytes_per_step": 4 * stage_bytes["fp32"],
+                             "algorithmic_bytes_per_step": step_bytes["fp32"],
                              "fp64_achieved_gbs": gbs["fp64"]},
             "note": "FP32 row includes one FP64 correction SpMV every 50 steps in its time"}
 
@@ -755,10 +760,28 @@ def run_reference(args):
     return out
 
 
+def run_only(args):
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    if args.only == "dense_small":
+        out = {"dense_n10": form_dense(args, dev, 10, 10_000, 1000),
+               "dense_n50": form_dense(args, dev, 50, 10_000, 1050)}
+    elif args.only == "sparse":
+        out = {"sparse_ladder": form_sparse(args, dev)}
+    elif args.only == "batched":
+        out = {"batched": form_batched(args, dev)}
+    else:
+        out = {"serving": form_serving(args, dev)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        run_only(args)
     else:
         run_gb300(args)
 

@@ -649,12 +649,62 @@ __global__ void __launch_bounds__(256) k_entries(BasisView B, AView A, const dou
   if (Aout) Aout[o] = q + r;
 }
 
+// Sign tables of the disjoint-edge closed form.  For an edge pair with
+// v = a_s < v' = b_s and (w, w') = (a_n, b_n) (wi = 0) or (b_n, a_n) (wi = 1),
+// every coefficient phase in the eight terms of the (S, S) and (S, J) sums
+// depends only on three vertex orders: b0 = [w < v], b1 = [v' < w],
+// b2 = [w' < v].  Bit (8 idx + 4 tn + 2 tl + {0: f term, 1: d term}) of
+// table wi is set when that term enters with a minus sign (idx = b0 + 2 b1 +
+// 4 b2; the minus of the d term and the conjugation of the wi = 0 reads are
+// included).
+constexpr int cp_(int t, bool x_lt_y) { return t == kS ? 0 : (x_lt_y ? 3 : 1); }
+constexpr int sf_(int ph) { return (ph & 3) == 1 ? 1 : -1; }
+constexpr int sd_(int ph) { return (ph & 3) == 0 ? 1 : -1; }
+constexpr unsigned long long disjoint_sign_table(int wi) {
+  unsigned long long T = 0;
+  for (int idx = 0; idx < 8; ++idx) {
+    const bool b0 = idx & 1, b1 = (idx >> 1) & 1, b2 = (idx >> 2) & 1;
+    const int isg = wi ? 1 : -1;
+    for (int tn = 0; tn < 2; ++tn) {
+      const int phn = cp_(tn, wi == 0);  // coef_phase(tn, w, w'): w < w' iff wi = 0
+      for (int tl = 0; tl < 2; ++tl) {
+        const int tk = 1 ^ tl, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+        const int sk = sf_(cp_(tk, b1) + cp_(tl, b0));
+        const int sf = sf_(phn + cp_(tjf, b2) + cp_(tl, !b0));
+        const int sd = sd_(phn + cp_(tjd, b2) + cp_(tl, !b0));
+        const unsigned long long nf = (sk * sf) < 0, nd = (-(sk * sd * isg)) < 0;
+        T |= nf << (idx * 8 + tn * 4 + tl * 2);
+        T |= nd << (idx * 8 + tn * 4 + tl * 2 + 1);
+      }
+    }
+  }
+  return T;
+}
+constexpr unsigned long long kDisjointSign0 = disjoint_sign_table(0);
+constexpr unsigned long long kDisjointSign1 = disjoint_sign_table(1);
+
+// x with its sign flipped when bit i of m is set (integer ops only)
+__device__ __forceinline__ double flip_if(double x, unsigned m, int i) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((unsigned long long)((m >> i) & 1u) << 63));
+}
+
+__device__ __noinline__ double neg_half_slow(double x) { return -0.5 * x; }
+
+// -x/2 with integer ops on the common path; the FP64 multiply only for zero,
+// subnormal, inf and nan inputs, in a call the compiler cannot if-convert.
+__device__ __forceinline__ double neg_half_nz(double x) {
+  const long long b = __double_as_longlong(x);
+  const long long ex = (b >> 52) & 0x7ff;
+  if (ex > 1 && ex < 0x7ff) return __longlong_as_double((b - (1LL << 52)) ^ (long long)(1ULL << 63));
+  return neg_half_slow(x);
+}
+
 // Closed-form pair x pair block, one thread per pair of edges (e(s), e(n))
 // computing the four entries (S/J of e(s)) x (S/J of e(n)): on disjoint
 // edges they are signed sums of the same eight entries of a (two per type
 // pair of the k- and j-edges for each of the two edge pairs (b_s, w), (a_s, w')),
 // read once for all four.  Lanes run over consecutive e(n) of one e(s).
-__global__ void __launch_bounds__(256) k_entries4_closed(BasisView B, AView A, const double* __restrict__ h,
+__global__ void __launch_bounds__(256, 4) k_entries4_closed(BasisView B, AView A, const double* __restrict__ h,
                                                          double* __restrict__ Aout, double* __restrict__ Qout,
                                                          double* __restrict__ Rout) {
   const int N = B.N;
@@ -665,7 +715,6 @@ __global__ void __launch_bounds__(256) k_entries4_closed(BasisView B, AView A, c
   if (pn >= P) return;
   const int32_t abs_ = __ldg(B.pair_ab + ps), abn = __ldg(B.pair_ab + pn);
   const int as = abs_ >> 16, bs = abs_ & 0xffff, an = abn >> 16, bn = abn & 0xffff;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // combo = ts * 2 + tn
   int shared = 0, cv = -1;
   if (as == an || as == bn) { ++shared; cv = as; }
   if (bs == an || bs == bn) { ++shared; cv = bs; }
@@ -674,71 +723,58 @@ __global__ void __launch_bounds__(256) k_entries4_closed(BasisView B, AView A, c
     // (S, S) terms times eps_wi and the (J, S) entry the (S, J) terms times
     // -eps_wi, with eps_0 = -1, eps_1 = +1 for every order of the four
     // vertices (the same entries of a, conjugated type pairs); so only the
-    // ts = S terms are formed and the J rows follow by sums and differences.
-    const int v = as, vp = bs;
-    double xs[2], xj[2];  // (S,S) and (S,J) partial sums per wi
+    // ts = S sums are formed and the J rows follow by sums and differences.
+    double xs[2], xj[2];
 #pragma unroll
     for (int wi = 0; wi < 2; ++wi) {
       const int w = wi ? bn : an, wp = wi ? an : bn;
-      const int64_t pk = pair_index_any(N, vp, w), pj = pair_index_any(N, v, wp);
-      // X[tj][tk] = a((v,w') tj, (v',w) tk); for wi = 0 the row of k is common to
-      // the warp and the conjugate a[k][j] is read (the sign of Im is flipped below)
-      double xr[2][2], xi[2][2];
-#pragma unroll
-      for (int tj = 0; tj < 2; ++tj)
-#pragma unroll
-        for (int tk = 0; tk < 2; ++tk) {
-          const int64_t j = tj * P + pj, k = tk * P + pk;
-          const double2 t = wi ? ldA(A, j, k) : ldA(A, k, j);
-          xr[tj][tk] = t.x;
-          xi[tj][tk] = t.y;
-        }
-      const int isg = wi ? 1 : -1;  // Im a_jk = isg * xi
-      const int ts = kS;
-      const int phs = coef_phase(ts, v, vp);
-#pragma unroll
-      for (int tn = 0; tn < 2; ++tn) {
-        const int phn = coef_phase(tn, w, wp);
-        double part = 0.0;
-#pragma unroll
-        for (int tl = 0; tl < 2; ++tl) {
-          const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
-          const int phl_wv = coef_phase(tl, w, v), phl_vw = coef_phase(tl, v, w);
-          const int sk = sgn_f(phs + coef_phase(tk, vp, w) + phl_wv);
-          const int sf = sgn_f(phn + coef_phase(tjf, wp, v) + phl_vw);
-          const int sd = sgn_d(phn + coef_phase(tjd, wp, v) + phl_vw);
-          part += sgn_mul(sk * sf, xr[tjf][tk]);
-          part -= sgn_mul(sk * sd * isg, xi[tjd][tk]);
-        }
-        if (tn == kS) xs[wi] = part; else xj[wi] = part;
-      }
+      const int64_t pk = pair_index_any(N, bs, w), pj = pair_index_any(N, as, wp);
+      // X[tj][tk] = a((as, w') tj, (bs, w) tk); for wi = 0 the k row is common
+      // to the warp, so a[k][j] is read (its conjugation is in the sign table)
+      const double2* base = wi ? A.a + pj * M + pk : A.a + pk * M + pj;
+      const int64_t oj = wi ? P * M : P, ok = wi ? P : P * M;
+      const double2 x00 = __ldg(base), x01 = __ldg(base + ok), x10 = __ldg(base + oj), x11 = __ldg(base + oj + ok);
+      const int idx = (w < as) | ((bs < w) << 1) | ((wp < as) << 2);
+      const unsigned m = (unsigned)((wi ? kDisjointSign1 : kDisjointSign0) >> (8 * idx)) & 0xffu;
+      // tn = S: tl = 0 -> (xr11, xi01), tl = 1 -> (xr00, xi10);
+      // tn = J: tl = 0 -> (xr01, xi11), tl = 1 -> (xr10, xi00)
+      xs[wi] = (flip_if(x11.x, m, 0) + flip_if(x01.y, m, 1)) + (flip_if(x00.x, m, 2) + flip_if(x10.y, m, 3));
+      xj[wi] = (flip_if(x01.x, m, 4) + flip_if(x11.y, m, 5)) + (flip_if(x10.x, m, 6) + flip_if(x00.y, m, 7));
     }
-    acc[0] = xs[0] + xs[1];  // (S, S)
-    acc[3] = xs[1] - xs[0];  // (J, J)
-    acc[1] = xj[0] + xj[1];  // (S, J)
-    acc[2] = xj[0] - xj[1];  // (J, S)
-  } else {
-    // edges meet: the D-section part in closed form (the l-pair part is added by
-    // k_shared_closed / k_same)
-    const int e1 = as == an, e2 = as == bn, e3 = bs == an, e4 = bs == bn;
-    const double cf = (double)(e1 - e2 - e3 + e4), cd = (double)(e1 + e2 - e3 - e4);
+    const double r[4] = {neg_half_nz(xs[0] + xs[1]), neg_half_nz(xj[0] + xj[1]), neg_half_nz(xj[0] - xj[1]),
+                         neg_half_nz(xs[1] - xs[0])};  // (S,S), (S,J), (J,S), (J,J)
 #pragma unroll
     for (int ts = 0; ts < 2; ++ts)
 #pragma unroll
       for (int tn = 0; tn < 2; ++tn) {
-        const int64_t sb = (int64_t)(1 - ts) * P + ps, n = (int64_t)tn * P + pn, nb = (int64_t)(1 - tn) * P + pn;
-        const double2 a1 = ldA_row(A, nb, sb), a2 = ldA_row(A, n, sb);
-        const double sgs = ts == kS ? 1.0 : -1.0, sgn = tn == kS ? 1.0 : -1.0;
-        acc[ts * 2 + tn] = sgs * (sgn * a1.x * cf - a2.y * cd);
+        const int64_t o = ((int64_t)ts * P + ps) * M + (int64_t)tn * P + pn;
+        if (Rout) Rout[o] = r[ts * 2 + tn];
+        if (Qout) Qout[o] = 0.0;  // Q vanishes on disjoint edges
+        if (Aout) Aout[o] = r[ts * 2 + tn];
       }
+    return;
   }
+  // edges meet: the D-section part in closed form (the l-pair part is added by
+  // k_shared_closed / k_same)
+  double acc[4];
+  const int e1 = as == an, e2 = as == bn, e3 = bs == an, e4 = bs == bn;
+  const double cf = (double)(e1 - e2 - e3 + e4), cd = (double)(e1 + e2 - e3 - e4);
+#pragma unroll
+  for (int ts = 0; ts < 2; ++ts)
+#pragma unroll
+    for (int tn = 0; tn < 2; ++tn) {
+      const int64_t sb = (int64_t)(1 - ts) * P + ps, n = (int64_t)tn * P + pn, nb = (int64_t)(1 - tn) * P + pn;
+      const double2 a1 = ldA_row(A, nb, sb), a2 = ldA_row(A, n, sb);
+      const double sgs = ts == kS ? 1.0 : -1.0, sgn = tn == kS ? 1.0 : -1.0;
+      acc[ts * 2 + tn] = sgs * (sgn * a1.x * cf - a2.y * cd);
+    }
 #pragma unroll
   for (int ts = 0; ts < 2; ++ts)
 #pragma unroll
     for (int tn = 0; tn < 2; ++tn) {
       const int64_t s = (int64_t)ts * P + ps, n = (int64_t)tn * P + pn;
       double q = 0.0;
-      if (h != nullptr && shared != 0) {
+      if (h != nullptr) {
         const Elem es = make_pair(ts, as, bs), en = make_pair(tn, an, bn);
         if (shared == 1) {
           const int p = (as == cv) ? bs : as, qv = (an == cv) ? bn : an;
@@ -753,7 +789,7 @@ __global__ void __launch_bounds__(256) k_entries4_closed(BasisView B, AView A, c
       const int64_t o = s * M + n;
       if (Rout) Rout[o] = r;
       if (Qout) Qout[o] = q;
-      if (Aout) Aout[o] = shared ? q + r : r;  // Q vanishes on disjoint edges
+      if (Aout) Aout[o] = q + r;
     }
 }
 

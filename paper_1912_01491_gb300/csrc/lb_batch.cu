@@ -116,10 +116,9 @@ __global__ void __launch_bounds__(256) k_rk4_batch(const BItem* __restrict__ ite
           const float* row = resident ? Rs + i * M : it.A32 + (r0 + i) * M;
           float a = 0.f;
           for (int64_t n = lane; n < M; n += 32) a = fmaf(row[n], x32[n], a);
-          double y = (double)a;
-          for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+          for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
           if (lane == 0) {
-            const double k = y + keff[i];
+            const double k = (double)a + keff[i];
             double nx;
             if (stage == 1) {
               acc[i] = k;

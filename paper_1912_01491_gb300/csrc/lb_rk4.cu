@@ -137,75 +137,70 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 }
 
 // ---------------------------------------------------------------- CSR
-// Eight lanes per row (four rows per warp): lanes stride the row's entries,
-// the partial sums meet in a segmented shuffle, and lane 0 of the group runs
-// the same stage epilogue as the dense kernel.
-constexpr int kCsrLanes = 8;
-
-template <int PREC>
-__device__ __forceinline__ double csr_row_dot(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                              const void* __restrict__ val, const double* __restrict__ x,
-                                              const float* __restrict__ x32, int64_t s, int sub, bool valid) {
-  // every lane of the warp reaches the shuffle below; rows past M add nothing
-  const int64_t b = valid ? __ldg(rowptr + s) : 0, e = valid ? __ldg(rowptr + s + 1) : 0;
-  double t;
-  if (PREC == LB_FP64) {
-    const double* __restrict__ v = static_cast<const double*>(val);
-    double a0 = 0.0;
-    for (int64_t q = b + sub; q < e; q += kCsrLanes) a0 = fma(__ldcs(v + q), __ldg(x + __ldcs(col + q)), a0);
-    t = a0;
-  } else {
-    const float* __restrict__ v = static_cast<const float*>(val);
-    float a0 = 0.f;
-    for (int64_t q = b + sub; q < e; q += kCsrLanes) a0 = fmaf(__ldcs(v + q), __ldg(x32 + __ldcs(col + q)), a0);
-    t = (double)a0;
-  }
-  for (int o = kCsrLanes / 2; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o, kCsrLanes);
-  return t;
-}
-
+// One thread per row: the rows of these systems are short (about seven
+// entries for the ladder model), so a thread walks its row's entries itself,
+// with no shuffle, and every lane runs the stage epilogue for its own row.
+// The state loads are issued before the row walk so that their latency
+// overlaps the row-pointer -> column -> gathered-x chain.  In FP32 mode the
+// row sum is FP32 and only the FP32 copy of the next stage vector is written
+// (the FP64 copy is not read by the FP32 product).
 template <int PREC, int STAGE>
 __global__ void __launch_bounds__(256)
     k_stage_csr(int64_t M, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                 const void* __restrict__ val, const double* __restrict__ Keff, const double* __restrict__ x,
                 const float* __restrict__ x32, double* __restrict__ xn, float* __restrict__ xn32,
                 double* __restrict__ acc, double* __restrict__ v, double h) {
-  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kCsrLanes;
-  const int sub = threadIdx.x % kCsrLanes;
-  const double y = csr_row_dot<PREC>(rowptr, col, val, x, x32, s, sub, s < M);
-  if (sub != 0 || s >= M) return;
-  const double k = y + Keff[s];
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  const double kf = __ldcs(Keff + s), vs = __ldcs(v + s);
+  const double ac = STAGE > 1 ? __ldcs(acc + s) : 0.0;
+  const int64_t b = __ldg(rowptr + s), e = __ldg(rowptr + s + 1);
+  double y;
+  if (PREC == LB_FP64) {
+    const double* __restrict__ vv = static_cast<const double*>(val);
+    double t = 0.0;
+#pragma unroll 4
+    for (int64_t q = b; q < e; ++q) t = fma(__ldcs(vv + q), __ldg(x + __ldcs(col + q)), t);
+    y = t;
+  } else {
+    const float* __restrict__ vv = static_cast<const float*>(val);
+    float t = 0.f;
+#pragma unroll 4
+    for (int64_t q = b; q < e; ++q) t = fmaf(__ldcs(vv + q), __ldg(x32 + __ldcs(col + q)), t);
+    y = (double)t;
+  }
+  const double k = y + kf;
   double nx;
   if (STAGE == 1) {
     acc[s] = k;
-    nx = v[s] + 0.5 * h * k;
+    nx = vs + 0.5 * h * k;
   } else if (STAGE == 2) {
-    acc[s] += 2.0 * k;
-    nx = v[s] + 0.5 * h * k;
+    acc[s] = ac + 2.0 * k;
+    nx = vs + 0.5 * h * k;
   } else if (STAGE == 3) {
-    acc[s] += 2.0 * k;
-    nx = v[s] + h * k;
+    acc[s] = ac + 2.0 * k;
+    nx = vs + h * k;
   } else {
-    nx = v[s] + (h / 6.0) * (acc[s] + k);
+    nx = vs + (h / 6.0) * (ac + k);
     v[s] = nx;
   }
-  xn[s] = nx;
-  if (PREC != LB_FP64) xn32[s] = (float)nx;
+  if (PREC == LB_FP64)
+    xn[s] = nx;
+  else
+    xn32[s] = (float)nx;
 }
 
-// c = (A64 - A32) v on the CSR pattern;  Keff = K + c.
+// c = (A64 - A32) v on the CSR pattern;  Keff = K + c.  One thread per row.
 __global__ void __launch_bounds__(256)
     k_correction_csr(int64_t M, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                      const double* __restrict__ v64, const float* __restrict__ v32, const double* __restrict__ x,
                      const double* __restrict__ K, double* __restrict__ Keff) {
-  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kCsrLanes;
-  const int sub = threadIdx.x % kCsrLanes;
-  const bool valid = s < M;  // all lanes reach the shuffle
-  const int64_t b = valid ? rowptr[s] : 0, e = valid ? rowptr[s + 1] : 0;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  const int64_t b = rowptr[s], e = rowptr[s + 1];
   double t = 0.0;
-  for (int64_t q = b + sub; q < e; q += kCsrLanes) t = fma(v64[q] - (double)v32[q], x[col[q]], t);
-  for (int o = kCsrLanes / 2; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o, kCsrLanes);
-  if (sub == 0 && valid) Keff[s] = K[s] + t;
+  for (int64_t q = b; q < e; ++q) t = fma(v64[q] - (double)v32[q], x[col[q]], t);
+  Keff[s] = K[s] + t;
 }
 
 __global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
@@ -294,7 +289,7 @@ template <int PREC>
 cudaError_t run_steps_csr(int64_t M, const int64_t* rowptr, const int32_t* col, const void* val,
                           const double* val64, int correct_every, const double* K, double* v, double dt,
                           int64_t nsteps, const Work& w, cudaStream_t st) {
-  const unsigned grid = (unsigned)((M * kCsrLanes + 255) / 256);
+  const unsigned grid = (unsigned)((M + 255) / 256);
   cudaError_t e;
   e = cudaMemcpyAsync(w.X, v, sizeof(double) * M, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
