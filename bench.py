@@ -471,8 +471,23 @@ def form_dense(args, dev, N, steps, seed):
     t64, t32 = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     err = float(torch.linalg.norm(v32 - v64) / torch.linalg.norm(v64))
     rho = B.rho(v64)
+    # the same trajectory in one persistent FP64 launch (cluster size tuned)
+    pers = None
+    if N <= 64:
+        vp = v0.clone()
+        bt = lb.Batch([N])
+        bt.set(0, a, h, vp)
+        bt.assemble("closed")
+        bt.set_precision("fp64")
+        C = int(bt.tune(width=4, probe_steps=50, dt=args.dt)[0])
+        ms = bt.integrate(args.dt, steps)
+        torch.cuda.synchronize()
+        bt.close()
+        pers = {"ms": ms, "steps_per_s": steps / (ms * 1e-3), "cluster": C,
+                "rel_diff_vs_stream_fp64": float(torch.linalg.norm(vp - v64) / torch.linalg.norm(v64))}
     B.close()
     return {"N": N, "M": M, "steps": steps, "dt": args.dt, "assembly_ms": sum(kms.values()),
+            "rk4_fp64_persistent": pers,
             "entries_per_s": M * M / (sum(kms.values()) * 1e-3),
             "rk4_fp64_ms": t64, "rk4_fp64_steps_per_s": steps / (t64 * 1e-3),
             "rk4_fp32c_ms": t32, "rk4_fp32c_steps_per_s": steps / (t32 * 1e-3),

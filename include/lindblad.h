@@ -299,6 +299,11 @@ int lb_batch_set_cluster(lb_batch_t *b, int r, int C);
  * (states restored afterwards).  choice (optional, count ints) receives it. */
 int lb_batch_tune(lb_batch_t *b, int width, int probe_steps, double dt, void *stream, int *choice);
 
+/* Storage and arithmetic of lb_batch_integrate and lb_batch_tune: LB_FP32
+ * (default; FP32 matrix and products, FP64 state and optional correction) or
+ * LB_FP64 (FP64 matrix and products; correct_every is ignored). */
+int lb_batch_set_precision(lb_batch_t *b, int precision);
+
 /* RK4 for every realization, nsteps steps of dt, FP32 matrix with FP32
  * products, FP64 state, FP64 defect correction every correct_every steps (0:
  * none).  One persistent cluster launch per cluster-size group: a cluster

@@ -7,12 +7,14 @@
 // from a global counter by the cluster's rank-0 block).  Each block of the
 // cluster owns a contiguous slice of rows; its slice of the FP32 matrix stays
 // in shared memory for the whole 4 x nsteps stages when it fits, else it is
-// re-read from global memory (L2) every stage.  After each stage every block
-// publishes its slice of the next stage vector in its shared memory, the
-// cluster barrier orders the writes, and every block gathers the full vector
-// from its peers through distributed shared memory (double-buffered, one
-// barrier per stage).  State, stage combination and the FP64 defect
-// correction stay FP64, as in the single-system kernels.
+// re-read from global memory (L2) every stage.  Each block keeps the whole
+// stage vector in its shared memory, double-buffered: while it reads one copy
+// for the product, the epilogue of every row stores the row's next-stage
+// value into the other copy of every block of the cluster (distributed
+// shared memory stores, one lane per destination block), and one cluster
+// barrier per stage orders those stores before the next stage reads them.
+// State, stage combination and the FP64 defect correction stay FP64, as in
+// the single-system kernels.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -30,7 +32,7 @@ using BItem = lbi::BatchItem;
 struct SmemLayout {
   int64_t slice, mmax;
   bool resident;
-  size_t off_x32, off_x64, off_pub32, off_pub64, off_v, off_acc, off_keff, off_r, off_item, total;
+  size_t off_x32, off_x64, off_v, off_acc, off_keff, off_r, off_item, total;
 };
 
 inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -42,10 +44,8 @@ SmemLayout layout(int64_t mmax, int C, bool resident) {
   L.resident = resident;
   size_t o = 0;
   L.off_item = o; o = a16(o + 16);
-  L.off_x32 = o; o = a16(o + sizeof(float) * mmax);
+  L.off_x32 = o; o = a16(o + sizeof(float) * 2 * mmax);
   L.off_x64 = o; o = a16(o + sizeof(double) * mmax);
-  L.off_pub32 = o; o = a16(o + sizeof(float) * 2 * L.slice);
-  L.off_pub64 = o; o = a16(o + sizeof(double) * L.slice);
   L.off_v = o; o = a16(o + sizeof(double) * L.slice);
   L.off_acc = o; o = a16(o + sizeof(double) * L.slice);
   L.off_keff = o; o = a16(o + sizeof(double) * L.slice);
@@ -53,6 +53,37 @@ SmemLayout layout(int64_t mmax, int C, bool resident) {
   if (resident) o = a16(o + sizeof(float) * L.slice * mmax);
   L.total = o;
   return L;
+}
+
+// Classical RK4 stage epilogue for one row (Table 1 step 3.1): k = A x + K,
+// acc and the next stage input as in the single-system kernels.
+__device__ __forceinline__ double stage_update(int stage, double k, double vi, double acci, double dt,
+                                               double* acc_out, double* v_out) {
+  if (stage == 1) {
+    *acc_out = k;
+    return vi + 0.5 * dt * k;
+  }
+  if (stage == 2) {
+    *acc_out = acci + 2.0 * k;
+    return vi + 0.5 * dt * k;
+  }
+  if (stage == 3) {
+    *acc_out = acci + 2.0 * k;
+    return vi + dt * k;
+  }
+  const double nx = vi + (dt / 6.0) * (acci + k);
+  *v_out = nx;
+  return nx;
+}
+
+// Takes the next realization for this cluster; every block returns the same
+// queue position.
+__device__ __forceinline__ int next_item(cg::cluster_group& cluster, int rank, int* item_slot, int* counter) {
+  if (rank == 0 && threadIdx.x == 0) *item_slot = atomicAdd(counter, 1);
+  cluster.sync();
+  const int qi = *cluster.map_shared_rank(item_slot, 0);
+  cluster.sync();  // every block has read the slot before rank 0 may overwrite it
+  return qi;
 }
 
 __global__ void __launch_bounds__(256) k_rk4_batch(const BItem* __restrict__ items, const int* __restrict__ order,
@@ -63,21 +94,16 @@ __global__ void __launch_bounds__(256) k_rk4_batch(const BItem* __restrict__ ite
   const int C = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   int* item_slot = reinterpret_cast<int*>(smem + L.off_item);
-  float* x32 = reinterpret_cast<float*>(smem + L.off_x32);
+  float* x32 = reinterpret_cast<float*>(smem + L.off_x32);  // [2][mmax]
   double* x64 = reinterpret_cast<double*>(smem + L.off_x64);
-  float* pub32 = reinterpret_cast<float*>(smem + L.off_pub32);
-  double* pub64 = reinterpret_cast<double*>(smem + L.off_pub64);
   double* vv = reinterpret_cast<double*>(smem + L.off_v);
   double* acc = reinterpret_cast<double*>(smem + L.off_acc);
   double* keff = reinterpret_cast<double*>(smem + L.off_keff);
   float* Rs = reinterpret_cast<float*>(smem + L.off_r);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t mmax = L.mmax;
   while (true) {
-    if (rank == 0 && threadIdx.x == 0) *item_slot = atomicAdd(counter, 1);
-    cluster.sync();
-    const int* slot0 = cluster.map_shared_rank(item_slot, 0);
-    const int qi = *slot0;
-    cluster.sync();  // every block has read the slot before rank 0 may overwrite it
+    const int qi = next_item(cluster, rank, item_slot, counter);
     if (qi >= nitems) break;
     const BItem it = items[order[qi]];
     const int64_t M = it.M;
@@ -85,7 +111,7 @@ __global__ void __launch_bounds__(256) k_rk4_batch(const BItem* __restrict__ ite
     const int64_t r0 = rank * slice, r1 = r0 + slice < M ? r0 + slice : M;
     const int64_t nrow = r1 > r0 ? r1 - r0 : 0;
     const bool resident = L.resident;
-    // own rows: state, K, (resident) matrix slice; full initial vector
+    const bool correct = correct_every > 0 && it.A64 != nullptr;
     for (int64_t i = threadIdx.x; i < nrow; i += blockDim.x) {
       vv[i] = it.v[r0 + i];
       keff[i] = it.K[r0 + i];
@@ -97,9 +123,8 @@ __global__ void __launch_bounds__(256) k_rk4_batch(const BItem* __restrict__ ite
       x64[n] = it.v[n];
     }
     __syncthreads();
-    int buf = 0;
     for (int64_t t = 0; t < nsteps; ++t) {
-      if (correct_every > 0 && it.A64 != nullptr && t % correct_every == 0) {
+      if (correct && t % correct_every == 0) {
         // FP64 defect c = (A64 - A32) v on own rows, with the full current v in x64
         for (int64_t i = warp; i < nrow; i += nw) {
           const int64_t s = r0 + i;
@@ -111,49 +136,121 @@ __global__ void __launch_bounds__(256) k_rk4_batch(const BItem* __restrict__ ite
         }
         __syncthreads();
       }
+      const bool push64 = correct && (t + 1) % correct_every == 0;
       for (int stage = 1; stage <= 4; ++stage) {
+        const float* xc = x32 + ((stage - 1) & 1) * mmax;
+        float* xn = x32 + (stage & 1) * mmax;
         for (int64_t i = warp; i < nrow; i += nw) {
           const float* row = resident ? Rs + i * M : it.A32 + (r0 + i) * M;
           float a = 0.f;
-          for (int64_t n = lane; n < M; n += 32) a = fmaf(row[n], x32[n], a);
+          for (int64_t n = lane; n < M; n += 32) a = fmaf(row[n], xc[n], a);
           for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+          // every lane holds the row sum: all form the update, lane 0 keeps
+          // the state, lane q < C stores the value into block q
+          const double vi = vv[i], ai = acc[i];
+          __syncwarp();
+          double acc_new = ai, v_new = vi;
+          const double nx = stage_update(stage, (double)a + keff[i], vi, ai, dt, &acc_new, &v_new);
           if (lane == 0) {
-            const double k = (double)a + keff[i];
-            double nx;
-            if (stage == 1) {
-              acc[i] = k;
-              nx = vv[i] + 0.5 * dt * k;
-            } else if (stage == 2) {
-              acc[i] += 2.0 * k;
-              nx = vv[i] + 0.5 * dt * k;
-            } else if (stage == 3) {
-              acc[i] += 2.0 * k;
-              nx = vv[i] + dt * k;
-            } else {
-              nx = vv[i] + (dt / 6.0) * (acc[i] + k);
-              vv[i] = nx;
-              pub64[i] = nx;
-            }
-            pub32[buf * L.slice + i] = (float)nx;
+            acc[i] = acc_new;
+            vv[i] = v_new;
+          }
+          if (lane < C) {
+            *cluster.map_shared_rank(xn + r0 + i, lane) = (float)nx;
+            if (stage == 4 && push64) *cluster.map_shared_rank(x64 + r0 + i, lane) = nx;
           }
         }
-        cluster.sync();  // slices of the next stage vector are published
-        for (int q = 0; q < C; ++q) {
-          const int64_t q0 = q * slice, q1 = q0 + slice < M ? q0 + slice : M;
-          if (q1 <= q0) continue;
-          const float* src = cluster.map_shared_rank(pub32 + buf * L.slice, q);
-          for (int64_t n = threadIdx.x; n < q1 - q0; n += blockDim.x) x32[q0 + n] = src[n];
-          if (stage == 4 && correct_every > 0 && it.A64 != nullptr && (t + 1) % correct_every == 0) {
-            const double* s64 = cluster.map_shared_rank(pub64, q);
-            for (int64_t n = threadIdx.x; n < q1 - q0; n += blockDim.x) x64[q0 + n] = s64[n];
-          }
-        }
-        __syncthreads();
-        buf ^= 1;
+        cluster.sync();  // every block's copy of the next stage vector is complete
       }
     }
     for (int64_t i = threadIdx.x; i < nrow; i += blockDim.x) it.v[r0 + i] = vv[i];
-    cluster.sync();  // peers are done reading this realization's published slices
+    cluster.sync();  // all blocks are done with this realization's buffers
+  }
+}
+
+// FP64 form of the same kernel: the matrix slice (resident or streamed) and
+// the exchanged stage vector are FP64, products are FP64 FMAs and there is
+// no correction.  For small M the per-stage work is a few microseconds, so
+// one persistent launch replaces 4 launches per step.
+struct SmemLayout64 {
+  int64_t slice, mmax;
+  bool resident;
+  size_t off_item, off_x, off_v, off_acc, off_keff, off_r, total;
+};
+
+SmemLayout64 layout64(int64_t mmax, int C, bool resident) {
+  SmemLayout64 L;
+  L.mmax = mmax;
+  L.slice = (mmax + C - 1) / C;
+  L.resident = resident;
+  size_t o = 0;
+  L.off_item = o; o = a16(o + 16);
+  L.off_x = o; o = a16(o + sizeof(double) * 2 * mmax);
+  L.off_v = o; o = a16(o + sizeof(double) * L.slice);
+  L.off_acc = o; o = a16(o + sizeof(double) * L.slice);
+  L.off_keff = o; o = a16(o + sizeof(double) * L.slice);
+  L.off_r = o;
+  if (resident) o = a16(o + sizeof(double) * L.slice * mmax);
+  L.total = o;
+  return L;
+}
+
+__global__ void __launch_bounds__(256) k_rk4_batch64(const BItem* __restrict__ items, const int* __restrict__ order,
+                                                     int nitems, int* __restrict__ counter, int64_t nsteps,
+                                                     double dt, SmemLayout64 L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  int* item_slot = reinterpret_cast<int*>(smem + L.off_item);
+  double* x = reinterpret_cast<double*>(smem + L.off_x);  // [2][mmax]
+  double* vv = reinterpret_cast<double*>(smem + L.off_v);
+  double* acc = reinterpret_cast<double*>(smem + L.off_acc);
+  double* keff = reinterpret_cast<double*>(smem + L.off_keff);
+  double* Rs = reinterpret_cast<double*>(smem + L.off_r);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t mmax = L.mmax;
+  while (true) {
+    const int qi = next_item(cluster, rank, item_slot, counter);
+    if (qi >= nitems) break;
+    const BItem it = items[order[qi]];
+    const int64_t M = it.M;
+    const int64_t slice = (M + C - 1) / C;
+    const int64_t r0 = rank * slice, r1 = r0 + slice < M ? r0 + slice : M;
+    const int64_t nrow = r1 > r0 ? r1 - r0 : 0;
+    const bool resident = L.resident;
+    for (int64_t i = threadIdx.x; i < nrow; i += blockDim.x) {
+      vv[i] = it.v[r0 + i];
+      keff[i] = it.K[r0 + i];
+    }
+    if (resident)
+      for (int64_t e = threadIdx.x; e < nrow * M; e += blockDim.x) Rs[e] = it.A64[r0 * M + e];
+    for (int64_t n = threadIdx.x; n < M; n += blockDim.x) x[n] = it.v[n];
+    __syncthreads();
+    for (int64_t t = 0; t < nsteps; ++t) {
+      for (int stage = 1; stage <= 4; ++stage) {
+        const double* xc = x + ((stage - 1) & 1) * mmax;
+        double* xn = x + (stage & 1) * mmax;
+        for (int64_t i = warp; i < nrow; i += nw) {
+          const double* row = resident ? Rs + i * M : it.A64 + (r0 + i) * M;
+          double a = 0.0;
+          for (int64_t n = lane; n < M; n += 32) a = fma(row[n], xc[n], a);
+          for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+          const double vi = vv[i], ai = acc[i];
+          __syncwarp();
+          double acc_new = ai, v_new = vi;
+          const double nx = stage_update(stage, a + keff[i], vi, ai, dt, &acc_new, &v_new);
+          if (lane == 0) {
+            acc[i] = acc_new;
+            vv[i] = v_new;
+          }
+          if (lane < C) *cluster.map_shared_rank(xn + r0 + i, lane) = nx;
+        }
+        cluster.sync();
+      }
+    }
+    for (int64_t i = threadIdx.x; i < nrow; i += blockDim.x) it.v[r0 + i] = vv[i];
+    cluster.sync();
   }
 }
 
@@ -170,6 +267,7 @@ struct lb_batch {
   std::vector<double*> A64, K;
   std::vector<float*> A32;
   std::vector<int> cluster;  // chosen cluster size per realization
+  int precision = LB_FP32;   // storage and arithmetic of the integration
   BItem* d_items = nullptr;
   int* d_order = nullptr;
   int* d_counter = nullptr;
@@ -230,16 +328,25 @@ SmemLayout pick_layout(int64_t mmax, int C) {
   return L;
 }
 
-// Launch configuration of k_rk4_batch for n items at cluster size C; the
-// number of clusters is what the device can hold at once, capped at n.  The
-// dynamic shared-memory limit is raised to the device maximum once (the same
-// value from every thread), so concurrent launches never see a smaller limit.
-cudaError_t configure(int C, const SmemLayout& L, int n, cudaStream_t st, cudaLaunchConfig_t* cfg,
+SmemLayout64 pick_layout64(int64_t mmax, int C) {
+  const size_t cap = (size_t)smem_optin();
+  SmemLayout64 L = layout64(mmax, C, true);
+  if (L.total > cap) L = layout64(mmax, C, false);
+  if (L.total > cap) L.total = 0;
+  return L;
+}
+
+// Launch configuration of a batched kernel (func) for n items at cluster size
+// C with smem bytes of dynamic shared memory; the number of clusters is what
+// the device can hold at once, capped at n.  The dynamic shared-memory limit
+// is raised to the device maximum (the same value from every thread), so
+// concurrent launches never see a smaller limit.
+cudaError_t configure(const void* func, int C, size_t smem, int n, cudaStream_t st, cudaLaunchConfig_t* cfg,
                       cudaLaunchAttribute* attr) {
-  cudaError_t e = cudaFuncSetAttribute(k_rk4_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+  cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
   if (e != cudaSuccess) return e;
   if (C > 8) {
-    e = cudaFuncSetAttribute(k_rk4_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
   *cfg = cudaLaunchConfig_t{};
@@ -248,13 +355,13 @@ cudaError_t configure(int C, const SmemLayout& L, int n, cudaStream_t st, cudaLa
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg->blockDim = dim3(256, 1, 1);
-  cfg->dynamicSmemBytes = L.total;
+  cfg->dynamicSmemBytes = smem;
   cfg->stream = st;
   cfg->attrs = attr;
   cfg->numAttrs = 1;
   cfg->gridDim = dim3((unsigned)C, 1, 1);
   int clusters = 0;
-  e = cudaOccupancyMaxActiveClusters(&clusters, k_rk4_batch, cfg);
+  e = cudaOccupancyMaxActiveClusters(&clusters, func, cfg);
   if (e != cudaSuccess) return e;
   if (clusters < 1) return cudaErrorInvalidConfiguration;
   clusters = std::min<int>(clusters, n);
@@ -273,18 +380,21 @@ cudaError_t batch_run_group(lb_batch* b, const std::vector<int>& ids, int C, int
   }
   int64_t mmax = 0;
   for (int r : ids) mmax = std::max<int64_t>(mmax, b->M[r]);
-  const SmemLayout L = pick_layout(mmax, C);
-  if (L.total == 0) return cudaErrorInvalidConfiguration;
+  const bool f64 = b->precision == LB_FP64;
+  const SmemLayout L = f64 ? SmemLayout{} : pick_layout(mmax, C);
+  const SmemLayout64 L64 = f64 ? pick_layout64(mmax, C) : SmemLayout64{};
+  if ((f64 ? L64.total : L.total) == 0) return cudaErrorInvalidConfiguration;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  cudaError_t e = configure(C, L, (int)ids.size(), st, &cfg, attr);
+  cudaError_t e = f64 ? configure((const void*)k_rk4_batch64, C, L64.total, (int)ids.size(), st, &cfg, attr)
+                      : configure((const void*)k_rk4_batch, C, L.total, (int)ids.size(), st, &cfg, attr);
   if (e != cudaSuccess) return e;
   // items in decreasing order of work (largest first)
   std::vector<int> ord(ids.begin(), ids.end());
   std::sort(ord.begin(), ord.end(), [&](int x, int y) { return b->M[x] > b->M[y]; });
   std::vector<BItem> host(b->count);
   for (int r = 0; r < b->count; ++r)
-    host[r] = BItem{b->M[r], b->A32[r], correct_every > 0 ? b->A64[r] : nullptr, b->K[r], b->v[r]};
+    host[r] = BItem{b->M[r], b->A32[r], (correct_every > 0 || f64) ? b->A64[r] : nullptr, b->K[r], b->v[r]};
   if ((e = cudaMemcpyAsync(b->d_items, host.data(), sizeof(BItem) * b->count, cudaMemcpyHostToDevice, st)) !=
       cudaSuccess)
     return e;
@@ -298,8 +408,12 @@ cudaError_t batch_run_group(lb_batch* b, const std::vector<int>& ids, int C, int
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
   }
-  e = cudaLaunchKernelEx(&cfg, k_rk4_batch, (const BItem*)b->d_items, (const int*)b->d_order, (int)ord.size(),
-                         b->d_counter, nsteps, dt, correct_every, L);
+  if (f64)
+    e = cudaLaunchKernelEx(&cfg, k_rk4_batch64, (const BItem*)b->d_items, (const int*)b->d_order, (int)ord.size(),
+                           b->d_counter, nsteps, dt, L64);
+  else
+    e = cudaLaunchKernelEx(&cfg, k_rk4_batch, (const BItem*)b->d_items, (const int*)b->d_order, (int)ord.size(),
+                           b->d_counter, nsteps, dt, correct_every, L);
   note_launch(1);
   if (ms) {
     cudaEventRecord(e1, st);
@@ -328,7 +442,7 @@ cudaError_t batch_launch_async(const BatchItem* items, int n, int C, int64_t nst
   if (L.total == 0) return cudaErrorInvalidConfiguration;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  cudaError_t e = configure(C, L, n, st, &cfg, attr);
+  cudaError_t e = configure((const void*)k_rk4_batch, C, L.total, n, st, &cfg, attr);
   if (e != cudaSuccess) return e;
   std::vector<int> ord(n);
   for (int i = 0; i < n; ++i) ord[i] = i;
@@ -452,6 +566,15 @@ int lb_batch_set_cluster(lb_batch_t* b, int r, int C) {
     return LB_EINVAL;
   }
   b->cluster[r] = C;
+  return LB_OK;
+}
+
+int lb_batch_set_precision(lb_batch_t* b, int precision) {
+  if (!b || (precision != LB_FP32 && precision != LB_FP64)) {
+    lbi::set_error("lb_batch_set_precision: bad arguments (LB_FP32 or LB_FP64)");
+    return LB_EINVAL;
+  }
+  b->precision = precision;
   return LB_OK;
 }
 

@@ -98,6 +98,7 @@ def load():
         "lb_batch_set": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
         "lb_batch_assemble": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
         "lb_batch_set_cluster": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+        "lb_batch_set_precision": (ctypes.c_int, [_vp, ctypes.c_int]),
         "lb_batch_tune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp, _vp]),
         "lb_batch_integrate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, _c_i64, _vp,
                                               ctypes.POINTER(ctypes.c_float)]),
@@ -425,6 +426,10 @@ class Batch:
 
     def set_cluster(self, r, C):
         _check(load().lb_batch_set_cluster(self._h, int(r), int(C)))
+
+    def set_precision(self, precision):
+        """"fp32" (default) or "fp64" for integrate and tune."""
+        _check(load().lb_batch_set_precision(self._h, PRECISIONS[precision]))
 
     def tune(self, width=6, probe_steps=20, dt=1e-3, stream=None):
         choice = np.zeros(len(self.Ns), np.int32)

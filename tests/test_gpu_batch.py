@@ -169,3 +169,46 @@ def test_batch_degenerate_and_errors():
     for r in range(2):
         assert torch.equal(ens.v[r], ens.v0[r])
     b.close()
+
+
+@pytest.mark.parametrize("C", [1, 4, 16])
+def test_batch_fp64_matches_single_system(C):
+    """FP64 persistent form: same RK4 in FP64 arithmetic, against the FP64
+    single-system trajectory within 1e-12 (summation order differs)."""
+    ens = _Ens([3, 6, 10, 17, 29], 7600, 1e-3, 300)
+    b = ens.batch()
+    b.set_precision("fp64")
+    for r in range(len(ens.Ns)):
+        b.set_cluster(r, C)
+    b.integrate(ens.dt, ens.steps)
+    errs = ens.errors()
+    b.close()
+    assert max(errs) < 1e-12, errs
+
+
+def test_batch_fp64_n10_full_trajectory_vs_oracle():
+    """Dense N = 10, rho0 = |0><0|, t = 10, dt = 1e-3 (10^4 steps) in one
+    persistent FP64 launch, against the oracle's RK4 within 1e-12 ||v||."""
+    N, dt, steps = 10, 1e-3, 10_000
+    H, a = _inputs(N, 1010)
+    lb = lbm()
+    with Oracle(N) as o:
+        h, _ = o.expand(H)
+        A = o.Q(h.real) + o.R(a)
+        K = o.K(a)
+        v0 = o.expand(wl.pure_state(N, 0))[0].real
+        ref, _ = ora_rk4(A, K, v0, dt, steps)
+    with lb.Basis(N) as B:
+        hd = B.expand(torch.tensor(H, device="cuda")).real.contiguous()
+    ad = torch.tensor(a, device="cuda")
+    v = torch.tensor(v0, device="cuda")
+    b = lb.Batch([N])
+    b.set(0, ad, hd, v)
+    b.assemble("closed")
+    b.set_precision("fp64")
+    choice = b.tune(width=4, probe_steps=20, dt=dt)
+    b.integrate(dt, steps)
+    torch.cuda.synchronize()
+    b.close()
+    got = v.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref), choice
