@@ -683,9 +683,96 @@ constexpr unsigned long long disjoint_sign_table(int wi) {
 constexpr unsigned long long kDisjointSign0 = disjoint_sign_table(0);
 constexpr unsigned long long kDisjointSign1 = disjoint_sign_table(1);
 
-// x with its sign flipped when bit i of m is set (integer ops only)
-__device__ __forceinline__ double flip_if(double x, unsigned m, int i) {
-  return __longlong_as_double(__double_as_longlong(x) ^ ((unsigned long long)((m >> i) & 1u) << 63));
+// Fixed-point summation of the disjoint-edge terms.  GB300's FP64 unit is
+// narrow (2 lanes per clock per SM) while the integer pipes are 64 lanes
+// wide, so the eight signed terms of a group are added exactly as 64-bit
+// integers instead of with FP64 adds: each term's 53-bit significand is
+// placed at bit 57 of an int64 for the group's largest exponent E and shifted
+// right by E - e_i (truncation error < 2^-57 of the largest term per term),
+// the signed sums are formed in int64 (|sum| < 2^61 for 8 terms), and the
+// result is rounded once to the nearest double, with the -1/2 of Eq. (09)
+// applied to the exponent and sign.  Zero sums give +0; inf/nan inputs and
+// results below the normal range take the FP64 path.
+struct FxTerm {
+  unsigned long long mant;  // significand with the implicit bit
+  int e;                    // biased exponent (subnormals: 1)
+  unsigned neg;             // sign bit
+};
+
+__device__ __forceinline__ FxTerm fx_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  FxTerm t;
+  t.mant = (b & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(ef != 0) << 52);
+  t.e = ef ? ef : 1;
+  t.neg = (unsigned)(b >> 63);
+  return t;
+}
+
+// term aligned to exponent E, negated when its sign bit XOR flip is set
+__device__ __forceinline__ long long fx_align(const FxTerm& t, int E, unsigned flip) {
+  const int sh = E - t.e;
+  const unsigned long long m = sh < 63 ? ((t.mant << 5) >> sh) : 0ull;
+  return ((t.neg ^ flip) & 1u) ? -(long long)m : (long long)m;
+}
+
+// -s/2 * 2^(E - 1080) as a double (s in units of 2^(E - 1080)); ok = false
+// when the result is below the normal range
+__device__ __forceinline__ double fx_neg_half(long long s, int E, bool& ok) {
+  ok = true;
+  if (s == 0) return 0.0;
+  const bool neg = s < 0;
+  const unsigned long long mag = neg ? (unsigned long long)(-s) : (unsigned long long)s;
+  const int lz = __clzll((long long)mag);
+  // value = mag * 2^(E - 1080) = 2^(63 - lz) * 1.f * 2^(E - 1080); times 1/2
+  int biased = (63 - lz) + E - 1080 + 1023 - 1;
+  const unsigned long long norm = mag << lz;  // top bit at 63
+  unsigned long long mant = norm >> 11;
+  const unsigned long long rem = norm & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ++mant;
+  if (mant >> 53) {
+    mant >>= 1;
+    ++biased;
+  }
+  if (biased <= 0) {
+    ok = false;
+    return 0.0;
+  }
+  const unsigned long long bits = ((unsigned long long)(!neg) << 63) | ((unsigned long long)biased << 52) |
+                                  (mant & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
+
+// Both outputs of one group of the disjoint closed form: with the four terms
+// of edge pair wi = 0 (p[0..3]) and wi = 1 (p[4..7]) and their table signs
+// (bit i of flips), out0 = -1/2 (sum0 + sum1), out1 = -1/2 (sum1 - sum0).
+__device__ __forceinline__ void fx_group(const double* p, unsigned flips, double& out0, double& out1) {
+  FxTerm t[8];
+  int E = 1;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    t[i] = fx_split(p[i]);
+    E = max(E, t[i].e);
+  }
+  bool ok0 = true, ok1 = true;
+  if (E < 0x7ff) {
+    long long s0 = 0, s1 = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s0 += fx_align(t[i], E, flips >> i);
+#pragma unroll
+    for (int i = 4; i < 8; ++i) s1 += fx_align(t[i], E, flips >> i);
+    out0 = fx_neg_half(s0 + s1, E, ok0);
+    out1 = fx_neg_half(s1 - s0, E, ok1);
+  }
+  if (E == 0x7ff || !ok0 || !ok1) {  // inf/nan input or a sum below the normal range
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s0 += ((flips >> i) & 1u) ? -p[i] : p[i];
+#pragma unroll
+    for (int i = 4; i < 8; ++i) s1 += ((flips >> i) & 1u) ? -p[i] : p[i];
+    out0 = -0.5 * (s0 + s1);
+    out1 = -0.5 * (s1 - s0);
+  }
 }
 
 __device__ __noinline__ double neg_half_slow(double x) { return -0.5 * x; }
@@ -724,7 +811,9 @@ __global__ void __launch_bounds__(256, 4) k_entries4_closed(BasisView B, AView A
     // -eps_wi, with eps_0 = -1, eps_1 = +1 for every order of the four
     // vertices (the same entries of a, conjugated type pairs); so only the
     // ts = S sums are formed and the J rows follow by sums and differences.
-    double xs[2], xj[2];
+    // group S: the terms of the (S, S) / (J, J) pair; group J: (S, J) / (J, S)
+    double gs[8], gj[8];
+    unsigned fs = 0, fj = 0;
 #pragma unroll
     for (int wi = 0; wi < 2; ++wi) {
       const int w = wi ? bn : an, wp = wi ? an : bn;
@@ -738,11 +827,24 @@ __global__ void __launch_bounds__(256, 4) k_entries4_closed(BasisView B, AView A
       const unsigned m = (unsigned)((wi ? kDisjointSign1 : kDisjointSign0) >> (8 * idx)) & 0xffu;
       // tn = S: tl = 0 -> (xr11, xi01), tl = 1 -> (xr00, xi10);
       // tn = J: tl = 0 -> (xr01, xi11), tl = 1 -> (xr10, xi00)
-      xs[wi] = (flip_if(x11.x, m, 0) + flip_if(x01.y, m, 1)) + (flip_if(x00.x, m, 2) + flip_if(x10.y, m, 3));
-      xj[wi] = (flip_if(x01.x, m, 4) + flip_if(x11.y, m, 5)) + (flip_if(x10.x, m, 6) + flip_if(x00.y, m, 7));
+      gs[4 * wi + 0] = x11.x;
+      gs[4 * wi + 1] = x01.y;
+      gs[4 * wi + 2] = x00.x;
+      gs[4 * wi + 3] = x10.y;
+      gj[4 * wi + 0] = x01.x;
+      gj[4 * wi + 1] = x11.y;
+      gj[4 * wi + 2] = x10.x;
+      gj[4 * wi + 3] = x00.y;
+      fs |= (m & 0xfu) << (4 * wi);
+      fj |= ((m >> 4) & 0xfu) << (4 * wi);
     }
-    const double r[4] = {neg_half_nz(xs[0] + xs[1]), neg_half_nz(xj[0] + xj[1]), neg_half_nz(xj[0] - xj[1]),
-                         neg_half_nz(xs[1] - xs[0])};  // (S,S), (S,J), (J,S), (J,J)
+    // (S,S) = -1/2 (xs0 + xs1), (J,J) = -1/2 (xs1 - xs0); (S,J) = -1/2 (xj0 + xj1),
+    // (J,S) = -1/2 (xj0 - xj1) = -(-1/2 (xj1 - xj0))
+    double r[4];
+    fx_group(gs, fs, r[0], r[3]);
+    double jm;
+    fx_group(gj, fj, r[1], jm);
+    r[2] = -jm;
 #pragma unroll
     for (int ts = 0; ts < 2; ++ts)
 #pragma unroll

@@ -76,6 +76,35 @@ __device__ __forceinline__ double stage_update(int stage, double k, double vi, d
   return nx;
 }
 
+// Lanes per row: small rows are shared by fewer lanes so that one warp
+// instruction of the FP64 epilogue serves 32 / W rows.
+__device__ __forceinline__ int row_group_width(int64_t M) {
+  return M >= 256 ? 32 : M >= 96 ? 16 : M >= 32 ? 8 : 4;
+}
+
+// Partial dot product of one lane of a W-lane row group: four independent
+// accumulators when the row is long (loads of four iterations in flight),
+// one when it is short (no extra adds, which matter for FP64).
+template <class T>
+__device__ __forceinline__ T group_dot(const T* __restrict__ row, const T* __restrict__ x, int64_t M, int sub,
+                                       int W) {
+  int64_t n = sub;
+  T a0 = T(0);
+  if (M >= 16 * (int64_t)W) {
+    T a1 = T(0), a2 = T(0), a3 = T(0);
+    for (; n + 3 * W < M; n += 4 * W) {
+      a0 = fma(row[n], x[n], a0);
+      a1 = fma(row[n + W], x[n + W], a1);
+      a2 = fma(row[n + 2 * W], x[n + 2 * W], a2);
+      a3 = fma(row[n + 3 * W], x[n + 3 * W], a3);
+    }
+    for (; n < M; n += W) a0 = fma(row[n], x[n], a0);
+    return (a0 + a1) + (a2 + a3);
+  }
+  for (; n < M; n += W) a0 = fma(row[n], x[n], a0);
+  return a0;
+}
+
 // Takes the next realization for this cluster; every block returns the same
 // queue position.
 __device__ __forceinline__ int next_item(cg::cluster_group& cluster, int rank, int* item_slot, int* counter) {
@@ -137,27 +166,35 @@ __global__ void __launch_bounds__(256) k_rk4_batch(const BItem* __restrict__ ite
         __syncthreads();
       }
       const bool push64 = correct && (t + 1) % correct_every == 0;
+      const int W = row_group_width(M), G = 32 / W, g = lane / W, sub = lane % W;
       for (int stage = 1; stage <= 4; ++stage) {
         const float* xc = x32 + ((stage - 1) & 1) * mmax;
         float* xn = x32 + (stage & 1) * mmax;
-        for (int64_t i = warp; i < nrow; i += nw) {
-          const float* row = resident ? Rs + i * M : it.A32 + (r0 + i) * M;
+        for (int64_t i0 = (int64_t)warp * G; i0 < nrow; i0 += (int64_t)nw * G) {
+          const int64_t i = i0 + g;
+          const bool valid = i < nrow;  // every lane reaches the shuffles
           float a = 0.f;
-          for (int64_t n = lane; n < M; n += 32) a = fmaf(row[n], xc[n], a);
-          for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-          // every lane holds the row sum: all form the update, lane 0 keeps
-          // the state, lane q < C stores the value into block q
-          const double vi = vv[i], ai = acc[i];
-          __syncwarp();
-          double acc_new = ai, v_new = vi;
-          const double nx = stage_update(stage, (double)a + keff[i], vi, ai, dt, &acc_new, &v_new);
-          if (lane == 0) {
-            acc[i] = acc_new;
-            vv[i] = v_new;
+          if (valid) {
+            const float* row = resident ? Rs + i * M : it.A32 + (r0 + i) * M;
+            a = group_dot(row, xc, M, sub, W);
           }
-          if (lane < C) {
-            *cluster.map_shared_rank(xn + r0 + i, lane) = (float)nx;
-            if (stage == 4 && push64) *cluster.map_shared_rank(x64 + r0 + i, lane) = nx;
+          for (int o = W >> 1; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+          // every lane of the group holds the row sum: all form the update,
+          // lane 0 of the group keeps the state, lanes store the value into
+          // blocks sub, sub + W, ...
+          const double vi = valid ? vv[i] : 0.0, ai = valid ? acc[i] : 0.0, ki = valid ? keff[i] : 0.0;
+          __syncwarp();
+          if (valid) {
+            double acc_new = ai, v_new = vi;
+            const double nx = stage_update(stage, (double)a + ki, vi, ai, dt, &acc_new, &v_new);
+            if (sub == 0) {
+              acc[i] = acc_new;
+              vv[i] = v_new;
+            }
+            for (int q = sub; q < C; q += W) {
+              *cluster.map_shared_rank(xn + r0 + i, q) = (float)nx;
+              if (stage == 4 && push64) *cluster.map_shared_rank(x64 + r0 + i, q) = nx;
+            }
           }
         }
         cluster.sync();  // every block's copy of the next stage vector is complete
@@ -227,24 +264,31 @@ __global__ void __launch_bounds__(256) k_rk4_batch64(const BItem* __restrict__ i
       for (int64_t e = threadIdx.x; e < nrow * M; e += blockDim.x) Rs[e] = it.A64[r0 * M + e];
     for (int64_t n = threadIdx.x; n < M; n += blockDim.x) x[n] = it.v[n];
     __syncthreads();
+    const int W = row_group_width(M), G = 32 / W, g = lane / W, sub = lane % W;
     for (int64_t t = 0; t < nsteps; ++t) {
       for (int stage = 1; stage <= 4; ++stage) {
         const double* xc = x + ((stage - 1) & 1) * mmax;
         double* xn = x + (stage & 1) * mmax;
-        for (int64_t i = warp; i < nrow; i += nw) {
-          const double* row = resident ? Rs + i * M : it.A64 + (r0 + i) * M;
+        for (int64_t i0 = (int64_t)warp * G; i0 < nrow; i0 += (int64_t)nw * G) {
+          const int64_t i = i0 + g;
+          const bool valid = i < nrow;
           double a = 0.0;
-          for (int64_t n = lane; n < M; n += 32) a = fma(row[n], xc[n], a);
-          for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-          const double vi = vv[i], ai = acc[i];
-          __syncwarp();
-          double acc_new = ai, v_new = vi;
-          const double nx = stage_update(stage, a + keff[i], vi, ai, dt, &acc_new, &v_new);
-          if (lane == 0) {
-            acc[i] = acc_new;
-            vv[i] = v_new;
+          if (valid) {
+            const double* row = resident ? Rs + i * M : it.A64 + (r0 + i) * M;
+            a = group_dot(row, xc, M, sub, W);
           }
-          if (lane < C) *cluster.map_shared_rank(xn + r0 + i, lane) = nx;
+          for (int o = W >> 1; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+          const double vi = valid ? vv[i] : 0.0, ai = valid ? acc[i] : 0.0, ki = valid ? keff[i] : 0.0;
+          __syncwarp();
+          if (valid) {
+            double acc_new = ai, v_new = vi;
+            const double nx = stage_update(stage, a + ki, vi, ai, dt, &acc_new, &v_new);
+            if (sub == 0) {
+              acc[i] = acc_new;
+              vv[i] = v_new;
+            }
+            for (int q = sub; q < C; q += W) *cluster.map_shared_rank(xn + r0 + i, q) = nx;
+          }
         }
         cluster.sync();
       }
