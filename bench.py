@@ -328,6 +328,23 @@ def run_gb300(args):
     return out
 
 
+# DRAM bytes (read + write) per launch of a kernel from one ncu capture on a
+# smaller case, with the units that capture processed; scaled to a launch of
+# the bench size by units.  Kept only for the kernel version the capture saw.
+NCU_TRAFFIC = {
+    "k_entries (pair x pair)": {"N": 100, "bytes": 2.848769e9 + 0.779408e9,
+                                "units": lambda N: (N * (N - 1.0)) ** 2,
+                                "source": "profiles/k_entries4_closed_n100.md"},
+}
+
+
+def ncu_traffic(kernel, N):
+    t = NCU_TRAFFIC.get(kernel)
+    if t is None:
+        return None, None
+    return t["bytes"] * t["units"](N) / t["units"](t["N"]), t["source"]
+
+
 def assembly_roofline(algorithm, top, top_ms, N, M, W, fp64_peak, peaks):
     """Roofline of the dominant assembly kernel (algorithmic work per launch
     over its event-timed launch duration)."""
@@ -337,8 +354,10 @@ def assembly_roofline(algorithm, top, top_ms, N, M, W, fp64_peak, peaks):
     if top.startswith("k_entries") and algorithm == "closed":
         # reads every a entry of the pair x pair block once, writes A there once
         byts = 24.0 * P2 * P2
+        traffic, src = ncu_traffic(top, N)
         return {"kernel": top, "bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": byts / t / 1e9 / hbm if hbm else None, "traffic": None,
+                "frac": byts / t / 1e9 / hbm if hbm else None, "traffic": traffic,
+                "traffic_source": src and ("%s, scaled from N=100 by (2P)^2" % src),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "algorithmic_bytes_per_launch": byts}
     if top.startswith("k_entries"):
