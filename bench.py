@@ -332,9 +332,9 @@ def run_gb300(args):
 # smaller case, with the units that capture processed; scaled to a launch of
 # the bench size by units.  Kept only for the kernel version the capture saw.
 NCU_TRAFFIC = {
-    "k_entries (pair x pair)": {"N": 100, "bytes": 2.848769e9 + 0.779408e9,
-                                "units": lambda N: (N * (N - 1.0)) ** 2,
-                                "source": "profiles/k_entries4_closed_n100.md"},
+    "k_entries (pair x pair; closed: disjoint edges by vertex quadruple)": {
+        "N": 100, "bytes": 1.223730e9 + 1.040116e9, "units": lambda N: N * (N - 1.0) * (N - 2.0) * (N - 3.0),
+        "source": "profiles/k_disjoint4_n100.md"},
 }
 
 
@@ -357,7 +357,7 @@ def assembly_roofline(algorithm, top, top_ms, N, M, W, fp64_peak, peaks):
         traffic, src = ncu_traffic(top, N)
         return {"kernel": top, "bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm, "unit": "GB/s",
                 "frac": byts / t / 1e9 / hbm if hbm else None, "traffic": traffic,
-                "traffic_source": src and ("%s, scaled from N=100 by (2P)^2" % src),
+                "traffic_source": src and ("%s, scaled from N=100 by the number of vertex quadruples" % src),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "algorithmic_bytes_per_launch": byts}
     if top.startswith("k_entries"):

@@ -685,14 +685,14 @@ constexpr unsigned long long kDisjointSign1 = disjoint_sign_table(1);
 
 // Fixed-point summation of the disjoint-edge terms.  GB300's FP64 unit is
 // narrow (2 lanes per clock per SM) while the integer pipes are 64 lanes
-// wide, so the eight signed terms of a group are added exactly as 64-bit
-// integers instead of with FP64 adds: each term's 53-bit significand is
-// placed at bit 57 of an int64 for the group's largest exponent E and shifted
-// right by E - e_i (truncation error < 2^-57 of the largest term per term),
-// the signed sums are formed in int64 (|sum| < 2^61 for 8 terms), and the
-// result is rounded once to the nearest double, with the -1/2 of Eq. (09)
-// applied to the exponent and sign.  Zero sums give +0; inf/nan inputs and
-// results below the normal range take the FP64 path.
+// wide, so the signed terms of an entry are added exactly as 64-bit integers
+// instead of with FP64 adds: each value's 53-bit significand is placed at bit
+// 57 of an int64 for the largest exponent E among the values that are summed
+// together, and shifted right by E - e_i (truncation error < 2^-57 of the
+// largest value per term).  The signed sums of 8 terms are formed in int64
+// (|sum| < 2^61), and each result is rounded once to the nearest double, with
+// the -1/2 of Eq. (09) applied to the exponent and sign.  Values that are not
+// finite, or too small for the exponent arithmetic, take the FP64 path.
 struct FxTerm {
   unsigned long long mant;  // significand with the implicit bit
   int e;                    // biased exponent (subnormals: 1)
@@ -709,6 +709,11 @@ __device__ __forceinline__ FxTerm fx_split(double x) {
   return t;
 }
 
+// biased exponent of x as fx_split counts it (subnormals: 1)
+__device__ __forceinline__ int fx_exponent(double x) {
+  return max((__double2hiint(x) >> 20) & 0x7ff, 1);
+}
+
 // term aligned to exponent E, negated when its sign bit XOR flip is set
 __device__ __forceinline__ long long fx_align(const FxTerm& t, int E, unsigned flip) {
   const int sh = E - t.e;
@@ -716,182 +721,294 @@ __device__ __forceinline__ long long fx_align(const FxTerm& t, int E, unsigned f
   return ((t.neg ^ flip) & 1u) ? -(long long)m : (long long)m;
 }
 
-// -s/2 * 2^(E - 1080) as a double (s in units of 2^(E - 1080)); ok = false
-// when the result is below the normal range
-__device__ __forceinline__ double fx_neg_half(long long s, int E, bool& ok) {
-  ok = true;
-  if (s == 0) return 0.0;
-  const bool neg = s < 0;
-  const unsigned long long mag = neg ? (unsigned long long)(-s) : (unsigned long long)s;
-  const int lz = __clzll((long long)mag);
-  // value = mag * 2^(E - 1080) = 2^(63 - lz) * 1.f * 2^(E - 1080); times 1/2
-  int biased = (63 - lz) + E - 1080 + 1023 - 1;
-  const unsigned long long norm = mag << lz;  // top bit at 63
-  unsigned long long mant = norm >> 11;
-  const unsigned long long rem = norm & 0x7FFull;
-  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ++mant;
-  if (mant >> 53) {
-    mant >>= 1;
-    ++biased;
-  }
-  if (biased <= 0) {
-    ok = false;
-    return 0.0;
-  }
-  const unsigned long long bits = ((unsigned long long)(!neg) << 63) | ((unsigned long long)biased << 52) |
-                                  (mant & 0xFFFFFFFFFFFFFull);
-  return __longlong_as_double((long long)bits);
+
+
+// ---------------------------------------------------------------------------
+// Disjoint pair x pair entries by vertex quadruple.  For four vertices
+// p < q < r < t the three perfect matchings
+//   m = 0: (p,q) | (r,t),   m = 1: (p,r) | (q,t),   m = 2: (p,t) | (q,r)
+// each give two ordered edge pairs (s, n), four type pairs each: 24 entries.
+// The closed form of an entry on matching m reads the a-block between the
+// two edges of each other matching (the k/j edge pairs of Eq. (09)), so the
+// 24 entries of the quadruple read the same 12 entries of a (one orientation
+// per matching; the other follows from a = a^dagger), and with the vertex
+// order fixed every sign is a compile-time constant.  Labels 0..3 stand for
+// p, q, r, t.
+constexpr int kQuadEdge[3][2][2] = {{{0, 1}, {2, 3}}, {{0, 2}, {1, 3}}, {{0, 3}, {1, 2}}};
+
+struct QuadTerm {
+  int y, i, j, c, neg;  // value D[y][i][j][c] (c: 0 re, 1 im), negated if neg
+};
+
+constexpr int quad_edge_of(int x, int y) {  // 2 m + e for the edge (x < y)
+  for (int m = 0; m < 3; ++m)
+    for (int e = 0; e < 2; ++e)
+      if (kQuadEdge[m][e][0] == x && kQuadEdge[m][e][1] == y) return 2 * m + e;
+  return -1;
 }
 
-// Both outputs of one group of the disjoint closed form: with the four terms
-// of edge pair wi = 0 (p[0..3]) and wi = 1 (p[4..7]) and their table signs
-// (bit i of flips), out0 = -1/2 (sum0 + sum1), out1 = -1/2 (sum1 - sum0).
-__device__ __forceinline__ void fx_group(const double* p, unsigned flips, double& out0, double& out1) {
-  FxTerm t[8];
+// Term `slot` (0..3: the (S,S) sum, 4..7: the (S,J) sum) of edge pair wi for
+// the output of matching m with s = edge ori, n = edge 1 - ori.  The loaded
+// values D[y][i][j] are a[e1 i][e2 j] for y = 0, 1 and a[e2 i][e1 j] for
+// y = 2 (e1 = the edge holding p); the sums take X[tj][tk] = a_jk for wi = 1
+// and its conjugate for wi = 0, as the sign tables assume.
+constexpr QuadTerm quad_term(int m, int ori, int wi, int slot) {
+  const int as = kQuadEdge[m][ori][0], bs = kQuadEdge[m][ori][1];
+  const int an = kQuadEdge[m][1 - ori][0], bn = kQuadEdge[m][1 - ori][1];
+  const int w = wi ? bn : an, wp = wi ? an : bn;
+  const int j0 = as < wp ? as : wp, j1 = as < wp ? wp : as;
+  const int me = quad_edge_of(j0, j1);
+  const int y = me / 2;
+  const bool jfirst = (me % 2) == 0;
+  const int idx = (w < as ? 1 : 0) | ((bs < w ? 1 : 0) << 1) | ((wp < as ? 1 : 0) << 2);
+  const unsigned mb = (unsigned)(((wi ? kDisjointSign1 : kDisjointSign0) >> (8 * idx)) & 0xffu);
+  // slots: (tj, tk, comp) = (1,1,re) (0,1,im) (0,0,re) (1,0,im) | (0,1,re) (1,1,im) (1,0,re) (0,0,im)
+  constexpr int stj[8] = {1, 0, 0, 1, 0, 1, 1, 0};
+  constexpr int stk[8] = {1, 1, 0, 0, 1, 1, 0, 0};
+  constexpr int sc[8] = {0, 1, 0, 1, 0, 1, 0, 1};
+  const int tj = stj[slot], tk = stk[slot], c = sc[slot];
+  int neg = (int)((mb >> slot) & 1u);
+  // a_jk = L_y[tj][tk] when j is e1 of matching y, else conj(L_y[tk][tj])
+  const int t1 = jfirst ? tj : tk, t2 = jfirst ? tk : tj;
+  const int conj = (wi == 0 ? 1 : 0) + (jfirst ? 0 : 1);
+  if (c == 1 && (conj & 1)) neg ^= 1;
+  QuadTerm r{y, t1, t2, c, neg};
+  if (y == 2) {  // loaded as a[e2][e1] = conj(L_2) transposed
+    r.i = t2;
+    r.j = t1;
+    if (c == 1) r.neg ^= 1;
+  }
+  return r;
+}
+
+template <class T, int MM, int ORI, int WI, int SLOT>
+__device__ __forceinline__ T quad_val(const T (&D)[3][2][2][2]) {
+  constexpr QuadTerm q = quad_term(MM, ORI, WI, SLOT);
+  return q.neg ? -D[q.y][q.i][q.j][q.c] : D[q.y][q.i][q.j][q.c];
+}
+
+template <class T, int MM, int ORI, int WI>
+__device__ __forceinline__ T quad_sum(const T (&D)[3][2][2][2], int half) {
+  return half == 0 ? (quad_val<T, MM, ORI, WI, 0>(D) + quad_val<T, MM, ORI, WI, 1>(D)) +
+                         (quad_val<T, MM, ORI, WI, 2>(D) + quad_val<T, MM, ORI, WI, 3>(D))
+                   : (quad_val<T, MM, ORI, WI, 4>(D) + quad_val<T, MM, ORI, WI, 5>(D)) +
+                         (quad_val<T, MM, ORI, WI, 6>(D) + quad_val<T, MM, ORI, WI, 7>(D));
+}
+
+// -s/2 * 2^(E - 1080) (s in units of 2^(E - 1080)): the integer converted by
+// the hardware (round to nearest), the power of two and the sign applied to
+// the bits; the caller has checked that the exponent stays normal.
+__device__ __forceinline__ double quad_out(long long s, int E) {
+  if (s == 0) return 0.0;
+  long long b = __double_as_longlong(__ll2double_rn(s));
+  b += (long long)(E - 1081) << 52;
+  return __longlong_as_double(b ^ (long long)(1ULL << 63));
+}
+
+struct QuadIdx {
+  int64_t e[6];  // pair index of the edges (0,1) (2,3) (0,2) (1,3) (0,3) (1,2)
+};
+
+constexpr int quad_slot(int x, int y) { return quad_edge_of(x, y); }  // 2 m + e -> e[] slot
+
+template <int MM, int ORI>
+__device__ __forceinline__ void quad_store(const QuadIdx& I, int64_t P, int64_t M, const double (&o)[4],
+                                           double* __restrict__ Aout, double* __restrict__ Qout,
+                                           double* __restrict__ Rout) {
+  constexpr int es = quad_slot(kQuadEdge[MM][ORI][0], kQuadEdge[MM][ORI][1]);
+  constexpr int en = quad_slot(kQuadEdge[MM][1 - ORI][0], kQuadEdge[MM][1 - ORI][1]);
+  const int64_t s = I.e[es], n = I.e[en];
+#pragma unroll
+  for (int ts = 0; ts < 2; ++ts)
+#pragma unroll
+    for (int tn = 0; tn < 2; ++tn) {
+      const int64_t off = ((int64_t)ts * P + s) * M + (int64_t)tn * P + n;
+      const double v = o[ts * 2 + tn];
+      if (Aout) Aout[off] = v;
+      if (Rout) Rout[off] = v;
+      if (Qout) Qout[off] = 0.0;  // Q vanishes on disjoint edges
+    }
+}
+
+
+// Fixed-point form of one output group (always computed; a group that is not
+// exact is stored again by the FP64 path afterwards).
+template <int MM, int ORI>
+__device__ __forceinline__ void quad_group(const long long (&D)[3][2][2][2], int E, int64_t P, int64_t M,
+                                           const QuadIdx& I, double* __restrict__ Aout, double* __restrict__ Qout,
+                                           double* __restrict__ Rout) {
+  const long long xs0 = quad_sum<long long, MM, ORI, 0>(D, 0), xs1 = quad_sum<long long, MM, ORI, 1>(D, 0);
+  const long long xj0 = quad_sum<long long, MM, ORI, 0>(D, 1), xj1 = quad_sum<long long, MM, ORI, 1>(D, 1);
+  const double o[4] = {quad_out(xs0 + xs1, E),   // (S, S)
+                       quad_out(xj0 + xj1, E),   // (S, J)
+                       quad_out(xj0 - xj1, E),   // (J, S)
+                       quad_out(xs1 - xs0, E)};  // (J, J)
+  quad_store<MM, ORI>(I, P, M, o, Aout, Qout, Rout);
+}
+
+// FP64 form of one output group (values not finite, or too small for the
+// fixed-point form).
+template <int MM, int ORI>
+__device__ __forceinline__ void quad_group_fp64_t(const double (&V)[3][2][2][2], double (&o)[4]) {
+  const double xs0 = quad_sum<double, MM, ORI, 0>(V, 0), xs1 = quad_sum<double, MM, ORI, 1>(V, 0);
+  const double xj0 = quad_sum<double, MM, ORI, 0>(V, 1), xj1 = quad_sum<double, MM, ORI, 1>(V, 1);
+  o[0] = -0.5 * (xs0 + xs1);
+  o[1] = -0.5 * (xj0 + xj1);
+  o[2] = -0.5 * (xj0 - xj1);
+  o[3] = -0.5 * (xs1 - xs0);
+}
+
+// Loads of matching y of the quadruple: a[(p,q)][(r,t)], a[(p,r)][(q,t)] and
+// a[(q,r)][(p,t)] (four type pairs each).
+template <int Y>
+__device__ __forceinline__ void quad_load(const AView& A, int64_t P, const QuadIdx& I, double2 (&L)[2][2]) {
+  constexpr int re = Y == 0 ? 0 : Y == 1 ? 2 : 5, ce = Y == 0 ? 1 : Y == 1 ? 3 : 4;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) L[i][j] = __ldg(A.a + (i * P + I.e[re]) * A.M + j * P + I.e[ce]);
+}
+
+// The eight entries of matching MM (both orientations): its values come from
+// the two other matchings, aligned to their own largest exponent.
+template <int MM>
+__device__ __forceinline__ void quad_pass(const AView& A, int64_t P, int64_t M, const QuadIdx& I,
+                                          double* __restrict__ Aout, double* __restrict__ Qout,
+                                          double* __restrict__ Rout) {
+  constexpr int Y = MM == 0 ? 1 : 0, Z = MM == 2 ? 1 : 2;
+  double2 Ly[2][2], Lz[2][2];
+  quad_load<Y>(A, P, I, Ly);
+  quad_load<Z>(A, P, I, Lz);
   int E = 1;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    t[i] = fx_split(p[i]);
-    E = max(E, t[i].e);
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+      E = max(E, max(max(fx_exponent(Ly[i][j].x), fx_exponent(Ly[i][j].y)),
+                     max(fx_exponent(Lz[i][j].x), fx_exponent(Lz[i][j].y))));
+  if (E < 64 || E > 2040) {  // not finite, or the converted exponent would leave the normal range: FP64
+    double V[3][2][2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        V[Y][i][j][0] = Ly[i][j].x;
+        V[Y][i][j][1] = Ly[i][j].y;
+        V[Z][i][j][0] = Lz[i][j].x;
+        V[Z][i][j][1] = Lz[i][j].y;
+      }
+    double o[4];
+    quad_group_fp64_t<MM, 0>(V, o);
+    quad_store<MM, 0>(I, P, M, o, Aout, Qout, Rout);
+    quad_group_fp64_t<MM, 1>(V, o);
+    quad_store<MM, 1>(I, P, M, o, Aout, Qout, Rout);
+    return;
   }
-  bool ok0 = true, ok1 = true;
-  if (E < 0x7ff) {
-    long long s0 = 0, s1 = 0;
+  long long D[3][2][2][2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) s0 += fx_align(t[i], E, flips >> i);
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int i = 4; i < 8; ++i) s1 += fx_align(t[i], E, flips >> i);
-    out0 = fx_neg_half(s0 + s1, E, ok0);
-    out1 = fx_neg_half(s1 - s0, E, ok1);
-  }
-  if (E == 0x7ff || !ok0 || !ok1) {  // inf/nan input or a sum below the normal range
-    double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) s0 += ((flips >> i) & 1u) ? -p[i] : p[i];
-#pragma unroll
-    for (int i = 4; i < 8; ++i) s1 += ((flips >> i) & 1u) ? -p[i] : p[i];
-    out0 = -0.5 * (s0 + s1);
-    out1 = -0.5 * (s1 - s0);
-  }
+    for (int j = 0; j < 2; ++j) {
+      D[Y][i][j][0] = fx_align(fx_split(Ly[i][j].x), E, 0u);
+      D[Y][i][j][1] = fx_align(fx_split(Ly[i][j].y), E, 0u);
+      D[Z][i][j][0] = fx_align(fx_split(Lz[i][j].x), E, 0u);
+      D[Z][i][j][1] = fx_align(fx_split(Lz[i][j].y), E, 0u);
+    }
+  quad_group<MM, 0>(D, E, P, M, I, Aout, Qout, Rout);
+  quad_group<MM, 1>(D, E, P, M, I, Aout, Qout, Rout);
 }
 
-__device__ __noinline__ double neg_half_slow(double x) { return -0.5 * x; }
-
-// -x/2 with integer ops on the common path; the FP64 multiply only for zero,
-// subnormal, inf and nan inputs, in a call the compiler cannot if-convert.
-__device__ __forceinline__ double neg_half_nz(double x) {
-  const long long b = __double_as_longlong(x);
-  const long long ex = (b >> 52) & 0x7ff;
-  if (ex > 1 && ex < 0x7ff) return __longlong_as_double((b - (1LL << 52)) ^ (long long)(1ULL << 63));
-  return neg_half_slow(x);
-}
-
-// Closed-form pair x pair block, one thread per pair of edges (e(s), e(n))
-// computing the four entries (S/J of e(s)) x (S/J of e(n)): on disjoint
-// edges they are signed sums of the same eight entries of a (two per type
-// pair of the k- and j-edges for each of the two edge pairs (b_s, w), (a_s, w')),
-// read once for all four.  Lanes run over consecutive e(n) of one e(s).
-__global__ void __launch_bounds__(256, 4) k_entries4_closed(BasisView B, AView A, const double* __restrict__ h,
-                                                         double* __restrict__ Aout, double* __restrict__ Qout,
-                                                         double* __restrict__ Rout) {
+// One block per edge (p, q); threads run over the edges (r, t) with
+// q < r < t, i.e. the contiguous pair indices from (q+1, q+2) to P - 1.  The
+// three output matchings are done one after the other, each reading the two
+// others (the second reads of a value hit L1).
+__global__ void __launch_bounds__(256, 2) k_disjoint4(BasisView B, AView A, double* __restrict__ Aout,
+                                                   double* __restrict__ Qout, double* __restrict__ Rout) {
   const int N = B.N;
   const int64_t P = B.P, M = B.M;
-  const int64_t chunks = (P + 255) / 256;
-  const int64_t ps = blockIdx.x / chunks;
-  const int64_t pn = (blockIdx.x % chunks) * 256 + threadIdx.x;
-  if (pn >= P) return;
-  const int32_t abs_ = __ldg(B.pair_ab + ps), abn = __ldg(B.pair_ab + pn);
-  const int as = abs_ >> 16, bs = abs_ & 0xffff, an = abn >> 16, bn = abn & 0xffff;
+  const int64_t pq = blockIdx.x;
+  const int32_t abq = __ldg(B.pair_ab + pq);
+  const int p = abq >> 16, q = abq & 0xffff;
+  if (q + 2 >= N) return;
+  const int64_t u0 = pair_index(N, q + 1, q + 2);
+  const int64_t base_p = (int64_t)p * (2 * N - p - 1) / 2 - p - 1;  // pair_index(p, y) = base_p + y
+  const int64_t base_q = (int64_t)q * (2 * N - q - 1) / 2 - q - 1;
+  for (int64_t u = u0 + threadIdx.x; u < P; u += blockDim.x) {
+    const int32_t art = __ldg(B.pair_ab + u);
+    const int r = art >> 16, t = art & 0xffff;
+    QuadIdx I;
+    I.e[0] = pq;
+    I.e[1] = u;
+    I.e[2] = base_p + r;
+    I.e[3] = base_q + t;
+    I.e[4] = base_p + t;
+    I.e[5] = base_q + r;
+    quad_pass<0>(A, P, M, I, Aout, Qout, Rout);
+    quad_pass<1>(A, P, M, I, Aout, Qout, Rout);
+    quad_pass<2>(A, P, M, I, Aout, Qout, Rout);
+  }
+}
+
+// Pair x pair entries whose edges meet (share one vertex, or are the same
+// edge): the D-section part of Eq. (09) in closed form and Q (Eq. (07)); the
+// l-pair part is added afterwards by k_shared_closed / k_same.  One thread
+// per (edge s, meeting edge n), four type pairs each.
+__global__ void __launch_bounds__(256) k_meet(BasisView B, AView A, const double* __restrict__ h,
+                                              double* __restrict__ Aout, double* __restrict__ Qout,
+                                              double* __restrict__ Rout) {
+  const int N = B.N;
+  const int64_t P = B.P, M = B.M;
+  const int64_t per = 2 * (int64_t)N - 3;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= P * per) return;
+  const int64_t ps = tid / per;
+  const int k = (int)(tid % per);
+  const int32_t abs_ = __ldg(B.pair_ab + ps);
+  const int as = abs_ >> 16, bs = abs_ & 0xffff;
+  int an, bn;
+  if (k == 2 * N - 4) {
+    an = as;
+    bn = bs;
+  } else {
+    const int v = k < N - 2 ? as : bs;
+    int w = k < N - 2 ? k : k - (N - 2);
+    if (w >= as) ++w;  // skip as and bs (as < bs)
+    if (w >= bs) ++w;
+    an = imin(v, w);
+    bn = imax(v, w);
+  }
+  const int64_t pn = pair_index(N, an, bn);
   int shared = 0, cv = -1;
   if (as == an || as == bn) { ++shared; cv = as; }
   if (bs == an || bs == bn) { ++shared; cv = bs; }
-  if (shared == 0) {
-    // For each of the two k/j edge pairs (wi), the (J, J) entry gets the
-    // (S, S) terms times eps_wi and the (J, S) entry the (S, J) terms times
-    // -eps_wi, with eps_0 = -1, eps_1 = +1 for every order of the four
-    // vertices (the same entries of a, conjugated type pairs); so only the
-    // ts = S sums are formed and the J rows follow by sums and differences.
-    // group S: the terms of the (S, S) / (J, J) pair; group J: (S, J) / (J, S)
-    double gs[8], gj[8];
-    unsigned fs = 0, fj = 0;
-#pragma unroll
-    for (int wi = 0; wi < 2; ++wi) {
-      const int w = wi ? bn : an, wp = wi ? an : bn;
-      const int64_t pk = pair_index_any(N, bs, w), pj = pair_index_any(N, as, wp);
-      // X[tj][tk] = a((as, w') tj, (bs, w) tk); for wi = 0 the k row is common
-      // to the warp, so a[k][j] is read (its conjugation is in the sign table)
-      const double2* base = wi ? A.a + pj * M + pk : A.a + pk * M + pj;
-      const int64_t oj = wi ? P * M : P, ok = wi ? P : P * M;
-      const double2 x00 = __ldg(base), x01 = __ldg(base + ok), x10 = __ldg(base + oj), x11 = __ldg(base + oj + ok);
-      const int idx = (w < as) | ((bs < w) << 1) | ((wp < as) << 2);
-      const unsigned m = (unsigned)((wi ? kDisjointSign1 : kDisjointSign0) >> (8 * idx)) & 0xffu;
-      // tn = S: tl = 0 -> (xr11, xi01), tl = 1 -> (xr00, xi10);
-      // tn = J: tl = 0 -> (xr01, xi11), tl = 1 -> (xr10, xi00)
-      gs[4 * wi + 0] = x11.x;
-      gs[4 * wi + 1] = x01.y;
-      gs[4 * wi + 2] = x00.x;
-      gs[4 * wi + 3] = x10.y;
-      gj[4 * wi + 0] = x01.x;
-      gj[4 * wi + 1] = x11.y;
-      gj[4 * wi + 2] = x10.x;
-      gj[4 * wi + 3] = x00.y;
-      fs |= (m & 0xfu) << (4 * wi);
-      fj |= ((m >> 4) & 0xfu) << (4 * wi);
-    }
-    // (S,S) = -1/2 (xs0 + xs1), (J,J) = -1/2 (xs1 - xs0); (S,J) = -1/2 (xj0 + xj1),
-    // (J,S) = -1/2 (xj0 - xj1) = -(-1/2 (xj1 - xj0))
-    double r[4];
-    fx_group(gs, fs, r[0], r[3]);
-    double jm;
-    fx_group(gj, fj, r[1], jm);
-    r[2] = -jm;
-#pragma unroll
-    for (int ts = 0; ts < 2; ++ts)
-#pragma unroll
-      for (int tn = 0; tn < 2; ++tn) {
-        const int64_t o = ((int64_t)ts * P + ps) * M + (int64_t)tn * P + pn;
-        if (Rout) Rout[o] = r[ts * 2 + tn];
-        if (Qout) Qout[o] = 0.0;  // Q vanishes on disjoint edges
-        if (Aout) Aout[o] = r[ts * 2 + tn];
-      }
-    return;
-  }
-  // edges meet: the D-section part in closed form (the l-pair part is added by
-  // k_shared_closed / k_same)
-  double acc[4];
   const int e1 = as == an, e2 = as == bn, e3 = bs == an, e4 = bs == bn;
   const double cf = (double)(e1 - e2 - e3 + e4), cd = (double)(e1 + e2 - e3 - e4);
 #pragma unroll
   for (int ts = 0; ts < 2; ++ts)
 #pragma unroll
     for (int tn = 0; tn < 2; ++tn) {
-      const int64_t sb = (int64_t)(1 - ts) * P + ps, n = (int64_t)tn * P + pn, nb = (int64_t)(1 - tn) * P + pn;
+      const int64_t s = (int64_t)ts * P + ps, n = (int64_t)tn * P + pn;
+      const int64_t sb = (int64_t)(1 - ts) * P + ps, nb = (int64_t)(1 - tn) * P + pn;
       const double2 a1 = ldA_row(A, nb, sb), a2 = ldA_row(A, n, sb);
       const double sgs = ts == kS ? 1.0 : -1.0, sgn = tn == kS ? 1.0 : -1.0;
-      acc[ts * 2 + tn] = sgs * (sgn * a1.x * cf - a2.y * cd);
-    }
-#pragma unroll
-  for (int ts = 0; ts < 2; ++ts)
-#pragma unroll
-    for (int tn = 0; tn < 2; ++tn) {
-      const int64_t s = (int64_t)ts * P + ps, n = (int64_t)tn * P + pn;
-      double q = 0.0;
+      const double acc = sgs * (sgn * a1.x * cf - a2.y * cd);
+      double qv = 0.0;
       if (h != nullptr) {
         const Elem es = make_pair(ts, as, bs), en = make_pair(tn, an, bn);
         if (shared == 1) {
-          const int p = (as == cv) ? bs : as, qv = (an == cv) ? bn : an;
-          const Elem em = make_pair(1 ^ tn ^ ts, p, qv);
-          q = __ldg(h + elem_index(B, em.kind, em.a, em.b)) * f_value(B, em, en, es);
+          const int pv = (as == cv) ? bs : as, qq = (an == cv) ? bn : an;
+          const Elem em = make_pair(1 ^ tn ^ ts, pv, qq);
+          qv = __ldg(h + elem_index(B, em.kind, em.a, em.b)) * f_value(B, em, en, es);
         } else if (tn != ts) {
           for (int lam = imax(as, 1); lam <= bs; ++lam)
-            q += __ldg(h + d_index(B, lam)) * f_value(B, make_d(lam), en, es);
+            qv += __ldg(h + d_index(B, lam)) * f_value(B, make_d(lam), en, es);
         }
       }
-      const double r = neg_half(acc[ts * 2 + tn]);
+      const double r = neg_half(acc);
       const int64_t o = s * M + n;
       if (Rout) Rout[o] = r;
-      if (Qout) Qout[o] = q;
-      if (Aout) Aout[o] = q + r;
+      if (Qout) Qout[o] = qv;
+      if (Aout) Aout[o] = qv + r;
     }
 }
 
@@ -1702,18 +1819,28 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
   };
   mark(0);
   const bool dense_out = A || Q || R;
-  // 0: pair x pair (closed: four type pairs per thread)
+  // 0: pair x pair (closed: disjoint edges, one thread per vertex quadruple)
   if (dense_out) {
     if (closed) {
-      const int64_t pc = (B.P + 255) / 256;
-      k_entries4_closed<<<(unsigned)(B.P * pc), 256, 0, st>>>(B, av, h, A, Q, R);
+      if (N >= 4) {
+        k_disjoint4<<<(unsigned)B.P, 256, 0, st>>>(B, av, A, Q, R);
+        note_launch(1);
+      }
     } else {
       k_entries<LB_ALG_JOIN><<<(unsigned)(P2 * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
+      note_launch(1);
     }
-    note_launch(1);
   }
   mark(1);
-  // 1: pair x diagonal
+  // 1: closed: pair x pair on meeting edges, D-section and Q parts (the
+  //    l-pair parts are added by kernels 5 and 6)
+  if (dense_out && closed && e == cudaSuccess) {
+    const int64_t threads = B.P * (2 * (int64_t)N - 3);
+    k_meet<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(B, av, h, A, Q, R);
+    note_launch(1);
+  }
+  mark(2);
+  // 2: pair x diagonal
   if (dense_out && e == cudaSuccess) {
     if (closed) {
       const size_t smem = sizeof(double) * 12 * (size_t)(N + 1);
@@ -1726,21 +1853,21 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
     }
     note_launch(1);
   }
-  mark(2);
-  // 2: diagonal x pair (closed: produced by k_shared_closed below)
+  mark(3);
+  // 3: diagonal x pair (closed: produced by k_shared_closed below)
   if (dense_out && !closed && e == cudaSuccess) {
     k_dp<<<(unsigned)((N - 1) * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
     note_launch(1);
   }
-  mark(3);
-  // 3: diagonal x diagonal
+  mark(4);
+  // 4: diagonal x diagonal
   if (dense_out && e == cudaSuccess) {
     const int64_t dd_warps = (int64_t)(N - 1) * (N - 1);
     k_dd<<<(unsigned)((dd_warps * 32 + 255) / 256), 256, 0, st>>>(B, av, A, Q, R);
     note_launch(1);
   }
-  mark(4);
-  // 4: pair x pair on edges sharing one vertex (adds to R / A); closed: one
+  mark(5);
+  // 5: pair x pair on edges sharing one vertex (adds to R / A); closed: one
   //    block per vertex pair, which also writes the diagonal x pair entries
   if (dense_out && closed && e == cudaSuccess) {
     const size_t smem = sizeof(double) * 16 * (size_t)(N + 1);
@@ -1753,26 +1880,28 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
     if (e == cudaSuccess) k_shared<<<(unsigned)(N * (N - 1)), 256, smem, st>>>(B, av, A, R);
     note_launch(1);
   }
-  mark(5);
-  // 5: pair x pair on the same edge (adds to R / A)
+  mark(6);
+  // 6: pair x pair on the same edge (adds to R / A)
   if ((A || R) && e == cudaSuccess) {
     k_same<<<(unsigned)B.P, kSameThreads, sizeof(double) * 2 * N, st>>>(B, av, A, R);
     note_launch(1);
   }
-  mark(6);
-  // 6: K
+  mark(7);
+  // 7: K
   if (K && e == cudaSuccess) {
     const int64_t warps = B.M;
     k_kvec<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(B, av, K);
     note_launch(1);
   }
-  mark(7);
+  mark(8);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 const char* assemble_kernel_name(int i) {
-  static const char* names[kAssembleKernels] = {"k_entries (pair x pair)", "k_pd (pair x diagonal)",
+  static const char* names[kAssembleKernels] = {"k_entries (pair x pair; closed: disjoint edges by vertex quadruple)",
+                                                "k_meet (closed: meeting edges, D-section and Q parts)",
+                                                "k_pd (pair x diagonal)",
                                                 "k_dp (diagonal x pair)", "k_dd (diagonal x diagonal)",
                                                 "k_shared (edges sharing a vertex; closed: + diagonal x pair)",
                                                 "k_same (same edge)", "k_kvec (K)"};

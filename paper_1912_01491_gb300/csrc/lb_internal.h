@@ -46,7 +46,7 @@ cudaError_t expand(const lb::BasisView& B, const double2* A, double2* coef, cuda
 cudaError_t rho(const lb::BasisView& B, const double* v, double2* out, cudaStream_t st);
 
 // dense assembly (lb_assemble.cu)
-constexpr int kAssembleKernels = 7;
+constexpr int kAssembleKernels = 8;
 cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double2* a,
                            double* A, double* Q, double* R, double* K, int algorithm, cudaStream_t st,
                            cudaEvent_t* ev = nullptr);
