@@ -331,11 +331,7 @@ def run_gb300(args):
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture on a
 # smaller case, with the units that capture processed; scaled to a launch of
 # the bench size by units.  Kept only for the kernel version the capture saw.
-NCU_TRAFFIC = {
-    "k_entries (pair x pair; closed: disjoint edges by vertex quadruple)": {
-        "N": 100, "bytes": 1.223730e9 + 1.040116e9, "units": lambda N: N * (N - 1.0) * (N - 2.0) * (N - 3.0),
-        "source": "profiles/k_disjoint4_n100.md"},
-}
+NCU_TRAFFIC = {}  # filled from the committed ncu summary of the current kernel version
 
 
 def ncu_traffic(kernel, N):
