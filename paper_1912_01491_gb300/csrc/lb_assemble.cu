@@ -1227,6 +1227,119 @@ __global__ void __launch_bounds__(256) k_dd(BasisView B, AView A, double* __rest
   }
 }
 
+// ---------------------------------------------------------------------------
+// Diagonal blocks through the Helmert structure of the D_l.  With d_l the
+// vector of the diagonal of D_l (d_l[k] = delta_k(l)), g_xy(l) = d_l[x] -
+// d_l[y] and h_xy(l) = d_l[x] + d_l[y], sums over pairs x < y of the form
+// sum g_xy(nu) (g_xy(mu) W_xy + 2 h_xy(mu) V_xy) are d_nu^T G d_mu with the
+// N x N matrix
+//   G = sum_{x<y} W_xy (e_x - e_y)(e_x - e_y)^T + 2 V_xy (e_x - e_y)(e_x + e_y)^T,
+// and every d_l^T x is c_l sum_{k<l} x_k - l c_l x_l: a prefix sum.  So the
+// diagonal x diagonal block costs O(N^2) instead of O(N^4).
+
+// W_xy = Re a(S_xy, S_xy) + Re a(J_xy, J_xy), V_xy = Im a(S_xy, J_xy), x < y
+__device__ __forceinline__ void dd_wv(const BasisView& B, const AView& A, int x, int y, double& W, double& V) {
+  const int64_t p = pair_index(B.N, x, y);
+  W = ldA(A, p, p).x + ldA(A, B.P + p, B.P + p).x;
+  V = ldA(A, p, B.P + p).y;
+}
+
+// Row k of G into Gm (N x N, row-major): off-diagonal G[k][j] = -W_kj + 2 V_kj
+// (k < j) or -W_jk - 2 V_jk (k > j); the diagonal is the row sum of
+// W_kj + 2 K_kj over j != k (K_kj = V_kj for k < j, -V_jk for k > j).
+// One block per row.
+__global__ void __launch_bounds__(128) k_dd_g(BasisView B, AView A, double* __restrict__ Gm) {
+  __shared__ double red[4];
+  const int N = B.N;
+  const int k = blockIdx.x;
+  double diag = 0.0;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    if (j == k) continue;
+    double W, V;
+    dd_wv(B, A, imin(k, j), imax(k, j), W, V);
+    const double kv = k < j ? V : -V;
+    Gm[(int64_t)k * N + j] = 2.0 * kv - W;
+    diag += W + 2.0 * kv;
+  }
+  diag = warp_sum(diag);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = diag;
+  __syncthreads();
+  if (threadIdx.x == 0) Gm[(int64_t)k * N + k] = (red[0] + red[1]) + (red[2] + red[3]);
+}
+
+// Row D_nu of the diagonal x diagonal block of R (Eq. (09)): T = d_nu^T G
+// (a prefix over the rows of G, coalesced across j), then
+// R[D_nu][D_mu] = -1/2 T d_mu (a prefix over j).  One block per nu.
+__global__ void __launch_bounds__(128) k_dd2(BasisView B, const double* __restrict__ Gm, double* __restrict__ Aout,
+                                             double* __restrict__ Qout, double* __restrict__ Rout) {
+  extern __shared__ double dsh[];
+  const int N = B.N;
+  const int64_t M = B.M;
+  const int nu = blockIdx.x + 1;
+  double* T = dsh;       // [N]
+  double* PT = dsh + N;  // [N + 1] prefix of T
+  const double cnu = ld_c(B, nu), dnn = dlt(B, nu, nu);
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    double col = 0.0;
+    for (int k = 0; k < nu; ++k) col += Gm[(int64_t)k * N + j];
+    T[j] = cnu * col + dnn * Gm[(int64_t)nu * N + j];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    PT[0] = 0.0;
+    for (int j = 0; j < N; ++j) {
+      acc += T[j];
+      PT[j + 1] = acc;
+    }
+  }
+  __syncthreads();
+  for (int mu = 1 + threadIdx.x; mu < N; mu += blockDim.x) {
+    const double acc = ld_c(B, mu) * PT[mu] + dlt(B, mu, mu) * T[mu];
+    const double r = -0.5 * acc;
+    const int64_t o = d_index(B, nu) * M + d_index(B, mu);
+    if (Rout) Rout[o] = r;
+    if (Qout) Qout[o] = 0.0;
+    if (Aout) Aout[o] = r;
+  }
+}
+
+// H = D X D^T for X = the D x D block of a (real and imaginary parts),
+// D[k][l] = delta_k(l): row k of D X, then row k of H.  One block per k.
+// H lets the same-edge kernel evaluate its D-section sums
+// sum_{nu,mu} z_nu X[nu][mu] g_mu with z, g in {D^T (e_a +- e_b)} in O(1).
+__global__ void __launch_bounds__(128) k_dh(BasisView B, AView A, double* __restrict__ Hr, double* __restrict__ Hi) {
+  extern __shared__ double hsh[];
+  const int N = B.N;
+  const int k = blockIdx.x;
+  double* DXr = hsh;      // [N], index mu
+  double* DXi = hsh + N;  // [N]
+  for (int mu = threadIdx.x; mu < N; mu += blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    if (mu >= 1) {
+      for (int lam = imax(k, 1); lam < N; ++lam) {
+        const double w = dlt(B, k, lam);
+        const double2 a = ldA(A, d_index(B, lam), d_index(B, mu));
+        sr = fma(w, a.x, sr);
+        si = fma(w, a.y, si);
+      }
+    }
+    DXr[mu] = sr;
+    DXi[mu] = si;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    double hr = 0.0, hi = 0.0;
+    for (int mu = imax(j, 1); mu < N; ++mu) {
+      const double w = dlt(B, j, mu);
+      hr = fma(w, DXr[mu], hr);
+      hi = fma(w, DXi[mu], hi);
+    }
+    Hr[(int64_t)k * N + j] = hr;
+    Hi[(int64_t)k * N + j] = hi;
+  }
+}
+
 // Pair-pair entries whose edges share one vertex v: s on (v, p), n on (v, q).
 // Shared memory: T1[w][tj][tk] = a[(q,w) tj][(p,w) tk],  T2[mu][t] = a[D_mu][(p,q) t].
 __global__ void __launch_bounds__(256) k_shared(BasisView B, AView A, double* __restrict__ Aout,
@@ -1465,45 +1578,23 @@ __device__ __forceinline__ double shared_entry_closed(const BasisView& B, const 
 
 // Diagonal row D_nu, pair column n on {p, q} of type tn, in closed form: the
 // l = (v, w) families for v = p and v = q (k = partner(l), j on (v', w)), the
-// l on e(n) itself (j = D_mu), and Q.  Returns (R entry, Q entry).
-__device__ __forceinline__ void dp_entry_closed(const BasisView& B, const PairStage& S, const double* h, int p,
-                                                int q, int nu, int tn, double& r, double& qout) {
+// l on e(n) itself (j = D_mu), and Q.  Returns (R entry, Q entry).  The
+// families reduce to d_nu^T U - delta_v(nu) sum_w U_w with the prefix arrays
+// PU[tr * 2 + tn] of U_w = sigma_v(w) sum_tl tau_l (sf Re a - sd Im a) built
+// by k_shared_closed (see there).
+__device__ __forceinline__ void dp_entry_closed(const BasisView& B, const PairStage& S, const double* PU,
+                                                const double* h, int p, int q, int nu, int tn, double& r,
+                                                double& qout) {
   const int N = B.N;
   const int64_t P = B.P;
-  const double cnu = ld_c(B, nu), lcnu = ld_lc(B, nu);
+  const int L = S.L;
+  const double cnu = ld_c(B, nu), dnn = dlt(B, nu, nu);
   double acc2 = 0.0;
+#pragma unroll
   for (int tr = 0; tr < 2; ++tr) {
-    const int v = tr ? q : p, vp = tr ? p : q;  // shared vertex of l and n, and the other one
-    // staged (for this orientation) a[(vp,w) tj][(v,w) tk], k = partner(l) of type 1 - tl
-    const double dv = dlt(B, v, nu);
-    int b0 = p, b1 = q, b2 = nu, tmp;
-    if (b1 > b2) { tmp = b1; b1 = b2; b2 = tmp; }
-    if (b0 > b1) { tmp = b0; b0 = b1; b1 = tmp; }
-    const int nodes[3] = {b0, b1, b2};
-    auto add = [&](int lo, int hi, double dw) {
-      if (lo > hi) return;
-      const int w = lo;
-      const double g = w < v ? dw - dv : dv - dw;  // delta_x(nu) - delta_y(nu), {x < y} = {v, w}
-      if (g == 0.0) return;
-      for (int tl = 0; tl < 2; ++tl) {
-        const int tjf = 1 ^ tl ^ tn, tjd = tl ^ tn, tkb = 1 - tl;
-        const int phl = coef_phase(tl, w, v);
-        const int phn = coef_phase(tn, v, vp);
-        const int sf = sgn_f(phn + coef_phase(tjf, vp, w) + phl);
-        const int sd = sgn_d(phn + coef_phase(tjd, vp, w) + phl);
-        const double t = sgn_mul(sf, S.sre(tr, tjf, tkb, lo, hi)) - sgn_mul(sd, S.sim(tr, tjd, tkb, lo, hi));
-        acc2 += tl == kS ? -g * t : g * t;  // f(partner(l), l, D_nu) = -+ g
-      }
-    };
-    int prev = 0;
-    for (int i = 0; i < 3; ++i) {
-      const int x = nodes[i];
-      if (x < prev) continue;
-      add(prev, x - 1, (x - 1) < nu ? cnu : 0.0);
-      if (x == nu && x != p && x != q) add(x, x, lcnu);
-      prev = x + 1;
-    }
-    add(prev, N - 1, 0.0);
+    const double* U = PU + (tr * 2 + tn) * L;
+    const double dv = dlt(B, tr ? q : p, nu);
+    acc2 += cnu * U[nu] + dnn * (U[nu + 1] - U[nu]) - dv * U[N];
   }
   double acc = acc2 * kInvSqrt2;
   qout = 0.0;
@@ -1541,6 +1632,7 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
   double* TY = sc + 10 * L;
   double* CX = sc + 12 * L;
   double* CY = sc + 14 * L;
+  double* PU = sc + 16 * L;  // [4][L]: prefix over w of U for (tr, tn)
   const int64_t ppq = blockIdx.x;
   for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
     const int w = t >> 2, jk = t & 3, tj = jk >> 1, tk = jk & 1;
@@ -1572,6 +1664,34 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
   }
   __syncthreads();
   const PairStage S{PX, PY, TX, TY, CX, CY, L};
+  // diagonal x pair families: for orientation tr (v = p or q, v' the other)
+  // and column type tn, U_w = sigma_v(w) sum_tl tau_l (sf X_re - sd X_im) at
+  // the single w, with X the staged a[(v',w) tj][(v,w) tk] (k = partner(l)),
+  // tau_l = -1 for l of type S and sigma_v(w) = [w < v] - [w > v]; the entry's
+  // sum over w is d_nu^T U - delta_v(nu) sum_w U_w.
+  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
+    const int tr = t / (2 * N), tn = (t / N) & 1, w = t % N;
+    double u = 0.0;
+    if (w != p && w != q) {
+      const int v = tr ? q : p, vp = tr ? p : q;
+#pragma unroll
+      for (int tl = 0; tl < 2; ++tl) {
+        const int tjf = 1 ^ tl ^ tn, tjd = tl ^ tn, tkb = 1 - tl;
+        const int phl = coef_phase(tl, w, v);
+        const int phn = coef_phase(tn, v, vp);
+        const int sf = sgn_f(phn + coef_phase(tjf, vp, w) + phl);
+        const int sd = sgn_d(phn + coef_phase(tjd, vp, w) + phl);
+        const double tv = sgn_mul(sf, S.sre(tr, tjf, tkb, w, w)) - sgn_mul(sd, S.sim(tr, tjd, tkb, w, w));
+        u += tl == kS ? -tv : tv;
+      }
+      if (w > v) u = -u;
+    }
+    PU[(tr * 2 + tn) * L + w + 1] = u;
+  }
+  if (threadIdx.x < 4) PU[threadIdx.x * L] = 0.0;
+  __syncthreads();
+  if (threadIdx.x < 4) scan_inplace(PU + threadIdx.x * L, N);
+  __syncthreads();
   // pair x pair, edges sharing a vertex: 2 orientations x N vertices v x 4 type pairs
   if (Aout || Rout) {
     for (int t = threadIdx.x; t < 8 * N; t += blockDim.x) {
@@ -1589,7 +1709,7 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
   for (int t = threadIdx.x; t < 2 * (N - 1); t += blockDim.x) {
     const int nu = 1 + (t >> 1), tn = t & 1;
     double r, qv;
-    dp_entry_closed(B, S, h, p, q, nu, tn, r, qv);
+    dp_entry_closed(B, S, PU, h, p, q, nu, tn, r, qv);
     const int64_t o = d_index(B, nu) * M + (tn * P + ppq);
     if (Rout) Rout[o] = r;
     if (Qout) Qout[o] = qv;
@@ -1617,7 +1737,7 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
   double* PGY = sq + L;       // prefix of gs(lam) YY[lam] over lam in [lo_s, bs]
   double* PG2C = sq + 2 * L;  // prefix of 2 gs(lam) c_lam
   double* PCY = sq + 3 * L;   // prefix of c_mu YY[mu]
-  double* PW = sq + 4 * L;    // [8][L]: (vi, tl, {Re a(partner(l),k), Im a(l,k)}) prefixes over w
+  double* PW = sq + 4 * L;    // [8][L]: (vi, tl, {U1, U2 terms}) prefixes over w (see below)
   __shared__ double cst[2];   // c1 = sum gs Re a[s][D_mu], c2 = sum gs Im a[partner(s)][D_mu]
   for (int x = threadIdx.x; x < N; x += blockDim.x) {
     const double y = x >= 1 ? ldA(A, sb, d_index(B, x)).y : 0.0;
@@ -1627,18 +1747,29 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
     PG2C[x + 1] = x >= 1 ? 2.0 * gs * ld_c(B, x) : 0.0;
     PCY[x + 1] = x >= 1 ? ld_c(B, x) * y : 0.0;
   }
+  // l = (v, w) sharing the vertex v with e(s): with bx = Re a(partner(l), k),
+  // ly = Im a(l, k), sk the sign of f(k, l, s), sigma = [w < v] - [w > v] and
+  // tau = -1 for l of type S, the family contributes
+  //   sum_w sk (tau sigma (delta_w(nu) - delta_v(nu)) bx - (delta_v(nu) + delta_w(nu)) ly)
+  //   = d_nu^T U1 + delta_v(nu) U2,  U1_w = sk (tau sigma bx - ly),  U2 = sum_w sk (-tau sigma bx - ly),
+  // and d_nu^T U1 = c_nu sum_{w<nu} U1_w + delta_nu(nu) U1_nu (a prefix over w).
   for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
     const int vi = t / (2 * N), w = (t / 2) % N, tl = t & 1;
-    double bx = 0.0, ly = 0.0;
+    double u1 = 0.0, u2 = 0.0;
     if (w != as && w != bs) {
       const int v = vi ? bs : as, vp = vi ? as : bs;
       const int64_t pl = pair_index_any(N, v, w), pk = pair_index_any(N, vp, w);
-      const int64_t k = (int64_t)(1 ^ tl ^ ts) * P + pk;
-      ly = ldA(A, (int64_t)tl * P + pl, k).y;
-      bx = ldA(A, (int64_t)(1 - tl) * P + pl, k).x;
+      const int tk = 1 ^ tl ^ ts;
+      const int64_t k = (int64_t)tk * P + pk;
+      const double ly = ldA(A, (int64_t)tl * P + pl, k).y;
+      const double bx = ldA(A, (int64_t)(1 - tl) * P + pl, k).x;
+      const int sk = sgn_f(coef_phase(ts, v, vp) + coef_phase(tk, vp, w) + coef_phase(tl, w, v));
+      const double tsb = ((tl == kS) != (w < v)) ? bx : -bx;  // tau sigma bx
+      u1 = sgn_mul(sk, tsb - ly);
+      u2 = sgn_mul(sk, -tsb - ly);
     }
-    PW[((vi * 2 + tl) * 2 + 0) * L + w + 1] = bx;
-    PW[((vi * 2 + tl) * 2 + 1) * L + w + 1] = ly;
+    PW[((vi * 2 + tl) * 2 + 0) * L + w + 1] = u1;
+    PW[((vi * 2 + tl) * 2 + 1) * L + w + 1] = u2;
   }
   if (threadIdx.x < 11) {
     double* arr = threadIdx.x < 3 ? PGY + threadIdx.x * L : PW + (threadIdx.x - 3) * L;
@@ -1667,39 +1798,17 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
       accD += gs * t2;
     }
     double acc = sgs * accD;
-    // l = (v, w) sharing a vertex with e(s): intervals of w split at as, bs, nu
+    // l = (v, w) sharing a vertex with e(s): d_nu^T U1 + delta_v(nu) U2 per (v, tl)
     double accA = 0.0;
-    int b0 = as, b1 = bs, b2 = nu, tmp;
-    if (b1 > b2) { tmp = b1; b1 = b2; b2 = tmp; }
-    if (b0 > b1) { tmp = b0; b0 = b1; b1 = tmp; }
-    const int nodes[3] = {b0, b1, b2};
+    const double cnu = ld_c(B, nu), dnn = dlt(B, nu, nu);
+#pragma unroll
     for (int vi = 0; vi < 2; ++vi) {
-      const int v = vi ? bs : as, vp = vi ? as : bs;
-      const int phs = coef_phase(ts, v, vp);
-      const double dv = dlt(B, v, nu);
+      const double dv = dlt(B, vi ? bs : as, nu);
+#pragma unroll
       for (int tl = 0; tl < 2; ++tl) {
-        const int tk = 1 ^ tl ^ ts;
-        const double* PB = PW + ((vi * 2 + tl) * 2 + 0) * L;
-        const double* PL = PW + ((vi * 2 + tl) * 2 + 1) * L;
-        // one interval [lo, hi] of w values (none in e(s)) with the given delta_w(nu)
-        auto add = [&](int lo, int hi, double dw) {
-          if (lo > hi) return;
-          const int w = lo;
-          const double hl = dv + dw;
-          const double gl = w < v ? dw - dv : dv - dw;
-          const double fl = tl == kS ? -gl : gl;
-          const int sk = sgn_f(phs + coef_phase(tk, vp, w) + coef_phase(tl, w, v));
-          accA += sgn_mul(sk, fl * isum(PB, lo, hi) - hl * isum(PL, lo, hi));
-        };
-        int prev = 0;
-        for (int i = 0; i < 3; ++i) {
-          const int x = nodes[i];
-          if (x < prev) continue;  // repeated node
-          add(prev, x - 1, (x - 1) < nu ? ld_c(B, nu) : 0.0);
-          if (x == nu && x != as && x != bs) add(x, x, ld_lc(B, nu));
-          prev = x + 1;
-        }
-        add(prev, N - 1, 0.0);  // every w here is above nu
+        const double* PU1 = PW + ((vi * 2 + tl) * 2 + 0) * L;
+        const double* PU2 = PW + ((vi * 2 + tl) * 2 + 1) * L;
+        accA += cnu * PU1[nu] + dnn * (PU1[nu + 1] - PU1[nu]) + dv * PU2[N];
       }
     }
     acc += accA * kInvSqrt2;
@@ -1724,35 +1833,39 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
 // z-fiber of (partner(s), n) at D_nu.
 constexpr int kSameThreads = 128;
 
-__global__ void __launch_bounds__(kSameThreads) k_same(BasisView B, AView A, double* __restrict__ Aout,
+template <bool CLOSED>
+__global__ void __launch_bounds__(kSameThreads) k_same(BasisView B, AView A, const double* __restrict__ Hr,
+                                                       const double* __restrict__ Hi, double* __restrict__ Aout,
                                                        double* __restrict__ Rout) {
-  extern __shared__ double shd[];
+  extern __shared__ double shd[];  // JOIN: G[N], Z[N]
   __shared__ double red[kSameThreads / 32];
   const int N = B.N;
   const int64_t P = B.P, M = B.M;
   const int64_t e = blockIdx.x;
   const int32_t ab = __ldg(B.pair_ab + e);
   const int a = ab >> 16, b = ab & 0xffff;
-  const int lo = imax(a, 1);
-  double* G = shd;      // [N]
-  double* Z = shd + N;  // [N]
   for (int combo = 0; combo < 4; ++combo) {
     const int ts = combo >> 1, tn = combo & 1;
     const bool dfib = ts != tn;  // n = partner(s) = l: d-fiber; n = s: f-fiber of partner(n)
-    __syncthreads();
-    for (int t = threadIdx.x; t < N; t += blockDim.x) {
-      const double g = (t >= lo && t <= b) ? dlt(B, a, t) - dlt(B, b, t) : 0.0;
-      G[t] = ts == kS ? -g : g;
-      double z = 0.0;
-      if (dfib) {
-        if (t >= lo && !(a == 0 && b == 1 && t == 1)) z = dlt(B, a, t) + dlt(B, b, t);
-      } else if (t >= lo && t <= b) {
-        z = dlt(B, a, t) - dlt(B, b, t);
-        if (tn == kS) z = -z;
+    __syncthreads();  // red[] (and G, Z) of the previous combination have been read
+    double* G = shd;
+    double* Z = shd + N;
+    if (!CLOSED) {
+      const int lo = imax(a, 1);
+      for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        const double g = (t >= lo && t <= b) ? dlt(B, a, t) - dlt(B, b, t) : 0.0;
+        G[t] = ts == kS ? -g : g;
+        double z = 0.0;
+        if (dfib) {
+          if (t >= lo && !(a == 0 && b == 1 && t == 1)) z = dlt(B, a, t) + dlt(B, b, t);
+        } else if (t >= lo && t <= b) {
+          z = dlt(B, a, t) - dlt(B, b, t);
+          if (tn == kS) z = -z;
+        }
+        Z[t] = z;
       }
-      Z[t] = z;
+      __syncthreads();
     }
-    __syncthreads();
     double acc2 = 0.0, accD = 0.0;
     // (A) e(l) = (v, w), v in {a, b}, w outside: k and j on (v', w)
     for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
@@ -1773,16 +1886,28 @@ __global__ void __launch_bounds__(kSameThreads) k_same(BasisView B, AView A, dou
         acc2 -= sgn_mul(sk * sd, a2.y);
       }
     }
-    // (B) l = partner(s): k = D_mu (mu in [lo, b]), j = D_nu
-    const int nhi = dfib ? N - 1 : b;
-    for (int mu = lo + threadIdx.x; mu <= b; mu += blockDim.x) {
-      const int64_t kmu = d_index(B, mu);
-      double inner = 0.0;
-      for (int nu = lo; nu <= nhi; ++nu) {
-        const double2 av = ldA(A, d_index(B, nu), kmu);
-        inner = fma(Z[nu], dfib ? -av.y : av.x, inner);
+    // (B) l = partner(s): k = D_mu, j = D_nu, i.e. sum_{mu,nu} G_mu Z_nu X[nu][mu] with
+    //     G = -+ D^T (e_a - e_b), Z = D^T (e_a + e_b) (d-fibre) or -+ D^T (e_a - e_b),
+    //     X = -Im or Re of the D x D block of a: entries of H = D X D^T
+    if (!CLOSED) {  // every join term of the D x D block
+      const int lo = imax(a, 1), nhi = dfib ? N - 1 : b;
+      for (int mu = lo + threadIdx.x; mu <= b; mu += blockDim.x) {
+        const int64_t kmu = d_index(B, mu);
+        double inner = 0.0;
+        for (int nu = lo; nu <= nhi; ++nu) {
+          const double2 av = ldA(A, d_index(B, nu), kmu);
+          inner = fma(Z[nu], dfib ? -av.y : av.x, inner);
+        }
+        accD = fma(G[mu], inner, accD);
       }
-      accD = fma(G[mu], inner, accD);
+    } else if (threadIdx.x == 0) {
+      const int64_t aa = (int64_t)a * N + a, ab_ = (int64_t)a * N + b, ba = (int64_t)b * N + a,
+                    bb = (int64_t)b * N + b;
+      const double sgs = ts == kS ? -1.0 : 1.0;
+      if (dfib)
+        accD = -sgs * ((Hi[aa] - Hi[ab_]) + (Hi[ba] - Hi[bb]));
+      else
+        accD = sgs * (tn == kS ? -1.0 : 1.0) * ((Hr[aa] - Hr[ab_]) - (Hr[ba] - Hr[bb]));
     }
     double tot = warp_sum(0.5 * acc2 + accD);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
@@ -1860,17 +1985,27 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
     note_launch(1);
   }
   mark(4);
-  // 4: diagonal x diagonal
-  if (dense_out && e == cudaSuccess) {
-    const int64_t dd_warps = (int64_t)(N - 1) * (N - 1);
-    k_dd<<<(unsigned)((dd_warps * 32 + 255) / 256), 256, 0, st>>>(B, av, A, Q, R);
+  // closed: stream-ordered scratch for G (diagonal x diagonal) and H (same edge)
+  double* scratch = nullptr;
+  if (closed && e == cudaSuccess && (dense_out || A || R))
+    e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(double) * 3 * (size_t)N * N, st);
+  // 4: diagonal x diagonal (closed: d_nu^T G d_mu by prefix sums)
+  if (dense_out && e == cudaSuccess && N >= 2) {
+    if (closed) {
+      k_dd_g<<<(unsigned)N, 128, 0, st>>>(B, av, scratch);
+      k_dd2<<<(unsigned)(N - 1), 128, sizeof(double) * (2 * (size_t)N + 1), st>>>(B, scratch, A, Q, R);
+      note_launch(2);
+    } else {
+      const int64_t dd_warps = (int64_t)(N - 1) * (N - 1);
+      k_dd<<<(unsigned)((dd_warps * 32 + 255) / 256), 256, 0, st>>>(B, av, A, Q, R);
+    }
     note_launch(1);
   }
   mark(5);
   // 5: pair x pair on edges sharing one vertex (adds to R / A); closed: one
   //    block per vertex pair, which also writes the diagonal x pair entries
   if (dense_out && closed && e == cudaSuccess) {
-    const size_t smem = sizeof(double) * 16 * (size_t)(N + 1);
+    const size_t smem = sizeof(double) * 20 * (size_t)(N + 1);
     e = cudaFuncSetAttribute(k_shared_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) k_shared_closed<<<(unsigned)B.P, 256, smem, st>>>(B, av, h, A, Q, R);
     note_launch(1);
@@ -1881,10 +2016,18 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
     note_launch(1);
   }
   mark(6);
-  // 6: pair x pair on the same edge (adds to R / A)
+  // 6: pair x pair on the same edge (adds to R / A); its D-section sums come
+  //    from H = D X D^T of the D x D block of a (stream-ordered scratch)
   if ((A || R) && e == cudaSuccess) {
-    k_same<<<(unsigned)B.P, kSameThreads, sizeof(double) * 2 * N, st>>>(B, av, A, R);
-    note_launch(1);
+    if (closed) {
+      double* H = scratch + (size_t)N * N;
+      k_dh<<<(unsigned)N, 128, sizeof(double) * 2 * (size_t)N, st>>>(B, av, H, H + (size_t)N * N);
+      k_same<true><<<(unsigned)B.P, kSameThreads, 0, st>>>(B, av, H, H + (size_t)N * N, A, R);
+      note_launch(2);
+    } else {
+      k_same<false><<<(unsigned)B.P, kSameThreads, sizeof(double) * 2 * N, st>>>(B, av, nullptr, nullptr, A, R);
+      note_launch(1);
+    }
   }
   mark(7);
   // 7: K
@@ -1894,6 +2037,10 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
     note_launch(1);
   }
   mark(8);
+  if (scratch) {
+    const cudaError_t ef = cudaFreeAsync(scratch, st);
+    if (e == cudaSuccess) e = ef;
+  }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
