@@ -1469,22 +1469,6 @@ __device__ __forceinline__ void scan_inplace(double* arr, int n) {
   }
 }
 
-// sum_{mu in [max(lo,1), hi]} (delta_lo(mu) + sg * delta_hi(mu)) x_mu, with
-// cpre the prefix of c_mu x_mu and x the raw values: the end points lo and hi
-// in full, the interior (where the factor is c_mu for both signs) from cpre.
-__device__ __forceinline__ double dsum(const BasisView& B, const double* cpre, const double* x, int lo, int hi,
-                                       double sg, int top) {
-  // mu = lo (lo >= 1): delta_lo = lc_lo, delta_hi = 0
-  double s = 0.0;
-  if (lo >= 1) s += ld_lc(B, lo) * x[lo];
-  // lo < mu < hi: delta_lo = c_mu, delta_hi = 0
-  s += isum(cpre, imax(lo + 1, 1), hi - 1);
-  // mu = hi: delta_lo = c_hi, delta_hi = lc_hi
-  if (hi >= 1 && hi <= top) s += (ld_c(B, hi) + sg * ld_lc(B, hi)) * x[hi];
-  // mu > hi (d-fibers only, sg = +1): delta_lo + delta_hi = 2 c_mu
-  if (top > hi) s += 2.0 * isum(cpre, hi + 1, top);
-  return s;
-}
 
 // Staged data of one unordered vertex pair {p < q}, and accessors for the
 // orientation (P_, Q_) = (p, q) (tr = 0) or (q, p) (tr = 1).  For (q, p) the
@@ -1496,7 +1480,13 @@ struct PairStage {
   const double* TY;  // [2][L] Im
   const double* CX;  // [2][L] prefix of c_mu Re a[D_mu][(p,q) t]
   const double* CY;  // [2][L] prefix of c_mu Im
+  const double* DX;  // [2][L] (D x)_k = sum_mu delta_k(mu) Re a[D_mu][(p,q) t], k = 0..N-1
+  const double* DY;  // [2][L] the same for Im
+  const double* TOT; // [32] signed totals of the (A1) sums, see k_shared_closed
   int L;
+  // sum_mu (delta_lo(mu) + sg delta_hi(mu)) x_mu for lo < hi (the d-vector form of dsum)
+  __device__ __forceinline__ double dx(int t, int lo, int hi, double sg) const { return DX[t * L + lo] + sg * DX[t * L + hi]; }
+  __device__ __forceinline__ double dy(int t, int lo, int hi, double sg) const { return DY[t * L + lo] + sg * DY[t * L + hi]; }
   __device__ __forceinline__ double sre(int tr, int tj, int tk, int lo, int hi) const {
     return isum(PX + (tr ? tk * 2 + tj : tj * 2 + tk) * L, lo, hi);
   }
@@ -1513,26 +1503,23 @@ __device__ __forceinline__ double shared_entry_closed(const BasisView& B, const 
   const int N = B.N;
   const int64_t P = B.P;
   double acc2 = 0.0, accD = 0.0;
-  // (A1): w outside {v, P_, Q_}, in the four intervals between the sorted vertices
-  int b0 = v, b1 = P_, b2 = Q_, tmp;
-  if (b0 > b1) { tmp = b0; b0 = b1; b1 = tmp; }
-  if (b1 > b2) { tmp = b1; b1 = b2; b2 = tmp; }
-  if (b0 > b1) { tmp = b0; b0 = b1; b1 = tmp; }
-  const int ilo[4] = {0, b0 + 1, b1 + 1, b2 + 1}, ihi[4] = {b0 - 1, b1 - 1, b2 - 1, N - 1};
-#pragma unroll
-  for (int iv = 0; iv < 4; ++iv) {
-    if (ilo[iv] > ihi[iv]) continue;
-    const int w = ilo[iv];  // any w of the interval gives the same signs
+  // (A1): all w outside {v, P_, Q_}.  Every J edge's phase moves by 2 when
+  // its vertex order flips, which flips the sign of f (odd phase sums) and of
+  // d (even sums); the order of w and v enters sk and sf (sd) once each and
+  // cancels, so with sigma(w) = (-1)^([P_ < w] tk + [Q_ < w] tj) the sum is
+  // kappa (TOT - sigma(v) X(v)), TOT the block's signed total over all w.
+  {
+    const int a_ = coef_phase(ts, v, P_), b_ = coef_phase(tn, v, Q_);
+    const int pv = P_ < v ? 1 : 0, qv = Q_ < v ? 1 : 0;
 #pragma unroll
     for (int tl = 0; tl < 2; ++tl) {
       const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
-      const int phl = coef_phase(tl, w, v);
-      const int sk = sgn_f(coef_phase(ts, v, P_) + coef_phase(tk, P_, w) + phl);
-      const int base = coef_phase(tn, v, Q_) + phl;
-      const int sf = sgn_f(base + coef_phase(tjf, Q_, w));
-      const int sd = sgn_d(base + coef_phase(tjd, Q_, w));
-      acc2 += sgn_mul(sk * sf, S.sre(tr, tjf, tk, ilo[iv], ihi[iv]));
-      acc2 -= sgn_mul(sk * sd, S.sim(tr, tjd, tk, ilo[iv], ihi[iv]));
+      const int sk = sgn_f(a_ + tk + tl);  // phases at [P_ < w] = [w < v] = 0
+      const int kf = sk * sgn_f(b_ + tl + tjf), kd = sk * sgn_d(b_ + tl + tjd);
+      const int sfv = ((pv & tk) ^ (qv & tjf)) ? -1 : 1, sdv = ((pv & tk) ^ (qv & tjd)) ? -1 : 1;
+      const double* T = S.TOT + ((tr * 2 + ts) * 2 + tn) * 4 + tl * 2;
+      acc2 += sgn_mul(kf, T[0] - sgn_mul(sfv, S.sre(tr, tjf, tk, v, v)));
+      acc2 -= sgn_mul(kd, T[1] - sgn_mul(sdv, S.sim(tr, tjd, tk, v, v)));
     }
   }
   // (A3) e(l) = (v, Q_): k on (P_, Q_), j = D_mu
@@ -1542,8 +1529,8 @@ __device__ __forceinline__ double shared_entry_closed(const BasisView& B, const 
       const int tk = 1 ^ tl ^ ts;
       const int sk = sgn_f(coef_phase(ts, v, P_) + coef_phase(tk, P_, Q_) + coef_phase(tl, Q_, v));
       double part;
-      if (tl == tn) part = -dsum(B, S.CY + tk * S.L, S.TY + tk * S.L, lo, hi, 1.0, N - 1);
-      else part = (tn == kS ? -1.0 : 1.0) * dsum(B, S.CX + tk * S.L, S.TX + tk * S.L, lo, hi, -1.0, hi);
+      if (tl == tn) part = -S.dy(tk, lo, hi, 1.0);
+      else part = (tn == kS ? -1.0 : 1.0) * S.dx(tk, lo, hi, -1.0);
       accD += sgn_mul(sk, part) * kInvSqrt2;
     }
   }
@@ -1554,8 +1541,7 @@ __device__ __forceinline__ double shared_entry_closed(const BasisView& B, const 
     const int base = coef_phase(tn, v, Q_) + coef_phase(tl, P_, v);
     const int sf = sgn_f(base + coef_phase(tjf, Q_, P_));
     const int sd = sgn_d(base + coef_phase(tjd, Q_, P_));
-    double part = sgn_mul(sf, dsum(B, S.CX + tjf * S.L, S.TX + tjf * S.L, lo, hi, -1.0, hi)) +
-                  sgn_mul(sd, dsum(B, S.CY + tjd * S.L, S.TY + tjd * S.L, lo, hi, -1.0, hi));
+    double part = sgn_mul(sf, S.dx(tjf, lo, hi, -1.0)) + sgn_mul(sd, S.dy(tjd, lo, hi, -1.0));
     if (ts == kS) part = -part;
     accD += part * kInvSqrt2;
   }
@@ -1605,8 +1591,8 @@ __device__ __forceinline__ void dp_entry_closed(const BasisView& B, const PairSt
       const double fk = tl == kS ? -gn : gn;  // f(partner(l), l, D_nu), l on e(n)
       const int tkb = 1 - tl;
       double t;
-      if (tl == tn) t = -dsum(B, S.CY + tkb * S.L, S.TY + tkb * S.L, p, q, 1.0, N - 1);
-      else t = (tn == kS ? -1.0 : 1.0) * dsum(B, S.CX + tkb * S.L, S.TX + tkb * S.L, p, q, -1.0, q);
+      if (tl == tn) t = -S.dy(tkb, p, q, 1.0);
+      else t = (tn == kS ? -1.0 : 1.0) * S.dx(tkb, p, q, -1.0);
       acc = fma(fk, t, acc);
     }
     if (h != nullptr) qout = __ldg(h + (int64_t)(1 - tn) * P + pair_index(N, p, q)) * (tn == kS ? -gn : gn);
@@ -1633,6 +1619,9 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
   double* CX = sc + 12 * L;
   double* CY = sc + 14 * L;
   double* PU = sc + 16 * L;  // [4][L]: prefix over w of U for (tr, tn)
+  double* DXs = sc + 20 * L;  // [2][L]
+  double* DYs = sc + 22 * L;  // [2][L]
+  __shared__ double TOTs[32];
   const int64_t ppq = blockIdx.x;
   for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
     const int w = t >> 2, jk = t & 3, tj = jk >> 1, tk = jk & 1;
@@ -1663,7 +1652,34 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
     scan_inplace(arr, N);
   }
   __syncthreads();
-  const PairStage S{PX, PY, TX, TY, CX, CY, L};
+  // (D x)_k for the four staged D-column vectors: sum_{mu > k} c_mu x_mu + delta_k(k) x_k
+  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
+    const int arr = t / N, k = t % N, tt = arr & 1;
+    const double* C = (arr < 2 ? CX : CY) + tt * L;
+    const double* X = (arr < 2 ? TX : TY) + tt * L;
+    double d = C[N] - C[k + 1];  // mu from k + 1 to N - 1
+    if (k >= 1) d += dlt(B, k, k) * X[k];
+    (arr < 2 ? DXs : DYs)[tt * L + k] = d;
+  }
+  // (A1) totals: for (tr, ts, tn, tl), sum over w of sigma(w) X with
+  // sigma(w) = (-1)^([P_ < w] tk + [Q_ < w] tj), f (Re, tj = tjf) and d (Im, tj = tjd)
+  const PairStage S0{PX, PY, TX, TY, CX, CY, DXs, DYs, TOTs, L};
+  if (threadIdx.x < 32 * 8) {
+    const int c = threadIdx.x >> 3, sub = threadIdx.x & 7;  // 8 threads per total
+    const int tr = c >> 4, ts = (c >> 3) & 1, tn = (c >> 2) & 1, tl = (c >> 1) & 1, fd = c & 1;
+    const int P_ = tr ? q : p, Q_ = tr ? p : q;
+    const int tk = 1 ^ tl ^ ts, tj = fd ? (tl ^ tn) : (1 ^ tl ^ tn);
+    double acc = 0.0;
+    for (int w = sub; w < N; w += 8) {
+      const double x = fd ? S0.sim(tr, tj, tk, w, w) : S0.sre(tr, tj, tk, w, w);
+      const int sg = ((P_ < w ? tk : 0) ^ (Q_ < w ? tj : 0)) ? -1 : 1;
+      acc += sgn_mul(sg, x);
+    }
+    for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, 8);
+    if (sub == 0) TOTs[c] = acc;
+  }
+  __syncthreads();
+  const PairStage S{PX, PY, TX, TY, CX, CY, DXs, DYs, TOTs, L};
   // diagonal x pair families: for orientation tr (v = p or q, v' the other)
   // and column type tn, U_w = sigma_v(w) sum_tl tau_l (sf X_re - sd X_im) at
   // the single w, with X the staged a[(v',w) tj][(v,w) tk] (k = partner(l)),
@@ -2005,7 +2021,7 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
   // 5: pair x pair on edges sharing one vertex (adds to R / A); closed: one
   //    block per vertex pair, which also writes the diagonal x pair entries
   if (dense_out && closed && e == cudaSuccess) {
-    const size_t smem = sizeof(double) * 20 * (size_t)(N + 1);
+    const size_t smem = sizeof(double) * 24 * (size_t)(N + 1);
     e = cudaFuncSetAttribute(k_shared_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) k_shared_closed<<<(unsigned)B.P, 256, smem, st>>>(B, av, h, A, Q, R);
     note_launch(1);
