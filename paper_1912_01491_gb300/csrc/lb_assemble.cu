@@ -858,72 +858,36 @@ __device__ __forceinline__ void quad_group_fp64_t(const double (&V)[3][2][2][2],
   o[3] = -0.5 * (xs1 - xs0);
 }
 
-// Loads of matching y of the quadruple: a[(p,q)][(r,t)], a[(p,r)][(q,t)] and
-// a[(q,r)][(p,t)] (four type pairs each).
-template <int Y>
-__device__ __forceinline__ void quad_load(const AView& A, int64_t P, const QuadIdx& I, double2 (&L)[2][2]) {
-  constexpr int re = Y == 0 ? 0 : Y == 1 ? 2 : 5, ce = Y == 0 ? 1 : Y == 1 ? 3 : 4;
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) L[i][j] = __ldg(A.a + (i * P + I.e[re]) * A.M + j * P + I.e[ce]);
-}
-
-// The eight entries of matching MM (both orientations): its values come from
-// the two other matchings, aligned to their own largest exponent.
+// FP64 form of the eight entries of matching MM from the loaded values.
 template <int MM>
-__device__ __forceinline__ void quad_pass(const AView& A, int64_t P, int64_t M, const QuadIdx& I,
-                                          double* __restrict__ Aout, double* __restrict__ Qout,
-                                          double* __restrict__ Rout) {
-  constexpr int Y = MM == 0 ? 1 : 0, Z = MM == 2 ? 1 : 2;
-  double2 Ly[2][2], Lz[2][2];
-  quad_load<Y>(A, P, I, Ly);
-  quad_load<Z>(A, P, I, Lz);
-  int E = 1;
+__device__ __forceinline__ void quad_fp64_matching(const double2 (&L)[3][2][2], int64_t P, int64_t M,
+                                                   const QuadIdx& I, double* __restrict__ Aout,
+                                                   double* __restrict__ Qout, double* __restrict__ Rout) {
+  double V[3][2][2][2];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-      E = max(E, max(max(fx_exponent(Ly[i][j].x), fx_exponent(Ly[i][j].y)),
-                     max(fx_exponent(Lz[i][j].x), fx_exponent(Lz[i][j].y))));
-  if (E < 64 || E > 2040) {  // not finite, or the converted exponent would leave the normal range: FP64
-    double V[3][2][2][2];
+  for (int y = 0; y < 3; ++y)
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        V[Y][i][j][0] = Ly[i][j].x;
-        V[Y][i][j][1] = Ly[i][j].y;
-        V[Z][i][j][0] = Lz[i][j].x;
-        V[Z][i][j][1] = Lz[i][j].y;
+        V[y][i][j][0] = L[y][i][j].x;
+        V[y][i][j][1] = L[y][i][j].y;
       }
-    double o[4];
-    quad_group_fp64_t<MM, 0>(V, o);
-    quad_store<MM, 0>(I, P, M, o, Aout, Qout, Rout);
-    quad_group_fp64_t<MM, 1>(V, o);
-    quad_store<MM, 1>(I, P, M, o, Aout, Qout, Rout);
-    return;
-  }
-  long long D[3][2][2][2];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      D[Y][i][j][0] = fx_align(fx_split(Ly[i][j].x), E, 0u);
-      D[Y][i][j][1] = fx_align(fx_split(Ly[i][j].y), E, 0u);
-      D[Z][i][j][0] = fx_align(fx_split(Lz[i][j].x), E, 0u);
-      D[Z][i][j][1] = fx_align(fx_split(Lz[i][j].y), E, 0u);
-    }
-  quad_group<MM, 0>(D, E, P, M, I, Aout, Qout, Rout);
-  quad_group<MM, 1>(D, E, P, M, I, Aout, Qout, Rout);
+  double o[4];
+  quad_group_fp64_t<MM, 0>(V, o);
+  quad_store<MM, 0>(I, P, M, o, Aout, Qout, Rout);
+  quad_group_fp64_t<MM, 1>(V, o);
+  quad_store<MM, 1>(I, P, M, o, Aout, Qout, Rout);
 }
 
 // One block per edge (p, q); threads run over the edges (r, t) with
-// q < r < t, i.e. the contiguous pair indices from (q+1, q+2) to P - 1.  The
-// three output matchings are done one after the other, each reading the two
-// others (the second reads of a value hit L1).
-__global__ void __launch_bounds__(256, 2) k_disjoint4(BasisView B, AView A, double* __restrict__ Aout,
-                                                   double* __restrict__ Qout, double* __restrict__ Rout) {
+// q < r < t, i.e. the contiguous pair indices from (q+1, q+2) to P - 1.  All
+// 12 a values of the quadruple are loaded at once; they are aligned to one
+// exponent E (the quadruple's largest), and an output matching whose own
+// values lie more than 10 binades below E is formed in FP64 instead.
+constexpr int kQuadThreads = 256;
+__global__ void __launch_bounds__(kQuadThreads, 1) k_disjoint4(BasisView B, AView A, double* __restrict__ Aout,
+                                                               double* __restrict__ Qout, double* __restrict__ Rout) {
   const int N = B.N;
   const int64_t P = B.P, M = B.M;
   const int64_t pq = blockIdx.x;
@@ -943,9 +907,52 @@ __global__ void __launch_bounds__(256, 2) k_disjoint4(BasisView B, AView A, doub
     I.e[3] = base_q + t;
     I.e[4] = base_p + t;
     I.e[5] = base_q + r;
-    quad_pass<0>(A, P, M, I, Aout, Qout, Rout);
-    quad_pass<1>(A, P, M, I, Aout, Qout, Rout);
-    quad_pass<2>(A, P, M, I, Aout, Qout, Rout);
+    double2 L[3][2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        L[0][i][j] = __ldg(A.a + (i * P + I.e[0]) * M + j * P + I.e[1]);
+        L[1][i][j] = __ldg(A.a + (i * P + I.e[2]) * M + j * P + I.e[3]);
+        L[2][i][j] = __ldg(A.a + (i * P + I.e[5]) * M + j * P + I.e[4]);
+      }
+    int Ey[3];
+#pragma unroll
+    for (int y = 0; y < 3; ++y) {
+      Ey[y] = 1;
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+          Ey[y] = max(Ey[y], max(fx_exponent(L[y][i][j].x), fx_exponent(L[y][i][j].y)));
+    }
+    const int E = max(Ey[0], max(Ey[1], Ey[2]));
+    const bool ok = E >= 64 && E <= 2040;
+    const bool ex0 = ok && E - max(Ey[1], Ey[2]) <= 10;  // matching 0 reads matchings 1 and 2
+    const bool ex1 = ok && E - max(Ey[0], Ey[2]) <= 10;
+    const bool ex2 = ok && E - max(Ey[0], Ey[1]) <= 10;
+    if (ex0 && ex1 && ex2) {
+      long long D[3][2][2][2];
+#pragma unroll
+      for (int y = 0; y < 3; ++y)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            D[y][i][j][0] = fx_align(fx_split(L[y][i][j].x), E, 0u);
+            D[y][i][j][1] = fx_align(fx_split(L[y][i][j].y), E, 0u);
+          }
+      quad_group<0, 0>(D, E, P, M, I, Aout, Qout, Rout);
+      quad_group<0, 1>(D, E, P, M, I, Aout, Qout, Rout);
+      quad_group<1, 0>(D, E, P, M, I, Aout, Qout, Rout);
+      quad_group<1, 1>(D, E, P, M, I, Aout, Qout, Rout);
+      quad_group<2, 0>(D, E, P, M, I, Aout, Qout, Rout);
+      quad_group<2, 1>(D, E, P, M, I, Aout, Qout, Rout);
+    } else {  // rare: values not finite, tiny, or of widely different magnitude
+      quad_fp64_matching<0>(L, P, M, I, Aout, Qout, Rout);
+      quad_fp64_matching<1>(L, P, M, I, Aout, Qout, Rout);
+      quad_fp64_matching<2>(L, P, M, I, Aout, Qout, Rout);
+    }
   }
 }
 
@@ -1964,7 +1971,7 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
   if (dense_out) {
     if (closed) {
       if (N >= 4) {
-        k_disjoint4<<<(unsigned)B.P, 256, 0, st>>>(B, av, A, Q, R);
+        k_disjoint4<<<(unsigned)B.P, kQuadThreads, 0, st>>>(B, av, A, Q, R);
         note_launch(1);
       }
     } else {
