@@ -331,7 +331,11 @@ def run_gb300(args):
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture on a
 # smaller case, with the units that capture processed; scaled to a launch of
 # the bench size by units.  Kept only for the kernel version the capture saw.
-NCU_TRAFFIC = {}  # filled from the committed ncu summary of the current kernel version
+NCU_TRAFFIC = {
+    "k_entries (pair x pair; closed: disjoint edges by vertex quadruple)": {
+        "N": 100, "bytes": 1.073918e9 + 0.845068e9, "units": lambda N: N * (N - 1.0) * (N - 2.0) * (N - 3.0),
+        "source": "profiles/dense_assembly_n100.md"},
+}
 
 
 def ncu_traffic(kernel, N):
@@ -348,8 +352,9 @@ def assembly_roofline(algorithm, top, top_ms, N, M, W, fp64_peak, peaks):
     t = top_ms * 1e-3
     hbm = peaks.get("hbm_gbs")
     if top.startswith("k_entries") and algorithm == "closed":
-        # reads every a entry of the pair x pair block once, writes A there once
-        byts = 24.0 * P2 * P2
+        # the disjoint pair x pair block: one orientation of the Hermitian a-block
+        # (8 B per entry) read once, A written once (8 B per entry)
+        byts = 16.0 * 24.0 * N * (N - 1.0) * (N - 2.0) * (N - 3.0) / 24.0
         traffic, src = ncu_traffic(top, N)
         return {"kernel": top, "bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm, "unit": "GB/s",
                 "frac": byts / t / 1e9 / hbm if hbm else None, "traffic": traffic,
