@@ -333,8 +333,8 @@ def run_gb300(args):
 # the bench size by units.  Kept only for the kernel version the capture saw.
 NCU_TRAFFIC = {
     "k_entries (pair x pair; closed: disjoint edges by vertex quadruple)": {
-        "N": 100, "bytes": 1.073918e9 + 0.845068e9, "units": lambda N: N * (N - 1.0) * (N - 2.0) * (N - 3.0),
-        "source": "profiles/dense_assembly_n100.md"},
+        "N": 200, "bytes": 18.53e9 + 16.98e9, "units": lambda N: N * (N - 1.0) * (N - 2.0) * (N - 3.0),
+        "source": "profiles/dense_assembly_n100.md (full-size DRAM capture at N=200)"},
 }
 
 
@@ -358,7 +358,7 @@ def assembly_roofline(algorithm, top, top_ms, N, M, W, fp64_peak, peaks):
         traffic, src = ncu_traffic(top, N)
         return {"kernel": top, "bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm, "unit": "GB/s",
                 "frac": byts / t / 1e9 / hbm if hbm else None, "traffic": traffic,
-                "traffic_source": src and ("%s, scaled from N=100 by the number of vertex quadruples" % src),
+                "traffic_source": src and ("%s, scaled by the number of vertex quadruples" % src),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "algorithmic_bytes_per_launch": byts}
     if top.startswith("k_entries"):
