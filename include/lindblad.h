@@ -349,6 +349,31 @@ int lb_system_get(const lb_system_t *sys, int part, double *out);
 int lb_integrate(lb_system_t *sys, int precision, int correct_every, const double *v0,
                  double t, double dt, double *v_out);
 
+/* Checkpoint and resume.  There is no counterpart in the paper; it serves
+ * long integrations that are stopped and continued.
+ *
+ * lb_system_save writes the system to the file `path`: a 64-byte header
+ * ("LBSYS001", N, M, a mask of the parts present, format version), then A
+ * (M x M FP64, row-major), K (M), and Q, R if they were kept, all little
+ * endian.  It copies in bounded chunks through host memory and is
+ * synchronous.  LB_EINVAL if the file cannot be written.
+ *
+ * lb_system_load reads such a file for basis b (whose N must match) into a
+ * new system owned by the caller; the low-precision copies are made again on
+ * first use.  LB_EINVAL for a missing, truncated or foreign file;
+ * LB_ENOMEM / LB_ECUDA on device failure.
+ *
+ * lb_integrate_resume advances the host state v (M doubles, in place) by
+ * nsteps RK4 steps of size dt.  When every earlier segment had a multiple of
+ * correct_every steps (any length for LB_FP64, or for correct_every = 0),
+ * the segments give the same bits as one lb_integrate over their total:
+ * each segment starts from v exactly as a step boundary of one run does.
+ * Synchronous. */
+int lb_system_save(const lb_system_t *sys, const char *path);
+int lb_system_load(const lb_basis_t *b, const char *path, lb_system_t **out);
+int lb_integrate_resume(lb_system_t *sys, int precision, int correct_every, double *v, double dt,
+                        int64_t nsteps);
+
 /* ------------------------------------------------------------------------
  * Measurement helpers (no counterpart in the paper).
  * --------------------------------------------------------------------- */

@@ -6,7 +6,10 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <vector>
 #include <cub/cub.cuh>
 #include <string>
 
@@ -501,6 +504,133 @@ int lb_system_destroy(lb_system_t* s) {
   return LB_OK;
 }
 
+namespace {
+
+// File format of lb_system_save: a 64-byte header, then the parts.
+struct SysFileHeader {
+  char magic[8];     // "LBSYS001"
+  int64_t N, M;
+  int64_t parts;     // bit 0 A, 1 K, 2 Q, 3 R
+  int64_t version;   // 1
+  int64_t reserved[3];
+};
+static_assert(sizeof(SysFileHeader) == 64, "header is 64 bytes");
+
+constexpr size_t kFileChunk = size_t(64) << 20;  // bytes per host bounce
+
+bool write_device(FILE* f, const double* d, size_t count, std::string& err) {
+  std::vector<char> buf(std::min(kFileChunk, 8 * count + 1));
+  size_t done = 0;
+  while (done < 8 * count) {
+    const size_t n = std::min(buf.size(), 8 * count - done);
+    const cudaError_t e = cudaMemcpy(buf.data(), reinterpret_cast<const char*>(d) + done, n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      err = cudaGetErrorString(e);
+      return false;
+    }
+    if (fwrite(buf.data(), 1, n, f) != n) {
+      err = "short write";
+      return false;
+    }
+    done += n;
+  }
+  return true;
+}
+
+bool read_device(FILE* f, double* d, size_t count, std::string& err) {
+  std::vector<char> buf(std::min(kFileChunk, 8 * count + 1));
+  size_t done = 0;
+  while (done < 8 * count) {
+    const size_t n = std::min(buf.size(), 8 * count - done);
+    if (fread(buf.data(), 1, n, f) != n) {
+      err = "file is truncated";
+      return false;
+    }
+    const cudaError_t e = cudaMemcpy(reinterpret_cast<char*>(d) + done, buf.data(), n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      err = cudaGetErrorString(e);
+      return false;
+    }
+    done += n;
+  }
+  return true;
+}
+
+}  // namespace
+
+int lb_system_save(const lb_system_t* s, const char* path) {
+  LB_REQUIRE(s && path, "lb_system_save: NULL argument");
+  FILE* f = fopen(path, "wb");
+  LB_REQUIRE(f != nullptr, "lb_system_save: cannot open %s for writing", path);
+  SysFileHeader h{};
+  memcpy(h.magic, "LBSYS001", 8);
+  h.N = s->basis->N;
+  h.M = s->M;
+  h.parts = (s->A ? 1 : 0) | (s->K ? 2 : 0) | (s->Q ? 4 : 0) | (s->R ? 8 : 0);
+  h.version = 1;
+  std::string err;
+  const size_t mm = (size_t)s->M * (size_t)s->M;
+  bool ok = fwrite(&h, sizeof h, 1, f) == 1;
+  if (!ok) err = "short write";
+  if (ok && s->A) ok = write_device(f, s->A, mm, err);
+  if (ok && s->K) ok = write_device(f, s->K, (size_t)s->M, err);
+  if (ok && s->Q) ok = write_device(f, s->Q, mm, err);
+  if (ok && s->R) ok = write_device(f, s->R, mm, err);
+  if (fclose(f) != 0 && ok) {
+    ok = false;
+    err = "close failed";
+  }
+  if (!ok) {
+    cudaGetLastError();
+    lbi::set_error("lb_system_save: %s: %s", path, err.c_str());
+    return LB_EINVAL;
+  }
+  return LB_OK;
+}
+
+int lb_system_load(const lb_basis_t* b, const char* path, lb_system_t** out) {
+  LB_REQUIRE(b && path && out, "lb_system_load: NULL argument");
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  LB_REQUIRE(f != nullptr, "lb_system_load: cannot open %s", path);
+  SysFileHeader h{};
+  const bool hdr = fread(&h, sizeof h, 1, f) == 1;
+  if (!hdr || memcmp(h.magic, "LBSYS001", 8) != 0 || h.version != 1 || h.N != b->N || h.M != b->M ||
+      !(h.parts & 1) || !(h.parts & 2)) {
+    fclose(f);
+    lbi::set_error("lb_system_load: %s is not a system file for N = %d", path, b->N);
+    return LB_EINVAL;
+  }
+  const size_t mm = (size_t)b->M * (size_t)b->M;
+  int rc;
+  DevBuf dA, dK, dQ, dR;
+  if ((rc = alloc_or_enomem(dA, 8 * mm, "A")) != LB_OK || (rc = alloc_or_enomem(dK, 8 * (size_t)b->M, "K")) != LB_OK ||
+      ((h.parts & 4) && (rc = alloc_or_enomem(dQ, 8 * mm, "Q")) != LB_OK) ||
+      ((h.parts & 8) && (rc = alloc_or_enomem(dR, 8 * mm, "R")) != LB_OK)) {
+    fclose(f);
+    return rc;
+  }
+  std::string err;
+  bool ok = read_device(f, dA.as<double>(), mm, err) && read_device(f, dK.as<double>(), (size_t)b->M, err);
+  if (ok && (h.parts & 4)) ok = read_device(f, dQ.as<double>(), mm, err);
+  if (ok && (h.parts & 8)) ok = read_device(f, dR.as<double>(), mm, err);
+  fclose(f);
+  if (!ok) {
+    cudaGetLastError();
+    lbi::set_error("lb_system_load: %s: %s", path, err.c_str());
+    return LB_EINVAL;
+  }
+  lb_system* s = new lb_system;
+  s->basis = b;
+  s->M = b->M;
+  s->A = static_cast<double*>(dA.release());
+  s->K = static_cast<double*>(dK.release());
+  s->Q = static_cast<double*>(dQ.release());
+  s->R = static_cast<double*>(dR.release());
+  *out = s;
+  return LB_OK;
+}
+
 int lb_system_get(const lb_system_t* s, int part, double* out) {
   LB_REQUIRE(s && out, "lb_system_get: NULL argument");
   const double* src = part == LB_SYS_A ? s->A : part == LB_SYS_Q ? s->Q : part == LB_SYS_R ? s->R
@@ -511,6 +641,9 @@ int lb_system_get(const lb_system_t* s, int part, double* out) {
   return LB_OK;
 }
 
+static int integrate_steps(lb_system_t* s, int precision, int correct_every, const double* v0, double dt,
+                           int64_t n, double* v_out);
+
 int lb_integrate(lb_system_t* s, int precision, int correct_every, const double* v0, double t, double dt,
                  double* v_out) {
   LB_REQUIRE(s && v0 && v_out, "lb_integrate: NULL argument");
@@ -518,6 +651,18 @@ int lb_integrate(lb_system_t* s, int precision, int correct_every, const double*
   const double nr = std::nearbyint(t / dt);
   const int64_t n = (int64_t)nr;
   LB_REQUIRE(std::fabs(nr * dt - t) <= 1e-9 * t, "lb_integrate: t = %g is not a multiple of dt = %g", t, dt);
+  return integrate_steps(s, precision, correct_every, v0, dt, n, v_out);
+}
+
+int lb_integrate_resume(lb_system_t* s, int precision, int correct_every, double* v, double dt, int64_t nsteps) {
+  LB_REQUIRE(s && v, "lb_integrate_resume: NULL argument");
+  LB_REQUIRE(dt > 0 && std::isfinite(dt) && nsteps >= 0 && correct_every >= 0,
+             "lb_integrate_resume: bad dt, step count or correction period");
+  return integrate_steps(s, precision, correct_every, v, dt, nsteps, v);
+}
+
+static int integrate_steps(lb_system_t* s, int precision, int correct_every, const double* v0, double dt,
+                           int64_t n, double* v_out) {
   const int64_t M = s->M;
   const size_t mm = (size_t)M * (size_t)M;
   int rc;

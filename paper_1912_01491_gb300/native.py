@@ -85,6 +85,9 @@ def load():
         "lb_assemble": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
         "lb_system_destroy": (ctypes.c_int, [_vp]),
         "lb_system_get": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+        "lb_system_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+        "lb_system_load": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.POINTER(_vp)]),
+        "lb_integrate_resume": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, _c_i64]),
         "lb_integrate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double,
                                         ctypes.c_double, _vp]),
         "lb_assemble_lowrank_csr": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp,
@@ -457,6 +460,9 @@ class System:
 
     def __init__(self, basis, a, H=None, keep_parts=False, algorithm="join"):
         lib = load()
+        if isinstance(a, _vp):  # an already created handle (System.load)
+            self._h, self.basis, self.M = a, basis, basis.M
+            return
         a = np.ascontiguousarray(a, np.complex128)
         assert a.shape == (basis.M, basis.M)
         Hc = None if H is None else np.ascontiguousarray(H, np.complex128)
@@ -490,6 +496,22 @@ class System:
         _check(load().lb_integrate(self._h, PRECISIONS[precision], int(correct_every), _ptr(v0), float(t),
                                    float(dt), _ptr(out)))
         return out
+
+    def integrate_resume(self, v, dt, nsteps, precision="fp64", correct_every=0):
+        """Advance the host state v (float64, M) in place by nsteps RK4 steps."""
+        assert isinstance(v, np.ndarray) and v.dtype == np.float64 and v.flags.c_contiguous
+        _check(load().lb_integrate_resume(self._h, PRECISIONS[precision], int(correct_every), _ptr(v), float(dt),
+                                          int(nsteps)))
+        return v
+
+    def save(self, path):
+        _check(load().lb_system_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, basis, path):
+        h = _vp()
+        _check(load().lb_system_load(basis.handle, os.fsencode(path), ctypes.byref(h)))
+        return cls(basis, h)
 
 
 def request_bytes(N, precision="fp32", with_H=True):

@@ -236,3 +236,37 @@ def test_empty_and_degenerate_inputs():
         assert torch.equal(v, torch.arange(8, dtype=torch.float64, device="cuda"))
     with pytest.raises(lb.LBError):
         lb.Basis(1)
+
+
+def test_system_save_load_and_resume(tmp_path):
+    """A saved and reloaded system is bit-identical; an integration split at
+    multiples of the correction period gives the bits of one run."""
+    N = 7
+    H, a = _case(N, 707)
+    lb = lbm()
+    with lb.Basis(N) as B, Oracle(N) as o:
+        sysm = lb.System(B, a, H=H, keep_parts=True, algorithm="closed")
+        path = str(tmp_path / "sys.lbs")
+        sysm.save(path)
+        back = lb.System.load(B, path)
+        for part in "AKQR":
+            assert np.array_equal(back.get(part), sysm.get(part)), part
+        v0 = o.expand(wl.pure_state(N, 1))[0].real
+        for prec, corr in (("fp64", 0), ("fp32", 50), ("bf16", 25)):
+            one = sysm.integrate(v0, 300 * 1e-3, 1e-3, precision=prec, correct_every=corr)
+            v = v0.copy()
+            back.integrate_resume(v, 1e-3, 100, precision=prec, correct_every=corr)
+            back.integrate_resume(v, 1e-3, 150, precision=prec, correct_every=corr)
+            back.integrate_resume(v, 1e-3, 50, precision=prec, correct_every=corr)
+            assert np.array_equal(v, one), prec
+        with lb.Basis(N + 1) as B2:
+            with pytest.raises(lb.LBError):
+                lb.System.load(B2, path)
+        with pytest.raises(lb.LBError):
+            lb.System.load(B, str(tmp_path / "missing.lbs"))
+        with open(path, "r+b") as f:  # truncate: the loader reports it, the GPU is untouched
+            f.truncate(1000)
+        with pytest.raises(lb.LBError):
+            lb.System.load(B, path)
+        back.close()
+        sysm.close()
