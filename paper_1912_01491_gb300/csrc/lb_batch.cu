@@ -82,27 +82,24 @@ __device__ __forceinline__ int row_group_width(int64_t M) {
   return M >= 256 ? 32 : M >= 96 ? 16 : M >= 32 ? 8 : 4;
 }
 
-// Partial dot product of one lane of a W-lane row group: four independent
-// accumulators when the row is long (loads of four iterations in flight),
-// one when it is short (no extra adds, which matter for FP64).
+// Multiply-add in the element type (an explicit FP32 FMA for float, so that
+// no operand is promoted to FP64).
+__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
+
+// Partial dot product of one lane of a W-lane row group.  Full-warp rows use
+// a compile-time stride, which the compiler unrolls with the loads of several
+// iterations in flight (long rows stream from L2); short rows use W lanes.
 template <class T>
 __device__ __forceinline__ T group_dot(const T* __restrict__ row, const T* __restrict__ x, int64_t M, int sub,
                                        int W) {
-  int64_t n = sub;
-  T a0 = T(0);
-  if (M >= 16 * (int64_t)W) {
-    T a1 = T(0), a2 = T(0), a3 = T(0);
-    for (; n + 3 * W < M; n += 4 * W) {
-      a0 = fma(row[n], x[n], a0);
-      a1 = fma(row[n + W], x[n + W], a1);
-      a2 = fma(row[n + 2 * W], x[n + 2 * W], a2);
-      a3 = fma(row[n + 3 * W], x[n + 3 * W], a3);
-    }
-    for (; n < M; n += W) a0 = fma(row[n], x[n], a0);
-    return (a0 + a1) + (a2 + a3);
+  T a = T(0);
+  if (W == 32) {
+    for (int64_t n = sub; n < M; n += 32) a = mad(row[n], x[n], a);
+  } else {
+    for (int64_t n = sub; n < M; n += W) a = mad(row[n], x[n], a);
   }
-  for (; n < M; n += W) a0 = fma(row[n], x[n], a0);
-  return a0;
+  return a;
 }
 
 // Takes the next realization for this cluster; every block returns the same
@@ -115,7 +112,7 @@ __device__ __forceinline__ int next_item(cg::cluster_group& cluster, int rank, i
   return qi;
 }
 
-__global__ void __launch_bounds__(256) k_rk4_batch(const BItem* __restrict__ items, const int* __restrict__ order,
+__global__ void __launch_bounds__(256, 4) k_rk4_batch(const BItem* __restrict__ items, const int* __restrict__ order,
                                                    int nitems, int* __restrict__ counter, int64_t nsteps, double dt,
                                                    int correct_every, SmemLayout L) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -232,7 +229,7 @@ SmemLayout64 layout64(int64_t mmax, int C, bool resident) {
   return L;
 }
 
-__global__ void __launch_bounds__(256) k_rk4_batch64(const BItem* __restrict__ items, const int* __restrict__ order,
+__global__ void __launch_bounds__(256, 4) k_rk4_batch64(const BItem* __restrict__ items, const int* __restrict__ order,
                                                      int nitems, int* __restrict__ counter, int64_t nsteps,
                                                      double dt, SmemLayout64 L) {
   extern __shared__ __align__(16) unsigned char smem[];
