@@ -314,6 +314,18 @@ def run_gb300(args):
             "frac": 2.0 * M * M * 4 * nrk * K_ / (rk_ms * 1e-3) / 1e12 / fp64_peak,
             "achieved_gbs": 8.0 * M * M * 4 * nrk * K_ / (rk_ms * 1e-3) / 1e9,
         },
+        "rk4_fp32_roofline": {
+            "kernel": "k_stage<FP32> (fused GEMV + stage update, 16-byte loads) + k_correction<FP32>",
+            "bound": "hbm",
+            # per RK4 step 4 reads of A32; one FP64 correction (A64 + A32) per 50 steps, and the
+            # run of nrk steps starts with one
+            "achieved": (4.0 * 4.0 * M * M * nrk + 12.0 * M * M * max(1, nrk // 50)) * K_
+                        / (rk32_ms * 1e-3) / 1e9,
+            "peak": peaks.get("hbm_gbs"),
+            "unit": "GB/s",
+            "frac": ((4.0 * 4.0 * M * M * nrk + 12.0 * M * M * max(1, nrk // 50)) * K_ / (rk32_ms * 1e-3) / 1e9
+                     / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
+        },
         "gpu_launches": launches,
         "clocks": clk,
     }

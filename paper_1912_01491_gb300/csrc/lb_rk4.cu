@@ -49,30 +49,66 @@ __device__ __forceinline__ double row_dot(int64_t M, int64_t s, const void* __re
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     return t;
   } else if (PREC == LB_FP32) {
+    // 16-byte loads of the row: a scalar head up to the first 16-byte
+    // boundary (rows start anywhere for odd M), float4 vectors, a scalar tail
     const float* __restrict__ row = static_cast<const float*>(Ap) + s * M;
+    const int64_t h4 = (int64_t)(((16 - ((uintptr_t)row & 15)) & 15) >> 2);
+    const int head = (int)(h4 < M ? h4 : M);
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    int64_t n = lane;
-    for (; n + 96 < M; n += 128) {
-      a0 = fmaf(__ldcs(row + n), __ldg(x32 + n), a0);
-      a1 = fmaf(__ldcs(row + n + 32), __ldg(x32 + n + 32), a1);
-      a2 = fmaf(__ldcs(row + n + 64), __ldg(x32 + n + 64), a2);
-      a3 = fmaf(__ldcs(row + n + 96), __ldg(x32 + n + 96), a3);
+    if (lane < head) a0 = fmaf(__ldcs(row + lane), __ldg(x32 + lane), a0);
+    const float4* __restrict__ rv = reinterpret_cast<const float4*>(row + head);
+    const float* __restrict__ xv = x32 + head;
+    const int64_t nv = (M - head) >> 2;
+    int64_t k = lane;
+    for (; k + 32 < nv; k += 64) {
+      const float4 u = __ldcs(rv + k), w = __ldcs(rv + k + 32);
+      const float* xu = xv + 4 * k;
+      const float* xw = xv + 4 * (k + 32);
+      a0 = fmaf(u.x, __ldg(xu), a0);
+      a1 = fmaf(u.y, __ldg(xu + 1), a1);
+      a2 = fmaf(u.z, __ldg(xu + 2), a2);
+      a3 = fmaf(u.w, __ldg(xu + 3), a3);
+      a0 = fmaf(w.x, __ldg(xw), a0);
+      a1 = fmaf(w.y, __ldg(xw + 1), a1);
+      a2 = fmaf(w.z, __ldg(xw + 2), a2);
+      a3 = fmaf(w.w, __ldg(xw + 3), a3);
     }
-    for (; n < M; n += 32) a0 = fmaf(__ldcs(row + n), __ldg(x32 + n), a0);
+    for (; k < nv; k += 32) {
+      const float4 u = __ldcs(rv + k);
+      const float* xu = xv + 4 * k;
+      a0 = fmaf(u.x, __ldg(xu), a0);
+      a1 = fmaf(u.y, __ldg(xu + 1), a1);
+      a2 = fmaf(u.z, __ldg(xu + 2), a2);
+      a3 = fmaf(u.w, __ldg(xu + 3), a3);
+    }
+    for (int64_t n = head + 4 * nv + lane; n < M; n += 32) a0 = fmaf(__ldcs(row + n), __ldg(x32 + n), a0);
     double t = ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     return t;
   } else {
+    // BF16: 16-byte loads of eight values, head and tail as for FP32
     const uint16_t* __restrict__ row = static_cast<const uint16_t*>(Ap) + s * M;
+    const int64_t h2 = (int64_t)(((16 - ((uintptr_t)row & 15)) & 15) >> 1);
+    const int head = (int)(h2 < M ? h2 : M);
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    int64_t n = lane;
-    for (; n + 96 < M; n += 128) {
-      a0 = fmaf(bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(row + n))), __ldg(x32 + n), a0);
-      a1 = fmaf(bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(row + n + 32))), __ldg(x32 + n + 32), a1);
-      a2 = fmaf(bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(row + n + 64))), __ldg(x32 + n + 64), a2);
-      a3 = fmaf(bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(row + n + 96))), __ldg(x32 + n + 96), a3);
+    if (lane < head)
+      a0 = fmaf(bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(row + lane))), __ldg(x32 + lane), a0);
+    const uint4* __restrict__ rv = reinterpret_cast<const uint4*>(row + head);
+    const float* __restrict__ xv = x32 + head;
+    const int64_t nv = (M - head) >> 3;
+    for (int64_t k = lane; k < nv; k += 32) {
+      const uint4 u = __ldcs(rv + k);
+      const float* xu = xv + 8 * k;
+      a0 = fmaf(__uint_as_float(u.x << 16), __ldg(xu), a0);
+      a1 = fmaf(__uint_as_float(u.x & 0xffff0000u), __ldg(xu + 1), a1);
+      a2 = fmaf(__uint_as_float(u.y << 16), __ldg(xu + 2), a2);
+      a3 = fmaf(__uint_as_float(u.y & 0xffff0000u), __ldg(xu + 3), a3);
+      a0 = fmaf(__uint_as_float(u.z << 16), __ldg(xu + 4), a0);
+      a1 = fmaf(__uint_as_float(u.z & 0xffff0000u), __ldg(xu + 5), a1);
+      a2 = fmaf(__uint_as_float(u.w << 16), __ldg(xu + 6), a2);
+      a3 = fmaf(__uint_as_float(u.w & 0xffff0000u), __ldg(xu + 7), a3);
     }
-    for (; n < M; n += 32)
+    for (int64_t n = head + 8 * nv + lane; n < M; n += 32)
       a0 = fmaf(bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(row + n))), __ldg(x32 + n), a0);
     double t = ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
