@@ -4,9 +4,9 @@
 // Eq. (rho).
 //
 // Canonical lists hold each unordered triple once as m <= n <= s, sorted by
-// (m, n, s).  Thread m walks its partners n in increasing index order and
-// for each the third indices s >= n in increasing order, so a count pass,
-// an exclusive scan over m and a fill pass give the sorted list without any
+// (m, n, s).  Row m's partners n come in increasing index order and for each
+// the third indices s >= n in increasing order, so a count pass, an
+// exclusive scan over m and a fill pass give the sorted list without any
 // sort.  The nonzero triples fall into three classes:
 //   * three pair elements whose edges form a triangle a-b-c: for given
 //     types of two of them the type of the third is fixed by parity (f: odd
@@ -59,101 +59,133 @@ __global__ void k_tables(int N, int32_t* pair_ab, double* tab) {
   }
 }
 
-// Visit the canonical triples (m, n, s) with m fixed, in (n, s) order.
-template <class Emit>
-__host__ __device__ void for_each_canonical(const BasisView& B, int64_t m, int which, Emit& emit) {
+// One warp per row m.  The candidates of a row are laid out as a sequence of
+// slots whose (n, s) order is the canonical order; the warp takes 32 slots at
+// a time, each lane evaluates one, and a ballot gives each nonzero its place,
+// so the output of a row is written in order by consecutive lanes.
+//
+// Pair row m = (k, a, b).  For each partner type tn >= k (tn < k gives n < m)
+// the partners are the 2N-3 edges that share a vertex with (a,b) or equal it,
+// in lexicographic order:
+//   e <  2a           : (e/2, a) for even e, (e/2, b) for odd e
+//   2a <= e < a+N-1   : (a, e-a+1)           -- holds (a,b) itself at e = a+b-1
+//   a+N-1 <= e < N+b-2: (e-N+2, b)
+//   N+b-2 <= e < 2N-3 : (b, e-N+3)
+// The slot of (a,b) itself is replaced by the run of D_l it pairs with:
+// f(S_ab, J_ab, D_l) for max(a,1) <= l <= b when tn != k, d(X_ab, X_ab, D_l)
+// for max(a,1) <= l < N when tn == k (the zero at (a,b,l) = (0,1,1) is
+// dropped by the value test).  With tn == k the row starts at (a,b).
+// A shared-vertex partner fixes the third edge and, by parity, its type; the
+// triple is canonical when s >= n.
+//
+// Diagonal row m = D_l (d only): d(D_l, D_l, D_r) for r >= l; the zero at
+// l = r = 1 is dropped by the value test.
+struct PairPlan {
+  int pab;    // slot of the edge (a,b): a + b - 1
+  int first;  // first slot of the row
+  int lo, nl; // D run l = lo .. lo + nl - 1
+  int total;  // slots: 2N-4 edges + nl
+};
+
+__device__ __forceinline__ PairPlan pair_plan(int N, const Elem& em, int tn, int which) {
+  PairPlan p;
+  p.pab = em.a + em.b - 1;
+  p.first = tn == em.kind ? p.pab : 0;
+  p.lo = imax(em.a, 1);
+  if (which == LB_F) p.nl = tn != em.kind ? em.b - p.lo + 1 : 0;
+  else p.nl = tn == em.kind ? N - p.lo : 0;
+  p.total = 2 * N - 4 + p.nl;
+  return p;
+}
+
+__device__ __forceinline__ void edge_of_slot(int N, int a, int b, int e, int& u, int& v) {
+  if (e < 2 * a) {
+    u = e >> 1;
+    v = (e & 1) ? b : a;
+  } else if (e < a + N - 1) {
+    u = a;
+    v = e - a + 1;
+  } else if (e < N + b - 2) {
+    u = e - N + 2;
+    v = b;
+  } else {
+    u = b;
+    v = e - N + 3;
+  }
+}
+
+// Evaluate slot j of a pair row: (n, s, value); false when the slot holds no
+// canonical triple.
+__device__ __forceinline__ bool pair_slot(const BasisView& B, const Elem& em, int tn, int which,
+                                          const PairPlan& p, int j, int64_t& n, int64_t& s, double& val) {
+  const int N = B.N;
+  double f, d;
+  if (j >= p.pab && j < p.pab + p.nl) {
+    const int l = p.lo + (j - p.pab);
+    n = (int64_t)tn * B.P + pair_index(N, em.a, em.b);
+    s = d_index(B, l);
+    fd_value(B, em, make_pair(tn, em.a, em.b), make_d(l), f, d);
+  } else {
+    int u, v;
+    edge_of_slot(N, em.a, em.b, j < p.pab ? j : j - p.nl + 1, u, v);
+    n = (int64_t)tn * B.P + pair_index(N, u, v);
+    const Elem en = make_pair(tn, u, v);
+    int lo, hi;
+    third_edge(em, en, common_vertex(em, en), lo, hi);
+    const int t3 = which == LB_F ? (1 ^ em.kind ^ tn) : (em.kind ^ tn);
+    s = (int64_t)t3 * B.P + pair_index(N, lo, hi);
+    if (s < n) return false;
+    fd_value(B, em, en, make_pair(t3, lo, hi), f, d);
+  }
+  val = which == LB_F ? f : d;
+  return val != 0.0;
+}
+
+// FILL = false: per_m[m] = number of nonzero canonical triples of row m.
+// FILL = true : write row m's triples from offset off[m].
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_rows(BasisView B, int which, int64_t* per_m, const int64_t* off,
+                                              int32_t* idx, double* val) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (m >= B.M) return;  // whole warps leave together
   const Elem em = decode(B, m);
   const int N = B.N;
+  int64_t pos = FILL ? off[m] : 0;
+  auto take = [&](bool nz, int64_t n, int64_t s, double v) {
+    const unsigned bal = __ballot_sync(0xffffffffu, nz);
+    if (FILL && nz) {
+      const int64_t o = pos + __popc(bal & below);
+      idx[3 * o] = (int32_t)m;
+      idx[3 * o + 1] = (int32_t)n;
+      idx[3 * o + 2] = (int32_t)s;
+      val[o] = v;
+    }
+    pos += __popc(bal);
+  };
   if (em.kind == kD) {
-    if (which != LB_D) return;
-    const int l = em.a;
-    for (int r = l; r < N; ++r) {
-      if (l == 1 && r == 1) continue;
-      emit(m, m, d_index(B, r), 2.0 * trace_ddd(B, l, l, r));
-    }
-    return;
-  }
-  const int a = em.a, b = em.b;
-  for (int tn = kS; tn <= kJ; ++tn) {
-    auto visit = [&](int u, int v) {
-      const int64_t n = (int64_t)tn * B.P + pair_index(N, u, v);
-      if (n < m) return;
-      const Elem en = make_pair(tn, u, v);
-      if (u == a && v == b) {  // same edge: the third element is a D_l
-        if (which == LB_F && tn != em.kind) {
-          for (int l = imax(a, 1); l <= b; ++l) {
-            double f, d;
-            fd_value(B, em, en, make_d(l), f, d);
-            emit(m, n, d_index(B, l), f);
-          }
-        } else if (which == LB_D && tn == em.kind) {
-          for (int l = imax(a, 1); l < N; ++l) {
-            if (a == 0 && b == 1 && l == 1) continue;
-            double f, d;
-            fd_value(B, em, en, make_d(l), f, d);
-            emit(m, n, d_index(B, l), d);
-          }
-        }
-        return;
+    if (which == LB_D) {
+      const int l = em.a;
+      for (int r0 = l; r0 < N; r0 += 32) {
+        const int r = r0 + lane;
+        const double v = r < N ? 2.0 * trace_ddd(B, l, l, r) : 0.0;
+        take(v != 0.0, m, d_index(B, r < N ? r : l), v);
       }
-      const int cv = common_vertex(em, en);
-      int lo, hi;
-      third_edge(em, en, cv, lo, hi);
-      const int t3 = which == LB_F ? (1 ^ em.kind ^ tn) : (em.kind ^ tn);
-      const int64_t s = (int64_t)t3 * B.P + pair_index(N, lo, hi);
-      if (s < n) return;
-      double f, d;
-      fd_value(B, em, en, make_pair(t3, lo, hi), f, d);
-      emit(m, n, s, which == LB_F ? f : d);
-    };
-    // edges sharing a vertex with (a,b), and (a,b) itself, in lexicographic order
-    for (int x = 0; x < N - 1 && x <= b; ++x) {
-      if (x < a) {
-        visit(x, a);
-        visit(x, b);
-      } else if (x == a) {
-        for (int y = a + 1; y < N; ++y) visit(a, y);
-      } else if (x < b) {
-        visit(x, b);
-      } else {  // x == b
-        for (int y = b + 1; y < N; ++y) visit(b, y);
+    }
+  } else {
+    for (int tn = em.kind; tn <= kJ; ++tn) {
+      const PairPlan p = pair_plan(N, em, tn, which);
+      for (int j0 = p.first; j0 < p.total; j0 += 32) {
+        const int j = j0 + lane;
+        int64_t n = 0, s = 0;
+        double v = 0.0;
+        const bool nz = j < p.total && pair_slot(B, em, tn, which, p, j, n, s, v);
+        take(nz, n, s, v);
       }
     }
   }
-}
-
-struct CountEmit {
-  int64_t n = 0;
-  __host__ __device__ void operator()(int64_t, int64_t, int64_t, double v) { n += (v != 0.0); }
-};
-
-struct FillEmit {
-  int32_t* idx;
-  double* val;
-  int64_t off;
-  __host__ __device__ void operator()(int64_t m, int64_t n, int64_t s, double v) {
-    if (v == 0.0) return;
-    idx[3 * off] = (int32_t)m;
-    idx[3 * off + 1] = (int32_t)n;
-    idx[3 * off + 2] = (int32_t)s;
-    val[off] = v;
-    ++off;
-  }
-};
-
-__global__ void k_count(BasisView B, int which, int64_t* per_m) {
-  int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (m >= B.M) return;
-  CountEmit e;
-  for_each_canonical(B, m, which, e);
-  per_m[m] = e.n;
-}
-
-__global__ void k_fill(BasisView B, int which, const int64_t* off, int32_t* idx, double* val) {
-  int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (m >= B.M) return;
-  FillEmit e{idx, val, off[m]};
-  for_each_canonical(B, m, which, e);
+  if (!FILL && lane == 0) per_m[m] = pos;
 }
 
 // Eq. (02): coef_j = Tr(F_j A) = sum_pq (F_j)_pq A_qp.
@@ -223,14 +255,14 @@ cudaError_t build_tables(int N, int32_t* pair_ab, double* tab, cudaStream_t st) 
 }
 
 cudaError_t structure_count(const lb::BasisView& B, int which, int64_t* per_m, cudaStream_t st) {
-  k_count<<<nblocks(B.M, 128), 128, 0, st>>>(B, which, per_m);
+  k_rows<false><<<nblocks(B.M * 32, 256), 256, 0, st>>>(B, which, per_m, nullptr, nullptr, nullptr);
   note_launch(1);
   return cudaGetLastError();
 }
 
 cudaError_t structure_fill(const lb::BasisView& B, int which, const int64_t* offsets,
                            int32_t* idx3, double* val, cudaStream_t st) {
-  k_fill<<<nblocks(B.M, 128), 128, 0, st>>>(B, which, offsets, idx3, val);
+  k_rows<true><<<nblocks(B.M * 32, 256), 256, 0, st>>>(B, which, nullptr, offsets, idx3, val);
   note_launch(1);
   return cudaGetLastError();
 }
