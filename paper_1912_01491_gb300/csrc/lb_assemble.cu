@@ -880,11 +880,105 @@ __device__ __forceinline__ void quad_fp64_matching(const double2 (&L)[3][2][2], 
   quad_store<MM, 1>(I, P, M, o, Aout, Qout, Rout);
 }
 
-// One block per edge (p, q); threads run over the edges (r, t) with
-// q < r < t, i.e. the contiguous pair indices from (q+1, q+2) to P - 1.  All
-// 12 a values of the quadruple are loaded at once; they are aligned to one
-// exponent E (the quadruple's largest), and an output matching whose own
-// values lie more than 10 binades below E is formed in FP64 instead.
+// The 12 a values of quadruple (p, q, r, t), where u = (r, t): matching 0
+// from rows (p,q), matching 1 from rows (p,r), matching 2 from rows (q,r)
+// (one orientation each).
+struct QuadLoad {
+  double2 L[3][2][2];
+};
+
+__device__ __forceinline__ void quad_index(int64_t pq, int64_t u, int r, int t, int64_t base_p, int64_t base_q,
+                                           QuadIdx& I) {
+  I.e[0] = pq;
+  I.e[1] = u;
+  I.e[2] = base_p + r;
+  I.e[3] = base_q + t;
+  I.e[4] = base_p + t;
+  I.e[5] = base_q + r;
+}
+
+__device__ __forceinline__ void quad_load(const AView& A, int64_t P, int64_t M, const QuadIdx& I, QuadLoad& q) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      q.L[0][i][j] = __ldg(A.a + (i * P + I.e[0]) * M + j * P + I.e[1]);
+      q.L[1][i][j] = __ldg(A.a + (i * P + I.e[2]) * M + j * P + I.e[3]);
+      q.L[2][i][j] = __ldg(A.a + (i * P + I.e[5]) * M + j * P + I.e[4]);
+    }
+}
+
+// All 12 values are aligned to one exponent E (the quadruple's largest); an
+// output matching whose own values lie more than 10 binades below E is
+// formed in FP64 instead.
+__device__ __forceinline__ void quad_emit(const double2 (&L)[3][2][2], int64_t P, int64_t M, const QuadIdx& I,
+                                          double* __restrict__ Aout, double* __restrict__ Qout,
+                                          double* __restrict__ Rout) {
+  int Ey[3];
+#pragma unroll
+  for (int y = 0; y < 3; ++y) {
+    Ey[y] = 1;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        Ey[y] = max(Ey[y], max(fx_exponent(L[y][i][j].x), fx_exponent(L[y][i][j].y)));
+  }
+  const int E = max(Ey[0], max(Ey[1], Ey[2]));
+  const bool ok = E >= 64 && E <= 2040;
+  const bool ex0 = ok && E - max(Ey[1], Ey[2]) <= 10;  // matching 0 reads matchings 1 and 2
+  const bool ex1 = ok && E - max(Ey[0], Ey[2]) <= 10;
+  const bool ex2 = ok && E - max(Ey[0], Ey[1]) <= 10;
+  if (ex0 && ex1 && ex2) {
+    long long D[3][2][2][2];
+#pragma unroll
+    for (int y = 0; y < 3; ++y)
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          D[y][i][j][0] = fx_align(fx_split(L[y][i][j].x), E, 0u);
+          D[y][i][j][1] = fx_align(fx_split(L[y][i][j].y), E, 0u);
+        }
+    quad_group<0, 0>(D, E, P, M, I, Aout, Qout, Rout);
+    quad_group<0, 1>(D, E, P, M, I, Aout, Qout, Rout);
+    quad_group<1, 0>(D, E, P, M, I, Aout, Qout, Rout);
+    quad_group<1, 1>(D, E, P, M, I, Aout, Qout, Rout);
+    quad_group<2, 0>(D, E, P, M, I, Aout, Qout, Rout);
+    quad_group<2, 1>(D, E, P, M, I, Aout, Qout, Rout);
+  } else {  // rare: values not finite, tiny, or of widely different magnitude
+    quad_fp64_matching<0>(L, P, M, I, Aout, Qout, Rout);
+    quad_fp64_matching<1>(L, P, M, I, Aout, Qout, Rout);
+    quad_fp64_matching<2>(L, P, M, I, Aout, Qout, Rout);
+  }
+}
+
+// One block per edge (p, q); its warps run over tiles of the edges (r, t)
+// with q < r < t: a tile is 4 consecutive r (r-group g: r0 = q + 1 + 4g) by 8
+// consecutive t, lane = 8 (r - r0) + (t - t0).  In a tile the stores whose
+// column is (p, r) or (q, r) cover 4 adjacent columns and those whose column
+// is (p, t), (q, t) or (r, t) 8, so most output sectors are written whole by
+// one warp instruction; only the column (p, q) is written 8 bytes per row.
+// A warp issues the loads of its next tile before it forms and stores the
+// current one, so the loads stay in flight across the arithmetic.
+struct QuadTile {
+  int64_t k;    // tile index within the block
+  int64_t cum;  // tiles of the r-groups before r0
+  int r0, cg;   // r-group start and its number of t-octets
+};
+
+// Move to tile k (>= the current one); false past the last r-group.
+__device__ __forceinline__ bool quad_tile_seek(int N, QuadTile& T, int64_t k) {
+  T.k = k;
+  while (k >= T.cum + T.cg) {
+    T.cum += T.cg;
+    T.r0 += 4;
+    if (T.r0 > N - 2) return false;
+    T.cg = (N - 1 - T.r0 + 7) >> 3;
+  }
+  return true;
+}
+
 constexpr int kQuadThreads = 256;
 __global__ void __launch_bounds__(kQuadThreads, 1) k_disjoint4(BasisView B, AView A, double* __restrict__ Aout,
                                                                double* __restrict__ Qout, double* __restrict__ Rout) {
@@ -894,65 +988,49 @@ __global__ void __launch_bounds__(kQuadThreads, 1) k_disjoint4(BasisView B, AVie
   const int32_t abq = __ldg(B.pair_ab + pq);
   const int p = abq >> 16, q = abq & 0xffff;
   if (q + 2 >= N) return;
-  const int64_t u0 = pair_index(N, q + 1, q + 2);
   const int64_t base_p = (int64_t)p * (2 * N - p - 1) / 2 - p - 1;  // pair_index(p, y) = base_p + y
   const int64_t base_q = (int64_t)q * (2 * N - q - 1) / 2 - q - 1;
-  for (int64_t u = u0 + threadIdx.x; u < P; u += blockDim.x) {
-    const int32_t art = __ldg(B.pair_ab + u);
-    const int r = art >> 16, t = art & 0xffff;
-    QuadIdx I;
-    I.e[0] = pq;
-    I.e[1] = u;
-    I.e[2] = base_p + r;
-    I.e[3] = base_q + t;
-    I.e[4] = base_p + t;
-    I.e[5] = base_q + r;
-    double2 L[3][2][2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        L[0][i][j] = __ldg(A.a + (i * P + I.e[0]) * M + j * P + I.e[1]);
-        L[1][i][j] = __ldg(A.a + (i * P + I.e[2]) * M + j * P + I.e[3]);
-        L[2][i][j] = __ldg(A.a + (i * P + I.e[5]) * M + j * P + I.e[4]);
-      }
-    int Ey[3];
-#pragma unroll
-    for (int y = 0; y < 3; ++y) {
-      Ey[y] = 1;
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-          Ey[y] = max(Ey[y], max(fx_exponent(L[y][i][j].x), fx_exponent(L[y][i][j].y)));
+  const int lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  QuadTile T;
+  T.cum = 0;
+  T.r0 = q + 1;
+  T.cg = (N - 1 - T.r0 + 7) >> 3;
+  if (!quad_tile_seek(N, T, threadIdx.x >> 5)) return;
+  auto coords = [&](const QuadTile& X, int& r, int& t) {
+    r = X.r0 + (lane >> 3);
+    t = X.r0 + 1 + 8 * (int)(X.k - X.cum) + (lane & 7);
+    return r <= N - 2 && t <= N - 1 && t > r;
+  };
+  auto index = [&](int r, int t, QuadIdx& I) {
+    const int64_t base_r = (int64_t)r * (2 * N - r - 1) / 2 - r - 1;
+    quad_index(pq, base_r + t, r, t, base_p, base_q, I);
+  };
+  int r, t;
+  bool ok = coords(T, r, t);
+  QuadIdx I;
+  QuadLoad cur;
+  if (ok) {
+    index(r, t, I);
+    quad_load(A, P, M, I, cur);
+  }
+  while (true) {
+    QuadTile Tn = T;
+    const bool more = quad_tile_seek(N, Tn, T.k + nw);
+    int rn = 0, tn = 0;
+    const bool okn = more && coords(Tn, rn, tn);
+    QuadIdx In;
+    QuadLoad nxt;
+    if (okn) {
+      index(rn, tn, In);
+      quad_load(A, P, M, In, nxt);
     }
-    const int E = max(Ey[0], max(Ey[1], Ey[2]));
-    const bool ok = E >= 64 && E <= 2040;
-    const bool ex0 = ok && E - max(Ey[1], Ey[2]) <= 10;  // matching 0 reads matchings 1 and 2
-    const bool ex1 = ok && E - max(Ey[0], Ey[2]) <= 10;
-    const bool ex2 = ok && E - max(Ey[0], Ey[1]) <= 10;
-    if (ex0 && ex1 && ex2) {
-      long long D[3][2][2][2];
-#pragma unroll
-      for (int y = 0; y < 3; ++y)
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            D[y][i][j][0] = fx_align(fx_split(L[y][i][j].x), E, 0u);
-            D[y][i][j][1] = fx_align(fx_split(L[y][i][j].y), E, 0u);
-          }
-      quad_group<0, 0>(D, E, P, M, I, Aout, Qout, Rout);
-      quad_group<0, 1>(D, E, P, M, I, Aout, Qout, Rout);
-      quad_group<1, 0>(D, E, P, M, I, Aout, Qout, Rout);
-      quad_group<1, 1>(D, E, P, M, I, Aout, Qout, Rout);
-      quad_group<2, 0>(D, E, P, M, I, Aout, Qout, Rout);
-      quad_group<2, 1>(D, E, P, M, I, Aout, Qout, Rout);
-    } else {  // rare: values not finite, tiny, or of widely different magnitude
-      quad_fp64_matching<0>(L, P, M, I, Aout, Qout, Rout);
-      quad_fp64_matching<1>(L, P, M, I, Aout, Qout, Rout);
-      quad_fp64_matching<2>(L, P, M, I, Aout, Qout, Rout);
-    }
+    if (ok) quad_emit(cur.L, P, M, I, Aout, Qout, Rout);
+    if (!more) break;
+    T = Tn;
+    ok = okn;
+    I = In;
+    cur = nxt;
   }
 }
 

@@ -270,3 +270,43 @@ def test_system_save_load_and_resume(tmp_path):
             lb.System.load(B, path)
         back.close()
         sysm.close()
+
+
+def test_dense_assembly_n200_sampled_entries():
+    """Dense random Lindbladian N = 200 (M = 39,999) in the launch the benchmark
+    times: closed algorithm, A = Q + R written in place, K beside it.  Two full
+    rows of A and 3000 random entries in each of four more rows (S, J and D
+    rows) against the oracle's entry-by-entry Eq. (07) + Eq. (09); K is
+    checked in full at N <= 50."""
+    N = 200
+    M, P = N * N - 1, N * (N - 1) // 2
+    lb = lbm()
+    a = wl.wishart_kossakowski_device(N, 20200)
+    H = wl.gue_hamiltonian(N, 20201)
+    with lb.Basis(N) as B:
+        h = B.expand(torch.tensor(H, device="cuda")).real.contiguous()
+        A = torch.empty((M, M), dtype=torch.float64, device="cuda")
+        K = torch.empty(M, dtype=torch.float64, device="cuda")
+        B.assemble_dense_timed(a, h=h, A=A, K=K, algorithm="closed")
+        torch.cuda.synchronize()
+    g = np.random.default_rng(200)
+    full = [P // 3, 2 * P + N // 2]
+    part = [0, P + P // 2, 2 * P - 1, M - 1]
+    s = np.concatenate([np.repeat(full, M), np.repeat(part, 3000)]).astype(np.int64)
+    n = np.concatenate([np.tile(np.arange(M), len(full)), g.integers(0, M, 3000 * len(part))]).astype(np.int64)
+    got = A[torch.as_tensor(s, device="cuda"), torch.as_tensor(n, device="cuda")].cpu().numpy()
+    assert np.isfinite(K.cpu().numpy()).all()
+    del A
+    with Oracle(N) as o:
+        need = o.rows_needed(np.unique(s))
+        rows = a[torch.as_tensor(need, device="cuda")].cpu().numpy()
+        del a
+        R, S = o.R_entries_rows(need, rows, s, n)
+        hh, _ = o.expand(H)
+        Q = o.Q_entries(hh.real, s, n)
+    ref = Q + R
+    err = np.abs(got - ref)
+    tol = 1e-12 * np.maximum(np.abs(ref), S + np.abs(Q)) + 1e-300
+    bad = np.flatnonzero(err > tol)
+    assert len(bad) == 0, "%d of %d sampled entries out of tolerance, first (s, n) = (%d, %d)" % (
+        len(bad), len(s), s[bad[0]], n[bad[0]])
