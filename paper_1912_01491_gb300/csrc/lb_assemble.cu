@@ -954,27 +954,43 @@ __device__ __forceinline__ void quad_emit(const double2 (&L)[3][2][2], int64_t P
 }
 
 // One block per edge (p, q); its warps run over tiles of the edges (r, t)
-// with q < r < t: a tile is 4 consecutive r (r-group g: r0 = q + 1 + 4g) by 8
-// consecutive t, lane = 8 (r - r0) + (t - t0).  In a tile the stores whose
-// column is (p, r) or (q, r) cover 4 adjacent columns and those whose column
-// is (p, t), (q, t) or (r, t) 8, so most output sectors are written whole by
-// one warp instruction; only the column (p, q) is written 8 bytes per row.
-// A warp issues the loads of its next tile before it forms and stores the
-// current one, so the loads stay in flight across the arithmetic.
+// with q < r < t.  A tile is kTileR consecutive r by kTileT consecutive t,
+// lane = kTileT (r - rbase) + (t - t0).  The r-groups are laid on one grid
+// from the top, rbase = N - 1 - kTileR (g + 1) for g = 0, 1, ..., the same
+// for every q (lanes with r <= q are idle), so the blocks of (p, q) and
+// (p, q + 1), which start close together, visit the rows (r, t) in the same
+// order and at about the same time.  In a tile the stores whose column is
+// (p, r) or (q, r) cover kTileR adjacent columns and those whose column is
+// (p, t), (q, t) or (r, t) kTileT, so these output sectors are written
+// nearly whole by one warp instruction; the stores into column (p, q) are
+// 8 bytes per row, and their sector neighbours come from the blocks of the
+// neighbouring q at about the same time.  A warp issues the loads of its
+// next tile before it forms and stores the current one, so the loads stay in
+// flight across the arithmetic.
+constexpr int kTileR = 8, kTileT = 4;
+static_assert(kTileR * kTileT == 32, "a tile is one warp");
+
 struct QuadTile {
   int64_t k;    // tile index within the block
-  int64_t cum;  // tiles of the r-groups before r0
-  int r0, cg;   // r-group start and its number of t-octets
+  int64_t cum;  // tiles of the r-groups before this one
+  int rbase;    // r = rbase + lane / kTileT
+  int t0, cg;   // first t of the group and its number of t-tiles
 };
 
+// Start the r-group whose lowest r is rbase, for the block of q.
+__device__ __forceinline__ void quad_group_start(int N, int q, int rbase, QuadTile& T) {
+  T.rbase = rbase;
+  T.t0 = max(rbase, q + 1) + 1;
+  T.cg = (N - T.t0 + kTileT - 1) / kTileT;
+}
+
 // Move to tile k (>= the current one); false past the last r-group.
-__device__ __forceinline__ bool quad_tile_seek(int N, QuadTile& T, int64_t k) {
+__device__ __forceinline__ bool quad_tile_seek(int N, int q, QuadTile& T, int64_t k) {
   T.k = k;
   while (k >= T.cum + T.cg) {
+    if (T.rbase <= q + 1) return false;  // that group held r = q + 1
     T.cum += T.cg;
-    T.r0 += 4;
-    if (T.r0 > N - 2) return false;
-    T.cg = (N - 1 - T.r0 + 7) >> 3;
+    quad_group_start(N, q, T.rbase - kTileR, T);
   }
   return true;
 }
@@ -994,13 +1010,12 @@ __global__ void __launch_bounds__(kQuadThreads, 1) k_disjoint4(BasisView B, AVie
   const int nw = blockDim.x >> 5;
   QuadTile T;
   T.cum = 0;
-  T.r0 = q + 1;
-  T.cg = (N - 1 - T.r0 + 7) >> 3;
-  if (!quad_tile_seek(N, T, threadIdx.x >> 5)) return;
+  quad_group_start(N, q, N - 1 - kTileR, T);
+  if (!quad_tile_seek(N, q, T, threadIdx.x >> 5)) return;
   auto coords = [&](const QuadTile& X, int& r, int& t) {
-    r = X.r0 + (lane >> 3);
-    t = X.r0 + 1 + 8 * (int)(X.k - X.cum) + (lane & 7);
-    return r <= N - 2 && t <= N - 1 && t > r;
+    r = X.rbase + lane / kTileT;
+    t = X.t0 + kTileT * (int)(X.k - X.cum) + lane % kTileT;
+    return r > q && r <= N - 2 && t <= N - 1 && t > r;
   };
   auto index = [&](int r, int t, QuadIdx& I) {
     const int64_t base_r = (int64_t)r * (2 * N - r - 1) / 2 - r - 1;
@@ -1016,7 +1031,7 @@ __global__ void __launch_bounds__(kQuadThreads, 1) k_disjoint4(BasisView B, AVie
   }
   while (true) {
     QuadTile Tn = T;
-    const bool more = quad_tile_seek(N, Tn, T.k + nw);
+    const bool more = quad_tile_seek(N, q, Tn, T.k + nw);
     int rn = 0, tn = 0;
     const bool okn = more && coords(Tn, rn, tn);
     QuadIdx In;
