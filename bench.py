@@ -40,7 +40,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=200, help="Hilbert-space dimension N")
-    p.add_argument("--rk4-steps", type=int, default=10, help="RK4 steps per bench step and precision")
+    p.add_argument("--rk4-steps", type=int, default=10, help="FP64 RK4 steps per bench step")
+    p.add_argument("--rk4-fp32-steps", type=int, default=50,
+                   help="FP32-storage RK4 steps per bench step (one FP64 correction window of 50 steps)")
     p.add_argument("--dt", type=float, default=1e-3)
     p.add_argument("--seed", type=int, default=20250)
     p.add_argument("--no-e2e", action="store_true")
@@ -151,7 +153,7 @@ def run_gb300(args):
         dist.init_process_group("nccl")
     N = args.n
     M = N * N - 1
-    dt, nrk = args.dt, args.rk4_steps
+    dt, nrk, nrk32 = args.dt, args.rk4_steps, args.rk4_fp32_steps
     dev = torch.device("cuda", local)
 
     # ---- inputs, resident in HBM before timing (one realization per rank)
@@ -204,7 +206,7 @@ def run_gb300(args):
         ev[3].record(stream)
         # a8: RK4 on FP32 storage with FP64 defect correction every 50 steps
         v32.copy_(v0)
-        lb.rk4_dense(A32, K, v32, dt, nrk, precision="fp32", A64=A, correct_every=50, work=work)
+        lb.rk4_dense(A32, K, v32, dt, nrk32, precision="fp32", A64=A, correct_every=50, work=work)
         ev[4].record(stream)
 
     hh = [None]
@@ -276,6 +278,7 @@ def run_gb300(args):
             dist.destroy_process_group()
         return None
     peaks = measured_peaks()
+    fp32_bytes = (4.0 * 4.0 * M * M * nrk32 + 12.0 * M * M * -(-nrk32 // 50)) * K_
     out = {
         "metric": "R entries assembled/s (dense random Lindbladian, N=%d)" % N,
         "value": value,
@@ -292,13 +295,13 @@ def run_gb300(args):
         "config": {
             "workload": ("dense random Lindbladian N=%d (M=%d): GUE H, Wishart a=GG^dag/Tr; per step kernel (a) "
                          "f/d enumeration, expansion, Q/R/K assembly, FP32 pack, %d RK4 steps FP64 + %d RK4 "
-                         "steps FP32 storage with FP64 correction (k=50), dt=%g" % (N, M, nrk, nrk, dt)),
+                         "steps FP32 storage with FP64 correction (k=50), dt=%g" % (N, M, nrk, nrk32, dt)),
             "N": N, "M": M, "join_terms": W,
             "l2": "inputs larger than L2 (a is %.1f GB)" % (16.0 * M * M / 1e9),
             "parallelism": "replicas" if world > 1 else "single",
         },
         "rk4_steps_per_s": world * K_ * nrk / (rk_ms * 1e-3),
-        "rk4_fp32_corrected_steps_per_s": world * K_ * nrk / (rk32_ms * 1e-3),
+        "rk4_fp32_corrected_steps_per_s": world * K_ * nrk32 / (rk32_ms * 1e-3),
         "assembly_algorithm": args.algorithm,
         "assembly_ms": asm_ms / K_,
         "assembly_kernel_ms": kern,
@@ -318,13 +321,11 @@ def run_gb300(args):
             "kernel": "k_stage<FP32> (fused GEMV + stage update, 16-byte loads) + k_correction<FP32>",
             "bound": "hbm",
             # per RK4 step 4 reads of A32; one FP64 correction (A64 + A32) per 50 steps, and the
-            # run of nrk steps starts with one
-            "achieved": (4.0 * 4.0 * M * M * nrk + 12.0 * M * M * max(1, nrk // 50)) * K_
-                        / (rk32_ms * 1e-3) / 1e9,
+            # run of nrk32 steps starts with one
+            "achieved": fp32_bytes / (rk32_ms * 1e-3) / 1e9,
             "peak": peaks.get("hbm_gbs"),
             "unit": "GB/s",
-            "frac": ((4.0 * 4.0 * M * M * nrk + 12.0 * M * M * max(1, nrk // 50)) * K_ / (rk32_ms * 1e-3) / 1e9
-                     / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
+            "frac": (fp32_bytes / (rk32_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
         },
         "gpu_launches": launches,
         "clocks": clk,
@@ -666,8 +667,9 @@ def form_batched(args, dev):
 
 def form_serving(args, dev, a200=None):
     """Poisson stream of realizations with N in {20, 50, 100, 150, 200}
-    through the server: FP32 storage for N <= 64 (cluster engine), BF16 above
-    (stream engine), FP64 correction every 50 steps, `serve_steps` RK4 steps.
+    through the server: FP32 storage for N <= 64 (cluster engine) with the
+    FP64 correction every 50 steps, BF16 above (stream engine) with the
+    correction every 10 steps, `serve_steps` RK4 steps.
     Inputs are synthesised before submission (one realization per N, reused
     by every request of that N; each request is assembled and integrated on
     its own) and excluded from latency.  The arrival rate is `serve_load`
@@ -678,8 +680,11 @@ def form_serving(args, dev, a200=None):
     import paper_1912_01491_gb300 as lb
     import workloads as wl
     Nset = (20, 50, 100, 150, 200)
-    steps, dt, corr = args.serve_steps, args.dt, 50
+    steps, dt = args.serve_steps, args.dt
     prec = {N: ("fp32" if N <= 64 else "bf16") for N in Nset}
+    # BF16 entries carry 2^-9 relative error: a shorter correction period
+    corr_of = {"fp32": 50, "bf16": 10}
+    corr = {N: corr_of[prec[N]] for N in Nset}
     pool, bases = {}, {}
     for N in Nset:
         H = torch.tensor(wl.gue_hamiltonian(N, args.seed + 500 + N), device=dev)
@@ -705,7 +710,7 @@ def form_serving(args, dev, a200=None):
         v0 = v0_for(N, 0)
         out = torch.empty_like(v0)
         torch.cuda.synchronize()
-        rid = srv.submit(a, v0, out, dt, steps, H=H, precision=prec[N], correct_every=corr)
+        rid = srv.submit(a, v0, out, dt, steps, H=H, precision=prec[N], correct_every=corr[N])
         alone[N] = srv.wait(rid)["latency_ms"]
     svc = float(np.mean([alone[N] for N in Nset]))
     rate = args.serve_load * 1000.0 / svc  # requests / s
@@ -721,7 +726,7 @@ def form_serving(args, dev, a200=None):
         while time.perf_counter() - t0 < arr[i]:
             time.sleep(0.0005)
         H, a = pool[N]
-        ids.append(srv.submit(a, v0, out, dt, steps, H=H, precision=prec[N], correct_every=corr))
+        ids.append(srv.submit(a, v0, out, dt, steps, H=H, precision=prec[N], correct_every=corr[N]))
         outs.append((N, i + 1, out))
     res = [srv.wait(rid) for rid in ids]
     wall = time.perf_counter() - t0
@@ -749,7 +754,7 @@ def form_serving(args, dev, a200=None):
     srv.close()
     for B in bases.values():
         B.close()
-    return {"requests": len(arr), "steps": steps, "dt": dt, "correct_every": corr,
+    return {"requests": len(arr), "steps": steps, "dt": dt, "correct_every": {str(N): corr[N] for N in Nset},
             "precision": {str(N): prec[N] for N in Nset}, "arrival_rate_per_s": rate, "load": args.serve_load,
             "p50_latency_ms": st["p50_ms"], "p99_latency_ms": st["p99_ms"],
             "throughput_realizations_per_s": st["throughput_per_s"], "wall_s": wall,

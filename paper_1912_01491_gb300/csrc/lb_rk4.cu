@@ -33,7 +33,7 @@ template <int PREC>
 __device__ __forceinline__ double row_dot(int64_t M, int64_t s, const void* __restrict__ Ap,
                                           const float* __restrict__ scale,
                                           const double* __restrict__ x,
-                                          const float* __restrict__ x32, int lane) {
+                                          const float* __restrict__ x32, int64_t xstride, int lane) {
   if (PREC == LB_FP64) {
     const double* __restrict__ row = static_cast<const double*>(Ap) + s * M;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -49,69 +49,87 @@ __device__ __forceinline__ double row_dot(int64_t M, int64_t s, const void* __re
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     return t;
   } else if (PREC == LB_FP32) {
-    // 16-byte loads of the row: a scalar head up to the first 16-byte
-    // boundary (rows start anywhere for odd M), float4 vectors, a scalar tail
+    // Lane k reads A as float4 at element head + 4k (a scalar head up to the
+    // first 16-byte boundary; rows start anywhere for odd M) and x as the
+    // matching float4 of the shifted copy o = head mod 4, so a warp reads
+    // 512 contiguous bytes of each per instruction.
     const float* __restrict__ row = static_cast<const float*>(Ap) + s * M;
     const int64_t h4 = (int64_t)(((16 - ((uintptr_t)row & 15)) & 15) >> 2);
     const int head = (int)(h4 < M ? h4 : M);
+    const int o = head & 3;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
     if (lane < head) a0 = fmaf(__ldcs(row + lane), __ldg(x32 + lane), a0);
     const float4* __restrict__ rv = reinterpret_cast<const float4*>(row + head);
-    const float* __restrict__ xv = x32 + head;
+    const float4* __restrict__ xv = reinterpret_cast<const float4*>(x32 + o * xstride + head - o);
     const int64_t nv = (M - head) >> 2;
     int64_t k = lane;
     for (; k + 32 < nv; k += 64) {
       const float4 u = __ldcs(rv + k), w = __ldcs(rv + k + 32);
-      const float* xu = xv + 4 * k;
-      const float* xw = xv + 4 * (k + 32);
-      a0 = fmaf(u.x, __ldg(xu), a0);
-      a1 = fmaf(u.y, __ldg(xu + 1), a1);
-      a2 = fmaf(u.z, __ldg(xu + 2), a2);
-      a3 = fmaf(u.w, __ldg(xu + 3), a3);
-      a0 = fmaf(w.x, __ldg(xw), a0);
-      a1 = fmaf(w.y, __ldg(xw + 1), a1);
-      a2 = fmaf(w.z, __ldg(xw + 2), a2);
-      a3 = fmaf(w.w, __ldg(xw + 3), a3);
+      const float4 xu = __ldg(xv + k), xw = __ldg(xv + k + 32);
+      a0 = fmaf(u.x, xu.x, a0);
+      a1 = fmaf(u.y, xu.y, a1);
+      a2 = fmaf(u.z, xu.z, a2);
+      a3 = fmaf(u.w, xu.w, a3);
+      a0 = fmaf(w.x, xw.x, a0);
+      a1 = fmaf(w.y, xw.y, a1);
+      a2 = fmaf(w.z, xw.z, a2);
+      a3 = fmaf(w.w, xw.w, a3);
     }
     for (; k < nv; k += 32) {
-      const float4 u = __ldcs(rv + k);
-      const float* xu = xv + 4 * k;
-      a0 = fmaf(u.x, __ldg(xu), a0);
-      a1 = fmaf(u.y, __ldg(xu + 1), a1);
-      a2 = fmaf(u.z, __ldg(xu + 2), a2);
-      a3 = fmaf(u.w, __ldg(xu + 3), a3);
+      const float4 u = __ldcs(rv + k), xu = __ldg(xv + k);
+      a0 = fmaf(u.x, xu.x, a0);
+      a1 = fmaf(u.y, xu.y, a1);
+      a2 = fmaf(u.z, xu.z, a2);
+      a3 = fmaf(u.w, xu.w, a3);
     }
     for (int64_t n = head + 4 * nv + lane; n < M; n += 32) a0 = fmaf(__ldcs(row + n), __ldg(x32 + n), a0);
     double t = ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    for (int o2 = 16; o2 > 0; o2 >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o2);
     return t;
   } else {
-    // BF16: 16-byte loads of eight values, head and tail as for FP32
+    // BF16: lane k reads four values (8 bytes) of A at element head + 4k
+    // (head up to the first 8-byte boundary) and the matching float4 of the
+    // shifted copy o = head mod 4 of x: 256 contiguous bytes of A and 512 of
+    // x per warp instruction.
     const uint16_t* __restrict__ row = static_cast<const uint16_t*>(Ap) + s * M;
-    const int64_t h2 = (int64_t)(((16 - ((uintptr_t)row & 15)) & 15) >> 1);
+    const int64_t h2 = (int64_t)(((8 - ((uintptr_t)row & 7)) & 7) >> 1);
     const int head = (int)(h2 < M ? h2 : M);
+    const int o = head & 3;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
     if (lane < head)
       a0 = fmaf(bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(row + lane))), __ldg(x32 + lane), a0);
-    const uint4* __restrict__ rv = reinterpret_cast<const uint4*>(row + head);
-    const float* __restrict__ xv = x32 + head;
-    const int64_t nv = (M - head) >> 3;
-    for (int64_t k = lane; k < nv; k += 32) {
-      const uint4 u = __ldcs(rv + k);
-      const float* xu = xv + 8 * k;
-      a0 = fmaf(__uint_as_float(u.x << 16), __ldg(xu), a0);
-      a1 = fmaf(__uint_as_float(u.x & 0xffff0000u), __ldg(xu + 1), a1);
-      a2 = fmaf(__uint_as_float(u.y << 16), __ldg(xu + 2), a2);
-      a3 = fmaf(__uint_as_float(u.y & 0xffff0000u), __ldg(xu + 3), a3);
-      a0 = fmaf(__uint_as_float(u.z << 16), __ldg(xu + 4), a0);
-      a1 = fmaf(__uint_as_float(u.z & 0xffff0000u), __ldg(xu + 5), a1);
-      a2 = fmaf(__uint_as_float(u.w << 16), __ldg(xu + 6), a2);
-      a3 = fmaf(__uint_as_float(u.w & 0xffff0000u), __ldg(xu + 7), a3);
+    const uint2* __restrict__ rv = reinterpret_cast<const uint2*>(row + head);
+    const float4* __restrict__ xv = reinterpret_cast<const float4*>(x32 + o * xstride + head - o);
+    const int64_t nv = (M - head) >> 2;
+    int64_t k = lane;
+    for (; k + 96 < nv; k += 128) {
+      uint2 u[4];
+      float4 xu[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        u[i] = __ldcs(rv + k + 32 * i);
+        xu[i] = __ldg(xv + k + 32 * i);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a0 = fmaf(__uint_as_float(u[i].x << 16), xu[i].x, a0);
+        a1 = fmaf(__uint_as_float(u[i].x & 0xffff0000u), xu[i].y, a1);
+        a2 = fmaf(__uint_as_float(u[i].y << 16), xu[i].z, a2);
+        a3 = fmaf(__uint_as_float(u[i].y & 0xffff0000u), xu[i].w, a3);
+      }
     }
-    for (int64_t n = head + 8 * nv + lane; n < M; n += 32)
+    for (; k < nv; k += 32) {
+      const uint2 u = __ldcs(rv + k);
+      const float4 xu = __ldg(xv + k);
+      a0 = fmaf(__uint_as_float(u.x << 16), xu.x, a0);
+      a1 = fmaf(__uint_as_float(u.x & 0xffff0000u), xu.y, a1);
+      a2 = fmaf(__uint_as_float(u.y << 16), xu.z, a2);
+      a3 = fmaf(__uint_as_float(u.y & 0xffff0000u), xu.w, a3);
+    }
+    for (int64_t n = head + 4 * nv + lane; n < M; n += 32)
       a0 = fmaf(bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(row + n))), __ldg(x32 + n), a0);
     double t = ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    for (int o2 = 16; o2 > 0; o2 >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o2);
     return t * (double)__ldg(scale + s);
   }
 }
@@ -121,11 +139,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_stage(int64_t M, const void* __restrict__ Ap, const float* __restrict__ scale,
             const double* __restrict__ Keff, const double* __restrict__ x,
             const float* __restrict__ x32, double* __restrict__ xn, float* __restrict__ xn32,
-            double* __restrict__ acc, double* __restrict__ v, double h) {
+            int64_t xstride, double* __restrict__ acc, double* __restrict__ v, double h) {
   const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (s >= M) return;
-  const double y = row_dot<PREC>(M, s, Ap, scale, x, x32, lane);
+  const double y = row_dot<PREC>(M, s, Ap, scale, x, x32, xstride, lane);
   if (lane != 0) return;
   const double k = y + Keff[s];
   double nx;
@@ -143,7 +161,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     v[s] = nx;
   }
   xn[s] = nx;
-  if (PREC != LB_FP64) xn32[s] = (float)nx;
+  if (PREC != LB_FP64) {  // the four shifted copies: copy o holds x[j + o] at j
+    const float f = (float)nx;
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+      if (s >= o) xn32[o * xstride + (s - o)] = f;
+  }
 }
 
 // c = (A64 - A_lp) v in FP64;  Keff = K + c.
@@ -161,12 +184,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const float* __restrict__ r = static_cast<const float*>(Ap) + s * M;
     for (int64_t n = lane; n < M; n += 32) t = fma(__ldcs(r64 + n) - (double)__ldcs(r + n), v[n], t);
   } else {
+    // sum_n A64_sn v_n - r_s sum_n q_sn v_n: two FP64 dot products (the
+    // difference is formed once per row, not per entry)
     const uint16_t* __restrict__ r = static_cast<const uint16_t*>(Ap) + s * M;
-    const double sc = (double)scale[s];
+    double tq = 0.0;
     for (int64_t n = lane; n < M; n += 32) {
-      const double q = (double)bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(r + n))) * sc;
-      t = fma(__ldcs(r64 + n) - q, v[n], t);
+      const double vn = v[n];
+      t = fma(__ldcs(r64 + n), vn, t);
+      tq = fma((double)bf16_bits_to_float(__ldcs(reinterpret_cast<const unsigned short*>(r + n))), vn, tq);
     }
+    for (int o = 16; o > 0; o >>= 1) tq += __shfl_xor_sync(0xffffffffu, tq, o);
+    if (lane == 0) t -= (double)scale[s] * tq;  // once, before the lane sum below
   }
   for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
   if (lane == 0) Keff[s] = K[s] + t;
@@ -245,6 +273,16 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restr
   for (; i < n; i += stride) b[i] = (float)a[i];
 }
 
+// The four shifted FP32 copies of x: copy o holds x[j + o] at index j.
+__global__ void k_to_f32_shifted(int64_t M, const double* __restrict__ x, float* __restrict__ y, int64_t xstride) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const float f = (float)x[j];
+#pragma unroll
+  for (int o = 0; o < 4; ++o)
+    if (j >= o) y[o * xstride + (j - o)] = f;
+}
+
 // One warp per row: r_s = max |A_sn| (as float), then bf16(A_sn / r_s).
 __global__ void k_pack_bf16(int64_t M, const double* __restrict__ A, uint16_t* __restrict__ Ab,
                             float* __restrict__ scale) {
@@ -268,15 +306,23 @@ __global__ void k_pack_bf16(int64_t M, const double* __restrict__ A, uint16_t* _
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// RK4 workspace: FP64 stage vectors X, Y, the running combination and
+// K + correction, and the FP32 stage vectors X32, Y32, each as four copies
+// shifted by 0..3 elements (xstride floats apart, 256-byte aligned) so that
+// every row of a dense FP32/BF16 product reads x with aligned 16-byte loads.
 struct Work {
   double *X, *Y, *acc, *Keff;
   float *X32, *Y32;
+  int64_t xstride;
 };
+
+inline int64_t x32_stride(int64_t M) { return (M + 63) & ~int64_t(63); }
 
 Work carve(void* base, int64_t M) {
   char* p = static_cast<char*>(base);
   Work w;
-  size_t d = align256(sizeof(double) * (size_t)M), f = align256(sizeof(float) * (size_t)M);
+  w.xstride = x32_stride(M);
+  size_t d = align256(sizeof(double) * (size_t)M), f = sizeof(float) * 4 * (size_t)w.xstride;
   w.X = reinterpret_cast<double*>(p); p += d;
   w.Y = reinterpret_cast<double*>(p); p += d;
   w.acc = reinterpret_cast<double*>(p); p += d;
@@ -298,19 +344,20 @@ cudaError_t run_steps(int64_t M, const void* Ap, const float* scale, const doubl
   e = cudaMemcpyAsync(w.Keff, K, sizeof(double) * M, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
   if (PREC != LB_FP64) {
-    k_to_f32<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, v, w.X32);
+    k_to_f32_shifted<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, v, w.X32, w.xstride);
     lbi::note_launch(1);
   }
   const bool correct = PREC != LB_FP64 && correct_every > 0 && A64 != nullptr;
+  const int64_t xs = w.xstride;
   for (int64_t t = 0; t < nsteps; ++t) {
     if (correct && t % correct_every == 0) {
       k_correction<PREC><<<grid, bs, 0, st>>>(M, A64, Ap, scale, v, K, w.Keff);
       lbi::note_launch(1);
     }
-    k_stage<PREC, 1><<<grid, bs, 0, st>>>(M, Ap, scale, w.Keff, w.X, w.X32, w.Y, w.Y32, w.acc, v, dt);
-    k_stage<PREC, 2><<<grid, bs, 0, st>>>(M, Ap, scale, w.Keff, w.Y, w.Y32, w.X, w.X32, w.acc, v, dt);
-    k_stage<PREC, 3><<<grid, bs, 0, st>>>(M, Ap, scale, w.Keff, w.X, w.X32, w.Y, w.Y32, w.acc, v, dt);
-    k_stage<PREC, 4><<<grid, bs, 0, st>>>(M, Ap, scale, w.Keff, w.Y, w.Y32, w.X, w.X32, w.acc, v, dt);
+    k_stage<PREC, 1><<<grid, bs, 0, st>>>(M, Ap, scale, w.Keff, w.X, w.X32, w.Y, w.Y32, xs, w.acc, v, dt);
+    k_stage<PREC, 2><<<grid, bs, 0, st>>>(M, Ap, scale, w.Keff, w.Y, w.Y32, w.X, w.X32, xs, w.acc, v, dt);
+    k_stage<PREC, 3><<<grid, bs, 0, st>>>(M, Ap, scale, w.Keff, w.X, w.X32, w.Y, w.Y32, xs, w.acc, v, dt);
+    k_stage<PREC, 4><<<grid, bs, 0, st>>>(M, Ap, scale, w.Keff, w.Y, w.Y32, w.X, w.X32, xs, w.acc, v, dt);
     lbi::note_launch(4);
     if (snaps && snap_every > 0 && (t + 1) % snap_every == 0) {
       e = cudaMemcpyAsync(snaps + ((t + 1) / snap_every - 1) * M, v, sizeof(double) * M,
@@ -386,7 +433,7 @@ cudaError_t pack_bf16(int64_t M, const double* A, uint16_t* Ab, float* scale, cu
 }
 
 size_t rk4_workspace_bytes(int64_t M) {
-  return 4 * align256(sizeof(double) * (size_t)M) + 2 * align256(sizeof(float) * (size_t)M);
+  return 4 * align256(sizeof(double) * (size_t)M) + 2 * sizeof(float) * 4 * (size_t)x32_stride(M);
 }
 
 cudaError_t rk4_dense(int64_t M, int precision, const void* Ap, const float* scale,
