@@ -346,8 +346,8 @@ def run_gb300(args):
 # the bench size by units.  Kept only for the kernel version the capture saw.
 NCU_TRAFFIC = {
     "k_entries (pair x pair; closed: disjoint edges by vertex quadruple)": {
-        "N": 200, "bytes": 18.53e9 + 16.98e9, "units": lambda N: N * (N - 1.0) * (N - 2.0) * (N - 3.0),
-        "source": "profiles/dense_assembly_n100.md (full-size DRAM capture at N=200)"},
+        "N": 200, "bytes": 17.55e9 + 15.68e9, "units": lambda N: N * (N - 1.0) * (N - 2.0) * (N - 3.0),
+        "source": "profiles/k_disjoint4_dense_n200.md (full-size DRAM capture at N=200)"},
 }
 
 
@@ -418,8 +418,16 @@ def run_e2e(args, lb, B, a, H_host, M, nrk, dt, dev, dist, world):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
     sa, st = tt.tolist()
     del a_host
+    # lb_assemble brings the upper triangle of a (row blocks of h rows, columns
+    # from the block's first row on) for M > 2048, all of a otherwise
+    if M > 2048:
+        h = max(256, (M + 63) // 64)
+        a_bytes = sum(16 * (min(M, j0 + h) - j0) * (M - j0) for j0 in range(0, M, h))
+    else:
+        a_bytes = 16 * M * M
     return {"value": world * args.steps * M * M / sa, "unit": "entries/s",
-            "h2d_bytes_per_step": 16 * M * M + 16 * B.N * B.N + 8 * M, "d2h_bytes_per_step": 8 * M,
+            "assemble_s_per_step": [round(x, 4) for x in t_asm],
+            "h2d_bytes_per_step": a_bytes + 16 * B.N * B.N + 8 * M, "d2h_bytes_per_step": 8 * M,
             "rk4_steps_per_s": world * args.steps * nrk / (st - sa),
             "api": "lb_assemble(host H, host a) + lb_integrate(host v0 -> host v)"}
 

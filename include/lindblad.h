@@ -330,8 +330,11 @@ int lb_batch_destroy(lb_batch_t *b);
 
 /* Expand H (host N x N complex, may be NULL) and assemble Q, R, K from the
  * host Kossakowski matrix a (M x M complex) with the given algorithm
- * (LB_ALG_JOIN or LB_ALG_CLOSED).  keep_parts != 0 also keeps Q and R
- * separately.  The device copy of a is freed before returning.  LB_ENOMEM if
+ * (LB_ALG_JOIN or LB_ALG_CLOSED).  a is Hermitian (the Kossakowski matrix of
+ * Eq. (1) is positive semidefinite); for M > 2048 only its upper triangle
+ * j <= k is read and the device copy takes a_kj = conj(a_jk) below the
+ * diagonal, so half of a crosses the host link.  keep_parts != 0 also keeps
+ * Q and R separately.  The device copy of a is freed before returning.  LB_ENOMEM if
  * the device cannot hold a, A (and Q, R): checked against cudaMemGetInfo
  * before any allocation.  Synchronous. */
 int lb_assemble(const lb_basis_t *b, const double *H, const double *a, int keep_parts,

@@ -464,7 +464,7 @@ int lb_assemble(const lb_basis_t* b, const double* H, const double* a, int keep_
     if ((rc = alloc_or_enomem(dQ, 8 * mm, "Q")) != LB_OK) return rc;
     if ((rc = alloc_or_enomem(dR, 8 * mm, "R")) != LB_OK) return rc;
   }
-  LB_TRY_CUDA(cudaMemcpy(da.p, a, 16 * mm, cudaMemcpyHostToDevice), "copy a");
+  LB_TRY_CUDA(lbi::upload_hermitian(reinterpret_cast<const double2*>(a), da.as<double2>(), M, nullptr), "copy a");
   if (H) {
     if ((rc = alloc_or_enomem(dH, 16 * (size_t)N * N, "H")) != LB_OK) return rc;
     if ((rc = alloc_or_enomem(dcoef, 16 * (size_t)M, "h")) != LB_OK) return rc;

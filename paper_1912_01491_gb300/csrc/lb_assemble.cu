@@ -18,6 +18,8 @@
 //     (k = D_mu); z_{j l n} != 0 if e(l) shares one vertex with e(n)
 //     (j = the third edge, both types) or e(l) = e(n) (j = D_mu).
 // No atomics: every entry is written once, rows of R contiguous per warp.
+#include <algorithm>
+
 #include "lb_internal.h"
 
 namespace {
@@ -2039,9 +2041,52 @@ __global__ void __launch_bounds__(kSameThreads) k_same(BasisView B, AView A, con
   }
 }
 
+// ---------------------------------------------------------------------------
+// Lower triangle of a Hermitian a from its upper triangle: a_kj = conj(a_jk)
+// for k > j, through a 32 x 32 tile in shared memory so that both the read of
+// the upper tile and the write of the lower tile are row-contiguous.  Block
+// (x, y) writes tile row y, tile column x (x <= y) and reads tile (x, y) of
+// the upper side, which no block writes.
+__global__ void __launch_bounds__(256) k_mirror_lower(double2* __restrict__ a, int64_t M) {
+  const int64_t tc = blockIdx.x, tr = blockIdx.y;
+  if (tc > tr) return;
+  __shared__ double2 t[32][33];
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int64_t r = tc * 32 + y, c = tr * 32 + threadIdx.x;
+    if (r < M && c < M) t[y][threadIdx.x] = a[r * M + c];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int64_t r = tr * 32 + y, c = tc * 32 + threadIdx.x;
+    if (r < M && c < M && r > c) {
+      double2 v = t[threadIdx.x][y];
+      v.y = -v.y;
+      a[r * M + c] = v;
+    }
+  }
+}
+
 }  // namespace
 
 namespace lbi {
+
+cudaError_t upload_hermitian(const double2* host, double2* dev, int64_t M, cudaStream_t st) {
+  if (M <= 2048) return cudaMemcpyAsync(dev, host, sizeof(double2) * M * M, cudaMemcpyHostToDevice, st);
+  // row block [j0, j1) brings columns [j0, M): the upper triangle and the
+  // lower half of the diagonal block
+  const int64_t h = std::max<int64_t>(256, (M + 63) / 64);
+  cudaError_t e = cudaSuccess;
+  for (int64_t j0 = 0; j0 < M && e == cudaSuccess; j0 += h) {
+    const int64_t j1 = std::min(M, j0 + h);
+    e = cudaMemcpy2DAsync(dev + j0 * M + j0, sizeof(double2) * M, host + j0 * M + j0, sizeof(double2) * M,
+                          sizeof(double2) * (M - j0), j1 - j0, cudaMemcpyHostToDevice, st);
+  }
+  if (e != cudaSuccess) return e;
+  const unsigned nt = (unsigned)((M + 31) / 32);
+  k_mirror_lower<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(dev, M);
+  note_launch(1);
+  return cudaGetLastError();
+}
 
 cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double2* a, double* A,
                            double* Q, double* R, double* K, int algorithm, cudaStream_t st,

@@ -47,6 +47,10 @@ cudaError_t rho(const lb::BasisView& B, const double* v, double2* out, cudaStrea
 
 // dense assembly (lb_assemble.cu)
 constexpr int kAssembleKernels = 8;
+// Copy a Hermitian M x M a from host memory to the device: only the upper
+// triangle crosses the link (one 2D copy per row block), the strict lower
+// triangle is then written on the device as a_kj = conj(a_jk).
+cudaError_t upload_hermitian(const double2* host, double2* dev, int64_t M, cudaStream_t st);
 cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double2* a,
                            double* A, double* Q, double* R, double* K, int algorithm, cudaStream_t st,
                            cudaEvent_t* ev = nullptr);

@@ -224,6 +224,30 @@ def test_host_buffer_api():
         sysm.close()
 
 
+@pytest.mark.parametrize("N", [46, 51])
+def test_host_buffer_upper_triangle_upload(N):
+    """Above M = 2048 only the upper triangle of the host a is read (a is
+    Hermitian): a host a whose strict lower triangle is NaN assembles to the
+    same bits as the full Hermitian a assembled from device memory."""
+    H, a = _case(N, 4600 + N)
+    M = N * N - 1
+    lb = lbm()
+    a_half = a.copy()
+    a_half[np.tril_indices(M, -1)] = np.nan
+    with lb.Basis(N) as B:
+        ref = _gpu_system(B, H, a, "closed")
+        for alg in ("closed", "join"):
+            sysm = lb.System(B, a_half, H=H, keep_parts=True, algorithm=alg)
+            got = sysm.get("A")
+            K = sysm.get("K")
+            sysm.close()
+            assert np.isfinite(got).all() and np.isfinite(K).all()
+            if alg == "closed":
+                assert np.array_equal(got, ref["A"]) and np.array_equal(K, ref["K"])
+            else:
+                _assert_entries(got, ref["A"], np.abs(ref["A"]).max(), "A (join)")
+
+
 def test_empty_and_degenerate_inputs():
     lb = lbm()
     # a = 0, H = 0: everything vanishes
