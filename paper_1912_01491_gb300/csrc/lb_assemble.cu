@@ -696,31 +696,34 @@ constexpr unsigned long long kDisjointSign1 = disjoint_sign_table(1);
 // the -1/2 of Eq. (09) applied to the exponent and sign.  Values that are not
 // finite, or too small for the exponent arithmetic, take the FP64 path.
 struct FxTerm {
-  unsigned long long mant;  // significand with the implicit bit
-  int e;                    // biased exponent (subnormals: 1)
+  unsigned long long mant;  // significand with the implicit bit set
+  int e;                    // biased exponent field (0 for zero and subnormals)
   unsigned neg;             // sign bit
 };
 
+// The implicit bit is set unconditionally: a zero or subnormal value has
+// e = 0, and the callers only align to E >= 64, so its shift E - e >= 63
+// drops it entirely (its magnitude is below 2^-1022, under the 2^-57
+// truncation of the largest term).
 __device__ __forceinline__ FxTerm fx_split(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int ef = (int)((b >> 52) & 0x7ff);
   FxTerm t;
-  t.mant = (b & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(ef != 0) << 52);
-  t.e = ef ? ef : 1;
+  t.mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  t.e = (int)((b >> 52) & 0x7ff);
   t.neg = (unsigned)(b >> 63);
   return t;
 }
 
-// biased exponent of x as fx_split counts it (subnormals: 1)
+// biased exponent of x (zero and subnormals: 1)
 __device__ __forceinline__ int fx_exponent(double x) {
   return max((__double2hiint(x) >> 20) & 0x7ff, 1);
 }
 
-// term aligned to exponent E, negated when its sign bit XOR flip is set
-__device__ __forceinline__ long long fx_align(const FxTerm& t, int E, unsigned flip) {
+// term aligned to exponent E (E >= 64), negated when its sign bit is set
+__device__ __forceinline__ long long fx_align(const FxTerm& t, int E) {
   const int sh = E - t.e;
   const unsigned long long m = sh < 63 ? ((t.mant << 5) >> sh) : 0ull;
-  return ((t.neg ^ flip) & 1u) ? -(long long)m : (long long)m;
+  return t.neg ? -(long long)m : (long long)m;
 }
 
 
@@ -939,8 +942,8 @@ __device__ __forceinline__ void quad_emit(const double2 (&L)[3][2][2], int64_t P
       for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          D[y][i][j][0] = fx_align(fx_split(L[y][i][j].x), E, 0u);
-          D[y][i][j][1] = fx_align(fx_split(L[y][i][j].y), E, 0u);
+          D[y][i][j][0] = fx_align(fx_split(L[y][i][j].x), E);
+          D[y][i][j][1] = fx_align(fx_split(L[y][i][j].y), E);
         }
     quad_group<0, 0>(D, E, P, M, I, Aout, Qout, Rout);
     quad_group<0, 1>(D, E, P, M, I, Aout, Qout, Rout);
