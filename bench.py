@@ -346,7 +346,7 @@ def run_gb300(args):
 # the bench size by units.  Kept only for the kernel version the capture saw.
 NCU_TRAFFIC = {
     "k_entries (pair x pair; closed: disjoint edges by vertex quadruple)": {
-        "N": 200, "bytes": 17.55e9 + 15.68e9, "units": lambda N: N * (N - 1.0) * (N - 2.0) * (N - 3.0),
+        "N": 200, "bytes": 17.45e9 + 15.56e9, "units": lambda N: N * (N - 1.0) * (N - 2.0) * (N - 3.0),
         "source": "profiles/k_disjoint4_dense_n200.md (full-size DRAM capture at N=200)"},
 }
 
