@@ -361,10 +361,12 @@ __global__ void __launch_bounds__(256) k_assemble(BasisView B, AView A, const do
 
 // Eq. (08): k_s = (i/N) sum_jk a_jk f_jks = -(1/N) sum_jk Im(a_jk) f_jks.
 // One warp per s; lanes stride over the j candidates.
+// CLOSED: the diagonal rows are left to k_kvec_diag_* below.
+template <bool CLOSED>
 __global__ void k_kvec(BasisView B, AView A, double* __restrict__ K) {
   const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (s >= B.M) return;
+  if (s >= (CLOSED ? 2 * B.P : B.M)) return;
   const int N = B.N;
   const Elem es = decode(B, s);
   double acc = 0.0;
@@ -412,6 +414,40 @@ __global__ void k_kvec(BasisView B, AView A, double* __restrict__ K) {
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0) K[s] = -acc / (double)N;
+}
+
+// K on the diagonal rows in closed form.  The only nonzero f_{j k D_nu} with
+// pair j, k are f(S_xy, J_xy, D_nu) = delta_x(nu) - delta_y(nu) = -f(J_xy,
+// S_xy, D_nu), and a is Hermitian, so with g_xy = 2 Im a_{S_xy, J_xy}
+//   K_{D_nu} = -(1/N) sum_{x<y} (delta_x(nu) - delta_y(nu)) g_xy
+//            = -(1/N) sum_k delta_k(nu) G_k,  G_k = sum_{y>k} g_ky - sum_{x<k} g_xk,
+// and sum_k delta_k(nu) G_k = c_nu sum_{k<nu} G_k - nu c_nu G_nu (the prefix
+// form of the Helmert vectors).  k_kvec_diag_g: one block per vertex k, a
+// fixed-order reduction; k_kvec_diag: one warp, the prefix over k.
+__global__ void __launch_bounds__(128) k_kvec_diag_g(BasisView B, AView A, double* __restrict__ G) {
+  const int N = B.N, k = blockIdx.x;
+  double acc = 0.0;
+  for (int u = threadIdx.x; u < N; u += blockDim.x) {
+    if (u == k) continue;
+    const int64_t p = pair_index_any(N, k, u);
+    const double g = 2.0 * ldA(A, p, B.P + p).y;
+    acc += u > k ? g : -g;
+  }
+  __shared__ double red[4];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) G[k] = (red[0] + red[1]) + (red[2] + red[3]);
+}
+
+__global__ void k_kvec_diag(BasisView B, const double* __restrict__ G, double* __restrict__ K) {
+  if (threadIdx.x != 0) return;
+  const int N = B.N;
+  double pre = 0.0;  // sum_{k < nu} G_k
+  for (int nu = 1; nu < N; ++nu) {
+    pre += G[nu - 1];
+    K[d_index(B, nu)] = -(ld_c(B, nu) * pre + ld_lc(B, nu) * G[nu]) / (double)N;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -2153,8 +2189,8 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
   mark(4);
   // closed: stream-ordered scratch for G (diagonal x diagonal) and H (same edge)
   double* scratch = nullptr;
-  if (closed && e == cudaSuccess && (dense_out || A || R))
-    e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(double) * 3 * (size_t)N * N, st);
+  if (closed && e == cudaSuccess && (dense_out || K))
+    e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(double) * (3 * (size_t)N * N + N), st);
   // 4: diagonal x diagonal (closed: d_nu^T G d_mu by prefix sums)
   if (dense_out && e == cudaSuccess && N >= 2) {
     if (closed) {
@@ -2196,11 +2232,20 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
     }
   }
   mark(7);
-  // 7: K
+  // 7: K (closed: the diagonal rows from the vertex sums G in the scratch)
   if (K && e == cudaSuccess) {
-    const int64_t warps = B.M;
-    k_kvec<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(B, av, K);
-    note_launch(1);
+    if (closed) {
+      const int64_t warps = 2 * B.P;
+      if (warps > 0) k_kvec<true><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(B, av, K);
+      double* G = scratch + 3 * (size_t)N * N;
+      k_kvec_diag_g<<<(unsigned)N, 128, 0, st>>>(B, av, G);
+      k_kvec_diag<<<1, 32, 0, st>>>(B, G, K);
+      note_launch(3);
+    } else {
+      const int64_t warps = B.M;
+      k_kvec<false><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(B, av, K);
+      note_launch(1);
+    }
   }
   mark(8);
   if (scratch) {
