@@ -17,7 +17,12 @@
 //     with e(s) (k = the third edge of the triangle) or l = partner(s)
 //     (k = D_mu); z_{j l n} != 0 if e(l) shares one vertex with e(n)
 //     (j = the third edge, both types) or e(l) = e(n) (j = D_mu).
-// No atomics: every entry is written once, rows of R contiguous per warp.
+// That is the JOIN algorithm (LB_ALG_JOIN).  The CLOSED algorithm (the
+// default) groups the entries by the relation of their two edges -- disjoint
+// (vertex quadruples), meeting at one vertex, the same edge, pair x diagonal,
+// diagonal x diagonal -- and sums each group's join terms in closed form;
+// an entry is written by one kernel and, for edges that meet, completed by
+// one later kernel on the same stream.  No atomics on either path.
 #include <algorithm>
 
 #include "lb_internal.h"
@@ -2146,7 +2151,7 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
   };
   mark(0);
   const bool dense_out = A || Q || R;
-  // 0: pair x pair (closed: disjoint edges, one thread per vertex quadruple)
+  // 0: pair x pair (closed: disjoint edges, one lane per vertex quadruple in warp tiles)
   if (dense_out) {
     if (closed) {
       if (N >= 4) {
