@@ -1622,8 +1622,8 @@ __device__ __forceinline__ void scan_inplace(double* arr, int n) {
 // orientation (P_, Q_) = (p, q) (tr = 0) or (q, p) (tr = 1).  For (q, p) the
 // staged a[(q,w) tj][(p,w) tk] becomes a[(p,w) tj][(q,w) tk] = conj(a[(q,w) tk][(p,w) tj]).
 struct PairStage {
-  const double* PX;  // [4][L] prefix over w of Re a[(q,w) tj][(p,w) tk], index tj*2+tk
-  const double* PY;  // [4][L] prefix of Im
+  const double* PX;  // [4][L] Re a[(q,w) tj][(p,w) tk] at w, index tj*2+tk
+  const double* PY;  // [4][L] Im
   const double* TX;  // [2][L] Re a[D_mu][(p,q) t] (raw, index mu)
   const double* TY;  // [2][L] Im
   const double* CX;  // [2][L] prefix of c_mu Re a[D_mu][(p,q) t]
@@ -1635,11 +1635,12 @@ struct PairStage {
   // sum_mu (delta_lo(mu) + sg delta_hi(mu)) x_mu for lo < hi (the d-vector form of dsum)
   __device__ __forceinline__ double dx(int t, int lo, int hi, double sg) const { return DX[t * L + lo] + sg * DX[t * L + hi]; }
   __device__ __forceinline__ double dy(int t, int lo, int hi, double sg) const { return DY[t * L + lo] + sg * DY[t * L + hi]; }
-  __device__ __forceinline__ double sre(int tr, int tj, int tk, int lo, int hi) const {
-    return isum(PX + (tr ? tk * 2 + tj : tj * 2 + tk) * L, lo, hi);
+  // Re / Im of a[(Q_,w) tj][(P_,w) tk] for orientation tr (P_, Q_ = p, q or q, p)
+  __device__ __forceinline__ double sre(int tr, int tj, int tk, int w) const {
+    return PX[(tr ? tk * 2 + tj : tj * 2 + tk) * L + w];
   }
-  __device__ __forceinline__ double sim(int tr, int tj, int tk, int lo, int hi) const {
-    const double x = isum(PY + (tr ? tk * 2 + tj : tj * 2 + tk) * L, lo, hi);
+  __device__ __forceinline__ double sim(int tr, int tj, int tk, int w) const {
+    const double x = PY[(tr ? tk * 2 + tj : tj * 2 + tk) * L + w];
     return tr ? -x : x;
   }
 };
@@ -1650,7 +1651,7 @@ __device__ __forceinline__ double shared_entry_closed(const BasisView& B, const 
                                                       int tr, int P_, int Q_, int v, int ts, int tn) {
   const int N = B.N;
   const int64_t P = B.P;
-  double acc2 = 0.0, accD = 0.0;
+  double acc2 = 0.0, accD = 0.0;  // accD in units of 1/sqrt2
   // (A1): all w outside {v, P_, Q_}.  Every J edge's phase moves by 2 when
   // its vertex order flips, which flips the sign of f (odd phase sums) and of
   // d (even sums); the order of w and v enters sk and sf (sd) once each and
@@ -1666,8 +1667,8 @@ __device__ __forceinline__ double shared_entry_closed(const BasisView& B, const 
       const int kf = sk * sgn_f(b_ + tl + tjf), kd = sk * sgn_d(b_ + tl + tjd);
       const int sfv = ((pv & tk) ^ (qv & tjf)) ? -1 : 1, sdv = ((pv & tk) ^ (qv & tjd)) ? -1 : 1;
       const double* T = S.TOT + ((tr * 2 + ts) * 2 + tn) * 4 + tl * 2;
-      acc2 += sgn_mul(kf, T[0] - sgn_mul(sfv, S.sre(tr, tjf, tk, v, v)));
-      acc2 -= sgn_mul(kd, T[1] - sgn_mul(sdv, S.sim(tr, tjd, tk, v, v)));
+      acc2 += sgn_mul(kf, T[0] - sgn_mul(sfv, S.sre(tr, tjf, tk, v)));
+      acc2 -= sgn_mul(kd, T[1] - sgn_mul(sdv, S.sim(tr, tjd, tk, v)));
     }
   }
   // (A3) e(l) = (v, Q_): k on (P_, Q_), j = D_mu
@@ -1678,8 +1679,8 @@ __device__ __forceinline__ double shared_entry_closed(const BasisView& B, const 
       const int sk = sgn_f(coef_phase(ts, v, P_) + coef_phase(tk, P_, Q_) + coef_phase(tl, Q_, v));
       double part;
       if (tl == tn) part = -S.dy(tk, lo, hi, 1.0);
-      else part = (tn == kS ? -1.0 : 1.0) * S.dx(tk, lo, hi, -1.0);
-      accD += sgn_mul(sk, part) * kInvSqrt2;
+      else part = tn == kS ? -S.dx(tk, lo, hi, -1.0) : S.dx(tk, lo, hi, -1.0);
+      accD += sgn_mul(sk, part);
     }
   }
   // (B) l = partner(s) on (v, P_): k = D_mu, j on (P_, Q_)
@@ -1690,8 +1691,7 @@ __device__ __forceinline__ double shared_entry_closed(const BasisView& B, const 
     const int sf = sgn_f(base + coef_phase(tjf, Q_, P_));
     const int sd = sgn_d(base + coef_phase(tjd, Q_, P_));
     double part = sgn_mul(sf, S.dx(tjf, lo, hi, -1.0)) + sgn_mul(sd, S.dy(tjd, lo, hi, -1.0));
-    if (ts == kS) part = -part;
-    accD += part * kInvSqrt2;
+    accD += ts == kS ? -part : part;
   }
   // (A2) e(l) = (P_, Q_): k on (v, Q_), j on (v, P_)
   const int64_t pvp = pair_index_any(N, v, P_), pvq = pair_index_any(N, v, Q_);
@@ -1707,7 +1707,7 @@ __device__ __forceinline__ double shared_entry_closed(const BasisView& B, const 
     acc2 += sgn_mul(sk * sf, a1.x);
     acc2 -= sgn_mul(sk * sd, a2.y);
   }
-  return -0.5 * (0.5 * acc2 + accD);
+  return -0.5 * fma(accD, kInvSqrt2, 0.5 * acc2);
 }
 
 // Diagonal row D_nu, pair column n on {p, q} of type tn, in closed form: the
@@ -1775,8 +1775,8 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
     const int w = t >> 2, jk = t & 3, tj = jk >> 1, tk = jk & 1;
     double2 val = make_double2(0.0, 0.0);
     if (w != p && w != q) val = ldA(A, tj * P + pair_index_any(N, q, w), tk * P + pair_index_any(N, p, w));
-    PX[jk * L + w + 1] = val.x;
-    PY[jk * L + w + 1] = val.y;
+    PX[jk * L + w] = val.x;
+    PY[jk * L + w] = val.y;
   }
   for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
     const int mu = t >> 1, tt = t & 1;
@@ -1786,19 +1786,9 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
     CX[tt * L + mu + 1] = mu >= 1 ? ld_c(B, mu) * val.x : 0.0;
     CY[tt * L + mu + 1] = mu >= 1 ? ld_c(B, mu) * val.y : 0.0;
   }
-  if (threadIdx.x < 12) {
-    double* arr = threadIdx.x < 4 ? PX + threadIdx.x * L
-                : threadIdx.x < 8 ? PY + (threadIdx.x - 4) * L
-                : threadIdx.x < 10 ? CX + (threadIdx.x - 8) * L : CY + (threadIdx.x - 10) * L;
-    arr[0] = 0.0;
-  }
+  if (threadIdx.x < 4) (threadIdx.x < 2 ? CX + threadIdx.x * L : CY + (threadIdx.x - 2) * L)[0] = 0.0;
   __syncthreads();
-  if (threadIdx.x < 12) {
-    double* arr = threadIdx.x < 4 ? PX + threadIdx.x * L
-                : threadIdx.x < 8 ? PY + (threadIdx.x - 4) * L
-                : threadIdx.x < 10 ? CX + (threadIdx.x - 8) * L : CY + (threadIdx.x - 10) * L;
-    scan_inplace(arr, N);
-  }
+  if (threadIdx.x < 4) scan_inplace(threadIdx.x < 2 ? CX + threadIdx.x * L : CY + (threadIdx.x - 2) * L, N);
   __syncthreads();
   // (D x)_k for the four staged D-column vectors: sum_{mu > k} c_mu x_mu + delta_k(k) x_k
   for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
@@ -1819,7 +1809,7 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
     const int tk = 1 ^ tl ^ ts, tj = fd ? (tl ^ tn) : (1 ^ tl ^ tn);
     double acc = 0.0;
     for (int w = sub; w < N; w += 8) {
-      const double x = fd ? S0.sim(tr, tj, tk, w, w) : S0.sre(tr, tj, tk, w, w);
+      const double x = fd ? S0.sim(tr, tj, tk, w) : S0.sre(tr, tj, tk, w);
       const int sg = ((P_ < w ? tk : 0) ^ (Q_ < w ? tj : 0)) ? -1 : 1;
       acc += sgn_mul(sg, x);
     }
@@ -1845,7 +1835,7 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
         const int phn = coef_phase(tn, v, vp);
         const int sf = sgn_f(phn + coef_phase(tjf, vp, w) + phl);
         const int sd = sgn_d(phn + coef_phase(tjd, vp, w) + phl);
-        const double tv = sgn_mul(sf, S.sre(tr, tjf, tkb, w, w)) - sgn_mul(sd, S.sim(tr, tjd, tkb, w, w));
+        const double tv = sgn_mul(sf, S.sre(tr, tjf, tkb, w)) - sgn_mul(sd, S.sim(tr, tjd, tkb, w));
         u += tl == kS ? -tv : tv;
       }
       if (w > v) u = -u;
