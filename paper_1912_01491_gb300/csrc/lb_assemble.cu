@@ -1891,7 +1891,9 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
   double* PGY = sq + L;       // prefix of gs(lam) YY[lam] over lam in [lo_s, bs]
   double* PG2C = sq + 2 * L;  // prefix of 2 gs(lam) c_lam
   double* PCY = sq + 3 * L;   // prefix of c_mu YY[mu]
-  double* PW = sq + 4 * L;    // [8][L]: (vi, tl, {U1, U2 terms}) prefixes over w (see below)
+  double* PU1 = sq + 4 * L;   // [2][L]: prefix over w of U1 (both tl), per vi (see below)
+  double* RU1 = sq + 6 * L;   // [2][L]: U1 at w (raw)
+  double* PU2 = sq + 8 * L;   // [2][L]: prefix over w of U2 (both tl), per vi
   __shared__ double cst[2];   // c1 = sum gs Re a[s][D_mu], c2 = sum gs Im a[partner(s)][D_mu]
   for (int x = threadIdx.x; x < N; x += blockDim.x) {
     const double y = x >= 1 ? ldA(A, sb, d_index(B, x)).y : 0.0;
@@ -1907,32 +1909,36 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
   //   sum_w sk (tau sigma (delta_w(nu) - delta_v(nu)) bx - (delta_v(nu) + delta_w(nu)) ly)
   //   = d_nu^T U1 + delta_v(nu) U2,  U1_w = sk (tau sigma bx - ly),  U2 = sum_w sk (-tau sigma bx - ly),
   // and d_nu^T U1 = c_nu sum_{w<nu} U1_w + delta_nu(nu) U1_nu (a prefix over w).
-  for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
-    const int vi = t / (2 * N), w = (t / 2) % N, tl = t & 1;
+  // The two tl of one (vi, w) enter every entry with the same coefficients,
+  // so they are summed here.
+  for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+    const int vi = t / N, w = t % N;
     double u1 = 0.0, u2 = 0.0;
     if (w != as && w != bs) {
       const int v = vi ? bs : as, vp = vi ? as : bs;
       const int64_t pl = pair_index_any(N, v, w), pk = pair_index_any(N, vp, w);
-      const int tk = 1 ^ tl ^ ts;
-      const int64_t k = (int64_t)tk * P + pk;
-      const double ly = ldA(A, (int64_t)tl * P + pl, k).y;
-      const double bx = ldA(A, (int64_t)(1 - tl) * P + pl, k).x;
-      const int sk = sgn_f(coef_phase(ts, v, vp) + coef_phase(tk, vp, w) + coef_phase(tl, w, v));
-      const double tsb = ((tl == kS) != (w < v)) ? bx : -bx;  // tau sigma bx
-      u1 = sgn_mul(sk, tsb - ly);
-      u2 = sgn_mul(sk, -tsb - ly);
+#pragma unroll
+      for (int tl = 0; tl < 2; ++tl) {
+        const int tk = 1 ^ tl ^ ts;
+        const int64_t k = (int64_t)tk * P + pk;
+        const double ly = ldA(A, (int64_t)tl * P + pl, k).y;
+        const double bx = ldA(A, (int64_t)(1 - tl) * P + pl, k).x;
+        const int sk = sgn_f(coef_phase(ts, v, vp) + coef_phase(tk, vp, w) + coef_phase(tl, w, v));
+        const double tsb = ((tl == kS) != (w < v)) ? bx : -bx;  // tau sigma bx
+        u1 += sgn_mul(sk, tsb - ly);
+        u2 += sgn_mul(sk, -tsb - ly);
+      }
     }
-    PW[((vi * 2 + tl) * 2 + 0) * L + w + 1] = u1;
-    PW[((vi * 2 + tl) * 2 + 1) * L + w + 1] = u2;
+    PU1[vi * L + w + 1] = u1;
+    RU1[vi * L + w] = u1;
+    PU2[vi * L + w + 1] = u2;
   }
-  if (threadIdx.x < 11) {
-    double* arr = threadIdx.x < 3 ? PGY + threadIdx.x * L : PW + (threadIdx.x - 3) * L;
-    arr[0] = 0.0;
-  }
+  // prefix arrays: PGY, PG2C, PCY, PU1[0..1], PU2[0..1]
+  auto scanned = [&](int i) { return i < 3 ? PGY + i * L : i < 5 ? PU1 + (i - 3) * L : PU2 + (i - 5) * L; };
+  if (threadIdx.x < 7) scanned(threadIdx.x)[0] = 0.0;
   __syncthreads();
-  if (threadIdx.x < 11) {
-    double* arr = threadIdx.x < 3 ? PGY + threadIdx.x * L : PW + (threadIdx.x - 3) * L;
-    scan_inplace(arr, N);
+  if (threadIdx.x < 7) {
+    scan_inplace(scanned(threadIdx.x), N);
   } else if (threadIdx.x == 32) {
     double c1 = 0.0;
     for (int mu = lo_s; mu <= bs; ++mu) c1 += (dlt(B, as, mu) - dlt(B, bs, mu)) * ldA(A, s, d_index(B, mu)).x;
@@ -1948,22 +1954,17 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
     if (nu >= lo_s && nu <= bs) {
       const double gs = dlt(B, as, nu) - dlt(B, bs, nu);
       double t2 = 2.0 * isum(PCY, nu + 1, N - 1);
-      if (nu != 1) t2 += 2.0 * (double)(1 - nu) * ld_c(B, nu) * YY[nu];
+      if (nu != 1) t2 += 2.0 * (ld_c(B, nu) + ld_lc(B, nu)) * YY[nu];  // (1 - nu) c_nu
       accD += gs * t2;
     }
     double acc = sgs * accD;
-    // l = (v, w) sharing a vertex with e(s): d_nu^T U1 + delta_v(nu) U2 per (v, tl)
+    // l = (v, w) sharing a vertex with e(s): d_nu^T U1 + delta_v(nu) U2 per v
     double accA = 0.0;
     const double cnu = ld_c(B, nu), dnn = dlt(B, nu, nu);
 #pragma unroll
     for (int vi = 0; vi < 2; ++vi) {
       const double dv = dlt(B, vi ? bs : as, nu);
-#pragma unroll
-      for (int tl = 0; tl < 2; ++tl) {
-        const double* PU1 = PW + ((vi * 2 + tl) * 2 + 0) * L;
-        const double* PU2 = PW + ((vi * 2 + tl) * 2 + 1) * L;
-        accA += cnu * PU1[nu] + dnn * (PU1[nu + 1] - PU1[nu]) + dv * PU2[N];
-      }
+      accA += cnu * PU1[vi * L + nu] + dnn * RU1[vi * L + nu] + dv * PU2[vi * L + N];
     }
     acc += accA * kInvSqrt2;
     // l = partner(s), k = D_mu
@@ -2165,7 +2166,7 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
   // 2: pair x diagonal
   if (dense_out && e == cudaSuccess) {
     if (closed) {
-      const size_t smem = sizeof(double) * 12 * (size_t)(N + 1);
+      const size_t smem = sizeof(double) * 10 * (size_t)(N + 1);
       e = cudaFuncSetAttribute(k_pd_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess) k_pd_closed<<<(unsigned)P2, kRowThreads, smem, st>>>(B, av, h, A, Q, R);
     } else {
