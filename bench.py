@@ -79,6 +79,22 @@ def dist_env():
     return world, rank, local
 
 
+def replica_max(values, dist, device):
+    """Per-rank timings -> their maximum over ranks (the slowest replica sets
+    the time of the job); unchanged without a process group."""
+    import torch
+    t = torch.tensor([float(x) for x in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def replica_value(world, units_per_rank, seconds):
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed over the max-over-ranks time."""
+    return world * units_per_rank / seconds
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples every 200 ms while running."""
 
@@ -246,12 +262,9 @@ def run_gb300(args):
     top = max(kern, key=kern.get)
     rk_ms = sum(e[2].elapsed_time(e[3]) for e in evs)
     rk32_ms = sum(e[3].elapsed_time(e[4]) for e in evs)
-    times = torch.tensor([total_ms, asm_ms, rk_ms, rk32_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    total_ms, asm_ms, rk_ms, rk32_ms = times.tolist()
+    total_ms, asm_ms, rk_ms, rk32_ms = replica_max([total_ms, asm_ms, rk_ms, rk32_ms], dist, dev)
     K_ = args.steps
-    value = world * K_ * M * M / (asm_ms * 1e-3)
+    value = replica_value(world, K_ * M * M, asm_ms * 1e-3)
     t_asm = asm_ms / K_ * 1e-3
     alg_bytes = 16.0 * M * M + 8.0 * M * M + 16.0 * M
     # the other algorithm, timed outside the timed region for comparison
@@ -300,8 +313,8 @@ def run_gb300(args):
             "l2": "inputs larger than L2 (a is %.1f GB)" % (16.0 * M * M / 1e9),
             "parallelism": "replicas" if world > 1 else "single",
         },
-        "rk4_steps_per_s": world * K_ * nrk / (rk_ms * 1e-3),
-        "rk4_fp32_corrected_steps_per_s": world * K_ * nrk32 / (rk32_ms * 1e-3),
+        "rk4_steps_per_s": replica_value(world, K_ * nrk, rk_ms * 1e-3),
+        "rk4_fp32_corrected_steps_per_s": replica_value(world, K_ * nrk32, rk32_ms * 1e-3),
         "assembly_algorithm": args.algorithm,
         "assembly_ms": asm_ms / K_,
         "assembly_kernel_ms": kern,
@@ -413,10 +426,7 @@ def run_e2e(args, lb, B, a, H_host, M, nrk, dt, dev, dist, world):
         if k > 0:
             t_asm.append(t1 - t0)
             t_tot.append(t2 - t0)
-    tt = torch.tensor([sum(t_asm), sum(t_tot)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    sa, st = tt.tolist()
+    sa, st = replica_max([sum(t_asm), sum(t_tot)], dist, dev)
     del a_host
     # lb_assemble brings the upper triangle of a (row blocks of h rows, columns
     # from the block's first row on) for M > 2048, all of a otherwise
@@ -425,10 +435,10 @@ def run_e2e(args, lb, B, a, H_host, M, nrk, dt, dev, dist, world):
         a_bytes = sum(16 * (min(M, j0 + h) - j0) * (M - j0) for j0 in range(0, M, h))
     else:
         a_bytes = 16 * M * M
-    return {"value": world * args.steps * M * M / sa, "unit": "entries/s",
+    return {"value": replica_value(world, args.steps * M * M, sa), "unit": "entries/s",
             "assemble_s_per_step": [round(x, 4) for x in t_asm],
             "h2d_bytes_per_step": a_bytes + 16 * B.N * B.N + 8 * M, "d2h_bytes_per_step": 8 * M,
-            "rk4_steps_per_s": world * args.steps * nrk / (st - sa),
+            "rk4_steps_per_s": replica_value(world, args.steps * nrk, st - sa),
             "api": "lb_assemble(host H, host a) + lb_integrate(host v0 -> host v)"}
 
 
