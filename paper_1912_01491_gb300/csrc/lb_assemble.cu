@@ -1988,11 +1988,9 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
 // z-fiber of (partner(s), n) at D_nu.
 constexpr int kSameThreads = 128;
 
-template <bool CLOSED>
-__global__ void __launch_bounds__(kSameThreads) k_same(BasisView B, AView A, const double* __restrict__ Hr,
-                                                       const double* __restrict__ Hi, double* __restrict__ Aout,
+__global__ void __launch_bounds__(kSameThreads) k_same(BasisView B, AView A, double* __restrict__ Aout,
                                                        double* __restrict__ Rout) {
-  extern __shared__ double shd[];  // JOIN: G[N], Z[N]
+  extern __shared__ double shd[];  // G[N], Z[N]
   __shared__ double red[kSameThreads / 32];
   const int N = B.N;
   const int64_t P = B.P, M = B.M;
@@ -2005,7 +2003,7 @@ __global__ void __launch_bounds__(kSameThreads) k_same(BasisView B, AView A, con
     __syncthreads();  // red[] (and G, Z) of the previous combination have been read
     double* G = shd;
     double* Z = shd + N;
-    if (!CLOSED) {
+    {
       const int lo = imax(a, 1);
       for (int t = threadIdx.x; t < N; t += blockDim.x) {
         const double g = (t >= lo && t <= b) ? dlt(B, a, t) - dlt(B, b, t) : 0.0;
@@ -2044,7 +2042,7 @@ __global__ void __launch_bounds__(kSameThreads) k_same(BasisView B, AView A, con
     // (B) l = partner(s): k = D_mu, j = D_nu, i.e. sum_{mu,nu} G_mu Z_nu X[nu][mu] with
     //     G = -+ D^T (e_a - e_b), Z = D^T (e_a + e_b) (d-fibre) or -+ D^T (e_a - e_b),
     //     X = -Im or Re of the D x D block of a: entries of H = D X D^T
-    if (!CLOSED) {  // every join term of the D x D block
+    {  // every join term of the D x D block
       const int lo = imax(a, 1), nhi = dfib ? N - 1 : b;
       for (int mu = lo + threadIdx.x; mu <= b; mu += blockDim.x) {
         const int64_t kmu = d_index(B, mu);
@@ -2055,14 +2053,6 @@ __global__ void __launch_bounds__(kSameThreads) k_same(BasisView B, AView A, con
         }
         accD = fma(G[mu], inner, accD);
       }
-    } else if (threadIdx.x == 0) {
-      const int64_t aa = (int64_t)a * N + a, ab_ = (int64_t)a * N + b, ba = (int64_t)b * N + a,
-                    bb = (int64_t)b * N + b;
-      const double sgs = ts == kS ? -1.0 : 1.0;
-      if (dfib)
-        accD = -sgs * ((Hi[aa] - Hi[ab_]) + (Hi[ba] - Hi[bb]));
-      else
-        accD = sgs * (tn == kS ? -1.0 : 1.0) * ((Hr[aa] - Hr[ab_]) - (Hr[ba] - Hr[bb]));
     }
     double tot = warp_sum(0.5 * acc2 + accD);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
@@ -2075,6 +2065,80 @@ __global__ void __launch_bounds__(kSameThreads) k_same(BasisView B, AView A, con
       if (Rout) Rout[o] += r;
       if (Aout) Aout[o] += r;
     }
+  }
+}
+
+// Same edge (a, b), closed form: the four type pairs (ts, tn) of the block's
+// edge at once.  For each (v, w) with w outside the edge the four values
+// a[(tj, (v', w))][(tk, (v', w))], tj, tk in {S, J}, are loaded once and
+// enter every (ts, tn, tl) term (the per-pair sums keep the order of one pair
+// at a time); the l = partner(s) part comes from H = D X D^T.
+__global__ void __launch_bounds__(kSameThreads) k_same_closed(BasisView B, AView A, const double* __restrict__ Hr,
+                                                              const double* __restrict__ Hi,
+                                                              double* __restrict__ Aout, double* __restrict__ Rout) {
+  __shared__ double red[kSameThreads / 32][4];
+  const int N = B.N;
+  const int64_t P = B.P, M = B.M;
+  const int64_t e = blockIdx.x;
+  const int32_t ab = __ldg(B.pair_ab + e);
+  const int a = ab >> 16, b = ab & 0xffff;
+  double acc2[4] = {0.0, 0.0, 0.0, 0.0};  // index ts * 2 + tn
+  // (A) e(l) = (v, w), v in {a, b}, w outside: k and j on (v', w)
+  for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+    const int vi = t / N, w = t % N;
+    if (w == a || w == b) continue;
+    const int v = vi ? b : a, vp = vi ? a : b;
+    const int64_t pw = pair_index_any(N, vp, w);
+    double2 X[2][2];  // X[tj][tk] = a[(tj, (v', w))][(tk, (v', w))]
+#pragma unroll
+    for (int tj = 0; tj < 2; ++tj)
+#pragma unroll
+      for (int tk = 0; tk < 2; ++tk) X[tj][tk] = ldA(A, tj * P + pw, tk * P + pw);
+#pragma unroll
+    for (int combo = 0; combo < 4; ++combo) {
+      const int ts = combo >> 1, tn = combo & 1;
+#pragma unroll
+      for (int tl = 0; tl < 2; ++tl) {
+        const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+        const int phl = coef_phase(tl, w, v);
+        const int sk = sgn_f(coef_phase(ts, v, vp) + coef_phase(tk, vp, w) + phl);
+        const int base = coef_phase(tn, v, vp) + phl;
+        const int sf = sgn_f(base + coef_phase(tjf, vp, w));
+        const int sd = sgn_d(base + coef_phase(tjd, vp, w));
+        acc2[combo] += sgn_mul(sk * sf, X[tjf][tk].x);
+        acc2[combo] -= sgn_mul(sk * sd, X[tjd][tk].y);
+      }
+    }
+  }
+  // (B) l = partner(s): k = D_mu, j = D_nu, from the entries of H = D X D^T
+  double accD[4] = {0.0, 0.0, 0.0, 0.0};
+  if (threadIdx.x == 0) {
+    const int64_t aa = (int64_t)a * N + a, ab_ = (int64_t)a * N + b, ba = (int64_t)b * N + a,
+                  bb = (int64_t)b * N + b;
+#pragma unroll
+    for (int combo = 0; combo < 4; ++combo) {
+      const int ts = combo >> 1, tn = combo & 1;
+      const double sgs = ts == kS ? -1.0 : 1.0;
+      if (ts != tn)  // n = partner(s) = l: d-fibre
+        accD[combo] = -sgs * ((Hi[aa] - Hi[ab_]) + (Hi[ba] - Hi[bb]));
+      else
+        accD[combo] = sgs * (tn == kS ? -1.0 : 1.0) * ((Hr[aa] - Hr[ab_]) - (Hr[ba] - Hr[bb]));
+    }
+  }
+#pragma unroll
+  for (int combo = 0; combo < 4; ++combo) {
+    const double tot = warp_sum(0.5 * acc2[combo] + accD[combo]);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][combo] = tot;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const int combo = threadIdx.x, ts = combo >> 1, tn = combo & 1;
+    double sum = 0.0;
+    for (int i = 0; i < kSameThreads / 32; ++i) sum += red[i][combo];
+    const double r = -0.5 * sum;
+    const int64_t o = (ts * P + e) * M + (tn * P + e);
+    if (Rout) Rout[o] += r;
+    if (Aout) Aout[o] += r;
   }
 }
 
@@ -2220,10 +2284,10 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
     if (closed) {
       double* H = scratch + (size_t)N * N;
       k_dh<<<(unsigned)N, 128, sizeof(double) * 2 * (size_t)N, st>>>(B, av, H, H + (size_t)N * N);
-      k_same<true><<<(unsigned)B.P, kSameThreads, 0, st>>>(B, av, H, H + (size_t)N * N, A, R);
+      k_same_closed<<<(unsigned)B.P, kSameThreads, 0, st>>>(B, av, H, H + (size_t)N * N, A, R);
       note_launch(2);
     } else {
-      k_same<false><<<(unsigned)B.P, kSameThreads, sizeof(double) * 2 * N, st>>>(B, av, nullptr, nullptr, A, R);
+      k_same<<<(unsigned)B.P, kSameThreads, sizeof(double) * 2 * N, st>>>(B, av, A, R);
       note_launch(1);
     }
   }
