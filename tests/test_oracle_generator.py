@@ -69,6 +69,29 @@ def test_q_antisymmetric_and_k_r_real():
     assert np.abs(Ri).max() < 1e-15 and np.abs(Ki).max() < 1e-15
 
 
+@pytest.mark.parametrize("N", [3, 6, 9])
+def test_k_diagonal_rows_closed_form(N):
+    """Eq. (08) on the diagonal rows: the only nonzero f_{j k D_nu} with pair
+    j, k are f(S_xy, J_xy, D_nu) = delta_x(nu) - delta_y(nu) = -f(J_xy, S_xy,
+    D_nu), so for Hermitian a, K_{D_nu} = -(1/N) sum_k delta_k(nu) G_k with
+    G_k = sum_{y>k} g_ky - sum_{x<k} g_xk and g_xy = 2 Im a_{S_xy, J_xy}; the
+    diagonal elements delta_k(nu) of D_nu come from the basis matrices."""
+    _, a = _random_case(N, 900 + N)
+    M, P = N * N - 1, N * (N - 1) // 2
+    pairs = [(x, y) for x in range(N) for y in range(x + 1, N)]
+    G = np.zeros(N)
+    for p_, (x, y) in enumerate(pairs):
+        g = 2.0 * a[p_, P + p_].imag
+        G[x] += g
+        G[y] -= g
+    with Oracle(N) as o:
+        K = o.K(a)
+        for nu in range(1, N):
+            delta = np.diag(o.basis_matrix(2 * P + nu - 1)).real
+            ref = -(delta @ G) / N
+            assert abs(K[2 * P + nu - 1] - ref) <= 1e-14 * max(np.abs(K).max(), 1e-300)
+
+
 def test_n2_bloch_precession():
     """H = (w/2) sigma_z: d<sx>/dt = -w <sy>, d<sy>/dt = w <sx>."""
     w = 1.7
