@@ -596,64 +596,6 @@ __device__ __forceinline__ double part_p_disjoint(const BasisView& B, const AVie
 }
 
 // Pair-pair block (s, n < 2P); one thread per entry, 256 consecutive n per block.
-// Closed form of part_d_pp.  The D_l (l = 1..N-1) together with 1/sqrt(N)
-// are an orthonormal basis of the diagonal matrices, so
-//   sum_lam delta_x(lam) delta_y(lam) = [x == y] - 1/N,
-// and the two lambda sums of part_d_pp are integer combinations of edge
-// coincidences (the 1/N terms cancel):
-//   sum gs gn = [as=an] - [as=bn] - [bs=an] + [bs=bn],
-//   sum gs hn = [as=an] + [as=bn] - [bs=an] - [bs=bn];
-// both vanish for disjoint edges.
-__device__ __forceinline__ double part_d_pp_closed(const AView& A, int as, int bs, int ts, int an, int bn,
-                                                   int tn, int64_t sb, int64_t n, int64_t nb) {
-  const int e1 = as == an, e2 = as == bn, e3 = bs == an, e4 = bs == bn;
-  const int cf = e1 - e2 - e3 + e4, cd = e1 + e2 - e3 - e4;
-  if (cf == 0 && cd == 0) return 0.0;
-  const double2 a1 = ldA_row(A, nb, sb);
-  const double2 a2 = ldA_row(A, n, sb);
-  const double sgs = ts == kS ? 1.0 : -1.0, sgn = tn == kS ? 1.0 : -1.0;
-  return sgs * (sgn * a1.x * (double)cf - a2.y * (double)cd);
-}
-
-// Closed form of part_p_disjoint.  The term of (v, w, l) and that of
-// (v', w', l') with the matching type of l' read the same entry of a, once
-// as a_jk and once as a_kj = conj(a_jk), with equal contributions, so the
-// eight terms with v = as, doubled, give the sum: 8 reads, 8 adds.
-__device__ __forceinline__ double part_p_disjoint_closed(const BasisView& B, const AView& A, int as, int bs,
-                                                         int ts, int an, int bn, int tn) {
-  const int N = B.N;
-  const int64_t P = B.P;
-  double acc2 = 0.0;
-  const int v = as, vp = bs;
-  const int phs = coef_phase(ts, v, vp);
-#pragma unroll
-  for (int wi = 0; wi < 2; ++wi) {
-    const int w = wi ? bn : an, wp = wi ? an : bn;
-    const int phn = coef_phase(tn, w, wp);
-    const int64_t pk = pair_index_any(N, vp, w), pj = pair_index_any(N, v, wp);
-#pragma unroll
-    for (int tl = 0; tl < 2; ++tl) {
-      const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
-      const int phl_wv = coef_phase(tl, w, v), phl_vw = coef_phase(tl, v, w);
-      const int sk = sgn_f(phs + coef_phase(tk, vp, w) + phl_wv);
-      const int sf = sgn_f(phn + coef_phase(tjf, wp, v) + phl_vw);
-      const int sd = sgn_d(phn + coef_phase(tjd, wp, v) + phl_vw);
-      const int64_t k = tk * P + pk, jf = tjf * P + pj, jd = tjd * P + pj;
-      double2 a1, a2;
-      if (wi == 0) {
-        a1 = ldA_row(A, jf, k);
-        a2 = ldA_row(A, jd, k);
-      } else {
-        a1 = ldA(A, jf, k);
-        a2 = ldA(A, jd, k);
-      }
-      acc2 += sgn_mul(sk * sf, a1.x);
-      acc2 -= sgn_mul(sk * sd, a2.y);
-    }
-  }
-  return acc2;  // = 2 * (1/2) * acc2
-}
-
 template <int ALG>
 __global__ void __launch_bounds__(256) k_entries(BasisView B, AView A, const double* __restrict__ h,
                                                  double* __restrict__ Aout, double* __restrict__ Qout,
@@ -666,15 +608,12 @@ __global__ void __launch_bounds__(256) k_entries(BasisView B, AView A, const dou
   const Elem es = decode(B, s), en = decode(B, n);
   double q = 0.0;
   const int as = es.a, bs = es.b, ts = es.kind, an = en.a, bn = en.b, tn = en.kind;
-  double acc = ALG == LB_ALG_CLOSED
-                   ? part_d_pp_closed(A, as, bs, ts, an, bn, tn, partner(B, s), n, partner(B, n))
-                   : part_d_pp<ALG>(B, A, as, bs, ts, an, bn, tn, partner(B, s), n, partner(B, n));
+  double acc = part_d_pp<ALG>(B, A, as, bs, ts, an, bn, tn, partner(B, s), n, partner(B, n));
   int shared = 0, cv = -1;
   if (as == an || as == bn) { ++shared; cv = as; }
   if (bs == an || bs == bn) { ++shared; cv = bs; }
   if (shared == 0)
-    acc += ALG == LB_ALG_CLOSED ? part_p_disjoint_closed(B, A, as, bs, ts, an, bn, tn)
-                                : part_p_disjoint(B, A, as, bs, ts, an, bn, tn);
+    acc += part_p_disjoint(B, A, as, bs, ts, an, bn, tn);
   if (h != nullptr) {
     if (shared == 1) {
       const int p = (as == cv) ? bs : as, qv = (an == cv) ? bn : an;
@@ -692,8 +631,13 @@ __global__ void __launch_bounds__(256) k_entries(BasisView B, AView A, const dou
   if (Aout) Aout[o] = q + r;
 }
 
-// Sign tables of the disjoint-edge closed form.  For an edge pair with
-// v = a_s < v' = b_s and (w, w') = (a_n, b_n) (wi = 0) or (b_n, a_n) (wi = 1),
+// Sign tables of the disjoint-edge closed form.  For disjoint edges e(s),
+// e(n) the l-pair part of Eq. (09) runs over l = (v, w) with v on e(s) and
+// w on e(n); the term of (v, w, l) and that of (v', w', l') (the other ends,
+// the matching type of l') read the same entry of a, once as a_jk and once
+// as a_kj = conj(a_jk), with equal contributions, so the eight terms with
+// v = a_s, doubled, give the sum.  For v = a_s < v' = b_s and
+// (w, w') = (a_n, b_n) (wi = 0) or (b_n, a_n) (wi = 1),
 // every coefficient phase in the eight terms of the (S, S) and (S, J) sums
 // depends only on three vertex orders: b0 = [w < v], b1 = [v' < w],
 // b2 = [w' < v].  Bit (8 idx + 4 tn + 2 tl + {0: f term, 1: d term}) of
