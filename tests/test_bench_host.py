@@ -1,0 +1,43 @@
+"""Host-side arithmetic of the benchmark's roofline report (CPU only): the
+algorithmic bytes of the vertex-quadruple kernel (16 B per disjoint
+pair x pair entry, 24 entries per quadruple) and the scaling of the stored
+DRAM capture by the number of quadruples."""
+import math
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+QUAD = "k_entries (pair x pair; closed: disjoint edges by vertex quadruple)"
+
+
+def test_quadruple_kernel_bytes_and_fraction():
+    N = 200
+    M = N * N - 1
+    peaks = {"hbm_gbs": 6769.4}
+    r = bench.assembly_roofline("closed", QUAD, 10.0, N, M, None, 1.25, peaks)
+    entries = 24 * math.comb(N, 4)
+    assert r["algorithmic_bytes_per_launch"] == pytest.approx(16.0 * entries)
+    assert r["achieved"] == pytest.approx(16.0 * entries / 0.010 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6769.4)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+
+
+def test_disjoint_entry_count_matches_edge_pairs():
+    # ordered pairs of disjoint edges times 4 type pairs = 24 C(N, 4)
+    for N in range(4, 12):
+        edges = [(a, b) for a in range(N) for b in range(a + 1, N)]
+        disjoint = sum(1 for e in edges for f in edges if not set(e) & set(f))
+        assert 4 * disjoint == 24 * math.comb(N, 4)
+
+
+def test_stored_traffic_scales_with_quadruples():
+    t200, src = bench.ncu_traffic(QUAD, 200)
+    t100, _ = bench.ncu_traffic(QUAD, 100)
+    assert src and t200 > 0
+    assert t100 / t200 == pytest.approx(math.comb(100, 4) / math.comb(200, 4))
+    assert bench.ncu_traffic("k_meet (closed: meeting edges, D-section and Q parts)", 200) == (None, None)
