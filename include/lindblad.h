@@ -16,7 +16,8 @@
  *   - The Kossakowski matrix `a` follows the index convention of Eqs. (08)
  *     and (09): L_D(rho) = sum_jk a_jk (F_j rho F_k - 1/2 {F_k F_j, rho}),
  *     i.e. a = K^T for the matrix K_mn of Eq. (1); a must be Hermitian and is
- *     passed as the full M x M matrix (both triangles).
+ *     passed as the full M x M matrix (both triangles; lb_assemble reads only
+ *     the upper one for M > 2048).
  *   - Every function returns an int status (LB_OK = 0 on success).  On error
  *     nothing is half-written to caller buffers except where stated, no
  *     exception or abort crosses the ABI, and lb_last_error() returns a
