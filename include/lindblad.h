@@ -172,10 +172,14 @@ int lb_assemble_dense(const lb_basis_t *b, const double *h, const double *a,
 
 /* algorithms of the dense R assembly */
 #define LB_ALG_JOIN 0   /* every join term visited, as in Sec. 4 item 2.5 (O(N^5)) */
-#define LB_ALG_CLOSED 1 /* the runs of D-section terms whose coefficients are all
-                           c_l^2 = 1/(l(l+1)) summed in closed form,
-                           sum_{l=x}^{y} c_l^2 = 1/x - 1/(y+1) (O(N^4)); same R
-                           up to rounding */
+#define LB_ALG_CLOSED 1 /* the join terms summed in closed form, grouped by the
+                           relation of the two edges of (s, n): completeness
+                           of the D_l (sum_l delta_x(l) delta_y(l) = [x = y] - 1/N),
+                           their Helmert prefix structure, the phase parity of
+                           J edges, and vertex quadruples for disjoint edges
+                           (signed sums of 8 entries of a, formed as integer
+                           sums of aligned significands); O(N^4); same R up to
+                           rounding */
 
 /* lb_assemble_dense with a choice of algorithm (LB_ALG_JOIN or LB_ALG_CLOSED). */
 int lb_assemble_dense_ex(const lb_basis_t *b, const double *h, const double *a,
