@@ -122,9 +122,11 @@ int lb_structure_export(const lb_basis_t *b, int which, int32_t *idx3, double *v
  * no cudaMalloc, cudaFree or allocating library routine.
  *   - Limit: M <= 65535 (N <= 256); a larger basis returns LB_EINVAL with a
  *     message naming the limit, and nothing is launched.
- *   - Set-up: the first call on each device looks up the array's device
- *     address with cudaGetSymbolAddress (that device current) and caches it;
- *     make that first call before any stream capture begins.
+ *   - Set-up: every call looks up the array's device address on the current
+ *     device with cudaGetSymbolAddress (nothing is cached, so the call stays
+ *     valid after a cudaDeviceReset or a recreated context); the first call
+ *     on a device loads the module there, so make it before any stream
+ *     capture begins.
  *   - Sharing: all calls on a device use the same array, which keeps the last
  *     call's contents (every word a call reads is written earlier in the same
  *     call, so nothing needs clearing).  The call returns after its fill has

@@ -7,9 +7,6 @@
 // scratch (the per-m counts and their exclusive scan) lives in a file-scope
 // __device__ array of fixed size instead of buffers allocated per call.  The
 // paper has no counterpart: it is a deployment concern of this library.
-#include <mutex>
-#include <vector>
-
 #include "lb_internal.h"
 
 namespace {
@@ -64,23 +61,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_single_block(const int64_
   if (t == kScanThreads - 1) off[M] = warp_tot[kScanThreads / 32 - 1];
 }
 
-// Device address of g_export_scratch, looked up once per device.
-std::mutex g_mu;
-std::vector<int64_t*> g_addr;
-
+// Device address of g_export_scratch in the current device's context, looked
+// up on every call (cheap next to the count and fill kernels).  A cached
+// address would outlive a cudaDeviceReset or a recreated primary context, in
+// which the module, and with it the array, is loaded again elsewhere.
 cudaError_t scratch_address(int64_t** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  int64_t* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_export_scratch);
   if (e != cudaSuccess) return e;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if ((int)g_addr.size() <= dev) g_addr.resize(dev + 1, nullptr);
-  if (g_addr[dev] == nullptr) {
-    int64_t* p = nullptr;
-    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_export_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 

@@ -181,6 +181,29 @@ def _f64(t):
     return t
 
 
+def export_capacity(idx, val):
+    """Capacity in triples of caller buffers for a structure export: idx a
+    contiguous int32 CUDA tensor of shape (n, 3), val a contiguous float64 CUDA
+    tensor; the smaller of the two counts.  Raises ValueError otherwise, before
+    anything reaches the library (the C entry point receives one capacity for
+    both buffers and cannot check them itself)."""
+    import torch
+    for name, t, dt in (("idx", idx, torch.int32), ("val", val, torch.float64)):
+        if not hasattr(t, "device") or not hasattr(t, "dtype"):
+            raise ValueError("%s must be a torch tensor" % name)
+        if t.device.type != "cuda":
+            raise ValueError("%s must be a CUDA tensor, got %s" % (name, t.device))
+        if t.dtype != dt:
+            raise ValueError("%s must be %s, got %s" % (name, dt, t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    if idx.dim() != 2 or idx.shape[1] != 3:
+        raise ValueError("idx must have shape (n, 3), got %s" % (tuple(idx.shape),))
+    if val.dim() != 1:
+        raise ValueError("val must be one-dimensional, got %s" % (tuple(val.shape),))
+    return min(int(val.numel()), int(idx.shape[0]))
+
+
 class Basis:
     """Device index tables of the SU(N) basis (lb_basis_create)."""
 
@@ -245,8 +268,9 @@ class Basis:
         entries) and val (float64, >= nnz) through the entry point that
         allocates no device memory (N <= 256).  Returns nnz."""
         w = {"f": LB_F, "d": LB_D}[which]
+        cap = export_capacity(idx, val)
         got = _c_i64()
-        _check(load().lb_structure_export_noalloc(self._h, w, _ptr(idx), _ptr(val), int(val.numel()),
+        _check(load().lb_structure_export_noalloc(self._h, w, _ptr(idx), _ptr(val), cap,
                                                   ctypes.byref(got), _stream(stream)))
         return got.value
 

@@ -76,3 +76,47 @@ def test_oracle_and_library_are_independent():
     for f in os.listdir(csrc):
         assert "oracle" not in "".join(re.findall(r'#include\s+[<"](.*?)[>"]', open(os.path.join(csrc, f)).read()))
     assert "#include \"" not in open(os.path.join(ROOT, "oracle", "lb_oracle.c")).read()
+
+
+class _FakeCuda:
+    """Shape, dtype and device of a CUDA tensor, without a GPU."""
+
+    def __init__(self, shape, dtype, contiguous=True):
+        import types
+        self.shape = tuple(shape)
+        self.dtype = dtype
+        self.device = types.SimpleNamespace(type="cuda")
+        self._c = contiguous
+
+    def is_contiguous(self):
+        return self._c
+
+    def dim(self):
+        return len(self.shape)
+
+    def numel(self):
+        n = 1
+        for x in self.shape:
+            n *= x
+        return n
+
+
+def test_export_buffers_checked_before_any_call():
+    """structure_into's capacity is the smaller of the two buffers, and bad
+    buffers raise in Python before the C entry point (and any kernel) runs."""
+    torch = pytest.importorskip("torch")
+    from paper_1912_01491_gb300.native import export_capacity
+    i32, f64 = torch.int32, torch.float64
+    assert export_capacity(_FakeCuda((10, 3), i32), _FakeCuda((12,), f64)) == 10
+    assert export_capacity(_FakeCuda((12, 3), i32), _FakeCuda((7,), f64)) == 7
+    bad = [
+        (torch.zeros((4, 3), dtype=i32), torch.zeros(4, dtype=f64)),          # host tensors
+        (_FakeCuda((4, 3), torch.int64), _FakeCuda((4,), f64)),                # wrong idx type
+        (_FakeCuda((4, 3), i32), _FakeCuda((4,), torch.float32)),              # wrong val type
+        (_FakeCuda((12,), i32), _FakeCuda((4,), f64)),                         # flat idx
+        (_FakeCuda((4, 3), i32, contiguous=False), _FakeCuda((4,), f64)),      # strided
+        (_FakeCuda((4, 3), i32), _FakeCuda((2, 2), f64)),                      # 2-D val
+    ]
+    for idx, val in bad:
+        with pytest.raises(ValueError):
+            export_capacity(idx, val)

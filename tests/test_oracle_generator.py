@@ -304,3 +304,86 @@ def test_ladder_pattern_counts(N):
         nz = np.nonzero(np.abs(l) > 0)[0]
         rp, col, val, K = lowrank_csr(o, h.real, [g], [(nz, l[nz])])
     assert rp[-1] == 7 * N * N - 11 * N + 1
+
+
+def _csr_from_dense(A):
+    """CSR arrays of the nonzero entries of a dense matrix (columns sorted)."""
+    M = A.shape[0]
+    rowptr = np.zeros(M + 1, np.int64)
+    cols, vals = [], []
+    for s in range(M):
+        nz = np.nonzero(A[s])[0]
+        rowptr[s + 1] = rowptr[s] + len(nz)
+        cols.append(nz)
+        vals.append(A[s, nz])
+    return rowptr, np.concatenate(cols).astype(np.int32), np.concatenate(vals)
+
+
+def test_rk4_csr_fourth_order_against_expm():
+    """The CSR RK4 of the oracle converges to the exact affine propagator at
+    order 4 (Sec. 4 item 3, classical RK4): a wrong stage weight or a dropped
+    K lowers the order or leaves an O(1) error.  The system is a random
+    Lindbladian with its zero entries removed (so K != 0 enters every stage)."""
+    from oracle import rk4_csr
+    N = 4
+    H, a = _random_case(N, 13)
+    with Oracle(N) as o:
+        Q, R, K = _oracle_system(o, H, a)
+        v0 = o.expand(wl.pure_state(N, 1))[0].real
+    A = Q + R
+    A[np.abs(A) < 1e-3 * np.abs(A).max()] = 0.0   # a genuinely sparse pattern
+    assert np.abs(K).max() > 1e-3
+    rp, col, val = _csr_from_dense(A)
+    assert rp[-1] < A.size
+    T = 1.0
+    ref = _exact(A, K, v0, T)
+    errs = []
+    for steps in (40, 80, 160):
+        v = rk4_csr(rp, col, val, K, v0, T / steps, steps)
+        errs.append(np.abs(v - ref).max())
+    assert errs[2] < 1e-7
+    assert errs[0] / errs[1] > 14 and errs[1] / errs[2] > 14
+    # K = None means K = 0: the exact solution of v' = A v
+    v = rk4_csr(rp, col, val, None, v0, T / 160, 160)
+    assert np.abs(v - _exact(A, np.zeros_like(K), v0, T)).max() < 1e-7
+
+
+def test_rk4_csr_ladder_death_process():
+    """Ladder model with diagonal H, assembled as CSR by the oracle's sparse
+    route and integrated by its CSR RK4: populations follow the exact binomial
+    death process p_n(t) = C(n0,n) e^{-g n t} (1 - e^{-g t})^{n0-n}."""
+    from oracle import lowrank_csr, rk4_csr
+    N = 6
+    H, L, g = wl.ladder_model(N, 3)
+    H = np.diag(np.diag(H))
+    n0 = N - 1
+    with Oracle(N) as o:
+        h, _ = o.expand(H)
+        l, _ = o.expand(L)
+        nz = np.nonzero(np.abs(l) > 0)[0]
+        rp, col, val, K = lowrank_csr(o, h.real, [g], [(nz, l[nz])])
+        v0 = o.expand(wl.pure_state(N, n0))[0].real
+        T = 3.0
+        v = rk4_csr(rp, col, val, K, v0, 1e-3, 3000)
+        p = np.diag(o.rho(v)).real
+    e = math.exp(-g * T)
+    ref = np.array([math.comb(n0, n) * e**n * (1 - e) ** (n0 - n) for n in range(N)])
+    assert np.abs(p - ref).max() < 1e-11
+
+
+def test_rk4_csr_equals_rk4_dense():
+    """Same system through the dense and the CSR RK4 of the oracle: the same
+    sums in the same column order, so they agree to rounding."""
+    from oracle import lowrank_csr, rk4_csr
+    N = 6
+    H, L, g = wl.ladder_model(N, 5)
+    with Oracle(N) as o:
+        h, _ = o.expand(H)
+        l, _ = o.expand(L)
+        nz = np.nonzero(np.abs(l) > 0)[0]
+        rp, col, val, K = lowrank_csr(o, h.real, [g], [(nz, l[nz])])
+        v0 = o.expand(wl.pure_state(N, 2))[0].real
+    D, _ = _dense_from_csr(rp, col, val, len(v0))
+    vd, _ = rk4_dense(D, K, v0, 1e-3, 500)
+    vc = rk4_csr(rp, col, val, K, v0, 1e-3, 500)
+    assert np.linalg.norm(vc - vd) <= 1e-14 * np.linalg.norm(vd)
