@@ -57,6 +57,7 @@ def load_library():
         lib.ora_rho.argtypes = [ctypes.c_void_p, _dp, _dp]
         lib.ora_Q.argtypes = [ctypes.c_void_p, _dp, _dp]
         lib.ora_K.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
+        lib.ora_K_on_f.argtypes = [ctypes.c_void_p, _dp, _dp]
         lib.ora_join_terms.restype = _i64
         lib.ora_join_terms.argtypes = [ctypes.c_void_p]
         lib.ora_R.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
@@ -204,6 +205,16 @@ class Oracle:
         Ki = np.zeros(self.M)
         self.lib.ora_K(self._ctx, _p(af), _p(K), _p(Ki))
         return (K, Ki) if return_imag else K
+
+    def K_on_f(self, ima):
+        """Eq. (08) from Im a_jk given only on the pairs (j, k) it reads:
+        ima[r] belongs to the r-th row (j, k, s) of structure("f", ordered=True)."""
+        ima = np.ascontiguousarray(ima, np.float64)
+        if ima.shape != (self.nnz("f", ordered=True),):
+            raise ValueError("ima must hold one value per ordered nonzero f")
+        K = np.zeros(self.M)
+        self.lib.ora_K_on_f(self._ctx, _p(ima), _p(K))
+        return K
 
     def R(self, a, return_imag=False, return_scale=False):
         a, af = _c128(a)

@@ -468,6 +468,20 @@ void ora_K(const ora_ctx *c, const double *a, double *K, double *Kimag) {
     free(sr); free(si);
 }
 
+/* Eq. (08) with a given only where the sum reads it: ima[r] = Im a_jk for the
+ * r-th ordered nonzero f_jks, in the order of ora_export_ordered.  For
+ * Hermitian a, K_s = -(1/N) sum_jk Im(a_jk) f_jks (the real part of the
+ * sum drops out, as in ora_K). */
+void ora_K_on_f(const ora_ctx *c, const double *ima, double *K) {
+    int64_t M = c->M;
+    for (int64_t s = 0; s < M; ++s) K[s] = 0.0;
+    for (int64_t r = 0; r < c->nf; ++r) {
+        int32_t s = c->f_idx[3 * r + 2];
+        K[s] += ima[r] * c->f_val[r];
+    }
+    for (int64_t s = 0; s < M; ++s) K[s] = -K[s] / c->N;
+}
+
 /* Lists grouped by the middle index l: F-section (k,s,f_kls) and
  * Z-section (j,n,z_jln); f and d never share a position, so z items are
  * either (f,0) or (0,d). */

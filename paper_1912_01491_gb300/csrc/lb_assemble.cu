@@ -1336,64 +1336,144 @@ __device__ __forceinline__ void dd_wv(const BasisView& B, const AView& A, int x,
   V = ldA(A, p, B.P + p).y;
 }
 
-// Row k of G into Gm (N x N, row-major): off-diagonal G[k][j] = -W_kj + 2 V_kj
-// (k < j) or -W_jk - 2 V_jk (k > j); the diagonal is the row sum of
-// W_kj + 2 K_kj over j != k (K_kj = V_kj for k < j, -V_jk for k > j).
-// One block per row.
-__global__ void __launch_bounds__(128) k_dd_g(BasisView B, AView A, double* __restrict__ Gm) {
-  __shared__ double red[4];
-  const int N = B.N;
-  const int k = blockIdx.x;
-  double diag = 0.0;
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    if (j == k) continue;
-    double W, V;
-    dd_wv(B, A, imin(k, j), imax(k, j), W, V);
-    const double kv = k < j ? V : -V;
-    Gm[(int64_t)k * N + j] = 2.0 * kv - W;
-    diag += W + 2.0 * kv;
+// The diagonal x diagonal block, R[D_nu][D_mu] = -1/2 sum_{x<y} g_xy(nu)
+// (g_xy(mu) W_xy + 2 h_xy(mu) V_xy), by cells of constant coefficient.  The
+// vertices split at lo = min(nu, mu) and hi = max(nu, mu) into the classes
+// [0, lo), {lo}, (lo, hi), {hi}, (hi, N); g_xy(l) and h_xy(l) depend only on
+// the classes of x and y (delta_x(l) is c_l below l, -l c_l at l, 0 above),
+// and g_xy(nu) != 0 needs x <= nu <= y, so every pair whose coefficient is
+// not zero lies in a cell (class of x) x (class of y) with x's class before
+// y's.  A cell's sum of W (or V) comes from tables of sums of terms that
+// all enter the entry: a point, a column prefix sum_{x<a} X_xy, a row range
+// from row suffixes RS[x][b] = sum_{y>=b, y>x} X_xy, or a corner range from
+// C[a][b] = sum_{x<a, y>=b, x<y} X_xy.  No cell sums pairs whose coefficient
+// is zero, so no such terms are added and cancelled (the prefix form
+// d_nu^T G d_mu over all pairs would cancel them only up to rounding,
+// relative to their own size).  O(N^2) tables, O(1) per entry.
+struct DDTables {
+  double *W, *V;      // [N][N], x < y
+  double *RSW, *RSV;  // [N][N + 1]
+  double *CPW, *CPV;  // [N][N + 1]: CP[y][a] = sum_{x<a, x<y} X_xy
+  double *CW, *CV;    // [N + 1][N + 1]
+  static size_t doubles(int N) { return 2 * (size_t)N * N + 4 * (size_t)N * (N + 1) + 2 * (size_t)(N + 1) * (N + 1); }
+  static DDTables carve(double* base, int N) {
+    DDTables t;
+    const size_t nn = (size_t)N * N, nr = (size_t)N * (N + 1), cc = (size_t)(N + 1) * (N + 1);
+    t.W = base;
+    t.V = t.W + nn;
+    t.RSW = t.V + nn;
+    t.RSV = t.RSW + nr;
+    t.CPW = t.RSV + nr;
+    t.CPV = t.CPW + nr;
+    t.CW = t.CPV + nr;
+    t.CV = t.CW + cc;
+    return t;
   }
-  diag = warp_sum(diag);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = diag;
-  __syncthreads();
-  if (threadIdx.x == 0) Gm[(int64_t)k * N + k] = (red[0] + red[1]) + (red[2] + red[3]);
-}
+};
 
-// Row D_nu of the diagonal x diagonal block of R (Eq. (09)): T = d_nu^T G
-// (a prefix over the rows of G, coalesced across j), then
-// R[D_nu][D_mu] = -1/2 T d_mu (a prefix over j).  One block per nu.
-__global__ void __launch_bounds__(128) k_dd2(BasisView B, const double* __restrict__ Gm, double* __restrict__ Aout,
-                                             double* __restrict__ Qout, double* __restrict__ Rout) {
-  extern __shared__ double dsh[];
-  const int N = B.N;
-  const int64_t M = B.M;
-  const int nu = blockIdx.x + 1;
-  double* T = dsh;       // [N]
-  double* PT = dsh + N;  // [N + 1] prefix of T
-  const double cnu = ld_c(B, nu), dnn = dlt(B, nu, nu);
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    double col = 0.0;
-    for (int k = 0; k < nu; ++k) col += Gm[(int64_t)k * N + j];
-    T[j] = cnu * col + dnn * Gm[(int64_t)nu * N + j];
+// Row x of W and V, and their row suffixes.  One block per x.
+__global__ void __launch_bounds__(128) k_dd_rows(BasisView B, AView A, DDTables T) {
+  const int N = B.N, x = blockIdx.x;
+  for (int y = threadIdx.x; y < N; y += blockDim.x) {
+    double W = 0.0, V = 0.0;
+    if (y > x) dd_wv(B, A, x, y, W, V);
+    T.W[(int64_t)x * N + y] = W;
+    T.V[(int64_t)x * N + y] = V;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 2) {
+    const double* X = (threadIdx.x ? T.V : T.W) + (int64_t)x * N;
+    double* RS = (threadIdx.x ? T.RSV : T.RSW) + (int64_t)x * (N + 1);
     double acc = 0.0;
-    PT[0] = 0.0;
-    for (int j = 0; j < N; ++j) {
-      acc += T[j];
-      PT[j + 1] = acc;
+    RS[N] = 0.0;
+    for (int b = N - 1; b >= 0; --b) {
+      if (b > x) acc += X[b];
+      RS[b] = acc;
     }
   }
-  __syncthreads();
-  for (int mu = 1 + threadIdx.x; mu < N; mu += blockDim.x) {
-    const double acc = ld_c(B, mu) * PT[mu] + dlt(B, mu, mu) * T[mu];
-    const double r = -0.5 * acc;
-    const int64_t o = d_index(B, nu) * M + d_index(B, mu);
-    if (Rout) Rout[o] = r;
-    if (Qout) Qout[o] = 0.0;
-    if (Aout) Aout[o] = r;
+}
+
+// Column prefixes CP[y][a] and corner sums C[a][b] = sum_{x<a} RS[x][b]:
+// thread t < 2N takes column y = t / 2 (W or V), thread t in [2N, 4N + 2)
+// takes corner column b.
+__global__ void __launch_bounds__(128) k_dd_cols(BasisView B, DDTables T) {
+  const int N = B.N;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 2 * N) {
+    const int y = t >> 1, wv = t & 1;
+    const double* X = wv ? T.V : T.W;
+    double* CP = (wv ? T.CPV : T.CPW) + (int64_t)y * (N + 1);
+    double acc = 0.0;
+    CP[0] = 0.0;
+    for (int a = 0; a < N; ++a) {
+      if (a < y) acc += X[(int64_t)a * N + y];
+      CP[a + 1] = acc;
+    }
+  } else if (t < 2 * N + 2 * (N + 1)) {
+    const int u = t - 2 * N, b = u >> 1, wv = u & 1;
+    const double* RS = wv ? T.RSV : T.RSW;
+    double* C = wv ? T.CV : T.CW;
+    double acc = 0.0;
+    C[b] = 0.0;  // a = 0
+    for (int a = 1; a <= N; ++a) {
+      acc += RS[(int64_t)(a - 1) * (N + 1) + b];
+      C[(int64_t)a * (N + 1) + b] = acc;
+    }
   }
+}
+
+// Sum of X over the cell [x0, x1) x [y0, y1) (x1 <= y0) from the tables.
+__device__ __forceinline__ double dd_cell(const double* X, const double* RS, const double* CP, const double* C,
+                                          int N, int x0, int x1, int y0, int y1) {
+  if (x1 - x0 == 1 && y1 - y0 == 1) return X[(int64_t)x0 * N + y0];
+  if (y1 - y0 == 1) return CP[(int64_t)y0 * (N + 1) + x1];  // x0 = 0
+  if (x1 - x0 == 1) return RS[(int64_t)x0 * (N + 1) + y0] - RS[(int64_t)x0 * (N + 1) + y1];
+  return C[(int64_t)x1 * (N + 1) + y0] - C[(int64_t)x1 * (N + 1) + y1];  // x0 = 0
+}
+
+// One thread per entry (nu, mu), nu, mu in 1..N-1.
+__global__ void __launch_bounds__(256) k_dd_cells(BasisView B, DDTables T, double* __restrict__ Aout,
+                                                  double* __restrict__ Qout, double* __restrict__ Rout) {
+  const int N = B.N;
+  const int64_t M = B.M;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)(N - 1) * (N - 1)) return;
+  const int nu = 1 + (int)(e / (N - 1)), mu = 1 + (int)(e % (N - 1));
+  const int lo = imin(nu, mu), hi = imax(nu, mu);
+  int c0[5], c1[5], nc = 0;
+  auto add = [&](int a, int b) {
+    if (b > a) {
+      c0[nc] = a;
+      c1[nc] = b;
+      ++nc;
+    }
+  };
+  add(0, lo);
+  add(lo, lo + 1);
+  if (hi > lo) {
+    add(lo + 1, hi);
+    add(hi, hi + 1);
+  }
+  add(hi + 1, N);
+  double acc = 0.0;
+  for (int i = 0; i < nc; ++i) {
+    const int x = c0[i];
+    const double dxn = dlt(B, x, nu), dxm = dlt(B, x, mu);
+    for (int j = i + 1; j < nc; ++j) {
+      const int y = c0[j];
+      const double g = dxn - dlt(B, y, nu);
+      if (g == 0.0) continue;
+      const double dym = dlt(B, y, mu);
+      const double cw = g * (dxm - dym), cv = 2.0 * g * (dxm + dym);
+      if (cw != 0.0) acc = fma(cw, dd_cell(T.W, T.RSW, T.CPW, T.CW, N, c0[i], c1[i], c0[j], c1[j]), acc);
+      if (cv != 0.0) acc = fma(cv, dd_cell(T.V, T.RSV, T.CPV, T.CV, N, c0[i], c1[i], c0[j], c1[j]), acc);
+    }
+  }
+  const double r = -0.5 * acc;
+  const int64_t o = d_index(B, nu) * M + d_index(B, mu);
+  if (Rout) Rout[o] = r;
+  if (Qout) Qout[o] = 0.0;
+  if (Aout) Aout[o] = r;
 }
 
 // H = D X D^T for X = the D x D block of a (real and imaginary parts),
@@ -1656,23 +1736,35 @@ __device__ __forceinline__ double shared_entry_closed(const BasisView& B, const 
 
 // Diagonal row D_nu, pair column n on {p, q} of type tn, in closed form: the
 // l = (v, w) families for v = p and v = q (k = partner(l), j on (v', w)), the
-// l on e(n) itself (j = D_mu), and Q.  Returns (R entry, Q entry).  The
-// families reduce to d_nu^T U - delta_v(nu) sum_w U_w with the prefix arrays
-// PU[tr * 2 + tn] of U_w = sigma_v(w) sum_tl tau_l (sf Re a - sd Im a) built
-// by k_shared_closed (see there).
+// l on e(n) itself (j = D_mu), and Q.  Returns (R entry, Q entry).  A family
+// is sum_w (delta_w(nu) - delta_v(nu)) U_w with U_w = sigma_v(w) sum_tl
+// tau_l (sf Re a - sd Im a), built by k_shared_closed (see there) as raw
+// values RU, prefix sums PU (PU[k] = sum_{w<k}) and suffix sums SU (SU[k] =
+// sum_{w>=k}).  The coefficient delta_w(nu) - delta_v(nu) is c_nu times an
+// integer that is constant on w < nu, w = nu and w > nu and vanishes on one
+// of these ranges, so the family is formed from the two ranges whose terms
+// enter Eq. (09), never as a total minus terms that do not (those would
+// cancel only up to rounding, relative to their own size):
+//   v < nu:  -c_nu ((nu + 1) U_nu + SU[nu + 1])
+//   v = nu:   c_nu ((nu + 1) PU[nu] + nu SU[nu + 1])      (U_v = 0)
+//   v > nu:   c_nu (PU[nu] - nu U_nu)
 __device__ __forceinline__ void dp_entry_closed(const BasisView& B, const PairStage& S, const double* PU,
-                                                const double* h, int p, int q, int nu, int tn, double& r,
-                                                double& qout) {
+                                                const double* RU, const double* SU, const double* h, int p,
+                                                int q, int nu, int tn, double& r, double& qout) {
   const int N = B.N;
   const int64_t P = B.P;
   const int L = S.L;
-  const double cnu = ld_c(B, nu), dnn = dlt(B, nu, nu);
+  const double cnu = ld_c(B, nu), fnu = (double)nu;
   double acc2 = 0.0;
 #pragma unroll
   for (int tr = 0; tr < 2; ++tr) {
-    const double* U = PU + (tr * 2 + tn) * L;
-    const double dv = dlt(B, tr ? q : p, nu);
-    acc2 += cnu * U[nu] + dnn * (U[nu + 1] - U[nu]) - dv * U[N];
+    const int o = (tr * 2 + tn) * L;
+    const int v = tr ? q : p;
+    double fam;
+    if (v < nu) fam = -((fnu + 1.0) * RU[o + nu] + SU[o + nu + 1]);
+    else if (v == nu) fam = (fnu + 1.0) * PU[o + nu] + fnu * SU[o + nu + 1];
+    else fam = PU[o + nu] - fnu * RU[o + nu];
+    acc2 = fma(cnu, fam, acc2);
   }
   double acc = acc2 * kInvSqrt2;
   qout = 0.0;
@@ -1713,6 +1805,8 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
   double* PU = sc + 16 * L;  // [4][L]: prefix over w of U for (tr, tn)
   double* DXs = sc + 20 * L;  // [2][L]
   double* DYs = sc + 22 * L;  // [2][L]
+  double* RU = sc + 24 * L;   // [4][L]: U at w (raw)
+  double* SU = sc + 28 * L;   // [4][L]: suffix over w of U
   __shared__ double TOTs[32];
   const int64_t ppq = blockIdx.x;
   for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
@@ -1785,10 +1879,22 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
       if (w > v) u = -u;
     }
     PU[(tr * 2 + tn) * L + w + 1] = u;
+    RU[(tr * 2 + tn) * L + w] = u;
   }
   if (threadIdx.x < 4) PU[threadIdx.x * L] = 0.0;
   __syncthreads();
-  if (threadIdx.x < 4) scan_inplace(PU + threadIdx.x * L, N);
+  if (threadIdx.x < 4) {
+    scan_inplace(PU + threadIdx.x * L, N);
+  } else if (threadIdx.x >= 32 && threadIdx.x < 36) {  // suffix sums, another warp
+    const double* X = RU + (threadIdx.x - 32) * L;
+    double* Y = SU + (threadIdx.x - 32) * L;
+    double acc = 0.0;
+    Y[N] = 0.0;
+    for (int w = N - 1; w >= 0; --w) {
+      acc += X[w];
+      Y[w] = acc;
+    }
+  }
   __syncthreads();
   // pair x pair, edges sharing a vertex: 2 orientations x N vertices v x 4 type pairs
   if (Aout || Rout) {
@@ -1807,7 +1913,7 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
   for (int t = threadIdx.x; t < 2 * (N - 1); t += blockDim.x) {
     const int nu = 1 + (t >> 1), tn = t & 1;
     double r, qv;
-    dp_entry_closed(B, S, PU, h, p, q, nu, tn, r, qv);
+    dp_entry_closed(B, S, PU, RU, SU, h, p, q, nu, tn, r, qv);
     const int64_t o = d_index(B, nu) * M + (tn * P + ppq);
     if (Rout) Rout[o] = r;
     if (Qout) Qout[o] = qv;
@@ -2191,27 +2297,34 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
     note_launch(1);
   }
   mark(4);
-  // closed: stream-ordered scratch for G (diagonal x diagonal) and H (same edge)
+  // closed: stream-ordered scratch for H (same edge), the vertex sums of K's
+  // diagonal rows and the diagonal x diagonal tables
   double* scratch = nullptr;
+  const size_t dd_at = 3 * (size_t)N * N + N;
   if (closed && e == cudaSuccess && (dense_out || K))
-    e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(double) * (3 * (size_t)N * N + N), st);
-  // 4: diagonal x diagonal (closed: d_nu^T G d_mu by prefix sums)
+    e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(double) * (dd_at + DDTables::doubles(N)), st);
+  // 4: diagonal x diagonal (closed: cells of constant coefficient from row,
+  //    column and corner sums)
   if (dense_out && e == cudaSuccess && N >= 2) {
     if (closed) {
-      k_dd_g<<<(unsigned)N, 128, 0, st>>>(B, av, scratch);
-      k_dd2<<<(unsigned)(N - 1), 128, sizeof(double) * (2 * (size_t)N + 1), st>>>(B, scratch, A, Q, R);
-      note_launch(2);
+      const DDTables T = DDTables::carve(scratch + dd_at, N);
+      const int cols = 2 * N + 2 * (N + 1);
+      const int64_t ents = (int64_t)(N - 1) * (N - 1);
+      k_dd_rows<<<(unsigned)N, 128, 0, st>>>(B, av, T);
+      k_dd_cols<<<(unsigned)((cols + 127) / 128), 128, 0, st>>>(B, T);
+      k_dd_cells<<<(unsigned)((ents + 255) / 256), 256, 0, st>>>(B, T, A, Q, R);
+      note_launch(3);
     } else {
       const int64_t dd_warps = (int64_t)(N - 1) * (N - 1);
       k_dd<<<(unsigned)((dd_warps * 32 + 255) / 256), 256, 0, st>>>(B, av, A, Q, R);
+      note_launch(1);
     }
-    note_launch(1);
   }
   mark(5);
   // 5: pair x pair on edges sharing one vertex (adds to R / A); closed: one
   //    block per vertex pair, which also writes the diagonal x pair entries
   if (dense_out && closed && e == cudaSuccess) {
-    const size_t smem = sizeof(double) * 24 * (size_t)(N + 1);
+    const size_t smem = sizeof(double) * 32 * (size_t)(N + 1);
     e = cudaFuncSetAttribute(k_shared_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) k_shared_closed<<<(unsigned)B.P, 256, smem, st>>>(B, av, h, A, Q, R);
     note_launch(1);

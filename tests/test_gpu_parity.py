@@ -300,8 +300,8 @@ def test_dense_assembly_n200_sampled_entries():
     """Dense random Lindbladian N = 200 (M = 39,999) in the launch the benchmark
     times: closed algorithm, A = Q + R written in place, K beside it.  Two full
     rows of A and 3000 random entries in each of four more rows (S, J and D
-    rows) against the oracle's entry-by-entry Eq. (07) + Eq. (09); K is
-    checked in full at N <= 50."""
+    rows) against the oracle's entry-by-entry Eq. (07) + Eq. (09); K in full
+    against the oracle's Eq. (08) over the pairs f reads."""
     N = 200
     M, P = N * N - 1, N * (N - 1) // 2
     lb = lbm()
@@ -319,8 +319,20 @@ def test_dense_assembly_n200_sampled_entries():
     s = np.concatenate([np.repeat(full, M), np.repeat(part, 3000)]).astype(np.int64)
     n = np.concatenate([np.tile(np.arange(M), len(full)), g.integers(0, M, 3000 * len(part))]).astype(np.int64)
     got = A[torch.as_tensor(s, device="cuda"), torch.as_tensor(n, device="cuda")].cpu().numpy()
-    assert np.isfinite(K.cpu().numpy()).all()
+    Kg = K.cpu().numpy()
+    assert np.isfinite(Kg).all()
     del A
+    # K (Eq. (08)) in full: the oracle reads a only where f touches it
+    with Oracle(N) as o:
+        fi, _ = o.structure("f", ordered=True)
+        j = torch.as_tensor(fi[:, 0].astype(np.int64), device="cuda")
+        k = torch.as_tensor(fi[:, 1].astype(np.int64), device="cuda")
+        del fi
+        ima = a.imag[j, k].cpu().numpy()
+        del j, k
+        Kref = o.K_on_f(ima)
+        del ima
+    assert np.abs(Kg - Kref).max() <= 1e-12 * np.abs(Kref).max()
     with Oracle(N) as o:
         need = o.rows_needed(np.unique(s))
         rows = a[torch.as_tensor(need, device="cuda")].cpu().numpy()
@@ -334,3 +346,93 @@ def test_dense_assembly_n200_sampled_entries():
     bad = np.flatnonzero(err > tol)
     assert len(bad) == 0, "%d of %d sampled entries out of tolerance, first (s, n) = (%d, %d)" % (
         len(bad), len(s), s[bad[0]], n[bad[0]])
+
+
+def _edge_scaled_kossakowski(N, seed, exps, zero_frac):
+    """Wishart a = D W D with D diagonal: every basis element of edge (x, y)
+    (its S and J index) is scaled by 2^e(x, y), every D_l by 2^e_l, e drawn
+    from `exps`, and a fraction of the edges and of the D_l by 0.  The three
+    matchings of a vertex quadruple then read a-blocks whose magnitudes
+    differ by up to 2 (max - min) binades, some of them vanish, and the
+    D-section sums mix magnitudes the same way."""
+    W = wl.wishart_kossakowski(N, seed)
+    g = np.random.default_rng(seed + 1)
+    P = N * (N - 1) // 2
+    M = N * N - 1
+    e = g.choice(exps, P).astype(float)
+    eD = g.choice(exps, N - 1).astype(float)
+    d = np.concatenate([2.0 ** e, 2.0 ** e, 2.0 ** eD])
+    zero = g.random(M) < zero_frac
+    d[:P][zero[:P]] = 0.0
+    d[P:2 * P][zero[:P]] = 0.0
+    d[2 * P:][zero[2 * P:]] = 0.0
+    return (d[:, None] * W) * d[None, :]
+
+
+@pytest.mark.parametrize("N,exps,zero_frac", [
+    (12, [-4, 0, 4], 0.0),           # spreads up to 8 binades: fixed-point sums near their limit
+    (13, [-5, 0, 5], 0.0),           # up to 10
+    (12, [-14, 0, 14], 0.0),         # far beyond: the FP64 form
+    (17, [-14, -8, 0, 8, 14], 0.15), # mostly beyond 10 binades, and zero blocks
+    (23, [-8, 0, 8], 0.3),
+    (12, [0], 0.3),                  # equal magnitudes, many zero blocks: entries whose terms all vanish
+])
+def test_closed_assembly_mixed_magnitude_kossakowski(N, exps, zero_frac):
+    """The closed form's disjoint-edge sums take an exact fixed-point path
+    when the values of a vertex quadruple lie within 10 binades of its
+    largest, and FP64 otherwise (and for zero blocks).  Both paths, and the
+    switch between them inside one launch, against the oracle at the
+    per-entry tolerance.  The diagonal rows sum only terms whose Eq. (09)
+    coefficient is not zero, so an entry whose terms all vanish is exactly
+    zero and a small entry beside large ones keeps its relative accuracy."""
+    H = wl.gue_hamiltonian(N, 3300 + N)
+    a = _edge_scaled_kossakowski(N, 3400 + N, exps, zero_frac)
+    with lbm().Basis(N) as B, Oracle(N) as o:
+        g = _gpu_system(B, H, a, "closed")
+        h, _ = o.expand(H)
+        Q = o.Q(h.real)
+        R, S = o.R(a, return_scale=True)
+        K = o.K(a)
+    _assert_entries(g["R"], R, S, "R")
+    _assert_entries(g["A"], Q + R, S + np.abs(Q), "A")
+    assert np.abs(g["K"] - K).max() <= 1e-12 * np.abs(K).max()
+
+
+@pytest.mark.parametrize("N", [12, 19])
+def test_closed_assembly_dense_ladder_kossakowski(N):
+    """The ladder model's rank-one a = g l l^dagger given as a dense matrix:
+    most vertex quadruples read zero blocks beside nonzero ones."""
+    H, L, gam = wl.ladder_model(N, 50 + N)
+    with lbm().Basis(N) as B, Oracle(N) as o:
+        l, _ = o.expand(L)
+        a = gam * np.outer(l, l.conj())
+        g = _gpu_system(B, H, a, "closed")
+        h, _ = o.expand(H)
+        Q = o.Q(h.real)
+        R, S = o.R(a, return_scale=True)
+        K = o.K(a)
+    _assert_entries(g["R"], R, S, "R")
+    _assert_entries(g["A"], Q + R, S + np.abs(Q), "A")
+    assert np.abs(g["K"] - K).max() <= 1e-12 * np.abs(K).max()
+
+
+def test_rk4_fp64_n50_full_trajectory():
+    """Dense N = 50 random Lindbladian (M = 2499), rho0 = |0><0|, 10^4 FP64
+    RK4 steps of dt = 1e-3: every 1000-step snapshot within 1e-12 ||v|| of the
+    oracle's RK4 on the oracle's own A and K."""
+    N, dt, steps, every = 50, 1e-3, 10_000, 1000
+    H, a = _case(N, 1050)
+    lb = lbm()
+    with lb.Basis(N) as B, Oracle(N) as o:
+        A, K = _oracle_system(o, H, a)
+        v0 = o.expand(wl.pure_state(N, 0))[0].real
+        ref_v, ref_snaps = ora_rk4(A, K, v0, dt, steps, snap_every=every)
+        g = B.assemble_dense(torch.tensor(a, device="cuda"),
+                             h=B.expand(torch.tensor(H, device="cuda")).real.contiguous(), algorithm="closed")
+        v = torch.tensor(v0, device="cuda")
+        snaps = lb.rk4_dense(g["A"], g["K"], v, dt, steps, precision="fp64", snap_every=every)
+        torch.cuda.synchronize()
+    snaps = snaps.cpu().numpy()
+    for t in range(len(ref_snaps)):
+        assert np.linalg.norm(snaps[t] - ref_snaps[t]) <= 1e-12 * np.linalg.norm(ref_snaps[t]), t
+    assert np.linalg.norm(v.cpu().numpy() - ref_v) <= 1e-12 * np.linalg.norm(ref_v)

@@ -387,3 +387,18 @@ def test_rk4_csr_equals_rk4_dense():
     vd, _ = rk4_dense(D, K, v0, 1e-3, 500)
     vc = rk4_csr(rp, col, val, K, v0, 1e-3, 500)
     assert np.linalg.norm(vc - vd) <= 1e-14 * np.linalg.norm(vd)
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 7])
+def test_k_on_f_equals_k(N):
+    """Eq. (08) from Im a on the pairs that f touches equals Eq. (08) from the
+    full a (itself pinned by brute force above); a Hermitian a's real part
+    does not enter."""
+    H, a = _random_case(N, 70 + N)
+    with Oracle(N) as o:
+        idx, _ = o.structure("f", ordered=True)
+        K = o.K(a)
+        Kp = o.K_on_f(a.imag[idx[:, 0], idx[:, 1]])
+        with pytest.raises(ValueError):
+            o.K_on_f(np.zeros(3))
+    assert np.abs(Kp - K).max() <= 1e-15 * max(np.abs(K).max(), 1.0)
