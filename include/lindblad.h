@@ -66,6 +66,22 @@ extern "C" {
 #define LB_SYS_R 2
 #define LB_SYS_K 3
 
+/* storage format of an assembled system (lb_assemble) */
+#define LB_DENSE 0
+#define LB_CSR 1
+
+/* kinds of Kossakowski matrix (lb_kossakowski) */
+#define LB_A_DENSE 0
+#define LB_A_LOWRANK 1
+
+/* phases of a host-buffer call (lb_system_timings) */
+#define LB_PHASE_ALLOC 0    /* host wall time of the device allocations (library pool) */
+#define LB_PHASE_H2D 1      /* host -> device copies of the inputs */
+#define LB_PHASE_KERNELS 2  /* expansion of H and assembly kernels */
+#define LB_PHASE_D2H 3      /* device -> host copies (none in lb_assemble) */
+#define LB_PHASE_FREE 4     /* return of the staging buffers to the pool */
+#define LB_PHASES 5
+
 typedef struct lb_basis lb_basis_t;
 typedef struct lb_system lb_system_t;
 
@@ -153,6 +169,13 @@ int lb_expand(const lb_basis_t *b, const double *A, double *coef, void *stream);
 /* Eq. (rho): rho = 1/N + sum_i v_i F_i as an N x N complex matrix (device). */
 int lb_rho(const lb_basis_t *b, const double *v, double *rho, void *stream);
 
+/* lb_expand and lb_rho with host buffers (Table 1 steps 2.1, 2.6, 3.2):
+ * A and rho are N x N complex (interleaved) in host memory, coef is M
+ * complex, v is M doubles.  The device copies come from the library pool
+ * and run on the library stream (see lb_assemble).  Synchronous. */
+int lb_expand_host(const lb_basis_t *b, const double *A, double *coef);
+int lb_rho_host(const lb_basis_t *b, const double *v, double *rho);
+
 /* ------------------------------------------------------------------------
  * a3-a5 -- dense assembly.  Eqs. (07)-(09), Table 1 steps 2.3-2.5.
  * --------------------------------------------------------------------- */
@@ -163,12 +186,12 @@ int lb_rho(const lb_basis_t *b, const double *v, double *rho, void *stream);
  * Outputs (each may be NULL, at least one of A, Q, R must not be):
  *   A = Q + R, Q, R : M x M doubles, row s = equation for dv_s/dt, column n
  *   K : M doubles (Eq. (08))
- * Each R entry is the sum of its join terms over the shared index l
- * (Eq. (09) in the one-term form r_sn = -1/2 Re sum_jkl a_jk z_jln f_kls,
- * identical to the printed two-term form with prefactor -1/4 for Hermitian a;
- * Sec. 4 item 2.5), accumulated in FP64 by the thread or warp that owns the
- * entry (no atomics).  N <= 512 (LB_EINVAL otherwise).  Same as
- * lb_assemble_dense_ex with algorithm = LB_ALG_JOIN. */
+ * R follows Eq. (09) in the one-term form r_sn = -1/2 Re sum_jkl a_jk z_jln
+ * f_kls (identical to the printed two-term form with prefactor -1/4 for
+ * Hermitian a; Sec. 4 item 2.5), accumulated in FP64 by the thread or warp
+ * that owns the entry (no atomics).  N <= 512 (LB_EINVAL otherwise).  Same as
+ * lb_assemble_dense_ex with algorithm = LB_ALG_CLOSED, the fast form; pass
+ * LB_ALG_JOIN there for the term-by-term join. */
 int lb_assemble_dense(const lb_basis_t *b, const double *h, const double *a,
                       double *A, double *Q, double *R, double *K, void *stream);
 
@@ -331,33 +354,92 @@ int lb_batch_destroy(lb_batch_t *b);
 
 /* ------------------------------------------------------------------------
  * Host-buffer interface (one call per paper step, inputs and outputs in
- * host memory, copies included).  The assembled system stays on the device
- * inside an lb_system_t.
+ * host memory, copies included; Table 1 steps 2.1-2.6 and 3.1-3.2).  The
+ * assembled system stays on the device inside an lb_system_t.
+ *
+ * Device memory and ordering: every call runs on one non-blocking library
+ * stream per device and takes its device memory from one library memory
+ * pool per device, which keeps what it has reserved between calls (no
+ * cudaMalloc / cudaFree, and no device-wide synchronization, once a size
+ * has been seen); lb_host_release returns the spare memory.  Calls are
+ * synchronous with respect to the host.  Concurrent calls from several
+ * host threads are correct and run one after another on the library stream.
  * --------------------------------------------------------------------- */
 
-/* Expand H (host N x N complex, may be NULL) and assemble Q, R, K from the
- * host Kossakowski matrix a (M x M complex) with the given algorithm
- * (LB_ALG_JOIN or LB_ALG_CLOSED).  a is Hermitian (the Kossakowski matrix of
- * Eq. (1) is positive semidefinite); for M > 2048 only its upper triangle
- * j <= k is read and the device copy takes a_kj = conj(a_jk) below the
- * diagonal, so half of a crosses the host link.  keep_parts != 0 also keeps
- * Q and R separately.  The device copy of a is freed before returning.  LB_ENOMEM if
- * the device cannot hold a, A (and Q, R): checked against cudaMemGetInfo
- * before any allocation.  Synchronous. */
-int lb_assemble(const lb_basis_t *b, const double *H, const double *a, int keep_parts,
-                int algorithm, lb_system_t **out);
+/* The Kossakowski matrix of an assembly, in the convention of Eqs. (08) and
+ * (09) (see above), either dense or as a sum over channels (Sec. 2: the
+ * dissipator as a sum over jump operators, a_jk = sum_p gamma_p l_pj
+ * conj(l_pk), with l_p the expansion of jump operator L_p, Eq. (02)).
+ * All arrays are host memory, read during the call only. */
+typedef struct lb_kossakowski {
+  int kind;               /* LB_A_DENSE or LB_A_LOWRANK */
+  const double *a;        /* LB_A_DENSE: M x M complex Hermitian (interleaved); for
+                             M > 2048 only its upper triangle j <= k is read */
+  int nP;                 /* LB_A_LOWRANK: number of channels (0 <= nP <= 4096) */
+  const double *gamma;    /* nP rates */
+  const int64_t *lp_ptr;  /* nP + 1 offsets into lp_idx / lp_val, lp_ptr[0] = 0 */
+  const int64_t *lp_idx;  /* basis indices j (0 <= j < M) of the nonzero l_pj */
+  const double *lp_val;   /* the values l_pj, complex interleaved */
+} lb_kossakowski;
+
+/* Expand H (host N x N complex Hermitian, may be NULL for H = 0; Eq. (02))
+ * and assemble A = Q + R and K (Eqs. (07)-(09)) from the Kossakowski matrix
+ * `a` into a new system *out (owned by the caller, released with
+ * lb_system_destroy).
+ *   format = LB_DENSE: A as M x M FP64 (N <= 512), by `algorithm`
+ *     (LB_ALG_CLOSED or LB_ALG_JOIN); keep_parts != 0 also keeps Q and R.  A
+ *     low-rank `a` is first formed as a dense matrix on the device.  The
+ *     Hermitian upper triangle of a dense `a` crosses the host link and the
+ *     lower one is mirrored on the device.
+ *   format = LB_CSR: A in CSR form from a low-rank `a` (the product form of
+ *     lb_assemble_lowrank_csr, same pattern rule); `algorithm` is not used.
+ *     A dense `a` or keep_parts != 0 give LB_EUNSUPPORTED.
+ * LB_ENOMEM if the device cannot hold the dense buffers (checked against
+ * free memory plus the pool's spare memory before any allocation) or an
+ * allocation is refused.  The staging copy of `a` is returned to the pool
+ * before the call returns.  Synchronous. */
+int lb_assemble(const lb_basis_t *b, const double *H, const lb_kossakowski *a, int format, int algorithm,
+                int keep_parts, lb_system_t **out);
 int lb_system_destroy(lb_system_t *sys);
 
+/* Format (LB_DENSE / LB_CSR), M and stored entries (M * M for dense) of a
+ * system; any output pointer may be NULL. */
+int lb_system_info(const lb_system_t *sys, int *format, int64_t *M, int64_t *nnz);
+
+/* Times in ms of the phases of the lb_assemble call that built sys, indexed
+ * by LB_PHASE_* (ms: LB_PHASES doubles).  Device phases are CUDA-event
+ * times on the library stream; LB_PHASE_ALLOC and LB_PHASE_FREE are host
+ * wall times.  Zero for systems from lb_system_load. */
+int lb_system_timings(const lb_system_t *sys, double *ms);
+
 /* Copy one part (LB_SYS_A, _Q, _R: M x M; LB_SYS_K: M) into host memory.
- * LB_EINVAL if the part was not kept. */
+ * LB_EINVAL if the part was not kept (and for A, Q, R of a CSR system). */
 int lb_system_get(const lb_system_t *sys, int part, double *out);
 
-/* RK4 from the host initial state v0 (M doubles) for n = round(t/dt) steps
- * (LB_EINVAL if |n dt - t| > 1e-9 t); the final state goes to v_out (host).
- * precision and correct_every as for lb_rk4_dense; the low-precision copy is
- * made (and cached in the system) on first use.  Synchronous. */
-int lb_integrate(lb_system_t *sys, int precision, int correct_every, const double *v0,
-                 double t, double dt, double *v_out);
+/* CSR arrays of a CSR system into host buffers (any may be NULL): rowptr
+ * (M + 1 int64), col (nnz int32, sorted within rows), val (nnz doubles).
+ * LB_EINVAL for a dense system. */
+int lb_system_get_csr(const lb_system_t *sys, int64_t *rowptr, int32_t *col, double *val);
+
+/* Classical RK4 (Sec. 4 item 3) from the host initial state v0 (M doubles)
+ * for n = round(t/dt) steps (LB_EINVAL if |n dt - t| > 1e-9 t).
+ *   snap_every = 0: v_out (host, M doubles) receives the final state.
+ *   snap_every > 0: n must be a multiple of it (else LB_EINVAL); v_out
+ *     (host, (n / snap_every) x M doubles) receives the state after every
+ *     snap_every steps, row i after (i + 1) snap_every steps, so the last row
+ *     is the final state.
+ * Dense systems: precision LB_FP64, LB_FP32 or LB_BF16 with correct_every as
+ * for lb_rk4_dense; the low-precision copy is made (and cached in the
+ * system) on first use.  CSR systems: LB_FP64 or LB_FP32 as for lb_rk4_csr;
+ * with LB_FP32 and correct_every > 0, snap_every must be a multiple of
+ * correct_every (the correction restarts at every snapshot).  Synchronous. */
+int lb_integrate(lb_system_t *sys, int precision, int correct_every, const double *v0, double t, double dt,
+                 int64_t snap_every, double *v_out);
+
+/* Return the spare device memory of the library pool of the current device
+ * (after the library stream has finished).  The next host-buffer call
+ * reserves again what it needs. */
+int lb_host_release(void);
 
 /* Checkpoint and resume.  There is no counterpart in the paper; it serves
  * long integrations that are stopped and continued.

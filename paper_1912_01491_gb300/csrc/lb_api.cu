@@ -7,8 +7,11 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <new>
 #include <vector>
 #include <cub/cub.cuh>
 #include <string>
@@ -91,9 +94,13 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 }  // namespace lbi
 
+// An assembled system of the host-buffer interface.  Dense systems hold A
+// (and Q, R if kept) as M x M FP64 in memory of the library pool, returned
+// to it (stream-ordered) on destruction; CSR systems hold A = Q + R in csr.
 struct lb_system {
   const lb_basis* basis = nullptr;
   int64_t M = 0;
+  int format = LB_DENSE;
   double* A = nullptr;
   double* Q = nullptr;
   double* R = nullptr;
@@ -101,13 +108,16 @@ struct lb_system {
   float* A32 = nullptr;
   uint16_t* Abf = nullptr;
   float* scale = nullptr;
+  lbi::CsrOut csr;               // LB_CSR: rowptr, col, val, K (K aliases csr.K)
+  float* csr32 = nullptr;        // FP32 copy of csr.val, made on first use
+  double ms[LB_PHASES] = {};     // phase times of the call that built it
 };
 
 extern "C" {
 
 const char* lb_last_error(void) { return g_err.c_str(); }
 
-int lb_version(void) { return 100; }
+int lb_version(void) { return 200; }
 
 int lb_basis_create(int N, void* stream, lb_basis_t** out) {
   LB_REQUIRE(out != nullptr, "lb_basis_create: out is NULL");
@@ -273,7 +283,7 @@ int lb_assemble_dense_ex(const lb_basis_t* b, const double* h, const double* a, 
 
 int lb_assemble_dense(const lb_basis_t* b, const double* h, const double* a, double* A, double* Q,
                       double* R, double* K, void* stream) {
-  return lb_assemble_dense_ex(b, h, a, A, Q, R, K, LB_ALG_JOIN, stream);
+  return lb_assemble_dense_ex(b, h, a, A, Q, R, K, LB_ALG_CLOSED, stream);
 }
 
 int lb_assemble_kernel_count(void) { return lbi::kAssembleKernels; }
@@ -438,71 +448,387 @@ int lb_rk4_csr(const lb_csr_t* c, int precision, int correct_every, double* v, d
   return LB_OK;
 }
 
+}  // extern "C"
+
 // ------------------------------------------------------------------ host API
 
-int lb_assemble(const lb_basis_t* b, const double* H, const double* a, int keep_parts, int algorithm,
-                lb_system_t** out) {
+namespace {
+
+// Per-device stream and memory pool of the host-buffer interface.  The pool
+// keeps what it has reserved (release threshold: unlimited) so that repeated
+// calls of the same size reuse device memory without cudaMalloc / cudaFree
+// (a cudaFree synchronizes the whole device); lb_host_release hands it back.
+struct HostCtx {
+  cudaStream_t st = nullptr;
+  cudaMemPool_t pool = nullptr;
+};
+std::mutex g_host_mu;
+std::vector<HostCtx> g_host;
+
+cudaError_t host_ctx(HostCtx* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_host_mu);
+  if ((int)g_host.size() <= dev) g_host.resize(dev + 1);
+  HostCtx& c = g_host[dev];
+  if (!c.st) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if ((e = cudaMemPoolCreate(&c.pool, &props)) != cudaSuccess) return e;
+    uint64_t keep = ~0ull;
+    if ((e = cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
+    if ((e = cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking)) != cudaSuccess) {
+      c.st = nullptr;
+      return e;
+    }
+  }
+  *out = c;
+  return cudaSuccess;
+}
+
+// Bytes the pool holds but no allocation uses: free for the next call.
+size_t pool_spare(cudaMemPool_t pool) {
+  uint64_t reserved = 0, used = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess) return 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) return 0;
+  return reserved > used ? (size_t)(reserved - used) : 0;
+}
+
+// Stream-ordered pool allocation on the library stream (freed with pool_free).
+struct PoolBuf {
+  void* p = nullptr;
+  cudaStream_t st = nullptr;
+  PoolBuf() = default;
+  PoolBuf(const PoolBuf&) = delete;
+  PoolBuf& operator=(const PoolBuf&) = delete;
+  ~PoolBuf() {
+    if (p) cudaFreeAsync(p, st);
+  }
+  int alloc(const HostCtx& c, size_t n, const char* what) {
+    st = c.st;
+    const cudaError_t e = cudaMallocFromPoolAsync(&p, n ? n : 1, c.pool, c.st);
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      p = nullptr;
+      lbi::set_error("device allocation of %zu bytes for %s refused", n, what);
+      return LB_ENOMEM;
+    }
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return lbi::cuda_fail(e, what);
+    }
+    return LB_OK;
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+  void* release() {
+    void* q = p;
+    p = nullptr;
+    return q;
+  }
+  void free_now() {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+  }
+};
+
+// Events around the phases of one call on the library stream.
+struct PhaseClock {
+  cudaEvent_t ev[LB_PHASES + 1] = {};
+  bool ok = true;
+  explicit PhaseClock(cudaStream_t st) : st_(st) {
+    for (auto& e : ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+  }
+  ~PhaseClock() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  void mark(int i) {
+    if (ok) ok = cudaEventRecord(ev[i], st_) == cudaSuccess;
+  }
+  // ms[i] = time from mark i to mark i + 1 (marks not recorded count as 0)
+  void read(double* ms, int from, int to) {
+    for (int i = from; i < to; ++i) {
+      float t = 0.f;
+      ms[i] = (ok && cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) ? t : 0.0;
+    }
+    cudaGetLastError();
+  }
+
+ private:
+  cudaStream_t st_;
+};
+
+// a_jk = sum_p gamma_p l_pj conj(l_pk) for one channel p, added onto a dense
+// M x M complex matrix: one thread per pair of the channel's nonzeros, so
+// each entry is touched once per channel.
+__global__ void k_lowrank_add(int64_t M, int n, const int64_t* __restrict__ idx, const double2* __restrict__ val,
+                              double gamma, double2* __restrict__ a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  const double2 x = val[i], y = val[j];
+  double2* o = a + idx[i] * M + idx[j];
+  o->x += gamma * (x.x * y.x + x.y * y.y);
+  o->y += gamma * (x.y * y.x - x.x * y.y);
+}
+
+// h_m = Re coef_m (stride-2 copy of the real parts), on st
+cudaError_t real_part(const double2* coef, double* h, int64_t M, cudaStream_t st) {
+  return cudaMemcpy2DAsync(h, sizeof(double), coef, 2 * sizeof(double), sizeof(double), (size_t)M,
+                           cudaMemcpyDeviceToDevice, st);
+}
+
+void pool_free(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_host_release(void) {
+  HostCtx c;
+  LB_TRY_CUDA(host_ctx(&c), "lb_host_release");
+  LB_TRY_CUDA(cudaStreamSynchronize(c.st), "lb_host_release");
+  LB_TRY_CUDA(cudaMemPoolTrimTo(c.pool, 0), "lb_host_release");
+  return LB_OK;
+}
+
+int lb_expand_host(const lb_basis_t* b, const double* A, double* coef) {
+  LB_REQUIRE(b && A && coef, "lb_expand_host: NULL argument");
+  HostCtx c;
+  LB_TRY_CUDA(host_ctx(&c), "lb_expand_host");
+  const size_t nn = (size_t)b->N * b->N;
+  PoolBuf dA, dc;
+  int rc;
+  if ((rc = dA.alloc(c, 16 * nn, "A")) != LB_OK || (rc = dc.alloc(c, 16 * (size_t)b->M, "coef")) != LB_OK) return rc;
+  LB_TRY_CUDA(cudaMemcpyAsync(dA.p, A, 16 * nn, cudaMemcpyHostToDevice, c.st), "lb_expand_host: copy A");
+  LB_TRY_CUDA(lbi::expand(b->view(), dA.as<double2>(), dc.as<double2>(), c.st), "lb_expand_host");
+  LB_TRY_CUDA(cudaMemcpyAsync(coef, dc.p, 16 * (size_t)b->M, cudaMemcpyDeviceToHost, c.st), "lb_expand_host: copy");
+  LB_TRY_CUDA(cudaStreamSynchronize(c.st), "lb_expand_host");
+  return LB_OK;
+}
+
+int lb_rho_host(const lb_basis_t* b, const double* v, double* rho) {
+  LB_REQUIRE(b && v && rho, "lb_rho_host: NULL argument");
+  HostCtx c;
+  LB_TRY_CUDA(host_ctx(&c), "lb_rho_host");
+  const size_t nn = (size_t)b->N * b->N;
+  PoolBuf dv, dr;
+  int rc;
+  if ((rc = dv.alloc(c, 8 * (size_t)b->M, "v")) != LB_OK || (rc = dr.alloc(c, 16 * nn, "rho")) != LB_OK) return rc;
+  LB_TRY_CUDA(cudaMemcpyAsync(dv.p, v, 8 * (size_t)b->M, cudaMemcpyHostToDevice, c.st), "lb_rho_host: copy v");
+  LB_TRY_CUDA(lbi::rho(b->view(), dv.as<double>(), dr.as<double2>(), c.st), "lb_rho_host");
+  LB_TRY_CUDA(cudaMemcpyAsync(rho, dr.p, 16 * nn, cudaMemcpyDeviceToHost, c.st), "lb_rho_host: copy");
+  LB_TRY_CUDA(cudaStreamSynchronize(c.st), "lb_rho_host");
+  return LB_OK;
+}
+
+int lb_assemble(const lb_basis_t* b, const double* H, const lb_kossakowski* a, int format, int algorithm,
+                int keep_parts, lb_system_t** out) {
   LB_REQUIRE(b && a && out, "lb_assemble: NULL argument");
-  LB_REQUIRE(b->N <= lbi::kMaxDenseN, "lb_assemble: N = %d above %d", b->N, lbi::kMaxDenseN);
-  LB_REQUIRE(algorithm == LB_ALG_JOIN || algorithm == LB_ALG_CLOSED, "lb_assemble: algorithm = %d", algorithm);
   *out = nullptr;
+  LB_REQUIRE(a->kind == LB_A_DENSE || a->kind == LB_A_LOWRANK, "lb_assemble: Kossakowski kind = %d", a->kind);
+  LB_REQUIRE(format == LB_DENSE || format == LB_CSR, "lb_assemble: format = %d", format);
+  LB_REQUIRE(algorithm == LB_ALG_JOIN || algorithm == LB_ALG_CLOSED, "lb_assemble: algorithm = %d", algorithm);
+  if (a->kind == LB_A_DENSE) LB_REQUIRE(a->a != nullptr, "lb_assemble: dense Kossakowski matrix is NULL");
+  if (a->kind == LB_A_LOWRANK) {
+    LB_REQUIRE(a->nP >= 0 && a->nP <= 4096, "lb_assemble: nP = %d", a->nP);
+    LB_REQUIRE(a->nP == 0 || (a->gamma && a->lp_ptr), "lb_assemble: NULL channel arrays");
+    LB_REQUIRE(a->nP == 0 || a->lp_ptr[0] == 0, "lb_assemble: lp_ptr[0] must be 0");
+    for (int p = 0; p < a->nP; ++p) {
+      LB_REQUIRE(a->lp_ptr[p + 1] >= a->lp_ptr[p], "lb_assemble: lp_ptr not monotone");
+      LB_REQUIRE(std::isfinite(a->gamma[p]), "lb_assemble: gamma[%d] not finite", p);
+    }
+    const int64_t nl = a->nP ? a->lp_ptr[a->nP] : 0;
+    LB_REQUIRE(nl == 0 || (a->lp_idx && a->lp_val), "lb_assemble: NULL channel arrays");
+    for (int64_t i = 0; i < nl; ++i)
+      LB_REQUIRE(a->lp_idx[i] >= 0 && a->lp_idx[i] < b->M, "lb_assemble: lp_idx[%lld] out of range",
+                 (long long)i);
+  }
+  if (format == LB_CSR) {
+    if (a->kind == LB_A_DENSE) {
+      lbi::set_error("lb_assemble: a CSR system needs a low-rank Kossakowski matrix (the sparse pattern keeps an "
+                     "entry by the size of its terms, which the dense kernels do not form)");
+      return LB_EUNSUPPORTED;
+    }
+    if (keep_parts) {
+      lbi::set_error("lb_assemble: Q and R are not kept separately in a CSR system");
+      return LB_EUNSUPPORTED;
+    }
+    LB_REQUIRE(b->M <= 0x7fffffffLL, "lb_assemble: M too large for int32 columns");
+  } else {
+    LB_REQUIRE(b->N <= lbi::kMaxDenseN, "lb_assemble: N = %d above %d for a dense system", b->N, lbi::kMaxDenseN);
+  }
+  HostCtx c;
+  LB_TRY_CUDA(host_ctx(&c), "lb_assemble: library stream");
   const int64_t M = b->M, N = b->N;
   const size_t mm = (size_t)M * (size_t)M;
-  size_t need = 16 * mm + 8 * mm * (keep_parts ? 3 : 1) + 64 * (size_t)M;
-  size_t fr = 0, tot = 0;
-  LB_TRY_CUDA(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
-  if (need > fr) {
-    lbi::set_error("lb_assemble: needs %zu bytes of device memory, %zu free", need, fr);
-    return LB_ENOMEM;
-  }
+  lb_system* sys = new lb_system;
+  sys->basis = b;
+  sys->M = M;
+  sys->format = format;
+  auto fail = [&](int rc) {
+    lb_system_destroy(sys);
+    return rc;
+  };
+  PhaseClock clk(c.st);
+  const auto t0 = std::chrono::steady_clock::now();
   int rc;
-  DevBuf da, dA, dQ, dR, dK, dH, dcoef, dh;
-  if ((rc = alloc_or_enomem(da, 16 * mm, "a")) != LB_OK) return rc;
-  if ((rc = alloc_or_enomem(dA, 8 * mm, "A")) != LB_OK) return rc;
-  if ((rc = alloc_or_enomem(dK, 8 * (size_t)M, "K")) != LB_OK) return rc;
-  if (keep_parts) {
-    if ((rc = alloc_or_enomem(dQ, 8 * mm, "Q")) != LB_OK) return rc;
-    if ((rc = alloc_or_enomem(dR, 8 * mm, "R")) != LB_OK) return rc;
+  // device memory (admission against what is free plus what the pool holds spare)
+  PoolBuf da, dH, dcoef, dh, dli, dlv;
+  const int64_t nl = (a->kind == LB_A_LOWRANK && a->nP) ? a->lp_ptr[a->nP] : 0;
+  if (format == LB_DENSE) {
+    const size_t need = 16 * mm + 8 * mm * (keep_parts ? 3 : 1) + 64 * (size_t)M;
+    size_t fr = 0, tot = 0;
+    LB_TRY_CUDA(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+    fr += pool_spare(c.pool);
+    if (need > fr) {
+      delete sys;
+      lbi::set_error("lb_assemble: needs %zu bytes of device memory, %zu free", need, fr);
+      return LB_ENOMEM;
+    }
+    PoolBuf dA, dQ, dR, dK;
+    if ((rc = da.alloc(c, 16 * mm, "a")) != LB_OK || (rc = dA.alloc(c, 8 * mm, "A")) != LB_OK ||
+        (rc = dK.alloc(c, 8 * (size_t)M, "K")) != LB_OK ||
+        (keep_parts && ((rc = dQ.alloc(c, 8 * mm, "Q")) != LB_OK || (rc = dR.alloc(c, 8 * mm, "R")) != LB_OK)))
+      return fail(rc);
+    sys->A = dA.as<double>();
+    sys->K = dK.as<double>();
+    sys->Q = dQ.as<double>();
+    sys->R = dR.as<double>();
+    dA.release();
+    dK.release();
+    dQ.release();
+    dR.release();
   }
-  LB_TRY_CUDA(lbi::upload_hermitian(reinterpret_cast<const double2*>(a), da.as<double2>(), M, nullptr), "copy a");
+  if (nl > 0) {
+    if ((rc = dli.alloc(c, 8 * (size_t)nl, "channel indices")) != LB_OK ||
+        (rc = dlv.alloc(c, 16 * (size_t)nl, "channel values")) != LB_OK)
+      return fail(rc);
+  }
   if (H) {
-    if ((rc = alloc_or_enomem(dH, 16 * (size_t)N * N, "H")) != LB_OK) return rc;
-    if ((rc = alloc_or_enomem(dcoef, 16 * (size_t)M, "h")) != LB_OK) return rc;
-    if ((rc = alloc_or_enomem(dh, 8 * (size_t)M, "h")) != LB_OK) return rc;
-    LB_TRY_CUDA(cudaMemcpy(dH.p, H, 16 * (size_t)N * N, cudaMemcpyHostToDevice), "copy H");
-    LB_TRY_CUDA(lbi::expand(b->view(), dH.as<double2>(), dcoef.as<double2>(), nullptr), "expand H");
-    // h_m = Re coef_m (strided copy of the real parts)
-    LB_TRY_CUDA(cudaMemcpy2D(dh.p, sizeof(double), dcoef.p, 2 * sizeof(double), sizeof(double), (size_t)M,
-                             cudaMemcpyDeviceToDevice),
-                "real part of h");
+    if ((rc = dH.alloc(c, 16 * (size_t)N * N, "H")) != LB_OK || (rc = dcoef.alloc(c, 16 * (size_t)M, "coef")) != LB_OK ||
+        (rc = dh.alloc(c, 8 * (size_t)M, "h")) != LB_OK)
+      return fail(rc);
   }
-  LB_TRY_CUDA(lbi::assemble_dense(b->view(), H ? dh.as<double>() : nullptr, da.as<double2>(), dA.as<double>(),
-                                  dQ.as<double>(), dR.as<double>(), dK.as<double>(), algorithm, nullptr),
-              "assemble");
-  LB_TRY_CUDA(cudaDeviceSynchronize(), "assemble");
-  lb_system* s = new lb_system;
-  s->basis = b;
-  s->M = M;
-  s->A = static_cast<double*>(dA.release());
-  s->K = static_cast<double*>(dK.release());
-  s->Q = static_cast<double*>(dQ.release());
-  s->R = static_cast<double*>(dR.release());
-  *out = s;
+  sys->ms[LB_PHASE_ALLOC] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  // inputs to the device
+  clk.mark(LB_PHASE_H2D);
+  cudaError_t e = cudaSuccess;
+  if (H) e = cudaMemcpyAsync(dH.p, H, 16 * (size_t)N * N, cudaMemcpyHostToDevice, c.st);
+  if (e == cudaSuccess && nl > 0) {
+    e = cudaMemcpyAsync(dli.p, a->lp_idx, 8 * (size_t)nl, cudaMemcpyHostToDevice, c.st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dlv.p, a->lp_val, 16 * (size_t)nl, cudaMemcpyHostToDevice, c.st);
+  }
+  if (e == cudaSuccess && format == LB_DENSE && a->kind == LB_A_DENSE)
+    e = lbi::upload_hermitian(reinterpret_cast<const double2*>(a->a), da.as<double2>(), M, c.st);
+  if (e != cudaSuccess) return fail(lbi::cuda_fail(e, "lb_assemble: copy inputs"));
+  // kernels
+  clk.mark(LB_PHASE_KERNELS);
+  if (H) {
+    e = lbi::expand(b->view(), dH.as<double2>(), dcoef.as<double2>(), c.st);
+    if (e == cudaSuccess) e = real_part(dcoef.as<double2>(), dh.as<double>(), M, c.st);
+  }
+  if (e == cudaSuccess && format == LB_DENSE && a->kind == LB_A_LOWRANK) {
+    e = cudaMemsetAsync(da.p, 0, 16 * mm, c.st);
+    for (int p = 0; p < a->nP && e == cudaSuccess; ++p) {
+      const int64_t n = a->lp_ptr[p + 1] - a->lp_ptr[p];
+      if (n == 0) continue;
+      const int64_t pairs = n * n;
+      k_lowrank_add<<<(unsigned)((pairs + 255) / 256), 256, 0, c.st>>>(
+          M, (int)n, dli.as<int64_t>() + a->lp_ptr[p], dlv.as<double2>() + a->lp_ptr[p], a->gamma[p], da.as<double2>());
+      lbi::note_launch(1);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess && format == LB_DENSE)
+    e = lbi::assemble_dense(b->view(), H ? dh.as<double>() : nullptr, da.as<double2>(), sys->A, sys->Q, sys->R,
+                            sys->K, algorithm, c.st);
+  if (e == cudaSuccess && format == LB_CSR) {
+    static const int64_t zero_ptr[1] = {0};
+    e = lbi::assemble_lowrank_csr(b->view(), H ? dh.as<double>() : nullptr, a->nP, a->gamma,
+                                  a->nP ? a->lp_ptr : zero_ptr, dli.as<int64_t>(), dlv.as<double2>(), &sys->csr, c.st);
+    sys->K = sys->csr.K;
+  }
+  clk.mark(LB_PHASE_D2H);
+  clk.mark(LB_PHASE_FREE);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
+  if (e != cudaSuccess) {
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      lbi::set_error("lb_assemble: device memory exhausted");
+      return fail(LB_ENOMEM);
+    }
+    return fail(lbi::cuda_fail(e, "lb_assemble"));
+  }
+  // the staging buffers go back to the pool here (stream-ordered)
+  const auto t1 = std::chrono::steady_clock::now();
+  da.free_now();
+  clk.mark(LB_PHASES);
+  cudaStreamSynchronize(c.st);
+  clk.read(sys->ms, LB_PHASE_H2D, LB_PHASES);
+  sys->ms[LB_PHASE_FREE] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+  *out = sys;
+  return LB_OK;
+}
+
+int lb_system_timings(const lb_system_t* s, double* ms) {
+  LB_REQUIRE(s && ms, "lb_system_timings: NULL argument");
+  for (int i = 0; i < LB_PHASES; ++i) ms[i] = s->ms[i];
+  return LB_OK;
+}
+
+int lb_system_info(const lb_system_t* s, int* format, int64_t* M, int64_t* nnz) {
+  LB_REQUIRE(s != nullptr, "lb_system_info: NULL handle");
+  if (format) *format = s->format;
+  if (M) *M = s->M;
+  if (nnz) *nnz = s->format == LB_CSR ? s->csr.nnz : s->M * s->M;
+  return LB_OK;
+}
+
+int lb_system_get_csr(const lb_system_t* s, int64_t* rowptr, int32_t* col, double* val) {
+  LB_REQUIRE(s != nullptr, "lb_system_get_csr: NULL handle");
+  LB_REQUIRE(s->format == LB_CSR, "lb_system_get_csr: the system is dense");
+  HostCtx c;
+  LB_TRY_CUDA(host_ctx(&c), "lb_system_get_csr");
+  if (rowptr)
+    LB_TRY_CUDA(cudaMemcpyAsync(rowptr, s->csr.rowptr, 8 * (size_t)(s->M + 1), cudaMemcpyDeviceToHost, c.st), "copy");
+  if (col) LB_TRY_CUDA(cudaMemcpyAsync(col, s->csr.col, 4 * (size_t)s->csr.nnz, cudaMemcpyDeviceToHost, c.st), "copy");
+  if (val) LB_TRY_CUDA(cudaMemcpyAsync(val, s->csr.val, 8 * (size_t)s->csr.nnz, cudaMemcpyDeviceToHost, c.st), "copy");
+  LB_TRY_CUDA(cudaStreamSynchronize(c.st), "lb_system_get_csr");
   return LB_OK;
 }
 
 int lb_system_destroy(lb_system_t* s) {
   if (!s) return LB_OK;
-  cudaFree(s->A);
-  cudaFree(s->Q);
-  cudaFree(s->R);
-  cudaFree(s->K);
-  cudaFree(s->A32);
-  cudaFree(s->Abf);
-  cudaFree(s->scale);
+  HostCtx c;
+  const bool have = host_ctx(&c) == cudaSuccess;
+  if (have) {  // pool memory, returned in the order of the library stream
+    pool_free(s->A, c.st);
+    pool_free(s->Q, c.st);
+    pool_free(s->R, c.st);
+    if (s->format == LB_DENSE) pool_free(s->K, c.st);
+    pool_free(s->A32, c.st);
+    pool_free(s->Abf, c.st);
+    pool_free(s->scale, c.st);
+  }
+  cudaFree(s->csr.rowptr);
+  cudaFree(s->csr.col);
+  cudaFree(s->csr.val);
+  cudaFree(s->csr.K);
+  cudaFree(s->csr32);
   delete s;
   return LB_OK;
 }
+
+}  // extern "C"
 
 namespace {
 
@@ -558,8 +884,17 @@ bool read_device(FILE* f, double* d, size_t count, std::string& err) {
 
 }  // namespace
 
+extern "C" {
+
 int lb_system_save(const lb_system_t* s, const char* path) {
   LB_REQUIRE(s && path, "lb_system_save: NULL argument");
+  if (s->format != LB_DENSE) {
+    lbi::set_error("lb_system_save: only dense systems are written to files");
+    return LB_EUNSUPPORTED;
+  }
+  HostCtx c;
+  LB_TRY_CUDA(host_ctx(&c), "lb_system_save");
+  LB_TRY_CUDA(cudaStreamSynchronize(c.st), "lb_system_save");
   FILE* f = fopen(path, "wb");
   LB_REQUIRE(f != nullptr, "lb_system_save: cannot open %s for writing", path);
   SysFileHeader h{};
@@ -603,12 +938,23 @@ int lb_system_load(const lb_basis_t* b, const char* path, lb_system_t** out) {
   }
   const size_t mm = (size_t)b->M * (size_t)b->M;
   int rc;
-  DevBuf dA, dK, dQ, dR;
-  if ((rc = alloc_or_enomem(dA, 8 * mm, "A")) != LB_OK || (rc = alloc_or_enomem(dK, 8 * (size_t)b->M, "K")) != LB_OK ||
-      ((h.parts & 4) && (rc = alloc_or_enomem(dQ, 8 * mm, "Q")) != LB_OK) ||
-      ((h.parts & 8) && (rc = alloc_or_enomem(dR, 8 * mm, "R")) != LB_OK)) {
+  HostCtx c;
+  const cudaError_t ec = host_ctx(&c);
+  if (ec != cudaSuccess) {
+    fclose(f);
+    return lbi::cuda_fail(ec, "lb_system_load: library stream");
+  }
+  PoolBuf dA, dK, dQ, dR;
+  if ((rc = dA.alloc(c, 8 * mm, "A")) != LB_OK || (rc = dK.alloc(c, 8 * (size_t)b->M, "K")) != LB_OK ||
+      ((h.parts & 4) && (rc = dQ.alloc(c, 8 * mm, "Q")) != LB_OK) ||
+      ((h.parts & 8) && (rc = dR.alloc(c, 8 * mm, "R")) != LB_OK)) {
     fclose(f);
     return rc;
+  }
+  const cudaError_t es = cudaStreamSynchronize(c.st);  // the copies below run on the legacy stream
+  if (es != cudaSuccess) {
+    fclose(f);
+    return lbi::cuda_fail(es, "lb_system_load");
   }
   std::string err;
   bool ok = read_device(f, dA.as<double>(), mm, err) && read_device(f, dK.as<double>(), (size_t)b->M, err);
@@ -635,67 +981,110 @@ int lb_system_get(const lb_system_t* s, int part, double* out) {
   LB_REQUIRE(s && out, "lb_system_get: NULL argument");
   const double* src = part == LB_SYS_A ? s->A : part == LB_SYS_Q ? s->Q : part == LB_SYS_R ? s->R
                       : part == LB_SYS_K ? s->K : nullptr;
-  LB_REQUIRE(src != nullptr, "lb_system_get: part %d not available", part);
+  LB_REQUIRE(src != nullptr, "lb_system_get: part %d not available%s", part,
+             s->format == LB_CSR && part != LB_SYS_K ? " (CSR system: use lb_system_get_csr)" : "");
+  HostCtx c;
+  LB_TRY_CUDA(host_ctx(&c), "lb_system_get");
   const size_t n = part == LB_SYS_K ? (size_t)s->M : (size_t)s->M * (size_t)s->M;
-  LB_TRY_CUDA(cudaMemcpy(out, src, 8 * n, cudaMemcpyDeviceToHost), "lb_system_get");
+  LB_TRY_CUDA(cudaMemcpyAsync(out, src, 8 * n, cudaMemcpyDeviceToHost, c.st), "lb_system_get");
+  LB_TRY_CUDA(cudaStreamSynchronize(c.st), "lb_system_get");
   return LB_OK;
 }
 
 static int integrate_steps(lb_system_t* s, int precision, int correct_every, const double* v0, double dt,
-                           int64_t n, double* v_out);
+                           int64_t n, int64_t snap_every, double* v_out);
 
 int lb_integrate(lb_system_t* s, int precision, int correct_every, const double* v0, double t, double dt,
-                 double* v_out) {
+                 int64_t snap_every, double* v_out) {
   LB_REQUIRE(s && v0 && v_out, "lb_integrate: NULL argument");
   LB_REQUIRE(dt > 0 && t >= 0 && std::isfinite(t) && std::isfinite(dt), "lb_integrate: bad t or dt");
+  LB_REQUIRE(correct_every >= 0 && snap_every >= 0, "lb_integrate: negative correction or snapshot period");
   const double nr = std::nearbyint(t / dt);
   const int64_t n = (int64_t)nr;
   LB_REQUIRE(std::fabs(nr * dt - t) <= 1e-9 * t, "lb_integrate: t = %g is not a multiple of dt = %g", t, dt);
-  return integrate_steps(s, precision, correct_every, v0, dt, n, v_out);
+  LB_REQUIRE(snap_every == 0 || n % snap_every == 0, "lb_integrate: %lld steps are not a multiple of snap_every = %lld",
+             (long long)n, (long long)snap_every);
+  return integrate_steps(s, precision, correct_every, v0, dt, n, snap_every, v_out);
 }
 
 int lb_integrate_resume(lb_system_t* s, int precision, int correct_every, double* v, double dt, int64_t nsteps) {
   LB_REQUIRE(s && v, "lb_integrate_resume: NULL argument");
   LB_REQUIRE(dt > 0 && std::isfinite(dt) && nsteps >= 0 && correct_every >= 0,
              "lb_integrate_resume: bad dt, step count or correction period");
-  return integrate_steps(s, precision, correct_every, v, dt, nsteps, v);
+  return integrate_steps(s, precision, correct_every, v, dt, nsteps, 0, v);
 }
 
 static int integrate_steps(lb_system_t* s, int precision, int correct_every, const double* v0, double dt,
-                           int64_t n, double* v_out) {
+                           int64_t n, int64_t snap_every, double* v_out) {
   const int64_t M = s->M;
   const size_t mm = (size_t)M * (size_t)M;
+  HostCtx c;
+  LB_TRY_CUDA(host_ctx(&c), "lb_integrate: library stream");
   int rc;
-  const void* Ap = s->A;
-  if (precision == LB_FP32) {
-    if (!s->A32) {
+  if (s->format == LB_CSR) {
+    LB_REQUIRE(precision == LB_FP64 || precision == LB_FP32, "lb_integrate: CSR precision = %d", precision);
+    LB_REQUIRE(snap_every == 0 || correct_every == 0 || precision == LB_FP64 || snap_every % correct_every == 0,
+               "lb_integrate: on a CSR system snap_every must be a multiple of correct_every");
+  } else {
+    LB_REQUIRE(precision == LB_FP64 || precision == LB_FP32 || precision == LB_BF16, "lb_integrate: precision = %d",
+               precision);
+  }
+  const void* Ap = s->format == LB_CSR ? (const void*)s->csr.val : (const void*)s->A;
+  if (precision == LB_FP32 && s->format == LB_CSR) {
+    if (!s->csr32) {
       DevBuf b32;
-      if ((rc = alloc_or_enomem(b32, 4 * mm, "A32")) != LB_OK) return rc;
-      LB_TRY_CUDA(lbi::pack_fp32(M, s->A, b32.as<float>(), nullptr), "pack fp32");
+      if ((rc = alloc_or_enomem(b32, sizeof(float) * (size_t)(s->csr.nnz + 1), "FP32 values")) != LB_OK) return rc;
+      LB_TRY_CUDA(lbi::to_f32(s->csr.nnz, s->csr.val, b32.as<float>(), c.st), "pack FP32 values");
+      s->csr32 = static_cast<float*>(b32.release());
+    }
+    Ap = s->csr32;
+  } else if (precision == LB_FP32) {
+    if (!s->A32) {
+      PoolBuf b32;
+      if ((rc = b32.alloc(c, 4 * mm, "A32")) != LB_OK) return rc;
+      LB_TRY_CUDA(lbi::pack_fp32(M, s->A, b32.as<float>(), c.st), "pack fp32");
       s->A32 = static_cast<float*>(b32.release());
     }
     Ap = s->A32;
   } else if (precision == LB_BF16) {
     if (!s->Abf) {
-      DevBuf bb, sc;
-      if ((rc = alloc_or_enomem(bb, 2 * mm, "Abf16")) != LB_OK) return rc;
-      if ((rc = alloc_or_enomem(sc, 4 * (size_t)M, "row scales")) != LB_OK) return rc;
-      LB_TRY_CUDA(lbi::pack_bf16(M, s->A, bb.as<uint16_t>(), sc.as<float>(), nullptr), "pack bf16");
+      PoolBuf bb, sc;
+      if ((rc = bb.alloc(c, 2 * mm, "Abf16")) != LB_OK) return rc;
+      if ((rc = sc.alloc(c, 4 * (size_t)M, "row scales")) != LB_OK) return rc;
+      LB_TRY_CUDA(lbi::pack_bf16(M, s->A, bb.as<uint16_t>(), sc.as<float>(), c.st), "pack bf16");
       s->Abf = static_cast<uint16_t*>(bb.release());
       s->scale = static_cast<float*>(sc.release());
     }
     Ap = s->Abf;
-  } else {
-    LB_REQUIRE(precision == LB_FP64, "lb_integrate: precision = %d", precision);
   }
-  DevBuf dv, work;
-  if ((rc = alloc_or_enomem(dv, 8 * (size_t)M, "v")) != LB_OK) return rc;
-  if ((rc = alloc_or_enomem(work, lbi::rk4_workspace_bytes(M), "RK4 workspace")) != LB_OK) return rc;
-  LB_TRY_CUDA(cudaMemcpy(dv.p, v0, 8 * (size_t)M, cudaMemcpyHostToDevice), "copy v0");
-  LB_TRY_CUDA(lbi::rk4_dense(M, precision, Ap, s->scale, s->A, correct_every, s->K, dv.as<double>(), dt, n,
-                             nullptr, 0, work.p, nullptr),
-              "RK4");
-  LB_TRY_CUDA(cudaMemcpy(v_out, dv.p, 8 * (size_t)M, cudaMemcpyDeviceToHost), "copy v");
+  const int64_t nsnap = snap_every ? n / snap_every : 0;
+  PoolBuf dv, work, dsn;
+  if ((rc = dv.alloc(c, 8 * (size_t)M, "v")) != LB_OK) return rc;
+  if ((rc = work.alloc(c, lbi::rk4_workspace_bytes(M), "RK4 workspace")) != LB_OK) return rc;
+  if (nsnap > 0 && (rc = dsn.alloc(c, 8 * (size_t)M * nsnap, "snapshots")) != LB_OK) return rc;
+  LB_TRY_CUDA(cudaMemcpyAsync(dv.p, v0, 8 * (size_t)M, cudaMemcpyHostToDevice, c.st), "copy v0");
+  if (s->format == LB_CSR) {
+    const int64_t seg = nsnap > 0 ? snap_every : n;
+    const int64_t nseg = nsnap > 0 ? nsnap : 1;
+    for (int64_t i = 0; i < nseg; ++i) {
+      LB_TRY_CUDA(lbi::rk4_csr(M, precision, s->csr.rowptr, s->csr.col, Ap, s->csr.val, correct_every, s->csr.K,
+                               dv.as<double>(), dt, seg, work.p, c.st),
+                  "RK4 (CSR)");
+      if (nsnap > 0)
+        LB_TRY_CUDA(cudaMemcpyAsync(dsn.as<double>() + (size_t)i * M, dv.p, 8 * (size_t)M, cudaMemcpyDeviceToDevice,
+                                    c.st),
+                    "snapshot");
+    }
+  } else {
+    LB_TRY_CUDA(lbi::rk4_dense(M, precision, Ap, s->scale, s->A, correct_every, s->K, dv.as<double>(), dt, n,
+                               nsnap > 0 ? dsn.as<double>() : nullptr, nsnap > 0 ? snap_every : 0, work.p, c.st),
+                "RK4");
+  }
+  if (nsnap > 0)
+    LB_TRY_CUDA(cudaMemcpyAsync(v_out, dsn.p, 8 * (size_t)M * nsnap, cudaMemcpyDeviceToHost, c.st), "copy snapshots");
+  else
+    LB_TRY_CUDA(cudaMemcpyAsync(v_out, dv.p, 8 * (size_t)M, cudaMemcpyDeviceToHost, c.st), "copy v");
+  LB_TRY_CUDA(cudaStreamSynchronize(c.st), "lb_integrate");
   return LB_OK;
 }
 

@@ -17,6 +17,10 @@ LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ETIMEOUT, LB_EUNSUPPORTED, LB_EAGAIN =
 LB_F, LB_D = 0, 1
 LB_FP64, LB_FP32, LB_BF16 = 0, 1, 2
 LB_SYS_A, LB_SYS_Q, LB_SYS_R, LB_SYS_K = 0, 1, 2, 3
+LB_DENSE, LB_CSR = 0, 1
+FORMATS = {"dense": LB_DENSE, "csr": LB_CSR}
+LB_A_DENSE, LB_A_LOWRANK = 0, 1
+PHASES = ("alloc", "h2d", "kernels", "d2h", "free")
 PRECISIONS = {"fp64": LB_FP64, "fp32": LB_FP32, "bf16": LB_BF16}
 LB_ALG_JOIN, LB_ALG_CLOSED = 0, 1
 ALGORITHMS = {"join": LB_ALG_JOIN, "closed": LB_ALG_CLOSED}
@@ -35,6 +39,11 @@ class LbRequest(ctypes.Structure):
                 ("dt", ctypes.c_double), ("nsteps", ctypes.c_int64), ("H", ctypes.c_void_p),
                 ("a", ctypes.c_void_p), ("v0", ctypes.c_void_p), ("v_out", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p)]
+
+
+class LbKossakowski(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_void_p), ("nP", ctypes.c_int), ("gamma", ctypes.c_void_p),
+                ("lp_ptr", ctypes.c_void_p), ("lp_idx", ctypes.c_void_p), ("lp_val", ctypes.c_void_p)]
 
 
 class LbResult(ctypes.Structure):
@@ -82,14 +91,21 @@ def load():
         "lb_rk4_workspace_bytes": (ctypes.c_size_t, [_c_i64]),
         "lb_rk4_dense": (ctypes.c_int, [_c_i64, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp, _vp,
                                         ctypes.c_double, _c_i64, _vp, _c_i64, _vp, _vp]),
-        "lb_assemble": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
+        "lb_assemble": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(LbKossakowski), ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(_vp)]),
+        "lb_system_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), _i64p, _i64p]),
+        "lb_system_timings": (ctypes.c_int, [_vp, _dp]),
+        "lb_system_get_csr": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+        "lb_host_release": (ctypes.c_int, []),
+        "lb_expand_host": (ctypes.c_int, [_vp, _vp, _vp]),
+        "lb_rho_host": (ctypes.c_int, [_vp, _vp, _vp]),
         "lb_system_destroy": (ctypes.c_int, [_vp]),
         "lb_system_get": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
         "lb_system_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
         "lb_system_load": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.POINTER(_vp)]),
         "lb_integrate_resume": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, _c_i64]),
         "lb_integrate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double,
-                                        ctypes.c_double, _vp]),
+                                        ctypes.c_double, _c_i64, _vp]),
         "lb_assemble_lowrank_csr": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp,
                                                    ctypes.POINTER(_vp), _vp]),
         "lb_csr_info": (ctypes.c_int, [_vp, _i64p, _i64p, _i64p]),
@@ -303,7 +319,23 @@ class Basis:
         _check(load().lb_rho(self._h, _ptr(v), _ptr(out), _stream(stream)))
         return out
 
-    def assemble_dense(self, a, h=None, A=True, Q=False, R=False, K=True, algorithm="join", stream=None):
+    def expand_host(self, A):
+        """Eq. (02) from a host N x N complex array (lb_expand_host) -> M complex (numpy)."""
+        A = np.ascontiguousarray(A, np.complex128)
+        assert A.shape == (self.N, self.N)
+        coef = np.zeros(self.M, np.complex128)
+        _check(load().lb_expand_host(self._h, _ptr(A), _ptr(coef)))
+        return coef
+
+    def rho_host(self, v):
+        """Eq. (rho) from a host M-vector (lb_rho_host) -> N x N complex (numpy)."""
+        v = np.ascontiguousarray(v, np.float64)
+        assert v.shape == (self.M,)
+        out = np.zeros((self.N, self.N), np.complex128)
+        _check(load().lb_rho_host(self._h, _ptr(v), _ptr(out)))
+        return out
+
+    def assemble_dense(self, a, h=None, A=True, Q=False, R=False, K=True, algorithm="closed", stream=None):
         """Dense Q, R, K (Eqs. (07)-(09)).  a: M x M complex128 device tensor.
 
         A, Q, R, K may be True (allocate), False/None (skip) or a preallocated
@@ -479,23 +511,52 @@ class Batch:
         return A, K
 
 
-class System:
-    """Host-buffer interface: lb_assemble / lb_system_get / lb_integrate."""
+def host_release():
+    """Return the spare device memory of the host-buffer interface's pool."""
+    _check(load().lb_host_release())
 
-    def __init__(self, basis, a, H=None, keep_parts=False, algorithm="join"):
+
+class System:
+    """Host-buffer interface: lb_assemble / lb_system_* / lb_integrate.
+
+    a: dense M x M complex Kossakowski matrix (numpy), or None with
+    channels = [(gamma, idx, values), ...] (host arrays: basis indices and
+    complex values of each l_p) for a = sum_p gamma_p l_p l_p^dagger.
+    format: "dense" or "csr" (CSR needs channels)."""
+
+    def __init__(self, basis, a=None, H=None, keep_parts=False, algorithm="closed", channels=None, format="dense"):
         lib = load()
         if isinstance(a, _vp):  # an already created handle (System.load)
             self._h, self.basis, self.M = a, basis, basis.M
+            self.format = "dense"
             return
-        a = np.ascontiguousarray(a, np.complex128)
-        assert a.shape == (basis.M, basis.M)
+        ks = LbKossakowski()
+        keep = []
+        if channels is not None:
+            gam = np.ascontiguousarray([float(g) for g, _, _ in channels], np.float64)
+            ptr = np.zeros(len(channels) + 1, np.int64)
+            for p, (_, idx, _) in enumerate(channels):
+                ptr[p + 1] = ptr[p] + len(idx)
+            idx = np.ascontiguousarray(np.concatenate([np.asarray(i, np.int64) for _, i, _ in channels])
+                                       if channels else np.zeros(1, np.int64))
+            val = np.ascontiguousarray(np.concatenate([np.asarray(v, np.complex128) for _, _, v in channels])
+                                       if channels else np.zeros(1, np.complex128))
+            keep += [gam, ptr, idx, val]
+            ks.kind, ks.nP = LB_A_LOWRANK, len(channels)
+            ks.gamma, ks.lp_ptr, ks.lp_idx, ks.lp_val = _ptr(gam), _ptr(ptr), _ptr(idx), _ptr(val)
+        else:
+            a = np.ascontiguousarray(a, np.complex128)
+            assert a.shape == (basis.M, basis.M)
+            keep.append(a)
+            ks.kind, ks.a = LB_A_DENSE, _ptr(a)
         Hc = None if H is None else np.ascontiguousarray(H, np.complex128)
         h = _vp()
-        _check(lib.lb_assemble(basis.handle, _ptr(Hc), _ptr(a), int(bool(keep_parts)), ALGORITHMS[algorithm],
-                               ctypes.byref(h)))
+        _check(lib.lb_assemble(basis.handle, _ptr(Hc), ctypes.byref(ks), FORMATS[format], ALGORITHMS[algorithm],
+                               int(bool(keep_parts)), ctypes.byref(h)))
         self._h = h
         self.basis = basis
         self.M = basis.M
+        self.format = format
 
     def close(self):
         if self._h:
@@ -508,17 +569,41 @@ class System:
         except Exception:
             pass
 
+    def info(self):
+        f, M, nnz = ctypes.c_int(), _c_i64(), _c_i64()
+        _check(load().lb_system_info(self._h, ctypes.byref(f), ctypes.byref(M), ctypes.byref(nnz)))
+        return {"format": {LB_DENSE: "dense", LB_CSR: "csr"}[f.value], "M": M.value, "nnz": nnz.value}
+
+    def timings(self):
+        """Phase times (ms) of the lb_assemble call that built the system."""
+        ms = (ctypes.c_double * len(PHASES))()
+        _check(load().lb_system_timings(self._h, ms))
+        return {k: float(ms[i]) for i, k in enumerate(PHASES)}
+
     def get(self, part):
         p = {"A": LB_SYS_A, "Q": LB_SYS_Q, "R": LB_SYS_R, "K": LB_SYS_K}[part]
         out = np.zeros(self.M if part == "K" else (self.M, self.M))
         _check(load().lb_system_get(self._h, p, _ptr(out)))
         return out
 
-    def integrate(self, v0, t, dt, precision="fp64", correct_every=0, out=None):
+    def get_csr(self):
+        """(rowptr int64, col int32, val float64) of a CSR system."""
+        nnz = self.info()["nnz"]
+        rp = np.zeros(self.M + 1, np.int64)
+        col = np.zeros(max(nnz, 1), np.int32)
+        val = np.zeros(max(nnz, 1), np.float64)
+        _check(load().lb_system_get_csr(self._h, _ptr(rp), _ptr(col), _ptr(val)))
+        return rp, col[:nnz], val[:nnz]
+
+    def integrate(self, v0, t, dt, precision="fp64", correct_every=0, snap_every=0, out=None):
+        """RK4 from host v0; returns the final state (M,) or, with snap_every,
+        the (n / snap_every, M) snapshots."""
         v0 = np.ascontiguousarray(v0, np.float64)
-        out = np.zeros(self.M) if out is None else out
+        n = int(round(t / dt))
+        shape = (n // snap_every, self.M) if snap_every else (self.M,)
+        out = np.zeros(shape) if out is None else out
         _check(load().lb_integrate(self._h, PRECISIONS[precision], int(correct_every), _ptr(v0), float(t),
-                                   float(dt), _ptr(out)))
+                                   float(dt), int(snap_every), _ptr(out)))
         return out
 
     def integrate_resume(self, v, dt, nsteps, precision="fp64", correct_every=0):

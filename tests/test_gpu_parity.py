@@ -436,3 +436,95 @@ def test_rk4_fp64_n50_full_trajectory():
     for t in range(len(ref_snaps)):
         assert np.linalg.norm(snaps[t] - ref_snaps[t]) <= 1e-12 * np.linalg.norm(ref_snaps[t]), t
     assert np.linalg.norm(v.cpu().numpy() - ref_v) <= 1e-12 * np.linalg.norm(ref_v)
+
+
+def _ladder_channels(o, N, seed):
+    H, L, g = wl.ladder_model(N, seed)
+    l, _ = o.expand(L)
+    nz = np.nonzero(np.abs(l) > 0)[0]
+    return H, g, nz, l[nz], g * np.outer(l, l.conj())
+
+
+@pytest.mark.parametrize("N", [5, 8])
+def test_host_api_lowrank_dense_and_csr_systems(N):
+    """lb_assemble with a low-rank Kossakowski matrix (one channel, the ladder
+    operator; Sec. 2's sum over jump operators) into a dense and into a CSR
+    system: dense A against the oracle's Q + R at the per-entry tolerance; the
+    CSR pattern bit-exact and its values against the oracle's sparse route;
+    snapshots of lb_integrate on both systems within 1e-12 ||v|| of the
+    oracle's RK4."""
+    from oracle import lowrank_csr
+    lb = lbm()
+    with lb.Basis(N) as B, Oracle(N) as o:
+        H, g, nz, lv, a = _ladder_channels(o, N, 900 + N)
+        h, _ = o.expand(H)
+        Q = o.Q(h.real)
+        R, S = o.R(a, return_scale=True)
+        K = o.K(a)
+        rp_o, col_o, val_o, K_o = lowrank_csr(o, h.real, [g], [(nz, lv)])
+        v0 = o.expand(wl.pure_state(N, N - 1))[0].real
+        ref_v, ref_snaps = ora_rk4(Q + R, K, v0, 1e-3, 600, snap_every=200)
+        ch = [(g, nz, lv)]
+        dense = lb.System(B, None, H=H, channels=ch, format="dense", keep_parts=True)
+        assert dense.info() == {"format": "dense", "M": B.M, "nnz": B.M * B.M}
+        _assert_entries(dense.get("R"), R, S, "R (low-rank a, dense system)")
+        _assert_entries(dense.get("A"), Q + R, S + np.abs(Q), "A (low-rank a, dense system)")
+        assert np.abs(dense.get("K") - K).max() <= 1e-12 * np.abs(K).max()
+        tm = dense.timings()
+        assert set(tm) == {"alloc", "h2d", "kernels", "d2h", "free"} and min(tm.values()) >= 0.0
+        csr = lb.System(B, None, H=H, channels=ch, format="csr")
+        rp, col, val = csr.get_csr()
+        assert csr.info()["format"] == "csr" and csr.info()["nnz"] == len(col)
+        assert np.array_equal(rp, rp_o) and np.array_equal(col, col_o)
+        assert np.abs(val - val_o).max() <= 1e-12 * np.abs(val_o).max()
+        assert np.abs(csr.get("K") - K_o).max() <= 1e-12 * max(np.abs(K_o).max(), 1e-300) + 1e-18
+        for sysm, prec in ((dense, "fp64"), (csr, "fp64")):
+            snaps = sysm.integrate(v0, 0.6, 1e-3, precision=prec, snap_every=200)
+            assert snaps.shape == ref_snaps.shape
+            for t in range(len(ref_snaps)):
+                assert np.linalg.norm(snaps[t] - ref_snaps[t]) <= 1e-12 * np.linalg.norm(ref_snaps[t])
+            fin = sysm.integrate(v0, 0.6, 1e-3, precision=prec)
+            assert np.array_equal(fin, snaps[-1])
+        with pytest.raises(lb.LBError) as e:
+            dense.integrate(v0, 0.6, 1e-3, snap_every=250)          # 600 steps, not a multiple
+        assert e.value.code == lb.native.LB_EINVAL
+        with pytest.raises(lb.LBError) as e:
+            csr.get("A")
+        assert e.value.code == lb.native.LB_EINVAL
+        dense.close()
+        csr.close()
+        with pytest.raises(lb.LBError) as e:                       # dense a into CSR
+            lb.System(B, a, H=H, format="csr")
+        assert e.value.code == lb.native.LB_EUNSUPPORTED
+        with pytest.raises(lb.LBError) as e:                       # Q, R not kept in CSR
+            lb.System(B, None, channels=ch, format="csr", keep_parts=True)
+        assert e.value.code == lb.native.LB_EUNSUPPORTED
+        lb.native.host_release()
+
+
+def test_host_api_expand_and_rho():
+    N = 9
+    g = np.random.default_rng(9)
+    A = g.standard_normal((N, N)) + 1j * g.standard_normal((N, N))
+    v = g.standard_normal(N * N - 1)
+    with lbm().Basis(N) as B, Oracle(N) as o:
+        assert np.abs(B.expand_host(A) - o.expand(A)[0]).max() < 1e-13
+        assert np.abs(B.rho_host(v) - o.rho(v)).max() < 1e-13
+
+
+def test_host_api_repeated_calls_reuse_memory():
+    """Repeated host-buffer assemblies of one size give the same bits (the
+    pool hands back the same reservation), and their allocation phase is
+    short once the size has been seen."""
+    N = 30
+    H, a = _case(N, 3030)
+    lb = lbm()
+    with lb.Basis(N) as B:
+        outs, allocs = [], []
+        for _ in range(3):
+            s = lb.System(B, a, H=H)
+            outs.append(s.get("A"))
+            allocs.append(s.timings()["alloc"])
+            s.close()
+        assert all(np.array_equal(outs[0], x) for x in outs[1:])
+        assert allocs[2] < 50.0
