@@ -334,6 +334,33 @@ int lb_batch_tune(lb_batch_t *b, int width, int probe_steps, double dt, void *st
  * LB_FP64 (FP64 matrix and products; correct_every is ignored). */
 int lb_batch_set_precision(lb_batch_t *b, int precision);
 
+/* Integration form of lb_batch_integrate and lb_batch_tune. */
+#define LB_FORM_RK4 0         /* the four RK4 stages per step (default) */
+#define LB_FORM_PROPAGATOR 1  /* one product per step with D' = (P(hA) - 1)/h */
+
+/* Select the integration form.  LB_FORM_PROPAGATOR: for the autonomous
+ * system dv/dt = A v + K, one classical RK4 step of size h (Sec. 4 item 3)
+ * equals v <- v + h (D' v + c') with
+ *   D' = A + (h/2) A (A + (h/3) A (A + (h/4) A A)) = (P(hA) - 1)/h,
+ *   P(x) = 1 + x + x^2/2 + x^3/6 + x^4/24,
+ *   c' = K + (h/2) A (K + (h/3) A (K + (h/4) A K)),
+ * so a step reads the matrix once and exchanges the state once.  D' and c'
+ * are formed for the step h of the first integration (or by
+ * lb_batch_form_propagator) and kept until h or the precision changes.
+ * Precision LB_FP64: D' and c' in FP64, FP64 products.  LB_FP32: D' formed
+ * from the FP32 A with FP32 products (its difference from A kept in FP32 as
+ * well), c' in FP64, FP64 state; with correct_every > 0 the FP64 defect
+ * (A64 + (D' - A)_FP32 - D'_FP32) v is added to c' every correct_every steps.
+ * The trajectory equals classical RK4's up to rounding. */
+int lb_batch_set_form(lb_batch_t *b, int form);
+
+/* Form D' and c' of every realization for step dt in the batch's precision
+ * now (three matrix products per realization, by this library's batched
+ * tiled GEMM, and three FP64 matrix-vector products); ms (optional)
+ * receives the device time.  Synchronous.  LB_ENOMEM if the device cannot
+ * hold D' (and D' - A) beside the batch. */
+int lb_batch_form_propagator(lb_batch_t *b, double dt, void *stream, float *ms);
+
 /* RK4 for every realization, nsteps steps of dt, FP32 matrix with FP32
  * products, FP64 state, FP64 defect correction every correct_every steps (0:
  * none).  One persistent cluster launch per cluster-size group: a cluster

@@ -18,6 +18,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -295,6 +296,193 @@ __global__ void __launch_bounds__(256, 4) k_rk4_batch64(const BItem* __restrict_
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Propagator form (lb_prop.cu): one step is v <- v + h (D' v + c'), one
+// product with the matrix and one exchange of the state per step.  The
+// cluster layout is that of k_rk4_batch: each block owns a slice of rows and
+// keeps its slice of D' in shared memory when it fits.
+//   FP32: D' stored in FP32 (D32 = fl(A32 + R32), R32 = D' - A in FP32),
+//     products FP32 FMAs of the FP32-rounded state, state FP64.  Every
+//     correct_every steps the FP64 defect d = (A64 + R32 - D32) v is formed
+//     from the FP64 state and added to c' until the next one: A64 - A32 is
+//     the storage error of A and A32 + R32 - D32 the rounding of the sum,
+//     the two FP32 errors of D' to first order (R32's own rounding is h|A|
+//     times smaller).
+//   FP64: D' in FP64, FP64 products, no correction.
+struct PItem {
+  int64_t M;
+  const float* D32;   // FP32 form: D' (M x M)
+  const float* R32;   // FP32 form: D' - A in FP32, for the correction
+  const double* A64;  // FP32 form with correction: A; FP64 form: D' (FP64)
+  const double* cp;   // c' (M)
+  double* v;          // M, in/out
+};
+
+struct SmemLayoutP {
+  int64_t slice, mmax;
+  bool resident;
+  size_t off_item, off_x32, off_x64, off_v, off_keff, off_r, total;
+};
+
+SmemLayoutP layoutP(int64_t mmax, int C, bool resident, bool f64) {
+  SmemLayoutP L;
+  L.mmax = mmax;
+  L.slice = (mmax + C - 1) / C;
+  L.resident = resident;
+  size_t o = 0;
+  L.off_item = o; o = a16(o + 16);
+  L.off_x32 = o; o = a16(o + (f64 ? 0 : sizeof(float) * 2 * mmax));
+  L.off_x64 = o; o = a16(o + sizeof(double) * (f64 ? 2 : 1) * mmax);
+  L.off_v = o; o = a16(o + sizeof(double) * L.slice);
+  L.off_keff = o; o = a16(o + sizeof(double) * L.slice);
+  L.off_r = o;
+  if (resident) o = a16(o + (f64 ? sizeof(double) : sizeof(float)) * L.slice * mmax);
+  L.total = o;
+  return L;
+}
+
+__global__ void __launch_bounds__(256, 4) k_prop_batch(const PItem* __restrict__ items, const int* __restrict__ order,
+                                                    int nitems, int* __restrict__ counter, int64_t nsteps, double h,
+                                                    int correct_every, SmemLayoutP L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  int* item_slot = reinterpret_cast<int*>(smem + L.off_item);
+  float* x32 = reinterpret_cast<float*>(smem + L.off_x32);  // [2][mmax]
+  double* x64 = reinterpret_cast<double*>(smem + L.off_x64);
+  double* vv = reinterpret_cast<double*>(smem + L.off_v);
+  double* keff = reinterpret_cast<double*>(smem + L.off_keff);
+  float* Ds = reinterpret_cast<float*>(smem + L.off_r);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t mmax = L.mmax;
+  while (true) {
+    const int qi = next_item(cluster, rank, item_slot, counter);
+    if (qi >= nitems) break;
+    const PItem it = items[order[qi]];
+    const int64_t M = it.M;
+    const int64_t slice = (M + C - 1) / C;
+    const int64_t r0 = rank * slice, r1 = r0 + slice < M ? r0 + slice : M;
+    const int64_t nrow = r1 > r0 ? r1 - r0 : 0;
+    const bool resident = L.resident;
+    const bool correct = correct_every > 0 && it.A64 != nullptr && it.R32 != nullptr;
+    for (int64_t i = threadIdx.x; i < nrow; i += blockDim.x) {
+      vv[i] = it.v[r0 + i];
+      keff[i] = it.cp[r0 + i];
+    }
+    if (resident)
+      for (int64_t e = threadIdx.x; e < nrow * M; e += blockDim.x) Ds[e] = it.D32[r0 * M + e];
+    for (int64_t n = threadIdx.x; n < M; n += blockDim.x) {
+      x32[n] = (float)it.v[n];
+      x64[n] = it.v[n];
+    }
+    __syncthreads();
+    const int W = row_group_width(M), G = 32 / W, g = lane / W, sub = lane % W;
+    for (int64_t t = 0; t < nsteps; ++t) {
+      if (correct && t % correct_every == 0) {
+        // FP64 defect d = (A64 + R32 - D32) v on own rows
+        for (int64_t i = warp; i < nrow; i += nw) {
+          const int64_t s = r0 + i;
+          double d = 0.0;
+          for (int64_t n = lane; n < M; n += 32) {
+            const int64_t q = s * M + n;
+            d = fma((it.A64[q] + (double)it.R32[q]) - (double)it.D32[q], x64[n], d);
+          }
+          for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+          if (lane == 0) keff[i] = it.cp[s] + d;
+        }
+        __syncthreads();
+      }
+      const bool push64 = correct && (t + 1) % correct_every == 0;
+      const float* xc = x32 + (t & 1) * mmax;
+      float* xn = x32 + ((t + 1) & 1) * mmax;
+      for (int64_t i0 = (int64_t)warp * G; i0 < nrow; i0 += (int64_t)nw * G) {
+        const int64_t i = i0 + g;
+        const bool valid = i < nrow;  // every lane reaches the shuffles
+        float a = 0.f;
+        if (valid) {
+          const float* row = resident ? Ds + i * M : it.D32 + (r0 + i) * M;
+          a = group_dot(row, xc, M, sub, W);
+        }
+        for (int o = W >> 1; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        const double vi = valid ? vv[i] : 0.0, ki = valid ? keff[i] : 0.0;
+        __syncwarp();
+        if (valid) {
+          const double nx = fma(h, (double)a + ki, vi);
+          if (sub == 0) vv[i] = nx;
+          for (int q = sub; q < C; q += W) {
+            *cluster.map_shared_rank(xn + r0 + i, q) = (float)nx;
+            if (push64) *cluster.map_shared_rank(x64 + r0 + i, q) = nx;
+          }
+        }
+      }
+      cluster.sync();  // every block's copy of the next state is complete
+    }
+    for (int64_t i = threadIdx.x; i < nrow; i += blockDim.x) it.v[r0 + i] = vv[i];
+    cluster.sync();  // all blocks are done with this realization's buffers
+  }
+}
+
+__global__ void __launch_bounds__(256, 4) k_prop_batch64(const PItem* __restrict__ items,
+                                                      const int* __restrict__ order, int nitems,
+                                                      int* __restrict__ counter, int64_t nsteps, double h,
+                                                      SmemLayoutP L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  int* item_slot = reinterpret_cast<int*>(smem + L.off_item);
+  double* x = reinterpret_cast<double*>(smem + L.off_x64);  // [2][mmax]
+  double* vv = reinterpret_cast<double*>(smem + L.off_v);
+  double* keff = reinterpret_cast<double*>(smem + L.off_keff);
+  double* Ds = reinterpret_cast<double*>(smem + L.off_r);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t mmax = L.mmax;
+  while (true) {
+    const int qi = next_item(cluster, rank, item_slot, counter);
+    if (qi >= nitems) break;
+    const PItem it = items[order[qi]];
+    const int64_t M = it.M;
+    const int64_t slice = (M + C - 1) / C;
+    const int64_t r0 = rank * slice, r1 = r0 + slice < M ? r0 + slice : M;
+    const int64_t nrow = r1 > r0 ? r1 - r0 : 0;
+    const bool resident = L.resident;
+    for (int64_t i = threadIdx.x; i < nrow; i += blockDim.x) {
+      vv[i] = it.v[r0 + i];
+      keff[i] = it.cp[r0 + i];
+    }
+    if (resident)
+      for (int64_t e = threadIdx.x; e < nrow * M; e += blockDim.x) Ds[e] = it.A64[r0 * M + e];
+    for (int64_t n = threadIdx.x; n < M; n += blockDim.x) x[n] = it.v[n];
+    __syncthreads();
+    const int W = row_group_width(M), G = 32 / W, g = lane / W, sub = lane % W;
+    for (int64_t t = 0; t < nsteps; ++t) {
+      const double* xc = x + (t & 1) * mmax;
+      double* xn = x + ((t + 1) & 1) * mmax;
+      for (int64_t i0 = (int64_t)warp * G; i0 < nrow; i0 += (int64_t)nw * G) {
+        const int64_t i = i0 + g;
+        const bool valid = i < nrow;
+        double a = 0.0;
+        if (valid) {
+          const double* row = resident ? Ds + i * M : it.A64 + (r0 + i) * M;
+          a = group_dot(row, xc, M, sub, W);
+        }
+        for (int o = W >> 1; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        const double vi = valid ? vv[i] : 0.0, ki = valid ? keff[i] : 0.0;
+        __syncwarp();
+        if (valid) {
+          const double nx = fma(h, a + ki, vi);
+          if (sub == 0) vv[i] = nx;
+          for (int q = sub; q < C; q += W) *cluster.map_shared_rank(xn + r0 + i, q) = nx;
+        }
+      }
+      cluster.sync();
+    }
+    for (int64_t i = threadIdx.x; i < nrow; i += blockDim.x) it.v[r0 + i] = vv[i];
+    cluster.sync();
+  }
+}
 }  // namespace
 
 struct lb_batch {
@@ -309,9 +497,17 @@ struct lb_batch {
   std::vector<float*> A32;
   std::vector<int> cluster;  // chosen cluster size per realization
   int precision = LB_FP32;   // storage and arithmetic of the integration
+  int form = LB_FORM_RK4;    // stage-by-stage RK4 or the propagator form
+  // propagator form, made for step prop_dt and precision prop_prec
+  double prop_dt = 0.0;
+  int prop_prec = -1;
+  std::vector<float*> D32, R32;  // FP32: D' and D' - A
+  std::vector<double*> D64, cp;  // FP64: D'; both: c'
+  float prop_ms = 0.f;           // device time of the last formation
   BItem* d_items = nullptr;
   int* d_order = nullptr;
   int* d_counter = nullptr;
+  void* d_prop_items = nullptr;
 };
 
 namespace lbi {
@@ -330,7 +526,22 @@ cudaError_t batch_alloc(lb_batch* b) {
   return cudaMalloc(&b->d_counter, sizeof(int) * 8);
 }
 
+void prop_free(lb_batch* b) {
+  for (auto* p : b->D32) cudaFree(p);
+  for (auto* p : b->R32) cudaFree(p);
+  for (auto* p : b->D64) cudaFree(p);
+  for (auto* p : b->cp) cudaFree(p);
+  b->D32.clear();
+  b->R32.clear();
+  b->D64.clear();
+  b->cp.clear();
+  cudaFree(b->d_prop_items);
+  b->d_prop_items = nullptr;
+  b->prop_prec = -1;
+}
+
 void batch_free(lb_batch* b) {
+  prop_free(b);
   for (int r = 0; r < b->count; ++r) {
     cudaFree(b->A64[r]);
     cudaFree(b->A32[r]);
@@ -352,6 +563,106 @@ cudaError_t batch_assemble(lb_batch* b, const std::vector<lb::BasisView>& views,
   return cudaGetLastError();
 }
 
+// D' and c' of every realization for step h in the batch's precision
+// (lb_prop.cu): G0 = A + (h/4) A A, G1 = A + (h/3) A G0, R' = (h/2) A G1,
+// D' = A + R' (FP32 from A32, or FP64 from A64); c' from A64 in FP64.
+cudaError_t batch_form_propagator(lb_batch* b, double h, cudaStream_t st) {
+  const bool f64 = b->precision == LB_FP64;
+  if (b->prop_prec != -1 && b->prop_prec == b->precision && b->prop_dt == h) return cudaSuccess;
+  prop_free(b);
+  const int n = b->count;
+  cudaError_t e = cudaSuccess;
+  b->cp.assign(n, nullptr);
+  if (f64) {
+    b->D64.assign(n, nullptr);
+  } else {
+    b->D32.assign(n, nullptr);
+    b->R32.assign(n, nullptr);
+  }
+  std::vector<void*> tmp;
+  auto scratch_free = [&]() {
+    for (auto* p : tmp) cudaFree(p);
+    tmp.clear();
+  };
+  for (int r = 0; r < n && e == cudaSuccess; ++r) {
+    const size_t mm = (size_t)b->M[r] * (size_t)b->M[r];
+    e = cudaMalloc(&b->cp[r], 8 * (size_t)b->M[r]);
+    if (e == cudaSuccess) e = f64 ? cudaMalloc(&b->D64[r], 8 * mm) : cudaMalloc(&b->D32[r], 4 * mm);
+    if (e == cudaSuccess && !f64) e = cudaMalloc(&b->R32[r], 4 * mm);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_prop_items, sizeof(PItem) * n);
+  // scratch: G0, G1 per realization, the job lists, the GEMV vectors
+  std::vector<void*> G0(n, nullptr), G1(n, nullptr), u(n, nullptr);
+  const size_t esz = f64 ? 8 : 4;
+  for (int r = 0; r < n && e == cudaSuccess; ++r) {
+    const size_t mm = (size_t)b->M[r] * (size_t)b->M[r];
+    if ((e = cudaMalloc(&G0[r], esz * mm)) == cudaSuccess) tmp.push_back(G0[r]);
+    if (e == cudaSuccess && (e = cudaMalloc(&G1[r], esz * mm)) == cudaSuccess) tmp.push_back(G1[r]);
+    if (e == cudaSuccess && (e = cudaMalloc(&u[r], 16 * (size_t)b->M[r])) == cudaSuccess) tmp.push_back(u[r]);
+  }
+  const size_t sb = std::max(batch_gemm_scratch_bytes(b->M), sizeof(GemvJob) * (size_t)n + 256);
+  void* js = nullptr;
+  if (e == cudaSuccess && (e = cudaMalloc(&js, sb)) == cudaSuccess) tmp.push_back(js);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e == cudaSuccess) e = cudaEventRecord(t0, st);
+  // the three products
+  for (int step = 0; step < 3 && e == cudaSuccess; ++step) {
+    const double alpha = step == 0 ? h / 4.0 : step == 1 ? h / 3.0 : h / 2.0;
+    if (f64) {
+      std::vector<GemmJob<double>> jobs;
+      for (int r = 0; r < n; ++r) {
+        const double* A = b->A64[r];
+        const double* G = step == 0 ? A : step == 1 ? static_cast<double*>(G0[r]) : static_cast<double*>(G1[r]);
+        double* Y = step == 0 ? static_cast<double*>(G0[r]) : step == 1 ? static_cast<double*>(G1[r]) : b->D64[r];
+        jobs.push_back(GemmJob<double>{b->M[r], A, G, step == 2 ? nullptr : A, Y, alpha});
+      }
+      e = batch_gemm<double>(jobs, js, sb, st);
+    } else {
+      std::vector<GemmJob<float>> jobs;
+      for (int r = 0; r < n; ++r) {
+        const float* A = b->A32[r];
+        const float* G = step == 0 ? A : step == 1 ? static_cast<float*>(G0[r]) : static_cast<float*>(G1[r]);
+        float* Y = step == 0 ? static_cast<float*>(G0[r]) : step == 1 ? static_cast<float*>(G1[r]) : b->R32[r];
+        jobs.push_back(GemmJob<float>{b->M[r], A, G, step == 2 ? nullptr : A, Y, (float)alpha});
+      }
+      e = batch_gemm<float>(jobs, js, sb, st);
+    }
+  }
+  // D' = A + R'
+  for (int r = 0; r < n && e == cudaSuccess; ++r) {
+    const int64_t mm = b->M[r] * b->M[r];
+    e = f64 ? add64(b->A64[r], b->D64[r], b->D64[r], mm, st) : add32(b->A32[r], b->R32[r], b->D32[r], mm, st);
+  }
+  // c' = K + (h/2) A (K + (h/3) A (K + (h/4) A K)) in FP64
+  for (int step = 0; step < 3 && e == cudaSuccess; ++step) {
+    const double alpha = step == 0 ? h / 4.0 : step == 1 ? h / 3.0 : h / 2.0;
+    std::vector<GemvJob> jobs;
+    for (int r = 0; r < n; ++r) {
+      double* ua = static_cast<double*>(u[r]);
+      double* ub = ua + b->M[r];
+      const double* x = step == 0 ? b->K[r] : step == 1 ? ua : ub;
+      double* y = step == 0 ? ua : step == 1 ? ub : b->cp[r];
+      jobs.push_back(GemvJob{b->M[r], b->A64[r], x, b->K[r], y, alpha});
+    }
+    e = batch_gemv64(jobs, js, sb, st);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&b->prop_ms, t0, t1);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  scratch_free();
+  if (e != cudaSuccess) {
+    prop_free(b);
+    return e;
+  }
+  b->prop_dt = h;
+  b->prop_prec = b->precision;
+  return cudaSuccess;
+}
+
 int smem_optin() {
   int dev = 0, v = 0;
   cudaGetDevice(&dev);
@@ -365,6 +676,14 @@ SmemLayout pick_layout(int64_t mmax, int C) {
   const size_t cap = (size_t)smem_optin();
   SmemLayout L = layout(mmax, C, true);
   if (L.total > cap) L = layout(mmax, C, false);
+  if (L.total > cap) L.total = 0;
+  return L;
+}
+
+SmemLayoutP pick_layoutP(int64_t mmax, int C, bool f64) {
+  const size_t cap = (size_t)smem_optin();
+  SmemLayoutP L = layoutP(mmax, C, true, f64);
+  if (L.total > cap) L = layoutP(mmax, C, false, f64);
   if (L.total > cap) L.total = 0;
   return L;
 }
@@ -410,6 +729,61 @@ cudaError_t configure(const void* func, int C, size_t smem, int n, cudaStream_t 
   return cudaSuccess;
 }
 
+// The propagator form of batch_run_group (formed for dt beforehand).
+cudaError_t batch_run_group_prop(lb_batch* b, const std::vector<int>& ids, int C, int64_t mmax, int64_t nsteps,
+                                 double dt, int correct_every, cudaStream_t st, float* ms) {
+  const bool f64 = b->precision == LB_FP64;
+  cudaError_t e = batch_form_propagator(b, dt, st);
+  if (e != cudaSuccess) return e;
+  const SmemLayoutP L = pick_layoutP(mmax, C, f64);
+  if (L.total == 0) return cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  e = f64 ? configure((const void*)k_prop_batch64, C, L.total, (int)ids.size(), st, &cfg, attr)
+          : configure((const void*)k_prop_batch, C, L.total, (int)ids.size(), st, &cfg, attr);
+  if (e != cudaSuccess) return e;
+  std::vector<int> ord(ids.begin(), ids.end());
+  std::sort(ord.begin(), ord.end(), [&](int x, int y) { return b->M[x] > b->M[y]; });
+  std::vector<PItem> host(b->count);
+  for (int r = 0; r < b->count; ++r) {
+    if (f64)
+      host[r] = PItem{b->M[r], nullptr, nullptr, b->D64[r], b->cp[r], b->v[r]};
+    else
+      host[r] = PItem{b->M[r], b->D32[r], b->R32[r], correct_every > 0 ? b->A64[r] : nullptr, b->cp[r], b->v[r]};
+  }
+  if ((e = cudaMemcpyAsync(b->d_prop_items, host.data(), sizeof(PItem) * b->count, cudaMemcpyHostToDevice, st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(b->d_order, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice, st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st)) != cudaSuccess) return e;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ms) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+  }
+  const PItem* items = static_cast<const PItem*>(b->d_prop_items);
+  if (f64)
+    e = cudaLaunchKernelEx(&cfg, k_prop_batch64, items, (const int*)b->d_order, (int)ord.size(), b->d_counter, nsteps,
+                           dt, L);
+  else
+    e = cudaLaunchKernelEx(&cfg, k_prop_batch, items, (const int*)b->d_order, (int)ord.size(), b->d_counter, nsteps,
+                           dt, correct_every, L);
+  note_launch(1);
+  if (ms) {
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  if (e != cudaSuccess) return e;
+  // the item list is read by the kernel: keep it until the launch is done
+  return cudaStreamSynchronize(st);
+}
+
 // Run the realizations `ids` (one cluster size C) for nsteps; synchronous when
 // ms is requested.  A cluster size the device cannot place with the needed
 // shared memory fails with cudaErrorInvalidConfiguration before any launch.
@@ -422,6 +796,7 @@ cudaError_t batch_run_group(lb_batch* b, const std::vector<int>& ids, int C, int
   int64_t mmax = 0;
   for (int r : ids) mmax = std::max<int64_t>(mmax, b->M[r]);
   const bool f64 = b->precision == LB_FP64;
+  if (b->form == LB_FORM_PROPAGATOR) return batch_run_group_prop(b, ids, C, mmax, nsteps, dt, correct_every, st, ms);
   const SmemLayout L = f64 ? SmemLayout{} : pick_layout(mmax, C);
   const SmemLayout64 L64 = f64 ? pick_layout64(mmax, C) : SmemLayout64{};
   if ((f64 ? L64.total : L.total) == 0) return cudaErrorInvalidConfiguration;
@@ -616,6 +991,33 @@ int lb_batch_set_precision(lb_batch_t* b, int precision) {
     return LB_EINVAL;
   }
   b->precision = precision;
+  return LB_OK;
+}
+
+int lb_batch_set_form(lb_batch_t* b, int form) {
+  if (!b || (form != LB_FORM_RK4 && form != LB_FORM_PROPAGATOR)) {
+    lbi::set_error("lb_batch_set_form: bad arguments (LB_FORM_RK4 or LB_FORM_PROPAGATOR)");
+    return LB_EINVAL;
+  }
+  b->form = form;
+  return LB_OK;
+}
+
+int lb_batch_form_propagator(lb_batch_t* b, double dt, void* stream, float* ms) {
+  if (!b || !(dt > 0.0) || !std::isfinite(dt)) {
+    lbi::set_error("lb_batch_form_propagator: bad arguments");
+    return LB_EINVAL;
+  }
+  cudaError_t e = lbi::batch_form_propagator(b, dt, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      lbi::set_error("lb_batch_form_propagator: device memory exhausted");
+      return LB_ENOMEM;
+    }
+    return lbi::cuda_fail(e, "lb_batch_form_propagator");
+  }
+  if (ms) *ms = b->prop_ms;
   return LB_OK;
 }
 

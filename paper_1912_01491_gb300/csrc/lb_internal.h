@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "lindblad.h"
 #include "su_n.cuh"
@@ -91,6 +92,38 @@ struct BatchItem {
   double* v;          // M, in/out
 };
 constexpr int kBatchMaxN = 64;
+
+// propagator form (lb_prop.cu): batched Y = B + alpha A G over square
+// M x M row-major matrices (B may be null), one launch over the 64 x 64
+// tiles of every job; and batched FP64 y = K + alpha A x.
+struct GemmTile {
+  int job, ti, tj;
+};
+template <class T>
+struct GemmJob {
+  int64_t M;
+  const T* A;
+  const T* G;
+  const T* B;
+  T* Y;
+  T alpha;
+};
+struct GemvJob {
+  int64_t M;
+  const double* A;
+  const double* x;
+  const double* K;
+  double* y;
+  double alpha;
+};
+// scratch: device memory for the job and tile lists (batch_gemm_scratch_bytes);
+// both calls return after their kernel has finished on st.
+template <class T>
+cudaError_t batch_gemm(const std::vector<GemmJob<T>>& jobs, void* scratch, size_t scratch_bytes, cudaStream_t st);
+size_t batch_gemm_scratch_bytes(const std::vector<int64_t>& Ms);
+cudaError_t batch_gemv64(const std::vector<GemvJob>& jobs, void* scratch, size_t scratch_bytes, cudaStream_t st);
+cudaError_t add32(const float* A, const float* R, float* Y, int64_t n, cudaStream_t st);
+cudaError_t add64(const double* A, const double* R, double* Y, int64_t n, cudaStream_t st);
 // Cluster size the batched kernel uses for dimension M when none is chosen:
 // the smallest of {1, 2, 4, 8, 16} whose slice of the FP32 matrix stays
 // resident in shared memory, else 16.

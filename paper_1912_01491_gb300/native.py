@@ -18,6 +18,7 @@ LB_F, LB_D = 0, 1
 LB_FP64, LB_FP32, LB_BF16 = 0, 1, 2
 LB_SYS_A, LB_SYS_Q, LB_SYS_R, LB_SYS_K = 0, 1, 2, 3
 LB_DENSE, LB_CSR = 0, 1
+LB_FORM_RK4, LB_FORM_PROPAGATOR = 0, 1
 FORMATS = {"dense": LB_DENSE, "csr": LB_CSR}
 LB_A_DENSE, LB_A_LOWRANK = 0, 1
 PHASES = ("alloc", "h2d", "kernels", "d2h", "free")
@@ -121,6 +122,8 @@ def load():
         "lb_batch_tune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp, _vp]),
         "lb_batch_integrate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, _c_i64, _vp,
                                               ctypes.POINTER(ctypes.c_float)]),
+        "lb_batch_set_form": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "lb_batch_form_propagator": (ctypes.c_int, [_vp, ctypes.c_double, _vp, ctypes.POINTER(ctypes.c_float)]),
         "lb_batch_system": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _i64p]),
         "lb_batch_copy_system": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
         "lb_batch_destroy": (ctypes.c_int, [_vp]),
@@ -489,6 +492,17 @@ class Batch:
     def set_precision(self, precision):
         """"fp32" (default) or "fp64" for integrate and tune."""
         _check(load().lb_batch_set_precision(self._h, PRECISIONS[precision]))
+
+    def set_form(self, form):
+        """"rk4" (default: four stages per step) or "propagator" (one product
+        per step with D' = (P(hA) - 1)/h)."""
+        _check(load().lb_batch_set_form(self._h, {"rk4": LB_FORM_RK4, "propagator": LB_FORM_PROPAGATOR}[form]))
+
+    def form_propagator(self, dt, stream=None):
+        """Form D' and c' for step dt now; returns the device time (ms)."""
+        ms = ctypes.c_float()
+        _check(load().lb_batch_form_propagator(self._h, float(dt), _stream(stream), ctypes.byref(ms)))
+        return ms.value
 
     def tune(self, width=6, probe_steps=20, dt=1e-3, stream=None):
         choice = np.zeros(len(self.Ns), np.int32)

@@ -212,3 +212,97 @@ def test_batch_fp64_n10_full_trajectory_vs_oracle():
     b.close()
     got = v.cpu().numpy()
     assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref), choice
+
+
+# ---------------------------------------------------------------- propagator form
+
+@pytest.mark.parametrize("N", [4, 7, 10])
+def test_propagator_fp64_full_trajectory_vs_oracle(N):
+    """The propagator form v <- v + h (D' v + c'), D' = (P(hA) - 1)/h, is one
+    classical RK4 step (Sec. 4 item 3) written as one product: in FP64 it
+    stays within 1e-12 ||v|| of the oracle's stage-by-stage RK4 over 10^4
+    steps of dt = 1e-3."""
+    dt, steps = 1e-3, 10_000
+    H, a = _inputs(N, 1100 + N)
+    lb = lbm()
+    with Oracle(N) as o:
+        h, _ = o.expand(H)
+        A = o.Q(h.real) + o.R(a)
+        K = o.K(a)
+        v0 = o.expand(wl.pure_state(N, N // 2))[0].real
+        ref, _ = ora_rk4(A, K, v0, dt, steps)
+    with lb.Basis(N) as B:
+        hd = B.expand(torch.tensor(H, device="cuda")).real.contiguous()
+    ad = torch.tensor(a, device="cuda")
+    v = torch.tensor(v0, device="cuda")
+    b = lb.Batch([N])
+    b.set(0, ad, hd, v)
+    b.assemble("closed")
+    b.set_precision("fp64")
+    b.set_form("propagator")
+    assert b.form_propagator(dt) >= 0.0
+    b.integrate(dt, steps)
+    torch.cuda.synchronize()
+    b.close()
+    got = v.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("C", [1, 4, 16])
+def test_propagator_fp32_corrected_every_cluster_size(C):
+    """FP32 propagator with the FP64 defect every 50 steps: within the FP32
+    bar of the corrected stage-by-stage form (2e-6 of the FP64 trajectory,
+    2000 steps), and the correction lowers the error."""
+    ens = _Ens([12, 9, 20, 5], 2200, 1e-3, 2000)
+    errs = {}
+    for corr in (0, 50):
+        b = ens.batch()
+        b.set_form("propagator")
+        for r in range(len(ens.Ns)):
+            b.set_cluster(r, C)
+        b.integrate(ens.dt, ens.steps, correct_every=corr)
+        errs[corr] = ens.errors()
+        b.close()
+    assert max(errs[0]) < 1e-5, errs
+    assert max(errs[50]) < 2e-6, errs
+    assert max(errs[50]) < 0.5 * max(errs[0]), errs
+
+
+def test_propagator_alone_equals_in_mix():
+    """A realization integrated by the propagator form gives the same bits
+    alone as inside a batch of mixed N (the clusters share nothing)."""
+    ens = _Ens([11, 6, 17, 30, 11], 2300, 1e-3, 300)
+    b = ens.batch()
+    b.set_form("propagator")
+    b.integrate(ens.dt, ens.steps, correct_every=50)
+    torch.cuda.synchronize()
+    mix = [x.clone() for x in ens.v]
+    b.close()
+    for r in (0, 3):
+        lb = lbm()
+        v = ens.v0[r].clone()
+        one = lb.Batch([ens.Ns[r]])
+        one.set(0, ens.a[r], ens.h[r], v)
+        one.assemble("closed")
+        one.set_form("propagator")
+        one.set_cluster(0, 1)
+        one.integrate(ens.dt, ens.steps, correct_every=50)
+        torch.cuda.synchronize()
+        one.close()
+        # the cluster size of the batch run is the default (1) for every realization
+        assert torch.equal(v, mix[r]), r
+
+
+def test_propagator_reformed_when_dt_changes():
+    """D' depends on h: integrating with another dt forms it again, and the
+    result equals a batch formed for that dt from the start."""
+    ens = _Ens([8, 13], 2400, 2e-3, 400)
+    b = ens.batch()
+    b.set_form("propagator")
+    b.set_precision("fp64")
+    b.form_propagator(1e-3)
+    b.integrate(2e-3, 400)
+    torch.cuda.synchronize()
+    errs = ens.errors()
+    b.close()
+    assert max(errs) < 1e-12, errs
