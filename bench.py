@@ -578,8 +578,36 @@ def form_dense(args, dev, N, steps, seed):
         bt.close()
         pers = {"ms": ms, "steps_per_s": steps / (ms * 1e-3), "cluster": C,
                 "rel_diff_vs_stream_fp64": float(torch.linalg.norm(vp - v64) / torch.linalg.norm(v64))}
+    # propagator form: one product per step with D' = (P(hA) - 1)/h, for 1 and
+    # 16 states at once (reported apart from classical RK4)
+    prop = {}
+    for prec in ("fp64", "fp32"):
+        corr = 50 if prec == "fp32" else 0
+        ev = _events(2)
+        ev[0].record()
+        P = lb.Propagator(A, K, args.dt, precision=prec, nrhs=16)
+        ev[1].record()
+        torch.cuda.synchronize()
+        entry = {"form_ms": ev[0].elapsed_time(ev[1])}
+        for R, n in ((1, steps), (16, max(steps // 10, 100))):
+            V = v0.repeat(R, 1).contiguous()
+            P.step(V, 50, correct_every=corr)  # warm-up
+            V = v0.repeat(R, 1).contiguous()
+            ev = _events(2)
+            ev[0].record()
+            P.step(V, n, correct_every=corr)
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1])
+            entry["states_%d" % R] = {"steps": n, "ms": ms, "steps_per_s": n / (ms * 1e-3),
+                                      "state_steps_per_s": R * n / (ms * 1e-3)}
+            if R == 1 and n == steps:
+                entry["rel_err_vs_rk4_fp64"] = float(torch.linalg.norm(V[0] - v64) / torch.linalg.norm(v64))
+        prop[prec] = entry
+        del P
     B.close()
     return {"N": N, "M": M, "steps": steps, "dt": args.dt, "assembly_ms": sum(kms.values()),
+            "propagator": prop,
             "rk4_fp64_persistent": pers,
             "entries_per_s": M * M / (sum(kms.values()) * 1e-3),
             "rk4_fp64_ms": t64, "rk4_fp64_steps_per_s": steps / (t64 * 1e-3),

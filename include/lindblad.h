@@ -251,6 +251,42 @@ int lb_rk4_dense(int64_t M, int precision, const void *Ap, const float *row_scal
                  double dt, int64_t nsteps, double *snaps, int64_t snap_every,
                  void *work, void *stream);
 
+/* Propagator form of classical RK4 for one system (Sec. 4 item 3): for
+ * dv/dt = A v + K one RK4 step of size h is v <- v + h (D' v + c'), with
+ *   D' = A + (h/2) A (A + (h/3) A (A + (h/4) A A)) = (P(hA) - 1)/h,
+ *   P(x) = 1 + x + x^2/2 + x^3/6 + x^4/24,
+ *   c' = K + (h/2) A (K + (h/3) A (K + (h/4) A K)),
+ * which follows from writing the four stages as polynomials in hA applied to
+ * A v + K.  A step then reads the matrix once (instead of four times), and
+ * several initial states share that read.
+ *
+ * Bytes of device workspace for M, nrhs (1 <= nrhs <= 64) and precision
+ * (LB_FP64 or LB_FP32); 0 for invalid arguments. */
+size_t lb_propagator_workspace_bytes(int64_t M, int nrhs, int precision);
+
+/* Form D' (Dp: M x M, double for LB_FP64, float for LB_FP32) and c' (cp: M
+ * doubles) for step dt from the FP64 A64 and K (device).  LB_FP32 forms D'
+ * from A32 = fl32(A64) with FP32 products and also returns R32 = D' - A32
+ * (M x M floats) for the FP64 correction of lb_propagate; c' is always FP64.
+ * Three matrix products by this library's tiled GEMM kernel.  Synchronous
+ * with respect to stream. */
+int lb_propagator_form(int64_t M, int precision, const double *A64, const float *A32, const double *K, double dt,
+                       void *Dp, float *R32, double *cp, void *work, void *stream);
+
+/* nsteps propagator steps of dt for nrhs states at once: V (device, nrhs x M
+ * doubles, state r in row r) in/out.  Each step is one product of D' with
+ * the block of states rounded to the precision of D' (FP64 or FP32), with
+ * the state kept in FP64.  LB_FP32 with correct_every > 0 (and A64, R32
+ * given): every correct_every steps the FP64 defect (A64 + R32 - D') v_r is
+ * formed for every state and added to c' until the next one (A64 - A32 is
+ * the storage error of A, A32 + R32 - D' the rounding of D').  snaps (may be
+ * NULL): after every snap_every steps a copy of V goes to block
+ * t/snap_every - 1 of snaps ((nsteps/snap_every) x nrhs x M).  dt must be the
+ * step D' was formed for.  work: lb_propagator_workspace_bytes bytes. */
+int lb_propagate(int64_t M, int nrhs, int precision, const void *Dp, const float *R32, const double *A64,
+                 const double *cp, int correct_every, double *V, double dt, int64_t nsteps, double *snaps,
+                 int64_t snap_every, void *work, void *stream);
+
 /* ------------------------------------------------------------------------
  * Sparse models (Sec. 3: sparse H and a Kossakowski matrix of few channels,
  * P = 1 for the paper's sparse model): CSR assembly of A = Q + R and K, and

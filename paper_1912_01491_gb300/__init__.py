@@ -7,5 +7,5 @@ behind the C ABI of ``include/lindblad.h``); ``native`` is its ctypes
 binding.  Build with ``python -m paper_1912_01491_gb300.build``.
 """
 from . import native  # noqa: F401
-from .native import (LBError, Basis, Batch, Csr, Server, System, pack_bf16, pack_fp32,  # noqa: F401
+from .native import (LBError, Basis, Batch, Csr, Propagator, Server, System, pack_bf16, pack_fp32,  # noqa: F401
                      request_bytes, rk4_dense, rk4_workspace, sched_simulate)

@@ -342,6 +342,42 @@ int lb_rk4_dense(int64_t M, int precision, const void* Ap, const float* row_scal
   return LB_OK;
 }
 
+// ------------------------------------------------------------------ propagator form
+
+size_t lb_propagator_workspace_bytes(int64_t M, int nrhs, int precision) {
+  if (M <= 0 || nrhs < 1 || nrhs > 64 || (precision != LB_FP64 && precision != LB_FP32)) return 0;
+  return std::max(lbi::propagator_form_workspace_bytes(M, precision),
+                  lbi::propagate_workspace_bytes(M, nrhs, precision));
+}
+
+int lb_propagator_form(int64_t M, int precision, const double* A64, const float* A32, const double* K, double dt,
+                       void* Dp, float* R32, double* cp, void* work, void* stream) {
+  LB_REQUIRE(M > 0 && A64 && K && Dp && cp && work, "lb_propagator_form: NULL argument or M <= 0");
+  LB_REQUIRE(precision == LB_FP64 || (precision == LB_FP32 && A32 && R32),
+             "lb_propagator_form: precision = %d (LB_FP32 needs A32 and R32)", precision);
+  LB_REQUIRE(dt > 0 && std::isfinite(dt), "lb_propagator_form: bad dt");
+  LB_TRY_CUDA(lbi::propagator_form(M, precision, A64, A32, K, dt, Dp, R32, cp, work,
+                                   lbi::propagator_form_workspace_bytes(M, precision), S(stream)),
+              "lb_propagator_form");
+  return LB_OK;
+}
+
+int lb_propagate(int64_t M, int nrhs, int precision, const void* Dp, const float* R32, const double* A64,
+                 const double* cp, int correct_every, double* V, double dt, int64_t nsteps, double* snaps,
+                 int64_t snap_every, void* work, void* stream) {
+  LB_REQUIRE(M > 0 && Dp && cp && V && work, "lb_propagate: NULL argument or M <= 0");
+  LB_REQUIRE(nrhs >= 1 && nrhs <= 64, "lb_propagate: nrhs = %d outside [1, 64]", nrhs);
+  LB_REQUIRE(precision == LB_FP64 || precision == LB_FP32, "lb_propagate: precision = %d", precision);
+  LB_REQUIRE(nsteps >= 0 && dt > 0 && std::isfinite(dt) && correct_every >= 0, "lb_propagate: bad arguments");
+  LB_REQUIRE(correct_every == 0 || precision == LB_FP64 || (R32 && A64),
+             "lb_propagate: the correction needs A64 and R32");
+  LB_REQUIRE(!snaps || snap_every > 0, "lb_propagate: snaps given without snap_every");
+  LB_TRY_CUDA(lbi::propagate(M, nrhs, precision, Dp, R32, A64, cp, correct_every, V, dt, nsteps, snaps, snap_every,
+                             work, S(stream)),
+              "lb_propagate");
+  return LB_OK;
+}
+
 // ------------------------------------------------------------------ sparse
 
 }  // extern "C"

@@ -124,6 +124,15 @@ size_t batch_gemm_scratch_bytes(const std::vector<int64_t>& Ms);
 cudaError_t batch_gemv64(const std::vector<GemvJob>& jobs, void* scratch, size_t scratch_bytes, cudaStream_t st);
 cudaError_t add32(const float* A, const float* R, float* Y, int64_t n, cudaStream_t st);
 cudaError_t add64(const double* A, const double* R, double* Y, int64_t n, cudaStream_t st);
+// single system (lb_prop.cu): D' (FP64, or FP32 with R32 = D' - A) and c'
+// for step h; then nsteps propagator steps of R states (V: R x M, FP64)
+size_t propagator_form_workspace_bytes(int64_t M, int precision);
+cudaError_t propagator_form(int64_t M, int precision, const double* A64, const float* A32, const double* K, double h,
+                            void* Dp, float* R32, double* cp, void* work, size_t work_bytes, cudaStream_t st);
+size_t propagate_workspace_bytes(int64_t M, int R, int precision);
+cudaError_t propagate(int64_t M, int R, int precision, const void* Dp, const float* R32, const double* A64,
+                      const double* cp, int correct_every, double* V, double h, int64_t nsteps, double* snaps,
+                      int64_t snap_every, void* work, cudaStream_t st);
 // Cluster size the batched kernel uses for dimension M when none is chosen:
 // the smallest of {1, 2, 4, 8, 16} whose slice of the FP32 matrix stays
 // resident in shared memory, else 16.

@@ -90,6 +90,11 @@ def load():
         "lb_pack_fp32": (ctypes.c_int, [_c_i64, _vp, _vp, _vp]),
         "lb_pack_bf16": (ctypes.c_int, [_c_i64, _vp, _vp, _vp, _vp]),
         "lb_rk4_workspace_bytes": (ctypes.c_size_t, [_c_i64]),
+        "lb_propagator_workspace_bytes": (ctypes.c_size_t, [_c_i64, ctypes.c_int, ctypes.c_int]),
+        "lb_propagator_form": (ctypes.c_int, [_c_i64, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp,
+                                              _vp, _vp]),
+        "lb_propagate": (ctypes.c_int, [_c_i64, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int, _vp,
+                                        ctypes.c_double, _c_i64, _vp, _c_i64, _vp, _vp]),
         "lb_rk4_dense": (ctypes.c_int, [_c_i64, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int, _vp, _vp,
                                         ctypes.c_double, _c_i64, _vp, _c_i64, _vp, _vp]),
         "lb_assemble": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(LbKossakowski), ctypes.c_int, ctypes.c_int,
@@ -397,6 +402,50 @@ def rk4_dense(Ap, K, v, dt, nsteps, precision="fp64", scale=None, A64=None, corr
                                float(dt), int(nsteps), _ptr(snaps), int(snap_every), _ptr(work),
                                _stream(stream)))
     return snaps
+
+
+class Propagator:
+    """Propagator form of RK4 for one dense system (lb_propagator_form /
+    lb_propagate): D' = (P(hA) - 1)/h and c' for step dt, then steps of
+    several states at once.  A64, K: device FP64 tensors.  precision "fp64"
+    (D' in FP64) or "fp32" (D' from fl32(A64), kept with D' - A for the FP64
+    correction)."""
+
+    def __init__(self, A64, K, dt, precision="fp64", nrhs=1, stream=None):
+        import torch
+        M = A64.shape[0]
+        self.M, self.dt, self.precision, self.nrhs = M, float(dt), precision, int(nrhs)
+        p = PRECISIONS[precision]
+        n = load().lb_propagator_workspace_bytes(M, self.nrhs, p)
+        if n == 0:
+            raise LBError(LB_EINVAL, "bad propagator arguments")
+        self.work = torch.empty(n, dtype=torch.uint8, device=A64.device)
+        self.A64 = A64
+        self.cp = torch.empty(M, dtype=torch.float64, device=A64.device)
+        if precision == "fp64":
+            self.D = torch.empty((M, M), dtype=torch.float64, device=A64.device)
+            self.R32 = None
+            A32 = None
+        else:
+            A32 = pack_fp32(A64, stream=stream)
+            self.D = torch.empty((M, M), dtype=torch.float32, device=A64.device)
+            self.R32 = torch.empty((M, M), dtype=torch.float32, device=A64.device)
+        _check(load().lb_propagator_form(M, p, _ptr(A64), _ptr(A32), _ptr(K), self.dt, _ptr(self.D), _ptr(self.R32),
+                                         _ptr(self.cp), _ptr(self.work), _stream(stream)))
+
+    def step(self, V, nsteps, correct_every=0, snap_every=0, stream=None):
+        """Advance V (float64 device tensor, nrhs x M or M) in place; returns snapshots or None."""
+        import torch
+        R = 1 if V.dim() == 1 else V.shape[0]
+        assert V.dtype == torch.float64 and V.is_contiguous() and V.numel() == R * self.M and R <= self.nrhs
+        snaps = None
+        if snap_every:
+            snaps = torch.empty((nsteps // snap_every, R, self.M), dtype=torch.float64, device=V.device)
+        _check(load().lb_propagate(self.M, R, PRECISIONS[self.precision], _ptr(self.D), _ptr(self.R32),
+                                   _ptr(self.A64) if correct_every else None, _ptr(self.cp), int(correct_every),
+                                   _ptr(V), self.dt, int(nsteps), _ptr(snaps), int(snap_every), _ptr(self.work),
+                                   _stream(stream)))
+        return snaps
 
 
 class Csr:
