@@ -288,6 +288,46 @@ int lb_propagate(int64_t M, int nrhs, int precision, const void *Dp, const float
                  int64_t snap_every, void *work, void *stream);
 
 /* ------------------------------------------------------------------------
+ * FP64 checks on the device (Sec. 2: rho = 1/N + sum_i v_i F_i is a density
+ * matrix, and the real system has the steady state of the Lindbladian).
+ * --------------------------------------------------------------------- */
+
+/* Bytes of device workspace of lb_steady_state for size M and restart
+ * length `restart` (0: the default, min(M, 1024)); 0 for bad arguments. */
+size_t lb_steady_workspace_bytes(int64_t M, int restart);
+
+/* Steady state of dv/dt = A v + K: solve A v = -K (A = Q + R, M x M FP64
+ * row-major, K: M, both device) by restarted GMRES(m) in FP64 with this
+ * library's kernels (classical Gram-Schmidt with one reorthogonalisation
+ * pass, Givens rotations on the host), m = restart (0: min(M, 1024); the
+ * Krylov basis takes (m + 1) M doubles of workspace), from the initial guess
+ * in v (device, M doubles; overwritten by the solution).  The Hamiltonian
+ * part spreads the spectrum along the imaginary axis while the damping
+ * keeps it near it, so long restarts converge where short ones stall.  Stops when the GMRES residual
+ * estimate is <= tol ||K|| or after max_iter inner iterations;
+ * *rel_residual receives the true relative residual ||K + A v|| / ||K|| of
+ * the returned v (0 with v = 0 for K = 0) and *iterations the inner
+ * iterations used.  Synchronous with respect to
+ * stream.  work: lb_steady_workspace_bytes(M) bytes. */
+int lb_steady_state(int64_t M, const double *A, const double *K, double *v, double tol, int max_iter, int restart,
+                    double *rel_residual, int *iterations, void *work, void *stream);
+
+/* Bytes of device workspace of lb_rho_checks for dimension N. */
+size_t lb_rho_checks_workspace_bytes(int N);
+
+/* For each of the nsnap states in V (device, nsnap x M doubles), rebuild
+ * rho (Eq. (rho)) on the device and write to out (host, nsnap x 3):
+ *   out[3k]     = Tr rho - 1,
+ *   out[3k + 1] = max |rho_jk - conj(rho_kj)|,
+ *   out[3k + 2] = the smallest pivot of the Cholesky factorisation of
+ *                 rho + psd_shift 1 (complex, FP64; positive exactly when
+ *                 the smallest eigenvalue of rho exceeds -psd_shift; the
+ *                 first non-positive pivot ends the factorisation).
+ * Synchronous with respect to stream.  work: lb_rho_checks_workspace_bytes(N). */
+int lb_rho_checks(const lb_basis_t *b, const double *V, int64_t nsnap, double psd_shift, double *out, void *work,
+                  void *stream);
+
+/* ------------------------------------------------------------------------
  * Sparse models (Sec. 3: sparse H and a Kossakowski matrix of few channels,
  * P = 1 for the paper's sparse model): CSR assembly of A = Q + R and K, and
  * RK4 on CSR.

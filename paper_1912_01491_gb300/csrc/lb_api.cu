@@ -378,6 +378,33 @@ int lb_propagate(int64_t M, int nrhs, int precision, const void* Dp, const float
   return LB_OK;
 }
 
+// ------------------------------------------------------------------ FP64 checks
+
+size_t lb_steady_workspace_bytes(int64_t M, int restart) {
+  return M > 0 && restart >= 0 ? lbi::steady_workspace_bytes(M, restart) : 0;
+}
+
+int lb_steady_state(int64_t M, const double* A, const double* K, double* v, double tol, int max_iter, int restart,
+                    double* rel_residual, int* iterations, void* work, void* stream) {
+  LB_REQUIRE(M > 0 && A && K && v && work && rel_residual && iterations, "lb_steady_state: NULL argument");
+  LB_REQUIRE(tol > 0 && std::isfinite(tol) && max_iter >= 1 && restart >= 0,
+             "lb_steady_state: bad tol, max_iter or restart");
+  LB_TRY_CUDA(lbi::steady_state(M, A, K, v, tol, max_iter, restart, rel_residual, iterations, work, S(stream)),
+              "lb_steady_state");
+  return LB_OK;
+}
+
+size_t lb_rho_checks_workspace_bytes(int N) { return N >= 2 ? lbi::rho_checks_workspace_bytes(N) : 0; }
+
+int lb_rho_checks(const lb_basis_t* b, const double* V, int64_t nsnap, double psd_shift, double* out, void* work,
+                  void* stream) {
+  LB_REQUIRE(b && V && out && work && nsnap >= 0, "lb_rho_checks: NULL argument or nsnap < 0");
+  LB_REQUIRE(psd_shift >= 0 && std::isfinite(psd_shift), "lb_rho_checks: bad psd_shift");
+  LB_REQUIRE(b->N <= 4096, "lb_rho_checks: N too large");
+  LB_TRY_CUDA(lbi::rho_checks(b->view(), V, nsnap, psd_shift, out, work, S(stream)), "lb_rho_checks");
+  return LB_OK;
+}
+
 // ------------------------------------------------------------------ sparse
 
 }  // extern "C"

@@ -129,6 +129,13 @@ cudaError_t add64(const double* A, const double* R, double* Y, int64_t n, cudaSt
 size_t propagator_form_workspace_bytes(int64_t M, int precision);
 cudaError_t propagator_form(int64_t M, int precision, const double* A64, const float* A32, const double* K, double h,
                             void* Dp, float* R32, double* cp, void* work, size_t work_bytes, cudaStream_t st);
+// FP64 checks (lb_steady.cu)
+size_t steady_workspace_bytes(int64_t M, int restart);
+cudaError_t steady_state(int64_t M, const double* A, const double* K, double* v, double tol, int max_iter,
+                         int restart, double* rel_res, int* iters, void* work, cudaStream_t st);
+size_t rho_checks_workspace_bytes(int N);
+cudaError_t rho_checks(const lb::BasisView& B, const double* V, int64_t nsnap, double delta, double* out_host,
+                       void* work, cudaStream_t st);
 size_t propagate_workspace_bytes(int64_t M, int R, int precision);
 cudaError_t propagate(int64_t M, int R, int precision, const void* Dp, const float* R32, const double* A64,
                       const double* cp, int correct_every, double* V, double h, int64_t nsteps, double* snaps,

@@ -90,6 +90,11 @@ def load():
         "lb_pack_fp32": (ctypes.c_int, [_c_i64, _vp, _vp, _vp]),
         "lb_pack_bf16": (ctypes.c_int, [_c_i64, _vp, _vp, _vp, _vp]),
         "lb_rk4_workspace_bytes": (ctypes.c_size_t, [_c_i64]),
+        "lb_steady_workspace_bytes": (ctypes.c_size_t, [_c_i64, ctypes.c_int]),
+        "lb_steady_state": (ctypes.c_int, [_c_i64, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp,
+                                           ctypes.POINTER(ctypes.c_int), _vp, _vp]),
+        "lb_rho_checks_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+        "lb_rho_checks": (ctypes.c_int, [_vp, _vp, _c_i64, ctypes.c_double, _vp, _vp, _vp]),
         "lb_propagator_workspace_bytes": (ctypes.c_size_t, [_c_i64, ctypes.c_int, ctypes.c_int]),
         "lb_propagator_form": (ctypes.c_int, [_c_i64, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp,
                                               _vp, _vp]),
@@ -402,6 +407,32 @@ def rk4_dense(Ap, K, v, dt, nsteps, precision="fp64", scale=None, A64=None, corr
                                float(dt), int(nsteps), _ptr(snaps), int(snap_every), _ptr(work),
                                _stream(stream)))
     return snaps
+
+
+def steady_state(A, K, v=None, tol=1e-12, max_iter=2000, restart=0, stream=None):
+    """FP64 solve of A v = -K on the device (restarted GMRES, lb_steady_state).
+    Returns (v, true relative residual, iterations)."""
+    import torch
+    M = A.shape[0]
+    v = torch.zeros(M, dtype=torch.float64, device=A.device) if v is None else v
+    work = torch.empty(load().lb_steady_workspace_bytes(M, int(restart)), dtype=torch.uint8, device=A.device)
+    res, it = ctypes.c_double(), ctypes.c_int()
+    _check(load().lb_steady_state(M, _ptr(A), _ptr(K), _ptr(v), float(tol), int(max_iter), int(restart),
+                                  ctypes.byref(res), ctypes.byref(it), _ptr(work), _stream(stream)))
+    return v, res.value, it.value
+
+
+def rho_checks(basis, V, psd_shift=1e-10, stream=None):
+    """(Tr rho - 1, max |rho - rho^dagger|, smallest Cholesky pivot of rho +
+    psd_shift 1) for each state (rows of V), computed on the device."""
+    import torch
+    V = V.reshape(-1, basis.M)
+    assert V.dtype == torch.float64 and V.is_contiguous()
+    out = np.zeros((V.shape[0], 3))
+    work = torch.empty(load().lb_rho_checks_workspace_bytes(basis.N), dtype=torch.uint8, device=V.device)
+    _check(load().lb_rho_checks(basis.handle, _ptr(V), V.shape[0], float(psd_shift), _ptr(out), _ptr(work),
+                                _stream(stream)))
+    return out
 
 
 class Propagator:

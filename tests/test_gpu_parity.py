@@ -583,3 +583,63 @@ def test_propagator_multistate_fp32_corrected():
     assert errs[50] < 0.5 * errs[0], errs
     with pytest.raises(lb.LBError):
         lb.Propagator(g["A"], g["K"], dt, precision="fp64", nrhs=65)
+
+
+@pytest.mark.parametrize("N", [5, 12, 30])
+def test_steady_state_against_oracle_solve(N):
+    """FP64 GMRES on the device for (Q + R) v* = -K (Sec. 2: the steady
+    state of the real system) against numpy's dense solve of the oracle's
+    A and K: true relative residual <= 1e-11, solution within 1e-8, and the
+    rebuilt rho* is a density matrix (trace 1, Hermitian, PSD within 1e-10)."""
+    H, a = _case(N, 1400 + N)
+    lb = lbm()
+    with lb.Basis(N) as B, Oracle(N) as o:
+        A, K = _oracle_system(o, H, a)
+        ref = np.linalg.solve(A, -K)
+        g = B.assemble_dense(torch.tensor(a, device="cuda"),
+                             h=B.expand(torch.tensor(H, device="cuda")).real.contiguous())
+        v, res, it = lb.steady_state(g["A"], g["K"], tol=1e-13, max_iter=5000)
+        torch.cuda.synchronize()
+        assert res <= 1e-11, (res, it)
+        vh = v.cpu().numpy()
+        assert np.linalg.norm(vh - ref) <= 1e-8 * np.linalg.norm(ref), (res, it)
+        chk = lb.rho_checks(B, v.contiguous(), psd_shift=1e-10)[0]
+        rho = o.rho(vh)
+    assert abs(chk[0]) < 1e-13 and chk[1] < 1e-13 and chk[2] > 0.0, chk
+    assert abs(np.trace(rho) - 1) < 1e-13 and np.linalg.eigvalsh(rho).min() > -1e-10
+
+
+def test_steady_state_degenerate_inputs():
+    """K = 0 (a = gamma 1): v* = 0 with zero residual and no iteration."""
+    N = 4
+    M = N * N - 1
+    lb = lbm()
+    with lb.Basis(N) as B:
+        g = B.assemble_dense(torch.eye(M, dtype=torch.complex128, device="cuda") * 0.3)
+        v = torch.ones(M, dtype=torch.float64, device="cuda")
+        v, res, it = lb.steady_state(g["A"], g["K"], v=v)
+        torch.cuda.synchronize()
+        assert res == 0.0 and it == 0 and v.abs().max().item() == 0.0
+
+
+def test_rho_checks_against_oracle():
+    """Trace, Hermiticity and the shifted-Cholesky PSD test of rho on the
+    device, on states with known answers: snapshots of an RK4 trajectory
+    (density matrices), a pure state (PSD, eigenvalue 0 present) and a
+    state scaled out of the PSD cone."""
+    N = 6
+    H, a = _case(N, 606)
+    lb = lbm()
+    with lb.Basis(N) as B, Oracle(N) as o:
+        A, K = _oracle_system(o, H, a)
+        v0 = o.expand(wl.pure_state(N, 2))[0].real
+        _, snaps = ora_rk4(A, K, v0, 1e-2, 400, snap_every=100)
+        states = np.concatenate([snaps, v0[None, :], -3.0 * v0[None, :]])
+        out = lb.rho_checks(B, torch.tensor(states, device="cuda"), psd_shift=1e-10)
+        for k in range(len(states)):
+            rho = o.rho(states[k])
+            assert abs(out[k, 0] - (np.trace(rho).real - 1.0)) < 1e-14
+            assert out[k, 1] < 1e-15
+        lam_min = [np.linalg.eigvalsh(o.rho(x)).min() for x in states]
+    assert all(out[k, 2] > 0.0 for k in range(len(snaps) + 1)), out
+    assert lam_min[-1] < -1e-3 and out[-1, 2] <= 0.0, (lam_min[-1], out[-1])
