@@ -13,8 +13,9 @@ Three independent routes to the same numbers (Meyerov et al., Sec. 2):
   matrix-unit basis, projected onto the SU(N) basis; never touches f or d.
 * ``Oracle``  -- O3: the paper's formulas, Eqs. (02)-(09), in plain C loops
   (``lb_oracle.c``), with f and d obtained by multiplying sparse basis
-  matrices (not by closed-form rules).  Plus classical RK4.
+  matrices (not by closed-form rules).  Plus classical RK4 (dense, CSR, and
+  with the time-dependent Q(t) = Q0 + eps(t) Q1 of the rocked dimer).
 """
 from .core import (Oracle, build_library, load_library, lowrank_csr, num_threads, rk4_csr,  # noqa: F401
-                   rk4_dense, set_threads)
+                   rk4_dense, rk4_dense_td, set_threads)
 from . import brute, superop  # noqa: F401

@@ -76,6 +76,8 @@ def load_library():
         lib.ora_free.argtypes = [ctypes.c_void_p]
         lib.ora_rk4_dense.argtypes = [_i64, _dp, _dp, _dp, ctypes.c_double, _i64, _i64, _dp, _dp]
         lib.ora_rk4_csr.argtypes = [_i64, _i64p, _i32p, _dp, _dp, _dp, ctypes.c_double, _i64, _dp]
+        lib.ora_rk4_dense_td.argtypes = [_i64, _dp, _dp, _dp, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                         ctypes.c_double, _dp, ctypes.c_double, _i64, _dp]
         lib.ora_num_threads.restype = ctypes.c_int
         lib.ora_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -350,4 +352,22 @@ def rk4_csr(rowptr, col, val, K, v0, dt, nsteps):
     vout = np.zeros(len(v0))
     lib.ora_rk4_csr(len(v0), _p(rowptr, _i64p), _p(col, _i32p), _p(val),
                     _p(K) if K is not None else None, _p(v0), float(dt), int(nsteps), _p(vout))
+    return vout
+
+
+def rk4_dense_td(A0, Q1, K, v0, dt, nsteps, seg_start, seg_eps, period, t0=0.0):
+    """Classical RK4 for dv/dt = (A0 + eps(t) Q1) v + K with eps periodic and
+    piecewise constant (eps = seg_eps[k] on [seg_start[k], seg_start[k+1])
+    of each period), each stage at its own time (the end stages taken 1e-6 dt
+    inside the step)."""
+    lib = load_library()
+    A0 = np.ascontiguousarray(A0, np.float64)
+    Q1 = np.ascontiguousarray(Q1, np.float64)
+    K = np.ascontiguousarray(K, np.float64)
+    v0 = np.ascontiguousarray(v0, np.float64)
+    ss = np.ascontiguousarray(seg_start, np.float64)
+    se = np.ascontiguousarray(seg_eps, np.float64)
+    vout = np.zeros(len(v0))
+    lib.ora_rk4_dense_td(len(v0), _p(A0), _p(Q1), _p(K), len(ss), _p(ss), _p(se), float(period), float(t0),
+                         _p(v0), float(dt), int(nsteps), _p(vout))
     return vout

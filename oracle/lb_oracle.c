@@ -1111,6 +1111,62 @@ void ora_rk4_csr(int64_t M, const int64_t *rp, const int32_t *ci, const double *
     free(v); free(x); free(k1); free(k2); free(k3); free(k4);
 }
 
+/*
+ * Classical RK4 for the time-dependent system dv/dt = (A0 + eps(t) Q1) v + K
+ * (Eq. (04) with Q(t) = Q0 + eps(t) Q1, Sec. 3: the rocked dimer): every
+ * stage uses eps at its own time, the stages at the ends of the step taken
+ * just inside it (t + 1e-6 dt, t + dt/2, t + dt/2, t + dt - 1e-6 dt), so
+ * that a step lying between two switches of eps sees one value in all four
+ * stages whatever the rounding of its end times.  eps is periodic with
+ * period T: eps(t) = seg_eps[k] for (t mod T) in [seg_start[k],
+ * seg_start[k + 1]) (seg_start[0] = 0, the last segment ends at T).  A0, Q1
+ * dense M x M; nsteps steps from time t0.
+ */
+static double eps_at(double t, int nseg, const double *seg_start, const double *seg_eps, double T) {
+    double u = fmod(t, T);
+    if (u < 0) u += T;
+    int k = 0;
+    while (k + 1 < nseg && u >= seg_start[k + 1]) ++k;
+    return seg_eps[k];
+}
+
+static void td_rhs(int64_t M, const double *A0, const double *Q1, double eps, const double *K,
+                   const double *x, double *y) {
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < M; ++s) {
+        const double *a = A0 + (size_t)s * M, *q = Q1 + (size_t)s * M;
+        double acc = 0;
+        for (int64_t n = 0; n < M; ++n) acc += (a[n] + eps * q[n]) * x[n];
+        y[s] = acc + K[s];
+    }
+}
+
+void ora_rk4_dense_td(int64_t M, const double *A0, const double *Q1, const double *K, int nseg,
+                      const double *seg_start, const double *seg_eps, double T, double t0,
+                      const double *v0, double dt, int64_t nsteps, double *vout) {
+    double *v = (double *)malloc(sizeof(double) * (size_t)M);
+    double *x = (double *)malloc(sizeof(double) * (size_t)M);
+    double *k1 = (double *)malloc(sizeof(double) * (size_t)M);
+    double *k2 = (double *)malloc(sizeof(double) * (size_t)M);
+    double *k3 = (double *)malloc(sizeof(double) * (size_t)M);
+    double *k4 = (double *)malloc(sizeof(double) * (size_t)M);
+    memcpy(v, v0, sizeof(double) * (size_t)M);
+    for (int64_t n = 0; n < nsteps; ++n) {
+        const double t = t0 + (double)n * dt;
+        td_rhs(M, A0, Q1, eps_at(t + 1e-6 * dt, nseg, seg_start, seg_eps, T), K, v, k1);
+        for (int64_t i = 0; i < M; ++i) x[i] = v[i] + 0.5 * dt * k1[i];
+        td_rhs(M, A0, Q1, eps_at(t + 0.5 * dt, nseg, seg_start, seg_eps, T), K, x, k2);
+        for (int64_t i = 0; i < M; ++i) x[i] = v[i] + 0.5 * dt * k2[i];
+        td_rhs(M, A0, Q1, eps_at(t + 0.5 * dt, nseg, seg_start, seg_eps, T), K, x, k3);
+        for (int64_t i = 0; i < M; ++i) x[i] = v[i] + dt * k3[i];
+        td_rhs(M, A0, Q1, eps_at(t + dt - 1e-6 * dt, nseg, seg_start, seg_eps, T), K, x, k4);
+        for (int64_t i = 0; i < M; ++i)
+            v[i] += dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+    }
+    memcpy(vout, v, sizeof(double) * (size_t)M);
+    free(v); free(x); free(k1); free(k2); free(k3); free(k4);
+}
+
 int ora_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -402,3 +402,84 @@ def test_k_on_f_equals_k(N):
         with pytest.raises(ValueError):
             o.K_on_f(np.zeros(3))
     assert np.abs(Kp - K).max() <= 1e-15 * max(np.abs(K).max(), 1.0)
+
+
+def _dimer_system(o, N):
+    H0, H1, L, rate, eps = wl.dimer_model(N)
+    h0, _ = o.expand(H0)
+    h1, _ = o.expand(H1)
+    l, _ = o.expand(L)
+    a = rate * np.outer(l, l.conj())
+    A0 = o.Q(h0.real) + o.R(a)
+    Q1 = o.Q(h1.real)
+    K = o.K(a)
+    return A0, Q1, K, eps
+
+
+def _exact_piecewise(A0, Q1, K, v0, eps, T, t_end):
+    """Exact solution of dv/dt = (A0 + eps(t) Q1) v + K for eps = eps[0] on
+    [0, T/2) and eps[1] on [T/2, T) of each period: the affine propagators
+    exp of the augmented matrix, segment by segment."""
+    M = len(v0)
+    x = np.concatenate([v0, [1.0]])
+    t = 0.0
+    while t < t_end - 1e-12:
+        u = t % T
+        k, end = (0, t - u + T / 2) if u < T / 2 - 1e-12 else (1, t - u + T)
+        d = min(end, t_end) - t
+        B = np.zeros((M + 1, M + 1))
+        B[:M, :M] = A0 + eps[k] * Q1
+        B[:M, M] = K
+        x = scipy.linalg.expm(B * d) @ x
+        t += d
+    return x[:M]
+
+
+def test_rk4_td_fourth_order_against_piecewise_exact():
+    """The time-dependent RK4 of the oracle (Q(t) = Q0 + eps(t) Q1, each
+    stage at its own time) on the rocked dimer (Sec. 3, Eqs. (10)-(11))
+    converges at order 4 to the exact piecewise-affine propagation over one
+    period, the switch of eps at T/2 falling on a step boundary."""
+    from oracle import rk4_dense_td
+    N = 4
+    T = 2.0 * math.pi
+    with Oracle(N) as o:
+        A0, Q1, K, eps = _dimer_system(o, N)
+        v0 = o.expand(wl.pure_state(N, 0))[0].real
+    ref = _exact_piecewise(A0, Q1, K, v0, eps, T, T)
+    errs = []
+    for steps in (400, 800, 1600):
+        v = rk4_dense_td(A0, Q1, K, v0, T / steps, steps, [0.0, T / 2], list(eps), T)
+        errs.append(np.abs(v - ref).max())
+    assert errs[2] < 1e-7
+    assert errs[0] / errs[1] > 14 and errs[1] / errs[2] > 14, errs
+
+
+def test_rk4_td_constant_eps_is_rk4():
+    """With eps constant the time-dependent RK4 is the autonomous RK4 of
+    A0 + eps Q1 (same sums, same order)."""
+    from oracle import rk4_dense_td
+    N = 5
+    with Oracle(N) as o:
+        A0, Q1, K, eps = _dimer_system(o, N)
+        v0 = o.expand(wl.pure_state(N, 2))[0].real
+    v_td = rk4_dense_td(A0, Q1, K, v0, 1e-3, 500, [0.0], [0.7], 1.0)
+    v, _ = rk4_dense(A0 + 0.7 * Q1, K, v0, 1e-3, 500)
+    assert np.abs(v_td - v).max() <= 1e-15 * np.abs(v).max()
+
+
+def test_dimer_trajectory_is_a_density_matrix():
+    """Over one period of the rocked dimer the trace stays 1 and rho stays
+    Hermitian and positive semidefinite (within 1e-10)."""
+    from oracle import rk4_dense_td
+    N = 6
+    T = 2.0 * math.pi
+    with Oracle(N) as o:
+        A0, Q1, K, eps = _dimer_system(o, N)
+        v = o.expand(wl.pure_state(N, N - 1))[0].real
+        for k in range(4):  # quarter periods
+            v = rk4_dense_td(A0, Q1, K, v, T / 4000, 1000, [0.0, T / 2], list(eps), T, t0=k * T / 4)
+            rho = o.rho(v)
+            assert abs(np.trace(rho) - 1) < 1e-13
+            assert np.allclose(rho, rho.conj().T, atol=1e-15)
+            assert np.linalg.eigvalsh(rho).min() > -1e-10

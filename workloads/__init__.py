@@ -139,3 +139,29 @@ def serving_trace(count, seed, rate, Ns=(20, 50, 100, 150, 200)):
     g = rng(seed)
     gaps = g.exponential(1.0 / rate, size=count)
     return np.cumsum(gaps), g.choice(np.asarray(Ns), size=count)
+
+
+def dimer_model(N, J=-1.0, U=2.2, E=-1.0, A=-1.5, gamma=0.1):
+    """The periodically rocked Bose-Hubbard dimer of Sec. 3 (Eqs. (10), (11))
+    with N - 1 bosons: Hilbert-space dimension N, basis |n> with n bosons on
+    site 1 and N - 1 - n on site 2.  Returns (H0, H1, L, rate, eps) with
+    H(t) = H0 + eps(t) H1, H0 = -J (b1^+ b2 + b1 b2^+) + 2U/(N-1) sum_j
+    n_j (n_j - 1), H1 = n2 - n1, the jump operator L = (b1^+ + b2^+)(b1 - b2)
+    (the printed L is Hermitian, which contradicts the non-Hermitian L the
+    text describes; this is the operator that recycles the out-of-phase mode
+    into the in-phase one), rate = gamma / (N - 1), and eps = (E + A, E - A),
+    the drive on the first and second half of the period T = 2 pi
+    (Theta = +1 on [0, T/2), -1 on [T/2, T))."""
+    n = np.arange(N, dtype=np.float64)
+    c = np.sqrt((n[:-1] + 1.0) * (N - 1.0 - n[:-1]))  # <n+1| b1^+ b2 |n>
+    hop = np.zeros((N, N))
+    hop[np.arange(1, N), np.arange(N - 1)] = c          # b1^+ b2
+    hop = hop + hop.T                                   # + b1 b2^+
+    n1, n2 = n, N - 1.0 - n
+    inter = 2.0 * U / (N - 1.0) * (n1 * (n1 - 1.0) + n2 * (n2 - 1.0))
+    H0 = -J * hop + np.diag(inter)
+    H1 = np.diag(n2 - n1)
+    # (b1^+ + b2^+)(b1 - b2) = n1 - n2 - b1^+ b2 + b2^+ b1
+    L = np.diag(n1 - n2) - np.tril(hop, -1) + np.triu(hop, 1)
+    return (H0.astype(np.complex128), H1.astype(np.complex128), L.astype(np.complex128),
+            gamma / (N - 1.0), (E + A, E - A))
