@@ -66,7 +66,9 @@ def parse():
     p.add_argument("--serve-budget-gb", type=float, default=96.0)
     p.add_argument("--sparse-n", type=int, default=2000)
     p.add_argument("--sparse-steps", type=int, default=200)
-    p.add_argument("--only", default=None, choices=["dense_small", "sparse", "batched", "serving"],
+    p.add_argument("--dimer-n", type=int, default=400)
+    p.add_argument("--dimer-steps", type=int, default=20000)
+    p.add_argument("--only", default=None, choices=["dense_small", "sparse", "dimer", "batched", "serving"],
                    help="run one of the other workloads alone and print its JSON (profiling aid)")
     return p.parse_args()
 
@@ -550,6 +552,7 @@ def run_forms(args, dev, a200=None):
         out["dense_n50"] = form_dense(args, dev, 50, 10_000, 1050)
     if not args.no_sparse:
         out["sparse_ladder"] = form_sparse(args, dev)
+        out["dimer"] = form_dimer(args, dev)
     if not args.no_batched:
         out["batched"] = form_batched(args, dev)
     if not args.no_serving:
@@ -700,6 +703,54 @@ def form_sparse(args, dev):
                              "algorithmic_bytes_per_step": step_bytes["fp32"],
                              "fp64_achieved_gbs": gbs["fp64"]},
             "note": "FP32 row includes one FP64 correction SpMV every 50 steps in its time"}
+
+
+def form_dimer(args, dev):
+    """The periodically rocked dimer of Sec. 3 (Eqs. (10)-(11)) as the paper
+    integrates it: N = dimer_n, CSR A0 = Q0 + R and Q1, FP64 RK4 over one
+    period T = 2 pi with dimer_steps steps, eps switching at T/2; the
+    density-matrix checks of the final state on the device."""
+    import math
+
+    import torch
+
+    import paper_1912_01491_gb300 as lb
+    import workloads as wl
+    N, steps = args.dimer_n, args.dimer_steps
+    M = N * N - 1
+    T = 2.0 * math.pi
+    H0, H1, L, rate, eps = wl.dimer_model(N)
+    B = lb.Basis(N)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    l = B.expand(torch.tensor(L, device=dev))
+    nz = torch.nonzero(l.abs() > 0).flatten()
+    A0 = lb.Csr(B, h=B.expand(torch.tensor(H0, device=dev)).real.contiguous(), channels=[(rate, nz, l[nz])])
+    Q1 = lb.Csr(B, h=B.expand(torch.tensor(H1, device=dev)).real.contiguous(), channels=())
+    torch.cuda.synchronize()
+    asm_s = time.perf_counter() - t0
+    rho0 = torch.zeros((N, N), dtype=torch.complex128, device=dev)
+    rho0[N - 1, N - 1] = 1.0
+    v = B.expand(rho0).real.contiguous()
+    work = lb.rk4_workspace(M, dev)
+    A0.rk4_td(Q1, v.clone(), T / steps, 10, [0.0, T / 2], list(eps), T, work=work)  # warm-up
+    ev = _events(2)
+    ev[0].record()
+    A0.rk4_td(Q1, v, T / steps, steps, [0.0, T / 2], list(eps), T, work=work)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    chk = lb.rho_checks(B, v, psd_shift=1e-10)[0]
+    out = {"N": N, "M": M, "nnz_A0": A0.nnz, "nnz_Q1": Q1.nnz, "steps_per_period": steps, "period": T,
+           "eps": list(eps), "assembly_s": asm_s, "period_s": ms * 1e-3, "steps_per_s": steps / (ms * 1e-3),
+           "rho_final": {"trace_minus_1": float(chk[0]), "hermiticity": float(chk[1]),
+                         "min_cholesky_pivot_shift_1e-10": float(chk[2])},
+           "note": "FP64 CSR RK4 with Q(t) = Q0 + eps(t) Q1, two SpMVs per stage fused in one kernel; "
+                   "rho0 = |N-1><N-1| (all bosons on site 1)"}
+    A0.close()
+    Q1.close()
+    B.close()
+    return out
 
 
 def form_batched(args, dev):
@@ -1042,6 +1093,8 @@ def run_only(args):
                "dense_n50": form_dense(args, dev, 50, 10_000, 1050)}
     elif args.only == "sparse":
         out = {"sparse_ladder": form_sparse(args, dev)}
+    elif args.only == "dimer":
+        out = {"dimer": form_dimer(args, dev)}
     elif args.only == "batched":
         out = {"batched": form_batched(args, dev)}
     else:

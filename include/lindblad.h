@@ -374,6 +374,22 @@ int lb_csr_copy(const lb_csr_t *c, int64_t *rowptr, int32_t *col, double *val, d
 int lb_rk4_csr(const lb_csr_t *c, int precision, int correct_every, double *v, double dt,
                int64_t nsteps, void *work, void *stream);
 
+/* RK4 with a time-dependent Hamiltonian H(t) = H0 + eps(t) H1 (Sec. 3: the
+ * periodically rocked dimer, Eq. (10), where eps(t) = E + A Theta(t)):
+ * dv/dt = (A0 + eps(t) Q1) v + K with A0 = Q0 + R and K from the CSR system
+ * A0 and Q1 the CSR matrix of Eq. (07) for H1 (e.g. lb_assemble_lowrank_csr
+ * with h1 and no channels; its K is not used).  eps is periodic with period
+ * `period` and piecewise constant: eps(t) = seg_eps[k] for (t mod period) in
+ * [seg_start[k], seg_start[k + 1]) (seg_start[0] = 0, increasing; the last
+ * segment ends at period).  Classical RK4 from time t0, each stage with eps
+ * at its own time, the stages at the ends of a step taken 1e-6 dt inside it
+ * (a step lying between two switches of eps sees one value in all four
+ * stages); FP64.  v (device, M doubles) in/out; work:
+ * lb_rk4_workspace_bytes(M).  Asynchronous on stream (seg arrays are host
+ * memory, read during the call). */
+int lb_rk4_csr_td(const lb_csr_t *A0, const lb_csr_t *Q1, int nseg, const double *seg_start, const double *seg_eps,
+                  double period, double t0, double *v, double dt, int64_t nsteps, void *work, void *stream);
+
 /* ------------------------------------------------------------------------
  * a9 -- batched form: many independent realizations of mixed N (the
  * ensemble sampling of Sec. 6, one sample per processor group), assembled

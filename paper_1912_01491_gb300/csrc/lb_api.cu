@@ -513,6 +513,29 @@ int lb_rk4_csr(const lb_csr_t* c, int precision, int correct_every, double* v, d
 
 }  // extern "C"
 
+extern "C" {
+
+int lb_rk4_csr_td(const lb_csr_t* A0, const lb_csr_t* Q1, int nseg, const double* seg_start, const double* seg_eps,
+                  double period, double t0, double* v, double dt, int64_t nsteps, void* work, void* stream) {
+  LB_REQUIRE(A0 && Q1 && v && work && seg_start && seg_eps, "lb_rk4_csr_td: NULL argument");
+  LB_REQUIRE(A0->m.M == Q1->m.M, "lb_rk4_csr_td: A0 and Q1 differ in size");
+  LB_REQUIRE(nseg >= 1 && nseg <= 1024 && seg_start[0] == 0.0, "lb_rk4_csr_td: nseg = %d, seg_start[0] = %g", nseg,
+             seg_start[0]);
+  LB_REQUIRE(period > 0 && std::isfinite(period) && std::isfinite(t0), "lb_rk4_csr_td: bad period or t0");
+  for (int k = 0; k < nseg; ++k) {
+    LB_REQUIRE(std::isfinite(seg_eps[k]), "lb_rk4_csr_td: seg_eps[%d] not finite", k);
+    LB_REQUIRE(k == 0 || (seg_start[k] > seg_start[k - 1] && seg_start[k] < period),
+               "lb_rk4_csr_td: seg_start must increase within [0, period)");
+  }
+  LB_REQUIRE(nsteps >= 0 && dt > 0 && std::isfinite(dt), "lb_rk4_csr_td: bad step count or dt");
+  LB_TRY_CUDA(lbi::rk4_csr_td(A0->m.M, A0->m.rowptr, A0->m.col, A0->m.val, Q1->m.rowptr, Q1->m.col, Q1->m.val,
+                              A0->m.K, nseg, seg_start, seg_eps, period, t0, v, dt, nsteps, work, S(stream)),
+              "lb_rk4_csr_td");
+  return LB_OK;
+}
+
+}  // extern "C"
+
 // ------------------------------------------------------------------ host API
 
 namespace {

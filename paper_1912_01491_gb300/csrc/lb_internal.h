@@ -73,6 +73,10 @@ cudaError_t rk4_csr(int64_t M, int precision, const int64_t* rowptr, const int32
                     const double* val64, int correct_every, const double* K, double* v, double dt, int64_t nsteps,
                     void* work, cudaStream_t st);
 cudaError_t to_f32(int64_t n, const double* x, float* y, cudaStream_t st);
+cudaError_t rk4_csr_td(int64_t M, const int64_t* rowptr, const int32_t* col, const double* val,
+                       const int64_t* rowptr1, const int32_t* col1, const double* val1, const double* K, int nseg,
+                       const double* seg_start, const double* seg_eps, double T, double t0, double* v, double dt,
+                       int64_t nsteps, void* work, cudaStream_t st);
 
 // RK4 (lb_rk4.cu)
 cudaError_t pack_fp32(int64_t M, const double* A, float* A32, cudaStream_t st);

@@ -19,6 +19,8 @@
 // c = (A64 - A_lp) v at the current v, added to K until the next one.
 #include <cuda_bf16.h>
 
+#include <cmath>
+
 #include "lb_internal.h"
 
 namespace {
@@ -254,6 +256,44 @@ __global__ void __launch_bounds__(256)
     xn32[s] = (float)nx;
 }
 
+// Time-dependent form (Sec. 3, the rocked dimer: Q(t) = Q0 + eps(t) Q1): the
+// stage of k_stage_csr<LB_FP64, STAGE> for A0 = Q0 + R plus eps Q1 x, both
+// row sums formed before the epilogue.  One thread per row.
+template <int STAGE>
+__global__ void __launch_bounds__(256)
+    k_stage_csr_td(int64_t M, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                   const double* __restrict__ val, const int64_t* __restrict__ rowptr1,
+                   const int32_t* __restrict__ col1, const double* __restrict__ val1, double eps,
+                   const double* __restrict__ K, const double* __restrict__ x, double* __restrict__ xn,
+                   double* __restrict__ acc, double* __restrict__ v, double h) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  const double kf = __ldcs(K + s), vs = __ldcs(v + s);
+  const double ac = STAGE > 1 ? __ldcs(acc + s) : 0.0;
+  const int64_t b = __ldg(rowptr + s), e = __ldg(rowptr + s + 1);
+  const int64_t b1 = __ldg(rowptr1 + s), e1 = __ldg(rowptr1 + s + 1);
+  double t = 0.0, t1 = 0.0;
+#pragma unroll 4
+  for (int64_t q = b; q < e; ++q) t = fma(__ldcs(val + q), __ldg(x + __ldcs(col + q)), t);
+  for (int64_t q = b1; q < e1; ++q) t1 = fma(__ldcs(val1 + q), __ldg(x + __ldcs(col1 + q)), t1);
+  const double k = fma(eps, t1, t) + kf;
+  double nx;
+  if (STAGE == 1) {
+    acc[s] = k;
+    nx = vs + 0.5 * h * k;
+  } else if (STAGE == 2) {
+    acc[s] = ac + 2.0 * k;
+    nx = vs + 0.5 * h * k;
+  } else if (STAGE == 3) {
+    acc[s] = ac + 2.0 * k;
+    nx = vs + h * k;
+  } else {
+    nx = vs + (h / 6.0) * (ac + k);
+    v[s] = nx;
+  }
+  xn[s] = nx;
+}
+
 // c = (A64 - A32) v on the CSR pattern;  Keff = K + c.  One thread per row.
 __global__ void __launch_bounds__(256)
     k_correction_csr(int64_t M, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
@@ -397,9 +437,44 @@ cudaError_t run_steps_csr(int64_t M, const int64_t* rowptr, const int32_t* col, 
   return cudaGetLastError();
 }
 
+// eps(t) periodic with period T: seg_eps[k] for (t mod T) in
+// [seg_start[k], seg_start[k + 1]).
+double eps_at(double t, int nseg, const double* seg_start, const double* seg_eps, double T) {
+  double u = std::fmod(t, T);
+  if (u < 0) u += T;
+  int k = 0;
+  while (k + 1 < nseg && u >= seg_start[k + 1]) ++k;
+  return seg_eps[k];
+}
+
 }  // namespace
 
 namespace lbi {
+
+// RK4 for dv/dt = (A0 + eps(t) Q1) v + K, each stage with eps at its own
+// time, the end stages taken 1e-6 dt inside the step (so that a step between
+// two switches sees one value whatever the rounding of its end times).
+cudaError_t rk4_csr_td(int64_t M, const int64_t* rowptr, const int32_t* col, const double* val,
+                       const int64_t* rowptr1, const int32_t* col1, const double* val1, const double* K, int nseg,
+                       const double* seg_start, const double* seg_eps, double T, double t0, double* v, double dt,
+                       int64_t nsteps, void* work, cudaStream_t st) {
+  Work w = carve(work, M);
+  const unsigned grid = (unsigned)((M + 255) / 256);
+  cudaError_t e = cudaMemcpyAsync(w.X, v, sizeof(double) * M, cudaMemcpyDeviceToDevice, st);
+  for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
+    const double t = t0 + (double)n * dt;
+    const double e1 = eps_at(t + 1e-6 * dt, nseg, seg_start, seg_eps, T);
+    const double e2 = eps_at(t + 0.5 * dt, nseg, seg_start, seg_eps, T);
+    const double e4 = eps_at(t + dt - 1e-6 * dt, nseg, seg_start, seg_eps, T);
+    k_stage_csr_td<1><<<grid, 256, 0, st>>>(M, rowptr, col, val, rowptr1, col1, val1, e1, K, w.X, w.Y, w.acc, v, dt);
+    k_stage_csr_td<2><<<grid, 256, 0, st>>>(M, rowptr, col, val, rowptr1, col1, val1, e2, K, w.Y, w.X, w.acc, v, dt);
+    k_stage_csr_td<3><<<grid, 256, 0, st>>>(M, rowptr, col, val, rowptr1, col1, val1, e2, K, w.X, w.Y, w.acc, v, dt);
+    k_stage_csr_td<4><<<grid, 256, 0, st>>>(M, rowptr, col, val, rowptr1, col1, val1, e4, K, w.Y, w.X, w.acc, v, dt);
+    lbi::note_launch(4);
+    e = cudaGetLastError();
+  }
+  return e;
+}
 
 cudaError_t rk4_csr(int64_t M, int precision, const int64_t* rowptr, const int32_t* col, const void* val,
                     const double* val64, int correct_every, const double* K, double* v, double dt, int64_t nsteps,

@@ -124,6 +124,8 @@ def load():
         "lb_csr_copy": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
         "lb_csr_destroy": (ctypes.c_int, [_vp]),
         "lb_rk4_csr": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, _c_i64, _vp, _vp]),
+        "lb_rk4_csr_td": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp,
+                                         ctypes.c_double, _c_i64, _vp, _vp]),
         "lb_batch_create": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
         "lb_batch_set": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
         "lb_batch_assemble": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
@@ -527,6 +529,16 @@ class Csr:
         K = np.zeros(self.M, np.float64)
         _check(load().lb_csr_copy(self._h, _ptr(rp), _ptr(col), _ptr(val), _ptr(K), None))
         return rp, col[:self.nnz], val[:self.nnz], K
+
+    def rk4_td(self, Q1, v, dt, nsteps, seg_start, seg_eps, period, t0=0.0, work=None, stream=None):
+        """FP64 RK4 of dv/dt = (A + eps(t) Q1) v + K, eps periodic and
+        piecewise constant (lb_rk4_csr_td); v updated in place."""
+        work = rk4_workspace(self.M, v.device) if work is None else work
+        ss = np.ascontiguousarray(seg_start, np.float64)
+        se = np.ascontiguousarray(seg_eps, np.float64)
+        assert len(ss) == len(se)
+        _check(load().lb_rk4_csr_td(self._h, Q1._h, len(ss), _ptr(ss), _ptr(se), float(period), float(t0), _ptr(v),
+                                    float(dt), int(nsteps), _ptr(work), _stream(stream)))
 
     def rk4(self, v, dt, nsteps, precision="fp64", correct_every=0, work=None, stream=None):
         """RK4 on the CSR system; v (float64 device tensor) updated in place."""

@@ -161,3 +161,66 @@ def test_ladder_n2000_pattern_size_and_death_process():
         ref = np.exp(logc + n * math.log(e) + (n0 - n) * math.log(1 - e))
     assert abs(p.sum() - 1.0) < 1e-12
     assert np.abs(p - ref).max() < 1e-6   # RK4 at h*gamma*N = 0.02: global error ~1e-7 at most
+
+
+def _dimer_gpu(B, N):
+    """CSR A0 = Q0 + R, the CSR Q1 of H1, and the drive of the rocked dimer."""
+    H0, H1, L, rate, eps = wl.dimer_model(N)
+    ch, _ = _channels_ladder(B, L, rate)
+    A0 = lbm().Csr(B, h=B.expand(torch.tensor(H0, device="cuda")).real.contiguous(), channels=ch)
+    Q1 = lbm().Csr(B, h=B.expand(torch.tensor(H1, device="cuda")).real.contiguous(), channels=())
+    return A0, Q1, eps
+
+
+@pytest.mark.parametrize("N", [6, 11])
+def test_dimer_time_dependent_rk4_vs_oracle(N):
+    """The periodically rocked dimer (Sec. 3, Eqs. (10)-(11)): Q(t) = Q0 +
+    eps(t) Q1 with eps = E + A Theta(t) switching at T/2, one period T = 2 pi
+    in 4000 steps, against the oracle's time-dependent RK4 on its own dense
+    A0 = Q0 + R, Q1 and K, within 1e-12 ||v|| at every quarter period."""
+    from oracle import rk4_dense_td
+    T = 2.0 * math.pi
+    steps = 4000
+    lb = lbm()
+    with lb.Basis(N) as B, Oracle(N) as o:
+        H0, H1, L, rate, eps = wl.dimer_model(N)
+        h0, _ = o.expand(H0)
+        h1, _ = o.expand(H1)
+        l, _ = o.expand(L)
+        a = rate * np.outer(l, l.conj())
+        A0o = o.Q(h0.real) + o.R(a)
+        Q1o = o.Q(h1.real)
+        Ko = o.K(a)
+        v0 = o.expand(wl.pure_state(N, N - 1))[0].real
+        A0, Q1, eps_g = _dimer_gpu(B, N)
+        assert tuple(eps_g) == tuple(eps)
+        v = torch.tensor(v0, device="cuda")
+        ref = v0.copy()
+        for q in range(4):
+            t0 = q * T / 4
+            ref = rk4_dense_td(A0o, Q1o, Ko, ref, T / steps, steps // 4, [0.0, T / 2], list(eps), T, t0=t0)
+            A0.rk4_td(Q1, v, T / steps, steps // 4, [0.0, T / 2], list(eps), T, t0=t0)
+            torch.cuda.synchronize()
+            got = v.cpu().numpy()
+            assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref), q
+        A0.close()
+        Q1.close()
+
+
+def test_dimer_constant_drive_equals_autonomous():
+    """With one segment the time-dependent RK4 is the autonomous CSR RK4 of
+    A0 + eps Q1 (here eps = 0: the same system, the same bits)."""
+    N = 9
+    lb = lbm()
+    with lb.Basis(N) as B, Oracle(N) as o:
+        A0, Q1, _ = _dimer_gpu(B, N)
+        v0 = torch.tensor(o.expand(wl.pure_state(N, 3))[0].real, device="cuda")
+        v1, v2 = v0.clone(), v0.clone()
+        A0.rk4_td(Q1, v1, 1e-3, 300, [0.0], [0.0], 1.0)
+        A0.rk4(v2, 1e-3, 300)
+        torch.cuda.synchronize()
+        assert torch.equal(v1, v2)
+        with pytest.raises(lb.LBError):
+            A0.rk4_td(Q1, v1, 1e-3, 10, [0.5], [1.0], 1.0)  # seg_start[0] must be 0
+        A0.close()
+        Q1.close()
