@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "lb_internal.h"
 
@@ -203,36 +204,59 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 }
 
 // ---------------------------------------------------------------- CSR
-// One thread per row: the rows of these systems are short (about seven
-// entries for the ladder model), so a thread walks its row's entries itself,
-// with no shuffle, and every lane runs the stage epilogue for its own row.
-// The state loads are issued before the row walk so that their latency
-// overlaps the row-pointer -> column -> gathered-x chain.  In FP32 mode the
-// row sum is FP32 and only the FP32 copy of the next stage vector is written
-// (the FP64 copy is not read by the FP32 product).
+// Block-staged form, for short rows (about seven entries for the ladder
+// model): the block's 256 consecutive rows own one contiguous range of the
+// column and value arrays, which the block first copies into shared memory
+// with coalesced loads; then every thread walks its own row there, gathers x
+// (FP32 copy in FP32 mode, which stays in L2) and runs the stage epilogue.  A
+// block whose range exceeds the staging capacity `cap` walks its rows in
+// global memory instead (the same arithmetic in the same order).  In FP32
+// mode the row sum is FP32 and only the FP32 copy of the next stage vector is
+// written (the FP64 copy is not read by the FP32 product).
 template <int PREC, int STAGE>
 __global__ void __launch_bounds__(256)
-    k_stage_csr(int64_t M, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                const void* __restrict__ val, const double* __restrict__ Keff, const double* __restrict__ x,
-                const float* __restrict__ x32, double* __restrict__ xn, float* __restrict__ xn32,
-                double* __restrict__ acc, double* __restrict__ v, double h) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    k_stage_csr_blk(int64_t M, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                    const void* __restrict__ val, int cap, const double* __restrict__ Keff,
+                    const double* __restrict__ x, const float* __restrict__ x32, double* __restrict__ xn,
+                    float* __restrict__ xn32, double* __restrict__ acc, double* __restrict__ v, double h) {
+  using V = typename std::conditional<PREC == LB_FP64, double, float>::type;
+  extern __shared__ __align__(16) unsigned char csr_stage[];
+  V* sval = reinterpret_cast<V*>(csr_stage);
+  int32_t* scol = reinterpret_cast<int32_t*>(csr_stage + sizeof(V) * (size_t)cap);
+  const V* __restrict__ vv = static_cast<const V*>(val);
+  const int64_t r0 = (int64_t)blockIdx.x * 256;
+  const int64_t r1 = r0 + 256 < M ? r0 + 256 : M;
+  const int64_t base = __ldg(rowptr + r0), n = __ldg(rowptr + r1) - base;
+  const bool staged = n <= cap;
+  if (staged)
+    for (int64_t i = threadIdx.x; i < n; i += 256) {
+      sval[i] = __ldcs(vv + base + i);
+      scol[i] = __ldcs(col + base + i);
+    }
+  __syncthreads();
+  const int64_t s = r0 + threadIdx.x;
   if (s >= M) return;
   const double kf = __ldcs(Keff + s), vs = __ldcs(v + s);
   const double ac = STAGE > 1 ? __ldcs(acc + s) : 0.0;
   const int64_t b = __ldg(rowptr + s), e = __ldg(rowptr + s + 1);
   double y;
   if (PREC == LB_FP64) {
-    const double* __restrict__ vv = static_cast<const double*>(val);
     double t = 0.0;
+    if (staged) {
+      for (int64_t q = b - base; q < e - base; ++q) t = fma((double)sval[q], __ldg(x + scol[q]), t);
+    } else {
 #pragma unroll 4
-    for (int64_t q = b; q < e; ++q) t = fma(__ldcs(vv + q), __ldg(x + __ldcs(col + q)), t);
+      for (int64_t q = b; q < e; ++q) t = fma((double)__ldcs(vv + q), __ldg(x + __ldcs(col + q)), t);
+    }
     y = t;
   } else {
-    const float* __restrict__ vv = static_cast<const float*>(val);
     float t = 0.f;
+    if (staged) {
+      for (int64_t q = b - base; q < e - base; ++q) t = fmaf((float)sval[q], __ldg(x32 + scol[q]), t);
+    } else {
 #pragma unroll 4
-    for (int64_t q = b; q < e; ++q) t = fmaf(__ldcs(vv + q), __ldg(x32 + __ldcs(col + q)), t);
+      for (int64_t q = b; q < e; ++q) t = fmaf((float)__ldcs(vv + q), __ldg(x32 + __ldcs(col + q)), t);
+    }
     y = (double)t;
   }
   const double k = y + kf;
@@ -256,9 +280,73 @@ __global__ void __launch_bounds__(256)
     xn32[s] = (float)nx;
 }
 
+// Row-group form, for long rows: W consecutive lanes share a row, so the
+// row's columns and values are read by consecutive lanes (coalesced), the
+// products are summed by W-lane shuffles, and every lane of the group forms
+// the FP64 epilogue (lane 0 of the group stores it).  The state loads of
+// the row are issued before the walk.
+template <int PREC, int STAGE, int W>
+__global__ void __launch_bounds__(256)
+    k_stage_csr_grp(int64_t M, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                    const void* __restrict__ val, const double* __restrict__ Keff, const double* __restrict__ x,
+                    const float* __restrict__ x32, double* __restrict__ xn, float* __restrict__ xn32,
+                    double* __restrict__ acc, double* __restrict__ v, double h) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t s = gt / W;
+  const int sub = (int)(gt % W);
+  const bool valid = s < M;
+  double kf = 0.0, vs = 0.0, ac = 0.0;
+  int64_t b = 0, e = 0;
+  if (valid) {
+    b = __ldg(rowptr + s);
+    e = __ldg(rowptr + s + 1);
+    if (sub == 0) {
+      kf = __ldcs(Keff + s);
+      vs = __ldcs(v + s);
+      if (STAGE > 1) ac = __ldcs(acc + s);
+    }
+  }
+  double y;
+  if (PREC == LB_FP64) {
+    const double* __restrict__ vv = static_cast<const double*>(val);
+    double t = 0.0;
+    for (int64_t q = b + sub; q < e; q += W) t = fma(__ldcs(vv + q), __ldg(x + __ldcs(col + q)), t);
+#pragma unroll
+    for (int o = W >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o, W);
+    y = t;
+  } else {
+    const float* __restrict__ vv = static_cast<const float*>(val);
+    float t = 0.f;
+    for (int64_t q = b + sub; q < e; q += W) t = fmaf(__ldcs(vv + q), __ldg(x32 + __ldcs(col + q)), t);
+#pragma unroll
+    for (int o = W >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o, W);
+    y = (double)t;
+  }
+  if (!valid || sub != 0) return;
+  const double k = y + kf;
+  double nx;
+  if (STAGE == 1) {
+    acc[s] = k;
+    nx = vs + 0.5 * h * k;
+  } else if (STAGE == 2) {
+    acc[s] = ac + 2.0 * k;
+    nx = vs + 0.5 * h * k;
+  } else if (STAGE == 3) {
+    acc[s] = ac + 2.0 * k;
+    nx = vs + h * k;
+  } else {
+    nx = vs + (h / 6.0) * (ac + k);
+    v[s] = nx;
+  }
+  if (PREC == LB_FP64)
+    xn[s] = nx;
+  else
+    xn32[s] = (float)nx;
+}
+
 // Time-dependent form (Sec. 3, the rocked dimer: Q(t) = Q0 + eps(t) Q1): the
-// stage of k_stage_csr<LB_FP64, STAGE> for A0 = Q0 + R plus eps Q1 x, both
-// row sums formed before the epilogue.  One thread per row.
+// FP64 stage for A0 = Q0 + R plus eps Q1 x, both row sums formed before the
+// epilogue, each in the order of k_stage_csr_blk.  One thread per row.
 template <int STAGE>
 __global__ void __launch_bounds__(256)
     k_stage_csr_td(int64_t M, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
@@ -276,6 +364,60 @@ __global__ void __launch_bounds__(256)
 #pragma unroll 4
   for (int64_t q = b; q < e; ++q) t = fma(__ldcs(val + q), __ldg(x + __ldcs(col + q)), t);
   for (int64_t q = b1; q < e1; ++q) t1 = fma(__ldcs(val1 + q), __ldg(x + __ldcs(col1 + q)), t1);
+  const double k = fma(eps, t1, t) + kf;
+  double nx;
+  if (STAGE == 1) {
+    acc[s] = k;
+    nx = vs + 0.5 * h * k;
+  } else if (STAGE == 2) {
+    acc[s] = ac + 2.0 * k;
+    nx = vs + 0.5 * h * k;
+  } else if (STAGE == 3) {
+    acc[s] = ac + 2.0 * k;
+    nx = vs + h * k;
+  } else {
+    nx = vs + (h / 6.0) * (ac + k);
+    v[s] = nx;
+  }
+  xn[s] = nx;
+}
+
+// Row-group form of k_stage_csr_td: W lanes per row, the row sums of A0 and
+// of Q1 formed in the lane order and shuffle tree of k_stage_csr_grp, so that
+// eps = 0 gives the bits of the autonomous step.
+template <int STAGE, int W>
+__global__ void __launch_bounds__(256)
+    k_stage_csr_td_grp(int64_t M, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                       const double* __restrict__ val, const int64_t* __restrict__ rowptr1,
+                       const int32_t* __restrict__ col1, const double* __restrict__ val1, double eps,
+                       const double* __restrict__ K, const double* __restrict__ x, double* __restrict__ xn,
+                       double* __restrict__ acc, double* __restrict__ v, double h) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t s = gt / W;
+  const int sub = (int)(gt % W);
+  const bool valid = s < M;
+  double kf = 0.0, vs = 0.0, ac = 0.0;
+  int64_t b = 0, e = 0, b1 = 0, e1 = 0;
+  if (valid) {
+    b = __ldg(rowptr + s);
+    e = __ldg(rowptr + s + 1);
+    b1 = __ldg(rowptr1 + s);
+    e1 = __ldg(rowptr1 + s + 1);
+    if (sub == 0) {
+      kf = __ldcs(K + s);
+      vs = __ldcs(v + s);
+      if (STAGE > 1) ac = __ldcs(acc + s);
+    }
+  }
+  double t = 0.0, t1 = 0.0;
+  for (int64_t q = b + sub; q < e; q += W) t = fma(__ldcs(val + q), __ldg(x + __ldcs(col + q)), t);
+  for (int64_t q = b1 + sub; q < e1; q += W) t1 = fma(__ldcs(val1 + q), __ldg(x + __ldcs(col1 + q)), t1);
+#pragma unroll
+  for (int o = W >> 1; o > 0; o >>= 1) {
+    t += __shfl_xor_sync(0xffffffffu, t, o, W);
+    t1 += __shfl_xor_sync(0xffffffffu, t1, o, W);
+  }
+  if (!valid || sub != 0) return;
   const double k = fma(eps, t1, t) + kf;
   double nx;
   if (STAGE == 1) {
@@ -408,6 +550,27 @@ cudaError_t run_steps(int64_t M, const void* Ap, const float* scale, const doubl
   return cudaGetLastError();
 }
 
+// Lanes per CSR row: the largest power of two W <= 32 with four or more
+// entries per lane on average (W = 1: the block-staged thread-per-row form).
+// Short rows favour one thread per row, which keeps 32 rows' loads in flight
+// per warp instruction; long rows favour lanes that share a row's entries.
+int csr_group_width(int64_t nnz, int64_t M) {
+  const double mean = M > 0 ? (double)nnz / (double)M : 0.0;
+  int w = 1;
+  while (w < 32 && 4.0 * (2 * w) <= mean) w *= 2;
+  return w;
+}
+
+// Staging capacity (entries) of k_stage_csr_blk: 1.5 times a block's mean
+// range plus one row of slack, within 48 KB of shared memory.
+int csr_stage_cap(int64_t nnz, int64_t M, size_t entry_bytes) {
+  const double mean = M > 0 ? (double)nnz / (double)M : 0.0;
+  const int64_t lim = (int64_t)((48 * 1024) / entry_bytes);
+  int64_t cap = (int64_t)(1.5 * mean * 256.0) + 256;
+  cap = (cap + 31) & ~int64_t(31);
+  return (int)(cap < lim ? cap : lim);
+}
+
 template <int PREC>
 cudaError_t run_steps_csr(int64_t M, const int64_t* rowptr, const int32_t* col, const void* val,
                           const double* val64, int correct_every, const double* K, double* v, double dt,
@@ -423,15 +586,58 @@ cudaError_t run_steps_csr(int64_t M, const int64_t* rowptr, const int32_t* col, 
     lbi::note_launch(1);
   }
   const bool correct = PREC == LB_FP32 && correct_every > 0 && val64 != nullptr;
+  // lanes per row from the mean row length; W = 1: the block-staged kernel
+  int64_t nnz = 0;
+  e = cudaMemcpyAsync(&nnz, rowptr + M, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  const int W = csr_group_width(nnz, M);
+  const unsigned ggrid = (unsigned)((M * W + 255) / 256);
+  using V = typename std::conditional<PREC == LB_FP64, double, float>::type;
+  const int cap = csr_stage_cap(nnz, M, sizeof(V) + sizeof(int32_t));
+  const size_t smem = (sizeof(V) + sizeof(int32_t)) * (size_t)cap;
+  if (W == 1) {
+    e = cudaFuncSetAttribute(k_stage_csr_blk<PREC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_stage_csr_blk<PREC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_stage_csr_blk<PREC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_stage_csr_blk<PREC, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  auto stage = [&](auto stage_c, const double* xc, const float* xc32, double* xn, float* xn32) {
+    constexpr int S = decltype(stage_c)::value;
+    switch (W) {
+      case 2:
+        k_stage_csr_grp<PREC, S, 2><<<ggrid, 256, 0, st>>>(M, rowptr, col, val, w.Keff, xc, xc32, xn, xn32, w.acc, v, dt);
+        break;
+      case 4:
+        k_stage_csr_grp<PREC, S, 4><<<ggrid, 256, 0, st>>>(M, rowptr, col, val, w.Keff, xc, xc32, xn, xn32, w.acc, v, dt);
+        break;
+      case 8:
+        k_stage_csr_grp<PREC, S, 8><<<ggrid, 256, 0, st>>>(M, rowptr, col, val, w.Keff, xc, xc32, xn, xn32, w.acc, v, dt);
+        break;
+      case 16:
+        k_stage_csr_grp<PREC, S, 16><<<ggrid, 256, 0, st>>>(M, rowptr, col, val, w.Keff, xc, xc32, xn, xn32, w.acc, v, dt);
+        break;
+      case 32:
+        k_stage_csr_grp<PREC, S, 32><<<ggrid, 256, 0, st>>>(M, rowptr, col, val, w.Keff, xc, xc32, xn, xn32, w.acc, v, dt);
+        break;
+      default:
+        k_stage_csr_blk<PREC, S><<<grid, 256, smem, st>>>(M, rowptr, col, val, cap, w.Keff, xc, xc32, xn, xn32,
+                                                          w.acc, v, dt);
+    }
+  };
   for (int64_t t = 0; t < nsteps; ++t) {
     if (correct && t % correct_every == 0) {
       k_correction_csr<<<grid, 256, 0, st>>>(M, rowptr, col, val64, static_cast<const float*>(val), v, K, w.Keff);
       lbi::note_launch(1);
     }
-    k_stage_csr<PREC, 1><<<grid, 256, 0, st>>>(M, rowptr, col, val, w.Keff, w.X, w.X32, w.Y, w.Y32, w.acc, v, dt);
-    k_stage_csr<PREC, 2><<<grid, 256, 0, st>>>(M, rowptr, col, val, w.Keff, w.Y, w.Y32, w.X, w.X32, w.acc, v, dt);
-    k_stage_csr<PREC, 3><<<grid, 256, 0, st>>>(M, rowptr, col, val, w.Keff, w.X, w.X32, w.Y, w.Y32, w.acc, v, dt);
-    k_stage_csr<PREC, 4><<<grid, 256, 0, st>>>(M, rowptr, col, val, w.Keff, w.Y, w.Y32, w.X, w.X32, w.acc, v, dt);
+    stage(std::integral_constant<int, 1>{}, w.X, w.X32, w.Y, w.Y32);
+    stage(std::integral_constant<int, 2>{}, w.Y, w.Y32, w.X, w.X32);
+    stage(std::integral_constant<int, 3>{}, w.X, w.X32, w.Y, w.Y32);
+    stage(std::integral_constant<int, 4>{}, w.Y, w.Y32, w.X, w.X32);
     lbi::note_launch(4);
   }
   return cudaGetLastError();
@@ -460,16 +666,44 @@ cudaError_t rk4_csr_td(int64_t M, const int64_t* rowptr, const int32_t* col, con
                        int64_t nsteps, void* work, cudaStream_t st) {
   Work w = carve(work, M);
   const unsigned grid = (unsigned)((M + 255) / 256);
-  cudaError_t e = cudaMemcpyAsync(w.X, v, sizeof(double) * M, cudaMemcpyDeviceToDevice, st);
+  int64_t nnz = 0;
+  cudaError_t e = cudaMemcpyAsync(&nnz, rowptr + M, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  const int W = csr_group_width(nnz, M);
+  const unsigned ggrid = (unsigned)((M * W + 255) / 256);
+  auto stage = [&](auto stage_c, double eps, const double* xc, double* xn) {
+    constexpr int S = decltype(stage_c)::value;
+    switch (W) {
+      case 2:
+        k_stage_csr_td_grp<S, 2><<<ggrid, 256, 0, st>>>(M, rowptr, col, val, rowptr1, col1, val1, eps, K, xc, xn, w.acc, v, dt);
+        break;
+      case 4:
+        k_stage_csr_td_grp<S, 4><<<ggrid, 256, 0, st>>>(M, rowptr, col, val, rowptr1, col1, val1, eps, K, xc, xn, w.acc, v, dt);
+        break;
+      case 8:
+        k_stage_csr_td_grp<S, 8><<<ggrid, 256, 0, st>>>(M, rowptr, col, val, rowptr1, col1, val1, eps, K, xc, xn, w.acc, v, dt);
+        break;
+      case 16:
+        k_stage_csr_td_grp<S, 16><<<ggrid, 256, 0, st>>>(M, rowptr, col, val, rowptr1, col1, val1, eps, K, xc, xn, w.acc, v, dt);
+        break;
+      case 32:
+        k_stage_csr_td_grp<S, 32><<<ggrid, 256, 0, st>>>(M, rowptr, col, val, rowptr1, col1, val1, eps, K, xc, xn, w.acc, v, dt);
+        break;
+      default:
+        k_stage_csr_td<S><<<grid, 256, 0, st>>>(M, rowptr, col, val, rowptr1, col1, val1, eps, K, xc, xn, w.acc, v, dt);
+    }
+  };
+  e = cudaMemcpyAsync(w.X, v, sizeof(double) * M, cudaMemcpyDeviceToDevice, st);
   for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) {
     const double t = t0 + (double)n * dt;
     const double e1 = eps_at(t + 1e-6 * dt, nseg, seg_start, seg_eps, T);
     const double e2 = eps_at(t + 0.5 * dt, nseg, seg_start, seg_eps, T);
     const double e4 = eps_at(t + dt - 1e-6 * dt, nseg, seg_start, seg_eps, T);
-    k_stage_csr_td<1><<<grid, 256, 0, st>>>(M, rowptr, col, val, rowptr1, col1, val1, e1, K, w.X, w.Y, w.acc, v, dt);
-    k_stage_csr_td<2><<<grid, 256, 0, st>>>(M, rowptr, col, val, rowptr1, col1, val1, e2, K, w.Y, w.X, w.acc, v, dt);
-    k_stage_csr_td<3><<<grid, 256, 0, st>>>(M, rowptr, col, val, rowptr1, col1, val1, e2, K, w.X, w.Y, w.acc, v, dt);
-    k_stage_csr_td<4><<<grid, 256, 0, st>>>(M, rowptr, col, val, rowptr1, col1, val1, e4, K, w.Y, w.X, w.acc, v, dt);
+    stage(std::integral_constant<int, 1>{}, e1, w.X, w.Y);
+    stage(std::integral_constant<int, 2>{}, e2, w.Y, w.X);
+    stage(std::integral_constant<int, 3>{}, e2, w.X, w.Y);
+    stage(std::integral_constant<int, 4>{}, e4, w.Y, w.X);
     lbi::note_launch(4);
     e = cudaGetLastError();
   }
