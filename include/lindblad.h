@@ -492,8 +492,10 @@ int lb_batch_destroy(lb_batch_t *b);
  * All arrays are host memory, read during the call only. */
 typedef struct lb_kossakowski {
   int kind;               /* LB_A_DENSE or LB_A_LOWRANK */
-  const double *a;        /* LB_A_DENSE: M x M complex Hermitian (interleaved); for
-                             M > 2048 only its upper triangle j <= k is read */
+  const double *a;        /* LB_A_DENSE: M x M complex Hermitian (interleaved); only
+                             its upper triangle j <= k is read when the array is
+                             page-locked (then by the GPU over the host link) or
+                             M > 2048; the whole array (pageable, M <= 2048) */
   int nP;                 /* LB_A_LOWRANK: number of channels (0 <= nP <= 4096) */
   const double *gamma;    /* nP rates */
   const int64_t *lp_ptr;  /* nP + 1 offsets into lp_idx / lp_val, lp_ptr[0] = 0 */
@@ -509,7 +511,9 @@ typedef struct lb_kossakowski {
  *     (LB_ALG_CLOSED or LB_ALG_JOIN); keep_parts != 0 also keeps Q and R.  A
  *     low-rank `a` is first formed as a dense matrix on the device.  The
  *     Hermitian upper triangle of a dense `a` crosses the host link and the
- *     lower one is mirrored on the device.
+ *     lower one is mirrored on the device.  A page-locked (pinned, mapped)
+ *     `a` is read by a kernel directly from host memory; a pageable one goes
+ *     through the copy engine in row blocks.
  *   format = LB_CSR: A in CSR form from a low-rank `a` (the product form of
  *     lb_assemble_lowrank_csr, same pattern rule); `algorithm` is not used.
  *     A dense `a` or keep_parts != 0 give LB_EUNSUPPORTED.

@@ -489,6 +489,15 @@ __device__ __forceinline__ double neg_half(double x) {
   return -0.5 * x;
 }
 
+// 2x, exactly, by exponent arithmetic for normal x below the top binade (no
+// FP64 instruction); zero, subnormal, inf and nan take the FP64 add.
+__device__ __forceinline__ double twice(double x) {
+  const long long b = __double_as_longlong(x);
+  const long long ex = (b >> 52) & 0x7ff;
+  if (ex >= 1 && ex < 0x7fe) return __longlong_as_double(b + (1LL << 52));
+  return x + x;
+}
+
 __device__ __forceinline__ double warp_sum(double x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
@@ -1054,69 +1063,6 @@ __global__ void __maxnreg__(168) k_disjoint4(BasisView B, AView A, double* __res
   }
 }
 
-// Pair x pair entries whose edges meet (share one vertex, or are the same
-// edge): the D-section part of Eq. (09) in closed form and Q (Eq. (07)); the
-// l-pair part is added afterwards by k_shared_closed / k_same.  One thread
-// per (edge s, meeting edge n), four type pairs each.
-__global__ void __launch_bounds__(256) k_meet(BasisView B, AView A, const double* __restrict__ h,
-                                              double* __restrict__ Aout, double* __restrict__ Qout,
-                                              double* __restrict__ Rout) {
-  const int N = B.N;
-  const int64_t P = B.P, M = B.M;
-  const int64_t per = 2 * (int64_t)N - 3;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= P * per) return;
-  const int64_t ps = tid / per;
-  const int k = (int)(tid % per);
-  const int32_t abs_ = __ldg(B.pair_ab + ps);
-  const int as = abs_ >> 16, bs = abs_ & 0xffff;
-  int an, bn;
-  if (k == 2 * N - 4) {
-    an = as;
-    bn = bs;
-  } else {
-    const int v = k < N - 2 ? as : bs;
-    int w = k < N - 2 ? k : k - (N - 2);
-    if (w >= as) ++w;  // skip as and bs (as < bs)
-    if (w >= bs) ++w;
-    an = imin(v, w);
-    bn = imax(v, w);
-  }
-  const int64_t pn = pair_index(N, an, bn);
-  int shared = 0, cv = -1;
-  if (as == an || as == bn) { ++shared; cv = as; }
-  if (bs == an || bs == bn) { ++shared; cv = bs; }
-  const int e1 = as == an, e2 = as == bn, e3 = bs == an, e4 = bs == bn;
-  const double cf = (double)(e1 - e2 - e3 + e4), cd = (double)(e1 + e2 - e3 - e4);
-#pragma unroll
-  for (int ts = 0; ts < 2; ++ts)
-#pragma unroll
-    for (int tn = 0; tn < 2; ++tn) {
-      const int64_t s = (int64_t)ts * P + ps, n = (int64_t)tn * P + pn;
-      const int64_t sb = (int64_t)(1 - ts) * P + ps, nb = (int64_t)(1 - tn) * P + pn;
-      const double2 a1 = ldA_row(A, nb, sb), a2 = ldA_row(A, n, sb);
-      const double sgs = ts == kS ? 1.0 : -1.0, sgn = tn == kS ? 1.0 : -1.0;
-      const double acc = sgs * (sgn * a1.x * cf - a2.y * cd);
-      double qv = 0.0;
-      if (h != nullptr) {
-        const Elem es = make_pair(ts, as, bs), en = make_pair(tn, an, bn);
-        if (shared == 1) {
-          const int pv = (as == cv) ? bs : as, qq = (an == cv) ? bn : an;
-          const Elem em = make_pair(1 ^ tn ^ ts, pv, qq);
-          qv = __ldg(h + elem_index(B, em.kind, em.a, em.b)) * f_value(B, em, en, es);
-        } else if (tn != ts) {
-          for (int lam = imax(as, 1); lam <= bs; ++lam)
-            qv += __ldg(h + d_index(B, lam)) * f_value(B, make_d(lam), en, es);
-        }
-      }
-      const double r = neg_half(acc);
-      const int64_t o = s * M + n;
-      if (Rout) Rout[o] = r;
-      if (Qout) Qout[o] = qv;
-      if (Aout) Aout[o] = qv + r;
-    }
-}
-
 // Pair row s = (as, bs) type ts, diagonal columns n = D_nu.  One block per
 // row; the a entries every nu of the row needs are staged in shared memory:
 //   Y[x] = a[partner(s)][D_x],  Z[x] = a[s][D_x],
@@ -1645,15 +1591,58 @@ __device__ __forceinline__ double isum(const double* pre, int lo, int hi) {
   return lo <= hi ? pre[hi + 1] - pre[lo] : 0.0;
 }
 
-// Sequential in-place prefix sum of arr[1..n] (arr[0] = 0 on entry).
-__device__ __forceinline__ void scan_inplace(double* arr, int n) {
-  double s = 0.0;
-  for (int i = 1; i <= n; ++i) {
-    s += arr[i];
-    arr[i] = s;
+// In-place prefix sums arr[1..n] of one array (arr[0] = 0 on entry) by one
+// whole warp: every lane sums a contiguous segment of about n/32 values, an
+// exclusive shuffle scan of the segment sums gives each lane its offset, and
+// the lane writes its running sums.  GB300's FP64 pipe takes a warp
+// instruction at the same cost whether 1 or 32 lanes are active, so a scan
+// by one lane per array costs n warp instructions; this one costs about
+// 2 n/32 + 5.
+__device__ __forceinline__ void warp_prefix(double* arr, int n) {
+  const int lane = threadIdx.x & 31;
+  const int seg = (n + 31) >> 5;
+  const int lo = 1 + lane * seg, hi = min(n, lo + seg - 1);
+  double t = 0.0;
+  for (int i = lo; i <= hi; ++i) t += arr[i];
+  double inc = t;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  double run = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (lane == 0) run = 0.0;
+  for (int i = lo; i <= hi; ++i) {
+    run += arr[i];
+    arr[i] = run;
   }
 }
 
+// Suffix sums y[k] = sum_{w >= k} x[w], k = 0..n-1, and y[n] = 0, by one
+// whole warp (segments from the top, as in warp_prefix).
+__device__ __forceinline__ void warp_suffix(const double* x, double* y, int n) {
+  const int lane = threadIdx.x & 31;
+  const int seg = (n + 31) >> 5;
+  const int hi = n - 1 - lane * seg, lo = max(0, hi - seg + 1);
+  double t = 0.0;
+  for (int i = hi; i >= lo; --i) t += x[i];
+  double inc = t;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  double run = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (lane == 0) run = 0.0;
+  for (int i = hi; i >= lo; --i) {
+    run += x[i];
+    y[i] = run;
+  }
+  if (lane == 0) y[n] = 0.0;
+}
+
+
+constexpr double kNegHalfInvSqrt2 = -0.5 * kInvSqrt2;  // exact: a power-of-two scaling
 
 // Staged data of one unordered vertex pair {p < q}, and accessors for the
 // orientation (P_, Q_) = (p, q) (tr = 0) or (q, p) (tr = 1).  For (q, p) the
@@ -1683,68 +1672,128 @@ struct PairStage {
 };
 
 // l-pair part of the pair x pair entry s on (v, P_), n on (v, Q_) (edges
-// sharing the vertex v), in closed form; returns -1/2 of the join sum.
-__device__ __forceinline__ double shared_entry_closed(const BasisView& B, const AView& A, const PairStage& S,
-                                                      int tr, int P_, int Q_, int v, int ts, int tn) {
-  const int N = B.N;
-  const int64_t P = B.P;
-  double acc2 = 0.0, accD = 0.0;  // accD in units of 1/sqrt2
-  // (A1): all w outside {v, P_, Q_}.  Every J edge's phase moves by 2 when
-  // its vertex order flips, which flips the sign of f (odd phase sums) and of
-  // d (even sums); the order of w and v enters sk and sf (sd) once each and
-  // cancels, so with sigma(w) = (-1)^([P_ < w] tk + [Q_ < w] tj) the sum is
-  // kappa (TOT - sigma(v) X(v)), TOT the block's signed total over all w.
-  {
-    const int a_ = coef_phase(ts, v, P_), b_ = coef_phase(tn, v, Q_);
-    const int pv = P_ < v ? 1 : 0, qv = Q_ < v ? 1 : 0;
-#pragma unroll
-    for (int tl = 0; tl < 2; ++tl) {
-      const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
-      const int sk = sgn_f(a_ + tk + tl);  // phases at [P_ < w] = [w < v] = 0
-      const int kf = sk * sgn_f(b_ + tl + tjf), kd = sk * sgn_d(b_ + tl + tjd);
-      const int sfv = ((pv & tk) ^ (qv & tjf)) ? -1 : 1, sdv = ((pv & tk) ^ (qv & tjd)) ? -1 : 1;
-      const double* T = S.TOT + ((tr * 2 + ts) * 2 + tn) * 4 + tl * 2;
-      acc2 += sgn_mul(kf, T[0] - sgn_mul(sfv, S.sre(tr, tjf, tk, v)));
-      acc2 -= sgn_mul(kd, T[1] - sgn_mul(sdv, S.sim(tr, tjd, tk, v)));
-    }
-  }
-  // (A3) e(l) = (v, Q_): k on (P_, Q_), j = D_mu
-  {
-    const int lo = imin(v, Q_), hi = imax(v, Q_);
-    for (int tl = 0; tl < 2; ++tl) {
-      const int tk = 1 ^ tl ^ ts;
-      const int sk = sgn_f(coef_phase(ts, v, P_) + coef_phase(tk, P_, Q_) + coef_phase(tl, Q_, v));
-      double part;
-      if (tl == tn) part = -S.dy(tk, lo, hi, 1.0);
-      else part = tn == kS ? -S.dx(tk, lo, hi, -1.0) : S.dx(tk, lo, hi, -1.0);
-      accD += sgn_mul(sk, part);
-    }
-  }
-  // (B) l = partner(s) on (v, P_): k = D_mu, j on (P_, Q_)
-  {
-    const int lo = imin(v, P_), hi = imax(v, P_), tl = 1 - ts;
-    const int tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
-    const int base = coef_phase(tn, v, Q_) + coef_phase(tl, P_, v);
-    const int sf = sgn_f(base + coef_phase(tjf, Q_, P_));
-    const int sd = sgn_d(base + coef_phase(tjd, Q_, P_));
-    double part = sgn_mul(sf, S.dx(tjf, lo, hi, -1.0)) + sgn_mul(sd, S.dy(tjd, lo, hi, -1.0));
-    accD += ts == kS ? -part : part;
-  }
-  // (A2) e(l) = (P_, Q_): k on (v, Q_), j on (v, P_)
-  const int64_t pvp = pair_index_any(N, v, P_), pvq = pair_index_any(N, v, Q_);
+// sharing the vertex v), in closed form, split into the terms that do not
+// depend on v (block constants: the block totals of (A1) and the D-vector
+// values at P_ and Q_ of (A3) and (B)), formed once per block for each
+// orientation, type pair and position of v against P_ and Q_, and the terms
+// at v, formed per entry.  The entry is -1/4 acc2 - 1/(2 sqrt2) accD.
+//
+// (A1): all w outside {v, P_, Q_}.  Every J edge's phase moves by 2 when its
+// vertex order flips, which flips the sign of f (odd phase sums) and of d
+// (even sums); the order of w and v enters sk and sf (sd) once each and
+// cancels, so with sigma(w) = (-1)^([P_ < w] tk + [Q_ < w] tj) the sum is
+// kappa (TOT - sigma(v) X(v)), TOT the block's signed total over all w.
+// (A3): e(l) = (v, Q_), k on (P_, Q_), j = D_mu.  (B): l = partner(s) on
+// (v, P_), k = D_mu, j on (P_, Q_).  (A2): e(l) = (P_, Q_), k on (v, Q_), j
+// on (v, P_), from the four values X[tj][tk] = a[(tj, (v, P_))][(tk, (v, Q_))].
+struct SharedSigns {  // the integer signs of one (ts, tn, tl) at one position of v
+  int kf, kd, sfv, sdv;
+};
+
+__device__ __forceinline__ SharedSigns shared_signs_a1(int ts, int tn, int tl, int a_, int b_, int pv, int qv) {
+  const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+  const int sk = sgn_f(a_ + tk + tl);  // phases at [P_ < w] = [w < v] = 0
+  SharedSigns g;
+  g.kf = sk * sgn_f(b_ + tl + tjf);
+  g.kd = sk * sgn_d(b_ + tl + tjd);
+  g.sfv = ((pv & tk) ^ (qv & tjf)) ? -1 : 1;
+  g.sdv = ((pv & tk) ^ (qv & tjd)) ? -1 : 1;
+  return g;
+}
+
+// Block constant of orientation tr, type pair (ts, tn), and v with
+// [P_ < v] = pv, [Q_ < v] = qv (v stands for any vertex in that position).
+__device__ __forceinline__ double shared_entry_const(const PairStage& S, int tr, int P_, int Q_, int pv, int qv,
+                                                     int ts, int tn) {
+  // a vertex v with the given position: only its comparisons with P_, Q_ enter
+  const int vlo_p = pv ? 0 : 1, vlo_q = qv ? 0 : 1;  // [v < P_], [v < Q_]
+  const int a_ = ts == kS ? 0 : (vlo_p ? 3 : 1), b_ = tn == kS ? 0 : (vlo_q ? 3 : 1);
+  double acc2 = 0.0, accD = 0.0;
 #pragma unroll
   for (int tl = 0; tl < 2; ++tl) {
+    const SharedSigns g = shared_signs_a1(ts, tn, tl, a_, b_, pv, qv);
+    const double* T = S.TOT + ((tr * 2 + ts) * 2 + tn) * 4 + tl * 2;
+    acc2 += sgn_mul(g.kf, T[0]);
+    acc2 -= sgn_mul(g.kd, T[1]);
+  }
+  // (A3): the value at Q_ of DX / DY
+#pragma unroll
+  for (int tl = 0; tl < 2; ++tl) {
+    const int tk = 1 ^ tl ^ ts;
+    const int ph_v_p = ts == kS ? 0 : (vlo_p ? 3 : 1);            // coef_phase(ts, v, P_)
+    const int ph_q_v = tl == kS ? 0 : (vlo_q ? 1 : 3);            // coef_phase(tl, Q_, v)
+    const int sk = sgn_f(ph_v_p + coef_phase(tk, P_, Q_) + ph_q_v);
+    double part;
+    if (tl == tn) part = -S.DY[tk * S.L + Q_];
+    else {
+      const double x = S.DX[tk * S.L + Q_];  // dx(lo, hi, -1) = X[lo] - X[hi], negated for tn = S
+      part = tn == kS ? (vlo_q ? x : -x) : (vlo_q ? -x : x);
+    }
+    accD += sgn_mul(sk, part);
+  }
+  // (B): the values at P_
+  {
+    const int tl = 1 - ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+    const int ph_v_q = tn == kS ? 0 : (vlo_q ? 3 : 1);  // coef_phase(tn, v, Q_)
+    const int ph_p_v = tl == kS ? 0 : (vlo_p ? 1 : 3);  // coef_phase(tl, P_, v)
+    const int base = ph_v_q + ph_p_v;
+    const int sf = sgn_f(base + coef_phase(tjf, Q_, P_));
+    const int sd = sgn_d(base + coef_phase(tjd, Q_, P_));
+    // dx(lo, hi, -1) = X[lo] - X[hi]: the P_ value enters with - when P_ is the upper end
+    const double part = sgn_mul(sf, S.DX[tjf * S.L + P_]) + sgn_mul(sd, S.DY[tjd * S.L + P_]);
+    const double pp = vlo_p ? -part : part;
+    accD += ts == kS ? -pp : pp;
+  }
+  return fma(-0.25, acc2, kNegHalfInvSqrt2 * accD);
+}
+
+// The terms at v of the same entry: returns (acc2, accD) to be scaled as in
+// shared_entry_const.
+__device__ __forceinline__ void shared_entry_var(const double2 (&X)[2][2], const PairStage& S, int tr, int P_,
+                                                 int Q_, int v, int ts, int tn, double& acc2, double& accD) {
+  const int pv = P_ < v ? 1 : 0, qv = Q_ < v ? 1 : 0;
+  const int a_ = coef_phase(ts, v, P_), b_ = coef_phase(tn, v, Q_);
+  acc2 = 0.0;
+  accD = 0.0;
+#pragma unroll
+  for (int tl = 0; tl < 2; ++tl) {  // (A1) at v
+    const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+    const SharedSigns g = shared_signs_a1(ts, tn, tl, a_, b_, pv, qv);
+    acc2 += sgn_mul(-g.kf * g.sfv, S.sre(tr, tjf, tk, v));
+    acc2 += sgn_mul(g.kd * g.sdv, S.sim(tr, tjd, tk, v));
+  }
+#pragma unroll
+  for (int tl = 0; tl < 2; ++tl) {  // (A2)
     const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
     const int sk = sgn_f(coef_phase(ts, P_, v) + coef_phase(tk, v, Q_) + coef_phase(tl, Q_, P_));
     const int base = coef_phase(tn, Q_, v) + coef_phase(tl, P_, Q_);
     const int sf = sgn_f(base + coef_phase(tjf, v, P_));
     const int sd = sgn_d(base + coef_phase(tjd, v, P_));
-    const int64_t k = tk * P + pvq;
-    const double2 a1 = ldA(A, tjf * P + pvp, k), a2 = ldA(A, tjd * P + pvp, k);
-    acc2 += sgn_mul(sk * sf, a1.x);
-    acc2 -= sgn_mul(sk * sd, a2.y);
+    acc2 += sgn_mul(sk * sf, X[tjf][tk].x);
+    acc2 -= sgn_mul(sk * sd, X[tjd][tk].y);
   }
-  return -0.5 * fma(accD, kInvSqrt2, 0.5 * acc2);
+  const int vlo_q = v < Q_, vlo_p = v < P_;
+#pragma unroll
+  for (int tl = 0; tl < 2; ++tl) {  // (A3) at v
+    const int tk = 1 ^ tl ^ ts;
+    const int sk = sgn_f(coef_phase(ts, v, P_) + coef_phase(tk, P_, Q_) + coef_phase(tl, Q_, v));
+    double part;
+    if (tl == tn) part = -S.DY[tk * S.L + v];
+    else {
+      const double x = S.DX[tk * S.L + v];  // dx(lo, hi, -1) = X[lo] - X[hi], negated for tn = S
+      part = tn == kS ? (vlo_q ? -x : x) : (vlo_q ? x : -x);
+    }
+    accD += sgn_mul(sk, part);
+  }
+  {  // (B) at v
+    const int tl = 1 - ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
+    const int base = coef_phase(tn, v, Q_) + coef_phase(tl, P_, v);
+    const int sf = sgn_f(base + coef_phase(tjf, Q_, P_));
+    const int sd = sgn_d(base + coef_phase(tjd, Q_, P_));
+    const double part = sgn_mul(sf, S.DX[tjf * S.L + v]) + sgn_mul(sd, S.DY[tjd * S.L + v]);
+    const double pv_ = vlo_p ? part : -part;
+    accD += ts == kS ? -pv_ : pv_;
+  }
 }
 
 // Diagonal row D_nu, pair column n on {p, q} of type tn, in closed form: the
@@ -1839,7 +1888,10 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
   }
   if (threadIdx.x < 4) (threadIdx.x < 2 ? CX + threadIdx.x * L : CY + (threadIdx.x - 2) * L)[0] = 0.0;
   __syncthreads();
-  if (threadIdx.x < 4) scan_inplace(threadIdx.x < 2 ? CX + threadIdx.x * L : CY + (threadIdx.x - 2) * L, N);
+  {
+    const int wi = threadIdx.x >> 5;  // warps 0..3 scan CX[0], CX[1], CY[0], CY[1]
+    if (wi < 4) warp_prefix(wi < 2 ? CX + wi * L : CY + (wi - 2) * L, N);
+  }
   __syncthreads();
   // (D x)_k for the four staged D-column vectors: sum_{mu > k} c_mu x_mu + delta_k(k) x_k
   for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
@@ -1869,6 +1921,12 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
   }
   __syncthreads();
   const PairStage S{PX, PY, TX, TY, CX, CY, DXs, DYs, TOTs, L};
+  // block constants of the shared-vertex entries: (tr, ts, tn, [P_ < v], [Q_ < v])
+  __shared__ double CST[32];
+  if (threadIdx.x < 32) {
+    const int c = threadIdx.x, tr = c >> 4, ts = (c >> 3) & 1, tn = (c >> 2) & 1, pv = (c >> 1) & 1, qv = c & 1;
+    CST[c] = shared_entry_const(S, tr, tr ? q : p, tr ? p : q, pv, qv, ts, tn);
+  }
   // diagonal x pair families: for orientation tr (v = p or q, v' the other)
   // and column type tn, U_w = sigma_v(w) sum_tl tau_l (sf X_re - sd X_im) at
   // the single w, with X the staged a[(v',w) tj][(v,w) tk] (k = partner(l)),
@@ -1896,30 +1954,52 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
   }
   if (threadIdx.x < 4) PU[threadIdx.x * L] = 0.0;
   __syncthreads();
-  if (threadIdx.x < 4) {
-    scan_inplace(PU + threadIdx.x * L, N);
-  } else if (threadIdx.x >= 32 && threadIdx.x < 36) {  // suffix sums, another warp
-    const double* X = RU + (threadIdx.x - 32) * L;
-    double* Y = SU + (threadIdx.x - 32) * L;
-    double acc = 0.0;
-    Y[N] = 0.0;
-    for (int w = N - 1; w >= 0; --w) {
-      acc += X[w];
-      Y[w] = acc;
-    }
+  {
+    const int wi = threadIdx.x >> 5;  // warps 0..3: prefix of U, 4..7: suffix
+    if (wi < 4)
+      warp_prefix(PU + wi * L, N);
+    else if (wi < 8)
+      warp_suffix(RU + (wi - 4) * L, SU + (wi - 4) * L, N);
   }
   __syncthreads();
-  // pair x pair, edges sharing a vertex: 2 orientations x N vertices v x 4 type pairs
-  if (Aout || Rout) {
-    for (int t = threadIdx.x; t < 8 * N; t += blockDim.x) {
-      const int tr = t / (4 * N), v = (t >> 2) % N, combo = t & 3;
+  // pair x pair, edges sharing a vertex: 2 orientations x N vertices v, the
+  // four type pairs of one (orientation, v) from the four a values
+  // X[tj][tk] = a[(tj, (v, P_))][(tk, (v, Q_))], written whole: the l-pair
+  // part above, the D-section part (completeness form, -1/2 sgs (sgn cf
+  // Re a_{partner(n) partner(s)} - cd Im a_{n partner(s)}) with cf, cd = +-1
+  // from the position of v) and Q = h_m f_{m n s} on the triangle (P_, Q_, v)
+  // with m the edge (P_, Q_) of type 1 ^ ts ^ tn.
+  {
+    const double hq[2] = {h ? __ldg(h + ppq) * kInvSqrt2 : 0.0, h ? __ldg(h + P + ppq) * kInvSqrt2 : 0.0};
+    for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+      const int tr = t / N, v = t % N;
       if (v == p || v == q) continue;
-      const int ts = combo >> 1, tn = combo & 1;
       const int P_ = tr ? q : p, Q_ = tr ? p : q;
-      const double r = shared_entry_closed(B, A, S, tr, P_, Q_, v, ts, tn);
-      const int64_t o = (ts * P + pair_index_any(N, v, P_)) * M + (tn * P + pair_index_any(N, v, Q_));
-      if (Rout) Rout[o] += r;
-      if (Aout) Aout[o] += r;
+      const int64_t pvp = pair_index_any(N, v, P_), pvq = pair_index_any(N, v, Q_);
+      double2 X[2][2];
+#pragma unroll
+      for (int tj = 0; tj < 2; ++tj)
+#pragma unroll
+        for (int tk = 0; tk < 2; ++tk) X[tj][tk] = ldA(A, tj * P + pvp, tk * P + pvq);
+      const int cf = ((v < P_) == (v < Q_)) ? 1 : -1, cd = v < P_ ? 1 : -1;
+#pragma unroll
+      for (int combo = 0; combo < 4; ++combo) {
+        const int ts = combo >> 1, tn = combo & 1;
+        const int sgs = ts == kS ? 1 : -1, sgn = tn == kS ? 1 : -1;
+        // a_{partner(n) partner(s)} = conj(X[1-ts][1-tn]), a_{n partner(s)} = conj(X[1-ts][tn])
+        const double am = sgn_mul(sgs * sgn * cf, X[1 - ts][1 - tn].x) + sgn_mul(sgs * cd, X[1 - ts][tn].y);
+        double acc2, accD;
+        shared_entry_var(X, S, tr, P_, Q_, v, ts, tn, acc2, accD);
+        const int ci = (((tr * 2 + ts) * 2 + tn) * 2 + (P_ < v ? 1 : 0)) * 2 + (Q_ < v ? 1 : 0);
+        const double r = CST[ci] + fma(-0.25, acc2, fma(kNegHalfInvSqrt2, accD, neg_half(am)));
+        const int tm = 1 ^ tn ^ ts;
+        const int ph = coef_phase(ts, v, P_) + coef_phase(tm, P_, Q_) + coef_phase(tn, Q_, v);
+        const double qv = (ph & 1) ? sgn_mul(sgn_f(ph), hq[tm]) : 0.0;
+        const int64_t o = (ts * P + pvp) * M + (tn * P + pvq);
+        if (Rout) Rout[o] = r;
+        if (Qout) Qout[o] = qv;
+        if (Aout) Aout[o] = qv + r;
+      }
     }
   }
   // diagonal x pair
@@ -1958,6 +2038,7 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
   double* RU1 = sq + 6 * L;   // [2][L]: U1 at w (raw)
   double* PU2 = sq + 8 * L;   // [2][L]: prefix over w of U2 (both tl), per vi
   __shared__ double cst[2];   // c1 = sum gs Re a[s][D_mu], c2 = sum gs Im a[partner(s)][D_mu]
+  __shared__ double cpart[kRowThreads / 32];
   for (int x = threadIdx.x; x < N; x += blockDim.x) {
     const double y = x >= 1 ? ldA(A, sb, d_index(B, x)).y : 0.0;
     const double gs = (x >= lo_s && x <= bs) ? dlt(B, as, x) - dlt(B, bs, x) : 0.0;
@@ -1980,65 +2061,81 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
     if (w != as && w != bs) {
       const int v = vi ? bs : as, vp = vi ? as : bs;
       const int64_t pl = pair_index_any(N, v, w), pk = pair_index_any(N, vp, w);
+      double2 lb[2];  // (ly, bx) of tl = S, J
+#pragma unroll
+      for (int tl = 0; tl < 2; ++tl) {
+        const int64_t k = (int64_t)(1 ^ tl ^ ts) * P + pk;
+        lb[tl] = make_double2(ldA(A, (int64_t)tl * P + pl, k).y, ldA(A, (int64_t)(1 - tl) * P + pl, k).x);
+      }
+      // u1 = sum_tl sk (tsb - ly) = Pb - Ly and u2 = sum_tl sk (-tsb - ly) = -Pb - Ly
+      double pb = 0.0, ly = 0.0;
 #pragma unroll
       for (int tl = 0; tl < 2; ++tl) {
         const int tk = 1 ^ tl ^ ts;
-        const int64_t k = (int64_t)tk * P + pk;
-        const double ly = ldA(A, (int64_t)tl * P + pl, k).y;
-        const double bx = ldA(A, (int64_t)(1 - tl) * P + pl, k).x;
         const int sk = sgn_f(coef_phase(ts, v, vp) + coef_phase(tk, vp, w) + coef_phase(tl, w, v));
-        const double tsb = ((tl == kS) != (w < v)) ? bx : -bx;  // tau sigma bx
-        u1 += sgn_mul(sk, tsb - ly);
-        u2 += sgn_mul(sk, -tsb - ly);
+        const int st = ((tl == kS) != (w < v)) ? sk : -sk;  // sk tau sigma
+        pb += sgn_mul(st, lb[tl].y);
+        ly += sgn_mul(sk, lb[tl].x);
       }
+      u1 = pb - ly;
+      u2 = -pb - ly;
     }
     PU1[vi * L + w + 1] = u1;
     RU1[vi * L + w] = u1;
     PU2[vi * L + w + 1] = u2;
   }
-  // prefix arrays: PGY, PG2C, PCY, PU1[0..1], PU2[0..1]
+  // c1 = sum gs(mu) Re a[s][D_mu] over mu in [lo_s, bs]: a block sum
+  {
+    double c1 = 0.0;
+    for (int mu = imax(lo_s, 1) + threadIdx.x; mu <= bs; mu += blockDim.x)
+      c1 += (dlt(B, as, mu) - dlt(B, bs, mu)) * ldA(A, s, d_index(B, mu)).x;
+    c1 = warp_sum(c1);
+    if ((threadIdx.x & 31) == 0) cpart[threadIdx.x >> 5] = c1;
+  }
+  // prefix arrays: PGY, PG2C, PCY, PU1[0..1], PU2[0..1], one warp each
   auto scanned = [&](int i) { return i < 3 ? PGY + i * L : i < 5 ? PU1 + (i - 3) * L : PU2 + (i - 5) * L; };
   if (threadIdx.x < 7) scanned(threadIdx.x)[0] = 0.0;
   __syncthreads();
-  if (threadIdx.x < 7) {
-    scan_inplace(scanned(threadIdx.x), N);
-  } else if (threadIdx.x == 32) {
+  for (int i = threadIdx.x >> 5; i < 7; i += kRowThreads / 32) warp_prefix(scanned(i), N);
+  if (threadIdx.x == 0) {
     double c1 = 0.0;
-    for (int mu = lo_s; mu <= bs; ++mu) c1 += (dlt(B, as, mu) - dlt(B, bs, mu)) * ldA(A, s, d_index(B, mu)).x;
+    for (int i = 0; i < kRowThreads / 32; ++i) c1 += cpart[i];
     cst[0] = c1;
   }
   __syncthreads();
   if (threadIdx.x == 0) cst[1] = isum(PGY, lo_s, bs);
   __syncthreads();
+  // per entry about 21 FP64 instructions: signs and the exact factors 2 and
+  // -1/2 are applied to the bits with integer operations
+  const double hsb = h != nullptr ? __ldg(h + sb) : 0.0;
   for (int nu = 1 + threadIdx.x; nu < N; nu += blockDim.x) {
+    const double cnu = ld_c(B, nu);
+    const bool inr = nu >= lo_s && nu <= bs;
+    const double gs = inr ? dlt(B, as, nu) - dlt(B, bs, nu) : 0.0;
     // l = D_lam
-    double accD = 2.0 * ld_c(B, nu) * isum(PGY, lo_s, imin(bs, nu - 1));
-    accD += YY[nu] * isum(PG2C, imax(lo_s, nu + 1), bs);
-    if (nu >= lo_s && nu <= bs) {
-      const double gs = dlt(B, as, nu) - dlt(B, bs, nu);
-      double t2 = 2.0 * isum(PCY, nu + 1, N - 1);
-      if (nu != 1) t2 += 2.0 * (ld_c(B, nu) + ld_lc(B, nu)) * YY[nu];  // (1 - nu) c_nu
-      accD += gs * t2;
+    double accD = twice(cnu) * isum(PGY, lo_s, imin(bs, nu - 1));
+    accD = fma(YY[nu], isum(PG2C, imax(lo_s, nu + 1), bs), accD);
+    if (inr) {
+      double t2 = twice(isum(PCY, nu + 1, N - 1));
+      if (nu != 1) t2 = fma(twice(cnu + ld_lc(B, nu)), YY[nu], t2);  // 2 (1 - nu) c_nu
+      accD = fma(gs, t2, accD);
     }
-    double acc = sgs * accD;
+    double acc = sgn_mul(ts == kS ? 1 : -1, accD);
     // l = (v, w) sharing a vertex with e(s): d_nu^T U1 + delta_v(nu) U2 per v
-    double accA = 0.0;
-    const double cnu = ld_c(B, nu), dnn = dlt(B, nu, nu);
-#pragma unroll
-    for (int vi = 0; vi < 2; ++vi) {
-      const double dv = dlt(B, vi ? bs : as, nu);
-      accA += cnu * PU1[vi * L + nu] + dnn * RU1[vi * L + nu] + dv * PU2[vi * L + N];
-    }
-    acc += accA * kInvSqrt2;
+    const double dnn = dlt(B, nu, nu);
+    double accA = cnu * (PU1[nu] + PU1[L + nu]);
+    accA = fma(dnn, RU1[nu] + RU1[L + nu], accA);
+    accA = fma(dlt(B, as, nu), PU2[N], accA);
+    accA = fma(dlt(B, bs, nu), PU2[L + N], accA);
+    acc = fma(accA, kInvSqrt2, acc);
     // l = partner(s), k = D_mu
     {
-      const double gnu = (nu >= lo_s && nu <= bs) ? dlt(B, as, nu) - dlt(B, bs, nu) : 0.0;
       const double hnu = (nu >= lo_s && !(as == 0 && bs == 1 && nu == 1)) ? dlt(B, as, nu) + dlt(B, bs, nu) : 0.0;
-      acc += -gnu * cst[0] + sgs * hnu * cst[1];
+      acc = fma(-gs, cst[0], acc);
+      acc = fma(hnu, sgn_mul(ts == kS ? 1 : -1, cst[1]), acc);
     }
-    double q = 0.0;
-    if (h != nullptr && nu >= lo_s && nu <= bs) q = __ldg(h + sb) * sgs * (dlt(B, as, nu) - dlt(B, bs, nu));
-    const double r = -0.5 * acc;
+    const double q = inr ? sgn_mul(ts == kS ? 1 : -1, hsb * gs) : 0.0;
+    const double r = neg_half(acc);
     const int64_t o = s * M + d_index(B, nu);
     if (Rout) Rout[o] = r;
     if (Qout) Qout[o] = q;
@@ -2135,11 +2232,15 @@ __global__ void __launch_bounds__(kSameThreads) k_same(BasisView B, AView A, dou
 // edge at once.  For each (v, w) with w outside the edge the four values
 // a[(tj, (v', w))][(tk, (v', w))], tj, tk in {S, J}, are loaded once and
 // enter every (ts, tn, tl) term (the per-pair sums keep the order of one pair
-// at a time); the l = partner(s) part comes from H = D X D^T.
-__global__ void __launch_bounds__(kSameThreads) k_same_closed(BasisView B, AView A, const double* __restrict__ Hr,
+// at a time); the l = partner(s) part comes from H = D X D^T.  The block
+// also forms the entries' D-section part (by completeness, -+Re a of the
+// partner pair) and Q, and writes the four entries whole.
+__global__ void __launch_bounds__(kSameThreads) k_same_closed(BasisView B, AView A, const double* __restrict__ h,
+                                                              const double* __restrict__ Hr,
                                                               const double* __restrict__ Hi,
-                                                              double* __restrict__ Aout, double* __restrict__ Rout) {
-  __shared__ double red[kSameThreads / 32][4];
+                                                              double* __restrict__ Aout, double* __restrict__ Qout,
+                                                              double* __restrict__ Rout) {
+  __shared__ double red[kSameThreads / 32][5];
   const int N = B.N;
   const int64_t P = B.P, M = B.M;
   const int64_t e = blockIdx.x;
@@ -2188,20 +2289,43 @@ __global__ void __launch_bounds__(kSameThreads) k_same_closed(BasisView B, AView
         accD[combo] = sgs * (tn == kS ? -1.0 : 1.0) * ((Hr[aa] - Hr[ab_]) - (Hr[ba] - Hr[bb]));
     }
   }
+  // Q of the type-changing pairs: sum_lam h_{D_lam} f(D_lam, J_ab, S_ab) over
+  // lam in [max(a, 1), b], f = delta_b(lam) - delta_a(lam); the lam < b terms
+  // take -h c_lam from delta_a, lam = b takes h_b (lc_b - c_b) and lam = a
+  // (a >= 1) -h_a lc_a.  The c_lam sum is split over the block.
+  double hc = 0.0;
+  if (h != nullptr)
+    for (int lam = a + 1 + threadIdx.x; lam <= b; lam += blockDim.x) hc += __ldg(h + d_index(B, lam)) * ld_c(B, lam);
 #pragma unroll
   for (int combo = 0; combo < 4; ++combo) {
     const double tot = warp_sum(0.5 * acc2[combo] + accD[combo]);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][combo] = tot;
   }
+  {
+    const double tot = warp_sum(hc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][4] = tot;
+  }
   __syncthreads();
   if (threadIdx.x < 4) {
     const int combo = threadIdx.x, ts = combo >> 1, tn = combo & 1;
-    double sum = 0.0;
-    for (int i = 0; i < kSameThreads / 32; ++i) sum += red[i][combo];
-    const double r = -0.5 * sum;
+    double sum = 0.0, hsum = 0.0;
+    for (int i = 0; i < kSameThreads / 32; ++i) {
+      sum += red[i][combo];
+      hsum += red[i][4];
+    }
+    // the D-section part (completeness form): -1/2 sgs sgn 2 Re a_{partner(n) partner(s)}
+    const double2 a1 = ldA_row(A, (int64_t)(1 - tn) * P + e, (int64_t)(1 - ts) * P + e);
+    const double r = sgn_mul((ts == tn) ? -1 : 1, a1.x) + -0.5 * sum;
+    double q = 0.0;
+    if (h != nullptr && ts != tn) {
+      double qsj = __ldg(h + d_index(B, b)) * ld_lc(B, b) - hsum;
+      if (a >= 1) qsj -= __ldg(h + d_index(B, a)) * ld_lc(B, a);
+      q = ts == kS ? qsj : -qsj;
+    }
     const int64_t o = (ts * P + e) * M + (tn * P + e);
-    if (Rout) Rout[o] += r;
-    if (Aout) Aout[o] += r;
+    if (Rout) Rout[o] = r;
+    if (Qout) Qout[o] = q;
+    if (Aout) Aout[o] = q + r;
   }
 }
 
@@ -2230,11 +2354,55 @@ __global__ void __launch_bounds__(256) k_mirror_lower(double2* __restrict__ a, i
   }
 }
 
+// Upper triangle (columns c >= r of every row r) of a from page-locked host
+// memory that is mapped into the device address space, read by the SMs over
+// the host link: each block walks whole rows with eight 16-byte loads in
+// flight per thread, so that the link, not the latency of one load, sets the
+// rate.  Reads stay within the M x M host array.
+__global__ void __launch_bounds__(256) k_upload_upper(const double2* __restrict__ host, double2* __restrict__ dev,
+                                                      int64_t M) {
+  constexpr int kU = 8;
+  for (int64_t r = blockIdx.x; r < M; r += gridDim.x) {
+    const double2* __restrict__ src = host + r * M;
+    double2* __restrict__ dst = dev + r * M;
+    for (int64_t c0 = r + threadIdx.x; c0 < M; c0 += 256 * kU) {
+      double2 v[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t c = c0 + 256 * u;
+        if (c < M) v[u] = src[c];
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t c = c0 + 256 * u;
+        if (c < M) dst[c] = v[u];
+      }
+    }
+  }
+}
+
 }  // namespace
 
 namespace lbi {
 
 cudaError_t upload_hermitian(const double2* host, double2* dev, int64_t M, cudaStream_t st) {
+  // Page-locked host memory mapped into the device address space: the SMs
+  // read the upper triangle directly (no staging copy), then the mirror.
+  cudaPointerAttributes pa;
+  const cudaError_t qa = cudaPointerGetAttributes(&pa, host);
+  if (qa == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr) {
+    int dev_id = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev_id);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = std::min<int64_t>(M, (int64_t)sms * 8);
+    k_upload_upper<<<(unsigned)blocks, 256, 0, st>>>(static_cast<const double2*>(pa.devicePointer), dev, M);
+    const unsigned nt = (unsigned)((M + 31) / 32);
+    k_mirror_lower<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(dev, M);
+    note_launch(2);
+    return cudaGetLastError();
+  }
+  if (qa != cudaSuccess) cudaGetLastError();  // the failed query's error is not the caller's
   if (M <= 2048) return cudaMemcpyAsync(dev, host, sizeof(double2) * M * M, cudaMemcpyHostToDevice, st);
   // row block [j0, j1) brings columns [j0, M): the upper triangle and the
   // lower half of the diagonal block
@@ -2282,15 +2450,7 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
     }
   }
   mark(1);
-  // 1: closed: pair x pair on meeting edges, D-section and Q parts (the
-  //    l-pair parts are added by kernels 5 and 6)
-  if (dense_out && closed && e == cudaSuccess) {
-    const int64_t threads = B.P * (2 * (int64_t)N - 3);
-    k_meet<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(B, av, h, A, Q, R);
-    note_launch(1);
-  }
-  mark(2);
-  // 2: pair x diagonal
+  // 1: pair x diagonal
   if (dense_out && e == cudaSuccess) {
     if (closed) {
       const size_t smem = sizeof(double) * 10 * (size_t)(N + 1);
@@ -2303,20 +2463,20 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
     }
     note_launch(1);
   }
-  mark(3);
-  // 3: diagonal x pair (closed: produced by k_shared_closed below)
+  mark(2);
+  // 2: diagonal x pair (closed: produced by k_shared_closed below)
   if (dense_out && !closed && e == cudaSuccess) {
     k_dp<<<(unsigned)((N - 1) * chunks), 256, 0, st>>>(B, av, h, A, Q, R);
     note_launch(1);
   }
-  mark(4);
+  mark(3);
   // closed: stream-ordered scratch for H (same edge), the vertex sums of K's
   // diagonal rows and the diagonal x diagonal tables
   double* scratch = nullptr;
   const size_t dd_at = 3 * (size_t)N * N + N;
   if (closed && e == cudaSuccess && (dense_out || K))
     e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(double) * (dd_at + DDTables::doubles(N)), st);
-  // 4: diagonal x diagonal (closed: cells of constant coefficient from row,
+  // 3: diagonal x diagonal (closed: cells of constant coefficient from row,
   //    column and corner sums)
   if (dense_out && e == cudaSuccess && N >= 2) {
     if (closed) {
@@ -2333,9 +2493,10 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
       note_launch(1);
     }
   }
-  mark(5);
-  // 5: pair x pair on edges sharing one vertex (adds to R / A); closed: one
-  //    block per vertex pair, which also writes the diagonal x pair entries
+  mark(4);
+  // 4: pair x pair on edges sharing one vertex (join: adds to R / A);
+  //    closed: one block per vertex pair writes these entries whole (the
+  //    D-section and Q parts too) and the diagonal x pair entries
   if (dense_out && closed && e == cudaSuccess) {
     const size_t smem = sizeof(double) * 32 * (size_t)(N + 1);
     e = cudaFuncSetAttribute(k_shared_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -2347,22 +2508,23 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
     if (e == cudaSuccess) k_shared<<<(unsigned)(N * (N - 1)), 256, smem, st>>>(B, av, A, R);
     note_launch(1);
   }
-  mark(6);
-  // 6: pair x pair on the same edge (adds to R / A); its D-section sums come
-  //    from H = D X D^T of the D x D block of a (stream-ordered scratch)
-  if ((A || R) && e == cudaSuccess) {
+  mark(5);
+  // 5: pair x pair on the same edge (closed: written whole, Q included; join:
+  //    adds to R / A); its D-section sums come from H = D X D^T of the D x D
+  //    block of a (stream-ordered scratch)
+  if ((closed ? dense_out : (A || R)) && e == cudaSuccess) {
     if (closed) {
       double* H = scratch + (size_t)N * N;
       k_dh<<<(unsigned)N, 128, sizeof(double) * 2 * (size_t)N, st>>>(B, av, H, H + (size_t)N * N);
-      k_same_closed<<<(unsigned)B.P, kSameThreads, 0, st>>>(B, av, H, H + (size_t)N * N, A, R);
+      k_same_closed<<<(unsigned)B.P, kSameThreads, 0, st>>>(B, av, h, H, H + (size_t)N * N, A, Q, R);
       note_launch(2);
     } else {
       k_same<<<(unsigned)B.P, kSameThreads, sizeof(double) * 2 * N, st>>>(B, av, A, R);
       note_launch(1);
     }
   }
-  mark(7);
-  // 7: K (closed: the diagonal rows from the vertex sums G in the scratch)
+  mark(6);
+  // 6: K (closed: the diagonal rows from the vertex sums G in the scratch)
   if (K && e == cudaSuccess) {
     if (closed) {
       const int64_t warps = 2 * B.P;
@@ -2377,7 +2539,7 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
       note_launch(1);
     }
   }
-  mark(8);
+  mark(7);
   if (scratch) {
     const cudaError_t ef = cudaFreeAsync(scratch, st);
     if (e == cudaSuccess) e = ef;
@@ -2387,12 +2549,11 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
 }
 
 const char* assemble_kernel_name(int i) {
-  static const char* names[kAssembleKernels] = {"k_entries (pair x pair; closed: disjoint edges by vertex quadruple)",
-                                                "k_meet (closed: meeting edges, D-section and Q parts)",
-                                                "k_pd (pair x diagonal)",
-                                                "k_dp (diagonal x pair)", "k_dd (diagonal x diagonal)",
-                                                "k_shared (edges sharing a vertex; closed: + diagonal x pair)",
-                                                "k_same (same edge)", "k_kvec (K)"};
+  static const char* names[kAssembleKernels] = {
+      "k_entries (pair x pair; closed: disjoint edges by vertex quadruple)", "k_pd (pair x diagonal)",
+      "k_dp (diagonal x pair)", "k_dd (diagonal x diagonal)",
+      "k_shared (edges sharing a vertex; closed: whole entries, + diagonal x pair)",
+      "k_same (same edge; closed: whole entries)", "k_kvec (K)"};
   return (i >= 0 && i < kAssembleKernels) ? names[i] : nullptr;
 }
 

@@ -47,7 +47,7 @@ cudaError_t expand(const lb::BasisView& B, const double2* A, double2* coef, cuda
 cudaError_t rho(const lb::BasisView& B, const double* v, double2* out, cudaStream_t st);
 
 // dense assembly (lb_assemble.cu)
-constexpr int kAssembleKernels = 8;
+constexpr int kAssembleKernels = 7;
 // Copy a Hermitian M x M a from host memory to the device: only the upper
 // triangle crosses the link (one 2D copy per row block), the strict lower
 // triangle is then written on the device as a_kj = conj(a_jk).

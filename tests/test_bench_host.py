@@ -40,4 +40,4 @@ def test_stored_traffic_scales_with_quadruples():
     t100, _ = bench.ncu_traffic(QUAD, 100)
     assert src and t200 > 0
     assert t100 / t200 == pytest.approx(math.comb(100, 4) / math.comb(200, 4))
-    assert bench.ncu_traffic("k_meet (closed: meeting edges, D-section and Q parts)", 200) == (None, None)
+    assert bench.ncu_traffic("k_pd (pair x diagonal)", 200) == (None, None)

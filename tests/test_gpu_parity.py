@@ -248,6 +248,26 @@ def test_host_buffer_upper_triangle_upload(N):
                 _assert_entries(got, ref["A"], np.abs(ref["A"]).max(), "A (join)")
 
 
+@pytest.mark.parametrize("N", [6, 46])
+def test_host_buffer_pinned_upload(N):
+    """A page-locked host a is read by the upload kernel over the host link,
+    upper triangle only, at every M: with the strict lower triangle NaN it
+    assembles to the bits of the device-resident a."""
+    H, a = _case(N, 4700 + N)
+    M = N * N - 1
+    lb = lbm()
+    pinned = torch.empty((M, M), dtype=torch.complex128, pin_memory=True)
+    pinned.copy_(torch.from_numpy(a))
+    pinned.numpy()[np.tril_indices(M, -1)] = np.nan
+    with lb.Basis(N) as B:
+        ref = _gpu_system(B, H, a, "closed")
+        sysm = lb.System(B, pinned.numpy(), H=H, keep_parts=True, algorithm="closed")
+        got, K = sysm.get("A"), sysm.get("K")
+        sysm.close()
+    assert np.array_equal(got, ref["A"]) and np.array_equal(K, ref["K"])
+    del pinned
+
+
 def test_empty_and_degenerate_inputs():
     lb = lbm()
     # a = 0, H = 0: everything vanishes
