@@ -1849,7 +1849,7 @@ __device__ __forceinline__ void dp_entry_closed(const BasisView& B, const PairSt
 // One block per unordered vertex pair {p < q}: the l-pair part of every
 // pair x pair entry on edges (v, p), (v, q) in both orientations, and the
 // diagonal x pair entries of the edge (p, q).
-__global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, const double* __restrict__ h,
+__global__ void __launch_bounds__(256, 3) k_shared_closed(BasisView B, AView A, const double* __restrict__ h,
                                                        double* __restrict__ Aout, double* __restrict__ Qout,
                                                        double* __restrict__ Rout) {
   extern __shared__ double sc[];
@@ -1903,21 +1903,33 @@ __global__ void __launch_bounds__(256) k_shared_closed(BasisView B, AView A, con
     (arr < 2 ? DXs : DYs)[tt * L + k] = d;
   }
   // (A1) totals: for (tr, ts, tn, tl), sum over w of sigma(w) X with
-  // sigma(w) = (-1)^([P_ < w] tk + [Q_ < w] tj), f (Re, tj = tjf) and d (Im, tj = tjd)
-  const PairStage S0{PX, PY, TX, TY, CX, CY, DXs, DYs, TOTs, L};
-  if (threadIdx.x < 32 * 8) {
-    const int c = threadIdx.x >> 3, sub = threadIdx.x & 7;  // 8 threads per total
-    const int tr = c >> 4, ts = (c >> 3) & 1, tn = (c >> 2) & 1, tl = (c >> 1) & 1, fd = c & 1;
-    const int P_ = tr ? q : p, Q_ = tr ? p : q;
-    const int tk = 1 ^ tl ^ ts, tj = fd ? (tl ^ tn) : (1 ^ tl ^ tn);
+  // sigma(w) = (-1)^([P_ < w] tk + [Q_ < w] tj), f (Re, tj = tjf) and d (Im,
+  // tj = tjd).  sigma is constant on the three vertex ranges w < p,
+  // p < w < q and w > q (the staged values at p and q are zero), so each
+  // total is a signed sum of three range sums of one staged array: 8 arrays
+  // (PX and PY of the four (tj, tk)) x 3 ranges, 8 threads per range sum.
+  __shared__ double RS[8][3];
+  if (threadIdx.x < 24 * 8) {
+    const int c = threadIdx.x >> 3, sub = threadIdx.x & 7;
+    const int arr = c / 3, rg = c % 3;
+    const double* X = (arr < 4 ? PX : PY) + (arr & 3) * L;
+    const int lo = rg == 0 ? 0 : (rg == 1 ? p + 1 : q + 1), hi = rg == 0 ? p : (rg == 1 ? q : N);
     double acc = 0.0;
-    for (int w = sub; w < N; w += 8) {
-      const double x = fd ? S0.sim(tr, tj, tk, w) : S0.sre(tr, tj, tk, w);
-      const int sg = ((P_ < w ? tk : 0) ^ (Q_ < w ? tj : 0)) ? -1 : 1;
-      acc += sgn_mul(sg, x);
-    }
+    for (int w = lo + sub; w < hi; w += 8) acc += X[w];
     for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, 8);
-    if (sub == 0) TOTs[c] = acc;
+    if (sub == 0) RS[arr][rg] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int c = threadIdx.x;
+    const int tr = c >> 4, ts = (c >> 3) & 1, tn = (c >> 2) & 1, tl = (c >> 1) & 1, fd = c & 1;
+    const int tk = 1 ^ tl ^ ts, tj = fd ? (tl ^ tn) : (1 ^ tl ^ tn);
+    // the staged array of sre / sim(tr, tj, tk, .), and sim's sign for tr = 1
+    const int arr = (fd ? 4 : 0) + (tr ? tk * 2 + tj : tj * 2 + tk);
+    // sigma on p < w < q: [P_ < w] = [P_ == p]; on w > q both flags are set
+    const int s1 = (tr ? tj : tk) ? -1 : 1, s2 = (tk ^ tj) ? -1 : 1;
+    const double t = RS[arr][0] + sgn_mul(s1, RS[arr][1]) + sgn_mul(s2, RS[arr][2]);
+    TOTs[c] = (fd && tr) ? -t : t;
   }
   __syncthreads();
   const PairStage S{PX, PY, TX, TY, CX, CY, DXs, DYs, TOTs, L};
