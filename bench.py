@@ -695,7 +695,7 @@ def form_sparse(args, dev):
     gbs = {p: step_bytes[p] * n / (res[p] * 1e-3) / 1e9 for p in res}
     c.close()
     B.close()
-    return {"N": N, "M": M, "nnz": nnz, "spgemm_terms": None, "assembly_s": t_asm,
+    return {"N": N, "M": M, "nnz": nnz, "row_terms": c.terms, "assembly_s": t_asm,
             "rk4_fp32c_steps_per_s": n / (res["fp32"] * 1e-3), "rk4_fp64_steps_per_s": n / (res["fp64"] * 1e-3),
             "rk4_roofline": {"kernel": "k_stage_csr_blk (CSR SpMV with the block's column/value range staged in shared memory, fused with the stage update)", "bound": "hbm",
                              "achieved": gbs["fp32"], "peak": hbm, "unit": "GB/s",

@@ -343,12 +343,18 @@ typedef struct lb_csr lb_csr_t;
  *   lp_idx : basis indices of the nonzero l_pj (device int64)
  *   lp_val : the values l_pj (device, complex interleaved), e.g. from lb_expand
  * Eq. (09) is evaluated per channel as r_sn = -1/2 gamma_p Re sum_l W_ls U_ln,
- * U_ln = sum_j l_j z_jln, W_ls = sum_k conj(l_k) f_kls (a sparse product).
+ * U_ln = sum_j l_j z_jln, W_ls = sum_k conj(l_k) f_kls (a sparse product:
+ * the terms are placed in buckets by row / column with count, scan and fill
+ * passes, and each row of A is summed in a hash table keyed by column; the
+ * diagonal components of l_p and of h enter through closed-form edge sums).
  * Pattern: an entry is stored iff |A_sn| exceeds 1e-12 times the sum of the
  * magnitudes of its terms (exact cancellations leave rounding residue only);
- * columns are sorted within rows.  *out owns the device arrays (see
+ * columns are sorted within rows.  Values are reproducible to rounding (the
+ * order in which duplicate terms are summed is not fixed).  Indices within
+ * one channel are expected to be distinct.  *out owns the device arrays (see
  * lb_csr_arrays); release with lb_csr_destroy.  Synchronous w.r.t. stream.
- * LB_ENOMEM when the intermediate coordinate lists do not fit. */
+ * LB_ENOMEM when the intermediate lists do not fit; LB_EUNSUPPORTED when a
+ * row of A has more than 8192 distinct columns. */
 int lb_assemble_lowrank_csr(const lb_basis_t *b, const double *h, int nP, const double *gamma,
                             const int64_t *lp_ptr, const int64_t *lp_idx, const double *lp_val,
                             lb_csr_t **out, void *stream);

@@ -428,7 +428,6 @@ int lb_assemble_lowrank_csr(const lb_basis_t* b, const double* h, int nP, const 
     LB_REQUIRE(std::isfinite(gamma[p]), "lb_assemble_lowrank_csr: gamma[%d] not finite", p);
   }
   LB_REQUIRE(nP == 0 || lp_ptr[nP] == 0 || (lp_idx && lp_val), "lb_assemble_lowrank_csr: NULL channel arrays");
-  LB_REQUIRE((double)nP * (double)b->M * (double)b->M < 9.0e18, "lb_assemble_lowrank_csr: key range overflow");
   *out = nullptr;
   lb_csr* c = new lb_csr;
   static const int64_t zero_ptr[1] = {0};
@@ -440,6 +439,10 @@ int lb_assemble_lowrank_csr(const lb_basis_t* b, const double* h, int nP, const 
       cudaGetLastError();
       lbi::set_error("lb_assemble_lowrank_csr: device memory exhausted");
       return LB_ENOMEM;
+    }
+    if (e == cudaErrorNotSupported) {
+      lbi::set_error("lb_assemble_lowrank_csr: a row of A has more than 8192 distinct columns");
+      return LB_EUNSUPPORTED;
     }
     return lbi::cuda_fail(e, "lb_assemble_lowrank_csr");
   }

@@ -6,41 +6,29 @@
 // Eq. (09) factorises per channel:
 //   r_sn = -1/2 gamma_p Re sum_l W_ls U_ln,
 //   U_ln = sum_j l_j z_jln,   W_ls = sum_k conj(l_k) f_kls,
-// so R is a sparse product: the fibres of the nonzero l_j give U and W as
-// coordinate lists (count pass, scan, fill pass), a radix sort by (p, l, .)
-// and a reduction by key merge duplicates, and every W entry is multiplied
-// with the U row of its l.  The products and the Q terms h_m f_mns are
-// sorted by (s, n) and reduced; an entry is kept when its value exceeds
-// 1e-12 times the sum of the magnitudes of its terms (entries whose terms
-// cancel exactly -- most of those the terms reach -- carry only rounding
-// residue).  Magnitudes are carried through U and W as sum |l_j z_jln| etc.
-#include <cub/cub.cuh>
-
+// so R is a sparse product.  Every step is a count / scan / fill pass of this
+// file's own kernels (no library sort):
+//   1. the fibres of the nonzero l_j and l_k emit the U terms into buckets by
+//      row l and the W terms into buckets by column s, each term tagged with
+//      its channel; the Q terms h_m f_mns go into buckets by row s.  A bucket
+//      is filled through a per-bucket cursor after an exclusive scan of the
+//      counts (terms of one bucket keep no particular order);
+//   2. one warp per row s (one block for long rows) accumulates the row in a
+//      hash table keyed by column n: every W term (p, l) of column s times
+//      every U term of row l with the same channel, and the row's Q terms;
+//      the value and the sum of the magnitudes of its terms are summed per
+//      column.  An entry is kept when its value exceeds 1e-12 times that
+//      magnitude (entries whose terms cancel exactly -- most of those the
+//      terms reach -- carry only rounding residue).  A first pass counts the
+//      kept entries of each row, a scan gives the row pointers, a second pass
+//      writes the columns in ascending order with their values.
+// Duplicate terms (the same (l, n) from several j) are summed in the order
+// the fill placed them, so values are reproducible to rounding only.
 #include "lb_internal.h"
 
 namespace {
 
 using namespace lb;
-
-struct CTerm {  // a complex coordinate entry with the magnitude of its terms
-  double re, im, mag;
-};
-
-struct RTerm {  // a real coordinate entry with the magnitude of its terms
-  double val, mag;
-};
-
-struct CTermSum {
-  __host__ __device__ CTerm operator()(const CTerm& a, const CTerm& b) const {
-    return CTerm{a.re + b.re, a.im + b.im, a.mag + b.mag};
-  }
-};
-
-struct RTermSum {
-  __host__ __device__ RTerm operator()(const RTerm& a, const RTerm& b) const {
-    return RTerm{a.val + b.val, a.mag + b.mag};
-  }
-};
 
 // Every (l, s) with f_{k l s} != 0, with the value.
 template <class Emit>
@@ -148,12 +136,6 @@ __device__ void for_each_z_fiber(const BasisView& B, int64_t j, Emit& emit) {
   }
 }
 
-struct Counter {
-  int64_t n = 0;
-  __device__ void operator()(int64_t, int64_t, double) { ++n; }
-  __device__ void operator()(int64_t, int64_t, double, double) { ++n; }
-};
-
 // Channel of a flattened nonzero index u (lp_ptr has nP + 1 entries).
 __device__ __forceinline__ int channel_of(const int64_t* lp_ptr, int nP, int64_t u) {
   int p = 0;
@@ -161,133 +143,220 @@ __device__ __forceinline__ int channel_of(const int64_t* lp_ptr, int nP, int64_t
   return p;
 }
 
-// W terms: key = (p M + l) M + s, value conj(l_k) f_kls, magnitude |l_k f|.
-__global__ void k_w_terms(BasisView B, int nP, const int64_t* lp_ptr, const int64_t* lp_idx,
-                          const double2* lp_val, int64_t nu, const int64_t* off, int64_t* key, CTerm* val,
-                          int64_t* count) {
+// A bucketed term: channel p (-1 for Q), index x (l of a W term, n of a U or
+// Q term), value (re, im) and the magnitude of its terms.
+struct BTerm {
+  int32_t p, x;
+  double re, im, mag;
+};
+
+// Count mode (out == nullptr): one more term in bucket b.  Fill mode: the
+// term goes to off[b] + (the bucket's cursor, advanced atomically).
+struct Bucketer {
+  unsigned long long* cnt;  // count, then cursor (reset to 0 between the passes)
+  const int64_t* off;
+  BTerm* out;
+  __device__ __forceinline__ void put(int64_t b, int p, int64_t x, double re, double im, double mag) const {
+    const unsigned long long k = atomicAdd(cnt + b, 1ull);
+    if (out) out[off[b] + (int64_t)k] = BTerm{p, (int32_t)x, re, im, mag};
+  }
+};
+
+// W terms into buckets by column s: (p, l, conj(l_k) f_kls, |l_k f|).
+__global__ void k_w_bucket(BasisView B, int nP, const int64_t* lp_ptr, const int64_t* lp_idx, const double2* lp_val,
+                           int64_t nu, Bucketer bk) {
   const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (u >= nu) return;
+  const int64_t k = lp_idx[u];
+  if (k >= 2 * B.P) return;  // diagonal components: k_dpart_bucket
   const int p = channel_of(lp_ptr, nP, u);
-  const int64_t k = lp_idx[u], M = B.M;
   const double2 lk = lp_val[u];
-  if (count) {
-    Counter c;
-    for_each_f_fiber(B, k, c);
-    count[u] = c.n;
-    return;
-  }
-  int64_t o = off[u];
-  auto emit = [&](int64_t l, int64_t s, double f) {
-    key[o] = ((int64_t)p * M + l) * M + s;
-    val[o] = CTerm{lk.x * f, -lk.y * f, sqrt(lk.x * lk.x + lk.y * lk.y) * fabs(f)};
-    ++o;
-  };
+  const double am = sqrt(lk.x * lk.x + lk.y * lk.y);
+  auto emit = [&](int64_t l, int64_t s, double f) { bk.put(s, p, l, lk.x * f, -lk.y * f, am * fabs(f)); };
   for_each_f_fiber(B, k, emit);
 }
 
-// U terms: key = (p M + l) M + n, value l_j z_jln, magnitude |l_j z|.
-__global__ void k_u_terms(BasisView B, int nP, const int64_t* lp_ptr, const int64_t* lp_idx,
-                          const double2* lp_val, int64_t nu, const int64_t* off, int64_t* key, CTerm* val,
-                          int64_t* count) {
+// U terms into buckets by row l: (p, n, l_j z_jln, |l_j z|).
+__global__ void k_u_bucket(BasisView B, int nP, const int64_t* lp_ptr, const int64_t* lp_idx, const double2* lp_val,
+                           int64_t nu, Bucketer bk) {
   const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (u >= nu) return;
+  const int64_t j = lp_idx[u];
+  if (j >= 2 * B.P) return;  // diagonal components: k_dpart_bucket, k_udd_bucket
   const int p = channel_of(lp_ptr, nP, u);
-  const int64_t j = lp_idx[u], M = B.M;
   const double2 lj = lp_val[u];
-  if (count) {
-    Counter c;
-    for_each_z_fiber(B, j, c);
-    count[u] = c.n;
-    return;
-  }
-  int64_t o = off[u];
+  const double am = sqrt(lj.x * lj.x + lj.y * lj.y);
   auto emit = [&](int64_t l, int64_t n, double zr, double zi) {
-    key[o] = ((int64_t)p * M + l) * M + n;
-    val[o] = CTerm{lj.x * zr - lj.y * zi, lj.x * zi + lj.y * zr,
-                   sqrt(lj.x * lj.x + lj.y * lj.y) * sqrt(zr * zr + zi * zi)};
-    ++o;
+    bk.put(l, p, n, lj.x * zr - lj.y * zi, lj.x * zi + lj.y * zr, am * sqrt(zr * zr + zi * zi));
   };
   for_each_z_fiber(B, j, emit);
 }
 
-__device__ __forceinline__ int64_t lower_bound_i64(const int64_t* a, int64_t n, int64_t x) {
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (a[mid] < x) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
-// Products of each W entry with the U row of its (p, l): count or fill terms
-// key2 = s M + n, value -1/2 gamma_p Re(W U), magnitude 1/2 gamma_p |W| |U|.
-__global__ void k_products(int64_t M, int nP, const double* gamma, const int64_t* wkey, const CTerm* wval,
-                           int64_t nw, const int64_t* ukey, const CTerm* uval, int64_t nuq, const int64_t* off,
-                           int64_t* key2, RTerm* val2, int64_t* count) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nw) return;
-  const int64_t pl = wkey[i] / M, s = wkey[i] % M;
-  const int64_t lo = lower_bound_i64(ukey, nuq, pl * M), hi = lower_bound_i64(ukey, nuq, (pl + 1) * M);
-  if (count) {
-    count[i] = hi - lo;
-    return;
-  }
-  const int p = (int)(pl / M);
-  const double g = gamma[p];
-  const CTerm w = wval[i];
-  int64_t o = off[i];
-  for (int64_t q = lo; q < hi; ++q) {
-    const CTerm u = uval[q];
-    key2[o] = s * M + ukey[q] % M;
-    val2[o] = RTerm{-0.5 * g * (w.re * u.re - w.im * u.im), 0.5 * g * w.mag * u.mag};
-    ++o;
-  }
-}
-
-// Q terms of the pair coefficients h_m (m < 2P, h_m != 0): f_{m n s}, (n, s) from the fibre.
-__global__ void k_q_pair_terms(BasisView B, const double* h, const int64_t* off, int64_t* key2, RTerm* val2,
-                               int64_t* count) {
+// Q terms of the pair coefficients h_m (m < 2P, h_m != 0) into buckets by
+// row s: f_{m n s} for (n, s) on the fibre of m.
+__global__ void k_q_pair_bucket(BasisView B, const double* h, Bucketer bk) {
   const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (m >= 2 * B.P) return;
   const double hm = h[m];
-  if (hm == 0.0) {
-    if (count) count[m] = 0;
-    return;
-  }
-  if (count) {
-    Counter c;
-    for_each_f_fiber(B, m, c);
-    count[m] = c.n;
-    return;
-  }
-  int64_t o = off[m];
-  const int64_t M = B.M;
-  auto emit = [&](int64_t n, int64_t s, double f) {
-    key2[o] = s * M + n;
-    val2[o] = RTerm{hm * f, fabs(hm * f)};
-    ++o;
-  };
+  if (hm == 0.0) return;
+  auto emit = [&](int64_t n, int64_t s, double f) { bk.put(s, -1, n, hm * f, 0.0, fabs(hm * f)); };
   for_each_f_fiber(B, m, emit);
 }
 
-// Q terms of the diagonal coefficients h_{D_lam}: they reach only (S_xy, J_xy)
-// and (J_xy, S_xy), with f(D_lam, J, S) etc.; one thread per edge, two terms.
-__global__ void k_q_diag_terms(BasisView B, const double* h, int64_t* key2, RTerm* val2) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= B.P) return;
-  const int32_t ab = __ldg(B.pair_ab + e);
-  const int x = ab >> 16, y = ab & 0xffff;
-  double v = 0.0, mag = 0.0;  // sum_lam h_{D_lam} f(D_lam, J_xy, S_xy)
-  for (int lam = imax(x, 1); lam <= y; ++lam) {
-    const double t = h[d_index(B, lam)] * f_value(B, make_d(lam), make_pair(kJ, x, y), make_pair(kS, x, y));
-    v += t;
-    mag += fabs(t);
+// ------------------------------------------------ diagonal components
+// The diagonal part of a vector x over the D_nu (nu = 1..N-1) enters the
+// products only through edge sums of delta_x(nu) = (D_nu)_xx (c_nu for
+// x < nu, -nu c_nu at x = nu, 0 above): with f(D_nu, S_xy, J_xy) =
+// delta_x(nu) - delta_y(nu) and d(D_nu, l, l) = delta_x(nu) + delta_y(nu)
+// (l on (x, y)), over nu in [max(x, 1), y] resp. nu >= max(x, 1),
+//   G_xy = [x >= 1] x_x lc_x + sum_{x < nu < y} x_nu c_nu + x_y (c_y - lc_y),
+//   H_xy = [x >= 1] x_x lc_x + sum_{x < nu < y} x_nu c_nu + x_y (c_y + lc_y)
+//          + 2 sum_{nu > y} x_nu c_nu,
+// and d(D_nu, D_lam, D_mu) = 2 sum_k delta_k(nu) delta_k(lam) delta_k(mu).
+// One thread per (source, x) walks y upward keeping the running sum over
+// x < nu < y, so every sum holds exactly the terms of its edge; each term
+// carries the sum of the magnitudes of its parts.
+
+// Diagonal components of every channel: dl[p N + nu] (complex), hasD[p].
+__global__ void k_dscatter(const BasisView B, int nP, const int64_t* lp_ptr, const int64_t* lp_idx,
+                           const double2* lp_val, int64_t nu_tot, double2* dl, int* hasD) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= nu_tot) return;
+  const int64_t k = lp_idx[u];
+  if (k < 2 * B.P) return;
+  const int p = channel_of(lp_ptr, nP, u);
+  const int64_t i = (int64_t)p * B.N + (k - 2 * B.P + 1);
+  atomicAdd(&dl[i].x, lp_val[u].x);
+  atomicAdd(&dl[i].y, lp_val[u].y);
+  hasD[p] = 1;
+}
+
+// suf[p N + y] = sum_{nu > y} x_nu c_nu and sufm the same over |x_nu| c_nu.
+__global__ void k_dsuffix(const BasisView B, int nP, const double2* dl, const int* hasD, double2* suf, double* sufm) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nP || !hasD[p]) return;
+  const int N = B.N;
+  const double2* x = dl + (int64_t)p * N;
+  double2 r = make_double2(0.0, 0.0);
+  double rm = 0.0;
+  for (int y = N - 1; y >= 0; --y) {
+    suf[(int64_t)p * N + y] = r;
+    sufm[(int64_t)p * N + y] = rm;
+    if (y >= 1) {
+      const double c = ld_c(B, y);
+      r.x += x[y].x * c;
+      r.y += x[y].y * c;
+      rm += sqrt(x[y].x * x[y].x + x[y].y * x[y].y) * c;
+    }
   }
-  const int64_t M = B.M, sS = e, sJ = B.P + e;
-  key2[2 * e] = sS * M + sJ;  // q_{S J} = sum h f_{m J S}
-  val2[2 * e] = RTerm{v, mag};
-  key2[2 * e + 1] = sJ * M + sS;  // q_{J S} = -q_{S J}
-  val2[2 * e + 1] = RTerm{-v, mag};
+}
+
+// W and U terms of the diagonal components of channel p on edge (x, y):
+//   W(l = S, s = J) = conj(G),  W(l = J, s = S) = -conj(G),
+//   U(S, J) = G,  U(J, S) = -G,  U(S, S) = U(J, J) = i H.
+// mode 0: W terms, mode 1: U terms.
+__global__ void k_dpart_bucket(const BasisView B, int nP, const double2* dl, const int* hasD, const double2* suf,
+                               const double* sufm, int mode, Bucketer bk) {
+  const int N = B.N;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nP * N) return;
+  const int p = (int)(t / N), x = (int)(t % N);
+  if (!hasD[p]) return;
+  const double2* dx = dl + (int64_t)p * N;
+  const double2 head = x >= 1 ? make_double2(dx[x].x * ld_lc(B, x), dx[x].y * ld_lc(B, x)) : make_double2(0.0, 0.0);
+  const double headm = x >= 1 ? sqrt(dx[x].x * dx[x].x + dx[x].y * dx[x].y) * fabs(ld_lc(B, x)) : 0.0;
+  double2 run = make_double2(0.0, 0.0);
+  double runm = 0.0;
+  const int64_t P = B.P;
+  for (int y = x + 1; y < N; ++y) {
+    const double cy = ld_c(B, y), lcy = ld_lc(B, y);
+    const double2 xy = dx[y];
+    const double ay = sqrt(xy.x * xy.x + xy.y * xy.y);
+    const double2 G = make_double2(head.x + run.x + xy.x * (cy - lcy), head.y + run.y + xy.y * (cy - lcy));
+    const double Gm = headm + runm + ay * (cy - lcy);
+    const int64_t e = pair_index(N, x, y), eS = e, eJ = P + e;
+    if (mode == 0) {
+      if (Gm > 0.0) {
+        bk.put(eJ, p, eS, G.x, -G.y, Gm);
+        bk.put(eS, p, eJ, -G.x, G.y, Gm);
+      }
+    } else {
+      const double2 sy = suf[(int64_t)p * N + y];
+      const double H_re = head.x + run.x + xy.x * (cy + lcy) + 2.0 * sy.x;
+      const double H_im = head.y + run.y + xy.y * (cy + lcy) + 2.0 * sy.y;
+      const double Hm = headm + runm + ay * fabs(cy + lcy) + 2.0 * sufm[(int64_t)p * N + y];
+      if (Gm > 0.0) {
+        bk.put(eS, p, eJ, G.x, G.y, Gm);
+        bk.put(eJ, p, eS, -G.x, -G.y, Gm);
+      }
+      if (Hm > 0.0) {
+        bk.put(eS, p, eS, -H_im, H_re, Hm);
+        bk.put(eJ, p, eJ, -H_im, H_re, Hm);
+      }
+    }
+    if (y < N - 1) {  // x < nu < y' for the next y' = y + 1
+      run.x += xy.x * cy;
+      run.y += xy.y * cy;
+      runm += ay * cy;
+    }
+  }
+}
+
+// U terms of the diagonal components on the D x D block, row D_lam, column
+// D_mu (one thread each): i 2 c_lam x_mu (mu < lam), i 2 c_mu x_lam
+// (mu > lam), i (2 sum_{nu > lam} x_nu c_nu + 2 (1 - lam) c_lam x_lam) (mu = lam).
+__global__ void k_udd_bucket(const BasisView B, int nP, const double2* dl, const int* hasD, const double2* suf,
+                             const double* sufm, Bucketer bk) {
+  const int N = B.N, D = N - 1;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nP * D * D) return;
+  const int p = (int)(t / ((int64_t)D * D));
+  if (!hasD[p]) return;
+  const int lam = 1 + (int)((t / D) % D), mu = 1 + (int)(t % D);
+  const double2* x = dl + (int64_t)p * N;
+  double re, im, mag;
+  if (mu != lam) {
+    const double c2 = 2.0 * ld_c(B, mu < lam ? lam : mu);
+    const double2 v = x[mu < lam ? mu : lam];
+    re = -c2 * v.y;
+    im = c2 * v.x;
+    mag = c2 * sqrt(v.x * v.x + v.y * v.y);
+  } else {
+    const double cc = 2.0 * (ld_c(B, lam) + ld_lc(B, lam));  // 2 (1 - lam) c_lam
+    const double2 sy = suf[(int64_t)p * N + lam];
+    const double sr = 2.0 * sy.x + cc * x[lam].x, si = 2.0 * sy.y + cc * x[lam].y;
+    re = -si;
+    im = sr;
+    mag = 2.0 * sufm[(int64_t)p * N + lam] + fabs(cc) * sqrt(x[lam].x * x[lam].x + x[lam].y * x[lam].y);
+  }
+  if (mag > 0.0) bk.put(d_index(B, lam), p, d_index(B, mu), re, im, mag);
+}
+
+// Q terms of the diagonal coefficients h_{D_lam}: only (S_xy, J_xy) and
+// (J_xy, S_xy), q_{S J} = sum_lam h_{D_lam} f(D_lam, J_xy, S_xy) = -G_xy[h]
+// and q_{J S} = -q_{S J}; one thread per x (the same running sums, real).
+__global__ void k_q_diag_bucket(BasisView B, const double* h, Bucketer bk) {
+  const int N = B.N;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= N) return;
+  const double* hd = h + 2 * B.P - 1;  // hd[nu] = h_{D_nu}
+  const double head = x >= 1 ? hd[x] * ld_lc(B, x) : 0.0;
+  const double headm = x >= 1 ? fabs(hd[x] * ld_lc(B, x)) : 0.0;
+  double run = 0.0, runm = 0.0;
+  for (int y = x + 1; y < N; ++y) {
+    const double cy = ld_c(B, y), lcy = ld_lc(B, y);
+    const double G = head + run + hd[y] * (cy - lcy);
+    const double Gm = headm + runm + fabs(hd[y]) * (cy - lcy);
+    if (Gm > 0.0) {
+      const int64_t e = pair_index(N, x, y);
+      bk.put(e, -1, B.P + e, -G, 0.0, Gm);
+      bk.put(B.P + e, -1, e, G, 0.0, Gm);
+    }
+    if (y < N - 1) {
+      run += hd[y] * cy;
+      runm += fabs(hd[y]) * cy;
+    }
+  }
 }
 
 // K (Eq. (08)): k_s = -(1/N) sum_jk Im(a_jk) f_jks over pairs (j, k) of one
@@ -329,21 +398,272 @@ __global__ void k_k_lowrank(BasisView B, int nP, const int64_t* lp_ptr, const do
   }
 }
 
-// Keep entries with |value| > 1e-12 * magnitude: flags and row counts.
-__global__ void k_keep(int64_t n, const int64_t* key, const RTerm* val, int64_t M, int* keep) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  keep[i] = fabs(val[i].val) > 1e-12 * val[i].mag ? 1 : 0;
+// ---------------------------------------------------------------- scan
+// Exclusive prefix sums of n int64 counts into off[0..n] (off[n] = total),
+// in three passes: tile sums, a scan of the tile sums by one block, and the
+// tile scans with their offsets.  A tile is 256 threads x 8 counts.
+constexpr int kScanThreads = 256, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t block_excl_scan(int64_t x, int64_t* warp_tot, int64_t& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) warp_tot[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int64_t w = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  total = warp_tot[kScanThreads / 32 - 1];
+  const int64_t before = wid > 0 ? warp_tot[wid - 1] : 0;
+  const int64_t r = before + inc - x;
+  __syncthreads();
+  return r;
 }
 
-__global__ void k_compact(int64_t n, const int64_t* key, const RTerm* val, const int* keep, const int64_t* pos,
-                          int64_t M, int64_t* rowcount, int32_t* col, double* out) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n || !keep[i]) return;
-  const int64_t o = pos[i];
-  col[o] = (int32_t)(key[i] % M);
-  out[o] = val[i].val;
-  atomicAdd(reinterpret_cast<unsigned long long*>(rowcount + key[i] / M), 1ULL);
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const unsigned long long* cnt, int64_t n,
+                                                             int64_t* off, int64_t* tile_sum, int add) {
+  __shared__ int64_t wt[kScanThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems], s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = base + i < n ? (int64_t)cnt[base + i] : 0;
+    s += v[i];
+  }
+  int64_t total;
+  int64_t run = block_excl_scan(s, wt, total);
+  if (!add) {
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+    return;
+  }
+  run += tile_sum[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < n) off[base + i] = run;
+    run += v[i];
+  }
+}
+
+// Exclusive scan of the tile sums in place (one block, chunks of 256); the
+// grand total goes to *total.
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(int64_t* tile_sum, int64_t nt, int64_t* total) {
+  __shared__ int64_t wt[kScanThreads / 32];
+  int64_t carry = 0;
+  for (int64_t b = 0; b < nt; b += kScanThreads) {
+    const int64_t i = b + threadIdx.x;
+    const int64_t x = i < nt ? tile_sum[i] : 0;
+    int64_t tot;
+    const int64_t e = block_excl_scan(x, wt, tot);
+    if (i < nt) tile_sum[i] = carry + e;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+// ---------------------------------------------------------------- rows
+constexpr int kRowCap = 512;          // hash slots of one warp (rows up to 256 terms)
+constexpr int kRowBound = 256;        // terms above which a row takes the block path
+constexpr int kRowWarps = 4;
+constexpr int kLongCap = 8192;        // hash slots of one block (long rows)
+constexpr int kLongThreads = 256;
+constexpr int32_t kEmpty = -1;
+
+struct RowInputs {
+  int64_t M;
+  const double* gamma;
+  const int64_t *woff, *uoff, *qoff;  // bucket offsets (M + 1 each; qoff may be null)
+  const BTerm *w, *u, *q;
+};
+
+__device__ __forceinline__ uint32_t slot_hash(int32_t n, uint32_t mask) {
+  return ((uint32_t)n * 2654435761u) & mask;
+}
+
+// Add (v, m) to column n; false if the table is full.
+__device__ __forceinline__ bool hash_add(int32_t* keys, double* val, double* mag, uint32_t mask, int32_t n, double v,
+                                         double m) {
+  uint32_t h = slot_hash(n, mask);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const int32_t k = atomicCAS(keys + h, kEmpty, n);
+    if (k == kEmpty || k == n) {
+      atomicAdd(val + h, v);
+      atomicAdd(mag + h, m);
+      return true;
+    }
+    h = (h + 1) & mask;
+  }
+  return false;
+}
+
+// Number of product and Q terms of row s (an upper bound of its columns).
+__device__ __forceinline__ int64_t row_terms(const RowInputs& I, int64_t s, int lane, int width) {
+  int64_t t = 0;
+  for (int64_t i = I.woff[s] + lane; i < I.woff[s + 1]; i += width) {
+    const int64_t l = I.w[i].x;
+    t += I.uoff[l + 1] - I.uoff[l];
+  }
+  if (lane == 0 && I.qoff) t += I.qoff[s + 1] - I.qoff[s];
+  return t;
+}
+
+// Accumulate row s into the table: threads `lane` of `width` take the W terms
+// of column s (each walks the U row of its l) and the row's Q terms.
+__device__ __forceinline__ bool row_accumulate(const RowInputs& I, int64_t s, int lane, int width, int32_t* keys,
+                                               double* val, double* mag, uint32_t mask) {
+  bool ok = true;
+  for (int64_t i = I.woff[s] + lane; i < I.woff[s + 1]; i += width) {
+    const BTerm wt = I.w[i];
+    const double g = I.gamma[wt.p];
+    for (int64_t j = I.uoff[wt.x]; j < I.uoff[wt.x + 1]; ++j) {
+      const BTerm ut = I.u[j];
+      if (ut.p != wt.p) continue;
+      ok &= hash_add(keys, val, mag, mask, ut.x, -0.5 * g * (wt.re * ut.re - wt.im * ut.im), 0.5 * g * wt.mag * ut.mag);
+    }
+  }
+  if (I.qoff)
+    for (int64_t i = I.qoff[s] + lane; i < I.qoff[s + 1]; i += width) {
+      const BTerm qt = I.q[i];
+      ok &= hash_add(keys, val, mag, mask, qt.x, qt.re, qt.mag);
+    }
+  return ok;
+}
+
+__device__ __forceinline__ bool kept(int32_t k, double v, double m) { return k != kEmpty && fabs(v) > 1e-12 * m; }
+
+// Move the kept entries of a table to its front (in slot order, 32 slots at a
+// time by ballot; a slot is read before any lane writes at or below it) and
+// return their number.  Called by one whole warp.
+__device__ __forceinline__ int warp_compact(int32_t* keys, double* val, const double* mag, int cap, int lane) {
+  int run = 0;
+  for (int base = 0; base < cap; base += 32) {
+    const int a = base + lane;
+    const int32_t k = keys[a];
+    const double v = val[a];
+    const bool kp = kept(k, v, mag[a]);
+    const unsigned bal = __ballot_sync(0xffffffffu, kp);
+    __syncwarp();
+    if (kp) {
+      const int pos = run + __popc(bal & ((1u << lane) - 1u));
+      keys[pos] = k;
+      val[pos] = v;
+    }
+    run += __popc(bal);
+    __syncwarp();
+  }
+  return run;
+}
+
+// Write k compacted entries in ascending column order: an entry's rank is
+// the number of entries with a smaller column.
+__device__ __forceinline__ void sorted_write(const int32_t* keys, const double* val, int k, int t, int nt,
+                                             int32_t* col, double* out) {
+  for (int e = t; e < k; e += nt) {
+    const int32_t ke = keys[e];
+    int rank = 0;
+    for (int f = 0; f < k; ++f) rank += keys[f] < ke ? 1 : 0;
+    col[rank] = ke;
+    out[rank] = val[e];
+  }
+}
+
+// Terms of every row (one warp per row): bound[s]; rows of more than
+// kRowBound terms go to the long list.
+__global__ void __launch_bounds__(kRowWarps * 32) k_row_terms(RowInputs I, unsigned long long* bound,
+                                                             int64_t* longlist, unsigned long long* nlong) {
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t s = (int64_t)blockIdx.x * kRowWarps + wid;
+  if (s >= I.M) return;
+  int64_t t = row_terms(I, s, lane, 32);
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) {
+    bound[s] = (unsigned long long)t;
+    if (t > kRowBound) longlist[atomicAdd(nlong, 1ull)] = s;
+  }
+}
+
+// One warp per row of at most kRowBound terms: accumulate the row once, write
+// its kept entries in ascending column order to the row's scratch range
+// (tmpoff[s], room for bound[s] >= kept entries) and their number to
+// rowcount[s].
+__global__ void __launch_bounds__(kRowWarps * 32) k_rows_warp(RowInputs I, const unsigned long long* bound,
+                                                             const int64_t* tmpoff, int32_t* tcol, double* tval,
+                                                             unsigned long long* rowcount, int* status) {
+  __shared__ int32_t keys_s[kRowWarps][kRowCap];
+  __shared__ double val_s[kRowWarps][kRowCap], mag_s[kRowWarps][kRowCap];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t s = (int64_t)blockIdx.x * kRowWarps + wid;
+  if (s >= I.M || bound[s] > (unsigned long long)kRowBound) return;
+  int32_t* keys = keys_s[wid];
+  double* val = val_s[wid];
+  double* mag = mag_s[wid];
+  for (int a = lane; a < kRowCap; a += 32) {
+    keys[a] = kEmpty;
+    val[a] = 0.0;
+    mag[a] = 0.0;
+  }
+  __syncwarp();
+  const bool ok = row_accumulate(I, s, lane, 32, keys, val, mag, kRowCap - 1);
+  if (!ok) atomicExch(status, 1);  // not reached: at most kRowBound columns in kRowCap slots
+  __syncwarp();
+  const int k = warp_compact(keys, val, mag, kRowCap, lane);
+  sorted_write(keys, val, k, lane, 32, tcol + tmpoff[s], tval + tmpoff[s]);
+  if (lane == 0) rowcount[s] = (unsigned long long)k;
+}
+
+// The same for one long row per block, a table of kLongCap slots in shared
+// memory; a row with more distinct columns sets *status = 2 (its kept
+// entries that found a slot are still written within its range).
+__global__ void __launch_bounds__(kLongThreads) k_rows_long(RowInputs I, const int64_t* longlist,
+                                                           const int64_t* tmpoff, int32_t* tcol, double* tval,
+                                                           unsigned long long* rowcount, int* status) {
+  extern __shared__ __align__(16) unsigned char lsm[];
+  double* val = reinterpret_cast<double*>(lsm);
+  double* mag = val + kLongCap;
+  int32_t* keys = reinterpret_cast<int32_t*>(mag + kLongCap);
+  __shared__ int kk;
+  const int64_t s = longlist[blockIdx.x];
+  for (int a = threadIdx.x; a < kLongCap; a += kLongThreads) {
+    keys[a] = kEmpty;
+    val[a] = 0.0;
+    mag[a] = 0.0;
+  }
+  __syncthreads();
+  const bool ok = row_accumulate(I, s, threadIdx.x, kLongThreads, keys, val, mag, kLongCap - 1);
+  if (!ok) atomicExch(status, 2);
+  __syncthreads();
+  if (threadIdx.x < 32) {  // compaction by warp 0
+    const int k = warp_compact(keys, val, mag, kLongCap, threadIdx.x);
+    if (threadIdx.x == 0) kk = k;
+  }
+  __syncthreads();
+  const int k = kk;
+  sorted_write(keys, val, k, threadIdx.x, kLongThreads, tcol + tmpoff[s], tval + tmpoff[s]);
+  if (threadIdx.x == 0) rowcount[s] = (unsigned long long)k;
+}
+
+// Rows from the scratch ranges to their CSR place (one warp per row).
+__global__ void __launch_bounds__(256) k_rows_copy(int64_t M, const int64_t* tmpoff, const int32_t* tcol,
+                                                  const double* tval, const int64_t* rowptr, int32_t* col,
+                                                  double* val) {
+  const int64_t s = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= M) return;
+  const int64_t src = tmpoff[s], dst = rowptr[s], k = rowptr[s + 1] - rowptr[s];
+  for (int64_t i = lane; i < k; i += 32) {
+    col[dst + i] = tcol[src + i];
+    val[dst + i] = tval[src + i];
+  }
 }
 
 inline unsigned nb(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -371,48 +691,42 @@ struct Buf {
     if (_e != cudaSuccess) return _e;     \
   } while (0)
 
-// exclusive scan of n int64 counts into off (n + 1 entries); returns the total
-static cudaError_t scan_counts(const int64_t* count, int64_t* off, int64_t n, int64_t* total, cudaStream_t st) {
-  size_t tmp = 0;
-  CK(cub::DeviceScan::ExclusiveSum(nullptr, tmp, count, off, (int)(n + 1), st));
-  Buf t;
-  CK(t.alloc(tmp));
-  CK(cub::DeviceScan::ExclusiveSum(t.p, tmp, count, off, (int)(n + 1), st));
+// off[0..n] = exclusive prefix sums of the n counts; *total (host) = off[n].
+static cudaError_t scan_counts(const unsigned long long* cnt, int64_t* off, int64_t n, int64_t* total,
+                               cudaStream_t st) {
+  const int64_t nt = (n + kScanTile - 1) / kScanTile;
+  Buf ts;
+  CK(ts.alloc(sizeof(int64_t) * (size_t)(nt + 1)));
+  if (nt > 0) {
+    k_scan_tiles<<<(unsigned)nt, kScanThreads, 0, st>>>(cnt, n, off, ts.as<int64_t>(), 0);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(ts.as<int64_t>(), nt, off + n);
+    k_scan_tiles<<<(unsigned)nt, kScanThreads, 0, st>>>(cnt, n, off, ts.as<int64_t>(), 1);
+    note_launch(3);
+  } else {
+    CK(cudaMemsetAsync(off, 0, sizeof(int64_t), st));
+  }
   CK(cudaMemcpyAsync(total, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   return cudaStreamSynchronize(st);
 }
 
-// sort (key, value) pairs and merge equal keys with op; returns unique count
-template <class V, class Op>
-static cudaError_t sort_reduce(int64_t n, Buf& key, Buf& val, Buf& okey, Buf& oval, int64_t* nuniq, Op op,
-                               int end_bit, cudaStream_t st) {
-  Buf k2, v2, tmp, nout;
-  CK(k2.alloc(sizeof(int64_t) * n));
-  CK(v2.alloc(sizeof(V) * n));
-  size_t tb = 0;
-  CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, key.as<int64_t>(), k2.as<int64_t>(), val.as<V>(), v2.as<V>(),
-                                     (int)n, 0, end_bit, st));
-  CK(tmp.alloc(tb));
-  CK(cub::DeviceRadixSort::SortPairs(tmp.p, tb, key.as<int64_t>(), k2.as<int64_t>(), val.as<V>(), v2.as<V>(),
-                                     (int)n, 0, end_bit, st));
-  CK(okey.alloc(sizeof(int64_t) * n));
-  CK(oval.alloc(sizeof(V) * n));
-  CK(nout.alloc(sizeof(int64_t)));
-  size_t tr = 0;
-  CK(cub::DeviceReduce::ReduceByKey(nullptr, tr, k2.as<int64_t>(), okey.as<int64_t>(), v2.as<V>(), oval.as<V>(),
-                                    nout.as<int64_t>(), op, (int)n, st));
-  Buf tmp2;
-  CK(tmp2.alloc(tr));
-  CK(cub::DeviceReduce::ReduceByKey(tmp2.p, tr, k2.as<int64_t>(), okey.as<int64_t>(), v2.as<V>(), oval.as<V>(),
-                                    nout.as<int64_t>(), op, (int)n, st));
-  CK(cudaMemcpyAsync(nuniq, nout.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  return cudaStreamSynchronize(st);
-}
+// Buckets of terms: counts (M + 1), offsets (M + 1), the terms.
+struct Buckets {
+  Buf cnt, off, terms;
+  int64_t total = 0;
+};
 
-static int bits_for(int64_t x) {
-  int b = 1;
-  while (b < 63 && (int64_t(1) << b) <= x) ++b;
-  return b;
+// Count with `emit(bucketer)`, scan, reset the cursors, fill with `emit`.
+template <class Emit>
+static cudaError_t build_buckets(int64_t M, Buckets& b, Emit emit, cudaStream_t st) {
+  CK(b.cnt.alloc(sizeof(unsigned long long) * (size_t)(M + 1)));
+  CK(b.off.alloc(sizeof(int64_t) * (size_t)(M + 1)));
+  CK(cudaMemsetAsync(b.cnt.p, 0, sizeof(unsigned long long) * (size_t)(M + 1), st));
+  CK(emit(Bucketer{b.cnt.as<unsigned long long>(), nullptr, nullptr}));
+  CK(scan_counts(b.cnt.as<unsigned long long>(), b.off.as<int64_t>(), M, &b.total, st));
+  CK(b.terms.alloc(sizeof(BTerm) * (size_t)b.total));
+  CK(cudaMemsetAsync(b.cnt.p, 0, sizeof(unsigned long long) * (size_t)(M + 1), st));
+  if (b.total > 0) CK(emit(Bucketer{b.cnt.as<unsigned long long>(), b.off.as<int64_t>(), b.terms.as<BTerm>()}));
+  return cudaSuccess;
 }
 
 cudaError_t assemble_lowrank_csr(const lb::BasisView& B, const double* h, int nP, const double* gamma_host,
@@ -422,133 +736,116 @@ cudaError_t assemble_lowrank_csr(const lb::BasisView& B, const double* h, int nP
   const int64_t nu = lp_ptr_host[nP];
   Buf dptr, dgamma;
   CK(dptr.alloc(sizeof(int64_t) * (nP + 1)));
-  CK(dgamma.alloc(sizeof(double) * nP));
+  CK(dgamma.alloc(sizeof(double) * (nP > 0 ? nP : 1)));
   CK(cudaMemcpyAsync(dptr.p, lp_ptr_host, sizeof(int64_t) * (nP + 1), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(dgamma.p, gamma_host, sizeof(double) * nP, cudaMemcpyHostToDevice, st));
-  const int kb = bits_for((int64_t)nP * M * M);
-  // ---- W and U coordinate lists
-  int64_t nwt = 0, nut = 0;
-  Buf cnt, off, wkey, wval, ukey, uval;
-  CK(cnt.alloc(sizeof(int64_t) * (nu + 1)));
-  CK(off.alloc(sizeof(int64_t) * (nu + 1)));
-  CK(cudaMemsetAsync(cnt.p, 0, sizeof(int64_t) * (nu + 1), st));
+  if (nP > 0) CK(cudaMemcpyAsync(dgamma.p, gamma_host, sizeof(double) * nP, cudaMemcpyHostToDevice, st));
+  const int64_t* dp = dptr.as<int64_t>();
+  // ---- diagonal components of the channels: dense per channel, suffix sums
+  const int N = B.N;
+  Buf dl, hasD, suf, sufm;
+  CK(dl.alloc(sizeof(double2) * (size_t)nP * N));
+  CK(hasD.alloc(sizeof(int) * (size_t)(nP > 0 ? nP : 1)));
+  CK(suf.alloc(sizeof(double2) * (size_t)nP * N));
+  CK(sufm.alloc(sizeof(double) * (size_t)nP * N));
+  CK(cudaMemsetAsync(dl.p, 0, sizeof(double2) * (size_t)nP * N, st));
+  CK(cudaMemsetAsync(hasD.p, 0, sizeof(int) * (size_t)(nP > 0 ? nP : 1), st));
   if (nu > 0) {
-    k_w_terms<<<nb(nu, 128), 128, 0, st>>>(B, nP, dptr.as<int64_t>(), lp_idx, lp_val, nu, nullptr, nullptr,
-                                           nullptr, cnt.as<int64_t>());
-    note_launch(1);
-  }
-  CK(scan_counts(cnt.as<int64_t>(), off.as<int64_t>(), nu, &nwt, st));
-  CK(wkey.alloc(sizeof(int64_t) * nwt));
-  CK(wval.alloc(sizeof(CTerm) * nwt));
-  if (nu > 0) {
-    k_w_terms<<<nb(nu, 128), 128, 0, st>>>(B, nP, dptr.as<int64_t>(), lp_idx, lp_val, nu, off.as<int64_t>(),
-                                           wkey.as<int64_t>(), wval.as<CTerm>(), nullptr);
-    k_u_terms<<<nb(nu, 128), 128, 0, st>>>(B, nP, dptr.as<int64_t>(), lp_idx, lp_val, nu, nullptr, nullptr,
-                                           nullptr, cnt.as<int64_t>());
+    k_dscatter<<<nb(nu, 256), 256, 0, st>>>(B, nP, dp, lp_idx, lp_val, nu, dl.as<double2>(), hasD.as<int>());
+    k_dsuffix<<<nb(nP, 128), 128, 0, st>>>(B, nP, dl.as<double2>(), hasD.as<int>(), suf.as<double2>(),
+                                           sufm.as<double>());
     note_launch(2);
   }
-  CK(scan_counts(cnt.as<int64_t>(), off.as<int64_t>(), nu, &nut, st));
-  CK(ukey.alloc(sizeof(int64_t) * nut));
-  CK(uval.alloc(sizeof(CTerm) * nut));
-  if (nu > 0) {
-    k_u_terms<<<nb(nu, 128), 128, 0, st>>>(B, nP, dptr.as<int64_t>(), lp_idx, lp_val, nu, off.as<int64_t>(),
-                                           ukey.as<int64_t>(), uval.as<CTerm>(), nullptr);
-    note_launch(1);
-  }
-  Buf wk, wv, uk, uv;
-  int64_t nw = 0, nuq = 0;
-  if (nwt > 0) CK(sort_reduce<CTerm>(nwt, wkey, wval, wk, wv, &nw, CTermSum(), kb, st));
-  if (nut > 0) CK(sort_reduce<CTerm>(nut, ukey, uval, uk, uv, &nuq, CTermSum(), kb, st));
-  // ---- R products and Q terms into one (s, n) coordinate list
-  Buf pcnt, poff;
-  int64_t np = 0;
-  CK(pcnt.alloc(sizeof(int64_t) * (nw + 1)));
-  CK(poff.alloc(sizeof(int64_t) * (nw + 1)));
-  CK(cudaMemsetAsync(pcnt.p, 0, sizeof(int64_t) * (nw + 1), st));
-  if (nw > 0 && nuq > 0) {
-    k_products<<<nb(nw, 256), 256, 0, st>>>(M, nP, dgamma.as<double>(), wk.as<int64_t>(), wv.as<CTerm>(), nw,
-                                            uk.as<int64_t>(), uv.as<CTerm>(), nuq, nullptr, nullptr, nullptr,
-                                            pcnt.as<int64_t>());
-    note_launch(1);
-  }
-  CK(scan_counts(pcnt.as<int64_t>(), poff.as<int64_t>(), nw, &np, st));
-  int64_t nqp = 0;
-  Buf qcnt, qoff;
-  const int64_t P2 = 2 * B.P;
+  const int64_t ndp = (int64_t)nP * N, ndd = (int64_t)nP * (N - 1) * (N - 1);
+  // ---- W (by column s), U (by row l), Q (by row s)
+  Buckets W, U, Q;
+  CK(build_buckets(M, W, [&](Bucketer bk) {
+    if (nu > 0) {
+      k_w_bucket<<<nb(nu, 128), 128, 0, st>>>(B, nP, dp, lp_idx, lp_val, nu, bk);
+      k_dpart_bucket<<<nb(ndp, 128), 128, 0, st>>>(B, nP, dl.as<double2>(), hasD.as<int>(), suf.as<double2>(),
+                                                   sufm.as<double>(), 0, bk);
+      note_launch(2);
+    }
+    return cudaGetLastError();
+  }, st));
+  CK(build_buckets(M, U, [&](Bucketer bk) {
+    if (nu > 0) {
+      k_u_bucket<<<nb(nu, 128), 128, 0, st>>>(B, nP, dp, lp_idx, lp_val, nu, bk);
+      k_dpart_bucket<<<nb(ndp, 128), 128, 0, st>>>(B, nP, dl.as<double2>(), hasD.as<int>(), suf.as<double2>(),
+                                                   sufm.as<double>(), 1, bk);
+      note_launch(2);
+      if (ndd > 0) {
+        k_udd_bucket<<<nb(ndd, 256), 256, 0, st>>>(B, nP, dl.as<double2>(), hasD.as<int>(), suf.as<double2>(),
+                                                   sufm.as<double>(), bk);
+        note_launch(1);
+      }
+    }
+    return cudaGetLastError();
+  }, st));
   if (h) {
-    CK(qcnt.alloc(sizeof(int64_t) * (P2 + 1)));
-    CK(qoff.alloc(sizeof(int64_t) * (P2 + 1)));
-    CK(cudaMemsetAsync(qcnt.p, 0, sizeof(int64_t) * (P2 + 1), st));
-    k_q_pair_terms<<<nb(P2, 128), 128, 0, st>>>(B, h, nullptr, nullptr, nullptr, qcnt.as<int64_t>());
-    note_launch(1);
-    CK(scan_counts(qcnt.as<int64_t>(), qoff.as<int64_t>(), P2, &nqp, st));
+    CK(build_buckets(M, Q, [&](Bucketer bk) {
+      k_q_pair_bucket<<<nb(2 * B.P, 128), 128, 0, st>>>(B, h, bk);
+      k_q_diag_bucket<<<nb(N, 128), 128, 0, st>>>(B, h, bk);
+      note_launch(2);
+      return cudaGetLastError();
+    }, st));
   }
-  const int64_t nqd = h ? 2 * B.P : 0;
-  const int64_t nt = np + nqp + nqd;
-  Buf tkey, tval;
-  CK(tkey.alloc(sizeof(int64_t) * nt));
-  CK(tval.alloc(sizeof(RTerm) * nt));
-  if (np > 0) {
-    k_products<<<nb(nw, 256), 256, 0, st>>>(M, nP, dgamma.as<double>(), wk.as<int64_t>(), wv.as<CTerm>(), nw,
-                                            uk.as<int64_t>(), uv.as<CTerm>(), nuq, poff.as<int64_t>(),
-                                            tkey.as<int64_t>(), tval.as<RTerm>(), nullptr);
+  // ---- rows: term bounds, one accumulation into scratch ranges, CSR
+  RowInputs I{M, dgamma.as<double>(), W.off.as<int64_t>(), U.off.as<int64_t>(), h ? Q.off.as<int64_t>() : nullptr,
+              W.terms.as<BTerm>(), U.terms.as<BTerm>(), h ? Q.terms.as<BTerm>() : nullptr};
+  Buf bound, tmpoff, longlist, ctr;  // ctr: [0] long rows, [1] status
+  CK(bound.alloc(sizeof(unsigned long long) * (size_t)(M + 1)));
+  CK(tmpoff.alloc(sizeof(int64_t) * (size_t)(M + 1)));
+  CK(longlist.alloc(sizeof(int64_t) * (size_t)M));
+  CK(ctr.alloc(sizeof(unsigned long long) * 2));
+  CK(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long) * 2, st));
+  unsigned long long* c = ctr.as<unsigned long long>();
+  int* status = reinterpret_cast<int*>(c + 1);
+  const unsigned rgrid = nb(M, kRowWarps);
+  k_row_terms<<<rgrid, kRowWarps * 32, 0, st>>>(I, bound.as<unsigned long long>(), longlist.as<int64_t>(), c);
+  note_launch(1);
+  int64_t nterms = 0;
+  CK(scan_counts(bound.as<unsigned long long>(), tmpoff.as<int64_t>(), M, &nterms, st));
+  unsigned long long hc[2];
+  CK(cudaMemcpyAsync(hc, c, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const int64_t nlong = (int64_t)hc[0];
+  Buf tcol, tval, rowc;
+  CK(tcol.alloc(sizeof(int32_t) * (size_t)(nterms + 1)));
+  CK(tval.alloc(sizeof(double) * (size_t)(nterms + 1)));
+  CK(rowc.alloc(sizeof(unsigned long long) * (size_t)(M + 1)));
+  k_rows_warp<<<rgrid, kRowWarps * 32, 0, st>>>(I, bound.as<unsigned long long>(), tmpoff.as<int64_t>(),
+                                                tcol.as<int32_t>(), tval.as<double>(), rowc.as<unsigned long long>(),
+                                                status);
+  note_launch(1);
+  if (nlong > 0) {
+    const size_t lsmem = (sizeof(double) * 2 + sizeof(int32_t)) * (size_t)kLongCap;
+    CK(cudaFuncSetAttribute(k_rows_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
+    k_rows_long<<<(unsigned)nlong, kLongThreads, lsmem, st>>>(I, longlist.as<int64_t>(), tmpoff.as<int64_t>(),
+                                                             tcol.as<int32_t>(), tval.as<double>(),
+                                                             rowc.as<unsigned long long>(), status);
     note_launch(1);
   }
-  if (nqp > 0) {
-    k_q_pair_terms<<<nb(P2, 128), 128, 0, st>>>(B, h, qoff.as<int64_t>(), tkey.as<int64_t>() + np,
-                                               tval.as<RTerm>() + np, nullptr);
-    note_launch(1);
-  }
-  if (nqd > 0) {
-    k_q_diag_terms<<<nb(B.P, 128), 128, 0, st>>>(B, h, tkey.as<int64_t>() + np + nqp,
-                                                tval.as<RTerm>() + np + nqp);
-    note_launch(1);
-  }
-  // ---- reduce by (s, n), keep, CSR
-  Buf fk, fv;
-  int64_t nf = 0;
-  if (nt > 0) CK(sort_reduce<RTerm>(nt, tkey, tval, fk, fv, &nf, RTermSum(), bits_for(M * M), st));
-  Buf keep, pos, rowc;
-  CK(keep.alloc(sizeof(int) * (nf + 1)));
-  CK(pos.alloc(sizeof(int64_t) * (nf + 1)));
-  CK(rowc.alloc(sizeof(int64_t) * (M + 1)));
-  CK(cudaMemsetAsync(rowc.p, 0, sizeof(int64_t) * (M + 1), st));
+  Buf rowptr;
+  CK(rowptr.alloc(sizeof(int64_t) * (size_t)(M + 1)));
   int64_t nnz = 0;
-  if (nf > 0) {
-    k_keep<<<nb(nf, 256), 256, 0, st>>>(nf, fk.as<int64_t>(), fv.as<RTerm>(), M, keep.as<int>());
-    note_launch(1);
-    size_t tmp = 0;
-    CK(cub::DeviceScan::ExclusiveSum(nullptr, tmp, keep.as<int>(), pos.as<int64_t>(), (int)nf, st));
-    Buf t;
-    CK(t.alloc(tmp));
-    CK(cub::DeviceScan::ExclusiveSum(t.p, tmp, keep.as<int>(), pos.as<int64_t>(), (int)nf, st));
-    int64_t lastpos = 0;
-    int lastkeep = 0;
-    CK(cudaMemcpyAsync(&lastpos, pos.as<int64_t>() + nf - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&lastkeep, keep.as<int>() + nf - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    nnz = lastpos + lastkeep;
-  }
-  Buf rowptr, col, val, K;
-  CK(rowptr.alloc(sizeof(int64_t) * (M + 1)));
-  CK(col.alloc(sizeof(int32_t) * (nnz + 1)));
-  CK(val.alloc(sizeof(double) * (nnz + 1)));
-  CK(K.alloc(sizeof(double) * M));
-  if (nf > 0) {
-    k_compact<<<nb(nf, 256), 256, 0, st>>>(nf, fk.as<int64_t>(), fv.as<RTerm>(), keep.as<int>(),
-                                          pos.as<int64_t>(), M, rowc.as<int64_t>(), col.as<int32_t>(),
-                                          val.as<double>());
-    note_launch(1);
-  }
-  int64_t total = 0;
-  CK(scan_counts(rowc.as<int64_t>(), rowptr.as<int64_t>(), M, &total, st));
+  CK(scan_counts(rowc.as<unsigned long long>(), rowptr.as<int64_t>(), M, &nnz, st));
+  CK(cudaMemcpyAsync(hc, c, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hc[1] != 0) return cudaErrorNotSupported;  // a row has more than kLongCap distinct columns
+  Buf col, val, K;
+  CK(col.alloc(sizeof(int32_t) * (size_t)(nnz + 1)));
+  CK(val.alloc(sizeof(double) * (size_t)(nnz + 1)));
+  CK(K.alloc(sizeof(double) * (size_t)M));
+  k_rows_copy<<<nb(M, 8), 256, 0, st>>>(M, tmpoff.as<int64_t>(), tcol.as<int32_t>(), tval.as<double>(),
+                                        rowptr.as<int64_t>(), col.as<int32_t>(), val.as<double>());
+  note_launch(1);
   // ---- K
   CK(cudaMemsetAsync(K.p, 0, sizeof(double) * M, st));
   int64_t maxn = 0;
   for (int p = 0; p < nP; ++p) maxn = lp_ptr_host[p + 1] - lp_ptr_host[p] > maxn ? lp_ptr_host[p + 1] - lp_ptr_host[p] : maxn;
   if (maxn > 0) {
     dim3 grid(nb(maxn * maxn, 256), nP);
-    k_k_lowrank<<<grid, 256, 0, st>>>(B, nP, dptr.as<int64_t>(), dgamma.as<double>(), lp_idx, lp_val, K.as<double>());
+    k_k_lowrank<<<grid, 256, 0, st>>>(B, nP, dp, dgamma.as<double>(), lp_idx, lp_val, K.as<double>());
     note_launch(1);
   }
   CK(cudaStreamSynchronize(st));
@@ -563,7 +860,7 @@ cudaError_t assemble_lowrank_csr(const lb::BasisView& B, const double* h, int nP
   val.p = nullptr;
   out->K = K.as<double>();
   K.p = nullptr;
-  out->terms = np + nqp + nqd;
+  out->terms = nterms;
   return cudaSuccess;
 }
 
