@@ -910,13 +910,17 @@ def form_serving(args, dev, a200=None):
 
     srv = lb.Server(int(args.serve_budget_gb * 2**30), slots=8, bypass_ms=2000.0)
     # alone latencies (also warms the pool and the graph path)
-    alone = {}
+    alone, alone_host = {}, {}
     for N in Nset:
         H, a, v0 = inputs(N, -1 - N, rings[N][0])
         out = torch.empty_like(v0)
         torch.cuda.synchronize()
         rid = srv.submit(a, v0, out, dt, steps, H=H, precision=prec[N], correct_every=corr[N])
-        alone[N] = srv.wait(rid)["latency_ms"]
+        r0 = srv.wait(rid)
+        alone[N] = r0["latency_ms"]
+        # host share of the service: admission -> completion seen by the host,
+        # minus the device span of the request's work
+        alone_host[N] = r0["latency_ms"] - r0["queue_ms"] - r0["gpu_ms"]
     # sustainable throughput: a burst of requests submitted at once (mixed N,
     # the trace's distribution), completions per second until the last
     burst_N = [int(x) for x in wl.rng(args.seed + 78).choice(np.asarray(Nset), size=args.serve_burst)]
@@ -1006,7 +1010,12 @@ def form_serving(args, dev, a200=None):
         if l:
             per_N[str(N)] = {"count": len(l), "p50_ms": float(np.percentile(l, 50)),
                              "p99_ms": float(np.percentile(l, 99)), "alone_ms": alone[N],
-                             "fp64_alone_ms": fp64_ms.get(N)}
+                             "alone_host_ms": alone_host[N], "fp64_alone_ms": fp64_ms.get(N)}
+    # what a device-resident request loop could remove at most: the host
+    # share of each request's service (admission -> completion seen by the
+    # host, minus the device span of its work)
+    host = np.array([r["latency_ms"] - r["queue_ms"] - r["gpu_ms"] for r in res])
+    svc = np.array([r["latency_ms"] - r["queue_ms"] for r in res])
     # one-at-a-time FP64 replay of the same trace (one slot, no memory limit)
     svc64 = np.array([fp64_ms[int(n)] for n in Nreq])
     start64, fin64 = lb.native.sched_simulate(np.asarray(arr) * 1e3, np.ones(len(arr), np.int64), svc64,
@@ -1031,6 +1040,10 @@ def form_serving(args, dev, a200=None):
                                            "service time per N, the same arrival trace through one slot"},
             "speedup_throughput_vs_fp64_one_at_a_time": st["throughput_per_s"] / thr64,
             "ring_waits": ring_waits,
+            "host_share": {"p50_ms": float(np.percentile(host, 50)), "max_ms": float(host.max()),
+                           "sum_over_service": float(host.sum() / svc.sum()),
+                           "note": "per request: latency - queue - device span of its work; the bound on what a "
+                                   "device-resident request loop could save"},
             "budget_gb": args.serve_budget_gb, "slots": 8,
             "note": "config 5's request stream with %d RK4 steps per request (the configuration names 5000) so "
                     "that the run stays within minutes; latency = submission (at the arrival time) to completion "

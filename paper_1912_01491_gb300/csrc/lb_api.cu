@@ -13,7 +13,6 @@
 #include <mutex>
 #include <new>
 #include <vector>
-#include <cub/cub.cuh>
 #include <string>
 
 #include "lb_internal.h"
@@ -194,15 +193,7 @@ int count_and_scan(const lb_basis_t* b, int which, DevBuf& offsets, int64_t* tot
   if ((rc = alloc_or_enomem(offsets, sizeof(int64_t) * (M + 1), "structure offsets")) != LB_OK) return rc;
   LB_TRY_CUDA(cudaMemsetAsync(per.as<int64_t>() + M, 0, sizeof(int64_t), st), "structure counts");
   LB_TRY_CUDA(lbi::structure_count(b->view(), which, per.as<int64_t>(), st), "kernel (a) count");
-  size_t tmp = 0;
-  LB_TRY_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, per.as<int64_t>(), offsets.as<int64_t>(),
-                                            (int)(M + 1), st),
-              "scan");
-  DevBuf tb;
-  if ((rc = alloc_or_enomem(tb, tmp, "scan workspace")) != LB_OK) return rc;
-  LB_TRY_CUDA(cub::DeviceScan::ExclusiveSum(tb.p, tmp, per.as<int64_t>(), offsets.as<int64_t>(),
-                                            (int)(M + 1), st),
-              "scan");
+  LB_TRY_CUDA(lbi::exclusive_scan(per.as<int64_t>(), offsets.as<int64_t>(), M, st), "scan");
   LB_TRY_CUDA(cudaMemcpyAsync(total, offsets.as<int64_t>() + M, sizeof(int64_t),
                               cudaMemcpyDeviceToHost, st),
               "structure total");

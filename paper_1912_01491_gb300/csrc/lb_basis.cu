@@ -16,8 +16,6 @@
 //     for l >= max(a,1) except (a,b,l) = (0,1,1);
 //   * d(D_l, D_l, D_r) for r >= l except l = r = 1 (canonical form of the
 //     "two smallest equal" rule).
-#include <cub/cub.cuh>
-
 #include "lb_internal.h"
 
 namespace {

@@ -30,108 +30,78 @@ namespace {
 
 using namespace lb;
 
-// Every (l, s) with f_{k l s} != 0, with the value.
+// The fibres of a pair element, cut into 2N - 1 slices so that one thread
+// takes one slice: slice t < N holds the entries whose third vertex is
+// w = t (none for w on the element's edge), slice t >= N the entries with
+// D_lam, lam = t - N + 1: fiber_slices(N) slices per element.
+__host__ __device__ inline int fiber_slices(int N) { return 2 * N - 1; }
+
+// Slice t of the f-fibre of the pair element k: every (l, s) with
+// f_{k l s} != 0, with the value.
 template <class Emit>
-__device__ void for_each_f_fiber(const BasisView& B, int64_t k, Emit& emit) {
+__device__ void f_fiber_slice(const BasisView& B, int64_t k, int t, Emit& emit) {
   const int N = B.N;
   const Elem ek = decode(B, k);
-  if (ek.kind != kD) {
-    const int a = ek.a, b = ek.b, tk = ek.kind;
+  const int a = ek.a, b = ek.b, tk = ek.kind;
+  if (t < N) {
+    const int w = t;
+    if (w == a || w == b) return;
     for (int vi = 0; vi < 2; ++vi) {
       const int v = vi ? b : a, vp = vi ? a : b;
-      for (int w = 0; w < N; ++w) {
-        if (w == a || w == b) continue;
-        for (int tl = kS; tl <= kJ; ++tl) {
-          const Elem el = make_pair(tl, v, w), es = make_pair(1 ^ tk ^ tl, vp, w);
-          emit(elem_index(B, tl, v, w), elem_index(B, es.kind, vp, w), f_value(B, ek, el, es));
-        }
+      for (int tl = kS; tl <= kJ; ++tl) {
+        const Elem el = make_pair(tl, v, w), es = make_pair(1 ^ tk ^ tl, vp, w);
+        emit(elem_index(B, tl, v, w), elem_index(B, es.kind, vp, w), f_value(B, ek, el, es));
       }
     }
+  } else {
+    const int lam = t - N + 1;
+    if (lam < imax(a, 1) || lam > b) return;
     const Elem ekb = make_pair(1 - tk, a, b);
     const int64_t kb = partner(B, k);
-    for (int lam = imax(a, 1); lam <= b; ++lam) {
-      emit(kb, d_index(B, lam), f_value(B, ek, ekb, make_d(lam)));
-      emit(d_index(B, lam), kb, f_value(B, ek, make_d(lam), ekb));
-    }
-  } else {
-    const int nu = ek.a;
-    for (int x = 0; x <= nu; ++x)
-      for (int y = imax(nu, x + 1); y < N; ++y)
-        for (int tl = kS; tl <= kJ; ++tl) {
-          const Elem el = make_pair(tl, x, y), es = make_pair(1 - tl, x, y);
-          emit(elem_index(B, tl, x, y), elem_index(B, 1 - tl, x, y), f_value(B, ek, el, es));
-        }
+    emit(kb, d_index(B, lam), f_value(B, ek, ekb, make_d(lam)));
+    emit(d_index(B, lam), kb, f_value(B, ek, make_d(lam), ekb));
   }
 }
 
-// Every (l, n) with z_{j l n} != 0, with z = f + i d.
+// Slice t of the z-fibre of the pair element j: every (l, n) with
+// z_{j l n} != 0, with z = f + i d.
 template <class Emit>
-__device__ void for_each_z_fiber(const BasisView& B, int64_t j, Emit& emit) {
+__device__ void z_fiber_slice(const BasisView& B, int64_t j, int t, Emit& emit) {
   const int N = B.N;
   const Elem ej = decode(B, j);
+  const int a = ej.a, b = ej.b, tj = ej.kind;
   double f, d;
-  if (ej.kind != kD) {
-    const int a = ej.a, b = ej.b, tj = ej.kind;
+  if (t < N) {
+    const int w = t;
+    if (w == a || w == b) return;
     for (int vi = 0; vi < 2; ++vi) {
       const int v = vi ? b : a, vp = vi ? a : b;
-      for (int w = 0; w < N; ++w) {
-        if (w == a || w == b) continue;
-        for (int tl = kS; tl <= kJ; ++tl) {
-          const Elem el = make_pair(tl, v, w);
-          const int64_t l = elem_index(B, tl, v, w);
-          const Elem enf = make_pair(1 ^ tj ^ tl, vp, w), end = make_pair(tj ^ tl, vp, w);
-          fd_value(B, ej, el, enf, f, d);
-          emit(l, elem_index(B, enf.kind, vp, w), f, 0.0);
-          fd_value(B, ej, el, end, f, d);
-          emit(l, elem_index(B, end.kind, vp, w), 0.0, d);
-        }
-      }
-    }
-    const Elem ejb = make_pair(1 - tj, a, b);
-    const int64_t jb = partner(B, j);
-    for (int lam = imax(a, 1); lam < N; ++lam) {
-      const Elem ed = make_d(lam);
-      if (lam <= b) {  // f-fibres: (partner(j), D) and (D, partner(j))
-        fd_value(B, ej, ejb, ed, f, d);
-        emit(jb, d_index(B, lam), f, 0.0);
-        fd_value(B, ej, ed, ejb, f, d);
-        emit(d_index(B, lam), jb, f, 0.0);
-      }
-      if (!(a == 0 && b == 1 && lam == 1)) {  // d-fibres: (j, D) and (D, j)
-        fd_value(B, ej, ej, ed, f, d);
-        emit(j, d_index(B, lam), 0.0, d);
-        fd_value(B, ej, ed, ej, f, d);
-        emit(d_index(B, lam), j, 0.0, d);
+      for (int tl = kS; tl <= kJ; ++tl) {
+        const Elem el = make_pair(tl, v, w);
+        const int64_t l = elem_index(B, tl, v, w);
+        const Elem enf = make_pair(1 ^ tj ^ tl, vp, w), end = make_pair(tj ^ tl, vp, w);
+        fd_value(B, ej, el, enf, f, d);
+        emit(l, elem_index(B, enf.kind, vp, w), f, 0.0);
+        fd_value(B, ej, el, end, f, d);
+        emit(l, elem_index(B, end.kind, vp, w), 0.0, d);
       }
     }
   } else {
-    const int nu = ej.a;
-    for (int x = 0; x < N; ++x)
-      for (int y = x + 1; y < N; ++y) {
-        if (nu < imax(x, 1)) continue;
-        for (int tl = kS; tl <= kJ; ++tl) {
-          const Elem el = make_pair(tl, x, y), elb = make_pair(1 - tl, x, y);
-          const int64_t l = elem_index(B, tl, x, y);
-          if (nu <= y) {
-            fd_value(B, ej, el, elb, f, d);
-            emit(l, partner(B, l), f, 0.0);
-          }
-          if (!(x == 0 && y == 1 && nu == 1)) {
-            fd_value(B, ej, el, el, f, d);
-            emit(l, l, 0.0, d);
-          }
-        }
-      }
-    for (int lam = 1; lam < N; ++lam) {
-      if (lam != nu) {
-        const int m = imin(lam, nu);
-        emit(d_index(B, lam), d_index(B, m), 0.0, 2.0 * trace_ddd(B, m, lam, nu));
-      } else {
-        for (int mu = nu; mu < N; ++mu) {
-          if (mu == 1 && nu == 1) continue;
-          emit(d_index(B, lam), d_index(B, mu), 0.0, 2.0 * trace_ddd(B, mu, lam, nu));
-        }
-      }
+    const int lam = t - N + 1;
+    if (lam < imax(a, 1)) return;
+    const Elem ejb = make_pair(1 - tj, a, b), ed = make_d(lam);
+    const int64_t jb = partner(B, j);
+    if (lam <= b) {  // f-fibres: (partner(j), D) and (D, partner(j))
+      fd_value(B, ej, ejb, ed, f, d);
+      emit(jb, d_index(B, lam), f, 0.0);
+      fd_value(B, ej, ed, ejb, f, d);
+      emit(d_index(B, lam), jb, f, 0.0);
+    }
+    if (!(a == 0 && b == 1 && lam == 1)) {  // d-fibres: (j, D) and (D, j)
+      fd_value(B, ej, ej, ed, f, d);
+      emit(j, d_index(B, lam), 0.0, d);
+      fd_value(B, ej, ed, ej, f, d);
+      emit(d_index(B, lam), j, 0.0, d);
     }
   }
 }
@@ -162,25 +132,31 @@ struct Bucketer {
   }
 };
 
-// W terms into buckets by column s: (p, l, conj(l_k) f_kls, |l_k f|).
+// W terms into buckets by column s: (p, l, conj(l_k) f_kls, |l_k f|); one
+// thread per (nonzero u of a pair element, fibre slice).
 __global__ void k_w_bucket(BasisView B, int nP, const int64_t* lp_ptr, const int64_t* lp_idx, const double2* lp_val,
                            int64_t nu, Bucketer bk) {
-  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (u >= nu) return;
+  const int S = fiber_slices(B.N);
+  const int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (it >= nu * S) return;
+  const int64_t u = it / S;
   const int64_t k = lp_idx[u];
   if (k >= 2 * B.P) return;  // diagonal components: k_dpart_bucket
   const int p = channel_of(lp_ptr, nP, u);
   const double2 lk = lp_val[u];
   const double am = sqrt(lk.x * lk.x + lk.y * lk.y);
   auto emit = [&](int64_t l, int64_t s, double f) { bk.put(s, p, l, lk.x * f, -lk.y * f, am * fabs(f)); };
-  for_each_f_fiber(B, k, emit);
+  f_fiber_slice(B, k, (int)(it % S), emit);
 }
 
-// U terms into buckets by row l: (p, n, l_j z_jln, |l_j z|).
+// U terms into buckets by row l: (p, n, l_j z_jln, |l_j z|); one thread per
+// (nonzero u of a pair element, fibre slice).
 __global__ void k_u_bucket(BasisView B, int nP, const int64_t* lp_ptr, const int64_t* lp_idx, const double2* lp_val,
                            int64_t nu, Bucketer bk) {
-  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (u >= nu) return;
+  const int S = fiber_slices(B.N);
+  const int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (it >= nu * S) return;
+  const int64_t u = it / S;
   const int64_t j = lp_idx[u];
   if (j >= 2 * B.P) return;  // diagonal components: k_dpart_bucket, k_udd_bucket
   const int p = channel_of(lp_ptr, nP, u);
@@ -189,18 +165,25 @@ __global__ void k_u_bucket(BasisView B, int nP, const int64_t* lp_ptr, const int
   auto emit = [&](int64_t l, int64_t n, double zr, double zi) {
     bk.put(l, p, n, lj.x * zr - lj.y * zi, lj.x * zi + lj.y * zr, am * sqrt(zr * zr + zi * zi));
   };
-  for_each_z_fiber(B, j, emit);
+  z_fiber_slice(B, j, (int)(it % S), emit);
 }
 
-// Q terms of the pair coefficients h_m (m < 2P, h_m != 0) into buckets by
-// row s: f_{m n s} for (n, s) on the fibre of m.
-__global__ void k_q_pair_bucket(BasisView B, const double* h, Bucketer bk) {
+// The pair indices m < 2P with h_m != 0, in any order: list, *count.
+__global__ void k_h_nonzero(int64_t P2, const double* h, int64_t* list, unsigned long long* count) {
   const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (m >= 2 * B.P) return;
+  if (m < P2 && h[m] != 0.0) list[atomicAdd(count, 1ull)] = m;
+}
+
+// Q terms of the nonzero pair coefficients h_m into buckets by row s:
+// f_{m n s} for (n, s) on the fibre of m; one thread per (m, fibre slice).
+__global__ void k_q_pair_bucket(BasisView B, const double* h, const int64_t* hlist, int64_t nh, Bucketer bk) {
+  const int S = fiber_slices(B.N);
+  const int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (it >= nh * S) return;
+  const int64_t m = hlist[it / S];
   const double hm = h[m];
-  if (hm == 0.0) return;
   auto emit = [&](int64_t n, int64_t s, double f) { bk.put(s, -1, n, hm * f, 0.0, fabs(hm * f)); };
-  for_each_f_fiber(B, m, emit);
+  f_fiber_slice(B, m, (int)(it % S), emit);
 }
 
 // ------------------------------------------------ diagonal components
@@ -431,8 +414,9 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t x, int64_t* warp_tot,
   return r;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const unsigned long long* cnt, int64_t n,
-                                                             int64_t* off, int64_t* tile_sum, int add) {
+template <class C>
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const C* cnt, int64_t n, int64_t* off,
+                                                             int64_t* tile_sum, int add) {
   __shared__ int64_t wt[kScanThreads / 32];
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
   int64_t v[kScanItems], s = 0;
@@ -691,22 +675,34 @@ struct Buf {
     if (_e != cudaSuccess) return _e;     \
   } while (0)
 
-// off[0..n] = exclusive prefix sums of the n counts; *total (host) = off[n].
-static cudaError_t scan_counts(const unsigned long long* cnt, int64_t* off, int64_t n, int64_t* total,
-                               cudaStream_t st) {
+// off[0..n] = exclusive prefix sums of the n counts (off[n] = the total).
+template <class C>
+static cudaError_t scan_device(const C* cnt, int64_t* off, int64_t n, cudaStream_t st) {
   const int64_t nt = (n + kScanTile - 1) / kScanTile;
   Buf ts;
   CK(ts.alloc(sizeof(int64_t) * (size_t)(nt + 1)));
   if (nt > 0) {
-    k_scan_tiles<<<(unsigned)nt, kScanThreads, 0, st>>>(cnt, n, off, ts.as<int64_t>(), 0);
+    k_scan_tiles<C><<<(unsigned)nt, kScanThreads, 0, st>>>(cnt, n, off, ts.as<int64_t>(), 0);
     k_scan_top<<<1, kScanThreads, 0, st>>>(ts.as<int64_t>(), nt, off + n);
-    k_scan_tiles<<<(unsigned)nt, kScanThreads, 0, st>>>(cnt, n, off, ts.as<int64_t>(), 1);
+    k_scan_tiles<C><<<(unsigned)nt, kScanThreads, 0, st>>>(cnt, n, off, ts.as<int64_t>(), 1);
     note_launch(3);
   } else {
     CK(cudaMemsetAsync(off, 0, sizeof(int64_t), st));
   }
+  // the tile sums are freed when this returns: the scan must be complete
+  return cudaStreamSynchronize(st);
+}
+
+// The same, and *total (host) = off[n].
+static cudaError_t scan_counts(const unsigned long long* cnt, int64_t* off, int64_t n, int64_t* total,
+                               cudaStream_t st) {
+  CK(scan_device(cnt, off, n, st));
   CK(cudaMemcpyAsync(total, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   return cudaStreamSynchronize(st);
+}
+
+cudaError_t exclusive_scan(const int64_t* counts, int64_t* off, int64_t n, cudaStream_t st) {
+  return scan_device(counts, off, n, st);
 }
 
 // Buckets of terms: counts (M + 1), offsets (M + 1), the terms.
@@ -756,11 +752,12 @@ cudaError_t assemble_lowrank_csr(const lb::BasisView& B, const double* h, int nP
     note_launch(2);
   }
   const int64_t ndp = (int64_t)nP * N, ndd = (int64_t)nP * (N - 1) * (N - 1);
+  const int S = fiber_slices(N);
   // ---- W (by column s), U (by row l), Q (by row s)
   Buckets W, U, Q;
   CK(build_buckets(M, W, [&](Bucketer bk) {
     if (nu > 0) {
-      k_w_bucket<<<nb(nu, 128), 128, 0, st>>>(B, nP, dp, lp_idx, lp_val, nu, bk);
+      k_w_bucket<<<nb(nu * S, 256), 256, 0, st>>>(B, nP, dp, lp_idx, lp_val, nu, bk);
       k_dpart_bucket<<<nb(ndp, 128), 128, 0, st>>>(B, nP, dl.as<double2>(), hasD.as<int>(), suf.as<double2>(),
                                                    sufm.as<double>(), 0, bk);
       note_launch(2);
@@ -769,7 +766,7 @@ cudaError_t assemble_lowrank_csr(const lb::BasisView& B, const double* h, int nP
   }, st));
   CK(build_buckets(M, U, [&](Bucketer bk) {
     if (nu > 0) {
-      k_u_bucket<<<nb(nu, 128), 128, 0, st>>>(B, nP, dp, lp_idx, lp_val, nu, bk);
+      k_u_bucket<<<nb(nu * S, 256), 256, 0, st>>>(B, nP, dp, lp_idx, lp_val, nu, bk);
       k_dpart_bucket<<<nb(ndp, 128), 128, 0, st>>>(B, nP, dl.as<double2>(), hasD.as<int>(), suf.as<double2>(),
                                                    sufm.as<double>(), 1, bk);
       note_launch(2);
@@ -782,10 +779,22 @@ cudaError_t assemble_lowrank_csr(const lb::BasisView& B, const double* h, int nP
     return cudaGetLastError();
   }, st));
   if (h) {
+    Buf hlist, hcount;
+    CK(hlist.alloc(sizeof(int64_t) * (size_t)(2 * B.P)));
+    CK(hcount.alloc(sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(hcount.p, 0, sizeof(unsigned long long), st));
+    k_h_nonzero<<<nb(2 * B.P, 256), 256, 0, st>>>(2 * B.P, h, hlist.as<int64_t>(), hcount.as<unsigned long long>());
+    note_launch(1);
+    unsigned long long nh = 0;
+    CK(cudaMemcpyAsync(&nh, hcount.p, sizeof(nh), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     CK(build_buckets(M, Q, [&](Bucketer bk) {
-      k_q_pair_bucket<<<nb(2 * B.P, 128), 128, 0, st>>>(B, h, bk);
+      if (nh > 0) {
+        k_q_pair_bucket<<<nb((int64_t)nh * S, 256), 256, 0, st>>>(B, h, hlist.as<int64_t>(), (int64_t)nh, bk);
+        note_launch(1);
+      }
       k_q_diag_bucket<<<nb(N, 128), 128, 0, st>>>(B, h, bk);
-      note_launch(2);
+      note_launch(1);
       return cudaGetLastError();
     }, st));
   }

@@ -66,6 +66,9 @@ struct CsrOut {
   double* val = nullptr;      // nnz
   double* K = nullptr;        // M
 };
+// off[0..n] = exclusive prefix sums of n int64 counts (off[n] = total);
+// synchronous with respect to st.
+cudaError_t exclusive_scan(const int64_t* counts, int64_t* off, int64_t n, cudaStream_t st);
 cudaError_t assemble_lowrank_csr(const lb::BasisView& B, const double* h, int nP, const double* gamma_host,
                                  const int64_t* lp_ptr_host, const int64_t* lp_idx, const double2* lp_val,
                                  CsrOut* out, cudaStream_t st);
