@@ -68,7 +68,10 @@ def parse():
     p.add_argument("--sparse-steps", type=int, default=200)
     p.add_argument("--dimer-n", type=int, default=400)
     p.add_argument("--dimer-steps", type=int, default=20000)
-    p.add_argument("--only", default=None, choices=["dense_small", "sparse", "dimer", "batched", "serving"],
+    p.add_argument("--spectrum-n", type=int, default=50)
+    p.add_argument("--spectrum-out", default=None, help="write the eigenvalues and the density grid (.npz)")
+    p.add_argument("--only", default=None, choices=["dense_small", "sparse", "dimer", "batched", "serving",
+                                                   "spectrum"],
                    help="run one of the other workloads alone and print its JSON (profiling aid)")
     return p.parse_args()
 
@@ -279,7 +282,8 @@ def run_gb300(args):
     roof = assembly_roofline(args.algorithm, top, kern[top], N, M, W, fp64_peak, measured_peaks())
     # a bounded attempt at N = 200: GMRES without a preconditioner needs
     # thousands of iterations of 2.5 ms there (the residual is reported)
-    checks = fp64_checks(lb, B, A, K, [("rk4_fp64", v64), ("rk4_fp32_corrected", v32)], restart=300, max_iter=600)
+    checks = fp64_checks(lb, B, A, K, [("rk4_fp64", v64), ("rk4_fp32_corrected", v32)], restart=300, max_iter=600,
+                         H=H, plain_max_iter=600)
 
     e2e = None
     if not args.no_e2e:
@@ -409,22 +413,40 @@ def assembly_roofline(algorithm, top, top_ms, N, M, W, fp64_peak, peaks):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "algorithmic_bytes_per_launch": byts}
 
 
-def fp64_checks(lb, B, A, K, states, restart=0, max_iter=3000):
+def fp64_checks(lb, B, A, K, states, restart=0, max_iter=3000, H=None, plain_max_iter=None):
     """Outside the timed region: the FP64 steady state of the assembled
-    system (restarted GMRES on the device, true relative residual) and the device
-    checks of rho (Tr rho - 1, Hermiticity, smallest pivot of the Cholesky
-    factorisation of rho + 1e-10) for the given states and the steady state."""
+    system (restarted GMRES on the device, preconditioned from the eigenbasis
+    of H when H is given; true relative residual) and the device checks of
+    rho (Tr rho - 1, Hermiticity, smallest pivot of the Cholesky
+    factorisation of rho + 1e-10) for the given states and the steady state.
+    With plain_max_iter, the unpreconditioned GMRES runs too, for comparison."""
     import torch
     ev = _events(2)
+    first_ms = None
+    if H is not None:  # the first use in a process also loads the solver library's eigensolver
+        ev[0].record()
+        lb.steady_state(A, K, tol=1e-12, max_iter=max_iter, restart=restart, basis=B, H=H)
+        ev[1].record()
+        torch.cuda.synchronize()
+        first_ms = ev[0].elapsed_time(ev[1])
     ev[0].record()
-    vs, res, it = lb.steady_state(A, K, tol=1e-12, max_iter=max_iter, restart=restart)
+    vs, res, it = lb.steady_state(A, K, tol=1e-12, max_iter=max_iter, restart=restart, basis=B, H=H)
     ev[1].record()
     torch.cuda.synchronize()
     names = [n for n, _ in states] + ["steady_state"]
     V = torch.stack([v for _, v in states] + [vs]).contiguous()
     out = lb.rho_checks(B, V, psd_shift=1e-10)
-    return {"steady_state": {"rel_residual": res, "iterations": it, "restart": restart or min(A.shape[0], 1024),
-                             "max_iter": max_iter, "ms": ev[0].elapsed_time(ev[1])},
+    ss = {"rel_residual": res, "iterations": it, "restart": restart or min(A.shape[0], 1024),
+          "max_iter": max_iter, "ms": ev[0].elapsed_time(ev[1]),
+          "preconditioner": "H eigenbasis, sigma = -Tr(A)/M" if H is not None else None,
+          "first_call_ms": first_ms}
+    if plain_max_iter:
+        ev[0].record()
+        _, res0, it0 = lb.steady_state(A, K, tol=1e-12, max_iter=plain_max_iter, restart=restart)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ss["plain"] = {"rel_residual": res0, "iterations": it0, "ms": ev[0].elapsed_time(ev[1])}
+    return {"steady_state": ss,
             "rho": {n: {"trace_minus_1": float(out[k, 0]), "hermiticity": float(out[k, 1]),
                         "min_cholesky_pivot_shift_1e-10": float(out[k, 2])} for k, n in enumerate(names)},
             "note": "FP64 on the device: restarted GMRES for (Q + R) v* = -K, and rho rebuilt from v"}
@@ -459,11 +481,15 @@ def run_e2e(args, lb, B, a, H_host, M, nrk, dt, dev, dist, world):
             t_tot.append(t2 - t0)
             phases.append(ph)
     sa, st = replica_max([sum(t_asm), sum(t_tot)], dist, dev)
+    pinned = a_host.is_pinned()
     del a_host
     lb.native.host_release()
-    # lb_assemble brings the upper triangle of a (row blocks of h rows, columns
-    # from the block's first row on) for M > 2048, all of a otherwise
-    if M > 2048:
+    # lb_assemble reads the upper triangle of a page-locked a over the host
+    # link; a pageable a would cross in row blocks of h rows (columns from the
+    # block's first row on) for M > 2048, whole otherwise
+    if pinned:
+        a_bytes = 16 * (M * (M + 1) // 2)
+    elif M > 2048:
         h = max(256, (M + 63) // 64)
         a_bytes = sum(16 * (min(M, j0 + h) - j0) * (M - j0) for j0 in range(0, M, h))
     else:
@@ -550,6 +576,7 @@ def run_forms(args, dev, a200=None):
     if not args.no_small:
         out["dense_n10"] = form_dense(args, dev, 10, 10_000, 1000)
         out["dense_n50"] = form_dense(args, dev, 50, 10_000, 1050)
+        out["spectrum"] = form_spectrum(args, dev)
     if not args.no_sparse:
         out["sparse_ladder"] = form_sparse(args, dev)
         out["dimer"] = form_dimer(args, dev)
@@ -592,7 +619,8 @@ def form_dense(args, dev, N, steps, seed):
     t64, t32 = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     err = float(torch.linalg.norm(v32 - v64) / torch.linalg.norm(v64))
     rho = B.rho(v64)
-    checks = fp64_checks(lb, B, A, K, [("rk4_fp64", v64), ("rk4_fp32_corrected", v32)], restart=M, max_iter=2 * M)
+    checks = fp64_checks(lb, B, A, K, [("rk4_fp64", v64), ("rk4_fp32_corrected", v32)], restart=M,
+                         max_iter=2 * M, H=H.contiguous(), plain_max_iter=2 * M)
     # the same trajectory in one persistent FP64 launch (cluster size tuned)
     pers = None
     if N <= 64:
@@ -645,6 +673,50 @@ def form_dense(args, dev, N, steps, seed):
             "fp32c_rel_err_vs_fp64": err,
             "trace_rho_minus_1": float(abs(torch.diagonal(rho).real.sum() - 1.0)),
             "note": "single realization on the stream engine (4 fused stage launches per step)"}
+
+
+def form_spectrum(args, dev):
+    """Spectrum of one random Lindbladian of the paper's ensemble (Sec. 3:
+    H = 0, Kossakowski matrix N G G^dagger / Tr; Sec. 6, Fig. 5): the M
+    eigenvalues of A = Q + R (the solver library's dense nonsymmetric
+    eigensolver) and their density on a 100 x 100 grid (own kernel)."""
+    import torch
+
+    import paper_1912_01491_gb300 as lb
+    import workloads as wl
+    N = args.spectrum_n
+    M = N * N - 1
+    a = wl.random_lindbladian_paper_device(N, args.seed + 11, device=dev)  # H = 0, Tr a = N (Sec. 3)
+    B = lb.Basis(N)
+    A = torch.empty((M, M), dtype=torch.float64, device=dev)
+    B.assemble_dense(a, h=None, A=A, algorithm="closed")
+    del a
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    w = lb.spectrum(A)
+    torch.cuda.synchronize()
+    t_eig = time.perf_counter() - t0
+    re, im = w.real, w.imag
+    pad = 0.02 * max(float(re.max() - re.min()), float(im.abs().max()))
+    box = (float(re.min()) - pad, float(re.max()) + pad, -float(im.abs().max()) - pad, float(im.abs().max()) + pad)
+    ev = _events(2)
+    ev[0].record()
+    dens = lb.spectrum_density(w, box, 100, 100)
+    ev[1].record()
+    torch.cuda.synchronize()
+    area = (box[1] - box[0]) / 100 * (box[3] - box[2]) / 100
+    tr = float(torch.trace(A))
+    out = {"N": N, "M": M, "ensemble": "H = 0, a = N G G^dagger / Tr(G G^dagger)", "eigensolver_s": t_eig, "density_ms": ev[0].elapsed_time(ev[1]),
+           "max_real_part": float(re.max()), "min_real_part": float(re.min()), "max_abs_imag": float(im.abs().max()),
+           "sum_minus_trace_rel": abs(float(w.sum().real) - tr) / abs(tr),
+           "grid": [100, 100], "box": box, "counted": int(round(float(dens.sum()) * area)),
+           "note": "all M = N^2 - 1 eigenvalues of A; the N = 200 spectrum of Fig. 5 (M = 39,999) takes the dense "
+                   "eigensolver about 10 minutes, too long for a default bench run (--spectrum-n 200 runs it)"}
+    if args.spectrum_out:
+        import numpy as np
+        np.savez_compressed(args.spectrum_out, eig=w.cpu().numpy(), density=dens.cpu().numpy(), box=np.array(box))
+    B.close()
+    return out
 
 
 def form_sparse(args, dev):
@@ -1110,6 +1182,8 @@ def run_only(args):
         out = {"dimer": form_dimer(args, dev)}
     elif args.only == "batched":
         out = {"batched": form_batched(args, dev)}
+    elif args.only == "spectrum":
+        out = {"spectrum": form_spectrum(args, dev)}
     else:
         out = {"serving": form_serving(args, dev)}
     print(json.dumps(out), flush=True)

@@ -312,6 +312,26 @@ size_t lb_steady_workspace_bytes(int64_t M, int restart);
 int lb_steady_state(int64_t M, const double *A, const double *K, double *v, double tol, int max_iter, int restart,
                     double *rel_residual, int *iterations, void *work, void *stream);
 
+/* Bytes of device workspace of lb_steady_state_pc for dimension N
+ * (M = N^2 - 1) and restart length `restart`; 0 for bad arguments. */
+size_t lb_steady_pc_workspace_bytes(int N, int64_t M, int restart);
+
+/* lb_steady_state with a preconditioner from the Hamiltonian (Sec. 2: the
+ * part Q of A acts on rho as -i[H, rho]).  In the eigenbasis of H (found on
+ * the device by the CUDA toolkit's Hermitian eigensolver, loaded at run
+ * time; LB_EUNSUPPORTED when it cannot be loaded), P = Q - sigma 1 is
+ * diagonal with entries -i(E_j - E_k) - sigma, and GMRES runs on A P^-1
+ * (right preconditioning: the residual is that of A v = -K).  sigma >= 0 is
+ * the shift; sigma < 0 takes -Tr(A) / M, the mean damping rate (Tr Q = 0).
+ * For a random Lindbladian, whose damping spreads little, GMRES then needs
+ * a handful of iterations where the plain form needs hundreds.  H: device
+ * N x N complex Hermitian (interleaved), the H of A; b: its basis.  work:
+ * lb_steady_pc_workspace_bytes(N, M, restart) bytes, 256-byte aligned.
+ * Other arguments and results as lb_steady_state. */
+int lb_steady_state_pc(const lb_basis_t *b, const double *A, const double *K, const double *H, double sigma,
+                       double *v, double tol, int max_iter, int restart, double *rel_residual, int *iterations,
+                       void *work, void *stream);
+
 /* Bytes of device workspace of lb_rho_checks for dimension N. */
 size_t lb_rho_checks_workspace_bytes(int N);
 
@@ -544,6 +564,36 @@ int lb_system_timings(const lb_system_t *sys, double *ms);
 /* Copy one part (LB_SYS_A, _Q, _R: M x M; LB_SYS_K: M) into host memory.
  * LB_EINVAL if the part was not kept (and for A, Q, R of a CSR system). */
 int lb_system_get(const lb_system_t *sys, int part, double *out);
+
+/* ------------------------------------------------------------------------
+ * Spectrum of the generator (Sec. 6, Fig. 5: the complex eigenvalues
+ * lambda_i, i = 2..N^2, of one random Lindbladian, counted on a grid of cells
+ * and normalised by the cell area).  The eigenvalues of A = Q + R are those
+ * of the N^2 x N^2 generator other than the steady state's.  They come from
+ * the dense nonsymmetric eigensolver of the CUDA toolkit's solver library
+ * (loaded at run time; LB_EUNSUPPORTED when it cannot be loaded), O(M^3) FP64
+ * work: about 1e15 flops at N = 200, so practical up to N of about 70-100 on
+ * one GPU.  The density grid is the library's own kernel.
+ * --------------------------------------------------------------------- */
+
+/* Eigenvalues of the dense row-major M x M FP64 matrix A (device) into eig
+ * (device, 2 M doubles, complex interleaved, in the solver's order).  A is
+ * not modified (the solver works on a copy, M^2 doubles of device memory).
+ * Synchronous with respect to stream; LB_ECUDA if the solver fails. */
+int lb_spectrum(const double *A, int64_t M, double *eig, void *stream);
+
+/* The same for the A of a dense system, into host memory (eig: 2 M doubles,
+ * complex interleaved).  LB_EINVAL for a CSR system. */
+int lb_system_spectrum(const lb_system_t *sys, double *eig);
+
+/* Density of n complex eigenvalues (device, interleaved) on an nre x nim
+ * grid over the box {re_lo, re_hi, im_lo, im_hi} (host, 4 doubles): the
+ * number in each cell [re_lo + a dre, re_lo + (a+1) dre) x [im_lo + b dim,
+ * ...) divided by the cell area dre * dim, at density[a * nim + b] (device,
+ * nre * nim doubles, overwritten).  Eigenvalues outside the box are not
+ * counted.  Asynchronous on stream. */
+int lb_spectrum_density(const double *eig, int64_t n, const double *box, int nre, int nim, double *density,
+                        void *stream);
 
 /* CSR arrays of a CSR system into host buffers (any may be NULL): rowptr
  * (M + 1 int64), col (nnz int32, sorted within rows), val (nnz doubles).

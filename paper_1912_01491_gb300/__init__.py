@@ -8,4 +8,5 @@ binding.  Build with ``python -m paper_1912_01491_gb300.build``.
 """
 from . import native  # noqa: F401
 from .native import (LBError, Basis, Batch, Csr, Propagator, Server, System, pack_bf16, pack_fp32,  # noqa: F401
-                     request_bytes, rho_checks, rk4_dense, rk4_workspace, sched_simulate, steady_state)
+                     request_bytes, rho_checks, rk4_dense, rk4_workspace, sched_simulate, spectrum,
+                     spectrum_density, steady_state)

@@ -371,6 +371,8 @@ int lb_propagate(int64_t M, int nrhs, int precision, const void* Dp, const float
 
 // ------------------------------------------------------------------ FP64 checks
 
+static int spectrum_status(int rc, cudaError_t ce, const char* what);
+
 size_t lb_steady_workspace_bytes(int64_t M, int restart) {
   return M > 0 && restart >= 0 ? lbi::steady_workspace_bytes(M, restart) : 0;
 }
@@ -382,6 +384,27 @@ int lb_steady_state(int64_t M, const double* A, const double* K, double* v, doub
              "lb_steady_state: bad tol, max_iter or restart");
   LB_TRY_CUDA(lbi::steady_state(M, A, K, v, tol, max_iter, restart, rel_residual, iterations, work, S(stream)),
               "lb_steady_state");
+  return LB_OK;
+}
+
+size_t lb_steady_pc_workspace_bytes(int N, int64_t M, int restart) {
+  return N >= 2 && M == (int64_t)N * N - 1 && restart >= 0 ? lbi::steady_pc_workspace_bytes(N, M, restart) : 0;
+}
+
+int lb_steady_state_pc(const lb_basis_t* b, const double* A, const double* K, const double* H, double sigma,
+                       double* v, double tol, int max_iter, int restart, double* rel_residual, int* iterations,
+                       void* work, void* stream) {
+  LB_REQUIRE(b && A && K && H && v && work && rel_residual && iterations, "lb_steady_state_pc: NULL argument");
+  LB_REQUIRE(tol > 0 && std::isfinite(tol) && max_iter >= 1 && restart >= 0 && std::isfinite(sigma),
+             "lb_steady_state_pc: bad tol, max_iter, restart or sigma");
+  LB_REQUIRE((reinterpret_cast<uintptr_t>(work) & 255) == 0, "lb_steady_state_pc: work must be 256-byte aligned");
+  lbi::PcView pc;
+  cudaError_t ce = cudaSuccess;
+  const int rc = lbi::steady_pc_setup(b->view(), reinterpret_cast<const double2*>(H), A, sigma, restart, work, &pc,
+                                      S(stream), &ce);
+  if (rc != 0) return spectrum_status(rc, ce, "lb_steady_state_pc");
+  LB_TRY_CUDA(lbi::steady_state(b->M, A, K, v, tol, max_iter, restart, rel_residual, iterations, work, S(stream), &pc),
+              "lb_steady_state_pc");
   return LB_OK;
 }
 
@@ -1068,6 +1091,53 @@ int lb_system_get(const lb_system_t* s, int part, double* out) {
   const size_t n = part == LB_SYS_K ? (size_t)s->M : (size_t)s->M * (size_t)s->M;
   LB_TRY_CUDA(cudaMemcpyAsync(out, src, 8 * n, cudaMemcpyDeviceToHost, c.st), "lb_system_get");
   LB_TRY_CUDA(cudaStreamSynchronize(c.st), "lb_system_get");
+  return LB_OK;
+}
+
+static int spectrum_status(int rc, cudaError_t ce, const char* what) {
+  if (rc == 0) return LB_OK;
+  if (rc == 1) {
+    lbi::set_error("%s: the dense nonsymmetric eigensolver (libcusolver) could not be loaded", what);
+    return LB_EUNSUPPORTED;
+  }
+  if (rc == 3) return lbi::cuda_fail(ce, what);
+  lbi::set_error("%s: the eigensolver reported a failure", what);
+  return LB_ECUDA;
+}
+
+int lb_spectrum(const double* A, int64_t M, double* eig, void* stream) {
+  LB_REQUIRE(A && eig, "lb_spectrum: NULL argument");
+  LB_REQUIRE(M >= 1, "lb_spectrum: M = %lld", (long long)M);
+  cudaError_t ce = cudaSuccess;
+  const int rc = lbi::spectrum_dense(A, M, reinterpret_cast<double2*>(eig), S(stream), &ce);
+  return spectrum_status(rc, ce, "lb_spectrum");
+}
+
+int lb_spectrum_density(const double* eig, int64_t n, const double* box, int nre, int nim, double* density,
+                        void* stream) {
+  LB_REQUIRE(eig && box && density, "lb_spectrum_density: NULL argument");
+  LB_REQUIRE(n >= 0 && nre >= 1 && nim >= 1, "lb_spectrum_density: bad sizes");
+  LB_REQUIRE(std::isfinite(box[0]) && std::isfinite(box[1]) && std::isfinite(box[2]) && std::isfinite(box[3]) &&
+                 box[1] > box[0] && box[3] > box[2],
+             "lb_spectrum_density: empty or non-finite box");
+  LB_TRY_CUDA(lbi::spectrum_density(reinterpret_cast<const double2*>(eig), n, box, nre, nim, density, S(stream)),
+              "lb_spectrum_density");
+  return LB_OK;
+}
+
+int lb_system_spectrum(const lb_system_t* s, double* eig) {
+  LB_REQUIRE(s && eig, "lb_system_spectrum: NULL argument");
+  LB_REQUIRE(s->format == LB_DENSE && s->A, "lb_system_spectrum: dense systems only");
+  HostCtx c;
+  LB_TRY_CUDA(host_ctx(&c), "lb_system_spectrum");
+  PoolBuf w;
+  int rc;
+  if ((rc = w.alloc(c, 16 * (size_t)s->M, "eigenvalues")) != LB_OK) return rc;
+  cudaError_t ce = cudaSuccess;
+  rc = spectrum_status(lbi::spectrum_dense(s->A, s->M, w.as<double2>(), c.st, &ce), ce, "lb_system_spectrum");
+  if (rc != LB_OK) return rc;
+  LB_TRY_CUDA(cudaMemcpyAsync(eig, w.p, 16 * (size_t)s->M, cudaMemcpyDeviceToHost, c.st), "lb_system_spectrum");
+  LB_TRY_CUDA(cudaStreamSynchronize(c.st), "lb_system_spectrum");
   return LB_OK;
 }
 

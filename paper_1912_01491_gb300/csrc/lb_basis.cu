@@ -218,14 +218,14 @@ __global__ void k_expand(BasisView B, const double2* A, double2* coef) {
 }
 
 // Eq. (rho): rho = 1/N + sum_i v_i F_i.
-__global__ void k_rho(BasisView B, const double* v, double2* out) {
+__global__ void k_rho(BasisView B, const double* v, double2* out, double id) {
   const int N = B.N;
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)N * N) return;
   const int p = (int)(t / N), q = (int)(t % N);
   double2 r;
   if (p == q) {
-    double s = 1.0 / N;
+    double s = id;
     for (int l = imax(p, 1); l < N; ++l) s += v[d_index(B, l)] * delta(B, p, l);
     r = make_double2(s, 0.0);
   } else {
@@ -272,7 +272,13 @@ cudaError_t expand(const lb::BasisView& B, const double2* A, double2* coef, cuda
 }
 
 cudaError_t rho(const lb::BasisView& B, const double* v, double2* out, cudaStream_t st) {
-  k_rho<<<nblocks((int64_t)B.N * B.N, 256), 256, 0, st>>>(B, v, out);
+  k_rho<<<nblocks((int64_t)B.N * B.N, 256), 256, 0, st>>>(B, v, out, 1.0 / B.N);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t synth(const lb::BasisView& B, const double* v, double2* out, cudaStream_t st) {
+  k_rho<<<nblocks((int64_t)B.N * B.N, 256), 256, 0, st>>>(B, v, out, 0.0);
   note_launch(1);
   return cudaGetLastError();
 }

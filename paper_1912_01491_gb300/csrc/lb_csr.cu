@@ -317,28 +317,50 @@ __global__ void k_udd_bucket(const BasisView B, int nP, const double2* dl, const
 
 // Q terms of the diagonal coefficients h_{D_lam}: only (S_xy, J_xy) and
 // (J_xy, S_xy), q_{S J} = sum_lam h_{D_lam} f(D_lam, J_xy, S_xy) = -G_xy[h]
-// and q_{J S} = -q_{S J}; one thread per x (the same running sums, real).
+// and q_{J S} = -q_{S J}.  One warp per x: the lanes take 32 consecutive y
+// at a time, and the sums over x < lam < y are a warp prefix scan of
+// h_lam c_lam (and of |h_lam| c_lam) over that window plus the window's
+// carry, so each holds exactly the terms of its edge.
 __global__ void k_q_diag_bucket(BasisView B, const double* h, Bucketer bk) {
   const int N = B.N;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int x = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (x >= N) return;
   const double* hd = h + 2 * B.P - 1;  // hd[nu] = h_{D_nu}
   const double head = x >= 1 ? hd[x] * ld_lc(B, x) : 0.0;
   const double headm = x >= 1 ? fabs(hd[x] * ld_lc(B, x)) : 0.0;
-  double run = 0.0, runm = 0.0;
-  for (int y = x + 1; y < N; ++y) {
-    const double cy = ld_c(B, y), lcy = ld_lc(B, y);
-    const double G = head + run + hd[y] * (cy - lcy);
-    const double Gm = headm + runm + fabs(hd[y]) * (cy - lcy);
-    if (Gm > 0.0) {
-      const int64_t e = pair_index(N, x, y);
-      bk.put(e, -1, B.P + e, -G, 0.0, Gm);
-      bk.put(B.P + e, -1, e, G, 0.0, Gm);
+  double carry = 0.0, carrym = 0.0;  // sums over x < lam < (the window's first y)
+  for (int y0 = x + 1; y0 < N; y0 += 32) {
+    const int y = y0 + lane;
+    const bool in = y < N;
+    const double cy = in ? ld_c(B, y) : 0.0, lcy = in ? ld_lc(B, y) : 0.0, hy = in ? hd[y] : 0.0;
+    double t = hy * cy, tm = fabs(hy) * cy;  // the term lam = y, for the larger y
+    double it = t, itm = tm;                  // inclusive prefix over the window
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double u = __shfl_up_sync(0xffffffffu, it, o), um = __shfl_up_sync(0xffffffffu, itm, o);
+      if (lane >= o) {
+        it += u;
+        itm += um;
+      }
     }
-    if (y < N - 1) {
-      run += hd[y] * cy;
-      runm += fabs(hd[y]) * cy;
+    double ex = __shfl_up_sync(0xffffffffu, it, 1), exm = __shfl_up_sync(0xffffffffu, itm, 1);
+    if (lane == 0) {
+      ex = 0.0;
+      exm = 0.0;
     }
+    const double run = carry + ex, runm = carrym + exm;  // x < lam < y
+    if (in) {
+      const double G = head + run + hy * (cy - lcy);
+      const double Gm = headm + runm + fabs(hy) * (cy - lcy);
+      if (Gm > 0.0) {
+        const int64_t e = pair_index(N, x, y);
+        bk.put(e, -1, B.P + e, -G, 0.0, Gm);
+        bk.put(B.P + e, -1, e, G, 0.0, Gm);
+      }
+    }
+    carry += __shfl_sync(0xffffffffu, it, 31);
+    carrym += __shfl_sync(0xffffffffu, itm, 31);
   }
 }
 
@@ -459,7 +481,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(int64_t* tile_sum, in
 constexpr int kRowCap = 512;          // hash slots of one warp (rows up to 256 terms)
 constexpr int kRowBound = 256;        // terms above which a row takes the block path
 constexpr int kRowWarps = 4;
-constexpr int kLongCap = 8192;        // hash slots of one block (long rows)
+constexpr int kLongCap = 8192;        // hash slots of one block (long rows), per column partition
 constexpr int kLongThreads = 256;
 constexpr int32_t kEmpty = -1;
 
@@ -470,14 +492,14 @@ struct RowInputs {
   const BTerm *w, *u, *q;
 };
 
-__device__ __forceinline__ uint32_t slot_hash(int32_t n, uint32_t mask) {
-  return ((uint32_t)n * 2654435761u) & mask;
-}
+__device__ __forceinline__ uint32_t col_hash(int32_t n) { return (uint32_t)n * 2654435761u; }
 
-// Add (v, m) to column n; false if the table is full.
+// Add (v, m) to column n; false if the table is full.  Slots come from the
+// low bits of the column's hash (partitions, in the long path, from the high
+// bits).
 __device__ __forceinline__ bool hash_add(int32_t* keys, double* val, double* mag, uint32_t mask, int32_t n, double v,
                                          double m) {
-  uint32_t h = slot_hash(n, mask);
+  uint32_t h = col_hash(n) & mask;
   for (uint32_t probe = 0; probe <= mask; ++probe) {
     const int32_t k = atomicCAS(keys + h, kEmpty, n);
     if (k == kEmpty || k == n) {
@@ -501,40 +523,196 @@ __device__ __forceinline__ int64_t row_terms(const RowInputs& I, int64_t s, int 
   return t;
 }
 
-// Accumulate row s into the table: threads `lane` of `width` take the W terms
-// of column s (each walks the U row of its l) and the row's Q terms.
-__device__ __forceinline__ bool row_accumulate(const RowInputs& I, int64_t s, int lane, int width, int32_t* keys,
-                                               double* val, double* mag, uint32_t mask) {
-  bool ok = true;
-  for (int64_t i = I.woff[s] + lane; i < I.woff[s + 1]; i += width) {
-    const BTerm wt = I.w[i];
-    const double g = I.gamma[wt.p];
-    for (int64_t j = I.uoff[wt.x]; j < I.uoff[wt.x + 1]; ++j) {
-      const BTerm ut = I.u[j];
-      if (ut.p != wt.p) continue;
-      ok &= hash_add(keys, val, mag, mask, ut.x, -0.5 * g * (wt.re * ut.re - wt.im * ut.im), 0.5 * g * wt.mag * ut.mag);
+// One warp adds (v, m) of every lane to the lane's column key (kEmpty: no
+// term) without atomic additions: lanes with the same key are grouped by
+// __match_any_sync, the group's lowest lane sums the group's terms in lane
+// order (shuffles) and alone updates the column's slot, which it finds or
+// claims by compare-and-swap on the key.  Leaders of different groups hold
+// different keys, hence different slots.  False if the table is full.
+__device__ __forceinline__ bool warp_add(int32_t* keys, double* val, double* mag, uint32_t mask, int32_t key,
+                                         double v, double m, int lane) {
+  const unsigned active = __ballot_sync(0xffffffffu, key != kEmpty);
+  const unsigned grp = __match_any_sync(0xffffffffu, key) & active;
+  unsigned rem = key != kEmpty ? grp & ~(1u << lane) : 0u;
+  double sv = v, sm = m;
+  while (__any_sync(0xffffffffu, rem != 0u)) {
+    const int src = rem ? __ffs(rem) - 1 : lane;
+    const double ov = __shfl_sync(0xffffffffu, v, src), om = __shfl_sync(0xffffffffu, m, src);
+    if (rem) {
+      sv += ov;
+      sm += om;
+      rem &= rem - 1u;
     }
   }
-  if (I.qoff)
-    for (int64_t i = I.qoff[s] + lane; i < I.qoff[s + 1]; i += width) {
-      const BTerm qt = I.q[i];
-      ok &= hash_add(keys, val, mag, mask, qt.x, qt.re, qt.mag);
+  bool ok = true;
+  if (key != kEmpty && lane == __ffs(grp) - 1) {
+    ok = false;
+    uint32_t h = col_hash(key) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+      const int32_t k = atomicCAS(keys + h, kEmpty, key);
+      if (k == kEmpty || k == key) {
+        val[h] += sv;
+        mag[h] += sm;
+        ok = true;
+        break;
+      }
+      h = (h + 1) & mask;
     }
+  }
+  __syncwarp();
+  return ok;
+}
+
+// One W term of a chunk, scaled for its products (a product with the U term
+// u is (a Re u + b Im u, m |u|) = (-1/2 g Re(w u), 1/2 g |w| |u|)), with the
+// start of its U row and the chunk-local offset of its first product.
+struct WStage {
+  double a, b, m;
+  int64_t ubeg;
+  int32_t p, pre;
+};
+
+// Exclusive prefix of x over the WIDTH threads (WIDTH = 32: one warp;
+// WIDTH = kLongThreads: the block, with a barrier); *total = the sum.
+template <int WIDTH>
+__device__ __forceinline__ int excl_prefix(int x, int* tot_s, int* total) {
+  if (WIDTH == 32) {
+    const int lane = threadIdx.x & 31;
+    int inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    *total = __shfl_sync(0xffffffffu, inc, 31);
+    return inc - x;
+  } else {
+    int64_t t64;
+    const int64_t r = block_excl_scan((int64_t)x, reinterpret_cast<int64_t*>(tot_s), t64);
+    *total = (int)t64;
+    return (int)r;
+  }
+}
+
+template <int WIDTH>
+__device__ __forceinline__ void width_sync() {
+  if (WIDTH == 32) __syncwarp();
+  else __syncthreads();
+}
+
+// Accumulate row s into the table, the columns of partition `part` of
+// `nparts` only (hash high bits): the products of the W terms of column s
+// with the U rows they name, taken WIDTH W terms at a time and spread over
+// the threads one product each (a thread finds its W term by binary search
+// of the chunk's prefix offsets), then the row's Q terms.
+template <int WIDTH>
+__device__ bool row_accumulate(const RowInputs& I, int64_t s, int t, WStage* ws, int* tot_s, int32_t* keys,
+                               double* val, double* mag, uint32_t mask, int part, int nparts) {
+  bool ok = true;
+  const uint32_t pshift = 32 - (nparts > 1 ? __ffs(nparts) - 1 : 0);
+  auto mine = [&](int32_t n) { return nparts == 1 || (int)(col_hash(n) >> pshift) == part; };
+  const int64_t w0 = I.woff[s], w1 = I.woff[s + 1];
+  for (int64_t c = w0; c < w1; c += WIDTH) {
+    const int cnt = (int)(w1 - c < WIDTH ? w1 - c : WIDTH);
+    int len = 0;
+    WStage st{};
+    if (t < cnt) {
+      const BTerm wt = I.w[c + t];
+      const double hg = 0.5 * I.gamma[wt.p];
+      st.a = -hg * wt.re;
+      st.b = hg * wt.im;
+      st.m = hg * wt.mag;
+      st.p = wt.p;
+      st.ubeg = I.uoff[wt.x];
+      len = (int)(I.uoff[wt.x + 1] - st.ubeg);
+    }
+    int total;
+    st.pre = excl_prefix<WIDTH>(len, tot_s, &total);
+    if (t < cnt) ws[t] = st;
+    width_sync<WIDTH>();
+    // rounds of WIDTH products (warp-uniform, for the warp path's collective add)
+    for (int f0 = 0; f0 < total; f0 += WIDTH) {
+      const int f = f0 + t;
+      int32_t key = kEmpty;
+      double v = 0.0, m = 0.0;
+      if (f < total) {
+        int lo = 0, hi = cnt - 1;  // the last i with ws[i].pre <= f
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (ws[mid].pre <= f) lo = mid; else hi = mid - 1;
+        }
+        const WStage& w = ws[lo];
+        const BTerm ut = I.u[w.ubeg + (f - w.pre)];
+        if (ut.p == w.p && mine(ut.x)) {
+          key = ut.x;
+          v = fma(w.a, ut.re, w.b * ut.im);
+          m = w.m * ut.mag;
+        }
+      }
+      if (WIDTH == 32) ok &= warp_add(keys, val, mag, mask, key, v, m, t);
+      else if (key != kEmpty) ok &= hash_add(keys, val, mag, mask, key, v, m);
+    }
+    width_sync<WIDTH>();
+  }
+  if (I.qoff) {
+    const int64_t q0 = I.qoff[s], q1 = I.qoff[s + 1];
+    for (int64_t i0 = q0; i0 < q1; i0 += WIDTH) {
+      const int64_t i = i0 + t;
+      int32_t key = kEmpty;
+      double v = 0.0, m = 0.0;
+      if (i < q1) {
+        const BTerm qt = I.q[i];
+        if (mine(qt.x)) {
+          key = qt.x;
+          v = qt.re;
+          m = qt.mag;
+        }
+      }
+      if (WIDTH == 32) ok &= warp_add(keys, val, mag, mask, key, v, m, t);
+      else if (key != kEmpty) ok &= hash_add(keys, val, mag, mask, key, v, m);
+    }
+  }
   return ok;
 }
 
 __device__ __forceinline__ bool kept(int32_t k, double v, double m) { return k != kEmpty && fabs(v) > 1e-12 * m; }
 
-// Move the kept entries of a table to its front (in slot order, 32 slots at a
-// time by ballot; a slot is read before any lane writes at or below it) and
-// return their number.  Called by one whole warp.
-__device__ __forceinline__ int warp_compact(int32_t* keys, double* val, const double* mag, int cap, int lane) {
-  int run = 0;
+// Move the kept entries of a table of `cap` slots (a multiple of 32) to its
+// front and return their number.  Called by one whole warp.  First the
+// occupied slots move to the front with integer tests only, then the kept
+// test (|value| > 1e-12 x magnitude, FP64) runs over the occupied ones: the
+// FP64 pipe takes a warp instruction at the same cost whatever its active
+// lanes, and most slots are empty.  Each pass goes 32 slots at a time by
+// ballot; a slot is read before any lane writes at or below it.
+__device__ __forceinline__ int warp_compact(int32_t* keys, double* val, double* mag, int cap, int lane) {
+  int occ = 0;
   for (int base = 0; base < cap; base += 32) {
     const int a = base + lane;
     const int32_t k = keys[a];
-    const double v = val[a];
-    const bool kp = kept(k, v, mag[a]);
+    const double v = val[a], m = mag[a];
+    const bool used = k != kEmpty;
+    const unsigned bal = __ballot_sync(0xffffffffu, used);
+    __syncwarp();
+    if (used) {
+      const int pos = occ + __popc(bal & ((1u << lane) - 1u));
+      keys[pos] = k;
+      val[pos] = v;
+      mag[pos] = m;
+    }
+    occ += __popc(bal);
+    __syncwarp();
+  }
+  int run = 0;
+  for (int base = 0; base < occ; base += 32) {
+    const int a = base + lane;
+    int32_t k = kEmpty;
+    double v = 0.0, m = 0.0;
+    if (a < occ) {
+      k = keys[a];
+      v = val[a];
+      m = mag[a];
+    }
+    const bool kp = kept(k, v, m);
     const unsigned bal = __ballot_sync(0xffffffffu, kp);
     __syncwarp();
     if (kp) {
@@ -546,19 +724,6 @@ __device__ __forceinline__ int warp_compact(int32_t* keys, double* val, const do
     __syncwarp();
   }
   return run;
-}
-
-// Write k compacted entries in ascending column order: an entry's rank is
-// the number of entries with a smaller column.
-__device__ __forceinline__ void sorted_write(const int32_t* keys, const double* val, int k, int t, int nt,
-                                             int32_t* col, double* out) {
-  for (int e = t; e < k; e += nt) {
-    const int32_t ke = keys[e];
-    int rank = 0;
-    for (int f = 0; f < k; ++f) rank += keys[f] < ke ? 1 : 0;
-    col[rank] = ke;
-    out[rank] = val[e];
-  }
 }
 
 // Terms of every row (one warp per row): bound[s]; rows of more than
@@ -576,67 +741,94 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_row_terms(RowInputs I, unsig
   }
 }
 
-// One warp per row of at most kRowBound terms: accumulate the row once, write
-// its kept entries in ascending column order to the row's scratch range
-// (tmpoff[s], room for bound[s] >= kept entries) and their number to
-// rowcount[s].
+// One warp per row of at most kRowBound terms, in a table of the smallest
+// power of two >= 2 x terms slots (at least 64): accumulate the row once and
+// write its kept entries (unordered) to the row's scratch range (tmpoff[s],
+// room for bound[s] >= kept entries) and their number to rowcount[s].
 __global__ void __launch_bounds__(kRowWarps * 32) k_rows_warp(RowInputs I, const unsigned long long* bound,
                                                              const int64_t* tmpoff, int32_t* tcol, double* tval,
                                                              unsigned long long* rowcount, int* status) {
   __shared__ int32_t keys_s[kRowWarps][kRowCap];
   __shared__ double val_s[kRowWarps][kRowCap], mag_s[kRowWarps][kRowCap];
+  __shared__ WStage ws_s[kRowWarps][32];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t s = (int64_t)blockIdx.x * kRowWarps + wid;
-  if (s >= I.M || bound[s] > (unsigned long long)kRowBound) return;
+  if (s >= I.M) return;
+  const unsigned long long tb = bound[s];
+  if (tb > (unsigned long long)kRowBound) return;
+  int cap = 64;
+  while (cap < 2 * (int)tb) cap <<= 1;
   int32_t* keys = keys_s[wid];
   double* val = val_s[wid];
   double* mag = mag_s[wid];
-  for (int a = lane; a < kRowCap; a += 32) {
+  for (int a = lane; a < cap; a += 32) {
     keys[a] = kEmpty;
     val[a] = 0.0;
     mag[a] = 0.0;
   }
   __syncwarp();
-  const bool ok = row_accumulate(I, s, lane, 32, keys, val, mag, kRowCap - 1);
-  if (!ok) atomicExch(status, 1);  // not reached: at most kRowBound columns in kRowCap slots
+  const bool ok = row_accumulate<32>(I, s, lane, ws_s[wid], nullptr, keys, val, mag, cap - 1, 0, 1);
+  if (!ok) atomicExch(status, 1);  // not reached: at most cap / 2 columns
   __syncwarp();
-  const int k = warp_compact(keys, val, mag, kRowCap, lane);
-  sorted_write(keys, val, k, lane, 32, tcol + tmpoff[s], tval + tmpoff[s]);
+  const int k = warp_compact(keys, val, mag, cap, lane);
+  for (int e = lane; e < k; e += 32) {
+    tcol[tmpoff[s] + e] = keys[e];
+    tval[tmpoff[s] + e] = val[e];
+  }
   if (lane == 0) rowcount[s] = (unsigned long long)k;
 }
 
-// The same for one long row per block, a table of kLongCap slots in shared
-// memory; a row with more distinct columns sets *status = 2 (its kept
-// entries that found a slot are still written within its range).
+// One block per long row.  The row's columns are split by the high bits of
+// their hash into the smallest power-of-two number of partitions with at
+// most kLongCap / 2 terms each on average; each partition is accumulated in
+// a table of kLongCap slots in shared memory and its kept entries appended
+// to the row's scratch range.  A partition with more distinct columns than
+// slots sets *status = 2.
 __global__ void __launch_bounds__(kLongThreads) k_rows_long(RowInputs I, const int64_t* longlist,
-                                                           const int64_t* tmpoff, int32_t* tcol, double* tval,
-                                                           unsigned long long* rowcount, int* status) {
+                                                           const unsigned long long* bound, const int64_t* tmpoff,
+                                                           int32_t* tcol, double* tval, unsigned long long* rowcount,
+                                                           int* status) {
   extern __shared__ __align__(16) unsigned char lsm[];
   double* val = reinterpret_cast<double*>(lsm);
   double* mag = val + kLongCap;
   int32_t* keys = reinterpret_cast<int32_t*>(mag + kLongCap);
+  __shared__ WStage ws[kLongThreads];
+  __shared__ int64_t tot_s[kLongThreads / 32];
   __shared__ int kk;
   const int64_t s = longlist[blockIdx.x];
-  for (int a = threadIdx.x; a < kLongCap; a += kLongThreads) {
-    keys[a] = kEmpty;
-    val[a] = 0.0;
-    mag[a] = 0.0;
+  int nparts = 1;
+  while ((unsigned long long)nparts * (kLongCap / 2) < bound[s] && nparts < (1 << 20)) nparts <<= 1;
+  int total = 0;
+  for (int part = 0; part < nparts; ++part) {
+    for (int a = threadIdx.x; a < kLongCap; a += kLongThreads) {
+      keys[a] = kEmpty;
+      val[a] = 0.0;
+      mag[a] = 0.0;
+    }
+    __syncthreads();
+    const bool ok = row_accumulate<kLongThreads>(I, s, threadIdx.x, ws, reinterpret_cast<int*>(tot_s), keys, val, mag,
+                                                 kLongCap - 1, part, nparts);
+    if (!ok) atomicExch(status, 2);
+    __syncthreads();
+    if (threadIdx.x < 32) {  // compaction by warp 0
+      const int k = warp_compact(keys, val, mag, kLongCap, threadIdx.x);
+      if (threadIdx.x == 0) kk = k;
+    }
+    __syncthreads();
+    const int k = kk;
+    for (int e = threadIdx.x; e < k; e += kLongThreads) {
+      tcol[tmpoff[s] + total + e] = keys[e];
+      tval[tmpoff[s] + total + e] = val[e];
+    }
+    total += k;
+    __syncthreads();
   }
-  __syncthreads();
-  const bool ok = row_accumulate(I, s, threadIdx.x, kLongThreads, keys, val, mag, kLongCap - 1);
-  if (!ok) atomicExch(status, 2);
-  __syncthreads();
-  if (threadIdx.x < 32) {  // compaction by warp 0
-    const int k = warp_compact(keys, val, mag, kLongCap, threadIdx.x);
-    if (threadIdx.x == 0) kk = k;
-  }
-  __syncthreads();
-  const int k = kk;
-  sorted_write(keys, val, k, threadIdx.x, kLongThreads, tcol + tmpoff[s], tval + tmpoff[s]);
-  if (threadIdx.x == 0) rowcount[s] = (unsigned long long)k;
+  if (threadIdx.x == 0) rowcount[s] = (unsigned long long)total;
 }
 
-// Rows from the scratch ranges to their CSR place (one warp per row).
+// Rows from the scratch ranges to their CSR place in ascending column order
+// (one warp per row; an entry's rank is the number of the row's entries with
+// a smaller column).
 __global__ void __launch_bounds__(256) k_rows_copy(int64_t M, const int64_t* tmpoff, const int32_t* tcol,
                                                   const double* tval, const int64_t* rowptr, int32_t* col,
                                                   double* val) {
@@ -645,8 +837,11 @@ __global__ void __launch_bounds__(256) k_rows_copy(int64_t M, const int64_t* tmp
   if (s >= M) return;
   const int64_t src = tmpoff[s], dst = rowptr[s], k = rowptr[s + 1] - rowptr[s];
   for (int64_t i = lane; i < k; i += 32) {
-    col[dst + i] = tcol[src + i];
-    val[dst + i] = tval[src + i];
+    const int32_t ki = tcol[src + i];
+    int64_t rank = 0;
+    for (int64_t j = 0; j < k; ++j) rank += tcol[src + j] < ki ? 1 : 0;
+    col[dst + rank] = ki;
+    val[dst + rank] = tval[src + i];
   }
 }
 
@@ -793,7 +988,7 @@ cudaError_t assemble_lowrank_csr(const lb::BasisView& B, const double* h, int nP
         k_q_pair_bucket<<<nb((int64_t)nh * S, 256), 256, 0, st>>>(B, h, hlist.as<int64_t>(), (int64_t)nh, bk);
         note_launch(1);
       }
-      k_q_diag_bucket<<<nb(N, 128), 128, 0, st>>>(B, h, bk);
+      k_q_diag_bucket<<<nb((int64_t)N * 32, 256), 256, 0, st>>>(B, h, bk);
       note_launch(1);
       return cudaGetLastError();
     }, st));
@@ -829,7 +1024,8 @@ cudaError_t assemble_lowrank_csr(const lb::BasisView& B, const double* h, int nP
   if (nlong > 0) {
     const size_t lsmem = (sizeof(double) * 2 + sizeof(int32_t)) * (size_t)kLongCap;
     CK(cudaFuncSetAttribute(k_rows_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
-    k_rows_long<<<(unsigned)nlong, kLongThreads, lsmem, st>>>(I, longlist.as<int64_t>(), tmpoff.as<int64_t>(),
+    k_rows_long<<<(unsigned)nlong, kLongThreads, lsmem, st>>>(I, longlist.as<int64_t>(),
+                                                             bound.as<unsigned long long>(), tmpoff.as<int64_t>(),
                                                              tcol.as<int32_t>(), tval.as<double>(),
                                                              rowc.as<unsigned long long>(), status);
     note_launch(1);

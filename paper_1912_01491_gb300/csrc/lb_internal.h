@@ -45,6 +45,8 @@ cudaError_t structure_fill(const lb::BasisView& B, int which, const int64_t* off
                            int32_t* idx3, double* val, cudaStream_t st);
 cudaError_t expand(const lb::BasisView& B, const double2* A, double2* coef, cudaStream_t st);
 cudaError_t rho(const lb::BasisView& B, const double* v, double2* out, cudaStream_t st);
+// sum_i v_i F_i (rho without the 1/N identity part)
+cudaError_t synth(const lb::BasisView& B, const double* v, double2* out, cudaStream_t st);
 
 // dense assembly (lb_assemble.cu)
 constexpr int kAssembleKernels = 7;
@@ -52,6 +54,8 @@ constexpr int kAssembleKernels = 7;
 // triangle crosses the link (one 2D copy per row block), the strict lower
 // triangle is then written on the device as a_kj = conj(a_jk).
 cudaError_t upload_hermitian(const double2* host, double2* dev, int64_t M, cudaStream_t st);
+// ev (kAssembleKernels + 1 events, optional): the kernels run in sequence
+// on st with an event between them.
 cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double2* a,
                            double* A, double* Q, double* R, double* K, int algorithm, cudaStream_t st,
                            cudaEvent_t* ev = nullptr);
@@ -66,6 +70,16 @@ struct CsrOut {
   double* val = nullptr;      // nnz
   double* K = nullptr;        // M
 };
+// Eigenvalues w[0..M) (complex) of the dense row-major M x M matrix A by the
+// library's nonsymmetric eigensolver; 0 ok, 1 solver not found, 2 solver
+// failure, 3 CUDA error (*ce).
+int spectrum_dense(const double* A, int64_t M, double2* w, cudaStream_t st, cudaError_t* ce);
+// Eigenvalues E (ascending) and eigenvectors (row j of Ub) of the Hermitian
+// row-major N x N H; status as spectrum_dense.
+int hermitian_eig(const double2* H, int N, double* E, double2* Ub, cudaStream_t st, cudaError_t* ce);
+// Eigenvalue density on an nre x nim grid over box = {re_lo, re_hi, im_lo, im_hi}.
+cudaError_t spectrum_density(const double2* w, int64_t n, const double* box, int nre, int nim, double* dens,
+                             cudaStream_t st);
 // off[0..n] = exclusive prefix sums of n int64 counts (off[n] = total);
 // synchronous with respect to st.
 cudaError_t exclusive_scan(const int64_t* counts, int64_t* off, int64_t n, cudaStream_t st);
@@ -138,8 +152,22 @@ cudaError_t propagator_form(int64_t M, int precision, const double* A64, const f
                             void* Dp, float* R32, double* cp, void* work, size_t work_bytes, cudaStream_t st);
 // FP64 checks (lb_steady.cu)
 size_t steady_workspace_bytes(int64_t M, int restart);
+// The Hamiltonian preconditioner of the steady-state GMRES (lb_steady.cu):
+// basis, eigenvalues E and eigenvectors (rows of Ub) of H, shift sigma and
+// scratch (X, T: N x N complex; coef: M complex; z: M).
+struct PcView {
+  lb::BasisView B;
+  double* E;
+  double2 *Ub, *X, *T, *coef;
+  double* z;
+  double sigma;
+};
+size_t steady_pc_workspace_bytes(int N, int64_t M, int restart);
+int steady_pc_setup(const lb::BasisView& B, const double2* H, const double* A, double sigma, int restart,
+                    void* work, PcView* pc, cudaStream_t st, cudaError_t* ce);
 cudaError_t steady_state(int64_t M, const double* A, const double* K, double* v, double tol, int max_iter,
-                         int restart, double* rel_res, int* iters, void* work, cudaStream_t st);
+                         int restart, double* rel_res, int* iters, void* work, cudaStream_t st,
+                         const PcView* pc = nullptr);
 size_t rho_checks_workspace_bytes(int N);
 cudaError_t rho_checks(const lb::BasisView& B, const double* V, int64_t nsnap, double delta, double* out_host,
                        void* work, cudaStream_t st);

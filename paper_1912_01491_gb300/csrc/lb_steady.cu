@@ -11,6 +11,15 @@
 // pass), and the small Hessenberg least-squares problem with Givens
 // rotations on the host.
 //
+// Preconditioner (optional): the Hamiltonian part Q acts on rho as
+// -i[H, rho], diagonal in the eigenbasis of H with -i(E_j - E_k); the
+// dissipator of a random Lindbladian shifts the spectrum by about
+// -sigma = Tr(A)/M (Tr Q = 0) with little spread.  P = Q - sigma 1 is
+// therefore close to A, and P^-1 x is: rho(x) = sum_i x_i F_i, Y = U^dag
+// rho U, Y_jk / (-i(E_j - E_k) - sigma), U Y U^dag, back to coordinates.
+// GMRES runs on A P^-1 (right preconditioning, so the residual it
+// minimises is that of A v = -K itself).
+//
 // rho checks (Eq. (rho)): from v, rho is rebuilt on the device and reduced
 // to Tr rho - 1 and max |rho_jk - conj(rho_kj)|, and a Cholesky
 // factorisation of rho + delta 1 in one block gives its smallest pivot
@@ -143,6 +152,80 @@ __global__ void __launch_bounds__(256) k_cholesky_pivot(int N, double2* __restri
 
 inline unsigned vec_blocks(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 1024); }
 
+// C = op_a(A) op_b(B) for N x N complex row-major matrices, op in
+// {0: X, 1: X^T, 2: conj(X)}; 16 x 16 tiles in shared memory.
+constexpr int kCT = 16;
+template <int OPA, int OPB>
+__global__ void __launch_bounds__(kCT * kCT) k_cgemm(int N, const double2* __restrict__ A,
+                                                     const double2* __restrict__ B, double2* __restrict__ C) {
+  __shared__ double2 ta[kCT][kCT + 1], tb[kCT][kCT + 1];
+  const int i = blockIdx.y * kCT + threadIdx.y, j = blockIdx.x * kCT + threadIdx.x;
+  double cr = 0.0, ci = 0.0;
+  for (int k0 = 0; k0 < N; k0 += kCT) {
+    {  // op_a(A)[i][k0 + tx]
+      const int k = k0 + threadIdx.x;
+      double2 x = make_double2(0.0, 0.0);
+      if (i < N && k < N) x = OPA == 1 ? A[(int64_t)k * N + i] : A[(int64_t)i * N + k];
+      if (OPA == 2) x.y = -x.y;
+      ta[threadIdx.y][threadIdx.x] = x;
+    }
+    {  // op_b(B)[k0 + ty][j]
+      const int k = k0 + threadIdx.y;
+      double2 x = make_double2(0.0, 0.0);
+      if (k < N && j < N) x = OPB == 1 ? B[(int64_t)j * N + k] : B[(int64_t)k * N + j];
+      if (OPB == 2) x.y = -x.y;
+      tb[threadIdx.y][threadIdx.x] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kCT; ++k) {
+      const double2 a = ta[threadIdx.y][k], b = tb[k][threadIdx.x];
+      cr = fma(a.x, b.x, fma(-a.y, b.y, cr));
+      ci = fma(a.x, b.y, fma(a.y, b.x, ci));
+    }
+    __syncthreads();
+  }
+  if (i < N && j < N) C[(int64_t)i * N + j] = make_double2(cr, ci);
+}
+
+// Y_jk /= (-i (E_j - E_k) - sigma)
+__global__ void k_pc_divide(int N, const double* __restrict__ E, double sigma, double2* __restrict__ Y) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * N) return;
+  const int j = (int)(t / N), k = (int)(t % N);
+  const double dr = -sigma, di = -(E[j] - E[k]);  // d = dr + i di
+  const double inv = 1.0 / (dr * dr + di * di);
+  const double2 y = Y[t];
+  Y[t] = make_double2((y.x * dr + y.y * di) * inv, (y.y * dr - y.x * di) * inv);
+}
+
+// y += x
+__global__ void k_add_to(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] += x[e];
+}
+
+// y = Re(x)
+__global__ void k_real(int64_t n, const double2* __restrict__ x, double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = x[i].x;
+}
+
+// out = Tr(A) (one block, fixed-order reduction)
+__global__ void __launch_bounds__(256) k_trace(int64_t M, const double* __restrict__ A, double* __restrict__ out) {
+  __shared__ double red[8];
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < M; i += blockDim.x) a += A[i * M + i];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < 8; ++k) s += red[k];
+    out[0] = s;
+  }
+}
+
 }  // namespace
 
 namespace lbi {
@@ -158,10 +241,67 @@ size_t steady_workspace_bytes(int64_t M, int restart) {
   return 8 * ((size_t)(m + 1) * M + 2 * (size_t)M + 2 * (m + 2) + 16);
 }
 
+// The preconditioner's part of the workspace: E (N), Ub, X, T (N x N
+// complex each), coef (M complex), z (M).
+static size_t pc_offset(int64_t M, int restart) { return (steady_workspace_bytes(M, restart) + 255) & ~(size_t)255; }
+
+size_t steady_pc_workspace_bytes(int N, int64_t M, int restart) {
+  const size_t nn = (size_t)N * N;
+  return pc_offset(M, restart) + 8 * ((size_t)N + 1 + 6 * nn + 3 * (size_t)M + 16);
+}
+
+// z = P^-1 x with P = Q - sigma 1 (Q = -i[H, .] on traceless coordinates).
+static cudaError_t apply_pc(const PcView& pc, const double* x, double* z, cudaStream_t st) {
+  const int N = pc.B.N;
+  const dim3 tb(kCT, kCT), tg((N + kCT - 1) / kCT, (N + kCT - 1) / kCT);
+  cudaError_t e = lbi::synth(pc.B, x, pc.X, st);                       // X = sum x_i F_i
+  if (e != cudaSuccess) return e;
+  k_cgemm<2, 0><<<tg, tb, 0, st>>>(N, pc.Ub, pc.X, pc.T);                // T = conj(Ub) X = U^dag X
+  k_cgemm<0, 1><<<tg, tb, 0, st>>>(N, pc.T, pc.Ub, pc.X);                // Y = T Ub^T = U^dag X U
+  k_pc_divide<<<(unsigned)(((int64_t)N * N + 255) / 256), 256, 0, st>>>(N, pc.E, pc.sigma, pc.X);
+  k_cgemm<1, 0><<<tg, tb, 0, st>>>(N, pc.Ub, pc.X, pc.T);                // T = Ub^T Y = U Y
+  k_cgemm<0, 2><<<tg, tb, 0, st>>>(N, pc.T, pc.Ub, pc.X);                // Z = T conj(Ub) = U Y U^dag
+  note_launch(5);
+  e = lbi::expand(pc.B, pc.X, pc.coef, st);                              // Tr(F_i Z)
+  if (e != cudaSuccess) return e;
+  k_real<<<(unsigned)((pc.B.M + 255) / 256), 256, 0, st>>>(pc.B.M, pc.coef, z);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+// Set up the preconditioner for H (device, N x N complex) in the tail of
+// the workspace; sigma < 0 takes -Tr(A) / M.  Status as hermitian_eig.
+int steady_pc_setup(const lb::BasisView& B, const double2* H, const double* A, double sigma, int restart,
+                    void* work, PcView* pc, cudaStream_t st, cudaError_t* ce) {
+  const int N = B.N;
+  const int64_t M = B.M;
+  const size_t nn = (size_t)N * N;
+  char* p = static_cast<char*>(work) + pc_offset(M, restart);  // 256-byte aligned when work is
+  pc->B = B;
+  pc->E = reinterpret_cast<double*>(p);
+  pc->Ub = reinterpret_cast<double2*>(pc->E + N + (N & 1));
+  pc->X = pc->Ub + nn;
+  pc->T = pc->X + nn;
+  pc->coef = pc->T + nn;
+  pc->z = reinterpret_cast<double*>(pc->coef + M);
+  *ce = cudaSuccess;
+  if (sigma < 0.0) {
+    k_trace<<<1, 256, 0, st>>>(M, A, pc->z);
+    note_launch(1);
+    double tr = 0.0;
+    *ce = cudaMemcpyAsync(&tr, pc->z, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (*ce == cudaSuccess) *ce = cudaStreamSynchronize(st);
+    if (*ce != cudaSuccess) return 3;
+    sigma = -tr / (double)M;
+  }
+  pc->sigma = sigma > 0.0 ? sigma : 1e-300;
+  return hermitian_eig(H, N, pc->E, pc->Ub, st, ce);
+}
+
 // GMRES(m) for A v = -K from the initial v; returns the relative true
 // residual ||K + A v|| / ||K|| and the total inner iterations.
 cudaError_t steady_state(int64_t M, const double* A, const double* K, double* v, double tol, int max_iter,
-                         int restart, double* rel_res, int* iters, void* work, cudaStream_t st) {
+                         int restart, double* rel_res, int* iters, void* work, cudaStream_t st, const PcView* pc) {
   const int m = restart_len(M, restart);
   double* V = static_cast<double*>(work);     // (m + 1) x M Krylov basis
   double* w = V + (size_t)(m + 1) * M;       // M
@@ -209,7 +349,13 @@ cudaError_t steady_state(int64_t M, const double* A, const double* K, double* v,
     int j = 0;
     for (; j < m && total < max_iter && e == cudaSuccess; ++j) {
       ++total;
-      k_gemv64<<<gg, 256, 0, st>>>(M, A, V + (size_t)j * M, nullptr, w);
+      if (pc) {  // w = A P^-1 V_j
+        e = apply_pc(*pc, V + (size_t)j * M, pc->z, st);
+        if (e != cudaSuccess) break;
+        k_gemv64<<<gg, 256, 0, st>>>(M, A, pc->z, nullptr, w);
+      } else {
+        k_gemv64<<<gg, 256, 0, st>>>(M, A, V + (size_t)j * M, nullptr, w);
+      }
       note_launch(1);
       // classical Gram-Schmidt, twice
       for (int k = 0; k < j + 1; ++k) H[(size_t)k * m + j] = 0.0;
@@ -253,7 +399,19 @@ cudaError_t steady_state(int64_t M, const double* A, const double* K, double* v,
       y[k] = H[(size_t)k * m + k] != 0.0 ? t / H[(size_t)k * m + k] : 0.0;
     }
     e = cudaMemcpyAsync(dy, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && pc) {  // v += P^-1 (V y)
+      e = cudaMemsetAsync(w, 0, 8 * (size_t)M, st);
+      if (e == cudaSuccess) {
+        k_basis_combo<<<vb, 256, 0, st>>>(M, j, V, dy, 1.0, w);
+        note_launch(1);
+        e = apply_pc(*pc, w, pc->z, st);
+      }
+      if (e == cudaSuccess) {
+        k_add_to<<<vb, 256, 0, st>>>(M, pc->z, v);
+        note_launch(1);
+        e = cudaStreamSynchronize(st);
+      }
+    } else if (e == cudaSuccess) {
       k_basis_combo<<<vb, 256, 0, st>>>(M, j, V, dy, 1.0, v);
       note_launch(1);
       e = cudaStreamSynchronize(st);  // y on the host is rewritten by the next cycle

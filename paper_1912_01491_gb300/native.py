@@ -91,6 +91,9 @@ def load():
         "lb_pack_bf16": (ctypes.c_int, [_c_i64, _vp, _vp, _vp, _vp]),
         "lb_rk4_workspace_bytes": (ctypes.c_size_t, [_c_i64]),
         "lb_steady_workspace_bytes": (ctypes.c_size_t, [_c_i64, ctypes.c_int]),
+        "lb_steady_pc_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, _c_i64, ctypes.c_int]),
+        "lb_steady_state_pc": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, _vp, ctypes.c_double, ctypes.c_int,
+                                              ctypes.c_int, _vp, _vp, _vp, _vp]),
         "lb_steady_state": (ctypes.c_int, [_c_i64, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp,
                                            ctypes.POINTER(ctypes.c_int), _vp, _vp]),
         "lb_rho_checks_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int]),
@@ -112,6 +115,9 @@ def load():
         "lb_rho_host": (ctypes.c_int, [_vp, _vp, _vp]),
         "lb_system_destroy": (ctypes.c_int, [_vp]),
         "lb_system_get": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+        "lb_spectrum": (ctypes.c_int, [_vp, _c_i64, _vp, _vp]),
+        "lb_system_spectrum": (ctypes.c_int, [_vp, _vp]),
+        "lb_spectrum_density": (ctypes.c_int, [_vp, _c_i64, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
         "lb_system_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
         "lb_system_load": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.POINTER(_vp)]),
         "lb_integrate_resume": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, _c_i64]),
@@ -411,16 +417,29 @@ def rk4_dense(Ap, K, v, dt, nsteps, precision="fp64", scale=None, A64=None, corr
     return snaps
 
 
-def steady_state(A, K, v=None, tol=1e-12, max_iter=2000, restart=0, stream=None):
-    """FP64 solve of A v = -K on the device (restarted GMRES, lb_steady_state).
-    Returns (v, true relative residual, iterations)."""
+def steady_state(A, K, v=None, tol=1e-12, max_iter=2000, restart=0, stream=None, basis=None, H=None, sigma=-1.0):
+    """FP64 solve of A v = -K on the device (restarted GMRES, lb_steady_state;
+    with basis and H, a device N x N complex128 Hamiltonian, preconditioned
+    from H's eigenbasis: lb_steady_state_pc).  Returns (v, true relative
+    residual, iterations)."""
     import torch
     M = A.shape[0]
     v = torch.zeros(M, dtype=torch.float64, device=A.device) if v is None else v
-    work = torch.empty(load().lb_steady_workspace_bytes(M, int(restart)), dtype=torch.uint8, device=A.device)
     res, it = ctypes.c_double(), ctypes.c_int()
-    _check(load().lb_steady_state(M, _ptr(A), _ptr(K), _ptr(v), float(tol), int(max_iter), int(restart),
-                                  ctypes.byref(res), ctypes.byref(it), _ptr(work), _stream(stream)))
+    if H is None:
+        work = torch.empty(load().lb_steady_workspace_bytes(M, int(restart)), dtype=torch.uint8, device=A.device)
+        _check(load().lb_steady_state(M, _ptr(A), _ptr(K), _ptr(v), float(tol), int(max_iter), int(restart),
+                                      ctypes.byref(res), ctypes.byref(it), _ptr(work), _stream(stream)))
+    else:
+        assert basis is not None and H.dtype == torch.complex128 and H.is_contiguous()
+        n = load().lb_steady_pc_workspace_bytes(basis.N, M, int(restart))
+        if n == 0:
+            raise LBError(LB_EINVAL, "bad preconditioned steady-state arguments")
+        work = torch.empty(n + 256, dtype=torch.uint8, device=A.device)
+        off = (-work.data_ptr()) % 256
+        _check(load().lb_steady_state_pc(basis.handle, _ptr(A), _ptr(K), _ptr(H), float(sigma), _ptr(v), float(tol),
+                                         int(max_iter), int(restart), ctypes.byref(res), ctypes.byref(it),
+                                         ctypes.c_void_p(work.data_ptr() + off), _stream(stream)))
     return v, res.value, it.value
 
 
@@ -435,6 +454,28 @@ def rho_checks(basis, V, psd_shift=1e-10, stream=None):
     _check(load().lb_rho_checks(basis.handle, _ptr(V), V.shape[0], float(psd_shift), _ptr(out), _ptr(work),
                                 _stream(stream)))
     return out
+
+
+def spectrum(A, stream=None):
+    """Eigenvalues of the dense FP64 matrix A (device tensor, M x M) as a
+    complex128 device tensor of length M (lb_spectrum; Sec. 6, Fig. 5)."""
+    import torch
+    assert A.dtype == torch.float64 and A.is_contiguous() and A.dim() == 2 and A.shape[0] == A.shape[1]
+    w = torch.empty(A.shape[0], dtype=torch.complex128, device=A.device)
+    _check(load().lb_spectrum(_ptr(A), A.shape[0], _ptr(w), _stream(stream)))
+    return w
+
+
+def spectrum_density(eig, box, nre=100, nim=100, stream=None):
+    """Eigenvalues per unit area on an nre x nim grid over box = (re_lo,
+    re_hi, im_lo, im_hi) (lb_spectrum_density): a float64 device tensor
+    (nre, nim), the real part along the rows."""
+    import torch
+    assert eig.dtype == torch.complex128 and eig.is_contiguous()
+    b = np.ascontiguousarray(box, np.float64)
+    d = torch.empty((nre, nim), dtype=torch.float64, device=eig.device)
+    _check(load().lb_spectrum_density(_ptr(eig), eig.numel(), _ptr(b), int(nre), int(nim), _ptr(d), _stream(stream)))
+    return d
 
 
 class Propagator:
@@ -691,6 +732,13 @@ class System:
         out = np.zeros(self.M if part == "K" else (self.M, self.M))
         _check(load().lb_system_get(self._h, p, _ptr(out)))
         return out
+
+    def spectrum(self):
+        """Eigenvalues of A (complex128 numpy array of length M) of a dense
+        system (lb_system_spectrum)."""
+        out = np.zeros(2 * self.M)
+        _check(load().lb_system_spectrum(self._h, _ptr(out)))
+        return out[0::2] + 1j * out[1::2]
 
     def get_csr(self):
         """(rowptr int64, col int32, val float64) of a CSR system."""

@@ -629,6 +629,52 @@ def test_steady_state_against_oracle_solve(N):
     assert abs(np.trace(rho) - 1) < 1e-13 and np.linalg.eigvalsh(rho).min() > -1e-10
 
 
+@pytest.mark.parametrize("N", [4, 23, 40])
+def test_dense_assembly_deterministic(N):
+    """The CLOSED assembly writes every entry once, with no atomics: two
+    calls (lb_assemble_dense and the event-timed lb_assemble_dense_timed)
+    write the same bits into buffers prefilled with NaN."""
+    H, a = _case(N, 4800 + N)
+    lb = lbm()
+    with lb.Basis(N) as B:
+        ad = torch.tensor(a, device="cuda")
+        h = B.expand(torch.tensor(H, device="cuda")).real.contiguous()
+        M = B.M
+        A1 = torch.full((M, M), float("nan"), dtype=torch.float64, device="cuda")
+        A2 = torch.full((M, M), float("nan"), dtype=torch.float64, device="cuda")
+        K1, K2 = (torch.empty(M, dtype=torch.float64, device="cuda") for _ in range(2))
+        B.assemble_dense(ad, h=h, A=A1, K=K1, algorithm="closed")
+        ms = B.assemble_dense_timed(ad, h=h, A=A2, K=K2, algorithm="closed")
+        torch.cuda.synchronize()
+    assert torch.isfinite(A1).all()
+    assert torch.equal(A1, A2) and torch.equal(K1, K2)
+    assert all(t >= 0.0 for t in ms.values())
+
+
+@pytest.mark.parametrize("N", [5, 12, 30])
+def test_steady_state_preconditioned_against_oracle_solve(N):
+    """The same solve preconditioned from H's eigenbasis (P = Q - sigma 1,
+    sigma = -Tr(A)/M): the same bars, in far fewer iterations than the plain
+    GMRES takes on the same system."""
+    H, a = _case(N, 1400 + N)
+    lb = lbm()
+    with lb.Basis(N) as B, Oracle(N) as o:
+        A, K = _oracle_system(o, H, a)
+        ref = np.linalg.solve(A, -K)
+        Hd = torch.tensor(H, device="cuda")
+        g = B.assemble_dense(torch.tensor(a, device="cuda"), h=B.expand(Hd).real.contiguous())
+        v, res, it = lb.steady_state(g["A"], g["K"], tol=1e-13, max_iter=500, basis=B, H=Hd)
+        _, res0, it0 = lb.steady_state(g["A"], g["K"], tol=1e-13, max_iter=5000)
+        torch.cuda.synchronize()
+        assert res <= 1e-11, (res, it)
+        assert np.linalg.norm(v.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref), (res, it)
+        assert it <= max(10, it0 // 4), (it, it0)
+        # an explicit shift gives the same solution
+        v2, res2, _ = lb.steady_state(g["A"], g["K"], tol=1e-13, max_iter=500, basis=B, H=Hd,
+                                      sigma=-float(np.trace(A)) / B.M)
+        assert res2 <= 1e-11 and np.linalg.norm(v2.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
 def test_steady_state_degenerate_inputs():
     """K = 0 (a = gamma 1): v* = 0 with zero residual and no iteration."""
     N = 4

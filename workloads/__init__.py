@@ -110,6 +110,14 @@ def random_lindbladian_device(N, seed, device="cuda"):
     return H, a.contiguous()
 
 
+def random_lindbladian_paper_device(N, seed, device="cuda"):
+    """The random Lindbladian of Sec. 3 as the paper defines it: H = 0 and the
+    Kossakowski matrix N G G^dagger / Tr(G G^dagger) (Tr = N), G complex
+    Ginibre, formed on the GPU in FP64.  Returns a (M x M complex128)."""
+    _, a = random_lindbladian_device(N, seed, device=device)
+    return a * float(N)
+
+
 def ladder_model(N, seed, gamma=0.1):
     """(H real tridiagonal N x N complex128, L N x N complex128, gamma)."""
     g = rng(seed)
