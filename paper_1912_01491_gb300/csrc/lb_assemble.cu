@@ -428,7 +428,8 @@ __global__ void k_kvec(BasisView B, AView A, double* __restrict__ K) {
 //            = -(1/N) sum_k delta_k(nu) G_k,  G_k = sum_{y>k} g_ky - sum_{x<k} g_xk,
 // and sum_k delta_k(nu) G_k = c_nu sum_{k<nu} G_k - nu c_nu G_nu (the prefix
 // form of the Helmert vectors).  k_kvec_diag_g: one block per vertex k, a
-// fixed-order reduction; k_kvec_diag: one warp, the prefix over k.
+// fixed-order reduction; k_kvec_diag: the prefix over k (one warp) and the
+// rows.
 __global__ void __launch_bounds__(128) k_kvec_diag_g(BasisView B, AView A, double* __restrict__ G) {
   const int N = B.N, k = blockIdx.x;
   double acc = 0.0;
@@ -445,14 +446,19 @@ __global__ void __launch_bounds__(128) k_kvec_diag_g(BasisView B, AView A, doubl
   if (threadIdx.x == 0) G[k] = (red[0] + red[1]) + (red[2] + red[3]);
 }
 
-__global__ void k_kvec_diag(BasisView B, const double* __restrict__ G, double* __restrict__ K) {
-  if (threadIdx.x != 0) return;
+__device__ __forceinline__ void warp_prefix(double* arr, int n);  // below
+
+__global__ void __launch_bounds__(256) k_kvec_diag(BasisView B, const double* __restrict__ G,
+                                                    double* __restrict__ K) {
+  __shared__ double pre[lbi::kMaxDenseN + 1];  // pre[nu] = sum_{k < nu} G_k
   const int N = B.N;
-  double pre = 0.0;  // sum_{k < nu} G_k
-  for (int nu = 1; nu < N; ++nu) {
-    pre += G[nu - 1];
-    K[d_index(B, nu)] = -(ld_c(B, nu) * pre + ld_lc(B, nu) * G[nu]) / (double)N;
-  }
+  for (int k = threadIdx.x; k < N; k += blockDim.x) pre[k + 1] = G[k];
+  if (threadIdx.x == 0) pre[0] = 0.0;
+  __syncthreads();
+  if (threadIdx.x < 32) warp_prefix(pre, N);
+  __syncthreads();
+  for (int nu = 1 + threadIdx.x; nu < N; nu += blockDim.x)
+    K[d_index(B, nu)] = -(ld_c(B, nu) * pre[nu] + ld_lc(B, nu) * G[nu]) / (double)N;
 }
 
 // ---------------------------------------------------------------------------
@@ -1753,13 +1759,14 @@ __device__ __forceinline__ void shared_entry_var(const double2 (&X)[2][2], const
                                                  int Q_, int v, int ts, int tn, double& acc2, double& accD) {
   const int pv = P_ < v ? 1 : 0, qv = Q_ < v ? 1 : 0;
   const int a_ = coef_phase(ts, v, P_), b_ = coef_phase(tn, v, Q_);
-  acc2 = 0.0;
-  accD = 0.0;
+  // the sums start from their first term (an add to 0.0 is an FP64
+  // instruction of its own)
 #pragma unroll
   for (int tl = 0; tl < 2; ++tl) {  // (A1) at v
     const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
     const SharedSigns g = shared_signs_a1(ts, tn, tl, a_, b_, pv, qv);
-    acc2 += sgn_mul(-g.kf * g.sfv, S.sre(tr, tjf, tk, v));
+    const double t1 = sgn_mul(-g.kf * g.sfv, S.sre(tr, tjf, tk, v));
+    acc2 = tl == 0 ? t1 : acc2 + t1;
     acc2 += sgn_mul(g.kd * g.sdv, S.sim(tr, tjd, tk, v));
   }
 #pragma unroll
@@ -1783,7 +1790,7 @@ __device__ __forceinline__ void shared_entry_var(const double2 (&X)[2][2], const
       const double x = S.DX[tk * S.L + v];  // dx(lo, hi, -1) = X[lo] - X[hi], negated for tn = S
       part = tn == kS ? (vlo_q ? -x : x) : (vlo_q ? x : -x);
     }
-    accD += sgn_mul(sk, part);
+    accD = tl == 0 ? sgn_mul(sk, part) : accD + sgn_mul(sk, part);
   }
   {  // (B) at v
     const int tl = 1 - ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
@@ -2026,12 +2033,26 @@ __global__ void __launch_bounds__(256, 3) k_shared_closed(BasisView B, AView A, 
   }
 }
 
-// Closed-form k_pd: per row s the nu-independent sums are prefix arrays,
-//   PGY[lam] = sum gs(lam') Im Y[lam'],  PG2C = sum 2 gs c,  PCY = sum c_mu Im Y[mu],
-//   and for each (vi, tl) the raw Re a(partner(l), k), Im a(l, k) over w.
+// Closed-form k_pd (pair row s, diagonal columns D_nu) and, when K is
+// given, K_s.  Per row, with gs(x) = delta_as(x) - delta_bs(x), which is c_x
+// for as < x < bs, lc_as at x = as >= 1 and (1 + bs) c_bs at x = bs:
+//   YY[x] = Im a[partner(s)][D_x] and PCY, the prefix of c_x YY[x]; the
+//     sums of gs(x) YY[x] over x are PCY differences plus the two ends;
+//   the sum of 2 gs(x) c_x over x from max(lo_s, nu + 1) to bs is 2/(nu + 1)
+//     for as <= nu < bs and 0 otherwise (sum_{x=l}^{m} c_x^2 = 1/l - 1/(m + 1),
+//     lc_as c_as = -1/(as + 1), (1 + bs) c_bs^2 = 1/bs);
+//   U1S[w] = the sum over the two vertices v of e(s) of U1(v)_w, raw and as
+//     a prefix over w; the totals U2(v) = sum_w U2(v)_w (see below);
+//   c1 = sum gs(mu) Re a[s][D_mu];  LY = sum of sk Im a(l, k) over the
+//     triangle terms (K's triangle part).
+// K_s = -(1/N) sum_jk Im(a_jk) f_jks: the triangle terms have
+// f(l, k, s) = -sk/sqrt2, and j = partner(s), k = D_l together with
+// j = D_l, k = partner(s) give 2 sgs sum_l gs(l) YY[l].
+constexpr int kPdRed = 4;  // block totals: U2(as), U2(bs), c1, LY
+
 __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A, const double* __restrict__ h,
                                                            double* __restrict__ Aout, double* __restrict__ Qout,
-                                                           double* __restrict__ Rout) {
+                                                           double* __restrict__ Rout, double* __restrict__ K) {
   extern __shared__ double sq[];
   const int N = B.N;
   const int64_t P = B.P, M = B.M;
@@ -2040,113 +2061,125 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
   const int as = es.a, bs = es.b, ts = es.kind;
   const int64_t sb = partner(B, s);
   const int lo_s = imax(as, 1);
-  const double sgs = ts == kS ? 1.0 : -1.0;
   const int L = N + 1;
   double* YY = sq;            // Im a[partner(s)][D_x]   (raw, index x)
-  double* PGY = sq + L;       // prefix of gs(lam) YY[lam] over lam in [lo_s, bs]
-  double* PG2C = sq + 2 * L;  // prefix of 2 gs(lam) c_lam
-  double* PCY = sq + 3 * L;   // prefix of c_mu YY[mu]
-  double* PU1 = sq + 4 * L;   // [2][L]: prefix over w of U1 (both tl), per vi (see below)
-  double* RU1 = sq + 6 * L;   // [2][L]: U1 at w (raw)
-  double* PU2 = sq + 8 * L;   // [2][L]: prefix over w of U2 (both tl), per vi
-  __shared__ double cst[2];   // c1 = sum gs Re a[s][D_mu], c2 = sum gs Im a[partner(s)][D_mu]
-  __shared__ double cpart[kRowThreads / 32];
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
-    const double y = x >= 1 ? ldA(A, sb, d_index(B, x)).y : 0.0;
-    const double gs = (x >= lo_s && x <= bs) ? dlt(B, as, x) - dlt(B, bs, x) : 0.0;
-    YY[x] = y;
-    PGY[x + 1] = gs * y;
-    PG2C[x + 1] = x >= 1 ? 2.0 * gs * ld_c(B, x) : 0.0;
-    PCY[x + 1] = x >= 1 ? ld_c(B, x) * y : 0.0;
-  }
+  double* PCY = sq + L;       // prefix of c_x YY[x]
+  double* PU1 = sq + 2 * L;   // prefix over w of U1S
+  double* RU1 = sq + 3 * L;   // U1S at w (raw)
+  __shared__ double red[kPdRed][kRowThreads];
+  __shared__ double cst[kPdRed + 1];  // totals, then sum_{x in [lo_s, bs]} gs(x) YY[x]
   // l = (v, w) sharing the vertex v with e(s): with bx = Re a(partner(l), k),
   // ly = Im a(l, k), sk the sign of f(k, l, s), sigma = [w < v] - [w > v] and
   // tau = -1 for l of type S, the family contributes
   //   sum_w sk (tau sigma (delta_w(nu) - delta_v(nu)) bx - (delta_v(nu) + delta_w(nu)) ly)
   //   = d_nu^T U1 + delta_v(nu) U2,  U1_w = sk (tau sigma bx - ly),  U2 = sum_w sk (-tau sigma bx - ly),
   // and d_nu^T U1 = c_nu sum_{w<nu} U1_w + delta_nu(nu) U1_nu (a prefix over w).
-  // The two tl of one (vi, w) enter every entry with the same coefficients,
-  // so they are summed here.
-  for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
-    const int vi = t / N, w = t % N;
-    double u1 = 0.0, u2 = 0.0;
-    if (w != as && w != bs) {
-      const int v = vi ? bs : as, vp = vi ? as : bs;
-      const int64_t pl = pair_index_any(N, v, w), pk = pair_index_any(N, vp, w);
-      double2 lb[2];  // (ly, bx) of tl = S, J
+  // The two tl of one (v, w) enter every entry with the same coefficients,
+  // and so do the two v for U1, so they are summed here.
+  double t_u2a = 0.0, t_u2b = 0.0, t_c1 = 0.0, t_ly = 0.0;
+  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+    const double y = x >= 1 ? ldA(A, sb, d_index(B, x)).y : 0.0;
+    YY[x] = y;
+    PCY[x + 1] = x >= 1 ? ld_c(B, x) * y : 0.0;
+    if (x >= lo_s && x <= bs) t_c1 = fma(dlt(B, as, x) - dlt(B, bs, x), ldA(A, s, d_index(B, x)).x, t_c1);
+    double u1s = 0.0, u1v[2];
+    if (x != as && x != bs) {
+      const int w = x;
 #pragma unroll
-      for (int tl = 0; tl < 2; ++tl) {
-        const int64_t k = (int64_t)(1 ^ tl ^ ts) * P + pk;
-        lb[tl] = make_double2(ldA(A, (int64_t)tl * P + pl, k).y, ldA(A, (int64_t)(1 - tl) * P + pl, k).x);
-      }
-      // u1 = sum_tl sk (tsb - ly) = Pb - Ly and u2 = sum_tl sk (-tsb - ly) = -Pb - Ly
-      double pb = 0.0, ly = 0.0;
+      for (int vi = 0; vi < 2; ++vi) {
+        const int v = vi ? bs : as, vp = vi ? as : bs;
+        const int64_t pl = pair_index_any(N, v, w), pk = pair_index_any(N, vp, w);
+        double lyv[2], bxv[2];
 #pragma unroll
-      for (int tl = 0; tl < 2; ++tl) {
-        const int tk = 1 ^ tl ^ ts;
-        const int sk = sgn_f(coef_phase(ts, v, vp) + coef_phase(tk, vp, w) + coef_phase(tl, w, v));
-        const int st = ((tl == kS) != (w < v)) ? sk : -sk;  // sk tau sigma
-        pb += sgn_mul(st, lb[tl].y);
-        ly += sgn_mul(sk, lb[tl].x);
+        for (int tl = 0; tl < 2; ++tl) {
+          const int64_t k = (int64_t)(1 ^ tl ^ ts) * P + pk;
+          const int tk = 1 ^ tl ^ ts;
+          const int sk = sgn_f(coef_phase(ts, v, vp) + coef_phase(tk, vp, w) + coef_phase(tl, w, v));
+          const int st = ((tl == kS) != (w < v)) ? sk : -sk;  // sk tau sigma
+          lyv[tl] = sgn_mul(sk, ldA(A, (int64_t)tl * P + pl, k).y);
+          bxv[tl] = sgn_mul(st, ldA(A, (int64_t)(1 - tl) * P + pl, k).x);
+        }
+        // u1 = Pb - Ly, u2 = -Pb - Ly
+        const double pb = bxv[0] + bxv[1], ly = lyv[0] + lyv[1];
+        u1v[vi] = pb - ly;
+        if (vi) t_u2b -= pb + ly;
+        else t_u2a -= pb + ly;
+        t_ly += ly;
       }
-      u1 = pb - ly;
-      u2 = -pb - ly;
+      u1s = u1v[0] + u1v[1];
     }
-    PU1[vi * L + w + 1] = u1;
-    RU1[vi * L + w] = u1;
-    PU2[vi * L + w + 1] = u2;
+    PU1[x + 1] = u1s;
+    RU1[x] = u1s;
   }
-  // c1 = sum gs(mu) Re a[s][D_mu] over mu in [lo_s, bs]: a block sum
-  {
-    double c1 = 0.0;
-    for (int mu = imax(lo_s, 1) + threadIdx.x; mu <= bs; mu += blockDim.x)
-      c1 += (dlt(B, as, mu) - dlt(B, bs, mu)) * ldA(A, s, d_index(B, mu)).x;
-    c1 = warp_sum(c1);
-    if ((threadIdx.x & 31) == 0) cpart[threadIdx.x >> 5] = c1;
+  red[0][threadIdx.x] = t_u2a;
+  red[1][threadIdx.x] = t_u2b;
+  red[2][threadIdx.x] = t_c1;
+  red[3][threadIdx.x] = t_ly;
+  if (threadIdx.x == 0) PCY[0] = PU1[0] = 0.0;
+  __syncthreads();
+  // warps 0, 1: the two prefix sums; warps 2, 3: the four block totals
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  static_assert(kRowThreads == 128 && kPdRed == 4, "four warps: two scans, four totals");
+  if (wid < 2) {
+    warp_prefix(wid == 0 ? PCY : PU1, N);
+    if (wid == 0) {
+      __syncwarp();
+      if (lane == 0) {  // sum_{x in [lo_s, bs]} gs(x) YY[x]: the two ends and a PCY difference
+        const double tas = as >= 1 ? ld_lc(B, as) * YY[as] : 0.0;
+        const double tbs = (ld_c(B, bs) - ld_lc(B, bs)) * YY[bs];
+        cst[kPdRed] = (tas + tbs) + isum(PCY, as + 1, bs - 1);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k2 = 0; k2 < 2; ++k2) {
+      const int r = 2 * (wid - 2) + k2;
+      double t = (red[r][lane] + red[r][lane + 32]) + (red[r][lane + 64] + red[r][lane + 96]);
+      t = warp_sum(t);
+      if (lane == 0) cst[r] = t;
+    }
   }
-  // prefix arrays: PGY, PG2C, PCY, PU1[0..1], PU2[0..1], one warp each
-  auto scanned = [&](int i) { return i < 3 ? PGY + i * L : i < 5 ? PU1 + (i - 3) * L : PU2 + (i - 5) * L; };
-  if (threadIdx.x < 7) scanned(threadIdx.x)[0] = 0.0;
   __syncthreads();
-  for (int i = threadIdx.x >> 5; i < 7; i += kRowThreads / 32) warp_prefix(scanned(i), N);
-  if (threadIdx.x == 0) {
-    double c1 = 0.0;
-    for (int i = 0; i < kRowThreads / 32; ++i) c1 += cpart[i];
-    cst[0] = c1;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) cst[1] = isum(PGY, lo_s, bs);
-  __syncthreads();
-  // per entry about 21 FP64 instructions: signs and the exact factors 2 and
+  const double u2a = cst[0], u2b = cst[1], c1 = cst[2], gy = cst[kPdRed];
+  const int sgs = ts == kS ? 1 : -1;
+  if (K != nullptr && threadIdx.x == 0)
+    K[s] = -(fma(cst[3], -kInvSqrt2, twice(sgn_mul(sgs, gy)))) / (double)N;
+  // the ends of sum_{x = lo_s}^{min(bs, nu - 1)} gs(x) YY[x]
+  const double tas = as >= 1 ? ld_lc(B, as) * YY[as] : 0.0;
+  const double tab = tas + (ld_c(B, bs) - ld_lc(B, bs)) * YY[bs];
+  const double pcy_lo = PCY[as + 1];
+  // per entry about 18 FP64 instructions: signs and the exact factors 2 and
   // -1/2 are applied to the bits with integer operations
   const double hsb = h != nullptr ? __ldg(h + sb) : 0.0;
   for (int nu = 1 + threadIdx.x; nu < N; nu += blockDim.x) {
     const double cnu = ld_c(B, nu);
     const bool inr = nu >= lo_s && nu <= bs;
     const double gs = inr ? dlt(B, as, nu) - dlt(B, bs, nu) : 0.0;
-    // l = D_lam
-    double accD = twice(cnu) * isum(PGY, lo_s, imin(bs, nu - 1));
-    accD = fma(YY[nu], isum(PG2C, imax(lo_s, nu + 1), bs), accD);
+    // l = D_lam: sum_{lam < nu} gs(lam) YY[lam] and sum_{lam > nu} 2 gs(lam) c_lam
+    const int hi = imin(bs - 1, nu - 1);
+    double g1 = hi >= as + 1 ? PCY[hi + 1] - pcy_lo : 0.0;
+    g1 += nu > bs ? tab : (nu > as ? tas : 0.0);
+    double accD = twice(cnu) * g1;
+    if (nu >= as && nu < bs) accD = fma(YY[nu], twice(__ldg(B.inv + nu + 1)), accD);
     if (inr) {
       double t2 = twice(isum(PCY, nu + 1, N - 1));
       if (nu != 1) t2 = fma(twice(cnu + ld_lc(B, nu)), YY[nu], t2);  // 2 (1 - nu) c_nu
       accD = fma(gs, t2, accD);
     }
-    double acc = sgn_mul(ts == kS ? 1 : -1, accD);
+    double acc = sgn_mul(sgs, accD);
     // l = (v, w) sharing a vertex with e(s): d_nu^T U1 + delta_v(nu) U2 per v
-    const double dnn = dlt(B, nu, nu);
-    double accA = cnu * (PU1[nu] + PU1[L + nu]);
-    accA = fma(dnn, RU1[nu] + RU1[L + nu], accA);
-    accA = fma(dlt(B, as, nu), PU2[N], accA);
-    accA = fma(dlt(B, bs, nu), PU2[L + N], accA);
+    double accA = cnu * PU1[nu];
+    accA = fma(dlt(B, nu, nu), RU1[nu], accA);
+    accA = fma(dlt(B, as, nu), u2a, accA);
+    accA = fma(dlt(B, bs, nu), u2b, accA);
     acc = fma(accA, kInvSqrt2, acc);
     // l = partner(s), k = D_mu
     {
       const double hnu = (nu >= lo_s && !(as == 0 && bs == 1 && nu == 1)) ? dlt(B, as, nu) + dlt(B, bs, nu) : 0.0;
-      acc = fma(-gs, cst[0], acc);
-      acc = fma(hnu, sgn_mul(ts == kS ? 1 : -1, cst[1]), acc);
+      acc = fma(-gs, c1, acc);
+      acc = fma(hnu, sgn_mul(sgs, gy), acc);
     }
-    const double q = inr ? sgn_mul(ts == kS ? 1 : -1, hsb * gs) : 0.0;
+    const double q = inr ? sgn_mul(sgs, hsb * gs) : 0.0;
     const double r = neg_half(acc);
     const int64_t o = s * M + d_index(B, nu);
     if (Rout) Rout[o] = r;
@@ -2252,7 +2285,8 @@ __global__ void __launch_bounds__(kSameThreads) k_same_closed(BasisView B, AView
                                                               const double* __restrict__ Hi,
                                                               double* __restrict__ Aout, double* __restrict__ Qout,
                                                               double* __restrict__ Rout) {
-  __shared__ double red[kSameThreads / 32][5];
+  __shared__ double red[5][kSameThreads];  // per thread: the four entries' sums, the Q sum
+  __shared__ double tot[5];
   const int N = B.N;
   const int64_t P = B.P, M = B.M;
   const int64_t e = blockIdx.x;
@@ -2308,23 +2342,25 @@ __global__ void __launch_bounds__(kSameThreads) k_same_closed(BasisView B, AView
   double hc = 0.0;
   if (h != nullptr)
     for (int lam = a + 1 + threadIdx.x; lam <= b; lam += blockDim.x) hc += __ldg(h + d_index(B, lam)) * ld_c(B, lam);
+  // block sums: the partial sums go to shared memory and one warp reduces
+  // each of the five (fewer FP64 warp instructions than a shuffle
+  // reduction per warp and value)
 #pragma unroll
-  for (int combo = 0; combo < 4; ++combo) {
-    const double tot = warp_sum(0.5 * acc2[combo] + accD[combo]);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][combo] = tot;
-  }
+  for (int combo = 0; combo < 4; ++combo) red[combo][threadIdx.x] = fma(0.5, acc2[combo], accD[combo]);
+  red[4][threadIdx.x] = hc;
+  __syncthreads();
+  static_assert(kSameThreads == 128, "four warps reduce five sums of 128 values");
   {
-    const double tot = warp_sum(hc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][4] = tot;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = wid; i < 5; i += 4) {
+      const double t = warp_sum((red[i][lane] + red[i][lane + 32]) + (red[i][lane + 64] + red[i][lane + 96]));
+      if (lane == 0) tot[i] = t;
+    }
   }
   __syncthreads();
   if (threadIdx.x < 4) {
     const int combo = threadIdx.x, ts = combo >> 1, tn = combo & 1;
-    double sum = 0.0, hsum = 0.0;
-    for (int i = 0; i < kSameThreads / 32; ++i) {
-      sum += red[i][combo];
-      hsum += red[i][4];
-    }
+    const double sum = tot[combo], hsum = tot[4];
     // the D-section part (completeness form): -1/2 sgs sgn 2 Re a_{partner(n) partner(s)}
     const double2 a1 = ldA_row(A, (int64_t)(1 - tn) * P + e, (int64_t)(1 - ts) * P + e);
     const double r = sgn_mul((ts == tn) ? -1 : 1, a1.x) + -0.5 * sum;
@@ -2465,9 +2501,9 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
   // 1: pair x diagonal
   if (dense_out && e == cudaSuccess) {
     if (closed) {
-      const size_t smem = sizeof(double) * 10 * (size_t)(N + 1);
+      const size_t smem = sizeof(double) * 4 * (size_t)(N + 1);
       e = cudaFuncSetAttribute(k_pd_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_pd_closed<<<(unsigned)P2, kRowThreads, smem, st>>>(B, av, h, A, Q, R);
+      if (e == cudaSuccess) k_pd_closed<<<(unsigned)P2, kRowThreads, smem, st>>>(B, av, h, A, Q, R, K);
     } else {
       const size_t smem = sizeof(double2) * 10 * (size_t)N;
       e = cudaFuncSetAttribute(k_pd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -2539,12 +2575,16 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
   // 6: K (closed: the diagonal rows from the vertex sums G in the scratch)
   if (K && e == cudaSuccess) {
     if (closed) {
+      // the pair rows of K come from k_pd_closed when it runs
       const int64_t warps = 2 * B.P;
-      if (warps > 0) k_kvec<true><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(B, av, K);
+      if (warps > 0 && !dense_out) {
+        k_kvec<true><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(B, av, K);
+        note_launch(1);
+      }
       double* G = scratch + 3 * (size_t)N * N;
       k_kvec_diag_g<<<(unsigned)N, 128, 0, st>>>(B, av, G);
-      k_kvec_diag<<<1, 32, 0, st>>>(B, G, K);
-      note_launch(3);
+      k_kvec_diag<<<1, 256, 0, st>>>(B, G, K);
+      note_launch(2);
     } else {
       const int64_t warps = B.M;
       k_kvec<false><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(B, av, K);
