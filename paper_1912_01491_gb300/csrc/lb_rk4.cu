@@ -280,6 +280,240 @@ __global__ void __launch_bounds__(256)
     xn32[s] = (float)nx;
 }
 
+// ---------------------------------------------------------------- CSR, pipelined
+// Persistent form of the block-staged stage: each block walks the chunks of
+// 256 rows c = blockIdx.x, blockIdx.x + gridDim.x, ... and, while it sums
+// chunk i out of one shared-memory buffer, the bulk-copy engine (TMA,
+// cp.async.bulk) fills the other with the column and value range of chunk
+// i + 1; the rows' own state (row pointers, Keff, v, acc) of chunk i + 1 is
+// loaded into registers during chunk i.  A copy starts at the range's first
+// entry rounded down to 16 bytes and ends at its last rounded up (up to three
+// entries of the neighbouring chunks on either side; never past nnz): a
+// chunk whose rounded range would pass nnz, or that exceeds `cap`, is summed
+// from global memory instead.  Every wait on a copy is bounded (about two
+// seconds of clock): on a timeout the block sets *err, waits (bounded) for its
+// other copy in flight and returns.
+constexpr long long kCopyWaitCycles = 4000000000LL;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// bulk copy global -> shared, completing on the mbarrier; `policy` is an L2
+// cache policy (the streamed arrays are marked evict-first, so that the
+// gathered vector stays in L2)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar,
+                                         uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// true once the phase of the given parity has completed; false after about
+// kCopyWaitCycles
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kCopyWaitCycles) return false;
+  }
+}
+
+// *out = the largest entry count of a chunk of 256 rows (clamped to int).
+__global__ void k_chunk_max_range(int64_t M, const int64_t* __restrict__ rowptr, int* __restrict__ out) {
+  const int64_t cc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((cc << 8) >= M) return;
+  const int64_t r0 = cc << 8, r1 = r0 + 256 < M ? r0 + 256 : M;
+  const int64_t n = rowptr[r1] - rowptr[r0];
+  atomicMax(out, n < 0x7fffffff ? (int)n : 0x7fffffff);
+}
+
+// Shared-memory layout of one buffer of k_stage_csr_pipe: the chunk's row
+// pointers (258 entries), Keff, v and acc (256 each), then its values and
+// columns (cap + 8 entries each: the range rounded out to 16 bytes).
+constexpr size_t kPipeRowBytes = 258 * 8 + 3 * 256 * 8;
+template <class V>
+__host__ __device__ inline size_t csr_pipe_vbytes(int cap) {
+  return ((sizeof(V) * (size_t)(cap + 8)) + 15) & ~size_t(15);
+}
+template <class V>
+__host__ __device__ inline size_t csr_pipe_buf_bytes(int cap) {
+  return kPipeRowBytes + csr_pipe_vbytes<V>(cap) + ((sizeof(int32_t) * (size_t)(cap + 8) + 15) & ~size_t(15));
+}
+
+template <int PREC, int STAGE>
+__global__ void __launch_bounds__(256)
+    k_stage_csr_pipe(int64_t M, int64_t nnz, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                     const void* __restrict__ val, int cap, const double* __restrict__ Keff,
+                     const double* __restrict__ x, const float* __restrict__ x32, double* __restrict__ xn,
+                     float* __restrict__ xn32, double* __restrict__ acc, double* __restrict__ v, double h,
+                     int* __restrict__ err) {
+  using V = typename std::conditional<PREC == LB_FP64, double, float>::type;
+  constexpr int64_t kVA = 16 / (int64_t)sizeof(V);  // entries per 16 bytes
+  extern __shared__ __align__(128) unsigned char csr_pipe[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ int64_t s_base[2];
+  __shared__ int s_offv[2], s_offc[2], s_staged[2], s_rows[2];
+  const size_t vbytes = csr_pipe_vbytes<V>(cap), buf_bytes = csr_pipe_buf_bytes<V>(cap);
+  const V* __restrict__ vv = static_cast<const V*>(val);
+  const int64_t nch = (M + 255) >> 8, G = gridDim.x;
+  int64_t c = blockIdx.x;
+  if (c >= nch) return;
+  const uint32_t bars[2] = {smem_u32(&bar[0]), smem_u32(&bar[1])};
+  // thread 0: stage chunk cc, whose entries are [base, end), into buffer b:
+  // its row arrays when the chunk is whole (and its 258th row pointer
+  // exists), its column and value range when within cap and nnz
+  auto issue = [&](int b, int64_t cc, int64_t base, int64_t end) {
+    const int64_t r0 = cc << 8;
+    const bool rows = r0 + 258 <= M + 1;
+    const int64_t a0c = base & ~int64_t(3), a1c = (end + 3) & ~int64_t(3);
+    const int64_t a0v = base & ~(kVA - 1), a1v = (end + kVA - 1) & ~(kVA - 1);
+    const bool st = end - base <= cap && a1c <= nnz;
+    s_base[b] = base;
+    s_offc[b] = (int)(base - a0c);
+    s_offv[b] = (int)(base - a0v);
+    s_staged[b] = st ? 1 : 0;
+    s_rows[b] = rows ? 1 : 0;
+    const uint32_t bc = st ? (uint32_t)(sizeof(int32_t) * (a1c - a0c)) : 0u;
+    const uint32_t bv = st ? (uint32_t)(sizeof(V) * (a1v - a0v)) : 0u;
+    const uint32_t br = rows ? (uint32_t)(258 * 8 + (STAGE > 1 ? 3 : 2) * 256 * 8) : 0u;
+    unsigned char* buf = csr_pipe + b * buf_bytes;
+    const uint64_t pol = l2_evict_first();
+    // the buffer was last read through the generic proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bars[b], bc + bv + br);
+    if (rows) {
+      bulk_g2s(smem_u32(buf), rowptr + r0, 258 * 8, bars[b], pol);
+      bulk_g2s(smem_u32(buf + 258 * 8), Keff + r0, 256 * 8, bars[b], pol);
+      bulk_g2s(smem_u32(buf + 258 * 8 + 2048), v + r0, 256 * 8, bars[b], pol);
+      if (STAGE > 1) bulk_g2s(smem_u32(buf + 258 * 8 + 4096), acc + r0, 256 * 8, bars[b], pol);
+    }
+    if (bv) bulk_g2s(smem_u32(buf + kPipeRowBytes), vv + a0v, bv, bars[b], pol);
+    if (bc) bulk_g2s(smem_u32(buf + kPipeRowBytes + vbytes), col + a0c, bc, bars[b], pol);
+  };
+  auto range = [&](int64_t cc, int64_t& base, int64_t& end) {
+    const int64_t r0 = cc << 8, r1 = r0 + 256 < M ? r0 + 256 : M;
+    base = __ldg(rowptr + r0);
+    end = __ldg(rowptr + r1);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(bars[0], 1);
+    mbar_init(bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t base, end;
+    range(c, base, end);
+    issue(0, c, base, end);
+    if (c + G < nch) {
+      range(c + G, base, end);
+      issue(1, c + G, base, end);
+    }
+  }
+  int64_t nb = 0, ne = 0;
+  for (int64_t i = 0; c < nch; ++i, c += G) {
+    const int b = (int)(i & 1);
+    // thread 0: the range of the chunk after the next, in flight during this one
+    if (threadIdx.x == 0 && c + 2 * G < nch) range(c + 2 * G, nb, ne);
+    const bool ok = mbar_wait(bars[b], (uint32_t)((i >> 1) & 1));
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) {  // the copies still in flight, bounded again
+        atomicExch(err, 1);
+        mbar_wait(bars[b], (uint32_t)((i >> 1) & 1));
+        if (c + G < nch) mbar_wait(bars[b ^ 1], (uint32_t)(((i + 1) >> 1) & 1));
+      }
+      return;
+    }
+    const unsigned char* buf = csr_pipe + b * buf_bytes;
+    const int64_t s = (c << 8) + threadIdx.x;
+    if (s < M) {
+      int64_t rb, re;
+      double kf, vs, ac = 0.0;
+      if (s_rows[b]) {
+        const int64_t* srp = reinterpret_cast<const int64_t*>(buf);
+        const double* sk = reinterpret_cast<const double*>(buf + 258 * 8);
+        rb = srp[threadIdx.x];
+        re = srp[threadIdx.x + 1];
+        kf = sk[threadIdx.x];
+        vs = sk[256 + threadIdx.x];
+        if (STAGE > 1) ac = sk[512 + threadIdx.x];
+      } else {
+        rb = __ldg(rowptr + s);
+        re = __ldg(rowptr + s + 1);
+        kf = __ldcs(Keff + s);
+        vs = __ldcs(v + s);
+        if (STAGE > 1) ac = __ldcs(acc + s);
+      }
+      double y;
+      if (s_staged[b]) {
+        // entry q of the range sits at index q - base + offset of its array
+        const V* sval = reinterpret_cast<const V*>(buf + kPipeRowBytes);
+        const int32_t* scol = reinterpret_cast<const int32_t*>(buf + kPipeRowBytes + vbytes);
+        const int qv = (int)(rb - s_base[b]) + s_offv[b], qc = (int)(rb - s_base[b]) + s_offc[b];
+        const int len = (int)(re - rb);
+        if (PREC == LB_FP64) {
+          double t = 0.0;
+          for (int q = 0; q < len; ++q) t = fma((double)sval[qv + q], __ldg(x + scol[qc + q]), t);
+          y = t;
+        } else {
+          float t = 0.f;
+          for (int q = 0; q < len; ++q) t = fmaf((float)sval[qv + q], __ldg(x32 + scol[qc + q]), t);
+          y = (double)t;
+        }
+      } else if (PREC == LB_FP64) {
+        double t = 0.0;
+#pragma unroll 4
+        for (int64_t q = rb; q < re; ++q) t = fma((double)__ldcs(vv + q), __ldg(x + __ldcs(col + q)), t);
+        y = t;
+      } else {
+        float t = 0.f;
+#pragma unroll 4
+        for (int64_t q = rb; q < re; ++q) t = fmaf((float)__ldcs(vv + q), __ldg(x32 + __ldcs(col + q)), t);
+        y = (double)t;
+      }
+      const double k = y + kf;
+      double nx;
+      if (STAGE == 1) {
+        acc[s] = k;
+        nx = vs + 0.5 * h * k;
+      } else if (STAGE == 2) {
+        acc[s] = ac + 2.0 * k;
+        nx = vs + 0.5 * h * k;
+      } else if (STAGE == 3) {
+        acc[s] = ac + 2.0 * k;
+        nx = vs + h * k;
+      } else {
+        nx = vs + (h / 6.0) * (ac + k);
+        v[s] = nx;
+      }
+      if (PREC == LB_FP64)
+        xn[s] = nx;
+      else
+        xn32[s] = (float)nx;
+    }
+    __syncthreads();  // buffer b is free
+    if (threadIdx.x == 0 && c + 2 * G < nch) issue(b, c + 2 * G, nb, ne);
+  }
+}
+
 // Row-group form, for long rows: W consecutive lanes share a row, so the
 // row's columns and values are read by consecutive lanes (coalesced), the
 // products are summed by W-lane shuffles, and every lane of the group forms
@@ -496,6 +730,7 @@ struct Work {
   double *X, *Y, *acc, *Keff;
   float *X32, *Y32;
   int64_t xstride;
+  int* err;  // set by a kernel whose bounded wait ran out
 };
 
 inline int64_t x32_stride(int64_t M) { return (M + 63) & ~int64_t(63); }
@@ -510,7 +745,8 @@ Work carve(void* base, int64_t M) {
   w.acc = reinterpret_cast<double*>(p); p += d;
   w.Keff = reinterpret_cast<double*>(p); p += d;
   w.X32 = reinterpret_cast<float*>(p); p += f;
-  w.Y32 = reinterpret_cast<float*>(p);
+  w.Y32 = reinterpret_cast<float*>(p); p += f;
+  w.err = reinterpret_cast<int*>(p);
   return w;
 }
 
@@ -596,16 +832,55 @@ cudaError_t run_steps_csr(int64_t M, const int64_t* rowptr, const int32_t* col, 
   using V = typename std::conditional<PREC == LB_FP64, double, float>::type;
   const int cap = csr_stage_cap(nnz, M, sizeof(V) + sizeof(int32_t));
   const size_t smem = (sizeof(V) + sizeof(int32_t)) * (size_t)cap;
-  if (W == 1) {
-    e = cudaFuncSetAttribute(k_stage_csr_blk<PREC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_stage_csr_blk<PREC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_stage_csr_blk<PREC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_stage_csr_blk<PREC, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // short rows: the pipelined kernel when the arrays allow 16-byte bulk
+  // copies (the library's own arrays always do), else the block-staged one
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  const bool pipe = W == 1 && al16(col) && al16(val) && al16(rowptr) && al16(v);
+  // its staging capacity: the largest range of a chunk of 256 rows, when two
+  // buffers of it stay within 112 KB (chunks above the capacity are summed
+  // from global memory)
+  int pcap = 0;
+  if (pipe) {
+    e = cudaMemsetAsync(w.err, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+      k_chunk_max_range<<<(unsigned)(((M + 255) / 256 + 255) / 256), 256, 0, st>>>(M, rowptr, w.err);
+      lbi::note_launch(1);
+      int mx = 0;
+      e = cudaMemcpyAsync(&mx, w.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      const int lim = (int)((56 * 1024 - kPipeRowBytes) / (sizeof(V) + sizeof(int32_t))) - 16;
+      pcap = ((mx < lim ? mx : lim) + 7) & ~7;
+    }
     if (e != cudaSuccess) return e;
   }
+  const size_t psmem = 2 * csr_pipe_buf_bytes<V>(pcap);
+  unsigned pgrid = 0;
+  if (W == 1) {
+    auto attr = [&](const void* k, size_t bytes) {
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    if (pipe) {
+      attr((const void*)k_stage_csr_pipe<PREC, 1>, psmem);
+      attr((const void*)k_stage_csr_pipe<PREC, 2>, psmem);
+      attr((const void*)k_stage_csr_pipe<PREC, 3>, psmem);
+      attr((const void*)k_stage_csr_pipe<PREC, 4>, psmem);
+      int dev = 0, sms = 0, per = 0;
+      if (e == cudaSuccess) e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_stage_csr_pipe<PREC, 1>, 256, psmem);
+      const int64_t nch = (M + 255) / 256, resident = (int64_t)sms * (per > 0 ? per : 1);
+      pgrid = (unsigned)(nch < resident ? nch : resident);
+    } else {
+      attr((const void*)k_stage_csr_blk<PREC, 1>, smem);
+      attr((const void*)k_stage_csr_blk<PREC, 2>, smem);
+      attr((const void*)k_stage_csr_blk<PREC, 3>, smem);
+      attr((const void*)k_stage_csr_blk<PREC, 4>, smem);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaMemsetAsync(w.err, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
   auto stage = [&](auto stage_c, const double* xc, const float* xc32, double* xn, float* xn32) {
     constexpr int S = decltype(stage_c)::value;
     switch (W) {
@@ -625,8 +900,12 @@ cudaError_t run_steps_csr(int64_t M, const int64_t* rowptr, const int32_t* col, 
         k_stage_csr_grp<PREC, S, 32><<<ggrid, 256, 0, st>>>(M, rowptr, col, val, w.Keff, xc, xc32, xn, xn32, w.acc, v, dt);
         break;
       default:
-        k_stage_csr_blk<PREC, S><<<grid, 256, smem, st>>>(M, rowptr, col, val, cap, w.Keff, xc, xc32, xn, xn32,
-                                                          w.acc, v, dt);
+        if (pipe)
+          k_stage_csr_pipe<PREC, S><<<pgrid, 256, psmem, st>>>(M, nnz, rowptr, col, val, pcap, w.Keff, xc, xc32, xn,
+                                                               xn32, w.acc, v, dt, w.err);
+        else
+          k_stage_csr_blk<PREC, S><<<grid, 256, smem, st>>>(M, rowptr, col, val, cap, w.Keff, xc, xc32, xn, xn32,
+                                                            w.acc, v, dt);
     }
   };
   for (int64_t t = 0; t < nsteps; ++t) {
@@ -640,7 +919,14 @@ cudaError_t run_steps_csr(int64_t M, const int64_t* rowptr, const int32_t* col, 
     stage(std::integral_constant<int, 4>{}, w.Y, w.Y32, w.X, w.X32);
     lbi::note_launch(4);
   }
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !pipe) return e;
+  // a bounded wait of the pipelined kernel that ran out
+  int flag = 0;
+  e = cudaMemcpyAsync(&flag, w.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && flag) e = cudaErrorLaunchTimeout;
+  return e;
 }
 
 // eps(t) periodic with period T: seg_eps[k] for (t mod T) in
@@ -742,7 +1028,7 @@ cudaError_t pack_bf16(int64_t M, const double* A, uint16_t* Ab, float* scale, cu
 }
 
 size_t rk4_workspace_bytes(int64_t M) {
-  return 4 * align256(sizeof(double) * (size_t)M) + 2 * sizeof(float) * 4 * (size_t)x32_stride(M);
+  return 4 * align256(sizeof(double) * (size_t)M) + 2 * sizeof(float) * 4 * (size_t)x32_stride(M) + 256;
 }
 
 cudaError_t rk4_dense(int64_t M, int precision, const void* Ap, const float* scale,
