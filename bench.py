@@ -769,7 +769,7 @@ def form_sparse(args, dev):
     B.close()
     return {"N": N, "M": M, "nnz": nnz, "row_terms": c.terms, "assembly_s": t_asm,
             "rk4_fp32c_steps_per_s": n / (res["fp32"] * 1e-3), "rk4_fp64_steps_per_s": n / (res["fp64"] * 1e-3),
-            "rk4_roofline": {"kernel": "k_stage_csr_blk (CSR SpMV with the block's column/value range staged in shared memory, fused with the stage update)", "bound": "hbm",
+            "rk4_roofline": {"kernel": "k_stage_csr_pipe (persistent CSR SpMV + stage update; each chunk of 256 rows staged two chunks ahead by cp.async.bulk with an evict-first L2 policy)", "bound": "hbm",
                              "achieved": gbs["fp32"], "peak": hbm, "unit": "GB/s",
                              "frac": gbs["fp32"] / hbm if hbm else None,
                              "algorithmic_bytes_per_step": step_bytes["fp32"],

@@ -132,6 +132,36 @@ def test_ladder_rk4_csr_matches_oracle():
         assert err32 < 1e-6, err32
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_pipelined_stage_equals_block_staged(precision):
+    """N = 800 (M = 639,999: about three chunks of 256 rows per resident
+    block, so both staging buffers are reused and the phase parity flips):
+    the bulk-copy pipelined stage (16-byte aligned v) and the block-staged
+    stage (v one element off that alignment) sum in the same order and give
+    the same bits."""
+    N, dt, steps = 800, 2e-4, 12
+    H, L, g = wl.ladder_model(N, 801)
+    lb = lbm()
+    with lb.Basis(N) as B:
+        ch, _ = _channels_ladder(B, L, g)
+        h = B.expand(torch.tensor(H, device="cuda")).real.contiguous()
+        c = lb.Csr(B, h=h, channels=ch)
+        v0 = B.expand(torch.tensor(wl.pure_state(N, N // 2), device="cuda")).real.contiguous()
+        va = v0.clone()
+        assert va.data_ptr() % 16 == 0
+        raw = torch.empty(B.M + 1, dtype=torch.float64, device="cuda")
+        vb = raw[1:]
+        assert vb.data_ptr() % 16 == 8
+        vb.copy_(v0)
+        c.rk4(va, dt, steps, precision=precision, correct_every=5 if precision == "fp32" else 0)
+        c.rk4(vb, dt, steps, precision=precision, correct_every=5 if precision == "fp32" else 0)
+        torch.cuda.synchronize()
+        assert torch.isfinite(va).all()
+        assert torch.equal(va, vb)
+        assert not torch.equal(va, v0)
+        c.close()
+
+
 def test_ladder_n2000_pattern_size_and_death_process():
     """M = 3,999,999: nnz(Q + R) = 7N^2 - 11N + 1; with H diagonal the
     populations follow p_n(t) = C(n0,n) e^{-g n t}(1 - e^{-g t})^{n0-n}."""
