@@ -447,6 +447,7 @@ __global__ void __launch_bounds__(128) k_kvec_diag_g(BasisView B, AView A, doubl
 }
 
 __device__ __forceinline__ void warp_prefix(double* arr, int n);  // below
+__device__ __forceinline__ void warp_suffix(const double* x, double* y, int n);  // below
 
 __global__ void __launch_bounds__(256) k_kvec_diag(BasisView B, const double* __restrict__ G,
                                                     double* __restrict__ K) {
@@ -1441,40 +1442,30 @@ __global__ void __launch_bounds__(256) k_dd_cells(BasisView B, DDTables T, doubl
   if (Aout) Aout[o] = r;
 }
 
-// H = D X D^T for X = the D x D block of a (real and imaginary parts),
-// D[k][l] = delta_k(l): row k of D X, then row k of H.  One block per k.
-// H lets the same-edge kernel evaluate its D-section sums
-// sum_{nu,mu} z_nu X[nu][mu] g_mu with z, g in {D^T (e_a +- e_b)} in O(1).
-__global__ void __launch_bounds__(128) k_dh(BasisView B, AView A, double* __restrict__ Hr, double* __restrict__ Hi) {
-  extern __shared__ double hsh[];
-  const int N = B.N;
-  const int k = blockIdx.x;
-  double* DXr = hsh;      // [N], index mu
-  double* DXi = hsh + N;  // [N]
-  for (int mu = threadIdx.x; mu < N; mu += blockDim.x) {
-    double sr = 0.0, si = 0.0;
-    if (mu >= 1) {
-      for (int lam = imax(k, 1); lam < N; ++lam) {
-        const double w = dlt(B, k, lam);
-        const double2 a = ldA(A, d_index(B, lam), d_index(B, mu));
-        sr = fma(w, a.x, sr);
-        si = fma(w, a.y, si);
-      }
+// Tables of the D x D block X[lam][mu] = a[D_lam][D_mu] for the same-edge
+// entries' D-section sums: CXr[lam][mu] = c_lam Re X[lam][mu] and the
+// suffix sums SXi[k][mu] = sum_{lam >= k} c_lam Im X[lam][mu] (k = 0..N,
+// SXi[N][mu] = 0).  One block per column mu >= 1; row-major N-wide tables.
+__global__ void __launch_bounds__(128) k_dtab(BasisView B, AView A, double* __restrict__ CXr,
+                                              double* __restrict__ SXi) {
+  __shared__ double xi[lbi::kMaxDenseN];
+  __shared__ double sx[lbi::kMaxDenseN + 1];
+  const int N = B.N, mu = 1 + blockIdx.x;
+  for (int lam = threadIdx.x; lam < N; lam += blockDim.x) {
+    double cr = 0.0, ci = 0.0;
+    if (lam >= 1) {
+      const double c = ld_c(B, lam);
+      const double2 x = ldA(A, d_index(B, lam), d_index(B, mu));
+      cr = c * x.x;
+      ci = c * x.y;
     }
-    DXr[mu] = sr;
-    DXi[mu] = si;
+    CXr[(int64_t)lam * N + mu] = cr;
+    xi[lam] = ci;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    double hr = 0.0, hi = 0.0;
-    for (int mu = imax(j, 1); mu < N; ++mu) {
-      const double w = dlt(B, j, mu);
-      hr = fma(w, DXr[mu], hr);
-      hi = fma(w, DXi[mu], hi);
-    }
-    Hr[(int64_t)k * N + j] = hr;
-    Hi[(int64_t)k * N + j] = hi;
-  }
+  if (threadIdx.x < 32) warp_suffix(xi, sx, N);
+  __syncthreads();
+  for (int k = threadIdx.x; k <= N; k += blockDim.x) SXi[(int64_t)k * N + mu] = sx[k];
 }
 
 // Pair-pair entries whose edges share one vertex v: s on (v, p), n on (v, q).
@@ -2036,8 +2027,11 @@ __global__ void __launch_bounds__(256, 3) k_shared_closed(BasisView B, AView A, 
 // Closed-form k_pd (pair row s, diagonal columns D_nu) and, when K is
 // given, K_s.  Per row, with gs(x) = delta_as(x) - delta_bs(x), which is c_x
 // for as < x < bs, lc_as at x = as >= 1 and (1 + bs) c_bs at x = bs:
-//   YY[x] = Im a[partner(s)][D_x] and PCY, the prefix of c_x YY[x]; the
-//     sums of gs(x) YY[x] over x are PCY differences plus the two ends;
+//   YY[x] = Im a[partner(s)][D_x]; PCA, the prefix of c_x YY[x] over
+//     x > as (zero up to as), and SCY, the suffix of c_x YY[x]: the sums of
+//     gs(x) YY[x] over x are PCA values plus the two ends, and every sum
+//     takes only the entry's own terms (a difference of two prefixes would
+//     cancel other terms, with their rounding);
 //   the sum of 2 gs(x) c_x over x from max(lo_s, nu + 1) to bs is 2/(nu + 1)
 //     for as <= nu < bs and 0 otherwise (sum_{x=l}^{m} c_x^2 = 1/l - 1/(m + 1),
 //     lc_as c_as = -1/(as + 1), (1 + bs) c_bs^2 = 1/bs);
@@ -2063,9 +2057,11 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
   const int lo_s = imax(as, 1);
   const int L = N + 1;
   double* YY = sq;            // Im a[partner(s)][D_x]   (raw, index x)
-  double* PCY = sq + L;       // prefix of c_x YY[x]
+  double* PCA = sq + L;       // prefix of c_x YY[x] over x > as
   double* PU1 = sq + 2 * L;   // prefix over w of U1S
   double* RU1 = sq + 3 * L;   // U1S at w (raw)
+  double* CY = sq + 4 * L;    // c_x YY[x] (raw)
+  double* SCY = sq + 5 * L;   // suffix of c_x YY[x]: SCY[k] = sum_{x >= k}
   __shared__ double red[kPdRed][kRowThreads];
   __shared__ double cst[kPdRed + 1];  // totals, then sum_{x in [lo_s, bs]} gs(x) YY[x]
   // l = (v, w) sharing the vertex v with e(s): with bx = Re a(partner(l), k),
@@ -2080,7 +2076,9 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
   for (int x = threadIdx.x; x < N; x += blockDim.x) {
     const double y = x >= 1 ? ldA(A, sb, d_index(B, x)).y : 0.0;
     YY[x] = y;
-    PCY[x + 1] = x >= 1 ? ld_c(B, x) * y : 0.0;
+    const double cy = x >= 1 ? ld_c(B, x) * y : 0.0;
+    CY[x] = cy;
+    PCA[x + 1] = x > as ? cy : 0.0;
     if (x >= lo_s && x <= bs) t_c1 = fma(dlt(B, as, x) - dlt(B, bs, x), ldA(A, s, d_index(B, x)).x, t_c1);
     double u1s = 0.0, u1v[2];
     if (x != as && x != bs) {
@@ -2115,25 +2113,27 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
   red[1][threadIdx.x] = t_u2b;
   red[2][threadIdx.x] = t_c1;
   red[3][threadIdx.x] = t_ly;
-  if (threadIdx.x == 0) PCY[0] = PU1[0] = 0.0;
+  if (threadIdx.x == 0) PCA[0] = PU1[0] = 0.0;
   __syncthreads();
-  // warps 0, 1: the two prefix sums; warps 2, 3: the four block totals
+  // warps 0, 1, 2: the prefix sums PCA and PU1 and the suffix SCY; warp 3:
+  // the four block totals
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  static_assert(kRowThreads == 128 && kPdRed == 4, "four warps: two scans, four totals");
+  static_assert(kRowThreads == 128 && kPdRed == 4, "four warps: three scans, four totals");
   if (wid < 2) {
-    warp_prefix(wid == 0 ? PCY : PU1, N);
+    warp_prefix(wid == 0 ? PCA : PU1, N);
     if (wid == 0) {
       __syncwarp();
-      if (lane == 0) {  // sum_{x in [lo_s, bs]} gs(x) YY[x]: the two ends and a PCY difference
+      if (lane == 0) {  // sum_{x in [lo_s, bs]} gs(x) YY[x]: the two ends and the own terms between
         const double tas = as >= 1 ? ld_lc(B, as) * YY[as] : 0.0;
         const double tbs = (ld_c(B, bs) - ld_lc(B, bs)) * YY[bs];
-        cst[kPdRed] = (tas + tbs) + isum(PCY, as + 1, bs - 1);
+        cst[kPdRed] = (tas + tbs) + PCA[bs];
       }
     }
+  } else if (wid == 2) {
+    warp_suffix(CY, SCY, N);
   } else {
 #pragma unroll
-    for (int k2 = 0; k2 < 2; ++k2) {
-      const int r = 2 * (wid - 2) + k2;
+    for (int r = 0; r < kPdRed; ++r) {
       double t = (red[r][lane] + red[r][lane + 32]) + (red[r][lane + 64] + red[r][lane + 96]);
       t = warp_sum(t);
       if (lane == 0) cst[r] = t;
@@ -2147,7 +2147,6 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
   // the ends of sum_{x = lo_s}^{min(bs, nu - 1)} gs(x) YY[x]
   const double tas = as >= 1 ? ld_lc(B, as) * YY[as] : 0.0;
   const double tab = tas + (ld_c(B, bs) - ld_lc(B, bs)) * YY[bs];
-  const double pcy_lo = PCY[as + 1];
   // per entry about 18 FP64 instructions: signs and the exact factors 2 and
   // -1/2 are applied to the bits with integer operations
   const double hsb = h != nullptr ? __ldg(h + sb) : 0.0;
@@ -2157,12 +2156,12 @@ __global__ void __launch_bounds__(kRowThreads) k_pd_closed(BasisView B, AView A,
     const double gs = inr ? dlt(B, as, nu) - dlt(B, bs, nu) : 0.0;
     // l = D_lam: sum_{lam < nu} gs(lam) YY[lam] and sum_{lam > nu} 2 gs(lam) c_lam
     const int hi = imin(bs - 1, nu - 1);
-    double g1 = hi >= as + 1 ? PCY[hi + 1] - pcy_lo : 0.0;
+    double g1 = hi >= as + 1 ? PCA[hi + 1] : 0.0;
     g1 += nu > bs ? tab : (nu > as ? tas : 0.0);
     double accD = twice(cnu) * g1;
     if (nu >= as && nu < bs) accD = fma(YY[nu], twice(__ldg(B.inv + nu + 1)), accD);
     if (inr) {
-      double t2 = twice(isum(PCY, nu + 1, N - 1));
+      double t2 = twice(SCY[nu + 1]);
       if (nu != 1) t2 = fma(twice(cnu + ld_lc(B, nu)), YY[nu], t2);  // 2 (1 - nu) c_nu
       accD = fma(gs, t2, accD);
     }
@@ -2277,12 +2276,13 @@ __global__ void __launch_bounds__(kSameThreads) k_same(BasisView B, AView A, dou
 // edge at once.  For each (v, w) with w outside the edge the four values
 // a[(tj, (v', w))][(tk, (v', w))], tj, tk in {S, J}, are loaded once and
 // enter every (ts, tn, tl) term (the per-pair sums keep the order of one pair
-// at a time); the l = partner(s) part comes from H = D X D^T.  The block
-// also forms the entries' D-section part (by completeness, -+Re a of the
-// partner pair) and Q, and writes the four entries whole.
+// at a time); the l = partner(s) part sums the D x D block over the edge's
+// window from the tables of k_dtab.  The block also forms the entries'
+// D-section part (by completeness, -+Re a of the partner pair) and Q, and
+// writes the four entries whole.
 __global__ void __launch_bounds__(kSameThreads) k_same_closed(BasisView B, AView A, const double* __restrict__ h,
-                                                              const double* __restrict__ Hr,
-                                                              const double* __restrict__ Hi,
+                                                              const double* __restrict__ CXr,
+                                                              const double* __restrict__ SXi,
                                                               double* __restrict__ Aout, double* __restrict__ Qout,
                                                               double* __restrict__ Rout) {
   __shared__ double red[5][kSameThreads];  // per thread: the four entries' sums, the Q sum
@@ -2320,20 +2320,43 @@ __global__ void __launch_bounds__(kSameThreads) k_same_closed(BasisView B, AView
       }
     }
   }
-  // (B) l = partner(s): k = D_mu, j = D_nu, from the entries of H = D X D^T
-  double accD[4] = {0.0, 0.0, 0.0, 0.0};
-  if (threadIdx.x == 0) {
-    const int64_t aa = (int64_t)a * N + a, ab_ = (int64_t)a * N + b, ba = (int64_t)b * N + a,
-                  bb = (int64_t)b * N + b;
-#pragma unroll
-    for (int combo = 0; combo < 4; ++combo) {
-      const int ts = combo >> 1, tn = combo & 1;
-      const double sgs = ts == kS ? -1.0 : 1.0;
-      if (ts != tn)  // n = partner(s) = l: d-fibre
-        accD[combo] = -sgs * ((Hi[aa] - Hi[ab_]) + (Hi[ba] - Hi[bb]));
-      else
-        accD[combo] = sgs * (tn == kS ? -1.0 : 1.0) * ((Hr[aa] - Hr[ab_]) - (Hr[ba] - Hr[bb]));
+  // (B) l = partner(s): k = D_mu, j = D_lam, summed over the entry's own
+  // terms only.  With g = D^T (e_a - e_b) (support W = [max(a, 1), b]:
+  // lc_a at a, c_mu between, c_b - lc_b at b) and h = D^T (e_a + e_b):
+  //   f-fibre (ts = tn): sum_{mu in W} g_mu sum_{lam in W} g_lam Re X[lam][mu],
+  //   d-fibre (ts != tn): sum_{mu in W} g_mu sum_lam h_lam Im X[lam][mu],
+  // the inner d sum from suffix sums over lam > a and lam > b (every term of
+  // them enters; h vanishes only at lam = 1 for the edge (0, 1)), the inner
+  // f sum term by term over the window (a difference of two longer sums
+  // would cancel terms outside it, with their rounding).
+  double tf = 0.0, td = 0.0;
+  {
+    const int lo = imax(a, 1);
+    for (int mu = lo + threadIdx.x; mu <= b; mu += blockDim.x) {
+      const double gmu = dlt(B, a, mu) - dlt(B, b, mu);
+      const double2 xb = ldA(A, d_index(B, b), d_index(B, mu));
+      const double2 xa = a >= 1 ? ldA(A, d_index(B, a), d_index(B, mu)) : make_double2(0.0, 0.0);
+      double inner = (ld_c(B, b) - ld_lc(B, b)) * xb.x;
+      for (int lam = a + 1; lam < b; ++lam) inner += CXr[(int64_t)lam * N + mu];
+      if (a >= 1) inner = fma(ld_lc(B, a), xa.x, inner);
+      tf = fma(gmu, inner, tf);
+      double j;
+      if (a == 0 && b == 1) {
+        j = twice(SXi[(int64_t)2 * N + mu]);
+      } else {
+        j = SXi[(int64_t)(a + 1) * N + mu] + SXi[(int64_t)(b + 1) * N + mu];
+        j = fma(ld_lc(B, b), xb.y, j);
+        if (a >= 1) j = fma(ld_lc(B, a), xa.y, j);
+      }
+      td = fma(gmu, j, td);
     }
+  }
+  double accD[4];
+#pragma unroll
+  for (int combo = 0; combo < 4; ++combo) {
+    const int ts = combo >> 1, tn = combo & 1;
+    const double sgs = ts == kS ? -1.0 : 1.0;
+    accD[combo] = ts != tn ? -sgs * td : sgs * (tn == kS ? -1.0 : 1.0) * tf;
   }
   // Q of the type-changing pairs: sum_lam h_{D_lam} f(D_lam, J_ab, S_ab) over
   // lam in [max(a, 1), b], f = delta_b(lam) - delta_a(lam); the lam < b terms
@@ -2501,7 +2524,7 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
   // 1: pair x diagonal
   if (dense_out && e == cudaSuccess) {
     if (closed) {
-      const size_t smem = sizeof(double) * 4 * (size_t)(N + 1);
+      const size_t smem = sizeof(double) * 6 * (size_t)(N + 1);
       e = cudaFuncSetAttribute(k_pd_closed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess) k_pd_closed<<<(unsigned)P2, kRowThreads, smem, st>>>(B, av, h, A, Q, R, K);
     } else {
@@ -2518,7 +2541,7 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
     note_launch(1);
   }
   mark(3);
-  // closed: stream-ordered scratch for H (same edge), the vertex sums of K's
+  // closed: stream-ordered scratch for the D x D tables (same edge), the vertex sums of K's
   // diagonal rows and the diagonal x diagonal tables
   double* scratch = nullptr;
   const size_t dd_at = 3 * (size_t)N * N + N;
@@ -2562,10 +2585,14 @@ cudaError_t assemble_dense(const lb::BasisView& B, const double* h, const double
   //    block of a (stream-ordered scratch)
   if ((closed ? dense_out : (A || R)) && e == cudaSuccess) {
     if (closed) {
-      double* H = scratch + (size_t)N * N;
-      k_dh<<<(unsigned)N, 128, sizeof(double) * 2 * (size_t)N, st>>>(B, av, H, H + (size_t)N * N);
-      k_same_closed<<<(unsigned)B.P, kSameThreads, 0, st>>>(B, av, h, H, H + (size_t)N * N, A, Q, R);
-      note_launch(2);
+      double* CXr = scratch;                     // N x N
+      double* SXi = scratch + (size_t)N * N;     // (N + 1) x N
+      if (N >= 2) {
+        k_dtab<<<(unsigned)(N - 1), 128, 0, st>>>(B, av, CXr, SXi);
+        note_launch(1);
+      }
+      k_same_closed<<<(unsigned)B.P, kSameThreads, 0, st>>>(B, av, h, CXr, SXi, A, Q, R);
+      note_launch(1);
     } else {
       k_same<<<(unsigned)B.P, kSameThreads, sizeof(double) * 2 * N, st>>>(B, av, A, R);
       note_launch(1);

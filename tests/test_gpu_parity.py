@@ -418,6 +418,33 @@ def test_closed_assembly_mixed_magnitude_kossakowski(N, exps, zero_frac):
     assert np.abs(g["K"] - K).max() <= 1e-12 * np.abs(K).max()
 
 
+@pytest.mark.parametrize("N,seed", [(12, 0), (16, 1), (21, 2)])
+def test_pair_diagonal_entries_own_terms_only(N, seed):
+    """Pair x diagonal rows (s, D_nu): their D-section sums run over the
+    D_x of a window of x set by s and nu.  A Kossakowski matrix whose
+    pair x D blocks are scaled by 2^eD(x) with eD = +-14 per D_x, and whose
+    pair x pair block is 2^-40 (so the D-section terms dominate every
+    entry's scale S), puts terms 2^28 apart inside and outside each window:
+    the closed form must not form a window sum as a difference of two wider
+    sums, whose rounding would be relative to the terms outside."""
+    W = wl.wishart_kossakowski(N, 3500 + seed)
+    g = np.random.default_rng(3600 + seed)
+    P = N * (N - 1) // 2
+    eD = g.choice([-14.0, 14.0], N - 1)
+    d = np.concatenate([np.full(2 * P, 2.0 ** -20), 2.0 ** eD])
+    a = (d[:, None] * W) * d[None, :]
+    H = wl.gue_hamiltonian(N, 3700 + seed)
+    with lbm().Basis(N) as B, Oracle(N) as o:
+        gsys = _gpu_system(B, H, a, "closed")
+        h, _ = o.expand(H)
+        Q = o.Q(h.real)
+        R, S = o.R(a, return_scale=True)
+        K = o.K(a)
+    _assert_entries(gsys["R"], R, S, "R")
+    _assert_entries(gsys["A"], Q + R, S + np.abs(Q), "A")
+    assert np.abs(gsys["K"] - K).max() <= 1e-12 * np.abs(K).max()
+
+
 @pytest.mark.parametrize("N", [12, 19])
 def test_closed_assembly_dense_ladder_kossakowski(N):
     """The ladder model's rank-one a = g l l^dagger given as a dense matrix:
