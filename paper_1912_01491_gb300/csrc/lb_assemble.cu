@@ -1649,8 +1649,8 @@ struct PairStage {
   const double* PY;  // [4][L] Im
   const double* TX;  // [2][L] Re a[D_mu][(p,q) t] (raw, index mu)
   const double* TY;  // [2][L] Im
-  const double* CX;  // [2][L] prefix of c_mu Re a[D_mu][(p,q) t]
-  const double* CY;  // [2][L] prefix of c_mu Im
+  const double* CX;  // [2][L] c_mu Re a[D_mu][(p,q) t]
+  const double* CY;  // [2][L] c_mu Im
   const double* DX;  // [2][L] (D x)_k = sum_mu delta_k(mu) Re a[D_mu][(p,q) t], k = 0..N-1
   const double* DY;  // [2][L] the same for Im
   const double* TOT; // [32] signed totals of the (A1) sums, see k_shared_closed
@@ -1881,22 +1881,23 @@ __global__ void __launch_bounds__(256, 3) k_shared_closed(BasisView B, AView A, 
     const double2 val = mu >= 1 ? ldA(A, d_index(B, mu), tt * P + ppq) : make_double2(0.0, 0.0);
     TX[tt * L + mu] = val.x;
     TY[tt * L + mu] = val.y;
-    CX[tt * L + mu + 1] = mu >= 1 ? ld_c(B, mu) * val.x : 0.0;
-    CY[tt * L + mu + 1] = mu >= 1 ? ld_c(B, mu) * val.y : 0.0;
+    CX[tt * L + mu] = mu >= 1 ? ld_c(B, mu) * val.x : 0.0;
+    CY[tt * L + mu] = mu >= 1 ? ld_c(B, mu) * val.y : 0.0;
   }
-  if (threadIdx.x < 4) (threadIdx.x < 2 ? CX + threadIdx.x * L : CY + (threadIdx.x - 2) * L)[0] = 0.0;
   __syncthreads();
   {
-    const int wi = threadIdx.x >> 5;  // warps 0..3 scan CX[0], CX[1], CY[0], CY[1]
-    if (wi < 4) warp_prefix(wi < 2 ? CX + wi * L : CY + (wi - 2) * L, N);
+    // warps 0..3: suffix sums of CX[0], CX[1], CY[0], CY[1] into the (not
+    // yet used) SU arrays: sums of the terms mu > k only, never a total
+    // minus the terms below k
+    const int wi = threadIdx.x >> 5;
+    if (wi < 4) warp_suffix(wi < 2 ? CX + wi * L : CY + (wi - 2) * L, SU + wi * L, N);
   }
   __syncthreads();
   // (D x)_k for the four staged D-column vectors: sum_{mu > k} c_mu x_mu + delta_k(k) x_k
   for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
     const int arr = t / N, k = t % N, tt = arr & 1;
-    const double* C = (arr < 2 ? CX : CY) + tt * L;
     const double* X = (arr < 2 ? TX : TY) + tt * L;
-    double d = C[N] - C[k + 1];  // mu from k + 1 to N - 1
+    double d = SU[arr * L + k + 1];  // mu from k + 1 to N - 1
     if (k >= 1) d += dlt(B, k, k) * X[k];
     (arr < 2 ? DXs : DYs)[tt * L + k] = d;
   }
