@@ -396,7 +396,11 @@ int lb_csr_copy(const lb_csr_t *c, int64_t *rowptr, int32_t *col, double *val, d
  * LB_FP64, or LB_FP32 values (converted once and cached in the handle) with
  * FP32 products and, if correct_every > 0, the FP64 defect
  * (A64 - A32) v added to K every correct_every steps.  v (device, M doubles)
- * in/out; work: lb_rk4_workspace_bytes(M) bytes of device memory. */
+ * in/out; work: lb_rk4_workspace_bytes(M) bytes of device memory.  With
+ * rows of fewer than 8 entries on average and a 16-byte aligned v, the
+ * stages stream their rows through shared memory by bulk copies with
+ * bounded waits; the call then returns after the steps have finished on
+ * `stream`, and LB_ETIMEOUT if a wait ran out. */
 int lb_rk4_csr(const lb_csr_t *c, int precision, int correct_every, double *v, double dt,
                int64_t nsteps, void *work, void *stream);
 

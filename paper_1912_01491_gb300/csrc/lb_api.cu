@@ -88,7 +88,8 @@ void set_error(const char* fmt, ...) {
 
 int cuda_fail(cudaError_t e, const char* what) {
   set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
-  return LB_ECUDA;
+  // the library's kernels report a bounded wait that ran out as a launch timeout
+  return e == cudaErrorLaunchTimeout ? LB_ETIMEOUT : LB_ECUDA;
 }
 
 }  // namespace lbi
