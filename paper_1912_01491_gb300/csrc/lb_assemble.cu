@@ -1744,21 +1744,19 @@ __device__ __forceinline__ double shared_entry_const(const PairStage& S, int tr,
   return fma(-0.25, acc2, kNegHalfInvSqrt2 * accD);
 }
 
-// The terms at v of the same entry: returns (acc2, accD) to be scaled as in
-// shared_entry_const.
+// The terms at v of the same entry, to be scaled as in shared_entry_const:
+// t[0..7] the signed terms of acc2 ((A1) at v, then (A2)), and accD (t[8],
+// t[9] are left to the caller).
 __device__ __forceinline__ void shared_entry_var(const double2 (&X)[2][2], const PairStage& S, int tr, int P_,
-                                                 int Q_, int v, int ts, int tn, double& acc2, double& accD) {
+                                                 int Q_, int v, int ts, int tn, double (&t)[10], double& accD) {
   const int pv = P_ < v ? 1 : 0, qv = Q_ < v ? 1 : 0;
   const int a_ = coef_phase(ts, v, P_), b_ = coef_phase(tn, v, Q_);
-  // the sums start from their first term (an add to 0.0 is an FP64
-  // instruction of its own)
 #pragma unroll
   for (int tl = 0; tl < 2; ++tl) {  // (A1) at v
     const int tk = 1 ^ tl ^ ts, tjf = 1 ^ tl ^ tn, tjd = tl ^ tn;
     const SharedSigns g = shared_signs_a1(ts, tn, tl, a_, b_, pv, qv);
-    const double t1 = sgn_mul(-g.kf * g.sfv, S.sre(tr, tjf, tk, v));
-    acc2 = tl == 0 ? t1 : acc2 + t1;
-    acc2 += sgn_mul(g.kd * g.sdv, S.sim(tr, tjd, tk, v));
+    t[2 * tl] = sgn_mul(-g.kf * g.sfv, S.sre(tr, tjf, tk, v));
+    t[2 * tl + 1] = sgn_mul(g.kd * g.sdv, S.sim(tr, tjd, tk, v));
   }
 #pragma unroll
   for (int tl = 0; tl < 2; ++tl) {  // (A2)
@@ -1767,9 +1765,10 @@ __device__ __forceinline__ void shared_entry_var(const double2 (&X)[2][2], const
     const int base = coef_phase(tn, Q_, v) + coef_phase(tl, P_, Q_);
     const int sf = sgn_f(base + coef_phase(tjf, v, P_));
     const int sd = sgn_d(base + coef_phase(tjd, v, P_));
-    acc2 += sgn_mul(sk * sf, X[tjf][tk].x);
-    acc2 -= sgn_mul(sk * sd, X[tjd][tk].y);
+    t[4 + 2 * tl] = sgn_mul(sk * sf, X[tjf][tk].x);
+    t[5 + 2 * tl] = sgn_mul(-sk * sd, X[tjd][tk].y);
   }
+  // accD starts from its first term (an add to 0.0 is an FP64 instruction of its own)
   const int vlo_q = v < Q_, vlo_p = v < P_;
 #pragma unroll
   for (int tl = 0; tl < 2; ++tl) {  // (A3) at v
@@ -1792,6 +1791,29 @@ __device__ __forceinline__ void shared_entry_var(const double2 (&X)[2][2], const
     const double pv_ = vlo_p ? part : -part;
     accD += ts == kS ? -pv_ : pv_;
   }
+}
+
+// -(t[0] + ... + t[7] + 2 t[8] + 2 t[9]) / 4, exactly rounded: the ten terms
+// in int64 fixed point at their largest exponent (see fx_split / fx_align;
+// truncation below 2^-57 of the largest term), one rounding at the end.
+// GB300's FP64 pipe takes a warp instruction in about 64 cycles of an SM
+// sub-partition against 2 for an integer one, so the ten-term sum costs the
+// FP64 pipe nothing.  false (and *out untouched) for values that are not
+// finite or too small for the exponent arithmetic.
+__device__ __forceinline__ bool fx_quarter_sum10(const double (&t)[10], double* out) {
+  int E = 1;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) E = max(E, fx_exponent(t[i]) + (i >= 8 ? 1 : 0));
+  if (E < 65 || E > 2040) return false;
+  long long s = 0;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    FxTerm f = fx_split(t[i]);
+    if (i >= 8) f.e += 1;  // 2 t[i]: the same significand one binade up
+    s += fx_align(f, E);
+  }
+  *out = quad_out(s, E - 1);  // -s/2 2^(E - 1 - 1080) = -(sum)/4
+  return true;
 }
 
 // Diagonal row D_nu, pair column n on {p, q} of type tn, in closed form: the
@@ -1998,11 +2020,21 @@ __global__ void __launch_bounds__(256, 3) k_shared_closed(BasisView B, AView A, 
         const int ts = combo >> 1, tn = combo & 1;
         const int sgs = ts == kS ? 1 : -1, sgn = tn == kS ? 1 : -1;
         // a_{partner(n) partner(s)} = conj(X[1-ts][1-tn]), a_{n partner(s)} = conj(X[1-ts][tn])
-        const double am = sgn_mul(sgs * sgn * cf, X[1 - ts][1 - tn].x) + sgn_mul(sgs * cd, X[1 - ts][tn].y);
-        double acc2, accD;
-        shared_entry_var(X, S, tr, P_, Q_, v, ts, tn, acc2, accD);
+        double tt[10], accD;
+        shared_entry_var(X, S, tr, P_, Q_, v, ts, tn, tt, accD);
+        tt[8] = sgn_mul(sgs * sgn * cf, X[1 - ts][1 - tn].x);
+        tt[9] = sgn_mul(sgs * cd, X[1 - ts][tn].y);
         const int ci = (((tr * 2 + ts) * 2 + tn) * 2 + (P_ < v ? 1 : 0)) * 2 + (Q_ < v ? 1 : 0);
-        const double r = CST[ci] + fma(-0.25, acc2, fma(kNegHalfInvSqrt2, accD, neg_half(am)));
+        // -acc2/4 - am/2 = -(acc2 + 2 am)/4 in fixed point; FP64 for the rare
+        // values outside its range
+        double q1;
+        if (!fx_quarter_sum10(tt, &q1)) {
+          double acc2 = tt[0];
+#pragma unroll
+          for (int i = 1; i < 8; ++i) acc2 += tt[i];
+          q1 = fma(-0.25, acc2, neg_half(tt[8] + tt[9]));
+        }
+        const double r = fma(kNegHalfInvSqrt2, accD, CST[ci] + q1);
         const int tm = 1 ^ tn ^ ts;
         const int ph = coef_phase(ts, v, P_) + coef_phase(tm, P_, Q_) + coef_phase(tn, Q_, v);
         const double qv = (ph & 1) ? sgn_mul(sgn_f(ph), hq[tm]) : 0.0;
