@@ -452,6 +452,19 @@ def fp64_checks(lb, B, A, K, states, restart=0, max_iter=3000, H=None, plain_max
             "note": "FP64 on the device: restarted GMRES for (Q + R) v* = -K, and rho rebuilt from v"}
 
 
+def upload_bytes(M, pinned):
+    """Bytes of a that lb_assemble moves to the device: the upper triangle of
+    a page-locked a, read over the host link; a pageable a crosses in row
+    blocks of h rows (columns from the block's first row on) for M > 2048,
+    whole otherwise."""
+    if pinned:
+        return 16 * (M * (M + 1) // 2)
+    if M > 2048:
+        h = max(256, (M + 63) // 64)
+        return sum(16 * (min(M, j0 + h) - j0) * (M - j0) for j0 in range(0, M, h))
+    return 16 * M * M
+
+
 def run_e2e(args, lb, B, a, H_host, M, nrk, dt, dev, dist, world):
     """Same metric through lb_assemble / lb_integrate with host buffers."""
     import numpy as np
@@ -484,16 +497,7 @@ def run_e2e(args, lb, B, a, H_host, M, nrk, dt, dev, dist, world):
     pinned = a_host.is_pinned()
     del a_host
     lb.native.host_release()
-    # lb_assemble reads the upper triangle of a page-locked a over the host
-    # link; a pageable a would cross in row blocks of h rows (columns from the
-    # block's first row on) for M > 2048, whole otherwise
-    if pinned:
-        a_bytes = 16 * (M * (M + 1) // 2)
-    elif M > 2048:
-        h = max(256, (M + 63) // 64)
-        a_bytes = sum(16 * (min(M, j0 + h) - j0) * (M - j0) for j0 in range(0, M, h))
-    else:
-        a_bytes = 16 * M * M
+    a_bytes = upload_bytes(M, pinned)
     mean_ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]} if phases else {}
     spread = (max(t_asm) - min(t_asm)) / statistics.mean(t_asm) if t_asm else None
     return {"value": replica_value(world, args.steps * M * M, sa), "unit": "entries/s",
@@ -719,6 +723,19 @@ def form_spectrum(args, dev):
     return out
 
 
+def csr_step_bytes(precision, nnz, M):
+    """Algorithmic bytes of one CSR RK4 step (4 stages): values and columns
+    and the row pointers (int64) read once per stage; the stage vector
+    gathered once per stage (FP32 copy in FP32 mode); Keff and v read every
+    stage, v written once; acc written (stage 1), read and written (2, 3),
+    read (4); the next stage vector written every stage (FP32 copy only in
+    FP32 mode)."""
+    val = 4.0 if precision == "fp32" else 8.0
+    x = 4.0 if precision == "fp32" else 8.0
+    per_stage = nnz * (val + 4.0) + (M + 1) * 8.0 + M * (x + 8.0 + 8.0 + x)
+    return 4.0 * per_stage + 8.0 * M + 48.0 * M
+
+
 def form_sparse(args, dev):
     """Sparse ladder model: CSR assembly of Q + R and K, CSR RK4 (FP32 values
     with FP64 correction every 50 steps, and FP64)."""
@@ -756,12 +773,7 @@ def form_sparse(args, dev):
         torch.cuda.synchronize()
         res[prec] = ev[0].elapsed_time(ev[1])
     nnz = c.nnz
-    # per RK4 step (4 stages): values + columns and row pointers 4x; the stage
-    # vector gathered once per stage (FP32 or FP64); Keff and v read 4x, v
-    # written once; acc written (stage 1), read and written (2, 3), read (4);
-    # the next stage vector written 4x (FP32 copy only in FP32 mode)
-    step_bytes = {"fp32": 32.0 * nnz + 32.0 * (M + 1) + 16.0 * M + 32.0 * M + 40.0 * M + 48.0 * M + 16.0 * M,
-                  "fp64": 48.0 * nnz + 32.0 * (M + 1) + 32.0 * M + 32.0 * M + 40.0 * M + 48.0 * M + 32.0 * M}
+    step_bytes = {p: csr_step_bytes(p, nnz, M) for p in ("fp32", "fp64")}
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     gbs = {p: step_bytes[p] * n / (res[p] * 1e-3) / 1e9 for p in res}

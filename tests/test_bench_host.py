@@ -41,3 +41,35 @@ def test_stored_traffic_scales_with_quadruples():
     assert src and t200 > 0
     assert t100 / t200 == pytest.approx(math.comb(100, 4) / math.comb(200, 4))
     assert bench.ncu_traffic("k_pd (pair x diagonal)", 200) == (None, None)
+
+
+def test_csr_step_bytes_by_stage():
+    """The CSR RK4 step's algorithmic bytes, listed stage by stage."""
+    for nnz, M in [(27978001, 3999999), (7, 3), (0, 5)]:
+        for prec, val, x in [("fp32", 4, 4), ("fp64", 8, 8)]:
+            total = 0
+            for stage in (1, 2, 3, 4):
+                total += nnz * (val + 4)          # values and int32 columns
+                total += (M + 1) * 8              # int64 row pointers
+                total += M * x                    # gathered stage vector
+                total += M * 8 + M * 8            # Keff and v read
+                total += M * x                    # next stage vector written
+                total += M * {1: 8, 2: 16, 3: 16, 4: 8}[stage]  # acc
+                if stage == 4:
+                    total += M * 8                # v written
+            assert bench.csr_step_bytes(prec, nnz, M) == total
+    nnz, M = 27978001, 3999999
+    assert bench.csr_step_bytes("fp32", nnz, M) == 32 * nnz + 32 * (M + 1) + 152 * M
+
+
+def test_upload_bytes_cover_the_copied_region():
+    """Page-locked a: exactly the upper triangle.  Pageable a: the row blocks
+    of the copy engine, counted element by element on small cases."""
+    for M in (3, 99, 2500):
+        assert bench.upload_bytes(M, True) == 16 * M * (M + 1) // 2
+    assert bench.upload_bytes(2000, False) == 16 * 2000 * 2000
+    M = 4097
+    h = max(256, (M + 63) // 64)
+    count = sum((min(M, j0 + h) - j0) * (M - j0) for j0 in range(0, M, h))
+    assert bench.upload_bytes(M, False) == 16 * count
+    assert 16 * M * (M + 1) // 2 < bench.upload_bytes(M, False) < 16 * M * M
